@@ -1,0 +1,291 @@
+"""ctypes binding of the FP64 CPU oracle (``xpr_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the package entry's
+``smoke()`` check and by the benchmark's CPU-baseline leg.  The product path
+never imports it.
+
+Every function takes numpy arrays.  Camera and config constants are passed as
+their float32 values widened to float64, so that thresholds (1/255, 0.99,
+1e-4) are the same numbers on both sides; arithmetic is FP64 except the
+exact-FP32 binning mode.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xpr_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+_F64P = ctypes.POINTER(ctypes.c_double)
+_F32P = ctypes.POINTER(ctypes.c_float)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.oracle_project.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
+                                     _I32P, _I32P, _F64P, _F64P]
+        L.oracle_bin.argtypes = [ctypes.c_int64, _F64P, _F32P, _I32P, _F64P, _F64P, ctypes.c_int, _I32P, _U64P,
+                                 _U32P]
+        L.oracle_bin.restype = ctypes.c_int64
+        L.oracle_sort.argtypes = [ctypes.c_int64, _U64P, _U32P, ctypes.c_int64, _I32P]
+        L.oracle_render_tiles.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, ctypes.c_double,
+                                          _F64P, _F64P, _I32P, _I32P]
+        L.oracle_render_pixels.argtypes = [ctypes.c_int64, _F64P, _I32P, ctypes.c_int64, _F64P, ctypes.c_double,
+                                           ctypes.c_double, _F64P, _F64P, _I32P, _U64P]
+        L.oracle_render_bwd_brute.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_render_bwd_tiles.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_project_bwd.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
+                                         _F64P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_sh_basis.argtypes = [ctypes.c_int, _F64P, _F64P, _F64P]
+        L.oracle_cull_one.argtypes = [_F64P, ctypes.c_int, ctypes.c_int, _F64P, _F64P]
+        L.oracle_cull_one.restype = ctypes.c_int
+        L.oracle_abi_version.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32v(v) -> float:
+    return float(np.float32(v))
+
+
+def cam_array(cam) -> np.ndarray:
+    """[W, H, fx, fy, cx, cy, V(12), z_near] with float32-rounded values."""
+    vm = np.asarray(cam.viewmat, np.float32).reshape(12).astype(np.float64)
+    return np.array([cam.width, cam.height, _f32v(cam.fx), _f32v(cam.fy), _f32v(cam.cx), _f32v(cam.cy), *vm,
+                     _f32v(cam.z_near)], np.float64)
+
+
+def cfg_array(cfg) -> np.ndarray:
+    """[tile_w, tile_h, alpha_t, alpha_max, t_eps, dilation, clip, sh_degree, bg(3)]."""
+    return np.array([cfg.tile_w, cfg.tile_h, _f32v(cfg.alpha_thresh), _f32v(cfg.alpha_max), _f32v(cfg.t_eps),
+                     _f32v(cfg.cov_dilation), _f32v(cfg.clip_factor), cfg.sh_degree,
+                     *[_f32v(b) for b in cfg.bg]], np.float64)
+
+
+def tiles_of(cam, cfg):
+    return (cam.width + cfg.tile_w - 1) // cfg.tile_w, (cam.height + cfg.tile_h - 1) // cfg.tile_h
+
+
+# --------------------------------------------------------------------------- projection
+
+def project(mu, scale, quat, opac, sh, cam, cfg):
+    """Projection (Listing 1 project).  Returns dict with rec[n,12] (f64),
+    bbox[n,4], tc[n], pre[n,4] (values before floor, tile units), cov[n,3]."""
+    mu, scale, quat, opac, sh = map(_f64, (mu, scale, quat, opac, sh))
+    n = mu.shape[0]
+    rec = np.zeros((n, 12), np.float64)
+    bbox = np.zeros((n, 4), np.int32)
+    tc = np.zeros(n, np.int32)
+    pre = np.zeros((n, 4), np.float64)
+    cov = np.zeros((n, 3), np.float64)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_project(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P), _p(sh, _F64P),
+                         _p(ca, _F64P), _p(fa, _F64P), _p(rec, _F64P), _p(bbox, _I32P), _p(tc, _I32P),
+                         _p(pre, _F64P), _p(cov, _F64P))
+    return dict(rec=rec, bbox=bbox, tc=tc, pre=pre, cov=cov)
+
+
+def project_scene(scene, cam, cfg):
+    return project(scene.mu, scene.scale, scene.quat, scene.opacity, scene.sh, cam, cfg)
+
+
+def project_bwd(mu, scale, quat, opac, sh, cam, cfg, d_rec):
+    mu, scale, quat, opac, sh, d_rec = map(_f64, (mu, scale, quat, opac, sh, d_rec))
+    n = mu.shape[0]
+    dmu = np.zeros((n, 3))
+    ds = np.zeros((n, 3))
+    dq = np.zeros((n, 4))
+    do = np.zeros(n)
+    dsh = np.zeros_like(sh)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_project_bwd(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P),
+                             _p(sh, _F64P), _p(ca, _F64P), _p(fa, _F64P), _p(d_rec, _F64P), _p(dmu, _F64P),
+                             _p(ds, _F64P), _p(dq, _F64P), _p(do, _F64P), _p(dsh, _F64P))
+    return dict(mu=dmu, scale=ds, quat=dq, opacity=do, sh=dsh)
+
+
+# --------------------------------------------------------------------------- binning / sort
+
+def bin_pairs(rec, bbox, cam, cfg, exact32: bool):
+    """Replicate + tile ID + cull in primitive order.  With exact32, ``rec``
+    must be float32 records (the decision is taken in FP32)."""
+    bbox = np.ascontiguousarray(bbox, np.int32)
+    n = bbox.shape[0]
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    r64 = None if exact32 else _f64(rec)
+    r32 = np.ascontiguousarray(rec, np.float32) if exact32 else None
+    counts = np.zeros(n, np.int32)
+    total = lib().oracle_bin(n, _p(r64, _F64P), _p(r32, _F32P), _p(bbox, _I32P), _p(ca, _F64P), _p(fa, _F64P),
+                             int(exact32), _p(counts, _I32P), None, None)
+    keys = np.zeros(max(total, 1), np.uint64)
+    vals = np.zeros(max(total, 1), np.uint32)
+    lib().oracle_bin(n, _p(r64, _F64P), _p(r32, _F32P), _p(bbox, _I32P), _p(ca, _F64P), _p(fa, _F64P),
+                     int(exact32), _p(counts, _I32P), _p(keys, _U64P), _p(vals, _U32P))
+    return counts, keys[:total].copy(), vals[:total].copy()
+
+
+def sort_pairs(keys, vals, n_tiles):
+    keys = np.array(keys, np.uint64, copy=True)
+    vals = np.array(vals, np.uint32, copy=True)
+    ranges = np.zeros((n_tiles, 2), np.int32)
+    kk = keys if keys.size else np.zeros(1, np.uint64)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    lib().oracle_sort(keys.size, _p(kk, _U64P), _p(vv, _U32P), n_tiles, _p(ranges, _I32P))
+    return kk[:keys.size], vv[:vals.size], ranges
+
+
+def cull_one(rec_row, tx, ty, cam, cfg) -> bool:
+    r = _f64(rec_row)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    return bool(lib().oracle_cull_one(_p(r, _F64P), tx, ty, _p(ca, _F64P), _p(fa, _F64P)))
+
+
+# --------------------------------------------------------------------------- compositing
+
+def render_tiles(rec, vals, ranges, cam, cfg, delta: float = 0.0):
+    rec = _f64(rec)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    H, W = cam.height, cam.width
+    image = np.zeros((3, H, W))
+    tfin = np.zeros((H, W))
+    nc = np.zeros((H, W), np.int32)
+    band = np.zeros((H, W), np.int32)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_tiles(rec.shape[0], _p(rec, _F64P), _p(vv, _U32P), _p(ranges, _I32P), _p(ca, _F64P),
+                              _p(fa, _F64P), delta, _p(image, _F64P), _p(tfin, _F64P), _p(nc, _I32P),
+                              _p(band, _I32P))
+    return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool))
+
+
+def render_pixels(rec, pix, cfg, delta: float = 0.0, dz: float = 0.0):
+    """Brute-force walk over every visible primitive at the listed pixels."""
+    rec = _f64(rec)
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
+    m = pix.shape[0]
+    color = np.zeros((m, 3))
+    tfin = np.zeros(m)
+    band = np.zeros(m, np.int32)
+    sig = np.zeros(1, np.uint64)
+    fa = cfg_array(cfg)
+    lib().oracle_render_pixels(rec.shape[0], _p(rec, _F64P), _p(pix, _I32P), m, _p(fa, _F64P), delta, dz,
+                               _p(color, _F64P), _p(tfin, _F64P), _p(band, _I32P), _p(sig, _U64P))
+    return dict(color=color, t_final=tfin, band=band.astype(bool), sig=int(sig[0]))
+
+
+def render_brute(rec, cam, cfg, delta: float = 0.0, dz: float = 0.0):
+    """Brute-force image (every pixel, every visible primitive; Sec. 3.1)."""
+    H, W = cam.height, cam.width
+    ys, xs = np.mgrid[0:H, 0:W]
+    pix = np.stack([xs.ravel(), ys.ravel()], 1)
+    r = render_pixels(rec, pix, cfg, delta, dz)
+    return dict(image=r["color"].T.reshape(3, H, W), t_final=r["t_final"].reshape(H, W),
+                band=r["band"].reshape(H, W), sig=r["sig"])
+
+
+def render_bwd_brute(rec, cam, cfg, d_image):
+    rec = _f64(rec)
+    d_image = _f64(d_image)
+    d_rec = np.zeros((rec.shape[0], 12))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_bwd_brute(rec.shape[0], _p(rec, _F64P), _p(ca, _F64P), _p(fa, _F64P),
+                                  _p(d_image, _F64P), _p(d_rec, _F64P))
+    return d_rec
+
+
+def render_bwd_tiles(rec, vals, ranges, cam, cfg, d_image):
+    rec = _f64(rec)
+    d_image = _f64(d_image)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    d_rec = np.zeros((rec.shape[0], 12))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_bwd_tiles(rec.shape[0], _p(rec, _F64P), _p(vv, _U32P), _p(ranges, _I32P),
+                                  _p(ca, _F64P), _p(fa, _F64P), _p(d_image, _F64P), _p(d_rec, _F64P))
+    return d_rec
+
+
+def sh_basis(deg, d, with_grad=False):
+    d = _f64(d)
+    K = (deg + 1) ** 2
+    Y = np.zeros(16)
+    G = np.zeros(48) if with_grad else None
+    lib().oracle_sh_basis(deg, _p(d, _F64P), _p(Y, _F64P), _p(G, _F64P))
+    return (Y[:K], G[:3 * K].reshape(K, 3)) if with_grad else Y[:K]
+
+
+# --------------------------------------------------------------------------- whole pipelines
+
+def pipeline_tiled(scene, cam, cfg, delta: float = 0.0):
+    """FP64 tiled pipeline: project -> bin (FP64 cull) -> sort -> per-tile walk."""
+    pr = project_scene(scene, cam, cfg)
+    Wt, Ht = tiles_of(cam, cfg)
+    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False)
+    keys, vals, ranges = sort_pairs(keys, vals, Wt * Ht)
+    out = render_tiles(pr["rec"], vals, ranges, cam, cfg, delta)
+    out.update(proj=pr, keys=keys, vals=vals, ranges=ranges)
+    return out
+
+
+def loss_brute(scene_arrays, cam, cfg, w):
+    """sum(w * image) of the brute-force FP64 render; also the decision hash."""
+    mu, s, q, o, sh = scene_arrays
+    pr = project(mu, s, q, o, sh, cam, cfg)
+    r = render_brute(pr["rec"], cam, cfg)
+    return float((w * r["image"]).sum()), r["sig"]
+
+
+def grads_brute(scene_arrays, cam, cfg, d_image):
+    """Analytic FP64 gradients of sum(d_image * image) w.r.t. all parameters."""
+    mu, s, q, o, sh = scene_arrays
+    pr = project(mu, s, q, o, sh, cam, cfg)
+    d_rec = render_bwd_brute(pr["rec"], cam, cfg, d_image)
+    g = project_bwd(mu, s, q, o, sh, cam, cfg, d_rec)
+    g["d_rec"] = d_rec
+    return g
+
+
+def threads_used() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+if __name__ == "__main__":  # pragma: no cover
+    build(force="--force" in sys.argv)
+    print(_LIB, lib().oracle_abi_version())

@@ -1,0 +1,976 @@
+/*
+ * xpr_oracle.c -- plain FP64 CPU oracle of the 3DGS tile-splatting path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the package entry's smoke check and the
+ * benchmark's CPU-baseline leg use it.  It shares no code, header, table or
+ * helper with the CUDA library.
+ *
+ * What it computes (citations are to the paper, arXiv 2606.11529):
+ *   - projection of one 3D Gaussian (Sec. 2 "Preprocess", Listing 1 project,
+ *     Appendix "Implementation of XPR-3DGS"): Sigma = R S S^T R^T, EWA
+ *     footprint, conic, opacity-aware extents, tile bounding box, tile count,
+ *     visibility flag, view-dependent SH colour;
+ *   - the StopThePop tile cull of Listing 1 tile_cull (max response point of
+ *     the tile), in an FP64 form and in an exact-FP32 form whose operation
+ *     order is fixed and FMA-free (decisions taken in the kernel's precision);
+ *   - replicate / assign-tile-ID / sort / segment bounds of Sec. 4.2;
+ *   - front-to-back alpha compositing c = sum c_i a_i T_i (Sec. 2 "Shader",
+ *     Algorithm 1) with the evaluate of Listing 1, as a brute-force
+ *     all-primitives walk per pixel (the evaluate_full view of Sec. 3.1) and
+ *     as a per-tile walk over given lists;
+ *   - the analytic adjoint of compositing and of the projection, written from
+ *     the definitions (explicit suffix sums, explicit matrix-inverse
+ *     derivative), for checking the hand-written CUDA backward.
+ * Readings of points the paper leaves open (dilation 0.3 and Jacobian clamp
+ * 1.3, alpha clamp 0.99, T_eps 1e-4 tested before accumulating, raw pixel
+ * coordinates for 3DGS, extents sqrt(2 ln(o/a_t) Sigma_xx), SH convention)
+ * are taken as the config values passed in.
+ *
+ * Camera array (19 doubles): W, H, fx, fy, cx, cy, V[12] (world->camera 3x4
+ * row-major), z_near.  Config array (11 doubles): tile_w, tile_h, alpha_t,
+ * alpha_max, t_eps, dilation, clip, sh_degree, bg_r, bg_g, bg_b.
+ *
+ * Record layout (12 per primitive): mx, my, c00, c01, c11, o, r, g, b,
+ * depth, ln_thr, visible.  bbox (4 ints): xmin, ymin, xmax, ymax (tiles,
+ * half-open).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (no fast-math: the
+ * exact-FP32 cull relies on IEEE single rounding of every operation).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define O_PI 3.14159265358979323846
+
+typedef struct {
+    int W, H;
+    double fx, fy, cx, cy;
+    double V[12];
+    double z_near;
+} ocam;
+
+typedef struct {
+    int tw, th;
+    double at, amax, teps, dil, clip;
+    int deg;
+    double bg[3];
+} ocfg;
+
+static ocam read_cam(const double *c) {
+    ocam k;
+    k.W = (int)c[0];
+    k.H = (int)c[1];
+    k.fx = c[2];
+    k.fy = c[3];
+    k.cx = c[4];
+    k.cy = c[5];
+    for (int i = 0; i < 12; ++i) k.V[i] = c[6 + i];
+    k.z_near = c[18];
+    return k;
+}
+
+static ocfg read_cfg(const double *c) {
+    ocfg g;
+    g.tw = (int)c[0];
+    g.th = (int)c[1];
+    g.at = c[2];
+    g.amax = c[3];
+    g.teps = c[4];
+    g.dil = c[5];
+    g.clip = c[6];
+    g.deg = (int)c[7];
+    g.bg[0] = c[8];
+    g.bg[1] = c[9];
+    g.bg[2] = c[10];
+    return g;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Real spherical harmonics (Condon-Shortley phase), general degree.         */
+/* For a unit direction (x, y, z):                                           */
+/*   Y_l^0  = K_l^0 Q_l^0(z)                                                 */
+/*   Y_l^m  = sqrt2 K_l^m Q_l^m(z) Re((x+iy)^m)      m > 0                   */
+/*   Y_l^-m = sqrt2 K_l^m Q_l^m(z) Im((x+iy)^m)      m > 0                   */
+/* with Q_l^m(z) = P_l^m(z) / (1-z^2)^{m/2} (associated Legendre with the    */
+/* Condon-Shortley phase, divided by sin^m theta) and                        */
+/* K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!).  Index k = l^2 + l + m.        */
+/* ------------------------------------------------------------------------ */
+
+static double factorial(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= (double)i;
+    return f;
+}
+
+/* Q[l][m] for l, m <= deg+1 via the standard three-term recurrence. */
+static void legendre_q(int lmax, double z, double Q[6][6]) {
+    for (int m = 0; m <= lmax; ++m) {
+        /* Q_m^m = (-1)^m (2m-1)!! */
+        double qmm = 1.0;
+        for (int i = 1; i <= m; ++i) qmm *= -(2.0 * i - 1.0);
+        Q[m][m] = qmm;
+        if (m + 1 <= lmax) Q[m + 1][m] = z * (2.0 * m + 1.0) * qmm;
+        for (int l = m + 2; l <= lmax; ++l)
+            Q[l][m] = ((2.0 * l - 1.0) * z * Q[l - 1][m] - (double)(l + m - 1) * Q[l - 2][m]) / (double)(l - m);
+    }
+}
+
+/* Y[k] and, if grad != NULL, dY/d(x,y,z) as [k][3] for the polynomial
+ * extension above (the caller projects onto the sphere's tangent plane). */
+void oracle_sh_basis(int deg, const double *d, double *Y, double *grad) {
+    double x = d[0], y = d[1], z = d[2];
+    double Q[6][6];
+    memset(Q, 0, sizeof(Q));
+    legendre_q(deg + 1, z, Q);
+    /* powers (x+iy)^m = re[m] + i im[m] */
+    double re[6], im[6];
+    re[0] = 1.0;
+    im[0] = 0.0;
+    for (int m = 1; m <= deg + 1; ++m) {
+        re[m] = re[m - 1] * x - im[m - 1] * y;
+        im[m] = re[m - 1] * y + im[m - 1] * x;
+    }
+    for (int l = 0; l <= deg; ++l) {
+        for (int m = 0; m <= l; ++m) {
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * O_PI) * factorial(l - m) / factorial(l + m));
+            /* dQ_l^m/dz = -Q_l^{m+1} (Q_l^{l+1} = 0) */
+            double q = Q[l][m];
+            double dq = (m + 1 <= l) ? -Q[l][m + 1] : 0.0;
+            if (m == 0) {
+                int k = l * l + l;
+                Y[k] = K * q;
+                if (grad) {
+                    grad[3 * k + 0] = 0.0;
+                    grad[3 * k + 1] = 0.0;
+                    grad[3 * k + 2] = K * dq;
+                }
+            } else {
+                double s2k = sqrt(2.0) * K;
+                int kp = l * l + l + m, kn = l * l + l - m;
+                Y[kp] = s2k * q * re[m];
+                Y[kn] = s2k * q * im[m];
+                if (grad) {
+                    /* d/dx (x+iy)^m = m (x+iy)^{m-1};  d/dy = i m (x+iy)^{m-1} */
+                    grad[3 * kp + 0] = s2k * q * m * re[m - 1];
+                    grad[3 * kp + 1] = s2k * q * (-(double)m * im[m - 1]);
+                    grad[3 * kp + 2] = s2k * dq * re[m];
+                    grad[3 * kn + 0] = s2k * q * m * im[m - 1];
+                    grad[3 * kn + 1] = s2k * q * m * re[m - 1];
+                    grad[3 * kn + 2] = s2k * dq * im[m];
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection of one primitive (Listing 1 project; Sec. 2 Preprocess).       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double qn[4], qnorm;
+    double R[9];      /* primitive rotation */
+    double Sig[9];    /* 3D covariance */
+    double mc[3];     /* camera-space mean */
+    double ux, uy;    /* clamped x/z, y/z used by the Jacobian */
+    int clx, cly;     /* 1 if clamped */
+    double J[6];      /* 2x3 */
+    double Tm[6];     /* J * W (2x3) */
+    double cov[3];    /* a, b, c of Sigma_2D (dilated) */
+    double det;
+    double conic[3];
+    double mu2d[2];
+    double ln_thr, ex, ey;
+    double pre[4];    /* values before floor: (mx-ex)/w, (my-ey)/h, (mx+ex)/w, (my+ey)/h */
+    int bbox[4], tc, visible;
+    double dir[3], vlen; /* unit view direction and |mu - campos| */
+    double raw[3], rgb[3];
+} oproj;
+
+static void quat_rot(const double *q, double *qn, double *qnorm, double *R) {
+    double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    *qnorm = n;
+    double w = q[0] / n, x = q[1] / n, y = q[2] / n, z = q[3] / n;
+    qn[0] = w;
+    qn[1] = x;
+    qn[2] = y;
+    qn[3] = z;
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static void project_one(const double *mu, const double *s, const double *q, double o, const double *sh,
+                        const ocam *cam, const ocfg *cfg, oproj *P) {
+    memset(P, 0, sizeof(*P));
+    const double *V = cam->V;
+    /* world -> camera */
+    for (int i = 0; i < 3; ++i) P->mc[i] = V[4 * i] * mu[0] + V[4 * i + 1] * mu[1] + V[4 * i + 2] * mu[2] + V[4 * i + 3];
+    double x = P->mc[0], y = P->mc[1], z = P->mc[2];
+
+    /* Sigma = R S S^T R^T (Sec. 2) */
+    quat_rot(q, P->qn, &P->qnorm, P->R);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += P->R[3 * i + k] * s[k] * s[k] * P->R[3 * j + k];
+            P->Sig[3 * i + j] = acc;
+        }
+
+    /* view direction and SH colour, rgb = max(0, sum sh_k Y_k(d) + 0.5) */
+    double cp[3]; /* camera position = -R_v^T t */
+    for (int i = 0; i < 3; ++i) cp[i] = -(V[i] * V[3] + V[4 + i] * V[7] + V[8 + i] * V[11]);
+    double v[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
+    P->vlen = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int i = 0; i < 3; ++i) P->dir[i] = v[i] / P->vlen;
+    int K = (cfg->deg + 1) * (cfg->deg + 1);
+    double Y[16];
+    oracle_sh_basis(cfg->deg, P->dir, Y, NULL);
+    for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k) acc += sh[3 * k + c] * Y[k];
+        P->raw[c] = acc + 0.5;
+        P->rgb[c] = P->raw[c] > 0.0 ? P->raw[c] : 0.0;
+    }
+
+    if (!(z > cam->z_near)) { /* behind the near plane: nothing else is defined */
+        P->visible = 0;
+        return;
+    }
+
+    /* EWA: J = d(pixel)/d(camera point), x/z and y/z clamped to 1.3 x half-fov */
+    double limx = cfg->clip * (0.5 * cam->W / cam->fx);
+    double limy = cfg->clip * (0.5 * cam->H / cam->fy);
+    double rx = x / z, ry = y / z;
+    P->ux = clampd(rx, -limx, limx);
+    P->uy = clampd(ry, -limy, limy);
+    P->clx = (rx < -limx || rx > limx);
+    P->cly = (ry < -limy || ry > limy);
+    P->J[0] = cam->fx / z;
+    P->J[1] = 0.0;
+    P->J[2] = -cam->fx * P->ux / z;
+    P->J[3] = 0.0;
+    P->J[4] = cam->fy / z;
+    P->J[5] = -cam->fy * P->uy / z;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += P->J[3 * i + k] * V[4 * k + j];
+            P->Tm[3 * i + j] = acc;
+        }
+    double C2[4];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) acc += P->Tm[3 * i + k] * P->Sig[3 * k + l] * P->Tm[3 * j + l];
+            C2[2 * i + j] = acc;
+        }
+    P->cov[0] = C2[0] + cfg->dil;
+    P->cov[1] = 0.5 * (C2[1] + C2[2]);
+    P->cov[2] = C2[3] + cfg->dil;
+    P->det = P->cov[0] * P->cov[2] - P->cov[1] * P->cov[1];
+    P->mu2d[0] = cam->fx * rx + cam->cx;
+    P->mu2d[1] = cam->fy * ry + cam->cy;
+    if (!(P->det > 0.0) || !(o >= cfg->at)) {
+        P->visible = 0;
+        return;
+    }
+    P->conic[0] = P->cov[2] / P->det;
+    P->conic[1] = -P->cov[1] / P->det;
+    P->conic[2] = P->cov[0] / P->det;
+
+    /* opacity-aware extents of {alpha >= alpha_t}: |dx| <= sqrt(2 ln(o/a_t) Sigma_xx) */
+    P->ln_thr = log(o / cfg->at);
+    P->ex = sqrt(2.0 * P->ln_thr * P->cov[0]);
+    P->ey = sqrt(2.0 * P->ln_thr * P->cov[2]);
+    double r = P->ex > P->ey ? P->ex : P->ey;
+
+    /* half-open tile-space bounding box (Sec. 4.2) */
+    int Wt = (cam->W + cfg->tw - 1) / cfg->tw, Ht = (cam->H + cfg->th - 1) / cfg->th;
+    P->pre[0] = (P->mu2d[0] - P->ex) / cfg->tw;
+    P->pre[1] = (P->mu2d[1] - P->ey) / cfg->th;
+    P->pre[2] = (P->mu2d[0] + P->ex) / cfg->tw;
+    P->pre[3] = (P->mu2d[1] + P->ey) / cfg->th;
+    P->bbox[0] = (int)clampd(floor(P->pre[0]), 0.0, (double)Wt);
+    P->bbox[1] = (int)clampd(floor(P->pre[1]), 0.0, (double)Ht);
+    P->bbox[2] = (int)clampd(floor(P->pre[2]) + 1.0, 0.0, (double)Wt);
+    P->bbox[3] = (int)clampd(floor(P->pre[3]) + 1.0, 0.0, (double)Ht);
+    int tc = (P->bbox[2] - P->bbox[0]) * (P->bbox[3] - P->bbox[1]);
+    /* visible = det>0 & o>=a_t & r>0 & tc>0 & z>z_near (Listing 1) */
+    P->visible = (r > 0.0) && (tc > 0);
+    P->tc = P->visible ? tc : 0;
+    if (!P->visible) memset(P->bbox, 0, sizeof(P->bbox));
+}
+
+static void write_rec(const oproj *P, double o, double *rec) {
+    memset(rec, 0, 12 * sizeof(double));
+    rec[9] = P->mc[2];
+    if (!P->visible) return;
+    rec[0] = P->mu2d[0];
+    rec[1] = P->mu2d[1];
+    rec[2] = P->conic[0];
+    rec[3] = P->conic[1];
+    rec[4] = P->conic[2];
+    rec[5] = o;
+    rec[6] = P->rgb[0];
+    rec[7] = P->rgb[1];
+    rec[8] = P->rgb[2];
+    rec[10] = P->ln_thr;
+    rec[11] = 1.0;
+}
+
+/* Projection of n primitives.  rec[n*12], bbox[n*4], tc[n]; pre[n*4] and
+ * cov[n*3] (dilated Sigma_2D) may be NULL. */
+void oracle_project(int64_t n, const double *mu, const double *scale, const double *quat, const double *opac,
+                    const double *sh, const double *camv, const double *cfgv, double *rec, int32_t *bbox,
+                    int32_t *tc, double *pre, double *cov) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int K = (cfg.deg + 1) * (cfg.deg + 1);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        oproj P;
+        project_one(mu + 3 * i, scale + 3 * i, quat + 4 * i, opac[i], sh + (int64_t)3 * K * i, &cam, &cfg, &P);
+        write_rec(&P, opac[i], rec + 12 * i);
+        for (int j = 0; j < 4; ++j) bbox[4 * i + j] = P.bbox[j];
+        tc[i] = P.tc;
+        if (pre)
+            for (int j = 0; j < 4; ++j) pre[4 * i + j] = P.visible ? P.pre[j] : 0.0;
+        if (cov)
+            for (int j = 0; j < 3; ++j) cov[3 * i + j] = P.cov[j];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* StopThePop tile cull (Listing 1 tile_cull; Appendix 3DGS implementation). */
+/* The response o exp(-q/2), q = d^T conic d, d = mu - p, is largest at the  */
+/* point p of the tile closest to mu in the conic metric: mu itself when mu  */
+/* lies in the tile, else the best point of the (at most two) tile edges     */
+/* that face mu; on an edge the 1-D quadratic is minimised in closed form    */
+/* and clamped to the edge.  Keep iff q/2 <= ln(o / alpha_t).               */
+/* Tile bounds are inclusive pixel coordinates:                              */
+/*   x0 = tx w, x1 = min(tx w + w - 1, W - 1)  (same in y).                  */
+/* ------------------------------------------------------------------------ */
+
+static int cull_f64(double mx, double my, double c0, double c1, double c2, double lt, double x0, double y0,
+                    double x1, double y1) {
+    int outx = (mx < x0) || (mx > x1);
+    int outy = (my < y0) || (my > y1);
+    if (!outx && !outy) return 0.0 <= lt;
+    double best = INFINITY;
+    if (outx) {
+        double ex = mx < x0 ? x0 : x1;
+        double dx = mx - ex;
+        double ys = clampd(my + c1 * dx / c2, y0, y1);
+        double dy = my - ys;
+        double p = 0.5 * (c0 * dx * dx + 2.0 * c1 * dx * dy + c2 * dy * dy);
+        if (p < best) best = p;
+    }
+    if (outy) {
+        double ey = my < y0 ? y0 : y1;
+        double dy = my - ey;
+        double xs = clampd(mx + c1 * dy / c0, x0, x1);
+        double dx = mx - xs;
+        double p = 0.5 * (c0 * dx * dx + 2.0 * c1 * dx * dy + c2 * dy * dy);
+        if (p < best) best = p;
+    }
+    return best <= lt;
+}
+
+/* Same decision in IEEE single precision, one rounding per operation, in
+ * this exact order (the CUDA kernel takes the decision in FP32 with the same
+ * sequence of correctly rounded operations). */
+static float f32_q(float c0, float c1, float c2, float dx, float dy) {
+    float a = dx * dx;
+    a = a * c0;
+    float b = dx * dy;
+    b = b * c1;
+    b = b + b;
+    float c = dy * dy;
+    c = c * c2;
+    float sacc = a + b;
+    sacc = sacc + c;
+    return 0.5f * sacc;
+}
+
+static int cull_f32(float mx, float my, float c0, float c1, float c2, float lt, float x0, float y0, float x1,
+                    float y1) {
+    int outx = (mx < x0) || (mx > x1);
+    int outy = (my < y0) || (my > y1);
+    if (!outx && !outy) return 0.0f <= lt;
+    float best = INFINITY;
+    if (outx) {
+        float ex = mx < x0 ? x0 : x1;
+        float dx = mx - ex;
+        float t = c1 * dx;
+        t = t / c2;
+        float ys = my + t;
+        ys = fminf(fmaxf(ys, y0), y1);
+        float dy = my - ys;
+        float p = f32_q(c0, c1, c2, dx, dy);
+        best = fminf(best, p);
+    }
+    if (outy) {
+        float ey = my < y0 ? y0 : y1;
+        float dy = my - ey;
+        float t = c1 * dy;
+        t = t / c0;
+        float xs = mx + t;
+        xs = fminf(fmaxf(xs, x0), x1);
+        float dx = mx - xs;
+        float p = f32_q(c0, c1, c2, dx, dy);
+        best = fminf(best, p);
+    }
+    return best <= lt;
+}
+
+static void tile_bounds(int tx, int ty, const ocam *cam, const ocfg *cfg, double *b) {
+    int x0 = tx * cfg->tw, y0 = ty * cfg->th;
+    int x1 = x0 + cfg->tw - 1, y1 = y0 + cfg->th - 1;
+    if (x1 > cam->W - 1) x1 = cam->W - 1;
+    if (y1 > cam->H - 1) y1 = cam->H - 1;
+    b[0] = x0;
+    b[1] = y0;
+    b[2] = x1;
+    b[3] = y1;
+}
+
+/* Exposed for the dense-sampling pin of the cull (FP64 form). */
+int oracle_cull_one(const double *rec, int tx, int ty, const double *camv, const double *cfgv) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    double b[4];
+    tile_bounds(tx, ty, &cam, &cfg, b);
+    return cull_f64(rec[0], rec[1], rec[2], rec[3], rec[4], rec[10], b[0], b[1], b[2], b[3]);
+}
+
+static uint32_t f32_bits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+/* Replicate + assign tile ID + cull (Sec. 4.2).  For every primitive in
+ * index order and every slot r in 0..tc-1 of its bounding box (row-major:
+ * x = xmin + r mod w_i, y = ymin + r div w_i, t = y W' + x), keep the pair if
+ * the cull passes and emit key = (t << 32) | bits(float(depth)), val = i.
+ * exact32 != 0: rec32 (float records) with the FP32 cull; else rec64 with the
+ * FP64 cull.  counts[n] receives the surviving count per primitive.  keys and
+ * vals may be NULL (count only).  Returns the total. */
+int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const int32_t *bbox, const double *camv,
+                   const double *cfgv, int exact32, int32_t *counts, uint64_t *keys, uint32_t *vals) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw;
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t *bb = bbox + 4 * i;
+        int w = bb[2] - bb[0], h = bb[3] - bb[1];
+        int tc = (w > 0 && h > 0) ? w * h : 0;
+        int cnt = 0;
+        for (int r = 0; r < tc; ++r) {
+            int tx = bb[0] + r % w, ty = bb[1] + r / w;
+            double b[4];
+            tile_bounds(tx, ty, &cam, &cfg, b);
+            int keep;
+            float depth32;
+            if (exact32) {
+                const float *R = rec32 + 12 * i;
+                keep = cull_f32(R[0], R[1], R[2], R[3], R[4], R[10], (float)b[0], (float)b[1], (float)b[2],
+                                (float)b[3]);
+                depth32 = R[9];
+            } else {
+                const double *R = rec64 + 12 * i;
+                keep = cull_f64(R[0], R[1], R[2], R[3], R[4], R[10], b[0], b[1], b[2], b[3]);
+                depth32 = (float)R[9];
+            }
+            if (!keep) continue;
+            if (keys) {
+                keys[total] = ((uint64_t)(uint32_t)(ty * Wt + tx) << 32) | (uint64_t)f32_bits(depth32);
+                vals[total] = (uint32_t)i;
+            }
+            ++total;
+            ++cnt;
+        }
+        if (counts) counts[i] = cnt;
+    }
+    return total;
+}
+
+/* Sort (key, val) pairs ascending by key then val and find per-tile
+ * segment bounds [start, end) (Sec. 4.2, "Sort and identify bounds").
+ * ranges[n_tiles*2] is fully written (empty tiles get [0,0)). */
+typedef struct {
+    uint64_t k;
+    uint32_t v;
+} kv_t;
+
+static int kv_cmp(const void *a, const void *b) {
+    const kv_t *x = (const kv_t *)a, *y = (const kv_t *)b;
+    if (x->k != y->k) return x->k < y->k ? -1 : 1;
+    if (x->v != y->v) return x->v < y->v ? -1 : 1;
+    return 0;
+}
+
+void oracle_sort(int64_t m, uint64_t *keys, uint32_t *vals, int64_t n_tiles, int32_t *ranges) {
+    kv_t *a = (kv_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(kv_t));
+    for (int64_t i = 0; i < m; ++i) {
+        a[i].k = keys[i];
+        a[i].v = vals[i];
+    }
+    qsort(a, (size_t)m, sizeof(kv_t), kv_cmp);
+    for (int64_t i = 0; i < m; ++i) {
+        keys[i] = a[i].k;
+        vals[i] = a[i].v;
+    }
+    free(a);
+    for (int64_t t = 0; t < 2 * n_tiles; ++t) ranges[t] = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t t = (int64_t)(keys[i] >> 32);
+        if (i == 0 || (int64_t)(keys[i - 1] >> 32) != t) ranges[2 * t] = (int32_t)i;
+        if (i == m - 1 || (int64_t)(keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (int32_t)(i + 1);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compositing (Sec. 2 Shader; Algorithm 1; Listing 1 evaluate).             */
+/* For a pixel at raw coordinate (px, py), walk the ordered list:            */
+/*   power = -(c00 dx^2 + 2 c01 dx dy + c11 dy^2)/2, d = px - mu_2D;         */
+/*   skip if power > 0 (valid flag);                                         */
+/*   alpha = min(alpha_max, o exp(power)); skip if alpha < alpha_t;          */
+/*   stop (without accumulating) if T (1 - alpha) < T_eps;                   */
+/*   C += c alpha T; T *= (1 - alpha).                                       */
+/* Finally C += T bg.  band is set when a decision lies within a relative    */
+/* delta of its threshold, or when two successive contributors have depths   */
+/* within a relative dz (order of near-ties is precision dependent).         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t idx;   /* primitive */
+    int pos;       /* position in the walked list */
+    double alpha, G, T; /* alpha, exp(power), transmittance before */
+    int clamped;
+    double dx, dy;
+} contrib_t;
+
+static int walk(double px, double py, const double *rec, const int64_t *list, int len, const ocfg *cfg,
+                double delta, double dz, double C[3], double *Tout, int *last, int *band, contrib_t *out,
+                uint64_t *sig) {
+    double T = 1.0;
+    C[0] = C[1] = C[2] = 0.0;
+    int nc = 0, bd = 0;
+    *last = 0;
+    double prev_depth = -1.0;
+    uint64_t h = sig ? *sig : 0;
+    for (int k = 0; k < len; ++k) {
+        const double *R = rec + 12 * list[k];
+        double dx = px - R[0], dy = py - R[1];
+        double power = -0.5 * (R[2] * dx * dx + 2.0 * R[3] * dx * dy + R[4] * dy * dy);
+        if (power > 0.0) continue;
+        double G = exp(power);
+        double og = R[5] * G;
+        double alpha = og < cfg->amax ? og : cfg->amax;
+        if (fabs(og - cfg->amax) <= delta * cfg->amax) bd = 1;
+        if (fabs(alpha - cfg->at) <= delta * cfg->at) bd = 1;
+        if (alpha < cfg->at) continue;
+        double tt = T * (1.0 - alpha);
+        if (fabs(tt - cfg->teps) <= delta * cfg->teps) bd = 1;
+        if (tt < cfg->teps) {
+            h = h * 1099511628211ULL ^ 0xffffULL;
+            break;
+        }
+        if (dz > 0.0 && prev_depth > 0.0 && fabs(R[9] - prev_depth) <= dz * R[9]) bd = 1;
+        prev_depth = R[9];
+        if (out) {
+            out[nc].idx = list[k];
+            out[nc].pos = k;
+            out[nc].alpha = alpha;
+            out[nc].G = G;
+            out[nc].T = T;
+            out[nc].clamped = !(og < cfg->amax);
+            out[nc].dx = dx;
+            out[nc].dy = dy;
+        }
+        h = (h ^ (uint64_t)(list[k] + 1)) * 1099511628211ULL;
+        for (int c = 0; c < 3; ++c) C[c] += R[6 + c] * alpha * T;
+        T = tt;
+        ++nc;
+        *last = k + 1;
+    }
+    for (int c = 0; c < 3; ++c) C[c] += T * cfg->bg[c];
+    *Tout = T;
+    *band = bd;
+    if (sig) *sig = h;
+    return nc;
+}
+
+typedef struct {
+    double depth;
+    int64_t idx;
+} dz_t;
+
+static int dz_cmp(const void *a, const void *b) {
+    const dz_t *x = (const dz_t *)a, *y = (const dz_t *)b;
+    if (x->depth != y->depth) return x->depth < y->depth ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx ? 1 : 0);
+}
+
+/* visible primitives ordered by (depth, index) */
+static int64_t depth_order(int64_t n, const double *rec, int64_t *order) {
+    dz_t *a = (dz_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(dz_t));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (rec[12 * i + 11] != 0.0) {
+            a[m].depth = rec[12 * i + 9];
+            a[m].idx = i;
+            ++m;
+        }
+    qsort(a, (size_t)m, sizeof(dz_t), dz_cmp);
+    for (int64_t i = 0; i < m; ++i) order[i] = a[i].idx;
+    free(a);
+    return m;
+}
+
+/* Brute force (no tiles): every visible primitive at every listed pixel.
+ * pix[npix*2] = (x, y) integer pixel coordinates; out color[npix*3],
+ * tfinal[npix], band[npix]; sig (may be NULL) = hash of all decisions. */
+void oracle_render_pixels(int64_t n, const double *rec, const int32_t *pix, int64_t npix, const double *cfgv,
+                          double delta, double dz, double *color, double *tfinal, int32_t *band, uint64_t *sig) {
+    ocfg cfg = read_cfg(cfgv);
+    int64_t *order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t m = depth_order(n, rec, order);
+    uint64_t hs = 1469598103934665603ULL;
+    uint64_t *hp = (uint64_t *)malloc((size_t)(npix > 0 ? npix : 1) * sizeof(uint64_t));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < npix; ++p) {
+        double C[3], T;
+        int last, bd;
+        uint64_t h = (uint64_t)p;
+        walk((double)pix[2 * p], (double)pix[2 * p + 1], rec, order, (int)m, &cfg, delta, dz, C, &T, &last, &bd,
+             NULL, &h);
+        for (int c = 0; c < 3; ++c) color[3 * p + c] = C[c];
+        tfinal[p] = T;
+        band[p] = bd;
+        hp[p] = h;
+    }
+    for (int64_t p = 0; p < npix; ++p) hs = (hs ^ hp[p]) * 1099511628211ULL;
+    if (sig) *sig = hs;
+    free(hp);
+    free(order);
+}
+
+/* Per-tile walk over given lists: vals[ranges[t,0]:ranges[t,1]] for tile t.
+ * image[3,H,W] (planar), tfinal[H,W], ncontrib[H,W] (position+1 of the last
+ * accumulated entry in the tile's list), band[H,W]. */
+void oracle_render_tiles(int64_t n, const double *rec, const uint32_t *vals, const int32_t *ranges,
+                         const double *camv, const double *cfgv, double delta, double *image, double *tfinal,
+                         int32_t *ncontrib, int32_t *band) {
+    (void)n;
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
+    int64_t HW = (int64_t)cam.W * cam.H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < Wt * Ht; ++t) {
+        int tx = t % Wt, ty = t / Wt;
+        int s = ranges[2 * t], e = ranges[2 * t + 1];
+        int len = e - s;
+        int64_t *list = (int64_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int64_t));
+        for (int k = 0; k < len; ++k) list[k] = vals[s + k];
+        for (int yy = 0; yy < cfg.th; ++yy)
+            for (int xx = 0; xx < cfg.tw; ++xx) {
+                int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
+                if (x >= cam.W || y >= cam.H) continue;
+                double C[3], T;
+                int last, bd;
+                walk((double)x, (double)y, rec, list, len, &cfg, delta, 0.0, C, &T, &last, &bd, NULL, NULL);
+                int64_t p = (int64_t)y * cam.W + x;
+                for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
+                tfinal[p] = T;
+                ncontrib[p] = last;
+                band[p] = bd;
+            }
+        free(list);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of compositing, written from the definition                       */
+/*   C = sum_i c_i a_i T_i + T_N bg,  T_i = prod_{j<i} (1 - a_j):           */
+/*   dC/dc_i = a_i T_i;                                                      */
+/*   dC/da_i = c_i T_i - S_i / (1 - a_i),  S_i = sum_{j>i} c_j a_j T_j + T_N bg */
+/* with S_i formed as an explicit suffix sum.  Through alpha = o exp(power)  */
+/* (zero through the 0.99 clamp), power = -(c00 dx^2 + 2 c01 dx dy +         */
+/* c11 dy^2)/2, dx = px - mx.  d_rec[n*12] accumulates (dmx, dmy, dc00,      */
+/* dc01, dc11, do, dr, dg, db); entries 9..11 stay zero.                     */
+/* ------------------------------------------------------------------------ */
+
+static void pixel_adjoint(const double *rec, const contrib_t *cs, int nc, double Tfin, const double *g,
+                          const ocfg *cfg, double *d_rec) {
+    if (nc == 0) return;
+    double *S = (double *)malloc((size_t)nc * 3 * sizeof(double));
+    /* explicit suffix sums */
+    for (int c = 0; c < 3; ++c) {
+        double acc = Tfin * cfg->bg[c];
+        for (int i = nc - 1; i >= 0; --i) {
+            S[3 * i + c] = acc;
+            acc += rec[12 * cs[i].idx + 6 + c] * cs[i].alpha * cs[i].T;
+        }
+    }
+    for (int i = 0; i < nc; ++i) {
+        const double *R = rec + 12 * cs[i].idx;
+        double *D = d_rec + 12 * cs[i].idx;
+        double a = cs[i].alpha, T = cs[i].T;
+        double da = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            D[6 + c] += g[c] * a * T;
+            da += g[c] * (R[6 + c] * T - S[3 * i + c] / (1.0 - a));
+        }
+        if (cs[i].clamped) continue;
+        /* alpha = o G, G = exp(power) */
+        D[5] += da * cs[i].G;
+        double dp = da * a; /* dL/dpower */
+        double dx = cs[i].dx, dy = cs[i].dy;
+        /* dpower/dc00 = -dx^2/2, dpower/dc01 = -dx dy, dpower/dc11 = -dy^2/2 */
+        D[2] += dp * (-0.5 * dx * dx);
+        D[3] += dp * (-dx * dy);
+        D[4] += dp * (-0.5 * dy * dy);
+        /* dpower/dmx = c00 dx + c01 dy ; dpower/dmy = c01 dx + c11 dy */
+        D[0] += dp * (R[2] * dx + R[3] * dy);
+        D[1] += dp * (R[3] * dx + R[4] * dy);
+    }
+    free(S);
+}
+
+/* Brute-force adjoint over all pixels of a W x H image (tiny scenes). */
+void oracle_render_bwd_brute(int64_t n, const double *rec, const double *camv, const double *cfgv,
+                             const double *d_image, double *d_rec) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int64_t *order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t m = depth_order(n, rec, order);
+    contrib_t *cs = (contrib_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(contrib_t));
+    int64_t HW = (int64_t)cam.W * cam.H;
+    memset(d_rec, 0, (size_t)n * 12 * sizeof(double));
+    for (int y = 0; y < cam.H; ++y)
+        for (int x = 0; x < cam.W; ++x) {
+            int64_t p = (int64_t)y * cam.W + x;
+            double g[3] = {d_image[p], d_image[HW + p], d_image[2 * HW + p]};
+            if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
+            double C[3], T;
+            int last, bd;
+            int nc = walk((double)x, (double)y, rec, order, (int)m, &cfg, 0.0, 0.0, C, &T, &last, &bd, cs, NULL);
+            pixel_adjoint(rec, cs, nc, T, g, &cfg, d_rec);
+        }
+    free(cs);
+    free(order);
+}
+
+/* Per-tile adjoint over given lists (serial; deterministic). */
+void oracle_render_bwd_tiles(int64_t n, const double *rec, const uint32_t *vals, const int32_t *ranges,
+                             const double *camv, const double *cfgv, const double *d_image, double *d_rec) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
+    int64_t HW = (int64_t)cam.W * cam.H;
+    memset(d_rec, 0, (size_t)n * 12 * sizeof(double));
+    for (int t = 0; t < Wt * Ht; ++t) {
+        int tx = t % Wt, ty = t / Wt;
+        int s = ranges[2 * t], e = ranges[2 * t + 1];
+        int len = e - s;
+        if (len <= 0) continue;
+        int64_t *list = (int64_t *)malloc((size_t)len * sizeof(int64_t));
+        contrib_t *cs = (contrib_t *)malloc((size_t)len * sizeof(contrib_t));
+        for (int k = 0; k < len; ++k) list[k] = vals[s + k];
+        for (int yy = 0; yy < cfg.th; ++yy)
+            for (int xx = 0; xx < cfg.tw; ++xx) {
+                int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
+                if (x >= cam.W || y >= cam.H) continue;
+                int64_t p = (int64_t)y * cam.W + x;
+                double g[3] = {d_image[p], d_image[HW + p], d_image[2 * HW + p]};
+                if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
+                double C[3], T;
+                int last, bd;
+                int nc = walk((double)x, (double)y, rec, list, len, &cfg, 0.0, 0.0, C, &T, &last, &bd, cs, NULL);
+                pixel_adjoint(rec, cs, nc, T, g, &cfg, d_rec);
+            }
+        free(cs);
+        free(list);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the projection (Listing 1 project), from screen-space          */
+/* gradients d_rec (dmx, dmy, dc00, dc01, dc11, do, dr, dg, db) to           */
+/* dmu[n*3], dscale[n*3], dquat[n*4], dopac[n], dsh[n*K*3].                  */
+/* Chain: conic = Sigma_2D^{-1} (d(A^{-1}) = -A^{-1} dA A^{-1});             */
+/* Sigma_2D = T Sigma T^T + dil I, T = J W; J(camera point) with the clamp;   */
+/* camera point = W mu + t; Sigma = M M^T, M = R(q/|q|) diag(s);             */
+/* mu_2D = (fx x/z + cx, fy y/z + cy); rgb = max(0, sum sh Y(d) + 0.5),      */
+/* d = (mu - campos)/|mu - campos|.  Invisible primitives get zero.          */
+/* ------------------------------------------------------------------------ */
+
+/* d R / d qn_k for the unit-quaternion rotation (w, x, y, z) */
+static void drot_dq(const double *qn, double dR[4][9]) {
+    double w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    /* w */
+    double Dw[9] = {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0};
+    /* x */
+    double Dx[9] = {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x};
+    /* y */
+    double Dy[9] = {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y};
+    /* z */
+    double Dz[9] = {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0};
+    memcpy(dR[0], Dw, sizeof(Dw));
+    memcpy(dR[1], Dx, sizeof(Dx));
+    memcpy(dR[2], Dy, sizeof(Dy));
+    memcpy(dR[3], Dz, sizeof(Dz));
+}
+
+void oracle_project_bwd(int64_t n, const double *mu, const double *scale, const double *quat, const double *opac,
+                        const double *sh, const double *camv, const double *cfgv, const double *d_rec,
+                        double *dmu, double *dscale, double *dquat, double *dopac, double *dsh) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int K = (cfg.deg + 1) * (cfg.deg + 1);
+    const double *V = cam.V;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        oproj P;
+        const double *D = d_rec + 12 * i;
+        const double *s = scale + 3 * i;
+        const double *shi = sh + (int64_t)3 * K * i;
+        double *gmu = dmu + 3 * i, *gs = dscale + 3 * i, *gq = dquat + 4 * i, *gsh = dsh + (int64_t)3 * K * i;
+        project_one(mu + 3 * i, s, quat + 4 * i, opac[i], shi, &cam, &cfg, &P);
+        memset(gmu, 0, 3 * sizeof(double));
+        memset(gs, 0, 3 * sizeof(double));
+        memset(gq, 0, 4 * sizeof(double));
+        memset(gsh, 0, (size_t)3 * K * sizeof(double));
+        dopac[i] = 0.0;
+        if (!P.visible) continue;
+        dopac[i] = D[5];
+
+        /* colour */
+        double Y[16], dY[48];
+        oracle_sh_basis(cfg.deg, P.dir, Y, dY);
+        double gdir[3] = {0, 0, 0};
+        for (int c = 0; c < 3; ++c) {
+            if (!(P.raw[c] > 0.0)) continue;
+            double g = D[6 + c];
+            for (int k = 0; k < K; ++k) {
+                gsh[3 * k + c] = Y[k] * g;
+                for (int j = 0; j < 3; ++j) gdir[j] += g * shi[3 * k + c] * dY[3 * k + j];
+            }
+        }
+        double dd = gdir[0] * P.dir[0] + gdir[1] * P.dir[1] + gdir[2] * P.dir[2];
+        for (int j = 0; j < 3; ++j) gmu[j] += (gdir[j] - P.dir[j] * dd) / P.vlen;
+
+        /* camera-space point gradient */
+        double x = P.mc[0], y = P.mc[1], z = P.mc[2];
+        double gmc[3] = {0, 0, 0};
+        gmc[0] += D[0] * cam.fx / z;
+        gmc[1] += D[1] * cam.fy / z;
+        gmc[2] += -D[0] * cam.fx * x / (z * z) - D[1] * cam.fy * y / (z * z);
+
+        /* conic -> Sigma_2D : dL/dA = -A^{-1} G A^{-1}, G symmetric with the
+         * off-diagonal record entry split over both matrix entries */
+        double Ai[4] = {P.conic[0], P.conic[1], P.conic[1], P.conic[2]};
+        double G[4] = {D[2], 0.5 * D[3], 0.5 * D[3], D[4]};
+        double AG[4], GA[4];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) {
+                AG[2 * r + c] = Ai[2 * r] * G[c] + Ai[2 * r + 1] * G[2 + c];
+            }
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) GA[2 * r + c] = -(AG[2 * r] * Ai[c] + AG[2 * r + 1] * Ai[2 + c]);
+        /* GA = dL/dSigma_2D as a symmetric matrix (equal to dL/d(T Sigma T^T)) */
+
+        /* Sigma_2D' = T Sigma T^T : dL/dSigma = T^T GA T ; dL/dT = 2 GA T Sigma */
+        double gSig[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int r = 0; r < 2; ++r)
+                    for (int c = 0; c < 2; ++c) acc += P.Tm[3 * r + a] * GA[2 * r + c] * P.Tm[3 * c + b];
+                gSig[3 * a + b] = acc;
+            }
+        double gT[6];
+        for (int r = 0; r < 2; ++r)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int c = 0; c < 2; ++c)
+                    for (int k = 0; k < 3; ++k) acc += GA[2 * r + c] * P.Tm[3 * c + k] * P.Sig[3 * k + b];
+                gT[3 * r + b] = 2.0 * acc;
+            }
+        /* T = J W : dL/dJ = dL/dT W^T */
+        double gJ[6];
+        for (int r = 0; r < 2; ++r)
+            for (int k = 0; k < 3; ++k) {
+                double acc = 0.0;
+                for (int b = 0; b < 3; ++b) acc += gT[3 * r + b] * V[4 * k + b];
+                gJ[3 * r + k] = acc;
+            }
+        /* J00 = fx/z, J02 = -fx ux/z (ux = x/z unless clamped), J11, J12 alike */
+        gmc[2] += gJ[0] * (-cam.fx / (z * z));
+        gmc[2] += gJ[4] * (-cam.fy / (z * z));
+        if (!P.clx) {
+            /* J02 = -fx x / z^2 */
+            gmc[0] += gJ[2] * (-cam.fx / (z * z));
+            gmc[2] += gJ[2] * (2.0 * cam.fx * x / (z * z * z));
+        } else {
+            /* J02 = -fx L / z with L constant */
+            gmc[2] += gJ[2] * (cam.fx * P.ux / (z * z));
+        }
+        if (!P.cly) {
+            gmc[1] += gJ[5] * (-cam.fy / (z * z));
+            gmc[2] += gJ[5] * (2.0 * cam.fy * y / (z * z * z));
+        } else {
+            gmc[2] += gJ[5] * (cam.fy * P.uy / (z * z));
+        }
+        /* camera point = W mu + t */
+        for (int j = 0; j < 3; ++j) gmu[j] += V[j] * gmc[0] + V[4 + j] * gmc[1] + V[8 + j] * gmc[2];
+
+        /* Sigma = M M^T, M = R diag(s) : dL/dM = 2 gSig M (gSig symmetric) */
+        double gSs[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) gSs[3 * a + b] = 0.5 * (gSig[3 * a + b] + gSig[3 * b + a]);
+        double gM[9];
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k) {
+                double acc = 0.0;
+                for (int b = 0; b < 3; ++b) acc += gSs[3 * a + b] * P.R[3 * b + k] * s[k];
+                gM[3 * a + k] = 2.0 * acc;
+            }
+        double gR[9];
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k) {
+                gs[k] += gM[3 * a + k] * P.R[3 * a + k];
+                gR[3 * a + k] = gM[3 * a + k] * s[k];
+            }
+        double dR[4][9];
+        drot_dq(P.qn, dR);
+        double gqn[4];
+        for (int j = 0; j < 4; ++j) {
+            double acc = 0.0;
+            for (int e = 0; e < 9; ++e) acc += gR[e] * dR[j][e];
+            gqn[j] = acc;
+        }
+        /* qn = q / |q| */
+        double dotq = gqn[0] * P.qn[0] + gqn[1] * P.qn[1] + gqn[2] * P.qn[2] + gqn[3] * P.qn[3];
+        for (int j = 0; j < 4; ++j) gq[j] = (gqn[j] - P.qn[j] * dotq) / P.qnorm;
+    }
+}
+
+int oracle_abi_version(void) { return 1; }
