@@ -1,0 +1,195 @@
+/*
+ * xpr.h -- C ABI of the GB300 (sm_103a) 3D Gaussian Splatting tile-splatting
+ * library (libxpr.so).
+ *
+ * The path follows the four-stage point-based pipeline of arXiv 2606.11529
+ * (Sec. 2 and Sec. 4): Preprocess (project each primitive), Rasterizer
+ * (replicate each primitive over the tiles of its bounding box, assign tile
+ * IDs, cull, sort by (tile, depth), find per-tile segment bounds) and Shader
+ * (front-to-back alpha compositing per pixel), plus the reverse-order adjoint
+ * of the shader and of the projection.  The 3DGS instance of the per-element
+ * functions is the paper's Listing 1 (project, tile_cull, evaluate).
+ *
+ * Conventions for every entry point
+ *   - All array pointers are DEVICE pointers (CUDA global memory) unless the
+ *     comment says "host".  The caller allocates and owns every buffer; the
+ *     library never allocates device memory and keeps no state between calls
+ *     except a per-host-thread last-error string and a process-wide counter
+ *     of launched kernels.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously on it; entry points that must return a count to
+ *     the host (xpr_tile_bin) synchronise that stream.
+ *   - Floating-point arrays are IEEE float32, row-major, densely packed.
+ *   - Return value: an XprStatus.  On error nothing is guaranteed about the
+ *     output buffers; xpr_last_error() describes the failure.
+ *   - Sizes: primitive count n < 2^31, intersection count < 2^31, image
+ *     width and height in [1, 32768], tile sizes 8 or 16.
+ */
+#ifndef XPR_H
+#define XPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum XprStatus {
+    XPR_OK = 0,
+    XPR_ERR_INVALID = 1,  /* bad argument: NULL pointer, size out of range, unsupported tile size */
+    XPR_ERR_CAPACITY = 2, /* intersection buffer too small; the required count is reported */
+    XPR_ERR_CUDA = 3,     /* a CUDA launch or runtime call failed */
+    XPR_ERR_TIMEOUT = 4,  /* a bounded device-side wait expired */
+    XPR_ERR_INTERNAL = 5  /* a device-side consistency check failed */
+} XprStatus;
+
+/* Pinhole camera (the paper's `cam` and `view` arguments of project, Sec. 3.1).
+ * viewmat: world-to-camera [R | t], 3x4 row-major; camera axes x right,
+ * y down, z forward.  Pixel (x, y) of a 3DGS image is evaluated at the raw
+ * coordinate (x, y) as in Listing 1 evaluate. */
+typedef struct XprCamera {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float viewmat[12];
+    float z_near; /* primitives with camera-space z <= z_near are invisible (Listing 1 visibility flag) */
+    int32_t model; /* 0 = pinhole (the only model implemented) */
+} XprCamera;
+
+/* Renderer constants.  alpha_thresh is the contribution threshold 1/255 of
+ * the Appendix (3DGS implementation); alpha_max (0.99), t_eps (1e-4),
+ * cov_dilation (0.3) and clip_factor (1.3, limit on |x/z| relative to the
+ * half field of view inside the EWA Jacobian) are the 3DGS conventions the
+ * paper's compute_cov_2D / blend loop leave to the config. */
+typedef struct XprConfig {
+    int32_t tile_w, tile_h; /* 8 or 16 each (the paper's GPU tile sizes, hyperparameter table) */
+    float alpha_thresh;
+    float alpha_max;
+    float t_eps;        /* stop when T (1 - alpha) < t_eps, before blending that primitive */
+    float cov_dilation;
+    float clip_factor;
+    int32_t sh_degree;  /* 0..3; K = (sh_degree + 1)^2 coefficients per colour channel */
+    float bg[3];        /* background colour added as T_final * bg */
+    int32_t batch_depth;/* render: entries staged per shared-memory batch; 0 = kernel default */
+} XprConfig;
+
+/* 3DGS PrimitiveParams (Appendix, 3DGS implementation), structure of arrays:
+ * mu[n,3] world-space means, scale[n,3] (positive, activated), quat[n,4]
+ * rotation (w, x, y, z; normalised inside), opacity[n] (activated, in (0,1)),
+ * sh[n,K,3] spherical-harmonic coefficients (real SH, Condon-Shortley
+ * phase; colour = max(0, sum_k sh_k Y_k(d) + 0.5), d = unit vector from the
+ * camera centre to mu). */
+typedef struct XprPrims {
+    const float *mu;
+    const float *scale;
+    const float *quat;
+    const float *opacity;
+    const float *sh;
+} XprPrims;
+
+/* Gradients with the same layout as XprPrims. */
+typedef struct XprPrimsGrad {
+    float *mu;
+    float *scale;
+    float *quat;
+    float *opacity;
+    float *sh;
+} XprPrimsGrad;
+
+/* Projected record, 12 floats per primitive (the paper's shader data p_sd,
+ * tile-cull data p_tcd and depth of ProjectResult, Listing 1):
+ *   [0] mu_2D.x  [1] mu_2D.y  [2] conic00  [3] conic01  [4] conic11
+ *   [5] opacity  [6] r  [7] g  [8] b  [9] depth (camera z)
+ *   [10] ln(opacity / alpha_thresh)  [11] visible (1.0 or 0.0)
+ * conic = Sigma_2D^{-1}.  Invisible primitives have every entry 0 except
+ * depth.  The same layout is used for screen-space gradients (d_rec):
+ *   [0..1] d mu_2D, [2..4] d conic, [5] d opacity, [6..8] d rgb, rest 0. */
+#define XPR_REC_FLOATS 12
+
+/* ---- Preprocess ----------------------------------------------------------
+ * xpr_project: Listing 1 project for n primitives (Sec. 4.1 Preprocess):
+ * camera-space mean, Sigma = R S S^T R^T, EWA footprint Sigma_2D = J W Sigma
+ * W^T J^T + dilation I, conic, opacity-aware extents sqrt(2 ln(o/a_t)
+ * Sigma_2D,xx) (and yy), half-open tile bounding box, tile count, visibility
+ * flag (det > 0, o >= a_t, r > 0, tc > 0, z > z_near) and SH colour.
+ * Outputs: rec[n,12], bbox[n,4] int32 (xmin, ymin, xmax, ymax in tiles,
+ * half-open; zero when invisible), tile_count[n] int32 (0 when invisible). */
+int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
+                int32_t *bbox, int32_t *tile_count, void *stream);
+
+/* ---- Rasterizer: replicate, assign tile ID, cull --------------------------
+ * xpr_tile_bin (Sec. 4.2 Replicate / Assign tile ID / Cull): for primitive i
+ * (in index order) and slot r = 0 .. tile_count[i]-1 of its bounding box,
+ * x = xmin + r mod w_i, y = ymin + r div w_i, t = y W' + x; the pair is kept
+ * iff the StopThePop cull of Listing 1 tile_cull passes (decision taken in
+ * FP32 with a fixed sequence of correctly rounded operations).  Culled pairs
+ * are not emitted (the paper's "tile ID T" slots are dropped instead of being
+ * sorted to the end).
+ * Outputs: offsets[n+1] int32 (exclusive prefix sum of surviving counts;
+ * offsets[n] = total), keys[total] = (t << 32) | float_bits(depth), vals[total]
+ * = primitive index, in (primitive, r) order; *n_isect (HOST) = total.
+ * If total > capacity, returns XPR_ERR_CAPACITY with *n_isect set and keys /
+ * vals untouched (the caller re-sizes and calls again).  Synchronises
+ * `stream` to read the total.  workspace: >= xpr_tile_bin_workspace(n) bytes,
+ * 256-byte aligned. */
+size_t xpr_tile_bin_workspace(int64_t n);
+int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, int64_t n, const XprCamera *cam,
+                 const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t capacity,
+                 int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---- Rasterizer: sort and identify bounds ---------------------------------
+ * xpr_sort (Sec. 4.2 "Sort and identify bounds"): stable LSD radix sort of
+ * (key, val) by key over the low 32 + ceil(log2(n_tiles)) bits, so equal
+ * (tile, depth) keys keep primitive order; then ranges[t] = [start, end) of
+ * tile t's segment in the sorted arrays ([0,0) for empty tiles).
+ * keys_in/vals_in are read only and must not alias keys_out/vals_out.
+ * workspace: >= xpr_sort_workspace(n_isect, n_tiles) bytes, 256-byte aligned. */
+size_t xpr_sort_workspace(int64_t n_isect, int32_t n_tiles);
+int xpr_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n_isect, int32_t n_tiles, uint64_t *keys_out,
+             uint32_t *vals_out, int32_t *ranges, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---- Shader ----------------------------------------------------------------
+ * xpr_render_fwd (Sec. 2 Shader, Algorithm 1, Listing 1 evaluate): one thread
+ * block per tile walks vals[ranges[t,0]:ranges[t,1]] front to back for each
+ * pixel (x, y): d = (x, y) - mu_2D, power = -(c00 dx^2 + 2 c01 dx dy +
+ * c11 dy^2)/2; skip if power > 0; alpha = min(alpha_max, o exp(power)); skip
+ * if alpha < alpha_thresh; stop if T (1 - alpha) < t_eps; else C += rgb alpha T,
+ * T *= 1 - alpha.  Finally C += T bg.
+ * Outputs: image[3,H,W] (planar), t_final[H,W], n_contrib[H,W] int32 (1 +
+ * position in the tile's list of the last blended entry; 0 if none). */
+int xpr_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                   const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, void *stream);
+
+/* ---- Adjoint ---------------------------------------------------------------
+ * xpr_render_bwd: adjoint of xpr_render_fwd given d_image[3,H,W] = dL/dimage
+ * and the forward's t_final / n_contrib.  Each tile is re-walked back to front
+ * from n_contrib, recomputing T_i = T_{i+1} / (1 - alpha_i) instead of storing
+ * per-pixel lists; dL/drgb_i = alpha_i T_i g, dL/dalpha_i = g.(rgb_i T_i -
+ * S_i / (1 - alpha_i)) with S_i the colour behind i (including T_final bg),
+ * zero through the alpha_max clamp.  Per-primitive gradients are reduced over
+ * each warp and thread block before one set of atomics per (tile, primitive).
+ * d_rec[n,12] is OVERWRITTEN with the screen-space gradients (layout above).
+ * If prims and d_prims are both non-NULL, the projection adjoint is applied
+ * too and d_prims (all five arrays) is OVERWRITTEN with dL/d(mu, scale, quat,
+ * opacity, sh); invisible primitives get zeros. */
+int xpr_render_bwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                   const XprConfig *cfg, const float *t_final, const int32_t *n_contrib, const float *d_image,
+                   float *d_rec, const XprPrims *prims, const XprPrimsGrad *d_prims, void *stream);
+
+/* xpr_project_bwd: the projection adjoint alone (screen-space d_rec -> d_prims,
+ * all five arrays overwritten).  Same math as the second half of
+ * xpr_render_bwd. */
+int xpr_project_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
+                    const float *d_rec, const XprPrimsGrad *d_prims, void *stream);
+
+/* ---- Misc ------------------------------------------------------------------ */
+const char *xpr_status_string(int status);
+const char *xpr_last_error(void); /* message of the last failing call on this host thread */
+int xpr_version(void);
+/* Number of kernels this library has launched in the process so far (all threads). */
+unsigned long long xpr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XPR_H */

@@ -1,0 +1,260 @@
+"""ctypes binding of libxpr.so (C ABI in include/xpr.h).
+
+Argument marshalling only: every function here passes device pointers of
+torch tensors to the entry point of the same name and raises ``XprError`` on a
+non-zero status.  Output tensors are allocated with ``torch.empty`` when the
+caller does not pass them (PyTorch is the allocator; the library never
+allocates).  There is no CPU fallback: if the library cannot be loaded the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+c_i32, c_i64, c_f32, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+
+
+class XprCamera(ctypes.Structure):
+    _fields_ = [("width", c_i32), ("height", c_i32), ("fx", c_f32), ("fy", c_f32), ("cx", c_f32), ("cy", c_f32),
+                ("viewmat", c_f32 * 12), ("z_near", c_f32), ("model", c_i32)]
+
+
+class XprConfig(ctypes.Structure):
+    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("alpha_thresh", c_f32), ("alpha_max", c_f32),
+                ("t_eps", c_f32), ("cov_dilation", c_f32), ("clip_factor", c_f32), ("sh_degree", c_i32),
+                ("bg", c_f32 * 3), ("batch_depth", c_i32)]
+
+
+class XprPrims(ctypes.Structure):
+    _fields_ = [("mu", c_vp), ("scale", c_vp), ("quat", c_vp), ("opacity", c_vp), ("sh", c_vp)]
+
+
+class XprPrimsGrad(ctypes.Structure):
+    _fields_ = [("mu", c_vp), ("scale", c_vp), ("quat", c_vp), ("opacity", c_vp), ("sh", c_vp)]
+
+
+XPR_OK, XPR_ERR_INVALID, XPR_ERR_CAPACITY, XPR_ERR_CUDA, XPR_ERR_TIMEOUT, XPR_ERR_INTERNAL = range(6)
+REC = 12
+
+# (name, restype, argtypes) of every exported entry point
+SIGNATURES = {
+    "xpr_project": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                            c_vp, c_vp, c_vp, c_vp]),
+    "xpr_tile_bin_workspace": (c_sz, [c_i64]),
+    "xpr_tile_bin": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
+                             c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
+    "xpr_sort_workspace": (c_sz, [c_i64, c_i32]),
+    "xpr_sort": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "xpr_render_fwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
+                               c_vp, c_vp, c_vp]),
+    "xpr_render_bwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
+                               c_vp, c_vp, c_vp, ctypes.POINTER(XprPrims), ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_project_bwd": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
+                                ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "xpr_last_error": (ctypes.c_char_p, []),
+    "xpr_version": (ctypes.c_int, []),
+    "xpr_launch_count": (ctypes.c_ulonglong, []),
+}
+
+_lib = None
+
+
+class XprError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        super().__init__(f"{fn} failed with status {status}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libxpr.so (building it first if needed and allowed)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libxpr.so not found at {path}; run paper_2606_11529_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, fn: str):
+    if status != XPR_OK:
+        msg = load().xpr_last_error().decode(errors="replace")
+        raise XprError(status, fn, msg)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_camera(cam) -> XprCamera:
+    """From a ``scenes.Camera``-like object."""
+    c = XprCamera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    vm = [float(v) for v in __import__("numpy").asarray(cam.viewmat, dtype="float32").reshape(12)]
+    c.viewmat[:] = vm
+    c.z_near = float(cam.z_near)
+    c.model = 0
+    return c
+
+
+def make_config(cfg) -> XprConfig:
+    g = XprConfig()
+    g.tile_w, g.tile_h = int(cfg.tile_w), int(cfg.tile_h)
+    g.alpha_thresh, g.alpha_max, g.t_eps = float(cfg.alpha_thresh), float(cfg.alpha_max), float(cfg.t_eps)
+    g.cov_dilation, g.clip_factor = float(cfg.cov_dilation), float(cfg.clip_factor)
+    g.sh_degree = int(cfg.sh_degree)
+    g.bg[:] = [float(b) for b in cfg.bg]
+    g.batch_depth = int(getattr(cfg, "batch_depth", 0))
+    return g
+
+
+def _as_c(x, C):
+    return x if isinstance(x, C) else (make_camera(x) if C is XprCamera else make_config(x))
+
+
+def _dev(t):
+    return t.device
+
+
+def _prims(mu, scale, quat, opacity, sh) -> XprPrims:
+    for name, t in (("mu", mu), ("scale", scale), ("quat", quat), ("opacity", opacity), ("sh", sh)):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return XprPrims(mu.data_ptr(), scale.data_ptr(), quat.data_ptr(), opacity.data_ptr(), sh.data_ptr())
+
+
+def tiles_of(cam, cfg):
+    return (int(cam.width) + int(cfg.tile_w) - 1) // int(cfg.tile_w), \
+           (int(cam.height) + int(cfg.tile_h) - 1) // int(cfg.tile_h)
+
+
+# ---------------------------------------------------------------------------------------- entry points
+
+def xpr_project(mu, scale, quat, opacity, sh, cam, cfg, rec=None, bbox=None, tile_count=None, stream=None):
+    L = load()
+    n = mu.shape[0]
+    dev = _dev(mu)
+    rec = torch.empty((n, REC), dtype=torch.float32, device=dev) if rec is None else rec
+    bbox = torch.empty((n, 4), dtype=torch.int32, device=dev) if bbox is None else bbox
+    tile_count = torch.empty(n, dtype=torch.int32, device=dev) if tile_count is None else tile_count
+    p = _prims(mu, scale, quat, opacity, sh)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_project(ctypes.byref(p), n, ctypes.byref(c), ctypes.byref(g), _ptr(rec), _ptr(bbox),
+                         _ptr(tile_count), _stream(stream)), "xpr_project")
+    return rec, bbox, tile_count
+
+
+def xpr_tile_bin(rec, bbox, tile_count, cam, cfg, capacity=None, offsets=None, keys=None, vals=None,
+                 workspace=None, stream=None):
+    """Returns (offsets[n+1], keys[I], vals[I], I).  ``capacity``: initial guess for the
+    intersection buffers; on XPR_ERR_CAPACITY they are re-allocated to the reported size and the
+    call is repeated."""
+    L = load()
+    n = rec.shape[0]
+    dev = rec.device
+    offsets = torch.empty(n + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
+    ws_need = int(L.xpr_tile_bin_workspace(n))
+    if workspace is None or workspace.numel() < ws_need:
+        workspace = torch.empty(max(ws_need, 256), dtype=torch.uint8, device=dev)
+    if keys is None or capacity is None:
+        cap = int(capacity) if capacity is not None else max(4 * n, 1024)
+        keys = torch.empty(cap, dtype=torch.int64, device=dev)
+        vals = torch.empty(cap, dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    for _ in range(2):
+        n_isect = c_i64(0)
+        s = L.xpr_tile_bin(_ptr(rec), _ptr(bbox), _ptr(tile_count), n, ctypes.byref(c), ctypes.byref(g),
+                           _ptr(offsets), _ptr(keys), _ptr(vals), keys.numel(), ctypes.byref(n_isect),
+                           _ptr(workspace), workspace.numel(), _stream(stream))
+        if s == XPR_ERR_CAPACITY and n_isect.value <= 0x7FFFFFFF:
+            keys = torch.empty(n_isect.value, dtype=torch.int64, device=dev)
+            vals = torch.empty(n_isect.value, dtype=torch.int32, device=dev)
+            continue
+        _check(s, "xpr_tile_bin")
+        I = int(n_isect.value)
+        return offsets, keys[:I], vals[:I], I
+    raise XprError(XPR_ERR_CAPACITY, "xpr_tile_bin", "capacity retry failed")
+
+
+def xpr_sort(keys, vals, n_tiles, keys_out=None, vals_out=None, ranges=None, workspace=None, stream=None):
+    L = load()
+    n = keys.numel()
+    dev = keys.device
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    vals_out = torch.empty_like(vals) if vals_out is None else vals_out
+    ranges = torch.empty((n_tiles, 2), dtype=torch.int32, device=dev) if ranges is None else ranges
+    need = int(L.xpr_sort_workspace(n, n_tiles))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    _check(L.xpr_sort(_ptr(keys), _ptr(vals), n, n_tiles, _ptr(keys_out), _ptr(vals_out), _ptr(ranges),
+                      _ptr(workspace), workspace.numel(), _stream(stream)), "xpr_sort")
+    return keys_out, vals_out, ranges
+
+
+def xpr_render_fwd(rec, vals, ranges, cam, cfg, image=None, t_final=None, n_contrib=None, stream=None):
+    L = load()
+    dev = rec.device
+    H, W = int(cam.height), int(cam.width)
+    image = torch.empty((3, H, W), dtype=torch.float32, device=dev) if image is None else image
+    t_final = torch.empty((H, W), dtype=torch.float32, device=dev) if t_final is None else t_final
+    n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev) if n_contrib is None else n_contrib
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_fwd(_ptr(rec), rec.shape[0], _ptr(vals), _ptr(ranges), ctypes.byref(c), ctypes.byref(g),
+                            _ptr(image), _ptr(t_final), _ptr(n_contrib), _stream(stream)), "xpr_render_fwd")
+    return image, t_final, n_contrib
+
+
+def xpr_render_bwd(rec, vals, ranges, cam, cfg, t_final, n_contrib, d_image, prims=None, d_rec=None,
+                   d_prims=None, stream=None):
+    """prims: optional (mu, scale, quat, opacity, sh) to also run the projection adjoint.
+    Returns d_rec[n,12] and, if prims is given, (dmu, dscale, dquat, dopacity, dsh)."""
+    L = load()
+    n = rec.shape[0]
+    dev = rec.device
+    d_rec = torch.empty((n, REC), dtype=torch.float32, device=dev) if d_rec is None else d_rec
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    pp = gp = None
+    grads = None
+    if prims is not None:
+        pp = _prims(*prims)
+        grads = d_prims if d_prims is not None else tuple(torch.empty_like(t) for t in prims)
+        gp = XprPrimsGrad(*[t.data_ptr() for t in grads])
+    _check(L.xpr_render_bwd(_ptr(rec), n, _ptr(vals), _ptr(ranges), ctypes.byref(c), ctypes.byref(g),
+                            _ptr(t_final), _ptr(n_contrib), _ptr(d_image.contiguous()), _ptr(d_rec),
+                            ctypes.byref(pp) if pp is not None else None,
+                            ctypes.byref(gp) if gp is not None else None, _stream(stream)), "xpr_render_bwd")
+    return (d_rec, grads) if prims is not None else d_rec
+
+
+def xpr_project_bwd(mu, scale, quat, opacity, sh, cam, cfg, d_rec, d_prims=None, stream=None):
+    L = load()
+    grads = d_prims if d_prims is not None else tuple(torch.empty_like(t) for t in (mu, scale, quat, opacity, sh))
+    p = _prims(mu, scale, quat, opacity, sh)
+    gp = XprPrimsGrad(*[t.data_ptr() for t in grads])
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_project_bwd(ctypes.byref(p), mu.shape[0], ctypes.byref(c), ctypes.byref(g), _ptr(d_rec),
+                             ctypes.byref(gp), _stream(stream)), "xpr_project_bwd")
+    return grads

@@ -1,0 +1,195 @@
+// C-ABI entry points of libxpr (declared in include/xpr.h): argument validation, workspace
+// carving and launches on the caller's stream.  No device memory is allocated here.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <atomic>
+
+#include "xpr_internal.cuh"
+
+namespace xpr {
+
+static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int fail(int status, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int check_launch(const char *what) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(XPR_ERR_CUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+    return XPR_OK;
+}
+
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int validate_camera_config(const XprCamera *cam, const XprConfig *cfg) {
+    if (!cam || !cfg) return fail(XPR_ERR_INVALID, "camera/config pointer is NULL");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+        return fail(XPR_ERR_INVALID, "image size %dx%d out of range [1, 32768]", cam->width, cam->height);
+    if (cam->model != 0) return fail(XPR_ERR_INVALID, "camera model %d not supported (0 = pinhole)", cam->model);
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(XPR_ERR_INVALID, "focal lengths must be positive");
+    if ((cfg->tile_w != 8 && cfg->tile_w != 16) || (cfg->tile_h != 8 && cfg->tile_h != 16))
+        return fail(XPR_ERR_INVALID, "tile size %dx%d not supported (8 or 16 each)", cfg->tile_w, cfg->tile_h);
+    if (cfg->sh_degree < 0 || cfg->sh_degree > 3)
+        return fail(XPR_ERR_INVALID, "sh_degree %d out of range [0, 3]", cfg->sh_degree);
+    if (!(cfg->alpha_thresh > 0.f) || !(cfg->alpha_max <= 1.f) || !(cfg->alpha_thresh <= cfg->alpha_max))
+        return fail(XPR_ERR_INVALID, "need 0 < alpha_thresh <= alpha_max <= 1");
+    if (!(cfg->alpha_max < 1.f)) return fail(XPR_ERR_INVALID, "alpha_max must be < 1");
+    if (!(cfg->t_eps >= 0.f)) return fail(XPR_ERR_INVALID, "t_eps must be >= 0");
+    return XPR_OK;
+}
+
+static int check_n(int64_t n) {
+    if (n < 0 || n > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "primitive count %lld out of range", (long long)n);
+    return XPR_OK;
+}
+
+}  // namespace xpr
+
+using namespace xpr;
+
+extern "C" {
+
+int xpr_version(void) { return 1; }
+
+unsigned long long xpr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *xpr_last_error(void) { return g_err; }
+
+const char *xpr_status_string(int s) {
+    switch (s) {
+        case XPR_OK: return "ok";
+        case XPR_ERR_INVALID: return "invalid argument";
+        case XPR_ERR_CAPACITY: return "intersection capacity exceeded";
+        case XPR_ERR_CUDA: return "CUDA error";
+        case XPR_ERR_TIMEOUT: return "device wait timed out";
+        case XPR_ERR_INTERNAL: return "internal consistency check failed";
+        default: return "unknown status";
+    }
+}
+
+int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
+                int32_t *bbox, int32_t *tile_count, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_n(n))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh || !rec || !bbox ||
+        !tile_count)
+        return fail(XPR_ERR_INVALID, "xpr_project: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(bbox, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project: quat, rec and bbox must be 16-byte aligned");
+    return launch_project_fwd(*prims, n, *cam, *cfg, rec, bbox, tile_count, as_stream(stream));
+}
+
+size_t xpr_tile_bin_workspace(int64_t n) { return scan_partials_bytes(n < 0 ? 0 : n); }
+
+int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, int64_t n, const XprCamera *cam,
+                 const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t capacity,
+                 int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_n(n))) return s;
+    if (!offsets || !n_isect || (n > 0 && (!rec || !bbox || !tile_count || !workspace)))
+        return fail(XPR_ERR_INVALID, "xpr_tile_bin: NULL pointer");
+    if (capacity < 0) return fail(XPR_ERR_INVALID, "xpr_tile_bin: negative capacity");
+    if (n > 0 && (!aligned(rec, 16) || !aligned(bbox, 16) || !aligned(workspace, 256)))
+        return fail(XPR_ERR_INVALID, "xpr_tile_bin: rec/bbox must be 16-byte and workspace 256-byte aligned");
+    if (ws_bytes < xpr_tile_bin_workspace(n))
+        return fail(XPR_ERR_INVALID, "xpr_tile_bin: workspace %zu < %zu bytes", ws_bytes, xpr_tile_bin_workspace(n));
+    cudaStream_t st = as_stream(stream);
+    if (n == 0) {
+        XPR_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int32_t), st));
+        *n_isect = 0;
+        return XPR_OK;
+    }
+    if ((s = launch_bin_count(rec, bbox, tile_count, n, *cam, *cfg, offsets, st))) return s;
+    if ((s = launch_exclusive_scan(offsets, offsets, n, workspace, nullptr, st))) return s;
+    const int64_t *tot_dev = scan_total_ptr(workspace, n);
+    int64_t total = 0;
+    XPR_CUDA_TRY(cudaMemcpyAsync(&total, tot_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    XPR_CUDA_TRY(cudaStreamSynchronize(st));
+    *n_isect = total;
+    if (total > 0x7fffffffLL) return fail(XPR_ERR_CAPACITY, "xpr_tile_bin: %lld intersections exceed 2^31-1",
+                                          (long long)total);
+    if (total > capacity)
+        return fail(XPR_ERR_CAPACITY, "xpr_tile_bin: %lld intersections > capacity %lld", (long long)total,
+                    (long long)capacity);
+    if (total > 0 && (!keys || !vals)) return fail(XPR_ERR_INVALID, "xpr_tile_bin: NULL keys/vals");
+    return launch_bin_emit(rec, bbox, tile_count, n, *cam, *cfg, offsets, keys, vals, st);
+}
+
+size_t xpr_sort_workspace(int64_t n_isect, int32_t n_tiles) {
+    return sort_workspace_bytes(n_isect < 0 ? 0 : n_isect, n_tiles);
+}
+
+int xpr_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n_isect, int32_t n_tiles, uint64_t *keys_out,
+             uint32_t *vals_out, int32_t *ranges, void *workspace, size_t ws_bytes, void *stream) {
+    if (n_isect < 0 || n_isect > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "xpr_sort: bad count");
+    if (n_tiles < 1) return fail(XPR_ERR_INVALID, "xpr_sort: n_tiles must be >= 1");
+    if (!ranges) return fail(XPR_ERR_INVALID, "xpr_sort: NULL ranges");
+    if (n_isect > 0 && (!keys_in || !vals_in || !keys_out || !vals_out || !workspace))
+        return fail(XPR_ERR_INVALID, "xpr_sort: NULL pointer");
+    if (n_isect > 0 && (keys_in == keys_out || vals_in == vals_out))
+        return fail(XPR_ERR_INVALID, "xpr_sort: input and output buffers must not alias");
+    if (n_isect > 0 && !aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_sort: workspace alignment");
+    return launch_sort(keys_in, vals_in, n_isect, n_tiles, keys_out, vals_out, ranges, workspace, ws_bytes,
+                       as_stream(stream));
+}
+
+int xpr_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                   const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_n(n))) return s;
+    if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_fwd: NULL pointer");
+    if (n > 0 && (!rec || !aligned(rec, 16))) return fail(XPR_ERR_INVALID, "xpr_render_fwd: rec NULL or unaligned");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_fwd: ranges must be 8-byte aligned");
+    return launch_render_fwd(rec, n, vals, ranges, *cam, *cfg, image, t_final, n_contrib, as_stream(stream));
+}
+
+int xpr_project_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
+                    const float *d_rec, const XprPrimsGrad *d_prims, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_n(n))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !d_prims || !d_rec || !prims->mu || !prims->scale || !prims->quat || !prims->opacity ||
+        !prims->sh || !d_prims->mu || !d_prims->scale || !d_prims->quat || !d_prims->opacity || !d_prims->sh)
+        return fail(XPR_ERR_INVALID, "xpr_project_bwd: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_rec, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_bwd: quat and d_rec must be 16-byte aligned");
+    return launch_project_bwd(*prims, n, *cam, *cfg, d_rec, *d_prims, as_stream(stream));
+}
+
+int xpr_render_bwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                   const XprConfig *cfg, const float *t_final, const int32_t *n_contrib, const float *d_image,
+                   float *d_rec, const XprPrims *prims, const XprPrimsGrad *d_prims, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_n(n))) return s;
+    if (!ranges || !t_final || !n_contrib || !d_image) return fail(XPR_ERR_INVALID, "xpr_render_bwd: NULL pointer");
+    if (n == 0) return XPR_OK;
+    if (!rec || !d_rec || !aligned(rec, 16) || !aligned(d_rec, 16))
+        return fail(XPR_ERR_INVALID, "xpr_render_bwd: rec/d_rec NULL or not 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    if ((s = launch_render_bwd(rec, vals, ranges, *cam, *cfg, t_final, n_contrib, d_image, d_rec, n, st))) return s;
+    if (prims && d_prims) return xpr_project_bwd(prims, n, cam, cfg, d_rec, d_prims, stream);
+    return XPR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// Rasterizer, second half (Sec. 4.2 "Sort and identify bounds"): stable LSD radix sort of the
+// (tile << 32 | depth bits, primitive) pairs over the bits that can be non-zero, then the per-tile
+// segment bounds [start, end).
+//
+// Each 8-bit pass is reduce-then-scan: a histogram kernel writes per-block digit counts in
+// digit-major order, the device-wide exclusive scan turns them into global output offsets, and
+// the scatter kernel ranks keys stably inside each warp with __match_any_sync (warp w owns a
+// contiguous run of 512 keys, visited in index order) before writing them to their offsets.
+#include "xpr_internal.cuh"
+
+namespace xpr {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kWarps = kThreads / 32;
+constexpr int kWarpKeys = 32 * kItems;   // 512
+constexpr int kTile = kThreads * kItems;  // 4096
+constexpr int kRadix = 256;
+
+__global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint64_t *__restrict__ kin, int64_t n, int shift,
+                                                              uint32_t mask, int32_t *__restrict__ hist,
+                                                              int64_t nb) {
+    __shared__ int s[kRadix];
+    s[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < kTile; k += kThreads) {
+        const int64_t j = base + k;
+        if (j < n) atomicAdd(&s[(uint32_t)(kin[j] >> shift) & mask], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nb + blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t *__restrict__ kin,
+                                                                 const uint32_t *__restrict__ vin,
+                                                                 uint64_t *__restrict__ kout,
+                                                                 uint32_t *__restrict__ vout, int64_t n, int shift,
+                                                                 uint32_t mask,
+                                                                 const int32_t *__restrict__ digit_off,
+                                                                 int64_t nb) {
+    __shared__ int s_hist[kWarps][kRadix];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kWarps * kRadix; d += kThreads) (&s_hist[0][0])[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * kWarpKeys;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    uint64_t key[kItems];
+    uint32_t val[kItems];
+    int rank[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t j = base + r * 32 + lane;
+        const bool valid = j < n;
+        key[r] = valid ? kin[j] : 0ull;
+        val[r] = valid ? vin[j] : 0u;
+        const int d = valid ? (int)((uint32_t)(key[r] >> shift) & mask) : kRadix;  // kRadix = padding
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        int cur = 0;
+        if (valid) cur = s_hist[w][d];
+        __syncwarp();
+        if (valid && lane == leader) s_hist[w][d] = cur + __popc(peers);
+        __syncwarp();
+        rank[r] = cur + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    {
+        // exclusive prefix over the warps of this block, offset by the block's global digit base
+        const int d = threadIdx.x;
+        int run = digit_off[(int64_t)d * nb + blockIdx.x];
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            const int c = s_hist[ww][d];
+            s_hist[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t j = base + r * 32 + lane;
+        if (j < n) {
+            const int d = (int)((uint32_t)(key[r] >> shift) & mask);
+            const int pos = s_hist[w][d] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+__global__ void tile_ranges_kernel(const uint64_t *__restrict__ keys, int64_t n, uint32_t n_tiles,
+                                   int2 *__restrict__ ranges) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    if (t >= n_tiles) return;  // keys outside the tile grid have no segment
+    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (int)i;
+    if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (int)(i + 1);
+}
+
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+int bits_for(int64_t x) {
+    int b = 0;
+    while (x > 0) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+}  // namespace
+
+size_t sort_workspace_bytes(int64_t n, int32_t n_tiles) {
+    (void)n_tiles;
+    const int64_t nb = (n + kTile - 1) / kTile;
+    const int64_t nh = (int64_t)kRadix * (nb > 0 ? nb : 1);
+    return align256((size_t)n * 8) + align256((size_t)n * 4) + align256((size_t)(nh + 1) * 4) +
+           scan_partials_bytes(nh);
+}
+
+int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, uint64_t *keys_out,
+                uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {
+    XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(int32_t), st));
+    if (n == 0) return XPR_OK;
+    if (ws_bytes < sort_workspace_bytes(n, n_tiles))
+        return fail(XPR_ERR_INVALID, "xpr_sort: workspace %zu bytes < required %zu", ws_bytes,
+                    sort_workspace_bytes(n, n_tiles));
+    const int64_t nb = (n + kTile - 1) / kTile;
+    const int64_t nh = (int64_t)kRadix * nb;
+    char *p = reinterpret_cast<char *>(ws);
+    uint64_t *alt_k = reinterpret_cast<uint64_t *>(p);
+    p += align256((size_t)n * 8);
+    uint32_t *alt_v = reinterpret_cast<uint32_t *>(p);
+    p += align256((size_t)n * 4);
+    int32_t *hist = reinterpret_cast<int32_t *>(p);
+    p += align256((size_t)(nh + 1) * 4);
+    void *scan_ws = p;
+
+    const int end_bit = 32 + bits_for((int64_t)n_tiles - 1);
+    const int passes = (end_bit + 7) / 8;
+    const uint64_t *src_k = keys_in;
+    const uint32_t *src_v = vals_in;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        const int nbits = min(8, end_bit - shift);
+        const uint32_t mask = (1u << nbits) - 1u;
+        const bool to_out = ((passes - 1 - pass) % 2) == 0;
+        uint64_t *dst_k = to_out ? keys_out : alt_k;
+        uint32_t *dst_v = to_out ? vals_out : alt_v;
+        radix_hist_kernel<<<(unsigned)nb, kThreads, 0, st>>>(src_k, n, shift, mask, hist, nb);
+        XPR_LAUNCH_CHECK("radix_hist_kernel");
+        int s = launch_exclusive_scan(hist, hist, nh, scan_ws, nullptr, st);
+        if (s != XPR_OK) return s;
+        radix_scatter_kernel<<<(unsigned)nb, kThreads, 0, st>>>(src_k, src_v, dst_k, dst_v, n, shift, mask, hist,
+                                                               nb);
+        XPR_LAUNCH_CHECK("radix_scatter_kernel");
+        src_k = dst_k;
+        src_v = dst_v;
+    }
+    tile_ranges_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys_out, n, (uint32_t)n_tiles,
+                                                                    reinterpret_cast<int2 *>(ranges));
+    XPR_LAUNCH_CHECK("tile_ranges_kernel");
+    return XPR_OK;
+}
+
+}  // namespace xpr

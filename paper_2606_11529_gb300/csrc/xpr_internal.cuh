@@ -1,0 +1,106 @@
+// Internal declarations shared by the libxpr translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/xpr.h"
+
+namespace xpr {
+
+// ---- error reporting (per host thread) ---------------------------------------------------
+void set_error(const char *fmt, ...);
+int fail(int status, const char *fmt, ...);
+int check_launch(const char *what);
+
+#define XPR_CUDA_TRY(expr)                                                                          \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess) return ::xpr::fail(XPR_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
+    } while (0)
+
+#define XPR_LAUNCH_CHECK(what)                  \
+    do {                                        \
+        int _s = ::xpr::check_launch(what);     \
+        if (_s != XPR_OK) return _s;            \
+    } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int tiles_x(const XprCamera &c, const XprConfig &g) { return (c.width + g.tile_w - 1) / g.tile_w; }
+inline int tiles_y(const XprCamera &c, const XprConfig &g) { return (c.height + g.tile_h - 1) / g.tile_h; }
+
+int validate_camera_config(const XprCamera *cam, const XprConfig *cfg);
+
+// ---- launch helpers implemented per translation unit -------------------------------------
+int launch_project_fwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg, float *rec,
+                       int32_t *bbox, int32_t *tc, cudaStream_t st);
+int launch_project_bwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg,
+                       const float *d_rec, const XprPrimsGrad &g, cudaStream_t st);
+
+// Device-wide exclusive scan of int32 counts (in place allowed): out[i] = sum_{j<i} in[j],
+// out[n] = total.  partials: >= scan_partials_bytes(n) bytes.  total_out: device int64.
+size_t scan_partials_bytes(int64_t n);
+int64_t *scan_total_ptr(void *partials, int64_t n);  // where the scan leaves the total when total_out == NULL
+int launch_exclusive_scan(const int32_t *in, int32_t *out, int64_t n, void *partials, int64_t *total_out,
+                          cudaStream_t st);
+
+int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, int64_t n, const XprCamera &cam,
+                     const XprConfig &cfg, int32_t *counts, cudaStream_t st);
+int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, int64_t n, const XprCamera &cam,
+                    const XprConfig &cfg, const int32_t *offsets, uint64_t *keys, uint32_t *vals, cudaStream_t st);
+
+size_t sort_workspace_bytes(int64_t n, int32_t n_tiles);
+int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, uint64_t *keys_out,
+                uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st);
+
+int launch_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges,
+                      const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final, int32_t *n_contrib,
+                      cudaStream_t st);
+int launch_render_bwd(const float *rec, const uint32_t *vals, const int32_t *ranges, const XprCamera &cam,
+                      const XprConfig &cfg, const float *t_final, const int32_t *n_contrib, const float *d_image,
+                      float *d_rec, int64_t n, cudaStream_t st);
+
+// ---- device helpers -----------------------------------------------------------------------
+#ifdef __CUDACC__
+constexpr float kLog2e = 1.4426950408889634f;  // log2(e)
+constexpr float kLn2 = 0.6931471805599453f;    // ln(2)
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Staged shading coefficients of one list entry (paper's p_sd with the conic pre-scaled
+// by log2(e) so that exp(power) = 2^(A dx^2 + B dx dy + C dy^2)).
+struct Shade {
+    float mx, my, A, B, C, o, r, g, b;
+};
+
+__device__ __forceinline__ Shade load_shade(const float *__restrict__ rec, uint32_t id) {
+    const float4 *p = reinterpret_cast<const float4 *>(rec + (size_t)id * XPR_REC_FLOATS);
+    float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    Shade s;
+    s.mx = a.x;
+    s.my = a.y;
+    s.A = __fmul_rn(-0.5f * kLog2e, a.z);
+    s.B = __fmul_rn(-kLog2e, a.w);
+    s.C = __fmul_rn(-0.5f * kLog2e, b.x);
+    s.o = b.y;
+    s.r = b.z;
+    s.g = b.w;
+    s.b = c.x;
+    return s;
+}
+
+// Listing 1 evaluate in base-2 form.  Every operation is an explicit IEEE intrinsic so
+// the forward and the backward kernels compute bit-identical powers and alphas.
+__device__ __forceinline__ float eval_power2(float A, float B, float C, float dx, float dy) {
+    float t = __fmaf_rn(A, dx, __fmul_rn(B, dy));  // A dx + B dy
+    float u = __fmul_rn(__fmul_rn(C, dy), dy);     // C dy^2
+    return __fmaf_rn(t, dx, u);                    // A dx^2 + B dx dy + C dy^2
+}
+#endif
+
+}  // namespace xpr

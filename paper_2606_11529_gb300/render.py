@@ -1,0 +1,155 @@
+"""3DGS tile-splatting path on the GPU: the plain per-stage calls and the
+``torch.autograd.Function`` that chains them.
+
+Forward  = xpr_project -> xpr_tile_bin -> xpr_sort -> xpr_render_fwd
+Backward = xpr_render_bwd (compositing adjoint, then projection adjoint)
+
+The Function takes activated parameters (mu, scale, quat, opacity, sh), as in
+the paper's PrimitiveParams, and returns the image [3, H, W].  Gradients are
+produced for all five parameter tensors.  Buffers are allocated by PyTorch's
+caching allocator; the intersection buffers start at the size seen on the
+previous call with the same ``Workspace`` so the capacity retry of
+xpr_tile_bin is rare.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import binding as B
+
+
+class Workspace:
+    """Per-stream state of the forward: the last intersection count (initial capacity guess for
+    xpr_tile_bin) and the transient scratch of xpr_tile_bin / xpr_sort.  Per-frame outputs are
+    fresh tensors from PyTorch's caching allocator, so a Frame stays valid after later calls."""
+
+    def __init__(self):
+        self.last_isect = 0
+        self.bufs = {}
+
+    def scratch(self, name, nbytes, device):
+        t = self.bufs.get(name)
+        if t is None or t.numel() < nbytes or t.device != device:
+            t = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+            self.bufs[name] = t
+        return t
+
+
+class StageTimers:
+    """Optional CUDA-event brackets around each C-ABI call (recorded on the launching stream)."""
+
+    def __init__(self):
+        self.events = {}
+
+    def start(self, name, stream=None):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        self.events.setdefault(name, []).append((e0, e1))
+
+    def stop(self, name, stream=None):
+        self.events[name][-1][1].record(stream)
+
+    def mean_ms(self):
+        torch.cuda.synchronize()
+        return {k: sum(a.elapsed_time(b) for a, b in v) / len(v) for k, v in self.events.items()}
+
+    def reset(self):
+        self.events = {}
+
+
+class _NoTimers:
+    def start(self, name, stream=None):
+        pass
+
+    def stop(self, name, stream=None):
+        pass
+
+
+_NO_TIMERS = _NoTimers()
+
+
+@dataclass
+class Frame:
+    """Everything the forward produces (kept for the backward and for tests)."""
+    rec: torch.Tensor
+    bbox: torch.Tensor
+    tile_count: torch.Tensor
+    offsets: torch.Tensor
+    keys: torch.Tensor
+    vals: torch.Tensor
+    n_isect: int
+    keys_sorted: torch.Tensor
+    vals_sorted: torch.Tensor
+    ranges: torch.Tensor
+    image: torch.Tensor
+    t_final: torch.Tensor
+    n_contrib: torch.Tensor
+
+
+def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
+                  timers=None) -> Frame:
+    """The four forward stages, each one C-ABI call."""
+    L = B.load()
+    tm = timers or _NO_TIMERS
+    ccam, ccfg = B.make_camera(cam), B.make_config(cfg)
+    n = mu.shape[0]
+    dev = mu.device
+    ws = ws or Workspace()
+    tm.start("project", stream)
+    rec, bbox, tc = B.xpr_project(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream)
+    tm.stop("project", stream)
+    cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
+    bin_ws = ws.scratch("bin", L.xpr_tile_bin_workspace(n), dev)
+    tm.start("tile_bin", stream)
+    offsets, keys, vals, I = B.xpr_tile_bin(rec, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
+                                            stream=stream)
+    tm.stop("tile_bin", stream)
+    ws.last_isect = I
+    Wt, Ht = B.tiles_of(cam, cfg)
+    nt = Wt * Ht
+    sort_ws = ws.scratch("sort", L.xpr_sort_workspace(I, nt), dev)
+    tm.start("sort", stream)
+    ks, vs, ranges = B.xpr_sort(keys, vals, nt, workspace=sort_ws, stream=stream)
+    tm.stop("sort", stream)
+    tm.start("render_fwd", stream)
+    image, t_final, n_contrib = B.xpr_render_fwd(rec, vs, ranges, ccam, ccfg, stream=stream)
+    tm.stop("render_fwd", stream)
+    return Frame(rec, bbox, tc, offsets, keys, vals, I, ks, vs, ranges, image, t_final, n_contrib)
+
+
+class SplatFunction(torch.autograd.Function):
+    """image = splat(mu, scale, quat, opacity, sh); backward gives all five gradients."""
+
+    @staticmethod
+    def forward(ctx, mu, scale, quat, opacity, sh, cam, cfg, ws, timers):
+        fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, timers=timers)
+        ctx.save_for_backward(mu, scale, quat, opacity, sh, fr.rec, fr.vals_sorted, fr.ranges, fr.t_final,
+                              fr.n_contrib)
+        ctx.cam, ctx.cfg, ctx.timers = cam, cfg, timers
+        return fr.image
+
+    @staticmethod
+    def backward(ctx, d_image):
+        mu, scale, quat, opacity, sh, rec, vals, ranges, t_final, n_contrib = ctx.saved_tensors
+        tm = ctx.timers or _NO_TIMERS
+        ccam, ccfg = B.make_camera(ctx.cam), B.make_config(ctx.cfg)
+        tm.start("render_bwd")
+        d_rec = B.xpr_render_bwd(rec, vals, ranges, ccam, ccfg, t_final, n_contrib, d_image.contiguous())
+        tm.stop("render_bwd")
+        tm.start("project_bwd")
+        grads = B.xpr_project_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_rec)
+        tm.stop("project_bwd")
+        return (*grads, None, None, None, None)
+
+
+def render(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, timers: StageTimers | None = None):
+    """Differentiable render of one view: returns image [3, H, W]."""
+    return SplatFunction.apply(mu, scale, quat, opacity, sh, cam, cfg, ws or Workspace(), timers)
+
+
+def scene_to_device(scene, device="cuda"):
+    """Float32 contiguous device tensors (mu, scale, quat, opacity, sh) of a scenes.Scene."""
+    return tuple(torch.from_numpy(a).to(device).contiguous() for a in scene.arrays())

@@ -1,0 +1,100 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every
+entry point declared in include/xpr.h, and rejects invalid arguments on the
+host before any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "xpr.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(xpr_\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_11529_gb300 import binding, build
+    build.build()
+    return binding.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2606_11529_gb300 import binding, build
+    names = _declared()
+    assert len(names) >= 10
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(xpr_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    # and the binding knows the signature of each of them
+    assert set(names) <= set(binding.SIGNATURES)
+
+
+def test_library_is_sm103a(lib):
+    from paper_2606_11529_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    assert lib.xpr_version() == 1
+
+
+def test_status_strings(lib):
+    assert lib.xpr_status_string(0) == b"ok"
+    assert b"capacity" in lib.xpr_status_string(2)
+    assert lib.xpr_status_string(99) == b"unknown status"
+
+
+def _cam_cfg(**over):
+    from paper_2606_11529_gb300 import binding, scenes
+    cam = binding.make_camera(scenes.pinhole(64, 48, 64.0))
+    cfg = binding.make_config(scenes.RenderConfig())
+    for k, v in over.items():
+        if hasattr(cam, k):
+            setattr(cam, k, v)
+        else:
+            setattr(cfg, k, v)
+    return cam, cfg
+
+
+@pytest.mark.parametrize("over,frag", [
+    (dict(tile_w=7), b"tile size"),
+    (dict(tile_h=32), b"tile size"),
+    (dict(width=0), b"image size"),
+    (dict(sh_degree=4), b"sh_degree"),
+    (dict(alpha_max=1.0), b"alpha_max"),
+    (dict(model=1), b"camera model"),
+])
+def test_invalid_arguments_rejected_on_host(lib, over, frag):
+    from paper_2606_11529_gb300 import binding
+    cam, cfg = _cam_cfg(**over)
+    p = binding.XprPrims(1, 1, 16, 1, 1)  # never dereferenced: validation fails first
+    s = lib.xpr_project(ctypes.byref(p), 1, ctypes.byref(cam), ctypes.byref(cfg), 16, 16, 16, None)
+    assert s == binding.XPR_ERR_INVALID
+    assert frag in lib.xpr_last_error()
+
+
+def test_null_and_alias_rejected(lib):
+    from paper_2606_11529_gb300 import binding
+    cam, cfg = _cam_cfg()
+    s = lib.xpr_project(None, 5, ctypes.byref(cam), ctypes.byref(cfg), None, None, None, None)
+    assert s == binding.XPR_ERR_INVALID
+    s = lib.xpr_sort(256, 256, 10, 4, 256, 512, 1024, 4096, 1 << 20, None)
+    assert s == binding.XPR_ERR_INVALID and b"alias" in lib.xpr_last_error()
+    n = ctypes.c_int64(0)
+    s = lib.xpr_tile_bin(256, 256, 256, 10, ctypes.byref(cam), ctypes.byref(cfg), 256, 256, 256, -1,
+                         ctypes.byref(n), 256, 1 << 20, None)
+    assert s == binding.XPR_ERR_INVALID and b"capacity" in lib.xpr_last_error()
+    s = lib.xpr_project(None, -1, ctypes.byref(cam), ctypes.byref(cfg), None, None, None, None)
+    assert s == binding.XPR_ERR_INVALID
+
+
+def test_workspace_sizes_monotone(lib):
+    a = lib.xpr_sort_workspace(1000, 256)
+    b = lib.xpr_sort_workspace(100000, 256)
+    assert 0 < a < b
+    assert lib.xpr_tile_bin_workspace(10) >= 16
+    assert lib.xpr_tile_bin_workspace(10_000_000) > lib.xpr_tile_bin_workspace(10)
