@@ -137,6 +137,25 @@ int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_coun
                  const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t capacity,
                  int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
 
+/* xpr_tile_bin_noalloc: xpr_tile_bin without a workspace argument, for callers
+ * that cannot allocate device memory (for example a process whose device
+ * memory belongs to another framework's pool, or a latency-critical loop that
+ * must not call cudaMalloc/cudaFree because they can synchronise the device).
+ * The paper has no counterpart; this is a convenience of the library.
+ * Scratch: a file-scope __device__ array of 131,328 bytes inside libxpr.so,
+ * held by every GPU that loads the library until the process exits.
+ * Limit: n <= 67,108,864 primitives; larger n returns XPR_ERR_INVALID.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call shares the array: nothing
+ * in it needs to start at zero (each call writes all it reads), but calls that
+ * overlap on the GPU (different streams, or different host threads on one
+ * device) race on it and must be serialised by the caller.  Allocates nothing;
+ * arguments, outputs and errors are those of xpr_tile_bin. */
+int xpr_tile_bin_noalloc(const float *rec, const int32_t *bbox, const int32_t *tile_count, int64_t n,
+                         const XprCamera *cam, const XprConfig *cfg, int32_t *offsets, uint64_t *keys,
+                         uint32_t *vals, int64_t capacity, int64_t *n_isect, void *stream);
+
 /* ---- Rasterizer: sort and identify bounds ---------------------------------
  * xpr_sort (Sec. 4.2 "Sort and identify bounds"): stable LSD radix sort of
  * (key, val) by key over the low 32 + ceil(log2(n_tiles)) bits, so equal

@@ -48,6 +48,8 @@ SIGNATURES = {
     "xpr_tile_bin_workspace": (c_sz, [c_i64]),
     "xpr_tile_bin": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
                              c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
+    "xpr_tile_bin_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                                     c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp]),
     "xpr_sort_workspace": (c_sz, [c_i64, c_i32]),
     "xpr_sort": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "xpr_render_fwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
