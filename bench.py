@@ -54,7 +54,10 @@ def peaks():
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 50 ms, timestamped) taken from before the warm-up to after the
+    timed region; the report uses the samples inside the timed window when there are any, else
+    all samples of the run (and says so)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -62,19 +65,33 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.f = None
+        self.window = None
 
     def start(self):
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    @staticmethod
+    def _epoch(ts):
+        import datetime
+        try:
+            dt = datetime.datetime.strptime(ts.strip(), "%Y/%m/%d %H:%M:%S.%f")
+            return time.mktime(dt.timetuple()) + dt.microsecond * 1e-6
+        except ValueError:
+            return None
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -82,25 +99,35 @@ class ClockSampler:
             self.proc.kill()
         self.f.flush()
         self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        rows = [[x.strip() for x in r.split(",")] for r in self.f.read().strip().splitlines() if r.strip()]
         self.f.close()
         os.unlink(self.f.name)
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        samples = []
         for r in rows:
-            r = [x.strip() for x in r]
-            if len(r) < 9:
+            if len(r) < 10:
                 continue
             try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
+                samples.append((self._epoch(r[0]), float(r[2]), float(r[3]), r[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, r[5:9]):
+        scope = "timed region"
+        sel = samples
+        if self.window:
+            inside = [s for s in samples if s[0] is not None and self.window[0] - 0.05 <= s[0] <= self.window[1] + 0.05]
+            if inside:
+                sel = inside
+            else:
+                scope = "whole run (timed region shorter than the sampling interval)"
+        reasons = set()
+        for s in sel:
+            for nm, v in zip(names, s[3]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        sm = [s[1] for s in sel]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(s[2] for s in sel) if sel else None, "reasons": sorted(reasons),
+                "samples": len(sel), "scope": scope}
 
 
 # --------------------------------------------------------------------------- reference arm (oracle on CPU)
@@ -184,20 +211,21 @@ def main():
         loss.backward()
         return loss
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
 
     timers = R.StageTimers()
-    clocks = ClockSampler(local)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = L.xpr_launch_count()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     t_wall = time.perf_counter()
+    t_epoch0 = time.time()
     for k in range(args.steps):
         flush.fill_(k & 0xFF)  # evict L2 between steps (outside the timed events)
         starts[k].record()
@@ -205,6 +233,7 @@ def main():
         ends[k].record()
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
+    clocks.mark(t_epoch0, time.time())
     clk = clocks.stop()
     launches = int(L.xpr_launch_count() - launches0)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -222,10 +251,11 @@ def main():
     pairs = int(fr.n_contrib.to(torch.int64).sum().item())
     I = fr.n_isect
     n = sc.n
-    passes = math.ceil((32 + max(1, (fr.ranges.shape[0] - 1).bit_length())) / 8)
+    passes = math.ceil(max(1, (fr.ranges.shape[0] - 1).bit_length()) / 8)  # tile bits only (depth-ordered input)
     pk = peaks()
     work = {
         "project": ("hbm", n * (PARAM_BYTES + REC_BYTES + 16 + 4)),
+        "depth_order": ("hbm", n * (4 + 4 + 4) + 4 * n * 24),  # key build + 4 passes over 12-byte pairs
         "tile_bin": ("hbm", n * 2 * (REC_BYTES + 16 + 4) + n * 4 + I * 12),
         "sort": ("hbm", passes * 24 * I),
         "render_fwd": ("alu", pairs * FWD_OPS_PER_PAIR),

@@ -29,6 +29,7 @@ _F32P = ctypes.POINTER(ctypes.c_float)
 _I32P = ctypes.POINTER(ctypes.c_int32)
 _U32P = ctypes.POINTER(ctypes.c_uint32)
 _U64P = ctypes.POINTER(ctypes.c_uint64)
+_I64P = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False) -> str:
@@ -51,7 +52,7 @@ def lib():
         L = ctypes.CDLL(_LIB)
         L.oracle_project.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                      _I32P, _I32P, _F64P, _F64P]
-        L.oracle_bin.argtypes = [ctypes.c_int64, _F64P, _F32P, _I32P, _F64P, _F64P, ctypes.c_int, _I32P, _U64P,
+        L.oracle_bin.argtypes = [ctypes.c_int64, _F64P, _F32P, _I32P, _F64P, _F64P, ctypes.c_int, _I64P, _I32P, _U64P,
                                  _U32P]
         L.oracle_bin.restype = ctypes.c_int64
         L.oracle_sort.argtypes = [ctypes.c_int64, _U64P, _U32P, ctypes.c_int64, _I32P]
@@ -141,22 +142,33 @@ def project_bwd(mu, scale, quat, opac, sh, cam, cfg, d_rec):
 
 # --------------------------------------------------------------------------- binning / sort
 
-def bin_pairs(rec, bbox, cam, cfg, exact32: bool):
-    """Replicate + tile ID + cull in primitive order.  With exact32, ``rec``
-    must be float32 records (the decision is taken in FP32)."""
+def bin_pairs(rec, bbox, cam, cfg, exact32: bool, order=None):
+    """Replicate + tile ID + cull, visiting primitives in ``order`` (index order when None);
+    counts are per visited position.  With exact32, ``rec`` must be float32 records (the decision
+    is taken in FP32)."""
     bbox = np.ascontiguousarray(bbox, np.int32)
     n = bbox.shape[0]
+    od = None if order is None else np.ascontiguousarray(order, np.int64)
     ca, fa = cam_array(cam), cfg_array(cfg)
     r64 = None if exact32 else _f64(rec)
     r32 = np.ascontiguousarray(rec, np.float32) if exact32 else None
     counts = np.zeros(n, np.int32)
     total = lib().oracle_bin(n, _p(r64, _F64P), _p(r32, _F32P), _p(bbox, _I32P), _p(ca, _F64P), _p(fa, _F64P),
-                             int(exact32), _p(counts, _I32P), None, None)
+                             int(exact32), _p(od, _I64P), _p(counts, _I32P), None, None)
     keys = np.zeros(max(total, 1), np.uint64)
     vals = np.zeros(max(total, 1), np.uint32)
     lib().oracle_bin(n, _p(r64, _F64P), _p(r32, _F32P), _p(bbox, _I32P), _p(ca, _F64P), _p(fa, _F64P),
-                     int(exact32), _p(counts, _I32P), _p(keys, _U64P), _p(vals, _U32P))
+                     int(exact32), _p(od, _I64P), _p(counts, _I32P), _p(keys, _U64P), _p(vals, _U32P))
     return counts, keys[:total].copy(), vals[:total].copy()
+
+
+def depth_order(rec, tc):
+    """Primitives with tiles by (float32 camera depth, index), then the rest in index order."""
+    d32 = np.asarray(rec, np.float64)[:, 9].astype(np.float32)
+    has = np.asarray(tc) > 0
+    idx = np.arange(len(has))
+    vis = idx[has][np.lexsort((idx[has], d32[has]))]
+    return np.concatenate([vis, idx[~has]]).astype(np.int64)
 
 
 def sort_pairs(keys, vals, n_tiles):

@@ -467,15 +467,19 @@ static uint32_t f32_bits(float f) {
  * x = xmin + r mod w_i, y = ymin + r div w_i, t = y W' + x), keep the pair if
  * the cull passes and emit key = (t << 32) | bits(float(depth)), val = i.
  * exact32 != 0: rec32 (float records) with the FP32 cull; else rec64 with the
- * FP64 cull.  counts[n] receives the surviving count per primitive.  keys and
- * vals may be NULL (count only).  Returns the total. */
+ * FP64 cull.  order (may be NULL = index order) gives the order in which the
+ * primitives are visited; counts[n] receives the surviving count per visited
+ * position.  keys and vals may be NULL (count only).  Returns the total. */
 int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const int32_t *bbox, const double *camv,
-                   const double *cfgv, int exact32, int32_t *counts, uint64_t *keys, uint32_t *vals) {
+                   const double *cfgv, int exact32, const int64_t *order, int32_t *counts, uint64_t *keys,
+                   uint32_t *vals) {
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
     int Wt = (cam.W + cfg.tw - 1) / cfg.tw;
     int64_t total = 0;
-    for (int64_t i = 0; i < n; ++i) {
+    /* primitives are visited in the given order (identity when NULL); counts are per position */
+    for (int64_t pos = 0; pos < n; ++pos) {
+        int64_t i = order ? order[pos] : pos;
         const int32_t *bb = bbox + 4 * i;
         int w = bb[2] - bb[0], h = bb[3] - bb[1];
         int tc = (w > 0 && h > 0) ? w * h : 0;
@@ -504,7 +508,7 @@ int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const int
             ++total;
             ++cnt;
         }
-        if (counts) counts[i] = cnt;
+        if (counts) counts[pos] = cnt;
     }
     return total;
 }

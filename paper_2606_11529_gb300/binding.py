@@ -46,12 +46,14 @@ SIGNATURES = {
     "xpr_project": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
                             c_vp, c_vp, c_vp, c_vp]),
     "xpr_tile_bin_workspace": (c_sz, [c_i64]),
-    "xpr_tile_bin": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
-                             c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
-    "xpr_tile_bin_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
-                                     c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp]),
+    "xpr_depth_order_workspace": (c_sz, [c_i64]),
+    "xpr_depth_order": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp]),
+    "xpr_tile_bin": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                             c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
+    "xpr_tile_bin_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera),
+                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp]),
     "xpr_sort_workspace": (c_sz, [c_i64, c_i32]),
-    "xpr_sort": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "xpr_sort": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "xpr_render_fwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
                                c_vp, c_vp, c_vp]),
     "xpr_render_bwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
@@ -169,11 +171,23 @@ def xpr_project(mu, scale, quat, opacity, sh, cam, cfg, rec=None, bbox=None, til
     return rec, bbox, tile_count
 
 
+def xpr_depth_order(rec, tile_count, order=None, workspace=None, stream=None):
+    L = load()
+    n = rec.shape[0]
+    order = torch.empty(n, dtype=torch.int32, device=rec.device) if order is None else order
+    need = int(L.xpr_depth_order_workspace(n))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=rec.device)
+    _check(L.xpr_depth_order(_ptr(rec), _ptr(tile_count), n, _ptr(order), _ptr(workspace), workspace.numel(),
+                             _stream(stream)), "xpr_depth_order")
+    return order
+
+
 def xpr_tile_bin(rec, bbox, tile_count, cam, cfg, capacity=None, offsets=None, keys=None, vals=None,
-                 workspace=None, stream=None):
-    """Returns (offsets[n+1], keys[I], vals[I], I).  ``capacity``: initial guess for the
-    intersection buffers; on XPR_ERR_CAPACITY they are re-allocated to the reported size and the
-    call is repeated."""
+                 workspace=None, stream=None, order=None):
+    """Returns (offsets[n+1], keys[I], vals[I], I).  ``order``: optional emission order (int32
+    permutation).  ``capacity``: initial guess for the intersection buffers; on XPR_ERR_CAPACITY
+    they are re-allocated to the reported size and the call is repeated."""
     L = load()
     n = rec.shape[0]
     dev = rec.device
@@ -188,7 +202,7 @@ def xpr_tile_bin(rec, bbox, tile_count, cam, cfg, capacity=None, offsets=None, k
     c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
     for _ in range(2):
         n_isect = c_i64(0)
-        s = L.xpr_tile_bin(_ptr(rec), _ptr(bbox), _ptr(tile_count), n, ctypes.byref(c), ctypes.byref(g),
+        s = L.xpr_tile_bin(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(order), n, ctypes.byref(c), ctypes.byref(g),
                            _ptr(offsets), _ptr(keys), _ptr(vals), keys.numel(), ctypes.byref(n_isect),
                            _ptr(workspace), workspace.numel(), _stream(stream))
         if s == XPR_ERR_CAPACITY and n_isect.value <= 0x7FFFFFFF:
@@ -201,7 +215,8 @@ def xpr_tile_bin(rec, bbox, tile_count, cam, cfg, capacity=None, offsets=None, k
     raise XprError(XPR_ERR_CAPACITY, "xpr_tile_bin", "capacity retry failed")
 
 
-def xpr_sort(keys, vals, n_tiles, keys_out=None, vals_out=None, ranges=None, workspace=None, stream=None):
+def xpr_sort(keys, vals, n_tiles, keys_out=None, vals_out=None, ranges=None, workspace=None, stream=None,
+             begin_bit=0):
     L = load()
     n = keys.numel()
     dev = keys.device
@@ -211,7 +226,7 @@ def xpr_sort(keys, vals, n_tiles, keys_out=None, vals_out=None, ranges=None, wor
     need = int(L.xpr_sort_workspace(n, n_tiles))
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
-    _check(L.xpr_sort(_ptr(keys), _ptr(vals), n, n_tiles, _ptr(keys_out), _ptr(vals_out), _ptr(ranges),
+    _check(L.xpr_sort(_ptr(keys), _ptr(vals), n, n_tiles, begin_bit, _ptr(keys_out), _ptr(vals_out), _ptr(ranges),
                       _ptr(workspace), workspace.numel(), _stream(stream)), "xpr_sort")
     return keys_out, vals_out, ranges
 

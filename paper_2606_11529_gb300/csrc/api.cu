@@ -98,9 +98,9 @@ int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const Xp
 
 size_t xpr_tile_bin_workspace(int64_t n) { return scan_partials_bytes(n < 0 ? 0 : n); }
 
-int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, int64_t n, const XprCamera *cam,
-                 const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t capacity,
-                 int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream) {
+int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
+                 const XprCamera *cam, const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *vals,
+                 int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
     if ((s = check_n(n))) return s;
@@ -117,7 +117,7 @@ int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_coun
         *n_isect = 0;
         return XPR_OK;
     }
-    if ((s = launch_bin_count(rec, bbox, tile_count, n, *cam, *cfg, offsets, st))) return s;
+    if ((s = launch_bin_count(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, st))) return s;
     if ((s = launch_exclusive_scan(offsets, offsets, n, workspace, nullptr, st))) return s;
     const int64_t *tot_dev = scan_total_ptr(workspace, n);
     int64_t total = 0;
@@ -130,25 +130,39 @@ int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_coun
         return fail(XPR_ERR_CAPACITY, "xpr_tile_bin: %lld intersections > capacity %lld", (long long)total,
                     (long long)capacity);
     if (total > 0 && (!keys || !vals)) return fail(XPR_ERR_INVALID, "xpr_tile_bin: NULL keys/vals");
-    return launch_bin_emit(rec, bbox, tile_count, n, *cam, *cfg, offsets, keys, vals, st);
+    return launch_bin_emit(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, keys, vals, st);
+}
+
+size_t xpr_depth_order_workspace(int64_t n) { return depth_order_workspace_bytes(n < 0 ? 0 : n); }
+
+int xpr_depth_order(const float *rec, const int32_t *tile_count, int64_t n, int32_t *order, void *workspace,
+                    size_t ws_bytes, void *stream) {
+    int s = check_n(n);
+    if (s) return s;
+    if (n == 0) return XPR_OK;
+    if (!rec || !tile_count || !order || !workspace) return fail(XPR_ERR_INVALID, "xpr_depth_order: NULL pointer");
+    if (!aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_depth_order: workspace must be 256-byte aligned");
+    return launch_depth_order(rec, tile_count, n, order, workspace, ws_bytes, as_stream(stream));
 }
 
 size_t xpr_sort_workspace(int64_t n_isect, int32_t n_tiles) {
     return sort_workspace_bytes(n_isect < 0 ? 0 : n_isect, n_tiles);
 }
 
-int xpr_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n_isect, int32_t n_tiles, uint64_t *keys_out,
-             uint32_t *vals_out, int32_t *ranges, void *workspace, size_t ws_bytes, void *stream) {
+int xpr_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n_isect, int32_t n_tiles, int32_t begin_bit,
+             uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *workspace, size_t ws_bytes,
+             void *stream) {
     if (n_isect < 0 || n_isect > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "xpr_sort: bad count");
     if (n_tiles < 1) return fail(XPR_ERR_INVALID, "xpr_sort: n_tiles must be >= 1");
+    if (begin_bit < 0 || begin_bit > 32) return fail(XPR_ERR_INVALID, "xpr_sort: begin_bit must be in [0, 32]");
     if (!ranges) return fail(XPR_ERR_INVALID, "xpr_sort: NULL ranges");
     if (n_isect > 0 && (!keys_in || !vals_in || !keys_out || !vals_out || !workspace))
         return fail(XPR_ERR_INVALID, "xpr_sort: NULL pointer");
     if (n_isect > 0 && (keys_in == keys_out || vals_in == vals_out))
         return fail(XPR_ERR_INVALID, "xpr_sort: input and output buffers must not alias");
     if (n_isect > 0 && !aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_sort: workspace alignment");
-    return launch_sort(keys_in, vals_in, n_isect, n_tiles, keys_out, vals_out, ranges, workspace, ws_bytes,
-                       as_stream(stream));
+    return launch_sort(keys_in, vals_in, n_isect, n_tiles, begin_bit, keys_out, vals_out, ranges, workspace,
+                       ws_bytes, as_stream(stream));
 }
 
 int xpr_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,

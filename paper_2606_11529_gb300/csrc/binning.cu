@@ -69,42 +69,110 @@ struct Grid {
     int W, H, tw, th, Wt, Ht;
 };
 
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kSmallBox = 16;  // boxes with more tiles than this are walked by a whole warp
+
+__device__ __forceinline__ bool keep_tile(const CullData &d, const Grid &g, int tx, int ty) {
+    const float x0 = (float)(tx * g.tw), x1 = (float)min(tx * g.tw + g.tw - 1, g.W - 1);
+    const float y0 = (float)(ty * g.th), y1 = (float)min(ty * g.th + g.th - 1, g.H - 1);
+    return tile_keep(d, x0, y0, x1, y1);
+}
+
+// Position j of the emission order handles primitive i = order[j] (identity when order is NULL).
+// COUNT (EMIT = false) writes the surviving count of position j into counts_or_offsets[j]; EMIT
+// writes the pairs at offsets[j] in slot order r (row-major over the box).  Boxes of at most
+// kSmallBox tiles are walked by their own thread; larger ones by the whole warp, 32 slots at a
+// time, with ballot prefix counts keeping the pairs in r order.
+//
+// Thread t visits position j = (t * stride) mod n with stride coprime to n (a bijection).  Outputs are
+// indexed by j, so the visiting order changes nothing but the schedule: in depth order the
+// near-camera primitives with the largest boxes are neighbours, and a contiguous assignment would
+// pile them onto the same few warps.
 template <bool EMIT>
 __global__ void __launch_bounds__(256) bin_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
-                                                  const int *__restrict__ tcount, int64_t n, Grid g,
+                                                  const int *__restrict__ tcount, const int *__restrict__ order,
+                                                  int64_t n, int64_t stride, Grid g,
                                                   int32_t *__restrict__ counts_or_offsets,
                                                   uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int cnt = 0;
-    const int tc = tcount[i];
-    int64_t out = EMIT ? (int64_t)counts_or_offsets[i] : 0;
-    if (tc > 0) {
-        int4 bb = bbox[i];
-        bb.x = max(bb.x, 0);  // never leave the tile grid, whatever the caller's boxes say
-        bb.y = max(bb.y, 0);
-        bb.z = min(bb.z, g.Wt);
-        bb.w = min(bb.w, g.Ht);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = t < n ? (int64_t)(((unsigned long long)t * (unsigned long long)stride) % (unsigned long long)n)
+                            : n;
+    const int lane = threadIdx.x & 31;
+    int i = 0, area = 0;
+    int4 bb = make_int4(0, 0, 0, 0);
+    if (j < n) {
+        i = order ? order[j] : (int)j;
+        if (tcount[i] > 0) {
+            bb = bbox[i];
+            bb.x = max(bb.x, 0);  // never leave the tile grid, whatever the caller's boxes say
+            bb.y = max(bb.y, 0);
+            bb.z = min(bb.z, g.Wt);
+            bb.w = min(bb.w, g.Ht);
+            const int w = bb.z - bb.x, h = bb.w - bb.y;
+            area = (w > 0 && h > 0) ? w * h : 0;
+        }
+    }
+    if (area > 0 && area <= kSmallBox) {
         const CullData d = load_cull(rec, i);
-        uint32_t depth_bits = 0;
-        if (EMIT) depth_bits = __float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]);
-        for (int ty = bb.y; ty < bb.w; ++ty) {
-            const float y0 = (float)(ty * g.th);
-            const float y1 = (float)min(ty * g.th + g.th - 1, g.H - 1);
+        const uint32_t depth_bits = EMIT ? __float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]) : 0u;
+        const int64_t out = EMIT ? (int64_t)counts_or_offsets[j] : 0;
+        int cnt = 0;
+        for (int ty = bb.y; ty < bb.w; ++ty)
             for (int tx = bb.x; tx < bb.z; ++tx) {
-                const float x0 = (float)(tx * g.tw);
-                const float x1 = (float)min(tx * g.tw + g.tw - 1, g.W - 1);
-                if (!tile_keep(d, x0, y0, x1, y1)) continue;
+                if (!keep_tile(d, g, tx, ty)) continue;
                 if (EMIT) {
-                    const uint32_t t = (uint32_t)(ty * g.Wt + tx);
-                    keys[out + cnt] = ((uint64_t)t << 32) | depth_bits;
+                    keys[out + cnt] = ((uint64_t)(uint32_t)(ty * g.Wt + tx) << 32) | depth_bits;
                     vals[out + cnt] = (uint32_t)i;
                 }
                 ++cnt;
             }
-        }
+        if (!EMIT) counts_or_offsets[j] = cnt;
+    } else if (!EMIT && j < n && area == 0) {
+        counts_or_offsets[j] = 0;
     }
-    if (!EMIT) counts_or_offsets[i] = cnt;
+    unsigned big = __ballot_sync(kFullMask, area > kSmallBox);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const long long jb = __shfl_sync(kFullMask, (long long)j, src);
+        const int ib = __shfl_sync(kFullMask, i, src);
+        const int areab = __shfl_sync(kFullMask, area, src);
+        const int bx = __shfl_sync(kFullMask, bb.x, src), by = __shfl_sync(kFullMask, bb.y, src);
+        const int bw = __shfl_sync(kFullMask, bb.z, src) - bx;
+        const CullData d = load_cull(rec, ib);
+        const uint32_t depth_bits = EMIT ? __float_as_uint(rec[(size_t)ib * XPR_REC_FLOATS + 9]) : 0u;
+        const int64_t out = EMIT ? (int64_t)counts_or_offsets[jb] : 0;
+        int cnt = 0;
+        for (int r0 = 0; r0 < areab; r0 += 32) {
+            const int r = r0 + lane;
+            int tx = 0, ty = 0;
+            bool keep = false;
+            if (r < areab) {
+                ty = by + r / bw;
+                tx = bx + r % bw;
+                keep = keep_tile(d, g, tx, ty);
+            }
+            const unsigned m = __ballot_sync(kFullMask, keep);
+            if (EMIT && keep) {
+                const int64_t pos = out + cnt + __popc(m & ((1u << lane) - 1u));
+                keys[pos] = ((uint64_t)(uint32_t)(ty * g.Wt + tx) << 32) | depth_bits;
+                vals[pos] = (uint32_t)ib;
+            }
+            cnt += __popc(m);
+        }
+        if (!EMIT && lane == 0) counts_or_offsets[jb] = cnt;
+    }
+}
+
+// Sort key of the depth order: camera-z bits of primitives that have tiles, all ones otherwise
+// (those go last, in index order).  Depth of a primitive with tiles is > z_near > 0, so its float
+// bits order like the values.
+__global__ void depth_key_kernel(const float *__restrict__ rec, const int *__restrict__ tcount, int64_t n,
+                                 uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = tcount[i] > 0 ? (uint64_t)__float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]) : 0xffffffffull;
+    vals[i] = (uint32_t)i;
 }
 
 // ---- device-wide exclusive scan (three phases: block reduce, scan of block sums, block scan) ----
@@ -237,25 +305,59 @@ static Grid make_grid(const XprCamera &cam, const XprConfig &cfg) {
     return g;
 }
 
-int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, int64_t n, const XprCamera &cam,
-                     const XprConfig &cfg, int32_t *counts, cudaStream_t st) {
+// A stride coprime to n for the thread -> position bijection (a prime that does not divide n).
+static int64_t visit_stride(int64_t n) {
+    static const int64_t primes[] = {7919, 7927, 7933, 7937, 7949, 7951, 7963, 7993};
+    for (int64_t p : primes)
+        if (n % p != 0) return p % n == 0 ? 1 : p;
+    return 1;  // n is a multiple of every listed prime (impossible for n < 2^31): contiguous visiting
+}
+
+int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
+                     const XprCamera &cam, const XprConfig &cfg, int32_t *counts, cudaStream_t st) {
     if (n == 0) return XPR_OK;
     const int tpb = 256;
     bin_kernel<false><<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, n, make_grid(cam, cfg), counts, nullptr, nullptr);
+        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, visit_stride(n), make_grid(cam, cfg), counts,
+        nullptr, nullptr);
     XPR_LAUNCH_CHECK("bin_count_kernel");
     return XPR_OK;
 }
 
-int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, int64_t n, const XprCamera &cam,
-                    const XprConfig &cfg, const int32_t *offsets, uint64_t *keys, uint32_t *vals, cudaStream_t st) {
+int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
+                    const XprCamera &cam, const XprConfig &cfg, const int32_t *offsets, uint64_t *keys,
+                    uint32_t *vals, cudaStream_t st) {
     if (n == 0) return XPR_OK;
     const int tpb = 256;
     bin_kernel<true><<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, n, make_grid(cam, cfg), const_cast<int32_t *>(offsets), keys,
-        vals);
+        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, visit_stride(n), make_grid(cam, cfg),
+        const_cast<int32_t *>(offsets), keys, vals);
     XPR_LAUNCH_CHECK("bin_emit_kernel");
     return XPR_OK;
+}
+
+size_t depth_order_workspace_bytes(int64_t n) {
+    const size_t a = ((size_t)n * 8 + 255) / 256 * 256, b = ((size_t)n * 4 + 255) / 256 * 256;
+    return 2 * a + b + 256 + sort_workspace_bytes(n, 1);
+}
+
+int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
+                       cudaStream_t st) {
+    if (n == 0) return XPR_OK;
+    if (ws_bytes < depth_order_workspace_bytes(n))
+        return fail(XPR_ERR_INVALID, "xpr_depth_order: workspace %zu < %zu bytes", ws_bytes,
+                    depth_order_workspace_bytes(n));
+    const size_t a = ((size_t)n * 8 + 255) / 256 * 256, b = ((size_t)n * 4 + 255) / 256 * 256;
+    char *p = reinterpret_cast<char *>(ws);
+    uint64_t *keys = reinterpret_cast<uint64_t *>(p);
+    uint64_t *keys_sorted = reinterpret_cast<uint64_t *>(p + a);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
+    int32_t *ranges = reinterpret_cast<int32_t *>(p + 2 * a + b);
+    void *sort_ws = p + 2 * a + b + 256;
+    depth_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, tc, n, keys, vals);
+    XPR_LAUNCH_CHECK("depth_key_kernel");
+    return launch_sort(keys, vals, n, 1, 0, keys_sorted, reinterpret_cast<uint32_t *>(order), ranges, sort_ws,
+                       sort_workspace_bytes(n, 1), st);
 }
 
 }  // namespace xpr

@@ -100,6 +100,32 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Sum 8 per-lane values over the warp with 9 shuffles instead of 40: at each of the first three
+// steps a lane keeps the half of its values selected by one bit of its lane index and sends the
+// other half to its partner, so after xor 16, 8, 4 lane l holds value (l >> 2) summed over the 8
+// lanes sharing bits 1..0; two more xor steps finish the sum.  Returns value (lane >> 2).
+__device__ __forceinline__ float reduce_scatter8(const float *v, int lane) {
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    float b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = u16 ? v[k] : v[k + 4];
+        const float keep = u16 ? v[k + 4] : v[k];
+        b[k] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+    float c[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = u8 ? b[k] : b[k + 2];
+        const float keep = u8 ? b[k + 2] : b[k];
+        c[k] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+    float d = (u4 ? c[1] : c[0]) + __shfl_xor_sync(kFull, u4 ? c[0] : c[1], 4);
+    d += __shfl_xor_sync(kFull, d, 2);
+    d += __shfl_xor_sync(kFull, d, 1);
+    return d;
+}
+
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) render_bwd_kernel(const float *__restrict__ rec,
                                                             const uint32_t *__restrict__ vals,
@@ -200,12 +226,12 @@ __global__ void __launch_bounds__(TW *TH) render_bwd_kernel(const float *__restr
                 }
             }
             if (__any_sync(kFull, hit)) {
-#pragma unroll
-                for (int c = 0; c < 9; ++c) v[c] = warp_sum(v[c]);
-                if (lane == 0) {
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) atomicAdd(&s_acc[c][j], v[c]);
-                }
+                // v[0..7]: transposed reduce-scatter (9 shuffles); afterwards lane l with l % 4 == 0
+                // holds the warp total of value l / 4.  v[8]: plain butterfly (5 shuffles).
+                const float s8 = warp_sum(v[8]);
+                const float r7 = reduce_scatter8(v, lane);
+                if ((lane & 3) == 0) atomicAdd(&s_acc[lane >> 2][j], r7);
+                if (lane == 0) atomicAdd(&s_acc[8][j], s8);
             }
         }
         __syncthreads();
@@ -218,16 +244,11 @@ __global__ void __launch_bounds__(TW *TH) render_bwd_kernel(const float *__restr
                 any |= (a[c] != 0.f);
             }
             if (any && s_id[t] < k.n) {
-                float *d = d_rec + (size_t)s_id[t] * XPR_REC_FLOATS;
-                atomicAdd(d + 0, -kLn2 * a[0]);
-                atomicAdd(d + 1, -kLn2 * a[1]);
-                atomicAdd(d + 2, -0.5f * a[2]);
-                atomicAdd(d + 3, -a[3]);
-                atomicAdd(d + 4, -0.5f * a[4]);
-                atomicAdd(d + 5, a[5]);
-                atomicAdd(d + 6, a[6]);
-                atomicAdd(d + 7, a[7]);
-                atomicAdd(d + 8, a[8]);
+                // record layout: [dmx, dmy, dc00, dc01] [dc11, do, dr, dg] [db, 0, 0, 0]; vector atomics
+                float4 *d = reinterpret_cast<float4 *>(d_rec + (size_t)s_id[t] * XPR_REC_FLOATS);
+                atomicAdd(d, make_float4(-kLn2 * a[0], -kLn2 * a[1], -0.5f * a[2], -a[3]));
+                atomicAdd(d + 1, make_float4(-0.5f * a[4], a[5], a[6], a[7]));
+                atomicAdd(reinterpret_cast<float *>(d + 2), a[8]);
             }
         }
     }

@@ -4,19 +4,25 @@
 //
 // Each 8-bit pass is reduce-then-scan: a histogram kernel writes per-block digit counts in
 // digit-major order, the device-wide exclusive scan turns them into global output offsets, and
-// the scatter kernel ranks keys stably inside each warp with __match_any_sync (warp w owns a
-// contiguous run of 512 keys, visited in index order) before writing them to their offsets.
+// the scatter kernel
+//   1. ranks its 4096 keys stably: warp w owns a contiguous run of 512 keys visited in index
+//      order, __match_any_sync groups equal digits within each round of 32;
+//   2. places every key at its rank in a block-local sorted copy in shared memory;
+//   3. writes the local copy out in order, so the threads of a warp write consecutive addresses
+//      of one digit's output run (coalesced) instead of 32 scattered buckets.
 #include "xpr_internal.cuh"
 
 namespace xpr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
+constexpr int kItems = 8;
 constexpr int kWarps = kThreads / 32;
-constexpr int kWarpKeys = 32 * kItems;   // 512
-constexpr int kTile = kThreads * kItems;  // 4096
+constexpr int kWarpKeys = 32 * kItems;   // 256
+constexpr int kTile = kThreads * kItems;  // 2048
 constexpr int kRadix = 256;
+constexpr size_t kScatterSmem = (size_t)kTile * 8 + (size_t)kTile * 4 + (size_t)kWarps * kRadix * 4 +
+                                2 * (size_t)kRadix * 4 + 64;
 
 __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint64_t *__restrict__ kin, int64_t n, int shift,
                                                               uint32_t mask, int32_t *__restrict__ hist,
@@ -41,22 +47,29 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t 
                                                                  uint32_t mask,
                                                                  const int32_t *__restrict__ digit_off,
                                                                  int64_t nb) {
-    __shared__ int s_hist[kWarps][kRadix];
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kTile * 8);
+    int(*s_hist)[kRadix] = reinterpret_cast<int(*)[kRadix]>(smem + (size_t)kTile * 12);
+    int *s_start = reinterpret_cast<int *>(smem + (size_t)kTile * 12 + (size_t)kWarps * kRadix * 4);
+    int *s_gofs = s_start + kRadix;
+    int *s_wsum = s_gofs + kRadix;  // kWarps partial sums for the digit scan
+
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kWarps * kRadix; d += kThreads) (&s_hist[0][0])[d] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * kWarpKeys;
+    const int64_t block_base = (int64_t)blockIdx.x * kTile;
+    const int64_t base = block_base + (int64_t)w * kWarpKeys;
+    const int count = (int)min((int64_t)kTile, n - block_base);
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint64_t key[kItems];
-    uint32_t val[kItems];
-    int rank[kItems];
+    // only (digit << 16 | rank within the warp) is kept in registers; keys and values are re-read
+    // (from L2, just touched) when they are placed
+    int dr[kItems];
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int64_t j = base + r * 32 + lane;
         const bool valid = j < n;
-        key[r] = valid ? kin[j] : 0ull;
-        val[r] = valid ? vin[j] : 0u;
-        const int d = valid ? (int)((uint32_t)(key[r] >> shift) & mask) : kRadix;  // kRadix = padding
+        const int d = valid ? (int)((uint32_t)(kin[j] >> shift) & mask) : kRadix;  // kRadix = padding
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         int cur = 0;
@@ -64,30 +77,52 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t 
         __syncwarp();
         if (valid && lane == leader) s_hist[w][d] = cur + __popc(peers);
         __syncwarp();
-        rank[r] = cur + __popc(peers & lt_mask);
+        dr[r] = (d << 16) | (cur + __popc(peers & lt_mask));
     }
     __syncthreads();
-    {
-        // exclusive prefix over the warps of this block, offset by the block's global digit base
-        const int d = threadIdx.x;
-        int run = digit_off[(int64_t)d * nb + blockIdx.x];
+    // per digit: prefix over warps (in place) and the digit's total in this block
+    const int d0 = threadIdx.x;
+    int tot = 0;
 #pragma unroll
-        for (int ww = 0; ww < kWarps; ++ww) {
-            const int c = s_hist[ww][d];
-            s_hist[ww][d] = run;
-            run += c;
-        }
+    for (int ww = 0; ww < kWarps; ++ww) {
+        const int c = s_hist[ww][d0];
+        s_hist[ww][d0] = tot;
+        tot += c;
     }
+    // exclusive scan of the digit totals over the block -> start of each digit in the local order
+    int x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[w] = x;
     __syncthreads();
+    int wpre = 0;
+    for (int ww = 0; ww < w; ++ww) wpre += s_wsum[ww];
+    const int start = wpre + x - tot;
+    s_start[d0] = start;
+    s_gofs[d0] = digit_off[(int64_t)d0 * nb + blockIdx.x] - start;
+    __syncthreads();
+    // place every key at its local rank
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int64_t j = base + r * 32 + lane;
         if (j < n) {
-            const int d = (int)((uint32_t)(key[r] >> shift) & mask);
-            const int pos = s_hist[w][d] + rank[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            const int d = dr[r] >> 16;
+            const int pos = s_start[d] + s_hist[w][d] + (dr[r] & 0xffff);
+            s_key[pos] = kin[j];
+            s_val[pos] = vin[j];
         }
+    }
+    __syncthreads();
+    // write the block's sorted run: consecutive threads, consecutive output addresses within a digit
+    for (int s = threadIdx.x; s < count; s += kThreads) {
+        const uint64_t k = s_key[s];
+        const int d = (int)((uint32_t)(k >> shift) & mask);
+        const int64_t g = (int64_t)s_gofs[d] + s;
+        kout[g] = k;
+        vout[g] = s_val[s];
     }
 }
 
@@ -122,13 +157,16 @@ size_t sort_workspace_bytes(int64_t n, int32_t n_tiles) {
            scan_partials_bytes(nh);
 }
 
-int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, uint64_t *keys_out,
-                uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {
+int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
+                uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {
     XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(int32_t), st));
     if (n == 0) return XPR_OK;
     if (ws_bytes < sort_workspace_bytes(n, n_tiles))
         return fail(XPR_ERR_INVALID, "xpr_sort: workspace %zu bytes < required %zu", ws_bytes,
                     sort_workspace_bytes(n, n_tiles));
+    // the dynamic shared-memory limit is a per-function attribute of the current device's module
+    XPR_CUDA_TRY(cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kScatterSmem));
     const int64_t nb = (n + kTile - 1) / kTile;
     const int64_t nh = (int64_t)kRadix * nb;
     char *p = reinterpret_cast<char *>(ws);
@@ -141,11 +179,15 @@ int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int
     void *scan_ws = p;
 
     const int end_bit = 32 + bits_for((int64_t)n_tiles - 1);
-    const int passes = (end_bit + 7) / 8;
+    const int passes = begin_bit < end_bit ? (end_bit - begin_bit + 7) / 8 : 0;
+    if (passes == 0) {
+        XPR_CUDA_TRY(cudaMemcpyAsync(keys_out, keys_in, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+        XPR_CUDA_TRY(cudaMemcpyAsync(vals_out, vals_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    }
     const uint64_t *src_k = keys_in;
     const uint32_t *src_v = vals_in;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
+        const int shift = begin_bit + 8 * pass;
         const int nbits = min(8, end_bit - shift);
         const uint32_t mask = (1u << nbits) - 1u;
         const bool to_out = ((passes - 1 - pass) % 2) == 0;
@@ -155,8 +197,8 @@ int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int
         XPR_LAUNCH_CHECK("radix_hist_kernel");
         int s = launch_exclusive_scan(hist, hist, nh, scan_ws, nullptr, st);
         if (s != XPR_OK) return s;
-        radix_scatter_kernel<<<(unsigned)nb, kThreads, 0, st>>>(src_k, src_v, dst_k, dst_v, n, shift, mask, hist,
-                                                               nb);
+        radix_scatter_kernel<<<(unsigned)nb, kThreads, kScatterSmem, st>>>(src_k, src_v, dst_k, dst_v, n, shift,
+                                                                           mask, hist, nb);
         XPR_LAUNCH_CHECK("radix_scatter_kernel");
         src_k = dst_k;
         src_v = dst_v;

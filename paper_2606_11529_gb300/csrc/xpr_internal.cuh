@@ -45,14 +45,18 @@ int64_t *scan_total_ptr(void *partials, int64_t n);  // where the scan leaves th
 int launch_exclusive_scan(const int32_t *in, int32_t *out, int64_t n, void *partials, int64_t *total_out,
                           cudaStream_t st);
 
-int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, int64_t n, const XprCamera &cam,
-                     const XprConfig &cfg, int32_t *counts, cudaStream_t st);
-int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, int64_t n, const XprCamera &cam,
-                    const XprConfig &cfg, const int32_t *offsets, uint64_t *keys, uint32_t *vals, cudaStream_t st);
+int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
+                     const XprCamera &cam, const XprConfig &cfg, int32_t *counts, cudaStream_t st);
+int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
+                    const XprCamera &cam, const XprConfig &cfg, const int32_t *offsets, uint64_t *keys,
+                    uint32_t *vals, cudaStream_t st);
+size_t depth_order_workspace_bytes(int64_t n);
+int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
+                       cudaStream_t st);
 
 size_t sort_workspace_bytes(int64_t n, int32_t n_tiles);
-int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, uint64_t *keys_out,
-                uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st);
+int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
+                uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st);
 
 int launch_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges,
                       const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final, int32_t *n_contrib,

@@ -101,18 +101,23 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     tm.start("project", stream)
     rec, bbox, tc = B.xpr_project(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream)
     tm.stop("project", stream)
+    # emit intersections in (depth, index) order so that the sort only has to order tile bits
+    tm.start("depth_order", stream)
+    order = B.xpr_depth_order(rec, tc, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(n), dev),
+                              stream=stream)
+    tm.stop("depth_order", stream)
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
     bin_ws = ws.scratch("bin", L.xpr_tile_bin_workspace(n), dev)
     tm.start("tile_bin", stream)
     offsets, keys, vals, I = B.xpr_tile_bin(rec, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
-                                            stream=stream)
+                                            stream=stream, order=order)
     tm.stop("tile_bin", stream)
     ws.last_isect = I
     Wt, Ht = B.tiles_of(cam, cfg)
     nt = Wt * Ht
     sort_ws = ws.scratch("sort", L.xpr_sort_workspace(I, nt), dev)
     tm.start("sort", stream)
-    ks, vs, ranges = B.xpr_sort(keys, vals, nt, workspace=sort_ws, stream=stream)
+    ks, vs, ranges = B.xpr_sort(keys, vals, nt, workspace=sort_ws, stream=stream, begin_bit=32)
     tm.stop("sort", stream)
     tm.start("render_fwd", stream)
     image, t_final, n_contrib = B.xpr_render_fwd(rec, vs, ranges, ccam, ccfg, stream=stream)

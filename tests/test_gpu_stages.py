@@ -52,14 +52,18 @@ def test_project_matches_oracle(oracle, deg, tile, view):
     assert np.all(tc[~vis_g] == 0)
 
 
-@pytest.mark.parametrize("tile", [8, 16])
-def test_tile_bin_bit_exact(oracle, tile):
+@pytest.mark.parametrize("tile,ordered", [(8, False), (16, False), (16, True), (8, True)])
+def test_tile_bin_bit_exact(oracle, tile, ordered):
     sc, cam, cfg = _case(0, tile, n=12_345, W=250, H=170)  # ragged image: partial edge tiles
+    sc.scale[::97] *= 12.0  # some large footprints: boxes of many tiles take the warp-cooperative path
     pr = oracle.project_scene(sc, cam, cfg)
     rec32 = pr["rec"].astype(np.float32)
-    counts, keys, vals = oracle.bin_pairs(rec32, pr["bbox"], cam, cfg, exact32=True)
-    off, k, v, I = B.xpr_tile_bin(dev(rec32), dev_i32(pr["bbox"]), dev_i32(pr["tc"]), cam, cfg)
+    order = oracle.depth_order(rec32, pr["tc"]) if ordered else None
+    counts, keys, vals = oracle.bin_pairs(rec32, pr["bbox"], cam, cfg, exact32=True, order=order)
+    off, k, v, I = B.xpr_tile_bin(dev(rec32), dev_i32(pr["bbox"]), dev_i32(pr["tc"]), cam, cfg,
+                                  order=None if order is None else dev_i32(order.astype(np.int32)))
     assert I == keys.size > 10_000
+    assert (pr["tc"] > 16).sum() > 50
     np.testing.assert_array_equal(off.cpu().numpy(), np.concatenate([[0], np.cumsum(counts)]).astype(np.int32))
     np.testing.assert_array_equal(host_u64(k), keys)
     np.testing.assert_array_equal(host_u32(v), vals)
@@ -81,7 +85,7 @@ def test_tile_bin_capacity_protocol(oracle):
     ws = torch.empty(L.xpr_tile_bin_workspace(n), dtype=torch.uint8, device="cuda")
     got = ctypes.c_int64(0)
     c, g = B.make_camera(cam), B.make_config(cfg)
-    s = L.xpr_tile_bin(args[0].data_ptr(), args[1].data_ptr(), args[2].data_ptr(), n, ctypes.byref(c),
+    s = L.xpr_tile_bin(args[0].data_ptr(), args[1].data_ptr(), args[2].data_ptr(), None, n, ctypes.byref(c),
                        ctypes.byref(g), off.data_ptr(), kbuf.data_ptr(), vbuf.data_ptr(), 8, ctypes.byref(got),
                        ws.data_ptr(), ws.numel(), None)
     torch.cuda.synchronize()
@@ -97,6 +101,31 @@ def test_sort_bit_exact_on_binned_pairs(oracle):
     pr = oracle.project_scene(sc, cam, cfg)
     _, keys, vals, sk, sv, ranges = oracle_lists(oracle, pr["rec"].astype(np.float32), pr["bbox"], cam, cfg)
     ks, vs, rg = B.xpr_sort(dev_i64(keys), dev_i32(vals), ranges.shape[0])
+    np.testing.assert_array_equal(host_u64(ks), sk)
+    np.testing.assert_array_equal(host_u32(vs), sv)
+    np.testing.assert_array_equal(rg.cpu().numpy(), ranges)
+
+
+def test_depth_order_matches_lexsort(oracle):
+    sc, cam, cfg = _case(0, 16, n=50_000)
+    sc.mu[::50, 2] = -1.0  # some invisible primitives go last, in index order
+    sc.mu[1::1000, 2] = sc.mu[0::1000, 2][: len(sc.mu[1::1000])]  # exact depth ties keep index order
+    rec, bbox, tc = B.xpr_project(*R.scene_to_device(sc), cam, cfg)
+    order = B.xpr_depth_order(rec, tc).cpu().numpy()
+    ref = oracle.depth_order(rec.cpu().numpy(), tc.cpu().numpy())
+    np.testing.assert_array_equal(order, ref.astype(np.int32))
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_tile_only_sort_of_depth_ordered_pairs_equals_full_sort(oracle, tile):
+    sc, cam, cfg = _case(0, tile, n=20_000)
+    pr = oracle.project_scene(sc, cam, cfg)
+    rec32 = pr["rec"].astype(np.float32)
+    order = oracle.depth_order(rec32, pr["tc"])
+    _, keys, vals = oracle.bin_pairs(rec32, pr["bbox"], cam, cfg, exact32=True, order=order)
+    Wt, Ht = oracle.tiles_of(cam, cfg)
+    sk, sv, ranges = oracle.sort_pairs(keys, vals, Wt * Ht)
+    ks, vs, rg = B.xpr_sort(dev_i64(keys), dev_i32(vals), Wt * Ht, begin_bit=32)
     np.testing.assert_array_equal(host_u64(ks), sk)
     np.testing.assert_array_equal(host_u32(vs), sv)
     np.testing.assert_array_equal(rg.cpu().numpy(), ranges)

@@ -138,6 +138,26 @@ def test_sort_and_ranges_partition(oracle):
     assert counts.sum() == sk.size
 
 
+def test_emission_order_does_not_change_sorted_lists(oracle):
+    # emitting in (depth, index) order and sorting by tile only == emitting in index order and
+    # sorting by the full (tile, depth) key with index tie-break
+    cam = scenes.pinhole(128, 96, 128.0)
+    cfg = scenes.RenderConfig(tile_w=8, tile_h=8)
+    sc = scenes.uniform_scene(1500, seed=9)
+    pr = oracle.project_scene(sc, cam, cfg)
+    rec32 = pr["rec"].astype(np.float32)
+    Wt, Ht = oracle.tiles_of(cam, cfg)
+    _, k0, v0 = oracle.bin_pairs(rec32, pr["bbox"], cam, cfg, exact32=True)
+    sk0, sv0, r0 = oracle.sort_pairs(k0, v0, Wt * Ht)
+    order = oracle.depth_order(rec32, pr["tc"])
+    c1, k1, v1 = oracle.bin_pairs(rec32, pr["bbox"], cam, cfg, exact32=True, order=order)
+    tiles = (k1 >> np.uint64(32)).astype(np.int64)
+    st = np.argsort(tiles, kind="stable")  # tile-only stable sort
+    np.testing.assert_array_equal(k1[st], sk0)
+    np.testing.assert_array_equal(v1[st], sv0)
+    assert c1.sum() == k0.size
+
+
 def test_empty_input(oracle):
     cam = scenes.pinhole(64, 64, 64.0)
     cfg = scenes.RenderConfig()

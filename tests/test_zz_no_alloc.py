@@ -18,7 +18,7 @@ from paper_2606_11529_gb300 import scenes
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(rec, bbox, tc, cam, cfg, capacity):
+def _noalloc(rec, bbox, tc, cam, cfg, capacity, order=None):
     L = B.load()
     n = rec.shape[0]
     off = torch.empty(n + 1, dtype=torch.int32, device="cuda")
@@ -26,7 +26,8 @@ def _noalloc(rec, bbox, tc, cam, cfg, capacity):
     vals = torch.full((max(capacity, 1),), -1, dtype=torch.int32, device="cuda")
     got = ctypes.c_int64(0)
     c, g = B.make_camera(cam), B.make_config(cfg)
-    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(), n, ctypes.byref(c), ctypes.byref(g),
+    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(),
+                               None if order is None else order.data_ptr(), n, ctypes.byref(c), ctypes.byref(g),
                                off.data_ptr(), keys.data_ptr(), vals.data_ptr(), capacity, ctypes.byref(got),
                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()
@@ -39,8 +40,9 @@ def test_noalloc_matches_tile_bin_on_consecutive_calls():
               scenes.RenderConfig(tile_w=8, tile_h=8, sh_degree=1))]
     for sc, cam, cfg in cases:  # two calls in a row share (and overwrite) the static scratch
         rec, bbox, tc = B.xpr_project(*R.scene_to_device(sc), cam, cfg)
-        off_ref, k_ref, v_ref, I = B.xpr_tile_bin(rec, bbox, tc, cam, cfg)
-        s, off, k, v, got = _noalloc(rec, bbox, tc, cam, cfg, I + 100)
+        order = B.xpr_depth_order(rec, tc)
+        off_ref, k_ref, v_ref, I = B.xpr_tile_bin(rec, bbox, tc, cam, cfg, order=order)
+        s, off, k, v, got = _noalloc(rec, bbox, tc, cam, cfg, I + 100, order)
         assert s == B.XPR_OK, B.load().xpr_last_error()
         assert got == I > 1000
         assert torch.equal(off, off_ref)
@@ -57,6 +59,6 @@ def test_noalloc_capacity_and_size_limit():
     L = B.load()
     c, g = B.make_camera(cam), B.make_config(cfg)
     n_out = ctypes.c_int64(0)
-    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(), (1 << 26) + 1, ctypes.byref(c),
+    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(), None, (1 << 26) + 1, ctypes.byref(c),
                                ctypes.byref(g), 256, 256, 256, 0, ctypes.byref(n_out), None)
     assert s == B.XPR_ERR_INVALID and b"limit" in L.xpr_last_error()
