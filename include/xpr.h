@@ -113,9 +113,13 @@ typedef struct XprPrimsGrad {
  * Sigma_2D,xx) (and yy), half-open tile bounding box, tile count, visibility
  * flag (det > 0, o >= a_t, r > 0, tc > 0, z > z_near) and SH colour.
  * Outputs: rec[n,12], bbox[n,4] int32 (xmin, ymin, xmax, ymax in tiles,
- * half-open; zero when invisible), tile_count[n] int32 (0 when invisible). */
+ * half-open; zero when invisible), tile_count[n] int32 (bounding-box tile
+ * count tc of Sec. 4.2; 0 when invisible).  isect_count[n] int32 (may be
+ * NULL): number of tiles of the box that pass the tile cull of xpr_tile_bin,
+ * i.e. the exact number of pairs the primitive will emit (the binning then
+ * needs no counting pass of its own). */
 int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
-                int32_t *bbox, int32_t *tile_count, void *stream);
+                int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream);
 
 /* ---- Rasterizer: replicate, assign tile ID, cull --------------------------
  * xpr_depth_order: order[n] = the primitives with tile_count > 0 sorted by
@@ -135,17 +139,22 @@ int xpr_depth_order(const float *rec, const int32_t *tile_count, int64_t n, int3
  * of Listing 1 tile_cull passes (decision taken in FP32 with a fixed sequence
  * of correctly rounded operations).  Culled pairs are not emitted (the
  * paper's "tile ID T" slots are dropped instead of being sorted to the end).
+ * isect_count (may be NULL) is xpr_project's per-primitive count of kept
+ * tiles; when NULL the counts are computed here in a separate pass.
  * Outputs: offsets[n+1] int32 (exclusive prefix sum over positions j of the
- * surviving counts; offsets[n] = total), keys[total] = (t << 32) |
- * float_bits(depth), vals[total] = primitive index, in (position, r) order;
- * *n_isect (HOST) = total.  If total > capacity, returns XPR_ERR_CAPACITY
- * with *n_isect set and keys / vals untouched (the caller re-sizes and calls
- * again).  Synchronises `stream` to read the total.  workspace:
+ * surviving counts; offsets[n] = total); per pair, in (position, r) order:
+ * keys[total] = (t << 32) | float_bits(depth) (u64, may be NULL),
+ * tiles[total] = t (u32, may be NULL; at least one of keys / tiles is
+ * required) and vals[total] = primitive index; *n_isect (HOST) = total.
+ * If total > capacity, returns XPR_ERR_CAPACITY with *n_isect set and the
+ * pair arrays untouched (the caller re-sizes and calls again).
+ * Synchronises `stream` to read the total.  workspace:
  * >= xpr_tile_bin_workspace(n) bytes, 256-byte aligned. */
 size_t xpr_tile_bin_workspace(int64_t n);
-int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
-                 const XprCamera *cam, const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *vals,
-                 int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
+int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                 const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *offsets,
+                 uint64_t *keys, uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                 void *workspace, size_t ws_bytes, void *stream);
 
 /* xpr_tile_bin_noalloc: xpr_tile_bin without a workspace argument, for callers
  * that cannot allocate device memory (for example a process whose device
@@ -162,9 +171,10 @@ int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_coun
  * overlap on the GPU (different streams, or different host threads on one
  * device) race on it and must be serialised by the caller.  Allocates nothing;
  * arguments, outputs and errors are those of xpr_tile_bin. */
-int xpr_tile_bin_noalloc(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order,
-                         int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *offsets, uint64_t *keys,
-                         uint32_t *vals, int64_t capacity, int64_t *n_isect, void *stream);
+int xpr_tile_bin_noalloc(const float *rec, const int32_t *bbox, const int32_t *tile_count,
+                         const int32_t *isect_count, const int32_t *order, int64_t n, const XprCamera *cam,
+                         const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *tiles, uint32_t *vals,
+                         int64_t capacity, int64_t *n_isect, void *stream);
 
 /* ---- Rasterizer: sort and identify bounds ---------------------------------
  * xpr_sort (Sec. 4.2 "Sort and identify bounds"): stable LSD radix sort of
@@ -180,6 +190,17 @@ size_t xpr_sort_workspace(int64_t n_isect, int32_t n_tiles);
 int xpr_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n_isect, int32_t n_tiles, int32_t begin_bit,
              uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *workspace, size_t ws_bytes,
              void *stream);
+
+/* xpr_sort_tiles: the same stable sort and segment bounds for pairs given as
+ * u32 tile ids (xpr_tile_bin's `tiles` output) instead of u64 keys; with pairs
+ * emitted in xpr_depth_order order the result is the (tile, depth) order of
+ * Sec. 4.2 while moving 8 instead of 12 bytes per pair and pass.
+ * tiles_in/vals_in must not alias tiles_out/vals_out.  workspace:
+ * >= xpr_sort_tiles_workspace(n_isect, n_tiles) bytes, 256-byte aligned. */
+size_t xpr_sort_tiles_workspace(int64_t n_isect, int32_t n_tiles);
+int xpr_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t n_isect, int32_t n_tiles,
+                   uint32_t *tiles_out, uint32_t *vals_out, int32_t *ranges, void *workspace, size_t ws_bytes,
+                   void *stream);
 
 /* ---- Shader ----------------------------------------------------------------
  * xpr_render_fwd (Sec. 2 Shader, Algorithm 1, Listing 1 evaluate): one thread

@@ -391,7 +391,9 @@ static int cull_f64(double mx, double my, double c0, double c1, double c2, doubl
 
 /* Same decision in IEEE single precision, one rounding per operation, in
  * this exact order (the CUDA kernel takes the decision in FP32 with the same
- * sequence of correctly rounded operations). */
+ * sequence of correctly rounded operations).  The edge minimiser divides by
+ * c2 (or c0) as a multiplication by the correctly rounded reciprocal 1/c2
+ * (1/c0), computed once per primitive. */
 static float f32_q(float c0, float c1, float c2, float dx, float dy) {
     float a = dx * dx;
     a = a * c0;
@@ -411,11 +413,12 @@ static int cull_f32(float mx, float my, float c0, float c1, float c2, float lt, 
     int outy = (my < y0) || (my > y1);
     if (!outx && !outy) return 0.0f <= lt;
     float best = INFINITY;
+    float ic2 = 1.0f / c2, ic0 = 1.0f / c0;
     if (outx) {
         float ex = mx < x0 ? x0 : x1;
         float dx = mx - ex;
         float t = c1 * dx;
-        t = t / c2;
+        t = t * ic2;
         float ys = my + t;
         ys = fminf(fmaxf(ys, y0), y1);
         float dy = my - ys;
@@ -426,7 +429,7 @@ static int cull_f32(float mx, float my, float c0, float c1, float c2, float lt, 
         float ey = my < y0 ? y0 : y1;
         float dy = my - ey;
         float t = c1 * dy;
-        t = t / c0;
+        t = t * ic0;
         float xs = mx + t;
         xs = fminf(fmaxf(xs, x0), x1);
         float dx = mx - xs;

@@ -44,16 +44,20 @@ REC = 12
 # (name, restype, argtypes) of every exported entry point
 SIGNATURES = {
     "xpr_project": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
-                            c_vp, c_vp, c_vp, c_vp]),
+                            c_vp, c_vp, c_vp, c_vp, c_vp]),
     "xpr_tile_bin_workspace": (c_sz, [c_i64]),
     "xpr_depth_order_workspace": (c_sz, [c_i64]),
     "xpr_depth_order": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_vp, c_sz, c_vp]),
-    "xpr_tile_bin": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
-                             c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
-    "xpr_tile_bin_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera),
-                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp]),
+    "xpr_tile_bin": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera),
+                             ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp,
+                             c_sz, c_vp]),
+    "xpr_tile_bin_noalloc": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera),
+                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64),
+                                     c_vp]),
     "xpr_sort_workspace": (c_sz, [c_i64, c_i32]),
     "xpr_sort": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "xpr_sort_tiles_workspace": (c_sz, [c_i64, c_i32]),
+    "xpr_sort_tiles": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "xpr_render_fwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
                                c_vp, c_vp, c_vp]),
     "xpr_render_bwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig), c_vp,
@@ -157,18 +161,22 @@ def tiles_of(cam, cfg):
 
 # ---------------------------------------------------------------------------------------- entry points
 
-def xpr_project(mu, scale, quat, opacity, sh, cam, cfg, rec=None, bbox=None, tile_count=None, stream=None):
+def xpr_project(mu, scale, quat, opacity, sh, cam, cfg, rec=None, bbox=None, tile_count=None, stream=None,
+                isect_count=None, with_isect_count=False):
+    """Returns (rec, bbox, tile_count), plus isect_count when ``with_isect_count`` (or a buffer) is given."""
     L = load()
     n = mu.shape[0]
     dev = _dev(mu)
     rec = torch.empty((n, REC), dtype=torch.float32, device=dev) if rec is None else rec
     bbox = torch.empty((n, 4), dtype=torch.int32, device=dev) if bbox is None else bbox
     tile_count = torch.empty(n, dtype=torch.int32, device=dev) if tile_count is None else tile_count
+    if isect_count is None and with_isect_count:
+        isect_count = torch.empty(n, dtype=torch.int32, device=dev)
     p = _prims(mu, scale, quat, opacity, sh)
     c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
     _check(L.xpr_project(ctypes.byref(p), n, ctypes.byref(c), ctypes.byref(g), _ptr(rec), _ptr(bbox),
-                         _ptr(tile_count), _stream(stream)), "xpr_project")
-    return rec, bbox, tile_count
+                         _ptr(tile_count), _ptr(isect_count), _stream(stream)), "xpr_project")
+    return (rec, bbox, tile_count) if isect_count is None else (rec, bbox, tile_count, isect_count)
 
 
 def xpr_depth_order(rec, tile_count, order=None, workspace=None, stream=None):
@@ -184,35 +192,54 @@ def xpr_depth_order(rec, tile_count, order=None, workspace=None, stream=None):
 
 
 def xpr_tile_bin(rec, bbox, tile_count, cam, cfg, capacity=None, offsets=None, keys=None, vals=None,
-                 workspace=None, stream=None, order=None):
-    """Returns (offsets[n+1], keys[I], vals[I], I).  ``order``: optional emission order (int32
-    permutation).  ``capacity``: initial guess for the intersection buffers; on XPR_ERR_CAPACITY
-    they are re-allocated to the reported size and the call is repeated."""
+                 workspace=None, stream=None, order=None, isect_count=None, tile_ids=False):
+    """Returns (offsets[n+1], pairs[I], vals[I], I) where pairs are u64 keys (int64 storage) or, with
+    ``tile_ids``, u32 tile ids (int32 storage).  ``order``: optional emission order (int32
+    permutation); ``isect_count``: per-primitive kept-tile counts from xpr_project.  ``capacity``:
+    initial guess for the pair buffers; on XPR_ERR_CAPACITY they are re-allocated to the reported
+    size and the call is repeated."""
     L = load()
     n = rec.shape[0]
     dev = rec.device
+    kdt = torch.int32 if tile_ids else torch.int64
     offsets = torch.empty(n + 1, dtype=torch.int32, device=dev) if offsets is None else offsets
     ws_need = int(L.xpr_tile_bin_workspace(n))
     if workspace is None or workspace.numel() < ws_need:
         workspace = torch.empty(max(ws_need, 256), dtype=torch.uint8, device=dev)
     if keys is None or capacity is None:
         cap = int(capacity) if capacity is not None else max(4 * n, 1024)
-        keys = torch.empty(cap, dtype=torch.int64, device=dev)
+        keys = torch.empty(cap, dtype=kdt, device=dev)
         vals = torch.empty(cap, dtype=torch.int32, device=dev)
     c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
     for _ in range(2):
         n_isect = c_i64(0)
-        s = L.xpr_tile_bin(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(order), n, ctypes.byref(c), ctypes.byref(g),
-                           _ptr(offsets), _ptr(keys), _ptr(vals), keys.numel(), ctypes.byref(n_isect),
+        s = L.xpr_tile_bin(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _ptr(order), n,
+                           ctypes.byref(c), ctypes.byref(g), _ptr(offsets), None if tile_ids else _ptr(keys),
+                           _ptr(keys) if tile_ids else None, _ptr(vals), keys.numel(), ctypes.byref(n_isect),
                            _ptr(workspace), workspace.numel(), _stream(stream))
         if s == XPR_ERR_CAPACITY and n_isect.value <= 0x7FFFFFFF:
-            keys = torch.empty(n_isect.value, dtype=torch.int64, device=dev)
+            keys = torch.empty(n_isect.value, dtype=kdt, device=dev)
             vals = torch.empty(n_isect.value, dtype=torch.int32, device=dev)
             continue
         _check(s, "xpr_tile_bin")
         I = int(n_isect.value)
         return offsets, keys[:I], vals[:I], I
     raise XprError(XPR_ERR_CAPACITY, "xpr_tile_bin", "capacity retry failed")
+
+
+def xpr_sort_tiles(tiles, vals, n_tiles, tiles_out=None, vals_out=None, ranges=None, workspace=None, stream=None):
+    L = load()
+    n = tiles.numel()
+    dev = tiles.device
+    tiles_out = torch.empty_like(tiles) if tiles_out is None else tiles_out
+    vals_out = torch.empty_like(vals) if vals_out is None else vals_out
+    ranges = torch.empty((n_tiles, 2), dtype=torch.int32, device=dev) if ranges is None else ranges
+    need = int(L.xpr_sort_tiles_workspace(n, n_tiles))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    _check(L.xpr_sort_tiles(_ptr(tiles), _ptr(vals), n, n_tiles, _ptr(tiles_out), _ptr(vals_out), _ptr(ranges),
+                            _ptr(workspace), workspace.numel(), _stream(stream)), "xpr_sort_tiles")
+    return tiles_out, vals_out, ranges
 
 
 def xpr_sort(keys, vals, n_tiles, keys_out=None, vals_out=None, ranges=None, workspace=None, stream=None,

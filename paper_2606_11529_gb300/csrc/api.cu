@@ -83,7 +83,7 @@ const char *xpr_status_string(int s) {
 }
 
 int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
-                int32_t *bbox, int32_t *tile_count, void *stream) {
+                int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
     if ((s = check_n(n))) return s;
@@ -93,14 +93,15 @@ int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const Xp
         return fail(XPR_ERR_INVALID, "xpr_project: NULL pointer");
     if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(bbox, 16))
         return fail(XPR_ERR_INVALID, "xpr_project: quat, rec and bbox must be 16-byte aligned");
-    return launch_project_fwd(*prims, n, *cam, *cfg, rec, bbox, tile_count, as_stream(stream));
+    return launch_project_fwd(*prims, n, *cam, *cfg, rec, bbox, tile_count, isect_count, as_stream(stream));
 }
 
 size_t xpr_tile_bin_workspace(int64_t n) { return scan_partials_bytes(n < 0 ? 0 : n); }
 
-int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
-                 const XprCamera *cam, const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *vals,
-                 int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream) {
+int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                 const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *offsets,
+                 uint64_t *keys, uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                 void *workspace, size_t ws_bytes, void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
     if ((s = check_n(n))) return s;
@@ -117,8 +118,13 @@ int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_coun
         *n_isect = 0;
         return XPR_OK;
     }
-    if ((s = launch_bin_count(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, st))) return s;
-    if ((s = launch_exclusive_scan(offsets, offsets, n, workspace, nullptr, st))) return s;
+    if (isect_count) {
+        // per-primitive counts from xpr_project, taken in emission order
+        if ((s = launch_exclusive_scan(isect_count, offsets, n, workspace, nullptr, st, order))) return s;
+    } else {
+        if ((s = launch_bin_count(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, st))) return s;
+        if ((s = launch_exclusive_scan(offsets, offsets, n, workspace, nullptr, st))) return s;
+    }
     const int64_t *tot_dev = scan_total_ptr(workspace, n);
     int64_t total = 0;
     XPR_CUDA_TRY(cudaMemcpyAsync(&total, tot_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -129,8 +135,27 @@ int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_coun
     if (total > capacity)
         return fail(XPR_ERR_CAPACITY, "xpr_tile_bin: %lld intersections > capacity %lld", (long long)total,
                     (long long)capacity);
-    if (total > 0 && (!keys || !vals)) return fail(XPR_ERR_INVALID, "xpr_tile_bin: NULL keys/vals");
-    return launch_bin_emit(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, keys, vals, st);
+    if (total > 0 && ((!keys && !tiles) || !vals)) return fail(XPR_ERR_INVALID, "xpr_tile_bin: NULL keys/tiles/vals");
+    return launch_bin_emit(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, keys, tiles, vals, st);
+}
+
+size_t xpr_sort_tiles_workspace(int64_t n_isect, int32_t n_tiles) {
+    return sort_tiles_workspace_bytes(n_isect < 0 ? 0 : n_isect, n_tiles);
+}
+
+int xpr_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t n_isect, int32_t n_tiles,
+                   uint32_t *tiles_out, uint32_t *vals_out, int32_t *ranges, void *workspace, size_t ws_bytes,
+                   void *stream) {
+    if (n_isect < 0 || n_isect > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "xpr_sort_tiles: bad count");
+    if (n_tiles < 1) return fail(XPR_ERR_INVALID, "xpr_sort_tiles: n_tiles must be >= 1");
+    if (!ranges) return fail(XPR_ERR_INVALID, "xpr_sort_tiles: NULL ranges");
+    if (n_isect > 0 && (!tiles_in || !vals_in || !tiles_out || !vals_out || !workspace))
+        return fail(XPR_ERR_INVALID, "xpr_sort_tiles: NULL pointer");
+    if (n_isect > 0 && (tiles_in == tiles_out || vals_in == vals_out))
+        return fail(XPR_ERR_INVALID, "xpr_sort_tiles: input and output buffers must not alias");
+    if (n_isect > 0 && !aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_sort_tiles: workspace alignment");
+    return launch_sort_tiles(tiles_in, vals_in, n_isect, n_tiles, tiles_out, vals_out, ranges, workspace, ws_bytes,
+                             as_stream(stream));
 }
 
 size_t xpr_depth_order_workspace(int64_t n) { return depth_order_workspace_bytes(n < 0 ? 0 : n); }

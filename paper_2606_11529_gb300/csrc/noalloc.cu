@@ -52,9 +52,10 @@ int scratch_for_current_device(void **out) {
 using namespace xpr;
 
 extern "C" int xpr_tile_bin_noalloc(const float *rec, const int32_t *bbox, const int32_t *tile_count,
-                                    const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg,
-                                    int32_t *offsets, uint64_t *keys, uint32_t *vals, int64_t capacity,
-                                    int64_t *n_isect, void *stream) {
+                                    const int32_t *isect_count, const int32_t *order, int64_t n,
+                                    const XprCamera *cam, const XprConfig *cfg, int32_t *offsets, uint64_t *keys,
+                                    uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                                    void *stream) {
     if (n > kNoAllocMaxN)
         return fail(XPR_ERR_INVALID, "xpr_tile_bin_noalloc: n = %lld exceeds the static-scratch limit of %lld "
                     "primitives; use xpr_tile_bin with a caller-provided workspace", (long long)n,
@@ -64,6 +65,6 @@ extern "C" int xpr_tile_bin_noalloc(const float *rec, const int32_t *bbox, const
     void *ws = nullptr;
     int s = scratch_for_current_device(&ws);
     if (s != XPR_OK) return s;
-    return xpr_tile_bin(rec, bbox, tile_count, order, n, cam, cfg, offsets, keys, vals, capacity, n_isect, ws,
-                        kNoAllocScratchBytes, stream);
+    return xpr_tile_bin(rec, bbox, tile_count, isect_count, order, n, cam, cfg, offsets, keys, tiles, vals, capacity,
+                        n_isect, ws, kNoAllocScratchBytes, stream);
 }

@@ -12,7 +12,7 @@
 //   colour        max(0, sum_k sh_k Y_k(d) + 0.5),  d = (mu - camera centre) / |.|
 // One thread per primitive; the primitive SoA is read once and the 48-byte record is
 // written with three float4 stores.
-#include "xpr_internal.cuh"
+#include "cull.cuh"
 
 namespace xpr {
 namespace {
@@ -175,14 +175,35 @@ __device__ __forceinline__ void geometry(const float *mu, const float *s, const 
     G.my = k.fy * ry + k.cy;
 }
 
+__device__ __forceinline__ void project_one(const float *__restrict__ mu, const float *__restrict__ scale,
+                                            const float *__restrict__ quat, const float *__restrict__ opac,
+                                            const float *__restrict__ sh, int64_t i, const XprCamera &cam,
+                                            const XprConfig &cfg, float *__restrict__ rec, int4 *__restrict__ bbox,
+                                            int *__restrict__ tcount, CullData &cd, int4 &bb, int &area);
+
 __global__ void __launch_bounds__(256) project_fwd_kernel(const float *__restrict__ mu, const float *__restrict__ scale,
                                                           const float *__restrict__ quat,
                                                           const float *__restrict__ opac,
                                                           const float *__restrict__ sh, int64_t n, XprCamera cam,
                                                           XprConfig cfg, float *__restrict__ rec,
-                                                          int4 *__restrict__ bbox, int *__restrict__ tcount) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+                                                          int4 *__restrict__ bbox, int *__restrict__ tcount,
+                                                          int *__restrict__ isect_count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    CullData cd = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int4 bb = make_int4(0, 0, 0, 0);
+    int area = 0;
+    if (i < n) project_one(mu, scale, quat, opac, sh, i, cam, cfg, rec, bbox, tcount, cd, bb, area);
+    if (isect_count) {  // exact number of kept (primitive, tile) pairs, counted with the binning's cull
+        const int cnt = count_kept_tiles(cd, bb, area, make_grid(cam, cfg));
+        if (i < n) isect_count[i] = cnt;
+    }
+}
+
+__device__ __forceinline__ void project_one(const float *__restrict__ mu, const float *__restrict__ scale,
+                                            const float *__restrict__ quat, const float *__restrict__ opac,
+                                            const float *__restrict__ sh, int64_t i, const XprCamera &cam,
+                                            const XprConfig &cfg, float *__restrict__ rec, int4 *__restrict__ bbox,
+                                            int *__restrict__ tcount, CullData &cd, int4 &bb, int &area) {
     const Cam k = make_cam(cam, cfg);
     const int deg = cfg.sh_degree;
     const int K = (deg + 1) * (deg + 1);
@@ -211,7 +232,6 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(const float *__restric
     float4 *out = reinterpret_cast<float4 *>(rec + (size_t)i * XPR_REC_FLOATS);
     bool vis = (z > k.z_near) && (G.det > 0.f) && (o >= cfg.alpha_thresh);
     float lt = 0.f, ex = 0.f, ey = 0.f;
-    int4 bb = make_int4(0, 0, 0, 0);
     int tc = 0;
     if (vis) {
         lt = logf(o / cfg.alpha_thresh);
@@ -228,18 +248,30 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(const float *__restric
         vis = (fmaxf(ex, ey) > 0.f) && (tc > 0);
     }
     if (vis) {
-        float idet = 1.f / G.det;
-        out[0] = make_float4(G.mx, G.my, G.c * idet, -G.b * idet);
-        out[1] = make_float4(G.a * idet, o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
+        const float idet = 1.f / G.det;
+        // the stored record values are the ones the cull reads back, so the count taken here from
+        // registers and the emit kernel's decisions from memory are bit-identical
+        cd.mx = G.mx;
+        cd.my = G.my;
+        cd.c0 = G.c * idet;
+        cd.c1 = -G.b * idet;
+        cd.c2 = G.a * idet;
+        cd.lt = lt;
+        cull_reciprocals(cd);
+        out[0] = make_float4(cd.mx, cd.my, cd.c0, cd.c1);
+        out[1] = make_float4(cd.c2, o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
         out[2] = make_float4(fmaxf(col[2], 0.f), z, lt, 1.f);
         bbox[i] = bb;
         tcount[i] = tc;
+        area = tc;
     } else {
         out[0] = make_float4(0.f, 0.f, 0.f, 0.f);
         out[1] = make_float4(0.f, 0.f, 0.f, 0.f);
         out[2] = make_float4(0.f, z, 0.f, 0.f);
         bbox[i] = make_int4(0, 0, 0, 0);
         tcount[i] = 0;
+        bb = make_int4(0, 0, 0, 0);
+        area = 0;
     }
 }
 
@@ -431,12 +463,12 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(const float *__restric
 }  // namespace
 
 int launch_project_fwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg, float *rec,
-                       int32_t *bbox, int32_t *tc, cudaStream_t st) {
+                       int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st) {
     if (n == 0) return XPR_OK;
     const int tpb = 256;
     const int64_t blocks = (n + tpb - 1) / tpb;
     project_fwd_kernel<<<(unsigned)blocks, tpb, 0, st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, n, cam, cfg, rec,
-                                                         reinterpret_cast<int4 *>(bbox), tc);
+                                                         reinterpret_cast<int4 *>(bbox), tc, isect_count);
     XPR_LAUNCH_CHECK("project_fwd_kernel");
     return XPR_OK;
 }

@@ -1,12 +1,13 @@
 // Rasterizer, second half (Sec. 4.2 "Sort and identify bounds"): stable LSD radix sort of the
-// (tile << 32 | depth bits, primitive) pairs over the bits that can be non-zero, then the per-tile
-// segment bounds [start, end).
+// intersection pairs by tile (and depth), then the per-tile segment bounds [start, end).
 //
+// Keys are either u64 (tile << 32 | depth bits; xpr_sort) or u32 tile ids (xpr_sort_tiles, for
+// pairs emitted in depth order, where a stable sort by tile alone gives the (tile, depth) order).
 // Each 8-bit pass is reduce-then-scan: a histogram kernel writes per-block digit counts in
 // digit-major order, the device-wide exclusive scan turns them into global output offsets, and
 // the scatter kernel
-//   1. ranks its 4096 keys stably: warp w owns a contiguous run of 512 keys visited in index
-//      order, __match_any_sync groups equal digits within each round of 32;
+//   1. ranks its keys stably: warp w owns a contiguous run of 256 keys visited in index order,
+//      __match_any_sync groups equal digits within each round of 32;
 //   2. places every key at its rank in a block-local sorted copy in shared memory;
 //   3. writes the local copy out in order, so the threads of a warp write consecutive addresses
 //      of one digit's output run (coalesced) instead of 32 scattered buckets.
@@ -21,10 +22,25 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kWarpKeys = 32 * kItems;   // 256
 constexpr int kTile = kThreads * kItems;  // 2048
 constexpr int kRadix = 256;
-constexpr size_t kScatterSmem = (size_t)kTile * 8 + (size_t)kTile * 4 + (size_t)kWarps * kRadix * 4 +
-                                2 * (size_t)kRadix * 4 + 64;
 
-__global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint64_t *__restrict__ kin, int64_t n, int shift,
+template <typename K>
+constexpr size_t scatter_smem() {
+    return (size_t)kTile * sizeof(K) + (size_t)kTile * 4 + (size_t)kWarps * kRadix * 4 + 2 * (size_t)kRadix * 4 + 64;
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t tile_of(K key);
+template <>
+__device__ __forceinline__ uint32_t tile_of<uint64_t>(uint64_t key) {
+    return (uint32_t)(key >> 32);
+}
+template <>
+__device__ __forceinline__ uint32_t tile_of<uint32_t>(uint32_t key) {
+    return key;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) radix_hist_kernel(const K *__restrict__ kin, int64_t n, int shift,
                                                               uint32_t mask, int32_t *__restrict__ hist,
                                                               int64_t nb) {
     __shared__ int s[kRadix];
@@ -40,18 +56,18 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint64_t *__
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = s[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t *__restrict__ kin,
+template <typename K>
+__global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const K *__restrict__ kin,
                                                                  const uint32_t *__restrict__ vin,
-                                                                 uint64_t *__restrict__ kout,
-                                                                 uint32_t *__restrict__ vout, int64_t n, int shift,
-                                                                 uint32_t mask,
+                                                                 K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                                 int64_t n, int shift, uint32_t mask,
                                                                  const int32_t *__restrict__ digit_off,
                                                                  int64_t nb) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *s_key = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kTile * 8);
-    int(*s_hist)[kRadix] = reinterpret_cast<int(*)[kRadix]>(smem + (size_t)kTile * 12);
-    int *s_start = reinterpret_cast<int *>(smem + (size_t)kTile * 12 + (size_t)kWarps * kRadix * 4);
+    K *s_key = reinterpret_cast<K *>(smem);
+    uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kTile * sizeof(K));
+    int(*s_hist)[kRadix] = reinterpret_cast<int(*)[kRadix]>(smem + (size_t)kTile * (sizeof(K) + 4));
+    int *s_start = reinterpret_cast<int *>(smem + (size_t)kTile * (sizeof(K) + 4) + (size_t)kWarps * kRadix * 4);
     int *s_gofs = s_start + kRadix;
     int *s_wsum = s_gofs + kRadix;  // kWarps partial sums for the digit scan
 
@@ -118,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t 
     __syncthreads();
     // write the block's sorted run: consecutive threads, consecutive output addresses within a digit
     for (int s = threadIdx.x; s < count; s += kThreads) {
-        const uint64_t k = s_key[s];
+        const K k = s_key[s];
         const int d = (int)((uint32_t)(k >> shift) & mask);
         const int64_t g = (int64_t)s_gofs[d] + s;
         kout[g] = k;
@@ -126,14 +142,15 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(const uint64_t 
     }
 }
 
-__global__ void tile_ranges_kernel(const uint64_t *__restrict__ keys, int64_t n, uint32_t n_tiles,
+template <typename K>
+__global__ void tile_ranges_kernel(const K *__restrict__ keys, int64_t n, uint32_t n_tiles,
                                    int2 *__restrict__ ranges) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
+    const uint32_t t = tile_of<K>(keys[i]);
     if (t >= n_tiles) return;  // keys outside the tile grid have no segment
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (int)i;
-    if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (int)(i + 1);
+    if (i == 0 || tile_of<K>(keys[i - 1]) != t) ranges[t].x = (int)i;
+    if (i == n - 1 || tile_of<K>(keys[i + 1]) != t) ranges[t].y = (int)(i + 1);
 }
 
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -147,66 +164,90 @@ int bits_for(int64_t x) {
     return b;
 }
 
-}  // namespace
-
-size_t sort_workspace_bytes(int64_t n, int32_t n_tiles) {
-    (void)n_tiles;
+template <typename K>
+size_t workspace_bytes(int64_t n) {
     const int64_t nb = (n + kTile - 1) / kTile;
     const int64_t nh = (int64_t)kRadix * (nb > 0 ? nb : 1);
-    return align256((size_t)n * 8) + align256((size_t)n * 4) + align256((size_t)(nh + 1) * 4) +
+    return align256((size_t)n * sizeof(K)) + align256((size_t)n * 4) + align256((size_t)(nh + 1) * 4) +
            scan_partials_bytes(nh);
 }
 
-int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
-                uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {
+// Sorts (kin, vin) by key bits [begin_bit, end_bit) into (kout, vout), then finds tile ranges.
+template <typename K>
+int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit, int end_bit,
+               K *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {
     XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(int32_t), st));
     if (n == 0) return XPR_OK;
-    if (ws_bytes < sort_workspace_bytes(n, n_tiles))
-        return fail(XPR_ERR_INVALID, "xpr_sort: workspace %zu bytes < required %zu", ws_bytes,
-                    sort_workspace_bytes(n, n_tiles));
+    if (ws_bytes < workspace_bytes<K>(n))
+        return fail(XPR_ERR_INVALID, "sort: workspace %zu bytes < required %zu", ws_bytes, workspace_bytes<K>(n));
     // the dynamic shared-memory limit is a per-function attribute of the current device's module
-    XPR_CUDA_TRY(cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kScatterSmem));
+    XPR_CUDA_TRY(cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)scatter_smem<K>()));
     const int64_t nb = (n + kTile - 1) / kTile;
     const int64_t nh = (int64_t)kRadix * nb;
     char *p = reinterpret_cast<char *>(ws);
-    uint64_t *alt_k = reinterpret_cast<uint64_t *>(p);
-    p += align256((size_t)n * 8);
+    K *alt_k = reinterpret_cast<K *>(p);
+    p += align256((size_t)n * sizeof(K));
     uint32_t *alt_v = reinterpret_cast<uint32_t *>(p);
     p += align256((size_t)n * 4);
     int32_t *hist = reinterpret_cast<int32_t *>(p);
     p += align256((size_t)(nh + 1) * 4);
     void *scan_ws = p;
 
-    const int end_bit = 32 + bits_for((int64_t)n_tiles - 1);
     const int passes = begin_bit < end_bit ? (end_bit - begin_bit + 7) / 8 : 0;
     if (passes == 0) {
-        XPR_CUDA_TRY(cudaMemcpyAsync(keys_out, keys_in, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+        XPR_CUDA_TRY(cudaMemcpyAsync(keys_out, keys_in, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, st));
         XPR_CUDA_TRY(cudaMemcpyAsync(vals_out, vals_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
     }
-    const uint64_t *src_k = keys_in;
+    const K *src_k = keys_in;
     const uint32_t *src_v = vals_in;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = begin_bit + 8 * pass;
         const int nbits = min(8, end_bit - shift);
         const uint32_t mask = (1u << nbits) - 1u;
         const bool to_out = ((passes - 1 - pass) % 2) == 0;
-        uint64_t *dst_k = to_out ? keys_out : alt_k;
+        K *dst_k = to_out ? keys_out : alt_k;
         uint32_t *dst_v = to_out ? vals_out : alt_v;
-        radix_hist_kernel<<<(unsigned)nb, kThreads, 0, st>>>(src_k, n, shift, mask, hist, nb);
+        radix_hist_kernel<K><<<(unsigned)nb, kThreads, 0, st>>>(src_k, n, shift, mask, hist, nb);
         XPR_LAUNCH_CHECK("radix_hist_kernel");
         int s = launch_exclusive_scan(hist, hist, nh, scan_ws, nullptr, st);
         if (s != XPR_OK) return s;
-        radix_scatter_kernel<<<(unsigned)nb, kThreads, kScatterSmem, st>>>(src_k, src_v, dst_k, dst_v, n, shift,
-                                                                           mask, hist, nb);
+        radix_scatter_kernel<K><<<(unsigned)nb, kThreads, scatter_smem<K>(), st>>>(src_k, src_v, dst_k, dst_v, n,
+                                                                                   shift, mask, hist, nb);
         XPR_LAUNCH_CHECK("radix_scatter_kernel");
         src_k = dst_k;
         src_v = dst_v;
     }
-    tile_ranges_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys_out, n, (uint32_t)n_tiles,
-                                                                    reinterpret_cast<int2 *>(ranges));
+    tile_ranges_kernel<K><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys_out, n, (uint32_t)n_tiles,
+                                                                       reinterpret_cast<int2 *>(ranges));
     XPR_LAUNCH_CHECK("tile_ranges_kernel");
     return XPR_OK;
+}
+
+}  // namespace
+
+size_t sort_workspace_bytes(int64_t n, int32_t n_tiles) {
+    (void)n_tiles;
+    return workspace_bytes<uint64_t>(n);
+}
+
+size_t sort_tiles_workspace_bytes(int64_t n, int32_t n_tiles) {
+    (void)n_tiles;
+    return workspace_bytes<uint32_t>(n);
+}
+
+int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
+                uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {
+    const int end_bit = 32 + bits_for((int64_t)n_tiles - 1);
+    return radix_sort<uint64_t>(keys_in, vals_in, n, n_tiles, begin_bit, end_bit, keys_out, vals_out, ranges, ws,
+                                ws_bytes, st);
+}
+
+int launch_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles,
+                      uint32_t *tiles_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes,
+                      cudaStream_t st) {
+    return radix_sort<uint32_t>(tiles_in, vals_in, n, n_tiles, 0, bits_for((int64_t)n_tiles - 1), tiles_out,
+                                vals_out, ranges, ws, ws_bytes, st);
 }
 
 }  // namespace xpr

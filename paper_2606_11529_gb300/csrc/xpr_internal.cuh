@@ -27,29 +27,34 @@ int check_launch(const char *what);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-inline int tiles_x(const XprCamera &c, const XprConfig &g) { return (c.width + g.tile_w - 1) / g.tile_w; }
-inline int tiles_y(const XprCamera &c, const XprConfig &g) { return (c.height + g.tile_h - 1) / g.tile_h; }
+__host__ __device__ inline int tiles_x(const XprCamera &c, const XprConfig &g) {
+    return (c.width + g.tile_w - 1) / g.tile_w;
+}
+__host__ __device__ inline int tiles_y(const XprCamera &c, const XprConfig &g) {
+    return (c.height + g.tile_h - 1) / g.tile_h;
+}
 
 int validate_camera_config(const XprCamera *cam, const XprConfig *cfg);
 
 // ---- launch helpers implemented per translation unit -------------------------------------
 int launch_project_fwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg, float *rec,
-                       int32_t *bbox, int32_t *tc, cudaStream_t st);
+                       int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st);
 int launch_project_bwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg,
                        const float *d_rec, const XprPrimsGrad &g, cudaStream_t st);
 
-// Device-wide exclusive scan of int32 counts (in place allowed): out[i] = sum_{j<i} in[j],
-// out[n] = total.  partials: >= scan_partials_bytes(n) bytes.  total_out: device int64.
+// Device-wide exclusive scan of int32 counts: out[j] = sum_{k<j} item(k), out[n] = total, where
+// item(k) = in[gather[k]] if gather is non-NULL, else in[k] (then in == out is allowed).
+// partials: >= scan_partials_bytes(n) bytes.  total_out: device int64.
 size_t scan_partials_bytes(int64_t n);
 int64_t *scan_total_ptr(void *partials, int64_t n);  // where the scan leaves the total when total_out == NULL
 int launch_exclusive_scan(const int32_t *in, int32_t *out, int64_t n, void *partials, int64_t *total_out,
-                          cudaStream_t st);
+                          cudaStream_t st, const int32_t *gather = nullptr);
 
 int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                      const XprCamera &cam, const XprConfig &cfg, int32_t *counts, cudaStream_t st);
 int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                     const XprCamera &cam, const XprConfig &cfg, const int32_t *offsets, uint64_t *keys,
-                    uint32_t *vals, cudaStream_t st);
+                    uint32_t *tiles, uint32_t *vals, cudaStream_t st);
 size_t depth_order_workspace_bytes(int64_t n);
 int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
                        cudaStream_t st);
@@ -57,6 +62,10 @@ int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *
 size_t sort_workspace_bytes(int64_t n, int32_t n_tiles);
 int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
                 uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st);
+size_t sort_tiles_workspace_bytes(int64_t n, int32_t n_tiles);
+int launch_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles,
+                      uint32_t *tiles_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes,
+                      cudaStream_t st);
 
 int launch_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges,
                       const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final, int32_t *n_contrib,

@@ -73,15 +73,19 @@ _NO_TIMERS = _NoTimers()
 
 @dataclass
 class Frame:
-    """Everything the forward produces (kept for the backward and for tests)."""
+    """Everything the forward produces (kept for the backward and for tests).  The pairs are
+    emitted in depth order, so `tiles` (u32 tile ids, int32 storage) sorted stably by tile give
+    the (tile, depth) order of Sec. 4.2."""
     rec: torch.Tensor
     bbox: torch.Tensor
     tile_count: torch.Tensor
+    isect_count: torch.Tensor
+    order: torch.Tensor
     offsets: torch.Tensor
-    keys: torch.Tensor
+    tiles: torch.Tensor
     vals: torch.Tensor
     n_isect: int
-    keys_sorted: torch.Tensor
+    tiles_sorted: torch.Tensor
     vals_sorted: torch.Tensor
     ranges: torch.Tensor
     image: torch.Tensor
@@ -91,7 +95,8 @@ class Frame:
 
 def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
                   timers=None) -> Frame:
-    """The four forward stages, each one C-ABI call."""
+    """The forward stages, each one C-ABI call: project (with exact kept-tile counts), depth
+    order, bin (emit only), sort by tile, render."""
     L = B.load()
     tm = timers or _NO_TIMERS
     ccam, ccfg = B.make_camera(cam), B.make_config(cfg)
@@ -99,9 +104,10 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     dev = mu.device
     ws = ws or Workspace()
     tm.start("project", stream)
-    rec, bbox, tc = B.xpr_project(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream)
+    rec, bbox, tc, cnt = B.xpr_project(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream,
+                                       with_isect_count=True)
     tm.stop("project", stream)
-    # emit intersections in (depth, index) order so that the sort only has to order tile bits
+    # emit intersections in (depth, index) order so that the sort only has to order tile ids
     tm.start("depth_order", stream)
     order = B.xpr_depth_order(rec, tc, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(n), dev),
                               stream=stream)
@@ -109,20 +115,20 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
     bin_ws = ws.scratch("bin", L.xpr_tile_bin_workspace(n), dev)
     tm.start("tile_bin", stream)
-    offsets, keys, vals, I = B.xpr_tile_bin(rec, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
-                                            stream=stream, order=order)
+    offsets, tiles, vals, I = B.xpr_tile_bin(rec, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
+                                             stream=stream, order=order, isect_count=cnt, tile_ids=True)
     tm.stop("tile_bin", stream)
     ws.last_isect = I
     Wt, Ht = B.tiles_of(cam, cfg)
     nt = Wt * Ht
-    sort_ws = ws.scratch("sort", L.xpr_sort_workspace(I, nt), dev)
+    sort_ws = ws.scratch("sort", L.xpr_sort_tiles_workspace(I, nt), dev)
     tm.start("sort", stream)
-    ks, vs, ranges = B.xpr_sort(keys, vals, nt, workspace=sort_ws, stream=stream, begin_bit=32)
+    ks, vs, ranges = B.xpr_sort_tiles(tiles, vals, nt, workspace=sort_ws, stream=stream)
     tm.stop("sort", stream)
     tm.start("render_fwd", stream)
     image, t_final, n_contrib = B.xpr_render_fwd(rec, vs, ranges, ccam, ccfg, stream=stream)
     tm.stop("render_fwd", stream)
-    return Frame(rec, bbox, tc, offsets, keys, vals, I, ks, vs, ranges, image, t_final, n_contrib)
+    return Frame(rec, bbox, tc, cnt, order, offsets, tiles, vals, I, ks, vs, ranges, image, t_final, n_contrib)
 
 
 class SplatFunction(torch.autograd.Function):

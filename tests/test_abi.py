@@ -72,7 +72,7 @@ def test_invalid_arguments_rejected_on_host(lib, over, frag):
     from paper_2606_11529_gb300 import binding
     cam, cfg = _cam_cfg(**over)
     p = binding.XprPrims(1, 1, 16, 1, 1)  # never dereferenced: validation fails first
-    s = lib.xpr_project(ctypes.byref(p), 1, ctypes.byref(cam), ctypes.byref(cfg), 16, 16, 16, None)
+    s = lib.xpr_project(ctypes.byref(p), 1, ctypes.byref(cam), ctypes.byref(cfg), 16, 16, 16, None, None)
     assert s == binding.XPR_ERR_INVALID
     assert frag in lib.xpr_last_error()
 
@@ -80,17 +80,17 @@ def test_invalid_arguments_rejected_on_host(lib, over, frag):
 def test_null_and_alias_rejected(lib):
     from paper_2606_11529_gb300 import binding
     cam, cfg = _cam_cfg()
-    s = lib.xpr_project(None, 5, ctypes.byref(cam), ctypes.byref(cfg), None, None, None, None)
+    s = lib.xpr_project(None, 5, ctypes.byref(cam), ctypes.byref(cfg), None, None, None, None, None)
     assert s == binding.XPR_ERR_INVALID
     s = lib.xpr_sort(256, 256, 10, 4, 0, 256, 512, 1024, 4096, 1 << 20, None)
     assert s == binding.XPR_ERR_INVALID and b"alias" in lib.xpr_last_error()
     s = lib.xpr_sort(256, 256, 10, 4, 33, 512, 768, 1024, 4096, 1 << 20, None)
     assert s == binding.XPR_ERR_INVALID and b"begin_bit" in lib.xpr_last_error()
     n = ctypes.c_int64(0)
-    s = lib.xpr_tile_bin(256, 256, 256, None, 10, ctypes.byref(cam), ctypes.byref(cfg), 256, 256, 256, -1,
-                         ctypes.byref(n), 256, 1 << 20, None)
+    s = lib.xpr_tile_bin(256, 256, 256, None, None, 10, ctypes.byref(cam), ctypes.byref(cfg), 256, 256, None, 256,
+                         -1, ctypes.byref(n), 256, 1 << 20, None)
     assert s == binding.XPR_ERR_INVALID and b"capacity" in lib.xpr_last_error()
-    s = lib.xpr_project(None, -1, ctypes.byref(cam), ctypes.byref(cfg), None, None, None, None)
+    s = lib.xpr_project(None, -1, ctypes.byref(cam), ctypes.byref(cfg), None, None, None, None, None)
     assert s == binding.XPR_ERR_INVALID
 
 

@@ -85,9 +85,9 @@ def test_tile_bin_capacity_protocol(oracle):
     ws = torch.empty(L.xpr_tile_bin_workspace(n), dtype=torch.uint8, device="cuda")
     got = ctypes.c_int64(0)
     c, g = B.make_camera(cam), B.make_config(cfg)
-    s = L.xpr_tile_bin(args[0].data_ptr(), args[1].data_ptr(), args[2].data_ptr(), None, n, ctypes.byref(c),
-                       ctypes.byref(g), off.data_ptr(), kbuf.data_ptr(), vbuf.data_ptr(), 8, ctypes.byref(got),
-                       ws.data_ptr(), ws.numel(), None)
+    s = L.xpr_tile_bin(args[0].data_ptr(), args[1].data_ptr(), args[2].data_ptr(), None, None, n, ctypes.byref(c),
+                       ctypes.byref(g), off.data_ptr(), kbuf.data_ptr(), None, vbuf.data_ptr(), 8,
+                       ctypes.byref(got), ws.data_ptr(), ws.numel(), None)
     torch.cuda.synchronize()
     assert s == B.XPR_ERR_CAPACITY and got.value == keys.size
     assert torch.all(kbuf == -7) and torch.all(vbuf == -7)
@@ -103,6 +103,57 @@ def test_sort_bit_exact_on_binned_pairs(oracle):
     ks, vs, rg = B.xpr_sort(dev_i64(keys), dev_i32(vals), ranges.shape[0])
     np.testing.assert_array_equal(host_u64(ks), sk)
     np.testing.assert_array_equal(host_u32(vs), sv)
+    np.testing.assert_array_equal(rg.cpu().numpy(), ranges)
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_projection_counts_equal_binning_counts(oracle, tile):
+    # xpr_project's per-primitive kept-tile counts drive the emit directly; they must equal what the
+    # binning's own counting pass finds, and the emitted pairs must not change
+    sc, cam, cfg = _case(0, tile, n=30_000, W=250, H=170)
+    sc.scale[::53] *= 15.0
+    rec, bbox, tc, cnt = B.xpr_project(*R.scene_to_device(sc), cam, cfg, with_isect_count=True)
+    order = B.xpr_depth_order(rec, tc)
+    off0, k0, v0, I0 = B.xpr_tile_bin(rec, bbox, tc, cam, cfg, order=order)
+    off1, k1, v1, I1 = B.xpr_tile_bin(rec, bbox, tc, cam, cfg, order=order, isect_count=cnt)
+    assert I0 == I1 > 10_000
+    assert torch.equal(off0, off1) and torch.equal(k0, k1) and torch.equal(v0, v1)
+    assert torch.equal(cnt[order.long()], (off0[1:] - off0[:-1]))
+    # and against the oracle's own projection + exact-FP32 cull (equal except near ties)
+    pr = oracle.project_scene(sc, cam, cfg)
+    c_o, _, _ = oracle.bin_pairs(pr["rec"].astype(np.float32), pr["bbox"], cam, cfg, exact32=True)
+    assert (cnt.cpu().numpy() == c_o).mean() > 0.998
+    # u32 tile ids carry the same pairs as the u64 keys
+    _, t2, v2, I2 = B.xpr_tile_bin(rec, bbox, tc, cam, cfg, order=order, isect_count=cnt, tile_ids=True)
+    assert torch.equal(v2, v0) and torch.equal(t2.long() & 0xffffffff, (k0 >> 32) & 0xffffffff)
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_sort_tiles_of_depth_ordered_pairs_bit_exact(oracle, tile):
+    sc, cam, cfg = _case(0, tile, n=20_000, W=250, H=170)
+    pr = oracle.project_scene(sc, cam, cfg)
+    rec32 = pr["rec"].astype(np.float32)
+    order = oracle.depth_order(rec32, pr["tc"])
+    _, keys, vals = oracle.bin_pairs(rec32, pr["bbox"], cam, cfg, exact32=True, order=order)
+    Wt, Ht = oracle.tiles_of(cam, cfg)
+    sk, sv, ranges = oracle.sort_pairs(keys, vals, Wt * Ht)
+    tiles = (keys >> np.uint64(32)).astype(np.uint32)
+    ts, vs, rg = B.xpr_sort_tiles(dev_i32(tiles), dev_i32(vals), Wt * Ht)
+    np.testing.assert_array_equal(host_u32(ts), (sk >> np.uint64(32)).astype(np.uint32))
+    np.testing.assert_array_equal(host_u32(vs), sv)
+    np.testing.assert_array_equal(rg.cpu().numpy(), ranges)
+
+
+@pytest.mark.parametrize("n,n_tiles", [(1, 1), (2047, 256), (2049, 8160), (100_003, 5000), (300_000, 65536)])
+def test_sort_tiles_random_stable(oracle, n, n_tiles):
+    rng = np.random.default_rng(n + 1)
+    tiles = rng.integers(0, n_tiles, size=n).astype(np.uint32)
+    vals = rng.permutation(n).astype(np.uint32)
+    order = np.argsort(tiles, kind="stable")
+    ts, vs, rg = B.xpr_sort_tiles(dev_i32(tiles), dev_i32(vals), n_tiles)
+    np.testing.assert_array_equal(host_u32(ts), tiles[order])
+    np.testing.assert_array_equal(host_u32(vs), vals[order])
+    _, _, ranges = oracle.sort_pairs(tiles.astype(np.uint64) << np.uint64(32), np.arange(n, dtype=np.uint32), n_tiles)
     np.testing.assert_array_equal(rg.cpu().numpy(), ranges)
 
 

@@ -26,9 +26,9 @@ def _noalloc(rec, bbox, tc, cam, cfg, capacity, order=None):
     vals = torch.full((max(capacity, 1),), -1, dtype=torch.int32, device="cuda")
     got = ctypes.c_int64(0)
     c, g = B.make_camera(cam), B.make_config(cfg)
-    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(),
+    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(), None,
                                None if order is None else order.data_ptr(), n, ctypes.byref(c), ctypes.byref(g),
-                               off.data_ptr(), keys.data_ptr(), vals.data_ptr(), capacity, ctypes.byref(got),
+                               off.data_ptr(), keys.data_ptr(), None, vals.data_ptr(), capacity, ctypes.byref(got),
                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()
     return s, off, keys[:got.value], vals[:got.value], got.value
@@ -59,6 +59,6 @@ def test_noalloc_capacity_and_size_limit():
     L = B.load()
     c, g = B.make_camera(cam), B.make_config(cfg)
     n_out = ctypes.c_int64(0)
-    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(), None, (1 << 26) + 1, ctypes.byref(c),
-                               ctypes.byref(g), 256, 256, 256, 0, ctypes.byref(n_out), None)
+    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(), None, None, (1 << 26) + 1,
+                               ctypes.byref(c), ctypes.byref(g), 256, 256, None, 256, 0, ctypes.byref(n_out), None)
     assert s == B.XPR_ERR_INVALID and b"limit" in L.xpr_last_error()
