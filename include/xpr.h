@@ -236,6 +236,47 @@ int xpr_render_bwd(const float *rec, int64_t n, const uint32_t *vals, const int3
 int xpr_project_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
                     const float *d_rec, const XprPrimsGrad *d_prims, void *stream);
 
+/* ---- Multi-view (batched) form ----------------------------------------------
+ * V = n_views (1..16) views of one scene of n primitives in one launch per
+ * stage.  Records are view-major: record v * n + i is primitive i seen from
+ * view v (rec[V*n,12], bbox[V*n,4], tile_count[V*n], isect_count[V*n]).
+ * All views of a render call share cam->width/height and the tile size; tile
+ * t of view v has global id v * T + t (T tiles per view), images are
+ * [V,3,H,W], t_final and n_contrib [V,H,W].  Every stage computes exactly what
+ * the single-view call computes for each view; only the scheduling differs:
+ *   xpr_project_views reads each primitive's parameters once for all views
+ *     (cams: HOST array of V cameras);
+ *   xpr_depth_order_views orders records by (view, depth, index);
+ *   xpr_tile_bin_views emits u32 global tile ids (tiles) and record indices
+ *     (vals) in that order;
+ *   xpr_sort_tiles with n_tiles = V * T gives the per-tile segments;
+ *   xpr_tile_worklist lists tiles by descending segment length, and the
+ *     render calls, given that list and a device int32 counter, run one
+ *     persistent grid whose blocks take tiles from it through the counter
+ *     (the paper's trip-count binning of Sec. 4.3 made dynamic); with
+ *     worklist NULL they launch one block per tile;
+ *   xpr_project_bwd_views sums the adjoint over views into d_prims. */
+int xpr_project_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views, const XprConfig *cfg,
+                      float *rec, int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream);
+int xpr_depth_order_views(const float *rec, const int32_t *tile_count, int64_t n, int32_t n_views, int32_t *order,
+                          void *workspace, size_t ws_bytes, void *stream); /* workspace: xpr_depth_order_workspace(V*n) */
+int xpr_tile_bin_views(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                       const int32_t *order, int64_t n, int32_t n_views, const XprCamera *cam, const XprConfig *cfg,
+                       int32_t *offsets, uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                       void *workspace, size_t ws_bytes, void *stream); /* offsets[V*n+1]; workspace: xpr_tile_bin_workspace(V*n) */
+size_t xpr_tile_worklist_workspace(int32_t n_tiles);
+int xpr_tile_worklist(const int32_t *ranges, int32_t n_tiles, int32_t *worklist, void *workspace, size_t ws_bytes,
+                      void *stream);
+int xpr_render_fwd_views(const float *rec, int64_t n, int32_t n_views, const uint32_t *vals, const int32_t *ranges,
+                         const XprCamera *cam, const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib,
+                         const int32_t *worklist, int32_t *counter, void *stream);
+int xpr_render_bwd_views(const float *rec, int64_t n, int32_t n_views, const uint32_t *vals, const int32_t *ranges,
+                         const XprCamera *cam, const XprConfig *cfg, const float *t_final, const int32_t *n_contrib,
+                         const float *d_image, float *d_rec, const int32_t *worklist, int32_t *counter,
+                         void *stream); /* d_rec[V*n,12] overwritten */
+int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
+                          const XprConfig *cfg, const float *d_rec, const XprPrimsGrad *d_prims, void *stream);
+
 /* ---- Misc ------------------------------------------------------------------ */
 const char *xpr_status_string(int status);
 const char *xpr_last_error(void); /* message of the last failing call on this host thread */

@@ -1,0 +1,157 @@
+"""Batched (multi-view) form of the splatting path and its autotuner.
+
+V views of one scene (V <= 16, one image size) run through one launch per
+stage: the projection reads each primitive once for all views, binning and
+the tile sort see the V x T tiles as one grid, and the render forward and
+adjoint run as persistent grids whose blocks take tiles from a list sorted by
+descending segment length (the paper's trip-count binning, Sec. 4.3, made
+dynamic) through an atomic counter.  Per view the result is exactly the
+single-view computation.
+
+The autotuner follows the paper's hyperparameter selection (Sec. 5,
+"Hyperparameters"): it renders the target views with each candidate tile size
+(8x8, 16x16, the paper's GPU search space) and shared-memory batch depth
+(entries staged per batch, the analogue of the paper's batch divisor), takes
+the median of repeated timed runs and caches the best setting per (device,
+scene, resolution).
+"""
+from __future__ import annotations
+
+import dataclasses
+import statistics
+
+import torch
+
+from . import binding as B
+
+TILE_CANDIDATES = ((8, 8), (16, 16))
+BATCH_CANDIDATES = (16, 32, 64, 128, 256)
+
+
+@dataclasses.dataclass
+class ViewsFrame:
+    rec: torch.Tensor
+    tile_count: torch.Tensor
+    n_isect: int
+    vals_sorted: torch.Tensor
+    ranges: torch.Tensor
+    worklist: torch.Tensor | None
+    image: torch.Tensor
+    t_final: torch.Tensor
+    n_contrib: torch.Tensor
+
+
+class ViewsWorkspace:
+    def __init__(self):
+        self.last_isect = 0
+        self.bufs = {}
+
+    def scratch(self, name, nbytes, device):
+        t = self.bufs.get(name)
+        if t is None or t.numel() < nbytes or t.device != device:
+            t = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+            self.bufs[name] = t
+        return t
+
+
+def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | None = None, persistent=True,
+                  stream=None) -> ViewsFrame:
+    L = B.load()
+    ws = ws or ViewsWorkspace()
+    n, V = mu.shape[0], len(cams)
+    dev = mu.device
+    cam0 = cams[0]
+    for c in cams:
+        if (c.width, c.height) != (cam0.width, cam0.height):
+            raise ValueError("all views of one batch must share the image size")
+    ccfg = B.make_config(cfg)
+    rec, bbox, tc, cnt = B.xpr_project_views(mu, scale, quat, opacity, sh, cams, ccfg, stream=stream)
+    order = B.xpr_depth_order_views(rec, tc, n, V, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(n * V),
+                                                                         dev), stream=stream)
+    cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
+    _, tiles, vals, I = B.xpr_tile_bin_views(rec, bbox, tc, cnt, order, n, V, cam0, ccfg, capacity=cap,
+                                             workspace=ws.scratch("bin", L.xpr_tile_bin_workspace(n * V), dev),
+                                             stream=stream)
+    ws.last_isect = I
+    Wt, Ht = B.tiles_of(cam0, cfg)
+    nt = V * Wt * Ht
+    _, vs, ranges = B.xpr_sort_tiles(tiles, vals, nt, workspace=ws.scratch("sort", L.xpr_sort_tiles_workspace(I, nt),
+                                                                             dev), stream=stream)
+    wl = B.xpr_tile_worklist(ranges, workspace=ws.scratch("wl", L.xpr_tile_worklist_workspace(nt), dev),
+                             stream=stream) if persistent else None
+    image, tfin, ncon = B.xpr_render_fwd_views(rec, n, V, vs, ranges, cam0, ccfg, worklist=wl, stream=stream)
+    return ViewsFrame(rec, tc, I, vs, ranges, wl, image, tfin, ncon)
+
+
+class MultiViewSplat(torch.autograd.Function):
+    """images[V,3,H,W] = splat of one scene from V cameras; backward sums over views."""
+
+    @staticmethod
+    def forward(ctx, mu, scale, quat, opacity, sh, cams, cfg, ws, persistent):
+        fr = forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws, persistent)
+        ctx.save_for_backward(mu, scale, quat, opacity, sh, fr.rec, fr.vals_sorted, fr.ranges, fr.t_final,
+                              fr.n_contrib, *(() if fr.worklist is None else (fr.worklist,)))
+        ctx.cams, ctx.cfg = cams, cfg
+        return fr.image
+
+    @staticmethod
+    def backward(ctx, d_image):
+        saved = ctx.saved_tensors
+        mu, scale, quat, opacity, sh, rec, vals, ranges, tfin, ncon = saved[:10]
+        wl = saved[10] if len(saved) > 10 else None
+        cams, ccfg = ctx.cams, B.make_config(ctx.cfg)
+        n, V = mu.shape[0], len(cams)
+        d_rec = B.xpr_render_bwd_views(rec, n, V, vals, ranges, cams[0], ccfg, tfin, ncon, d_image.contiguous(),
+                                       worklist=wl)
+        grads = B.xpr_project_bwd_views(mu, scale, quat, opacity, sh, cams, ccfg, d_rec)
+        return (*grads, None, None, None, None)
+
+
+def render_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | None = None, persistent=True):
+    """Differentiable render of V views in one launch per stage: returns images [V, 3, H, W]."""
+    return MultiViewSplat.apply(mu, scale, quat, opacity, sh, list(cams), cfg, ws or ViewsWorkspace(), persistent)
+
+
+# ------------------------------------------------------------------------------------------- autotuner
+
+_CACHE: dict = {}
+
+
+def _time_ms(fn, reps):
+    times = []
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e))
+    return statistics.median(times)
+
+
+def autotune(params, cams, cfg, scene_id="scene", backward=True, reps=5, tiles=TILE_CANDIDATES,
+             batches=BATCH_CANDIDATES):
+    """Returns (best_cfg, table) where table maps (tile_w, tile_h, batch) -> median ms of one batched
+    forward (+ backward) over all `cams`.  Results are cached per (device, scene_id, resolution)."""
+    key = (torch.cuda.get_device_name(), scene_id, cams[0].width, cams[0].height, len(cams), backward)
+    if key in _CACHE:
+        return _CACHE[key]
+    table = {}
+    d_img = None
+    for tw, th in tiles:
+        for bd in batches:
+            c = dataclasses.replace(cfg, tile_w=tw, tile_h=th, batch_depth=bd)
+            ws = ViewsWorkspace()
+            P = [p.detach().requires_grad_(backward) for p in params]
+
+            def run():
+                img = render_views(*P, cams, c, ws)
+                if backward:
+                    img.backward(d_img if d_img is not None else torch.ones_like(img))
+
+            run()  # warm-up (and capacity sizing)
+            table[(tw, th, bd)] = _time_ms(run, reps)
+    best = min(table, key=table.get)
+    out = (dataclasses.replace(cfg, tile_w=best[0], tile_h=best[1], batch_depth=best[2]), table)
+    _CACHE[key] = out
+    return out

@@ -64,6 +64,20 @@ SIGNATURES = {
                                c_vp, c_vp, c_vp, ctypes.POINTER(XprPrims), ctypes.POINTER(XprPrimsGrad), c_vp]),
     "xpr_project_bwd": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
                                 ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_project_views": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), c_i32,
+                                  ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_depth_order_views": (c_i32, [c_vp, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp]),
+    "xpr_tile_bin_views": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(XprCamera),
+                                   ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp,
+                                   c_sz, c_vp]),
+    "xpr_tile_worklist_workspace": (c_sz, [c_i32]),
+    "xpr_tile_worklist": (c_i32, [c_vp, c_i32, c_vp, c_vp, c_sz, c_vp]),
+    "xpr_render_fwd_views": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp, ctypes.POINTER(XprCamera),
+                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_render_bwd_views": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp, ctypes.POINTER(XprCamera),
+                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_project_bwd_views": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), c_i32,
+                                      ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
     "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
@@ -301,4 +315,123 @@ def xpr_project_bwd(mu, scale, quat, opacity, sh, cam, cfg, d_rec, d_prims=None,
     c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
     _check(L.xpr_project_bwd(ctypes.byref(p), mu.shape[0], ctypes.byref(c), ctypes.byref(g), _ptr(d_rec),
                              ctypes.byref(gp), _stream(stream)), "xpr_project_bwd")
+    return grads
+
+
+# ---------------------------------------------------------------------------------------- multi-view form
+
+def camera_array(cams):
+    arr = (XprCamera * len(cams))()
+    for v, c in enumerate(cams):
+        arr[v] = c if isinstance(c, XprCamera) else make_camera(c)
+    return arr
+
+
+def xpr_project_views(mu, scale, quat, opacity, sh, cams, cfg, stream=None):
+    """Returns rec[V*n,12], bbox[V*n,4], tile_count[V*n], isect_count[V*n] (view-major)."""
+    L = load()
+    n, V = mu.shape[0], len(cams)
+    dev = mu.device
+    rec = torch.empty((V * n, REC), dtype=torch.float32, device=dev)
+    bbox = torch.empty((V * n, 4), dtype=torch.int32, device=dev)
+    tc = torch.empty(V * n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(V * n, dtype=torch.int32, device=dev)
+    p = _prims(mu, scale, quat, opacity, sh)
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_project_views(ctypes.byref(p), n, camera_array(cams), V, ctypes.byref(g), _ptr(rec), _ptr(bbox),
+                               _ptr(tc), _ptr(cnt), _stream(stream)), "xpr_project_views")
+    return rec, bbox, tc, cnt
+
+
+def xpr_depth_order_views(rec, tile_count, n, n_views, workspace=None, stream=None):
+    L = load()
+    order = torch.empty(n * n_views, dtype=torch.int32, device=rec.device)
+    need = int(L.xpr_depth_order_workspace(n * n_views))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=rec.device)
+    _check(L.xpr_depth_order_views(_ptr(rec), _ptr(tile_count), n, n_views, _ptr(order), _ptr(workspace),
+                                   workspace.numel(), _stream(stream)), "xpr_depth_order_views")
+    return order
+
+
+def xpr_tile_bin_views(rec, bbox, tile_count, isect_count, order, n, n_views, cam, cfg, capacity=None,
+                       workspace=None, stream=None):
+    """Returns (offsets[V*n+1], tiles[I] (global u32 ids, int32 storage), vals[I], I)."""
+    L = load()
+    dev = rec.device
+    N = n * n_views
+    offsets = torch.empty(N + 1, dtype=torch.int32, device=dev)
+    need = int(L.xpr_tile_bin_workspace(N))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    cap = int(capacity) if capacity is not None else max(4 * N, 1024)
+    tiles = torch.empty(cap, dtype=torch.int32, device=dev)
+    vals = torch.empty(cap, dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    for _ in range(2):
+        got = c_i64(0)
+        s = L.xpr_tile_bin_views(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _ptr(order), n,
+                                 n_views, ctypes.byref(c), ctypes.byref(g), _ptr(offsets), _ptr(tiles), _ptr(vals),
+                                 tiles.numel(), ctypes.byref(got), _ptr(workspace), workspace.numel(),
+                                 _stream(stream))
+        if s == XPR_ERR_CAPACITY and got.value <= 0x7FFFFFFF:
+            tiles = torch.empty(got.value, dtype=torch.int32, device=dev)
+            vals = torch.empty(got.value, dtype=torch.int32, device=dev)
+            continue
+        _check(s, "xpr_tile_bin_views")
+        I = int(got.value)
+        return offsets, tiles[:I], vals[:I], I
+    raise XprError(XPR_ERR_CAPACITY, "xpr_tile_bin_views", "capacity retry failed")
+
+
+def xpr_tile_worklist(ranges, workspace=None, stream=None):
+    L = load()
+    nt = ranges.shape[0]
+    wl = torch.empty(nt, dtype=torch.int32, device=ranges.device)
+    need = int(L.xpr_tile_worklist_workspace(nt))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=ranges.device)
+    _check(L.xpr_tile_worklist(_ptr(ranges), nt, _ptr(wl), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "xpr_tile_worklist")
+    return wl
+
+
+def xpr_render_fwd_views(rec, n, n_views, vals, ranges, cam, cfg, worklist=None, counter=None, stream=None):
+    L = load()
+    dev = rec.device
+    H, W = int(cam.height), int(cam.width)
+    image = torch.empty((n_views, 3, H, W), dtype=torch.float32, device=dev)
+    tfin = torch.empty((n_views, H, W), dtype=torch.float32, device=dev)
+    ncon = torch.empty((n_views, H, W), dtype=torch.int32, device=dev)
+    if worklist is not None and counter is None:
+        counter = torch.empty(1, dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_fwd_views(_ptr(rec), n, n_views, _ptr(vals), _ptr(ranges), ctypes.byref(c), ctypes.byref(g),
+                                  _ptr(image), _ptr(tfin), _ptr(ncon), _ptr(worklist), _ptr(counter),
+                                  _stream(stream)), "xpr_render_fwd_views")
+    return image, tfin, ncon
+
+
+def xpr_render_bwd_views(rec, n, n_views, vals, ranges, cam, cfg, t_final, n_contrib, d_image, worklist=None,
+                         counter=None, stream=None):
+    L = load()
+    dev = rec.device
+    d_rec = torch.empty((n * n_views, REC), dtype=torch.float32, device=dev)
+    if worklist is not None and counter is None:
+        counter = torch.empty(1, dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_bwd_views(_ptr(rec), n, n_views, _ptr(vals), _ptr(ranges), ctypes.byref(c), ctypes.byref(g),
+                                  _ptr(t_final), _ptr(n_contrib), _ptr(d_image.contiguous()), _ptr(d_rec),
+                                  _ptr(worklist), _ptr(counter), _stream(stream)), "xpr_render_bwd_views")
+    return d_rec
+
+
+def xpr_project_bwd_views(mu, scale, quat, opacity, sh, cams, cfg, d_rec, stream=None):
+    L = load()
+    grads = tuple(torch.empty_like(t) for t in (mu, scale, quat, opacity, sh))
+    p = _prims(mu, scale, quat, opacity, sh)
+    gp = XprPrimsGrad(*[t.data_ptr() for t in grads])
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_project_bwd_views(ctypes.byref(p), mu.shape[0], camera_array(cams), len(cams), ctypes.byref(g),
+                                   _ptr(d_rec), ctypes.byref(gp), _stream(stream)), "xpr_project_bwd_views")
     return grads

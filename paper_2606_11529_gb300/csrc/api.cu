@@ -98,10 +98,15 @@ int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const Xp
 
 size_t xpr_tile_bin_workspace(int64_t n) { return scan_partials_bytes(n < 0 ? 0 : n); }
 
-int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
-                 const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *offsets,
-                 uint64_t *keys, uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
-                 void *workspace, size_t ws_bytes, void *stream) {
+}  // extern "C"
+
+namespace xpr {
+// n records; per_view > 0: records are view-major with per_view records per view and tile ids are
+// offset by view * tiles-per-view.
+int tile_bin_impl(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                  const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *offsets,
+                  uint64_t *keys, uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                  void *workspace, size_t ws_bytes, void *stream, int64_t per_view) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
     if ((s = check_n(n))) return s;
@@ -136,7 +141,18 @@ int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_coun
         return fail(XPR_ERR_CAPACITY, "xpr_tile_bin: %lld intersections > capacity %lld", (long long)total,
                     (long long)capacity);
     if (total > 0 && ((!keys && !tiles) || !vals)) return fail(XPR_ERR_INVALID, "xpr_tile_bin: NULL keys/tiles/vals");
-    return launch_bin_emit(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, keys, tiles, vals, st);
+    return launch_bin_emit(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, keys, tiles, vals, st, per_view);
+}
+}  // namespace xpr
+
+extern "C" {
+
+int xpr_tile_bin(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                 const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *offsets,
+                 uint64_t *keys, uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                 void *workspace, size_t ws_bytes, void *stream) {
+    return tile_bin_impl(rec, bbox, tile_count, isect_count, order, n, cam, cfg, offsets, keys, tiles, vals,
+                         capacity, n_isect, workspace, ws_bytes, stream, 0);
 }
 
 size_t xpr_sort_tiles_workspace(int64_t n_isect, int32_t n_tiles) {
@@ -229,6 +245,112 @@ int xpr_render_bwd(const float *rec, int64_t n, const uint32_t *vals, const int3
     if ((s = launch_render_bwd(rec, vals, ranges, *cam, *cfg, t_final, n_contrib, d_image, d_rec, n, st))) return s;
     if (prims && d_prims) return xpr_project_bwd(prims, n, cam, cfg, d_rec, d_prims, stream);
     return XPR_OK;
+}
+
+// ---- multi-view (batched) form ------------------------------------------------------------
+
+static int check_views(int32_t n_views, int64_t n) {
+    if (n_views < 1 || n_views > kMaxViews)
+        return fail(XPR_ERR_INVALID, "view count %d out of range [1, %d]", n_views, kMaxViews);
+    if (n < 0 || n * (int64_t)n_views > 0x7fffffffLL)
+        return fail(XPR_ERR_INVALID, "views x primitives = %lld x %d exceeds 2^31-1 records", (long long)n, n_views);
+    return XPR_OK;
+}
+
+int xpr_project_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views, const XprConfig *cfg,
+                      float *rec, int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream) {
+    int s = check_views(n_views, n);
+    if (s) return s;
+    if (!cams) return fail(XPR_ERR_INVALID, "xpr_project_views: NULL cameras");
+    for (int v = 0; v < n_views; ++v)
+        if ((s = validate_camera_config(cams + v, cfg))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh || !rec || !bbox ||
+        !tile_count)
+        return fail(XPR_ERR_INVALID, "xpr_project_views: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(bbox, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_views: quat, rec and bbox must be 16-byte aligned");
+    return launch_project_fwd_views(*prims, n, cams, n_views, *cfg, rec, bbox, tile_count, isect_count,
+                                    as_stream(stream));
+}
+
+int xpr_depth_order_views(const float *rec, const int32_t *tile_count, int64_t n, int32_t n_views, int32_t *order,
+                          void *workspace, size_t ws_bytes, void *stream) {
+    int s = check_views(n_views, n);
+    if (s) return s;
+    if (n == 0) return XPR_OK;
+    if (!rec || !tile_count || !order || !workspace) return fail(XPR_ERR_INVALID, "xpr_depth_order_views: NULL");
+    if (!aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_depth_order_views: workspace alignment");
+    return launch_depth_order(rec, tile_count, n * n_views, order, workspace, ws_bytes, as_stream(stream), n,
+                              n_views);
+}
+
+int xpr_tile_bin_views(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                       const int32_t *order, int64_t n, int32_t n_views, const XprCamera *cam, const XprConfig *cfg,
+                       int32_t *offsets, uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                       void *workspace, size_t ws_bytes, void *stream) {
+    int s = check_views(n_views, n);
+    if (s) return s;
+    return tile_bin_impl(rec, bbox, tile_count, isect_count, order, n * n_views, cam, cfg, offsets, nullptr, tiles,
+                         vals, capacity, n_isect, workspace, ws_bytes, stream, n);
+}
+
+size_t xpr_tile_worklist_workspace(int32_t n_tiles) { return worklist_workspace_bytes(n_tiles < 0 ? 0 : n_tiles); }
+
+int xpr_tile_worklist(const int32_t *ranges, int32_t n_tiles, int32_t *worklist, void *workspace, size_t ws_bytes,
+                      void *stream) {
+    if (n_tiles < 0) return fail(XPR_ERR_INVALID, "xpr_tile_worklist: negative tile count");
+    if (n_tiles == 0) return XPR_OK;
+    if (!ranges || !worklist || !workspace) return fail(XPR_ERR_INVALID, "xpr_tile_worklist: NULL pointer");
+    if (!aligned(ranges, 8) || !aligned(workspace, 256))
+        return fail(XPR_ERR_INVALID, "xpr_tile_worklist: ranges/workspace alignment");
+    return launch_tile_worklist(ranges, n_tiles, worklist, workspace, ws_bytes, as_stream(stream));
+}
+
+int xpr_render_fwd_views(const float *rec, int64_t n, int32_t n_views, const uint32_t *vals, const int32_t *ranges,
+                         const XprCamera *cam, const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib,
+                         const int32_t *worklist, int32_t *counter, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_views(n_views, n))) return s;
+    if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_fwd_views: NULL");
+    if (n > 0 && (!rec || !aligned(rec, 16))) return fail(XPR_ERR_INVALID, "xpr_render_fwd_views: rec");
+    if (worklist && !counter) return fail(XPR_ERR_INVALID, "xpr_render_fwd_views: worklist needs a counter");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_fwd_views: ranges must be 8-byte aligned");
+    return launch_render_fwd_views(rec, n * n_views, vals, ranges, n_views, *cam, *cfg, image, t_final, n_contrib,
+                                   worklist, counter, as_stream(stream));
+}
+
+int xpr_render_bwd_views(const float *rec, int64_t n, int32_t n_views, const uint32_t *vals, const int32_t *ranges,
+                         const XprCamera *cam, const XprConfig *cfg, const float *t_final, const int32_t *n_contrib,
+                         const float *d_image, float *d_rec, const int32_t *worklist, int32_t *counter,
+                         void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_views(n_views, n))) return s;
+    if (!ranges || !t_final || !n_contrib || !d_image) return fail(XPR_ERR_INVALID, "xpr_render_bwd_views: NULL");
+    if (n == 0) return XPR_OK;
+    if (!rec || !d_rec || !aligned(rec, 16) || !aligned(d_rec, 16))
+        return fail(XPR_ERR_INVALID, "xpr_render_bwd_views: rec/d_rec NULL or not 16-byte aligned");
+    if (worklist && !counter) return fail(XPR_ERR_INVALID, "xpr_render_bwd_views: worklist needs a counter");
+    return launch_render_bwd_views(rec, vals, ranges, n_views, *cam, *cfg, t_final, n_contrib, d_image, d_rec,
+                                   n * n_views, worklist, counter, as_stream(stream));
+}
+
+int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
+                          const XprConfig *cfg, const float *d_rec, const XprPrimsGrad *d_prims, void *stream) {
+    int s = check_views(n_views, n);
+    if (s) return s;
+    if (!cams) return fail(XPR_ERR_INVALID, "xpr_project_bwd_views: NULL cameras");
+    for (int v = 0; v < n_views; ++v)
+        if ((s = validate_camera_config(cams + v, cfg))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !d_prims || !d_rec || !prims->mu || !prims->scale || !prims->quat || !prims->opacity ||
+        !prims->sh || !d_prims->mu || !d_prims->scale || !d_prims->quat || !d_prims->opacity || !d_prims->sh)
+        return fail(XPR_ERR_INVALID, "xpr_project_bwd_views: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_rec, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_bwd_views: quat and d_rec must be 16-byte aligned");
+    return launch_project_bwd_views(*prims, n, cams, n_views, *cfg, d_rec, *d_prims, as_stream(stream));
 }
 
 }  // extern "C"

@@ -54,10 +54,13 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float *__restrict_
 // most kSmallBox tiles are walked by their own thread; larger ones by the whole warp, 32 slots at a
 // time, with ballot prefix counts keeping the pairs in r order.  keys (u64 tile << 32 | depth bits)
 // and tiles (u32 tile id) are each written when non-NULL.
+// Records of a multi-view launch are view-major (record i belongs to view i div per_view) and the
+// tile id of a pair is offset by view * tiles_per_view (per_view = 0: a single view).
 __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
                                                        const int *__restrict__ tcount,
                                                        const int *__restrict__ order, int64_t n, int64_t stride,
-                                                       Grid g, const int32_t *__restrict__ offsets,
+                                                       Grid g, int64_t per_view, int tiles_per_view,
+                                                       const int32_t *__restrict__ offsets,
                                                        uint64_t *__restrict__ keys, uint32_t *__restrict__ tiles,
                                                        uint32_t *__restrict__ vals) {
     const int64_t j = visited_position(n, stride);
@@ -71,12 +74,13 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
     if (area > 0 && area <= kSmallBox) {
         const CullData d = load_cull(rec, i);
         const uint32_t depth_bits = __float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]);
+        const uint32_t tbase = per_view ? (uint32_t)(i / per_view) * (uint32_t)tiles_per_view : 0u;
         const int64_t out = offsets[j];
         int cnt = 0;
         for (int ty = bb.y; ty < bb.w; ++ty)
             for (int tx = bb.x; tx < bb.z; ++tx) {
                 if (!keep_tile(d, g, tx, ty)) continue;
-                const uint32_t t = (uint32_t)(ty * g.Wt + tx);
+                const uint32_t t = tbase + (uint32_t)(ty * g.Wt + tx);
                 if (keys) keys[out + cnt] = ((uint64_t)t << 32) | depth_bits;
                 if (tiles) tiles[out + cnt] = t;
                 vals[out + cnt] = (uint32_t)i;
@@ -94,6 +98,7 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
         const int bw = __shfl_sync(kFullMask, bb.z, src) - bx;
         const CullData d = load_cull(rec, ib);
         const uint32_t depth_bits = __float_as_uint(rec[(size_t)ib * XPR_REC_FLOATS + 9]);
+        const uint32_t tbase = per_view ? (uint32_t)(ib / per_view) * (uint32_t)tiles_per_view : 0u;
         const int64_t out = offsets[jb];
         SlotWalk sw(bx, by, bw, lane);
         int cnt = 0;
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
             const unsigned m = __ballot_sync(kFullMask, keep);
             if (keep) {
                 const int64_t pos = out + cnt + __popc(m & ((1u << lane) - 1u));
-                const uint32_t t = (uint32_t)(sw.ty * g.Wt + sw.tx);
+                const uint32_t t = tbase + (uint32_t)(sw.ty * g.Wt + sw.tx);
                 if (keys) keys[pos] = ((uint64_t)t << 32) | depth_bits;
                 if (tiles) tiles[pos] = t;
                 vals[pos] = (uint32_t)ib;
@@ -116,11 +121,14 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
 // Sort key of the depth order: camera-z bits of primitives that have tiles, all ones otherwise
 // (those go last, in index order).  Depth of a primitive with tiles is > z_near > 0, so its float
 // bits order like the values.
+// Multi-view: the view of record i (i div per_view) goes in bits 32.. so views stay in order.
 __global__ void depth_key_kernel(const float *__restrict__ rec, const int *__restrict__ tcount, int64_t n,
-                                 uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                                 int64_t per_view, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    keys[i] = tcount[i] > 0 ? (uint64_t)__float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]) : 0xffffffffull;
+    const uint64_t view = per_view ? (uint64_t)(i / per_view) : 0ull;
+    const uint64_t d = tcount[i] > 0 ? (uint64_t)__float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]) : 0xffffffffull;
+    keys[i] = (view << 32) | d;
     vals[i] = (uint32_t)i;
 }
 
@@ -270,38 +278,40 @@ int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, c
 
 int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                     const XprCamera &cam, const XprConfig &cfg, const int32_t *offsets, uint64_t *keys,
-                    uint32_t *tiles, uint32_t *vals, cudaStream_t st) {
+                    uint32_t *tiles, uint32_t *vals, cudaStream_t st, int64_t per_view) {
     if (n == 0) return XPR_OK;
     const int tpb = 256;
     bin_emit_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, visit_stride(n), make_grid(cam, cfg), offsets, keys,
-        tiles, vals);
+        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, visit_stride(n), make_grid(cam, cfg), per_view,
+        tiles_x(cam, cfg) * tiles_y(cam, cfg), offsets, keys, tiles, vals);
     XPR_LAUNCH_CHECK("bin_emit_kernel");
     return XPR_OK;
 }
 
 size_t depth_order_workspace_bytes(int64_t n) {
     const size_t a = ((size_t)n * 8 + 255) / 256 * 256, b = ((size_t)n * 4 + 255) / 256 * 256;
-    return 2 * a + b + 256 + sort_workspace_bytes(n, 1);
+    return 2 * a + b + 256 + sort_workspace_bytes(n, kMaxViews);
 }
 
 int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
-                       cudaStream_t st) {
+                       cudaStream_t st, int64_t per_view, int n_views) {
     if (n == 0) return XPR_OK;
     if (ws_bytes < depth_order_workspace_bytes(n))
         return fail(XPR_ERR_INVALID, "xpr_depth_order: workspace %zu < %zu bytes", ws_bytes,
                     depth_order_workspace_bytes(n));
+    if (n_views < 1 || n_views > kMaxViews) return fail(XPR_ERR_INVALID, "xpr_depth_order: bad view count");
     const size_t a = ((size_t)n * 8 + 255) / 256 * 256, b = ((size_t)n * 4 + 255) / 256 * 256;
     char *p = reinterpret_cast<char *>(ws);
     uint64_t *keys = reinterpret_cast<uint64_t *>(p);
     uint64_t *keys_sorted = reinterpret_cast<uint64_t *>(p + a);
     uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
-    int32_t *ranges = reinterpret_cast<int32_t *>(p + 2 * a + b);
+    int32_t *ranges = reinterpret_cast<int32_t *>(p + 2 * a + b);  // n_views int2 (unused by the caller)
     void *sort_ws = p + 2 * a + b + 256;
-    depth_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, tc, n, keys, vals);
+    depth_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, tc, n, per_view, keys, vals);
     XPR_LAUNCH_CHECK("depth_key_kernel");
-    return launch_sort(keys, vals, n, 1, 0, keys_sorted, reinterpret_cast<uint32_t *>(order), ranges, sort_ws,
-                       sort_workspace_bytes(n, 1), st);
+    // the sort's "tile" is the view: keys (view << 32 | depth bits) sort over 32 + ceil(log2 views) bits
+    return launch_sort(keys, vals, n, n_views, 0, keys_sorted, reinterpret_cast<uint32_t *>(order), ranges, sort_ws,
+                       sort_workspace_bytes(n, n_views), st);
 }
 
 }  // namespace xpr

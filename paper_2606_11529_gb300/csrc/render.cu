@@ -1,8 +1,9 @@
 // Shader stage (Sec. 2 Shader; Sec. 4.3; Algorithm 1; Listing 1 evaluate) and its adjoint.
 //
-// Forward (K4): one thread block per tile, one thread per pixel.  The tile's depth-sorted list is
-// consumed in batches: every thread stages one entry's shading record into shared memory, then each
-// pixel walks the batch front to back:
+// Forward (K4): one thread block per tile; each thread owns two pixels of the tile, (x, y) and
+// (x, y + h/2), so every shared-memory read of a list entry and every warp reduction of the
+// adjoint serves two pixels.  The tile's depth-sorted list is consumed in batches of
+// `batch` entries staged in shared memory, then each pixel walks the batch front to back:
 //   power = -(c00 dx^2 + 2 c01 dx dy + c11 dy^2)/2  (base-2 form, conic pre-scaled by log2 e)
 //   skip if power > 0;  alpha = min(alpha_max, o 2^power2);  skip if alpha < alpha_t
 //   stop if T (1 - alpha) < t_eps (that entry is not blended);  C += c alpha T;  T *= 1 - alpha
@@ -13,84 +14,149 @@
 // recomputing T_i = T_{i+1} / (1 - alpha_i) and the colour behind, S (starting at T_final bg):
 //   dL/dc_i = g alpha_i T_i,   dL/dalpha_i = g . (c_i T_i - S_i / (1 - alpha_i))
 // then through alpha = o exp(power) (zero through the clamp) to o, mu_2D and the conic.  The 9
-// per-pixel partial gradients of one entry are summed over the warp with shuffles, over the block
-// in shared memory, and added to global memory with one set of atomics per (tile, entry).
+// per-pixel partial gradients of one entry are summed over the thread's two pixels, over the
+// warp with shuffles, over the block in shared memory, and added to global memory with one set
+// of vector atomics per (tile, entry).
+//
+// Views: tile gt of a multi-view launch is tile gt mod T of view gt div T (T tiles per view, all
+// views of one size); images are [views, 3, H, W].  Scheduling: one block per tile, or a
+// persistent grid whose blocks take tiles from a work list (tiles by descending list length,
+// the paper's trip-count binning made dynamic) through an atomic counter.
 #include "xpr_internal.cuh"
 
 namespace xpr {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPX = 2;          // pixels per thread: (x, y) and (x, y + h/2)
+constexpr int kMaxBatch = 256;  // largest shared-memory batch (entries)
 
 struct Consts {
-    int W, H, Wt;
-    uint32_t n;  // primitive count: list entries >= n are ignored
+    int W, H, Wt, T;  // image size, tiles per row, tiles per view
+    uint32_t n;       // number of records: list entries >= n are ignored
+    int batch;        // entries staged per batch, 1 .. kMaxBatch
     float at, amax, teps, bg0, bg1, bg2;
 };
 
+struct Work {  // persistent scheduling: tiles list[0 .. count) taken through *counter
+    const int *list;
+    int *counter;
+    int count;
+};
+
+__device__ __forceinline__ void stage(const float *__restrict__ rec, const uint32_t *__restrict__ vals, int e,
+                                      uint32_t n, float4 *s_g, float4 *s_c, float *s_b, uint32_t *s_id, int slot) {
+    const uint32_t id = __ldg(vals + e);
+    const Shade s = id < n ? load_shade(rec, id) : Shade{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    s_g[slot] = make_float4(s.mx, s.my, s.A, s.B);
+    s_c[slot] = make_float4(s.C, s.o, s.r, s.g);
+    s_b[slot] = s.b;
+    if (s_id) s_id[slot] = id;
+}
+
+struct PixelFwd {
+    float fy, T, r, g, b;
+    int last;
+    bool done;
+};
+
+// Blends entry (g, c, cb) at list position pos into pixel P (front to back).
+__device__ __forceinline__ void blend(PixelFwd &P, float dx, const float4 &g, const float4 &c, float cb, int pos,
+                                      const Consts &k) {
+    const float dy = __fsub_rn(P.fy, g.y);
+    const float p = eval_power2(g.z, g.w, c.x, dx, dy);
+    if (p > 0.f) return;
+    const float og = __fmul_rn(c.y, ex2_approx(p));
+    const float al = fminf(k.amax, og);
+    if (al < k.at) return;
+    const float tt = __fmul_rn(P.T, __fsub_rn(1.f, al));
+    if (tt < k.teps) {
+        P.done = true;
+        return;
+    }
+    const float w = al * P.T;
+    P.r = fmaf(c.z, w, P.r);
+    P.g = fmaf(c.w, w, P.g);
+    P.b = fmaf(cb, w, P.b);
+    P.T = tt;
+    P.last = pos + 1;
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) render_fwd_kernel(const float *__restrict__ rec,
-                                                            const uint32_t *__restrict__ vals,
-                                                            const int2 *__restrict__ ranges, Consts k,
-                                                            float *__restrict__ image, float *__restrict__ tfin,
-                                                            int *__restrict__ ncon) {
-    constexpr int NT = TW * TH;
-    __shared__ float4 s_g[NT];  // mx, my, A, B
-    __shared__ float4 s_c[NT];  // C, o, r, g
-    __shared__ float s_b[NT];   // b
-    const int tile = blockIdx.x;
+__device__ __forceinline__ void fwd_tile(int gt, const float *__restrict__ rec, const uint32_t *__restrict__ vals,
+                                         const int2 *__restrict__ ranges, const Consts &k, float *__restrict__ image,
+                                         float *__restrict__ tfin, int *__restrict__ ncon, float4 *s_g, float4 *s_c,
+                                         float *s_b) {
+    constexpr int NT = TW * TH / kPX;
+    const int v = gt / k.T, tile = gt - v * k.T;
     const int tx = tile % k.Wt, ty = tile / k.Wt;
     const int t = threadIdx.x;
-    const int px = tx * TW + (t % TW), py = ty * TH + (t / TW);
-    const bool inside = (px < k.W) && (py < k.H);
-    const int2 rg = ranges[tile];
-    const float fx = (float)px, fy = (float)py;
-    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
-    int last = 0;
-    bool done = !inside;
-    for (int base = rg.x; base < rg.y; base += NT) {
-        if (__syncthreads_and(done)) break;
-        const int e = base + t;
-        if (e < rg.y) {
-            const uint32_t id = __ldg(vals + e);
-            const Shade s = id < k.n ? load_shade(rec, id) : Shade{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            s_g[t] = make_float4(s.mx, s.my, s.A, s.B);
-            s_c[t] = make_float4(s.C, s.o, s.r, s.g);
-            s_b[t] = s.b;
-        }
+    const int px = tx * TW + t % TW, py0 = ty * TH + t / TW, py1 = py0 + TH / kPX;
+    const bool in0 = px < k.W && py0 < k.H, in1 = px < k.W && py1 < k.H;
+    const int2 rg = ranges[gt];
+    const float fx = (float)px;
+    PixelFwd P0 = {(float)py0, 1.f, 0.f, 0.f, 0.f, 0, !in0};
+    PixelFwd P1 = {(float)py1, 1.f, 0.f, 0.f, 0.f, 0, !in1};
+    for (int base = rg.x; base < rg.y; base += k.batch) {
+        if (__syncthreads_and(P0.done && P1.done)) break;
+        const int cnt = min(k.batch, rg.y - base);
+        for (int e = t; e < cnt; e += NT) stage(rec, vals, base + e, k.n, s_g, s_c, s_b, nullptr, e);
         __syncthreads();
-        if (!done) {
-            const int cnt = min(NT, rg.y - base);
+        if (!(P0.done && P1.done)) {
             for (int j = 0; j < cnt; ++j) {
                 const float4 g = s_g[j];
                 const float4 c = s_c[j];
-                const float dx = __fsub_rn(fx, g.x), dy = __fsub_rn(fy, g.y);
-                const float p = eval_power2(g.z, g.w, c.x, dx, dy);
-                if (p > 0.f) continue;
-                const float og = __fmul_rn(c.y, ex2_approx(p));
-                const float al = fminf(k.amax, og);
-                if (al < k.at) continue;
-                const float tt = __fmul_rn(T, __fsub_rn(1.f, al));
-                if (tt < k.teps) {
-                    done = true;
-                    break;
-                }
-                const float w = al * T;
-                cr = fmaf(c.z, w, cr);
-                cg = fmaf(c.w, w, cg);
-                cb = fmaf(s_b[j], w, cb);
-                T = tt;
-                last = base + j - rg.x + 1;
+                const float cb = s_b[j];
+                const float dx = __fsub_rn(fx, g.x);
+                const int pos = base + j - rg.x;
+                if (!P0.done) blend(P0, dx, g, c, cb, pos, k);
+                if (!P1.done) blend(P1, dx, g, c, cb, pos, k);
+                if (P0.done && P1.done) break;
             }
         }
     }
-    if (inside) {
-        const int64_t pix = (int64_t)py * k.W + px, HW = (int64_t)k.W * k.H;
-        image[pix] = fmaf(T, k.bg0, cr);
-        image[HW + pix] = fmaf(T, k.bg1, cg);
-        image[2 * HW + pix] = fmaf(T, k.bg2, cb);
-        tfin[pix] = T;
-        ncon[pix] = last;
+    const int64_t HW = (int64_t)k.W * k.H;
+    float *img = image + (int64_t)v * 3 * HW;
+    if (in0) {
+        const int64_t pix = (int64_t)py0 * k.W + px;
+        img[pix] = fmaf(P0.T, k.bg0, P0.r);
+        img[HW + pix] = fmaf(P0.T, k.bg1, P0.g);
+        img[2 * HW + pix] = fmaf(P0.T, k.bg2, P0.b);
+        tfin[v * HW + pix] = P0.T;
+        ncon[v * HW + pix] = P0.last;
+    }
+    if (in1) {
+        const int64_t pix = (int64_t)py1 * k.W + px;
+        img[pix] = fmaf(P1.T, k.bg0, P1.r);
+        img[HW + pix] = fmaf(P1.T, k.bg1, P1.g);
+        img[2 * HW + pix] = fmaf(P1.T, k.bg2, P1.b);
+        tfin[v * HW + pix] = P1.T;
+        ncon[v * HW + pix] = P1.last;
+    }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / kPX) render_fwd_kernel(const float *__restrict__ rec,
+                                                                  const uint32_t *__restrict__ vals,
+                                                                  const int2 *__restrict__ ranges, Consts k,
+                                                                  float *__restrict__ image,
+                                                                  float *__restrict__ tfin, int *__restrict__ ncon,
+                                                                  Work w) {
+    __shared__ float4 s_g[kMaxBatch];  // mx, my, A, B
+    __shared__ float4 s_c[kMaxBatch];  // C, o, r, g
+    __shared__ float s_b[kMaxBatch];   // b
+    if (w.list == nullptr) {
+        fwd_tile<TW, TH>(blockIdx.x, rec, vals, ranges, k, image, tfin, ncon, s_g, s_c, s_b);
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(w.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= w.count) break;
+        fwd_tile<TW, TH>(w.list[item], rec, vals, ranges, k, image, tfin, ncon, s_g, s_c, s_b);
     }
 }
 
@@ -108,17 +174,17 @@ __device__ __forceinline__ float reduce_scatter8(const float *v, int lane) {
     const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
     float b[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float send = u16 ? v[k] : v[k + 4];
-        const float keep = u16 ? v[k + 4] : v[k];
-        b[k] = keep + __shfl_xor_sync(kFull, send, 16);
+    for (int q = 0; q < 4; ++q) {
+        const float send = u16 ? v[q] : v[q + 4];
+        const float keep = u16 ? v[q + 4] : v[q];
+        b[q] = keep + __shfl_xor_sync(kFull, send, 16);
     }
     float c[2];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float send = u8 ? b[k] : b[k + 2];
-        const float keep = u8 ? b[k + 2] : b[k];
-        c[k] = keep + __shfl_xor_sync(kFull, send, 8);
+    for (int q = 0; q < 2; ++q) {
+        const float send = u8 ? b[q] : b[q + 2];
+        const float keep = u8 ? b[q + 2] : b[q];
+        c[q] = keep + __shfl_xor_sync(kFull, send, 8);
     }
     float d = (u4 ? c[1] : c[0]) + __shfl_xor_sync(kFull, u4 ? c[0] : c[1], 4);
     d += __shfl_xor_sync(kFull, d, 2);
@@ -126,131 +192,171 @@ __device__ __forceinline__ float reduce_scatter8(const float *v, int lane) {
     return d;
 }
 
+struct PixelBwd {
+    float fy, T, g0, g1, g2, S0, S1, S2;
+    int last;
+};
+
+// Adds pixel P's partial gradients for the entry at list position pos (back to front) into v[9]:
+// v = [qx dp, qy dp, dp dx^2, dp dx dy, dp dy^2, dL/do, dL/dr, dL/dg, dL/db] in the base-2 form.
+__device__ __forceinline__ bool adjoint(PixelBwd &P, float dx, const float4 &g, const float4 &c, float cb, int pos,
+                                        const Consts &k, float *v) {
+    if (pos >= P.last) return false;
+    const float dy = __fsub_rn(P.fy, g.y);
+    const float p = eval_power2(g.z, g.w, c.x, dx, dy);
+    if (p > 0.f) return false;
+    const float G = ex2_approx(p);
+    const float og = __fmul_rn(c.y, G);
+    const float al = fminf(k.amax, og);
+    if (al < k.at) return false;
+    const float inv = __frcp_rn(1.f - al);
+    const float Ti = P.T * inv;
+    const float w = al * Ti;
+    v[6] = fmaf(P.g0, w, v[6]);
+    v[7] = fmaf(P.g1, w, v[7]);
+    v[8] = fmaf(P.g2, w, v[8]);
+    const float dal = P.g0 * (c.z * Ti - P.S0 * inv) + P.g1 * (c.w * Ti - P.S1 * inv) + P.g2 * (cb * Ti - P.S2 * inv);
+    P.S0 = fmaf(c.z, w, P.S0);
+    P.S1 = fmaf(c.w, w, P.S1);
+    P.S2 = fmaf(cb, w, P.S2);
+    P.T = Ti;
+    if (og < k.amax) {
+        const float dp = dal * al;  // dL/dpower (natural log units)
+        v[5] = fmaf(dal, G, v[5]);
+        v[0] = fmaf(dp, fmaf(2.f * g.z, dx, g.w * dy), v[0]);
+        v[1] = fmaf(dp, fmaf(g.w, dx, 2.f * c.x * dy), v[1]);
+        v[2] = fmaf(dp * dx, dx, v[2]);
+        v[3] = fmaf(dp * dx, dy, v[3]);
+        v[4] = fmaf(dp * dy, dy, v[4]);
+    }
+    return true;
+}
+
+__device__ __forceinline__ PixelBwd load_pixel_bwd(bool inside, float fy, int64_t pix, int64_t HW,
+                                                   const float *__restrict__ tfin, const int *__restrict__ ncon,
+                                                   const float *__restrict__ dimg, const Consts &k) {
+    PixelBwd P = {fy, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    if (inside) {
+        P.T = tfin[pix];
+        P.last = ncon[pix];
+        P.g0 = dimg[pix];
+        P.g1 = dimg[HW + pix];
+        P.g2 = dimg[2 * HW + pix];
+    }
+    P.S0 = P.T * k.bg0;
+    P.S1 = P.T * k.bg1;
+    P.S2 = P.T * k.bg2;
+    return P;
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) render_bwd_kernel(const float *__restrict__ rec,
-                                                            const uint32_t *__restrict__ vals,
-                                                            const int2 *__restrict__ ranges, Consts k,
-                                                            const float *__restrict__ tfin,
-                                                            const int *__restrict__ ncon,
-                                                            const float *__restrict__ dimg,
-                                                            float *__restrict__ d_rec) {
-    constexpr int NT = TW * TH;
-    constexpr int NW = NT / 32;
-    __shared__ float4 s_g[NT];
-    __shared__ float4 s_c[NT];
-    __shared__ float s_b[NT];
-    __shared__ uint32_t s_id[NT];
-    __shared__ float s_acc[9][NT];
-    __shared__ int s_wmax[NW];
-    const int tile = blockIdx.x;
+__device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, const uint32_t *__restrict__ vals,
+                                         const int2 *__restrict__ ranges, const Consts &k,
+                                         const float *__restrict__ tfin, const int *__restrict__ ncon,
+                                         const float *__restrict__ dimg, float *__restrict__ d_rec, float4 *s_g,
+                                         float4 *s_c, float *s_b, uint32_t *s_id, float (*s_acc)[kMaxBatch],
+                                         int *s_wmax) {
+    constexpr int NT = TW * TH / kPX;
+    constexpr int NW = NT / 32 > 0 ? NT / 32 : 1;
+    const int v = gt / k.T, tile = gt - v * k.T;
     const int tx = tile % k.Wt, ty = tile / k.Wt;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int px = tx * TW + (t % TW), py = ty * TH + (t / TW);
-    const bool inside = (px < k.W) && (py < k.H);
-    const int2 rg = ranges[tile];
-    const float fx = (float)px, fy = (float)py;
-    const int64_t pix = (int64_t)py * k.W + px, HW = (int64_t)k.W * k.H;
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    int last = 0;
-    if (inside) {
-        T = tfin[pix];
-        last = ncon[pix];
-        g0 = dimg[pix];
-        g1 = dimg[HW + pix];
-        g2 = dimg[2 * HW + pix];
-    }
-    float S0 = T * k.bg0, S1 = T * k.bg1, S2 = T * k.bg2;
-    const int wlast = __reduce_max_sync(kFull, last);
+    const int px = tx * TW + t % TW, py0 = ty * TH + t / TW, py1 = py0 + TH / kPX;
+    const bool in0 = px < k.W && py0 < k.H, in1 = px < k.W && py1 < k.H;
+    const int2 rg = ranges[gt];
+    const float fx = (float)px;
+    const int64_t HW = (int64_t)k.W * k.H;
+    const float *tf = tfin + v * HW;
+    const int *nc = ncon + v * HW;
+    const float *di = dimg + (int64_t)v * 3 * HW;
+    PixelBwd P0 = load_pixel_bwd(in0, (float)py0, (int64_t)py0 * k.W + px, HW, tf, nc, di, k);
+    PixelBwd P1 = load_pixel_bwd(in1, (float)py1, (int64_t)py1 * k.W + px, HW, tf, nc, di, k);
+    const int wlast = __reduce_max_sync(kFull, max(P0.last, P1.last));
     if (lane == 0) s_wmax[wid] = wlast;
     __syncthreads();
     int bmax = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) bmax = max(bmax, s_wmax[w]);
 
-    for (int end = rg.x + bmax; end > rg.x; end -= NT) {
-        const int start = max(rg.x, end - NT);
+    for (int end = rg.x + bmax; end > rg.x; end -= k.batch) {
+        const int start = max(rg.x, end - k.batch);
         const int cnt = end - start;
         __syncthreads();
-        if (t < cnt) {
-            const uint32_t id = __ldg(vals + start + t);
-            const Shade s = id < k.n ? load_shade(rec, id) : Shade{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            s_g[t] = make_float4(s.mx, s.my, s.A, s.B);
-            s_c[t] = make_float4(s.C, s.o, s.r, s.g);
-            s_b[t] = s.b;
-            s_id[t] = id;
+        for (int e = t; e < cnt; e += NT) {
+            stage(rec, vals, start + e, k.n, s_g, s_c, s_b, s_id, e);
 #pragma unroll
-            for (int c = 0; c < 9; ++c) s_acc[c][t] = 0.f;
+            for (int c = 0; c < 9; ++c) s_acc[c][e] = 0.f;
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const int pos = start + j - rg.x;
             if (pos >= wlast) continue;  // warp-uniform: no pixel of this warp reached the entry
-            float v[9];
+            float vv[9];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) v[c] = 0.f;
-            bool hit = false;
-            if (pos < last) {
-                const float4 g = s_g[j];
-                const float4 c = s_c[j];
-                const float dx = __fsub_rn(fx, g.x), dy = __fsub_rn(fy, g.y);
-                const float p = eval_power2(g.z, g.w, c.x, dx, dy);
-                if (p <= 0.f) {
-                    const float G = ex2_approx(p);
-                    const float og = __fmul_rn(c.y, G);
-                    const float al = fminf(k.amax, og);
-                    if (al >= k.at) {
-                        hit = true;
-                        const float cb = s_b[j];
-                        const float inv = __frcp_rn(1.f - al);
-                        const float Ti = T * inv;
-                        const float w = al * Ti;
-                        v[6] = g0 * w;
-                        v[7] = g1 * w;
-                        v[8] = g2 * w;
-                        const float dal = g0 * (c.z * Ti - S0 * inv) + g1 * (c.w * Ti - S1 * inv) +
-                                          g2 * (cb * Ti - S2 * inv);
-                        S0 = fmaf(c.z, w, S0);
-                        S1 = fmaf(c.w, w, S1);
-                        S2 = fmaf(cb, w, S2);
-                        T = Ti;
-                        if (og < k.amax) {
-                            const float dp = dal * al;  // dL/dpower (natural log units)
-                            v[5] = dal * G;
-                            v[0] = dp * fmaf(2.f * g.z, dx, g.w * dy);
-                            v[1] = dp * fmaf(g.w, dx, 2.f * c.x * dy);
-                            v[2] = dp * dx * dx;
-                            v[3] = dp * dx * dy;
-                            v[4] = dp * dy * dy;
-                        }
-                    }
-                }
-            }
+            for (int c = 0; c < 9; ++c) vv[c] = 0.f;
+            const float4 g = s_g[j];
+            const float4 c = s_c[j];
+            const float cb = s_b[j];
+            const float dx = __fsub_rn(fx, g.x);
+            bool hit = adjoint(P0, dx, g, c, cb, pos, k, vv);
+            hit |= adjoint(P1, dx, g, c, cb, pos, k, vv);
             if (__any_sync(kFull, hit)) {
-                // v[0..7]: transposed reduce-scatter (9 shuffles); afterwards lane l with l % 4 == 0
-                // holds the warp total of value l / 4.  v[8]: plain butterfly (5 shuffles).
-                const float s8 = warp_sum(v[8]);
-                const float r7 = reduce_scatter8(v, lane);
+                // vv[0..7]: transposed reduce-scatter (9 shuffles); afterwards lane l with l % 4 == 0
+                // holds the warp total of value l / 4.  vv[8]: plain butterfly (5 shuffles).
+                const float s8 = warp_sum(vv[8]);
+                const float r7 = reduce_scatter8(vv, lane);
                 if ((lane & 3) == 0) atomicAdd(&s_acc[lane >> 2][j], r7);
                 if (lane == 0) atomicAdd(&s_acc[8][j], s8);
             }
         }
         __syncthreads();
-        if (t < cnt) {
+        for (int e = t; e < cnt; e += NT) {
             float a[9];
             bool any = false;
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
-                a[c] = s_acc[c][t];
+                a[c] = s_acc[c][e];
                 any |= (a[c] != 0.f);
             }
-            if (any && s_id[t] < k.n) {
+            if (any && s_id[e] < k.n) {
                 // record layout: [dmx, dmy, dc00, dc01] [dc11, do, dr, dg] [db, 0, 0, 0]; vector atomics
-                float4 *d = reinterpret_cast<float4 *>(d_rec + (size_t)s_id[t] * XPR_REC_FLOATS);
+                float4 *d = reinterpret_cast<float4 *>(d_rec + (size_t)s_id[e] * XPR_REC_FLOATS);
                 atomicAdd(d, make_float4(-kLn2 * a[0], -kLn2 * a[1], -0.5f * a[2], -a[3]));
                 atomicAdd(d + 1, make_float4(-0.5f * a[4], a[5], a[6], a[7]));
                 atomicAdd(reinterpret_cast<float *>(d + 2), a[8]);
             }
         }
+    }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / kPX) render_bwd_kernel(const float *__restrict__ rec,
+                                                                  const uint32_t *__restrict__ vals,
+                                                                  const int2 *__restrict__ ranges, Consts k,
+                                                                  const float *__restrict__ tfin,
+                                                                  const int *__restrict__ ncon,
+                                                                  const float *__restrict__ dimg,
+                                                                  float *__restrict__ d_rec, Work w) {
+    __shared__ float4 s_g[kMaxBatch];
+    __shared__ float4 s_c[kMaxBatch];
+    __shared__ float s_b[kMaxBatch];
+    __shared__ uint32_t s_id[kMaxBatch];
+    __shared__ float s_acc[9][kMaxBatch];
+    __shared__ int s_wmax[8];
+    if (w.list == nullptr) {
+        bwd_tile<TW, TH>(blockIdx.x, rec, vals, ranges, k, tfin, ncon, dimg, d_rec, s_g, s_c, s_b, s_id, s_acc,
+                         s_wmax);
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();  // the previous tile's last reads of shared memory are done
+        if (threadIdx.x == 0) s_item = atomicAdd(w.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= w.count) break;
+        bwd_tile<TW, TH>(w.list[item], rec, vals, ranges, k, tfin, ncon, dimg, d_rec, s_g, s_c, s_b, s_id, s_acc,
+                         s_wmax);
     }
 }
 
@@ -260,6 +366,8 @@ Consts make_consts(const XprCamera &cam, const XprConfig &cfg, int64_t n) {
     k.W = cam.width;
     k.H = cam.height;
     k.Wt = tiles_x(cam, cfg);
+    k.T = tiles_x(cam, cfg) * tiles_y(cam, cfg);
+    k.batch = cfg.batch_depth > 0 ? min(cfg.batch_depth, kMaxBatch) : kMaxBatch;
     k.at = cfg.alpha_thresh;
     k.amax = cfg.alpha_max;
     k.teps = cfg.t_eps;
@@ -269,37 +377,75 @@ Consts make_consts(const XprCamera &cam, const XprConfig &cfg, int64_t n) {
     return k;
 }
 
+template <typename KernelT>
+int persistent_grid(KernelT kernel, int threads, int items) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return items;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return items;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return max(1, min(items, sms * per_sm));
+}
+
 }  // namespace
 
-#define XPR_TILE_DISPATCH(TWV, THV, CALL)                                                  \
-    if (cfg.tile_w == 16 && cfg.tile_h == 16) { constexpr int TWV = 16, THV = 16; CALL; }  \
-    else if (cfg.tile_w == 8 && cfg.tile_h == 8) { constexpr int TWV = 8, THV = 8; CALL; } \
-    else if (cfg.tile_w == 16 && cfg.tile_h == 8) { constexpr int TWV = 16, THV = 8; CALL; } \
-    else { constexpr int TWV = 8, THV = 16; CALL; }
+#define XPR_TILE_DISPATCH(TWV, THV, ...)                                                         \
+    if (cfg.tile_w == 16 && cfg.tile_h == 16) { constexpr int TWV = 16, THV = 16; __VA_ARGS__; }  \
+    else if (cfg.tile_w == 8 && cfg.tile_h == 8) { constexpr int TWV = 8, THV = 8; __VA_ARGS__; } \
+    else if (cfg.tile_w == 16 && cfg.tile_h == 8) { constexpr int TWV = 16, THV = 8; __VA_ARGS__; } \
+    else { constexpr int TWV = 8, THV = 16; __VA_ARGS__; }
+
+// worklist/counter NULL: one block per tile over n_views * T tiles.  Otherwise a persistent grid
+// walks worklist[0 .. n_views * T); *counter is zeroed here.
+int launch_render_fwd_views(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
+                            const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final,
+                            int32_t *n_contrib, const int32_t *worklist, int32_t *counter, cudaStream_t st) {
+    const Consts k = make_consts(cam, cfg, n);
+    const int items = n_views * k.T;
+    if (items == 0) return XPR_OK;
+    const int2 *rg = reinterpret_cast<const int2 *>(ranges);
+    Work w = {worklist, counter, items};
+    if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
+    XPR_TILE_DISPATCH(TW, TH, {
+        const int threads = TW * TH / kPX;
+        const int grid = worklist ? persistent_grid(render_fwd_kernel<TW, TH>, threads, items) : items;
+        render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, image, t_final, n_contrib, w);
+    });
+    XPR_LAUNCH_CHECK("render_fwd_kernel");
+    return XPR_OK;
+}
+
+int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_t *ranges, int n_views,
+                            const XprCamera &cam, const XprConfig &cfg, const float *t_final,
+                            const int32_t *n_contrib, const float *d_image, float *d_rec, int64_t n,
+                            const int32_t *worklist, int32_t *counter, cudaStream_t st) {
+    XPR_CUDA_TRY(cudaMemsetAsync(d_rec, 0, (size_t)n * XPR_REC_FLOATS * sizeof(float), st));
+    const Consts k = make_consts(cam, cfg, n);
+    const int items = n_views * k.T;
+    if (items == 0) return XPR_OK;
+    const int2 *rg = reinterpret_cast<const int2 *>(ranges);
+    Work w = {worklist, counter, items};
+    if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
+    XPR_TILE_DISPATCH(TW, TH, {
+        const int threads = TW * TH / kPX;
+        const int grid = worklist ? persistent_grid(render_bwd_kernel<TW, TH>, threads, items) : items;
+        render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, t_final, n_contrib, d_image, d_rec, w);
+    });
+    XPR_LAUNCH_CHECK("render_bwd_kernel");
+    return XPR_OK;
+}
 
 int launch_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges,
                       const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final, int32_t *n_contrib,
                       cudaStream_t st) {
-    const Consts k = make_consts(cam, cfg, n);
-    const unsigned nt = (unsigned)(tiles_x(cam, cfg) * tiles_y(cam, cfg));
-    const int2 *rg = reinterpret_cast<const int2 *>(ranges);
-    XPR_TILE_DISPATCH(TW, TH, (render_fwd_kernel<TW, TH><<<nt, TW * TH, 0, st>>>(rec, vals, rg, k, image, t_final,
-                                                                                   n_contrib)));
-    XPR_LAUNCH_CHECK("render_fwd_kernel");
-    return XPR_OK;
+    return launch_render_fwd_views(rec, n, vals, ranges, 1, cam, cfg, image, t_final, n_contrib, nullptr, nullptr, st);
 }
 
 int launch_render_bwd(const float *rec, const uint32_t *vals, const int32_t *ranges, const XprCamera &cam,
                       const XprConfig &cfg, const float *t_final, const int32_t *n_contrib, const float *d_image,
                       float *d_rec, int64_t n, cudaStream_t st) {
-    XPR_CUDA_TRY(cudaMemsetAsync(d_rec, 0, (size_t)n * XPR_REC_FLOATS * sizeof(float), st));
-    const Consts k = make_consts(cam, cfg, n);
-    const unsigned nt = (unsigned)(tiles_x(cam, cfg) * tiles_y(cam, cfg));
-    const int2 *rg = reinterpret_cast<const int2 *>(ranges);
-    XPR_TILE_DISPATCH(TW, TH, (render_bwd_kernel<TW, TH><<<nt, TW * TH, 0, st>>>(rec, vals, rg, k, t_final, n_contrib,
-                                                                                   d_image, d_rec)));
-    XPR_LAUNCH_CHECK("render_bwd_kernel");
-    return XPR_OK;
+    return launch_render_bwd_views(rec, vals, ranges, 1, cam, cfg, t_final, n_contrib, d_image, d_rec, n, nullptr,
+                                   nullptr, st);
 }
 
 }  // namespace xpr

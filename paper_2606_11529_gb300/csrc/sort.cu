@@ -224,7 +224,41 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
     return XPR_OK;
 }
 
+// key = UINT32_MAX - list length: ascending keys = descending lengths (ties keep tile order)
+__global__ void worklist_keys_kernel(const int2 *__restrict__ ranges, int n_tiles, uint32_t *__restrict__ keys,
+                                     uint32_t *__restrict__ vals) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const int2 r = ranges[t];
+    keys[t] = 0xffffffffu - (uint32_t)(r.y - r.x);
+    vals[t] = (uint32_t)t;
+}
+
 }  // namespace
+
+size_t worklist_workspace_bytes(int32_t n_tiles) {
+    const size_t a = align256((size_t)n_tiles * 4);
+    return 3 * a + 256 + workspace_bytes<uint32_t>(n_tiles);
+}
+
+int launch_tile_worklist(const int32_t *ranges, int32_t n_tiles, int32_t *worklist, void *ws, size_t ws_bytes,
+                         cudaStream_t st) {
+    if (n_tiles <= 0) return XPR_OK;
+    if (ws_bytes < worklist_workspace_bytes(n_tiles))
+        return fail(XPR_ERR_INVALID, "xpr_tile_worklist: workspace %zu < %zu bytes", ws_bytes,
+                    worklist_workspace_bytes(n_tiles));
+    const size_t a = align256((size_t)n_tiles * 4);
+    char *p = reinterpret_cast<char *>(ws);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(p);
+    uint32_t *keys_sorted = reinterpret_cast<uint32_t *>(p + a);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
+    int32_t *dummy_ranges = reinterpret_cast<int32_t *>(p + 3 * a);
+    worklist_keys_kernel<<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(reinterpret_cast<const int2 *>(ranges),
+                                                                            n_tiles, keys, vals);
+    XPR_LAUNCH_CHECK("worklist_keys_kernel");
+    return radix_sort<uint32_t>(keys, vals, n_tiles, 1, 0, 32, keys_sorted, reinterpret_cast<uint32_t *>(worklist),
+                                dummy_ranges, p + 3 * a + 256, workspace_bytes<uint32_t>(n_tiles), st);
+}
 
 size_t sort_workspace_bytes(int64_t n, int32_t n_tiles) {
     (void)n_tiles;

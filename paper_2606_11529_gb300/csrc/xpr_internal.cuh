@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/xpr.h"
 
@@ -37,10 +38,27 @@ __host__ __device__ inline int tiles_y(const XprCamera &c, const XprConfig &g) {
 int validate_camera_config(const XprCamera *cam, const XprConfig *cfg);
 
 // ---- launch helpers implemented per translation unit -------------------------------------
+constexpr int kMaxViews = 16;  // views per multi-view launch (cameras travel as a kernel argument)
+
 int launch_project_fwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg, float *rec,
                        int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st);
 int launch_project_bwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg,
                        const float *d_rec, const XprPrimsGrad &g, cudaStream_t st);
+int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
+                             float *rec, int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st);
+int launch_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
+                             const float *d_rec, const XprPrimsGrad &g, cudaStream_t st);
+int launch_render_fwd_views(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
+                            const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final,
+                            int32_t *n_contrib, const int32_t *worklist, int32_t *counter, cudaStream_t st);
+int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_t *ranges, int n_views,
+                            const XprCamera &cam, const XprConfig &cfg, const float *t_final,
+                            const int32_t *n_contrib, const float *d_image, float *d_rec, int64_t n,
+                            const int32_t *worklist, int32_t *counter, cudaStream_t st);
+// tiles sorted by descending list length (ranges[t,1] - ranges[t,0]), for persistent scheduling
+size_t worklist_workspace_bytes(int32_t n_tiles);
+int launch_tile_worklist(const int32_t *ranges, int32_t n_tiles, int32_t *worklist, void *ws, size_t ws_bytes,
+                         cudaStream_t st);
 
 // Device-wide exclusive scan of int32 counts: out[j] = sum_{k<j} item(k), out[n] = total, where
 // item(k) = in[gather[k]] if gather is non-NULL, else in[k] (then in == out is allowed).
@@ -54,10 +72,10 @@ int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, c
                      const XprCamera &cam, const XprConfig &cfg, int32_t *counts, cudaStream_t st);
 int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                     const XprCamera &cam, const XprConfig &cfg, const int32_t *offsets, uint64_t *keys,
-                    uint32_t *tiles, uint32_t *vals, cudaStream_t st);
+                    uint32_t *tiles, uint32_t *vals, cudaStream_t st, int64_t per_view = 0);
 size_t depth_order_workspace_bytes(int64_t n);
 int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
-                       cudaStream_t st);
+                       cudaStream_t st, int64_t per_view = 0, int n_views = 1);
 
 size_t sort_workspace_bytes(int64_t n, int32_t n_tiles);
 int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
