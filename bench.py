@@ -167,6 +167,112 @@ def cpu_baseline_leg():
     return {"value": 1000.0 * est, "unit": UNIT, "cores": baseline.threads(), "kind": "oracle", "sample": desc}
 
 
+def _median_ms(fn, reps, flush=None):
+    import torch
+    times = []
+    for k in range(reps):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e))
+    return statistics.median(times)
+
+
+def batched_leg(dev, reps, flush):
+    """Batched form: 3M uniform Gaussians seen by 8 pinhole cameras (1600x1064, focal 800, yaw
+    -15..+15 degrees), forward + backward of all 8 views; one batched pass (autotuned tile size and
+    batch depth, persistent render grids) against 8 plain single-view passes."""
+    import numpy as np
+    import torch
+    from paper_2606_11529_gb300 import batched as BT
+    from paper_2606_11529_gb300 import render as R
+    from paper_2606_11529_gb300 import scenes
+    sc = scenes.uniform_scene(3_000_000, seed=0)
+    cams = scenes.multiview_cameras(8, 1600, 1064, 800.0, seed=0)
+    base = scenes.RenderConfig(sh_degree=0)
+    P = [t.to(dev) for t in R.scene_to_device(sc)]
+    w = torch.from_numpy(np.random.default_rng(2).normal(size=(8, 3, 1064, 1600)).astype(np.float32)).to(dev)
+    best, table = BT.autotune(P, cams, base, scene_id="uniform-3M", reps=5)
+    Pg = [p.detach().requires_grad_(True) for p in P]
+    ws = BT.ViewsWorkspace()
+
+    def batched():
+        for p in Pg:
+            p.grad = None
+        (BT.render_views(*Pg, cams, best, ws) * w).sum().backward()
+
+    wss = [R.Workspace() for _ in cams]
+
+    def plain():
+        for p in Pg:
+            p.grad = None
+        for v, cam in enumerate(cams):
+            (R.render(*Pg, cam, base, wss[v]) * w[v]).sum().backward()
+
+    for _ in range(3):
+        batched()
+        plain()
+    torch.cuda.synchronize()
+    tb = _median_ms(batched, reps, flush)
+    tp = _median_ms(plain, reps, flush)
+    fr = BT.forward_views(*P, cams, best, BT.ViewsWorkspace())
+    return {"workload": "3M uniform SH-0 Gaussians (xy U[-1,1], z U[2,6]), 8 pinhole views 1600x1064 f=800, "
+                        "yaw -15..+15 deg, fwd+bwd of all 8 views, seed 0",
+            "ms_batched": round(tb, 3), "ms_plain_8x": round(tp, 3), "speedup": round(tp / tb, 3),
+            "intersections": fr.n_isect, "tile": [best.tile_w, best.tile_h], "batch_depth": best.batch_depth,
+            "autotune_ms": {f"{k[0]}x{k[1]}/b{k[2]}": (round(v, 3) if v != float("inf") else None)
+                            for k, v in table.items()},
+            "timing": f"median of {reps} (L2 flushed before each)"}
+
+
+def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
+    """Serving form: 16 resident clustered SH-3 scenes (sizes log-uniform in [1e5, 3e6]), Poisson
+    arrivals at 200 requests/s, sizes 512x512 / 1280x720 / 1920x1080; the continuous-batching server
+    against the plain one-at-a-time queue on the same trace, then the server under a small pool."""
+    import torch
+    from paper_2606_11529_gb300 import render as R
+    from paper_2606_11529_gb300 import scenes
+    from paper_2606_11529_gb300 import serve as SV
+    t0 = time.perf_counter()
+    resident = [tuple(t.to(dev) for t in R.scene_to_device(s))
+                for s in scenes.serving_scenes(16, seed=0, scale_down=scale_down)]
+    gen_s = time.perf_counter() - t0
+    cfg = scenes.RenderConfig(sh_degree=3)
+    free, _ = torch.cuda.mem_get_info(dev)
+    pool = int(max(free - (16 << 30), 8 << 30))
+    srv = SV.Server(resident, cfg, pool_bytes=pool, slots=3)
+    srv.calibrate()
+    # warm every (scene, size) once so lazy module loading and allocator growth stay outside
+    SV.run_plain(resident, cfg, SV.make_trace(48, rate_hz=1e6, seed=99), srv)
+    trace = SV.make_trace(n_requests + warmup, rate_hz=200.0, seed=0)
+    srv.run(trace)
+    ours = SV.latency_stats(trace, warmup)
+    ours["pool_peak_gb"] = round(srv.budget.peak / 2 ** 30, 3)
+    ptrace = SV.make_trace(n_requests + warmup, rate_hz=200.0, seed=0)
+    SV.run_plain(resident, cfg, ptrace, srv)
+    plain = SV.latency_stats(ptrace, warmup)
+    n_cap = max(n_requests // 4, 100)
+    capped = SV.Server(resident, cfg, pool_bytes=int(cap_gb * 2 ** 30), slots=3)
+    capped.calib = srv.calib
+    ctrace = SV.make_trace(n_cap + warmup // 4, rate_hz=200.0, seed=1)
+    capped.run(ctrace)
+    cst = SV.latency_stats(ctrace, warmup // 4)
+    cst["pool_gb"], cst["pool_peak_gb"] = cap_gb, round(capped.budget.peak / 2 ** 30, 3)
+    scene_prims = [int(s[0].shape[0]) for s in resident]
+    return {"workload": f"16 resident clustered SH-3 scenes ({sum(scene_prims)} Gaussians, "
+                        f"{min(scene_prims)}-{max(scene_prims)} per scene), Poisson 200 req/s, "
+                        "512x512 / 1280x720 / 1920x1080 (f = width), forward only, image delivered to pinned host",
+            "requests": n_requests, "warmup_requests": warmup, "slots": 3,
+            "p50_ms": ours["p50_ms"], "p99_ms": ours["p99_ms"], "views_per_s": ours["views_per_s"],
+            "server": ours, "plain_queue": plain, "capped_pool": cst,
+            "resident_gb": round(sum(sum(t.numel() * 4 for t in s) for s in resident) / 2 ** 30, 3),
+            "scene_gen_s": round(gen_s, 1)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +281,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=1_000_000, help="primitive count (default: the headline 1M)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 8-view batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-cap-gb", type=float, default=4.0)
+    ap.add_argument("--serve-scale-down", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -256,6 +368,9 @@ def main():
     work = {
         "project": ("hbm", n * (PARAM_BYTES + REC_BYTES + 16 + 4)),
         "depth_order": ("hbm", n * (4 + 4 + 4) + 4 * n * 24),  # key build + 4 passes over 12-byte pairs
+        # fused bin + sort: read order, box, tile count and record per primitive; write one u32 per
+        # kept pair and one [start, end) per tile
+        "bin_sort": ("hbm", n * (4 + 16 + 4 + REC_BYTES) + I * 4 + fr.ranges.shape[0] * 8),
         "tile_bin": ("hbm", n * 2 * (REC_BYTES + 16 + 4) + n * 4 + I * 12),
         "sort": ("hbm", passes * 24 * I),
         "render_fwd": ("alu", pairs * FWD_OPS_PER_PAIR),
@@ -305,6 +420,24 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    del fr
+    # the same step with the fused bin + sort (xpr_bin_sorted in place of xpr_tile_bin + xpr_sort_tiles)
+    ws_key = R.Workspace(fused=True)
+
+    def key_step():
+        for p in P:
+            p.grad = None
+        (R.render(*P, cam, cfg, ws_key) * w).sum().backward()
+
+    for _ in range(3):
+        key_step()
+    key_ms = _median_ms(key_step, args.steps, flush)
+    batched = None if args.no_batched else batched_leg(dev, max(args.steps // 2, 5), flush)
+    serve = None
+    if not args.no_serve:
+        torch.cuda.empty_cache()
+        serve = serve_leg(dev, args.serve_requests, args.serve_warmup, args.serve_cap_gb, args.serve_scale_down)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg()
@@ -317,10 +450,13 @@ def main():
             "config": {"workload": WORKLOAD, "primitives": n, "resolution": [cam.width, cam.height],
                        "tile": [cfg.tile_w, cfg.tile_h], "intersections": I, "pairs_blended": pairs,
                        "views_per_s_total": round(world * 1000.0 / ms, 2),
+                       "fused_bin_sort_path_ms": round(key_ms, 4),
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
             "stages": stages,
+            "batched": batched,
+            "serve": serve,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": launches,

@@ -18,7 +18,7 @@
  *     of launched kernels.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *     enqueued asynchronously on it; entry points that must return a count to
- *     the host (xpr_tile_bin) synchronise that stream.
+ *     the host (xpr_tile_bin, xpr_bin_sorted) synchronise that stream.
  *   - Floating-point arrays are IEEE float32, row-major, densely packed.
  *   - Return value: an XprStatus.  On error nothing is guaranteed about the
  *     output buffers; xpr_last_error() describes the failure.
@@ -195,6 +195,9 @@ int xpr_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n_isect, 
  * u32 tile ids (xpr_tile_bin's `tiles` output) instead of u64 keys; with pairs
  * emitted in xpr_depth_order order the result is the (tile, depth) order of
  * Sec. 4.2 while moving 8 instead of 12 bytes per pair and pass.
+ * tiles_out may be NULL when only vals_out and ranges are wanted: the last
+ * pass then writes no tile ids, and with more than two 8-bit passes
+ * (n_tiles > 65536) tiles_in is overwritten (used as the second key buffer).
  * tiles_in/vals_in must not alias tiles_out/vals_out.  workspace:
  * >= xpr_sort_tiles_workspace(n_isect, n_tiles) bytes, 256-byte aligned. */
 size_t xpr_sort_tiles_workspace(int64_t n_isect, int32_t n_tiles);
@@ -276,6 +279,35 @@ int xpr_render_bwd_views(const float *rec, int64_t n, int32_t n_views, const uin
                          void *stream); /* d_rec[V*n,12] overwritten */
 int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
                           const XprConfig *cfg, const float *d_rec, const XprPrimsGrad *d_prims, void *stream);
+
+/* ---- Fused bin + sort ---------------------------------------------------------
+ * xpr_bin_sorted: Sec. 4.2's replicate / assign tile id / cull followed by
+ * "sort and identify bounds", with no key array: it writes the sorted record
+ * indices and the tile segments directly.  The result is bit-identical to
+ * xpr_tile_bin (in the same emission order) followed by xpr_sort_tiles: the
+ * same kept pairs (same FP32 cull), each tile's list in emission order.
+ *   rec, bbox, tile_count: from xpr_project (_views), n records per view;
+ *   order[V*n]: the emission order, from xpr_depth_order (_views) (record
+ *     indices, view-major);
+ *   ranges[V*T,2] (int32, device): OVERWRITTEN, tile t of view v at v*T + t,
+ *     [0, 0) for a tile with no pairs (as xpr_sort_tiles);
+ *   vals[capacity] (u32, device): record indices, tile-major, in emission order
+ *     within a tile;
+ *   *n_isect (HOST): the number of kept pairs I.  If I > capacity the call
+ *     returns XPR_ERR_CAPACITY without writing vals (ranges are already valid
+ *     for I pairs); call again with capacity >= I.
+ * The call synchronises the stream once (to read I).  It does a counting pass,
+ * a prefix over a (chunk x tile) count matrix and a writing pass; every tile's
+ * segment is [start, end) of vals.  Tile rows are walked in bands of
+ * BR = max(1, min(8, 2048 / tiles_x)) rows; grids with more than 6400 tile
+ * columns or more than 2048 bands over all views are rejected with
+ * XPR_ERR_INVALID (use xpr_tile_bin + xpr_sort_tiles for them).  workspace
+ * (device, 256-byte aligned, caller-owned): xpr_bin_sorted_workspace(n, V,
+ * cam, cfg) bytes, 0 for invalid arguments. */
+size_t xpr_bin_sorted_workspace(int64_t n, int32_t n_views, const XprCamera *cam, const XprConfig *cfg);
+int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
+                   int32_t n_views, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges, uint32_t *vals,
+                   int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
 
 /* ---- Misc ------------------------------------------------------------------ */
 const char *xpr_status_string(int status);

@@ -18,6 +18,7 @@ scene, resolution).
 from __future__ import annotations
 
 import dataclasses
+import math
 import statistics
 
 import torch
@@ -55,7 +56,7 @@ class ViewsWorkspace:
 
 
 def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | None = None, persistent=True,
-                  stream=None) -> ViewsFrame:
+                  stream=None, fused=False) -> ViewsFrame:
     L = B.load()
     ws = ws or ViewsWorkspace()
     n, V = mu.shape[0], len(cams)
@@ -65,18 +66,25 @@ def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | 
         if (c.width, c.height) != (cam0.width, cam0.height):
             raise ValueError("all views of one batch must share the image size")
     ccfg = B.make_config(cfg)
-    rec, bbox, tc, cnt = B.xpr_project_views(mu, scale, quat, opacity, sh, cams, ccfg, stream=stream)
+    fused = fused and B.binsort_ok(cam0, cfg, V)
+    rec, bbox, tc, cnt = B.xpr_project_views(mu, scale, quat, opacity, sh, cams, ccfg, stream=stream,
+                                             with_isect_count=not fused)
     order = B.xpr_depth_order_views(rec, tc, n, V, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(n * V),
                                                                          dev), stream=stream)
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
-    _, tiles, vals, I = B.xpr_tile_bin_views(rec, bbox, tc, cnt, order, n, V, cam0, ccfg, capacity=cap,
-                                             workspace=ws.scratch("bin", L.xpr_tile_bin_workspace(n * V), dev),
-                                             stream=stream)
-    ws.last_isect = I
     Wt, Ht = B.tiles_of(cam0, cfg)
     nt = V * Wt * Ht
-    _, vs, ranges = B.xpr_sort_tiles(tiles, vals, nt, workspace=ws.scratch("sort", L.xpr_sort_tiles_workspace(I, nt),
-                                                                             dev), stream=stream)
+    if fused:
+        ranges, vs, I = B.xpr_bin_sorted(rec, bbox, tc, order, n, cam0, ccfg, n_views=V, capacity=cap,
+                                         workspace=ws.scratch("binsort", B.bin_sorted_workspace_bytes(
+                                             n, V, cam0, ccfg), dev), stream=stream)
+    else:
+        _, tiles, vals, I = B.xpr_tile_bin_views(rec, bbox, tc, cnt, order, n, V, cam0, ccfg, capacity=cap,
+                                                 workspace=ws.scratch("bin", L.xpr_tile_bin_workspace(n * V), dev),
+                                                 stream=stream)
+        _, vs, ranges = B.xpr_sort_tiles(tiles, vals, nt, workspace=ws.scratch(
+            "sort", L.xpr_sort_tiles_workspace(I, nt), dev), stream=stream, want_tiles=False)
+    ws.last_isect = I
     wl = B.xpr_tile_worklist(ranges, workspace=ws.scratch("wl", L.xpr_tile_worklist_workspace(nt), dev),
                              stream=stream) if persistent else None
     image, tfin, ncon = B.xpr_render_fwd_views(rec, n, V, vs, ranges, cam0, ccfg, worklist=wl, stream=stream)
@@ -132,7 +140,8 @@ def _time_ms(fn, reps):
 def autotune(params, cams, cfg, scene_id="scene", backward=True, reps=5, tiles=TILE_CANDIDATES,
              batches=BATCH_CANDIDATES):
     """Returns (best_cfg, table) where table maps (tile_w, tile_h, batch) -> median ms of one batched
-    forward (+ backward) over all `cams`.  Results are cached per (device, scene_id, resolution)."""
+    forward (+ backward) over all `cams` (inf where the batch has more than 2^31 - 1 pairs).
+    Results are cached per (device, scene_id, resolution)."""
     key = (torch.cuda.get_device_name(), scene_id, cams[0].width, cams[0].height, len(cams), backward)
     if key in _CACHE:
         return _CACHE[key]
@@ -149,7 +158,13 @@ def autotune(params, cams, cfg, scene_id="scene", backward=True, reps=5, tiles=T
                 if backward:
                     img.backward(d_img if d_img is not None else torch.ones_like(img))
 
-            run()  # warm-up (and capacity sizing)
+            try:
+                run()  # warm-up (and capacity sizing)
+            except B.XprError as e:
+                if e.status != B.XPR_ERR_CAPACITY:
+                    raise
+                table[(tw, th, bd)] = math.inf  # more than 2^31 - 1 pairs: this tile size does not fit
+                continue
             table[(tw, th, bd)] = _time_ms(run, reps)
     best = min(table, key=table.get)
     out = (dataclasses.replace(cfg, tile_w=best[0], tile_h=best[1], batch_depth=best[2]), table)

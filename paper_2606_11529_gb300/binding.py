@@ -78,6 +78,10 @@ SIGNATURES = {
                                      ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "xpr_project_bwd_views": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), c_i32,
                                       ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_bin_sorted_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig)]),
+    "xpr_bin_sorted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(XprCamera),
+                               ctypes.POINTER(XprConfig), c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz,
+                               c_vp]),
     "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
@@ -241,11 +245,17 @@ def xpr_tile_bin(rec, bbox, tile_count, cam, cfg, capacity=None, offsets=None, k
     raise XprError(XPR_ERR_CAPACITY, "xpr_tile_bin", "capacity retry failed")
 
 
-def xpr_sort_tiles(tiles, vals, n_tiles, tiles_out=None, vals_out=None, ranges=None, workspace=None, stream=None):
+def xpr_sort_tiles(tiles, vals, n_tiles, tiles_out=None, vals_out=None, ranges=None, workspace=None, stream=None,
+                   want_tiles=True):
+    """Returns (tiles_sorted or None, vals_sorted, ranges).  want_tiles=False skips writing the
+    sorted tile ids (and lets the sort use `tiles` as scratch when it needs more than 2 passes)."""
     L = load()
     n = tiles.numel()
     dev = tiles.device
-    tiles_out = torch.empty_like(tiles) if tiles_out is None else tiles_out
+    if want_tiles:
+        tiles_out = torch.empty_like(tiles) if tiles_out is None else tiles_out
+    else:
+        tiles_out = None
     vals_out = torch.empty_like(vals) if vals_out is None else vals_out
     ranges = torch.empty((n_tiles, 2), dtype=torch.int32, device=dev) if ranges is None else ranges
     need = int(L.xpr_sort_tiles_workspace(n, n_tiles))
@@ -327,15 +337,16 @@ def camera_array(cams):
     return arr
 
 
-def xpr_project_views(mu, scale, quat, opacity, sh, cams, cfg, stream=None):
-    """Returns rec[V*n,12], bbox[V*n,4], tile_count[V*n], isect_count[V*n] (view-major)."""
+def xpr_project_views(mu, scale, quat, opacity, sh, cams, cfg, stream=None, with_isect_count=True):
+    """Returns rec[V*n,12], bbox[V*n,4], tile_count[V*n], isect_count[V*n] (view-major; None when
+    not asked for)."""
     L = load()
     n, V = mu.shape[0], len(cams)
     dev = mu.device
     rec = torch.empty((V * n, REC), dtype=torch.float32, device=dev)
     bbox = torch.empty((V * n, 4), dtype=torch.int32, device=dev)
     tc = torch.empty(V * n, dtype=torch.int32, device=dev)
-    cnt = torch.empty(V * n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(V * n, dtype=torch.int32, device=dev) if with_isect_count else None
     p = _prims(mu, scale, quat, opacity, sh)
     g = _as_c(cfg, XprConfig)
     _check(L.xpr_project_views(ctypes.byref(p), n, camera_array(cams), V, ctypes.byref(g), _ptr(rec), _ptr(bbox),
@@ -382,6 +393,48 @@ def xpr_tile_bin_views(rec, bbox, tile_count, isect_count, order, n, n_views, ca
         I = int(got.value)
         return offsets, tiles[:I], vals[:I], I
     raise XprError(XPR_ERR_CAPACITY, "xpr_tile_bin_views", "capacity retry failed")
+
+
+def binsort_ok(cam, cfg, n_views=1):
+    """Whether xpr_bin_sorted takes this grid: at most 6400 tile columns (its per-band counters)
+    and at most 2048 bands of 8 (or 2048 // columns) tile rows over all views."""
+    Wt, Ht = tiles_of(cam, cfg)
+    br = max(1, min(8, 2048 // Wt))
+    return Wt <= 6400 and Ht < 32768 and n_views * ((Ht + br - 1) // br) <= 2048
+
+
+def bin_sorted_workspace_bytes(n, n_views, cam, cfg):
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    return int(load().xpr_bin_sorted_workspace(n, n_views, ctypes.byref(c), ctypes.byref(g)))
+
+
+def xpr_bin_sorted(rec, bbox, tile_count, order, n, cam, cfg, n_views=1, capacity=None, workspace=None,
+                   stream=None):
+    """Fused bin + sort: returns (ranges[V*T,2], vals[I] (record indices, int32 storage), I).
+    ``capacity``: initial size of vals; on XPR_ERR_CAPACITY it is re-allocated to I and the call
+    repeated."""
+    L = load()
+    dev = rec.device
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    Wt, Ht = tiles_of(cam, cfg)
+    ranges = torch.empty((n_views * Wt * Ht, 2), dtype=torch.int32, device=dev)
+    need = int(L.xpr_bin_sorted_workspace(n, n_views, ctypes.byref(c), ctypes.byref(g)))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    cap = int(capacity) if capacity is not None else max(4 * n * n_views, 1024)
+    vals = torch.empty(cap, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        got = c_i64(0)
+        s = L.xpr_bin_sorted(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(order), n, n_views, ctypes.byref(c),
+                             ctypes.byref(g), _ptr(ranges), _ptr(vals), vals.numel(), ctypes.byref(got),
+                             _ptr(workspace), workspace.numel(), _stream(stream))
+        if s == XPR_ERR_CAPACITY and got.value <= 0x7FFFFFFF:
+            vals = torch.empty(max(got.value, 1), dtype=torch.int32, device=dev)
+            continue
+        _check(s, "xpr_bin_sorted")
+        I = int(got.value)
+        return ranges, vals[:I], I
+    raise XprError(XPR_ERR_CAPACITY, "xpr_bin_sorted", "capacity retry failed")
 
 
 def xpr_tile_worklist(ranges, workspace=None, stream=None):

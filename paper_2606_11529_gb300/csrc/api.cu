@@ -165,7 +165,7 @@ int xpr_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t n_
     if (n_isect < 0 || n_isect > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "xpr_sort_tiles: bad count");
     if (n_tiles < 1) return fail(XPR_ERR_INVALID, "xpr_sort_tiles: n_tiles must be >= 1");
     if (!ranges) return fail(XPR_ERR_INVALID, "xpr_sort_tiles: NULL ranges");
-    if (n_isect > 0 && (!tiles_in || !vals_in || !tiles_out || !vals_out || !workspace))
+    if (n_isect > 0 && (!tiles_in || !vals_in || !vals_out || !workspace))
         return fail(XPR_ERR_INVALID, "xpr_sort_tiles: NULL pointer");
     if (n_isect > 0 && (tiles_in == tiles_out || vals_in == vals_out))
         return fail(XPR_ERR_INVALID, "xpr_sort_tiles: input and output buffers must not alias");
@@ -351,6 +351,31 @@ int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cam
     if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_rec, 16))
         return fail(XPR_ERR_INVALID, "xpr_project_bwd_views: quat and d_rec must be 16-byte aligned");
     return launch_project_bwd_views(*prims, n, cams, n_views, *cfg, d_rec, *d_prims, as_stream(stream));
+}
+
+size_t xpr_bin_sorted_workspace(int64_t n, int32_t n_views, const XprCamera *cam, const XprConfig *cfg) {
+    if (!cam || !cfg || n < 0 || n_views < 1 || n_views > kMaxViews || validate_camera_config(cam, cfg) != XPR_OK)
+        return 0;
+    return binsort_workspace_bytes(n, n_views, *cam, *cfg);
+}
+
+int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
+                   int32_t n_views, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges, uint32_t *vals,
+                   int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_views(n_views, n))) return s;
+    if (!binsort_supported(*cam, *cfg, n_views))
+        return fail(XPR_ERR_INVALID, "xpr_bin_sorted: a %d x %d tile grid (x %d views) exceeds the band limits",
+                    tiles_x(*cam, *cfg), tiles_y(*cam, *cfg), n_views);
+    if (!ranges || !n_isect) return fail(XPR_ERR_INVALID, "xpr_bin_sorted: NULL ranges or n_isect");
+    if (capacity < 0) return fail(XPR_ERR_INVALID, "xpr_bin_sorted: negative capacity");
+    if (n > 0 && (!rec || !bbox || !tile_count || !order || !workspace))
+        return fail(XPR_ERR_INVALID, "xpr_bin_sorted: NULL pointer");
+    if (n > 0 && (!aligned(rec, 16) || !aligned(bbox, 16) || !aligned(workspace, 256)))
+        return fail(XPR_ERR_INVALID, "xpr_bin_sorted: rec/bbox must be 16-byte and workspace 256-byte aligned");
+    return launch_binsort(rec, bbox, tile_count, order, n, n_views, *cam, *cfg, ranges, vals, capacity, n_isect,
+                          workspace, ws_bytes, as_stream(stream));
 }
 
 }  // extern "C"

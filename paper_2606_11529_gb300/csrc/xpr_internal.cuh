@@ -77,6 +77,13 @@ size_t depth_order_workspace_bytes(int64_t n);
 int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
                        cudaStream_t st, int64_t per_view = 0, int n_views = 1);
 
+// fused bin + sort (binsort.cu)
+size_t binsort_workspace_bytes(int64_t n, int n_views, const XprCamera &cam, const XprConfig &cfg);
+bool binsort_supported(const XprCamera &cam, const XprConfig &cfg, int n_views);
+int launch_binsort(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
+                   int n_views, const XprCamera &cam, const XprConfig &cfg, int32_t *ranges, uint32_t *vals,
+                   int64_t capacity, int64_t *n_isect, void *ws, size_t ws_bytes, cudaStream_t st);
+
 size_t sort_workspace_bytes(int64_t n, int32_t n_tiles);
 int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
                 uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st);

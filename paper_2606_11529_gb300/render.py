@@ -1,7 +1,8 @@
 """3DGS tile-splatting path on the GPU: the plain per-stage calls and the
 ``torch.autograd.Function`` that chains them.
 
-Forward  = xpr_project -> xpr_tile_bin -> xpr_sort -> xpr_render_fwd
+Forward  = xpr_project -> xpr_depth_order -> xpr_bin_sorted -> xpr_render_fwd
+           (or xpr_tile_bin -> xpr_sort_tiles in place of xpr_bin_sorted)
 Backward = xpr_render_bwd (compositing adjoint, then projection adjoint)
 
 The Function takes activated parameters (mu, scale, quat, opacity, sh), as in
@@ -25,9 +26,10 @@ class Workspace:
     xpr_tile_bin) and the transient scratch of xpr_tile_bin / xpr_sort.  Per-frame outputs are
     fresh tensors from PyTorch's caching allocator, so a Frame stays valid after later calls."""
 
-    def __init__(self):
+    def __init__(self, fused: bool = False):
         self.last_isect = 0
         self.bufs = {}
+        self.fused = fused  # xpr_bin_sorted (True) or xpr_tile_bin + xpr_sort_tiles (False)
 
     def scratch(self, name, nbytes, device):
         t = self.bufs.get(name)
@@ -73,9 +75,10 @@ _NO_TIMERS = _NoTimers()
 
 @dataclass
 class Frame:
-    """Everything the forward produces (kept for the backward and for tests).  The pairs are
-    emitted in depth order, so `tiles` (u32 tile ids, int32 storage) sorted stably by tile give
-    the (tile, depth) order of Sec. 4.2."""
+    """Everything the forward produces (kept for the backward and for tests).  On the key path the
+    pairs are emitted in depth order, so `tiles` (u32 tile ids, int32 storage) sorted stably by
+    tile give the (tile, depth) order of Sec. 4.2; the fused path produces `vals_sorted` and
+    `ranges` directly and leaves isect_count, offsets, tiles, vals and tiles_sorted as None."""
     rec: torch.Tensor
     bbox: torch.Tensor
     tile_count: torch.Tensor
@@ -94,37 +97,49 @@ class Frame:
 
 
 def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
-                  timers=None) -> Frame:
-    """The forward stages, each one C-ABI call: project (with exact kept-tile counts), depth
-    order, bin (emit only), sort by tile, render."""
+                  timers=None, fused: bool = False, keep_sorted_tiles: bool = False) -> Frame:
+    """The forward stages, each one C-ABI call: project, depth order, then either the key path
+    (xpr_tile_bin emitting u32 tile ids in depth order + xpr_sort_tiles, the default) or the fused
+    bin + sort (xpr_bin_sorted), then render.  Both give the same sorted lists bit for bit."""
     L = B.load()
     tm = timers or _NO_TIMERS
     ccam, ccfg = B.make_camera(cam), B.make_config(cfg)
+    fused = fused and B.binsort_ok(cam, cfg)
     n = mu.shape[0]
     dev = mu.device
     ws = ws or Workspace()
     tm.start("project", stream)
-    rec, bbox, tc, cnt = B.xpr_project(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream,
-                                       with_isect_count=True)
+    out = B.xpr_project(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream, with_isect_count=not fused)
+    rec, bbox, tc = out[:3]
+    cnt = out[3] if len(out) > 3 else None
     tm.stop("project", stream)
-    # emit intersections in (depth, index) order so that the sort only has to order tile ids
+    # emit intersections in (depth, index) order so that only tile ids remain to be ordered
     tm.start("depth_order", stream)
     order = B.xpr_depth_order(rec, tc, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(n), dev),
                               stream=stream)
     tm.stop("depth_order", stream)
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
-    bin_ws = ws.scratch("bin", L.xpr_tile_bin_workspace(n), dev)
-    tm.start("tile_bin", stream)
-    offsets, tiles, vals, I = B.xpr_tile_bin(rec, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
-                                             stream=stream, order=order, isect_count=cnt, tile_ids=True)
-    tm.stop("tile_bin", stream)
-    ws.last_isect = I
     Wt, Ht = B.tiles_of(cam, cfg)
     nt = Wt * Ht
-    sort_ws = ws.scratch("sort", L.xpr_sort_tiles_workspace(I, nt), dev)
-    tm.start("sort", stream)
-    ks, vs, ranges = B.xpr_sort_tiles(tiles, vals, nt, workspace=sort_ws, stream=stream)
-    tm.stop("sort", stream)
+    if fused:
+        bs_ws = ws.scratch("binsort", B.bin_sorted_workspace_bytes(n, 1, ccam, ccfg), dev)
+        tm.start("bin_sort", stream)
+        ranges, vs, I = B.xpr_bin_sorted(rec, bbox, tc, order, n, ccam, ccfg, capacity=cap, workspace=bs_ws,
+                                         stream=stream)
+        tm.stop("bin_sort", stream)
+        offsets = tiles = vals = ks = None
+    else:
+        bin_ws = ws.scratch("bin", L.xpr_tile_bin_workspace(n), dev)
+        tm.start("tile_bin", stream)
+        offsets, tiles, vals, I = B.xpr_tile_bin(rec, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
+                                                 stream=stream, order=order, isect_count=cnt, tile_ids=True)
+        tm.stop("tile_bin", stream)
+        sort_ws = ws.scratch("sort", L.xpr_sort_tiles_workspace(I, nt), dev)
+        tm.start("sort", stream)
+        ks, vs, ranges = B.xpr_sort_tiles(tiles, vals, nt, workspace=sort_ws, stream=stream,
+                                          want_tiles=keep_sorted_tiles)
+        tm.stop("sort", stream)
+    ws.last_isect = I
     tm.start("render_fwd", stream)
     image, t_final, n_contrib = B.xpr_render_fwd(rec, vs, ranges, ccam, ccfg, stream=stream)
     tm.stop("render_fwd", stream)
@@ -136,7 +151,7 @@ class SplatFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, mu, scale, quat, opacity, sh, cam, cfg, ws, timers):
-        fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, timers=timers)
+        fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, timers=timers, fused=ws.fused)
         ctx.save_for_backward(mu, scale, quat, opacity, sh, fr.rec, fr.vals_sorted, fr.ranges, fr.t_final,
                               fr.n_contrib)
         ctx.cam, ctx.cfg, ctx.timers = cam, cfg, timers

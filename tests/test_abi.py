@@ -100,3 +100,22 @@ def test_workspace_sizes_monotone(lib):
     assert 0 < a < b
     assert lib.xpr_tile_bin_workspace(10) >= 16
     assert lib.xpr_tile_bin_workspace(10_000_000) > lib.xpr_tile_bin_workspace(10)
+
+
+def test_bin_sorted_host_checks(lib):
+    from paper_2606_11529_gb300 import binding
+    cam, cfg = _cam_cfg()
+    ws = lib.xpr_bin_sorted_workspace(1000, 1, ctypes.byref(cam), ctypes.byref(cfg))
+    assert ws > 1000 * 8
+    assert lib.xpr_bin_sorted_workspace(1000, 3, ctypes.byref(cam), ctypes.byref(cfg)) > ws
+    assert lib.xpr_bin_sorted_workspace(1000, 17, ctypes.byref(cam), ctypes.byref(cfg)) == 0
+    n = ctypes.c_int64(0)
+    s = lib.xpr_bin_sorted(256, 256, 256, 256, 10, 1, ctypes.byref(cam), ctypes.byref(cfg), None, 256, 100,
+                           ctypes.byref(n), 256, 1 << 20, None)
+    assert s == binding.XPR_ERR_INVALID and b"NULL" in lib.xpr_last_error()
+    s = lib.xpr_bin_sorted(256, 256, 256, 256, 10, 1, ctypes.byref(cam), ctypes.byref(cfg), 256, 256, -1,
+                           ctypes.byref(n), 256, 1 << 20, None)
+    assert s == binding.XPR_ERR_INVALID and b"capacity" in lib.xpr_last_error()
+    # every valid camera (width <= 32768, 8x8 tiles: 4096 columns) fits the per-band counters
+    widest, cfg8 = _cam_cfg(width=32768, tile_w=8, tile_h=8)
+    assert binding.binsort_ok(widest, cfg8) and binding.binsort_ok(cam, cfg)
