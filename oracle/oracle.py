@@ -65,7 +65,7 @@ def lib():
         L.oracle_project_bwd.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                          _F64P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_sh_basis.argtypes = [ctypes.c_int, _F64P, _F64P, _F64P]
-        L.oracle_cull_one.argtypes = [_F64P, ctypes.c_int, ctypes.c_int, _F64P, _F64P]
+        L.oracle_cull_one.argtypes = [_F64P, ctypes.c_int, ctypes.c_int, _F64P, _F64P, ctypes.c_int]
         L.oracle_cull_one.restype = ctypes.c_int
         L.oracle_abi_version.restype = ctypes.c_int
         _lib = L
@@ -181,10 +181,12 @@ def sort_pairs(keys, vals, n_tiles):
     return kk[:keys.size], vv[:vals.size], ranges
 
 
-def cull_one(rec_row, tx, ty, cam, cfg) -> bool:
+def cull_one(rec_row, tx, ty, cam, cfg, form: int = 0) -> bool:
+    """Tile cull decision for one record and tile.  form 0: per-tile minimum (FP64); 1: row form
+    (FP64); 2: row form in FP32 on the float-rounded record (the kernels' decision)."""
     r = _f64(rec_row)
     ca, fa = cam_array(cam), cfg_array(cfg)
-    return bool(lib().oracle_cull_one(_p(r, _F64P), tx, ty, _p(ca, _F64P), _p(fa, _F64P)))
+    return bool(lib().oracle_cull_one(_p(r, _F64P), tx, ty, _p(ca, _F64P), _p(fa, _F64P), form))
 
 
 # --------------------------------------------------------------------------- compositing

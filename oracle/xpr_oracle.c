@@ -12,8 +12,10 @@
  *     footprint, conic, opacity-aware extents, tile bounding box, tile count,
  *     visibility flag, view-dependent SH colour;
  *   - the StopThePop tile cull of Listing 1 tile_cull (max response point of
- *     the tile), in an FP64 form and in an exact-FP32 form whose operation
- *     order is fixed and FMA-free (decisions taken in the kernel's precision);
+ *     the tile) in FP64, its row form (per tile row, the x-extent of the
+ *     ellipse within the row's strip) in FP64, and the row form in an
+ *     exact-FP32 version whose operation order is fixed and FMA-free
+ *     (decisions taken in the kernels' precision);
  *   - replicate / assign-tile-ID / sort / segment bounds of Sec. 4.2;
  *   - front-to-back alpha compositing c = sum c_i a_i T_i (Sec. 2 "Shader",
  *     Algorithm 1) with the evaluate of Listing 1, as a brute-force
@@ -389,54 +391,126 @@ static int cull_f64(double mx, double my, double c0, double c1, double c2, doubl
     return best <= lt;
 }
 
-/* Same decision in IEEE single precision, one rounding per operation, in
- * this exact order (the CUDA kernel takes the decision in FP32 with the same
- * sequence of correctly rounded operations).  The edge minimiser divides by
- * c2 (or c0) as a multiplication by the correctly rounded reciprocal 1/c2
- * (1/c0), computed once per primitive. */
-static float f32_q(float c0, float c1, float c2, float dx, float dy) {
-    float a = dx * dx;
-    a = a * c0;
-    float b = dx * dy;
-    b = b * c1;
-    b = b + b;
-    float c = dy * dy;
-    c = c * c2;
-    float sacc = a + b;
-    sacc = sacc + c;
-    return 0.5f * sacc;
+/* Row form of the same cull.  Inside one tile row (pixel rows [y0, y1]) the
+ * largest response over a tile reaches alpha_t iff the tile's pixel columns
+ * [x0, x1] meet S = {x : min over y in [y0, y1] of q(x, y) <= 2 ln_thr}, the
+ * x-extent of E ∩ strip with E = {q <= T}, T = 2 ln_thr.  E ∩ strip is
+ * convex, so S is one interval [xa, xb]: xa (xb) is the least (greatest) x
+ * among the leftmost (rightmost) point of E when its y lies in the strip and
+ * the crossings of the boundary of E with the lines y = y0 and y = y1.  With
+ * conic [[a, b], [b, c]], det = ac - b^2: the leftmost / rightmost points are
+ * (mx -/+ ex, my +/- sb), ex = sqrt(T c / det), sb = b sqrt(T / (c det)); the
+ * crossings with y = Y are x = mx + (-b dY -/+ sqrt(a T - det dY^2)) / a,
+ * dY = Y - my.  In exact arithmetic this keeps exactly the tiles the
+ * per-tile minimum keeps; it costs one evaluation per row instead of one per
+ * tile.  Returns 0 when the strip misses E. */
+static int row_span_f64(double mx, double my, double a, double b, double c, double lt, double y0, double y1,
+                        double *xa, double *xb) {
+    double T = 2.0 * lt;
+    if (!(T >= 0.0)) return 0;
+    double det = a * c - b * b;
+    double ex = sqrt(T * c / det), sb = b * sqrt(T / (c * det));
+    double lo = INFINITY, hi = -INFINITY;
+    double yl = my + sb, yr = my - sb;
+    if (yl >= y0 && yl <= y1) lo = mx - ex;
+    if (yr >= y0 && yr <= y1) hi = mx + ex;
+    double ys[2] = {y0, y1};
+    for (int k = 0; k < 2; ++k) {
+        double dY = ys[k] - my;
+        double disc = a * T - det * dY * dY;
+        if (disc >= 0.0) {
+            double r = sqrt(disc);
+            double xl = mx + (-b * dY - r) / a, xr = mx + (-b * dY + r) / a;
+            if (xl < lo) lo = xl;
+            if (xr > hi) hi = xr;
+        }
+    }
+    if (!(lo <= hi)) return 0;
+    *xa = lo;
+    *xb = hi;
+    return 1;
 }
 
-static int cull_f32(float mx, float my, float c0, float c1, float c2, float lt, float x0, float y0, float x1,
-                    float y1) {
-    int outx = (mx < x0) || (mx > x1);
-    int outy = (my < y0) || (my > y1);
-    if (!outx && !outy) return 0.0f <= lt;
-    float best = INFINITY;
-    float ic2 = 1.0f / c2, ic0 = 1.0f / c0;
-    if (outx) {
-        float ex = mx < x0 ? x0 : x1;
-        float dx = mx - ex;
-        float t = c1 * dx;
-        t = t * ic2;
-        float ys = my + t;
-        ys = fminf(fmaxf(ys, y0), y1);
-        float dy = my - ys;
-        float p = f32_q(c0, c1, c2, dx, dy);
-        best = fminf(best, p);
+/* Per-tile decision of the row form in FP64: keep iff [x0, x1] meets [xa, xb]. */
+static int cull_row_f64(double mx, double my, double c0, double c1, double c2, double lt, double x0, double y0,
+                        double x1, double y1) {
+    double xa, xb;
+    if (!row_span_f64(mx, my, c0, c1, c2, lt, y0, y1, &xa, &xb)) return 0;
+    return x1 >= xa && x0 <= xb;
+}
+
+/* The row form in IEEE single precision, one rounding per operation in this
+ * exact order, no FMA (the CUDA kernels take the decision in FP32 with the
+ * same sequence of correctly rounded operations: +, -, *, /, sqrt, and the
+ * correctly rounded reciprocal 1/a).  Per primitive: */
+typedef struct {
+    float mx, my, b, det, aT, ia, ex, yl, yr;
+    int ok;
+} rowcull32;
+
+static rowcull32 rowcull32_make(const float *R) {
+    rowcull32 r;
+    float a = R[2], b = R[3], c = R[4], lt = R[10];
+    float T = lt + lt;
+    r.mx = R[0];
+    r.my = R[1];
+    r.b = b;
+    r.ok = T >= 0.0f;
+    float ac = a * c, bb = b * b;
+    r.det = ac - bb;
+    r.aT = a * T;
+    r.ia = 1.0f / a;
+    float e1 = T * c;
+    float e2 = e1 / r.det;
+    r.ex = sqrtf(e2);
+    float s1 = c * r.det;
+    float s2 = T / s1;
+    float s3 = sqrtf(s2);
+    float sb = b * s3;
+    r.yl = r.my + sb;
+    r.yr = r.my - sb;
+    return r;
+}
+
+/* Kept tile columns [*ka, *kb] of tile row ty (pixel rows y0..y1); 0 if none.
+ * Tile k spans pixel columns [k w, k w + w - 1] (the last one clamped to
+ * W - 1): k w + w - 1 >= xa  <=>  k >= ceil((xa + 1) / w) - 1, and k w <= xb
+ * <=> k <= floor(xb / w); a span starting right of the image or ending left
+ * of it keeps nothing. */
+static int row_tiles_f32(const rowcull32 *r, float y0, float y1, int w, int W, int *ka, int *kb) {
+    if (!r->ok) return 0;
+    float lo = INFINITY, hi = -INFINITY;
+    if (r->yl >= y0 && r->yl <= y1) lo = r->mx - r->ex;
+    if (r->yr >= y0 && r->yr <= y1) hi = r->mx + r->ex;
+    float ys[2] = {y0, y1};
+    for (int k = 0; k < 2; ++k) {
+        float dY = ys[k] - r->my;
+        float q1 = r->det * dY;
+        float q2 = q1 * dY;
+        float disc = r->aT - q2;
+        if (disc >= 0.0f) {
+            float rt = sqrtf(disc);
+            float m = r->b * dY;
+            float nm = -m;
+            float ul = nm - rt, ur = nm + rt;
+            float xl = ul * r->ia, xr = ur * r->ia;
+            xl = r->mx + xl;
+            xr = r->mx + xr;
+            lo = fminf(lo, xl);
+            hi = fmaxf(hi, xr);
+        }
     }
-    if (outy) {
-        float ey = my < y0 ? y0 : y1;
-        float dy = my - ey;
-        float t = c1 * dy;
-        t = t * ic0;
-        float xs = mx + t;
-        xs = fminf(fmaxf(xs, x0), x1);
-        float dx = mx - xs;
-        float p = f32_q(c0, c1, c2, dx, dy);
-        best = fminf(best, p);
-    }
-    return best <= lt;
+    if (!(lo <= hi)) return 0;
+    if (lo > (float)(W - 1) || hi < 0.0f) return 0;
+    float iw = 1.0f / (float)w;
+    float t = lo + 1.0f;
+    t = t * iw;
+    float u = hi * iw;
+    t = fmaxf(t, -1.0f);
+    u = fminf(u, (float)(W / w + 2));
+    *ka = (int)ceilf(t) - 1;
+    *kb = (int)floorf(u);
+    return *ka <= *kb;
 }
 
 static void tile_bounds(int tx, int ty, const ocam *cam, const ocfg *cfg, double *b) {
@@ -450,12 +524,23 @@ static void tile_bounds(int tx, int ty, const ocam *cam, const ocfg *cfg, double
     b[3] = y1;
 }
 
-/* Exposed for the dense-sampling pin of the cull (FP64 form). */
-int oracle_cull_one(const double *rec, int tx, int ty, const double *camv, const double *cfgv) {
+/* Exposed for the dense-sampling pin of the cull (FP64 form). form 0: the
+ * per-tile minimum; 1: the row form (FP64); 2: the row form in FP32 on the
+ * float-rounded record (the kernels' decision). */
+int oracle_cull_one(const double *rec, int tx, int ty, const double *camv, const double *cfgv, int form) {
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
     double b[4];
     tile_bounds(tx, ty, &cam, &cfg, b);
+    if (form == 1) return cull_row_f64(rec[0], rec[1], rec[2], rec[3], rec[4], rec[10], b[0], b[1], b[2], b[3]);
+    if (form == 2) {
+        float R[12];
+        for (int k = 0; k < 12; ++k) R[k] = (float)rec[k];
+        rowcull32 rc = rowcull32_make(R);
+        int ka, kb;
+        if (!row_tiles_f32(&rc, (float)b[1], (float)b[3], cfg.tw, cam.W, &ka, &kb)) return 0;
+        return tx >= ka && tx <= kb;
+    }
     return cull_f64(rec[0], rec[1], rec[2], rec[3], rec[4], rec[10], b[0], b[1], b[2], b[3]);
 }
 
@@ -487,6 +572,9 @@ int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const int
         int w = bb[2] - bb[0], h = bb[3] - bb[1];
         int tc = (w > 0 && h > 0) ? w * h : 0;
         int cnt = 0;
+        rowcull32 rc;
+        if (exact32 && tc > 0) rc = rowcull32_make(rec32 + 12 * i);
+        int row_ty = -1, ka = 0, kb = -1;
         for (int r = 0; r < tc; ++r) {
             int tx = bb[0] + r % w, ty = bb[1] + r / w;
             double b[4];
@@ -495,8 +583,14 @@ int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const int
             float depth32;
             if (exact32) {
                 const float *R = rec32 + 12 * i;
-                keep = cull_f32(R[0], R[1], R[2], R[3], R[4], R[10], (float)b[0], (float)b[1], (float)b[2],
-                                (float)b[3]);
+                if (ty != row_ty) {  /* one span per tile row */
+                    row_ty = ty;
+                    if (!row_tiles_f32(&rc, (float)b[1], (float)b[3], cfg.tw, cam.W, &ka, &kb)) {
+                        ka = 0;
+                        kb = -1;
+                    }
+                }
+                keep = tx >= ka && tx <= kb;
                 depth32 = R[9];
             } else {
                 const double *R = rec64 + 12 * i;

@@ -72,6 +72,30 @@ def test_cull_matches_box_constrained_minimum(oracle):
     assert checked > 250
 
 
+def test_row_form_equals_per_tile_minimum(oracle):
+    # the row form (x-extent of ellipse ∩ tile-row strip) keeps exactly the tiles whose rectangle
+    # minimum passes, on random conics, means in and around a ragged image (partial edge tiles),
+    # both tile sizes; the FP32 row form on float-rounded records agrees away from near-ties
+    rng = np.random.default_rng(11)
+    flips32 = 0
+    total = 0
+    for W, H, tile in [(250, 170, 16), (250, 170, 8), (64, 48, 16)]:
+        cam = scenes.pinhole(W, H, float(W))
+        cfg = scenes.RenderConfig(tile_w=tile, tile_h=tile)
+        Wt, Ht = (W + tile - 1) // tile, (H + tile - 1) // tile
+        for _ in range(120):
+            c = _conic(rng)
+            mx, my = rng.uniform(-30, W + 30), rng.uniform(-30, H + 30)
+            rec = _rec(mx, my, c, rng.uniform(0.01, 1.0))
+            for ty in range(Ht):
+                for tx in range(Wt):
+                    a = oracle.cull_one(rec, tx, ty, cam, cfg, form=0)
+                    assert oracle.cull_one(rec, tx, ty, cam, cfg, form=1) == a, (W, tile, tx, ty, rec)
+                    flips32 += oracle.cull_one(rec, tx, ty, cam, cfg, form=2) != a
+                    total += 1
+    assert total > 50_000 and flips32 <= total * 1e-4
+
+
 def test_cull_is_conservative_at_pixels(oracle):
     # every (primitive, tile) pair with alpha >= alpha_t at some pixel of the tile is kept
     cam = scenes.pinhole(128, 128, 128.0)
