@@ -10,15 +10,6 @@
 namespace xpr {
 namespace {
 
-// Thread t visits position j = (t * stride) mod n with stride coprime to n (a bijection).  Outputs are
-// indexed by j, so the visiting order changes nothing but the schedule: in depth order the
-// near-camera primitives with the largest boxes are neighbours, and a contiguous assignment would
-// pile them onto the same few warps.
-__device__ __forceinline__ int64_t visited_position(int64_t n, int64_t stride) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    return t < n ? (int64_t)(((unsigned long long)t * (unsigned long long)stride) % (unsigned long long)n) : n;
-}
-
 __device__ __forceinline__ int box_of(const int4 *__restrict__ bbox, const int *__restrict__ tcount, int i,
                                       const Grid &g, int4 &bb) {
     bb = make_int4(0, 0, 0, 0);
@@ -35,12 +26,12 @@ __device__ __forceinline__ int box_of(const int4 *__restrict__ bbox, const int *
 // Count pass (used when the caller has no per-primitive counts): counts[j] = kept tiles of position j.
 __global__ void __launch_bounds__(256) bin_count_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
                                                         const int *__restrict__ tcount,
-                                                        const int *__restrict__ order, int64_t n, int64_t stride,
-                                                        Grid g, int32_t *__restrict__ counts) {
-    const int64_t j = visited_position(n, stride);
+                                                        const int *__restrict__ order, int64_t n, Grid g,
+                                                        int32_t *__restrict__ counts) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int i = 0, area = 0;
     int4 bb = make_int4(0, 0, 0, 0);
-    CullData d = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    CullData d = {};
     if (j < n) {
         i = order ? order[j] : (int)j;
         area = box_of(bbox, tcount, i, g, bb);
@@ -50,71 +41,91 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float *__restrict_
     if (j < n) counts[j] = cnt;
 }
 
-// Emit pass: the pairs of position j go to [offsets[j], offsets[j+1]) in slot order r.  Boxes of at
-// most kSmallBox tiles are walked by their own thread; larger ones by the whole warp, 32 slots at a
-// time, with ballot prefix counts keeping the pairs in r order.  keys (u64 tile << 32 | depth bits)
-// and tiles (u32 tile id) are each written when non-NULL.
+__device__ __forceinline__ void put_pair(uint64_t *keys, uint32_t *tiles, uint32_t *vals, int64_t pos, uint32_t t,
+                                         uint32_t depth_bits, uint32_t i) {
+    if (keys) keys[pos] = ((uint64_t)t << 32) | depth_bits;
+    if (tiles) tiles[pos] = t;
+    vals[pos] = i;
+}
+
+// Emit pass.  Warp w of the grid takes the 32 positions w, w + nw, w + 2 nw, ... (nw warps in
+// all), so every warp gets primitives from all depths (in depth order the near-camera boxes, which
+// hold most pairs, are neighbours and would pile onto a few warps).  The pairs of position j go to
+// [offsets[j], offsets[j+1]) in slot order (the box's rows in order, each row's kept span in
+// order).  The tile rows of the warp's 32 boxes are spread over the lanes 32 at a time: each lane
+// finds its row's kept span (cull.cuh), a warp scan of the span lengths places the rows (each
+// position keeps a running output cursor across steps), and the warp writes the step's pairs 32
+// at a time, a lane finding the row of its pair by a binary search over the scanned lengths, so a
+// row's pairs are written by consecutive lanes to consecutive addresses.
+// keys (u64 tile << 32 | depth bits) and tiles (u32 tile id) are each written when non-NULL.
 // Records of a multi-view launch are view-major (record i belongs to view i div per_view) and the
 // tile id of a pair is offset by view * tiles_per_view (per_view = 0: a single view).
 __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
                                                        const int *__restrict__ tcount,
-                                                       const int *__restrict__ order, int64_t n, int64_t stride,
-                                                       Grid g, int64_t per_view, int tiles_per_view,
+                                                       const int *__restrict__ order, int64_t n, Grid g,
+                                                       int64_t per_view, int tiles_per_view,
                                                        const int32_t *__restrict__ offsets,
                                                        uint64_t *__restrict__ keys, uint32_t *__restrict__ tiles,
                                                        uint32_t *__restrict__ vals) {
-    const int64_t j = visited_position(n, stride);
     const int lane = threadIdx.x & 31;
+    const int64_t nw = (n + 31) / 32;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= nw) return;
+    const int64_t j = w + (int64_t)lane * nw;
     int i = 0, area = 0;
     int4 bb = make_int4(0, 0, 0, 0);
+    CullData d = {};
+    uint32_t depth_bits = 0, tbase = 0;
+    int cursor = 0;  // next output slot of this lane's position
     if (j < n) {
         i = order ? order[j] : (int)j;
+        cursor = offsets[j];
         area = box_of(bbox, tcount, i, g, bb);
-    }
-    if (area > 0 && area <= kSmallBox) {
-        const CullData d = load_cull(rec, i);
-        const uint32_t depth_bits = __float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]);
-        const uint32_t tbase = per_view ? (uint32_t)(i / per_view) * (uint32_t)tiles_per_view : 0u;
-        const int64_t out = offsets[j];
-        int cnt = 0;
-        for (int ty = bb.y; ty < bb.w; ++ty)
-            for (int tx = bb.x; tx < bb.z; ++tx) {
-                if (!keep_tile(d, g, tx, ty)) continue;
-                const uint32_t t = tbase + (uint32_t)(ty * g.Wt + tx);
-                if (keys) keys[out + cnt] = ((uint64_t)t << 32) | depth_bits;
-                if (tiles) tiles[out + cnt] = t;
-                vals[out + cnt] = (uint32_t)i;
-                ++cnt;
-            }
-    }
-    unsigned big = __ballot_sync(kFullMask, area > kSmallBox);
-    while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const long long jb = __shfl_sync(kFullMask, (long long)j, src);
-        const int ib = __shfl_sync(kFullMask, i, src);
-        const int areab = __shfl_sync(kFullMask, area, src);
-        const int bx = __shfl_sync(kFullMask, bb.x, src), by = __shfl_sync(kFullMask, bb.y, src);
-        const int bw = __shfl_sync(kFullMask, bb.z, src) - bx;
-        const CullData d = load_cull(rec, ib);
-        const uint32_t depth_bits = __float_as_uint(rec[(size_t)ib * XPR_REC_FLOATS + 9]);
-        const uint32_t tbase = per_view ? (uint32_t)(ib / per_view) * (uint32_t)tiles_per_view : 0u;
-        const int64_t out = offsets[jb];
-        SlotWalk sw(bx, by, bw, lane);
-        int cnt = 0;
-        for (int r0 = 0; r0 < areab; r0 += 32) {
-            const bool keep = r0 + lane < areab && keep_tile(d, g, sw.tx, sw.ty);
-            const unsigned m = __ballot_sync(kFullMask, keep);
-            if (keep) {
-                const int64_t pos = out + cnt + __popc(m & ((1u << lane) - 1u));
-                const uint32_t t = tbase + (uint32_t)(sw.ty * g.Wt + sw.tx);
-                if (keys) keys[pos] = ((uint64_t)t << 32) | depth_bits;
-                if (tiles) tiles[pos] = t;
-                vals[pos] = (uint32_t)ib;
-            }
-            cnt += __popc(m);
-            sw.step();
+        if (area > 0) {
+            d = load_cull(rec, i);
+            depth_bits = __float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]);
+            tbase = per_view ? (uint32_t)(i / per_view) * (uint32_t)tiles_per_view : 0u;
         }
+    }
+    const int h = area > 0 ? bb.w - bb.y : 0;
+    const int incl = warp_incl_scan(h);
+    const int rows = __shfl_sync(kFullMask, incl, 31);
+    const int excl = incl - h;
+    for (int f0 = 0; f0 < rows; f0 += 32) {
+        const int f = f0 + lane;
+        const int p = lane_of(incl, f);
+        const CullData e = shfl_cull(d, p);
+        const int excl_p = __shfl_sync(kFullMask, excl, p);
+        const int ty = __shfl_sync(kFullMask, bb.y, p) + f - excl_p;
+        const int x0 = __shfl_sync(kFullMask, bb.x, p), x1 = __shfl_sync(kFullMask, bb.z, p);
+        int ka = 0, kb = -1;
+        const int c = f < rows ? row_span_in_box(e, g, ty, x0, x1, ka, kb) : 0;
+        const int ci = warp_incl_scan(c);
+        const int cx = ci - c;
+        // output slot of this row's first pair: the position's cursor plus its earlier rows here
+        const int first = max(excl_p - f0, 0);  // lane of the position's first row in this step
+        const int out_row = __shfl_sync(kFullMask, cursor, p) + cx - __shfl_sync(kFullMask, cx, first);
+        const int total = __shfl_sync(kFullMask, ci, 31);
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            const int r = lane_of(ci, k);
+            const int ka_r = __shfl_sync(kFullMask, ka, r);
+            const int in_r = k - __shfl_sync(kFullMask, cx, r);
+            const int ty_r = __shfl_sync(kFullMask, ty, r);
+            const int o_r = __shfl_sync(kFullMask, out_row, r);
+            const int p_r = __shfl_sync(kFullMask, p, r);
+            const int i_r = __shfl_sync(kFullMask, i, p_r);
+            const uint32_t tb = __shfl_sync(kFullMask, tbase, p_r);
+            const uint32_t db = __shfl_sync(kFullMask, depth_bits, p_r);
+            if (k < total)
+                put_pair(keys, tiles, vals, (int64_t)o_r + in_r, tb + (uint32_t)(ty_r * g.Wt + ka_r + in_r), db,
+                         (uint32_t)i_r);
+        }
+        // advance each position's cursor by its rows' pairs in this step
+        const int lo = max(excl - f0, 0), hi = min(incl - 1 - f0, 31);
+        const int s_hi = __shfl_sync(kFullMask, ci, max(hi, 0));
+        const int s_lo = __shfl_sync(kFullMask, ci, max(lo - 1, 0));
+        if (h > 0 && hi >= 0 && lo <= 31 && lo <= hi) cursor += s_hi - (lo > 0 ? s_lo : 0);
     }
 }
 
@@ -227,14 +238,6 @@ __global__ void __launch_bounds__(kScanThreads) scan_downsweep_kernel(const int3
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (int32_t)*total;
 }
 
-// A stride coprime to n for the thread -> position bijection (a prime that does not divide n).
-int64_t visit_stride(int64_t n) {
-    static const int64_t primes[] = {7919, 7927, 7933, 7937, 7949, 7951, 7963, 7993};
-    for (int64_t p : primes)
-        if (n % p != 0) return p % n == 0 ? 1 : p;
-    return 1;  // n is a multiple of every listed prime (impossible for n < 2^31): contiguous visiting
-}
-
 }  // namespace
 
 int64_t *scan_total_ptr(void *partials, int64_t n) {
@@ -271,7 +274,7 @@ int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, c
     if (n == 0) return XPR_OK;
     const int tpb = 256;
     bin_count_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, visit_stride(n), make_grid(cam, cfg), counts);
+        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg), counts);
     XPR_LAUNCH_CHECK("bin_count_kernel");
     return XPR_OK;
 }
@@ -281,8 +284,9 @@ int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, co
                     uint32_t *tiles, uint32_t *vals, cudaStream_t st, int64_t per_view) {
     if (n == 0) return XPR_OK;
     const int tpb = 256;
-    bin_emit_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, visit_stride(n), make_grid(cam, cfg), per_view,
+    const int64_t warps = (n + 31) / 32;
+    bin_emit_kernel<<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, st>>>(
+        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg), per_view,
         tiles_x(cam, cfg) * tiles_y(cam, cfg), offsets, keys, tiles, vals);
     XPR_LAUNCH_CHECK("bin_emit_kernel");
     return XPR_OK;

@@ -375,20 +375,12 @@ __global__ void __launch_bounds__(kUnitWarps * 32) walk_kernel(const float *__re
             const bool hit = b.x1 > b.x0 && b.y0 < r1 && b.y1 > r0;
             unsigned m = __ballot_sync(kFullMask, hit);
             if (!m) continue;
-            CullData cd = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            CullData cd = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1.f};
             if (hit) cd = load_cull(rec, i);
             while (m) {
                 const int src = __ffs(m) - 1;
                 m &= m - 1;
-                CullData e;
-                e.mx = __shfl_sync(kFullMask, cd.mx, src);
-                e.my = __shfl_sync(kFullMask, cd.my, src);
-                e.c0 = __shfl_sync(kFullMask, cd.c0, src);
-                e.c1 = __shfl_sync(kFullMask, cd.c1, src);
-                e.c2 = __shfl_sync(kFullMask, cd.c2, src);
-                e.lt = __shfl_sync(kFullMask, cd.lt, src);
-                e.ic0 = __shfl_sync(kFullMask, cd.ic0, src);
-                e.ic2 = __shfl_sync(kFullMask, cd.ic2, src);
+                const CullData e = shfl_cull(cd, src);
                 const int is = __shfl_sync(kFullMask, i, src);
                 const int x0 = __shfl_sync(kFullMask, b.x0, src), x1 = __shfl_sync(kFullMask, b.x1, src);
                 const int y0 = max(__shfl_sync(kFullMask, b.y0, src), r0);

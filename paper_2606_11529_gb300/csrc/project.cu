@@ -272,15 +272,10 @@ __device__ __forceinline__ void project_view(const Params &P, const float *__res
         const float idet = 1.f / G.det;
         // the stored record values are the ones the cull reads back, so the count taken here from
         // registers and the emit kernel's decisions from memory are bit-identical
-        cd.mx = G.mx;
-        cd.my = G.my;
-        cd.c0 = G.c * idet;
-        cd.c1 = -G.b * idet;
-        cd.c2 = G.a * idet;
-        cd.lt = f.lt;
-        cull_reciprocals(cd);
-        o4[0] = make_float4(cd.mx, cd.my, cd.c0, cd.c1);
-        o4[1] = make_float4(cd.c2, P.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
+        const float c0 = G.c * idet, c1 = -G.b * idet, c2 = G.a * idet;
+        cd = make_cull(G.mx, G.my, c0, c1, c2, f.lt);
+        o4[0] = make_float4(G.mx, G.my, c0, c1);
+        o4[1] = make_float4(c2, P.o, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f));
         o4[2] = make_float4(fmaxf(col[2], 0.f), z, f.lt, 1.f);
         bbox[out] = f.bb;
         tcount[out] = f.tc;
