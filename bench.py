@@ -36,7 +36,17 @@ SH_FLOATS = 48
 PARAM_BYTES = 4 * (3 + 3 + 4 + 1 + SH_FLOATS)  # 236 B per primitive
 REC_BYTES = 48
 FWD_OPS_PER_PAIR = 16   # FP32-pipe operations per (pixel, entry) pair of the forward walk
-BWD_OPS_PER_PAIR = 41   # FP32-pipe operations per (pixel, entry) pair of the adjoint walk
+BWD_OPS_PER_PAIR = 45   # FP32-pipe operations per (pixel, entry) pair of the adjoint walk
+# stages that are one kernel launch (the render adjoint's bracket also holds the zero-fill of d_rec)
+SINGLE_KERNEL = {"project": "project_fwd_kernel<3>", "render_fwd": "render_fwd_kernel<16,16>",
+                 "render_bwd": "render_bwd_kernel<16,16>", "project_bwd": "project_bwd_kernel<3>"}
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernel, and where it is
+TRAFFIC = {"render_bwd_kernel<16,16>": 45_104_640, "render_fwd_kernel<16,16>": 10_314_752,
+           "project_bwd_kernel<3>": 462_717_952, "project_fwd_kernel<3>": 288_131_840}  # bytes
+TRAFFIC_SOURCE = {"render_bwd_kernel<16,16>": "profiles/render_bwd_headline.md",
+                  "render_fwd_kernel<16,16>": "profiles/render_fwd_headline.md",
+                  "project_bwd_kernel<3>": "profiles/project_bwd_headline.md",
+                  "project_fwd_kernel<3>": "profiles/project_fwd_headline.md"}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -390,15 +400,23 @@ def main():
             ach = amount / (t * 1e-3)
             stages[name] = {"ms": round(t, 4), "bound": "alu", "achieved_tops": round(ach / 1e12, 3),
                             "frac": round(ach / pk["alu_ops"], 4)}
-    dom = max(stages, key=lambda k: stages[k]["ms"])
+    # roofline of the dominant kernel: the largest stage that is a single kernel launch
+    single = {k: v for k, v in stages.items() if k in SINGLE_KERNEL}
+    dom = max(single, key=lambda k: single[k]["ms"])
     d = stages[dom]
+    kname = SINGLE_KERNEL[dom]
+    traffic = TRAFFIC.get(kname)
     if d["bound"] == "hbm":
-        roof = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": d["frac"], "traffic": None, "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs)"}
+        roof = {"kernel": kname, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": d["frac"], "traffic": traffic,
+                "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs)"}
     else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": d["achieved_tops"], "peak": round(pk["alu_ops"] / 1e12, 2),
-                "unit": "TOP/s", "frac": d["frac"], "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (FP32 lane-ops/s)"}
+        roof = {"kernel": kname, "bound": "alu", "achieved": d["achieved_tops"],
+                "peak": round(pk["alu_ops"] / 1e12, 2), "unit": "TOP/s", "frac": d["frac"], "traffic": traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (FP32 lane-ops/s), derived"}
+    roof["timing"] = "CUDA events around the C-ABI call on the launching stream, mean over the timed steps"
+    if traffic is not None:
+        roof["traffic_source"] = TRAFFIC_SOURCE[kname]
 
     # end to end through the public API: pinned H2D of the step's inputs, fwd+bwd, D2H of the loss
     e2e_s = torch.cuda.Event(enable_timing=True)
