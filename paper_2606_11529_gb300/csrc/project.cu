@@ -324,8 +324,54 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(const float *__restric
 template <int DEG>
 struct Acc {
     float mu[3], s[3], qn[4], o;
-    float sh[(DEG + 1) * (DEG + 1) * 3];
 };
+
+// Sum over k of w_k grad Y_k (the partials of sh_basis_grad, folded into the sum term by term so
+// that no per-basis gradient array is kept).
+template <int DEG>
+__device__ __forceinline__ float3 sh_grad_dot(float x, float y, float z, const float *w) {
+    float rx = 0.f, ry = 0.f, rz = 0.f;
+    if constexpr (DEG >= 1) {
+        ry -= kC1 * w[1];
+        rz += kC1 * w[2];
+        rx -= kC1 * w[3];
+    }
+    if constexpr (DEG >= 2) {
+        rx += kC2a * (w[4] * y - w[7] * z) + 2.f * x * (kC2c * w[8] - kC2b * w[6]);
+        ry += kC2a * (w[4] * x - w[5] * z) - 2.f * y * (kC2b * w[6] + kC2c * w[8]);
+        rz += kC2a * (-w[5] * y - w[7] * x) + 4.f * kC2b * z * w[6];
+        if constexpr (DEG >= 3) {
+            const float xx = x * x, yy = y * y, zz = z * z;
+            // G9 = (-6 C3a x y, -C3a (3xx - 3yy), 0)
+            rx += -kC3a * 6.f * x * y * w[9];
+            ry += -kC3a * (3.f * xx - 3.f * yy) * w[9];
+            // G10 = C3b (y z, x z, x y)
+            rx += kC3b * y * z * w[10];
+            ry += kC3b * x * z * w[10];
+            rz += kC3b * x * y * w[10];
+            // G11 = (2 C3c x y, -C3c (4zz - xx - 3yy), -8 C3c y z)
+            rx += kC3c * 2.f * x * y * w[11];
+            ry += -kC3c * (4.f * zz - xx - 3.f * yy) * w[11];
+            rz += -kC3c * 8.f * y * z * w[11];
+            // G12 = (-6 C3d x z, -6 C3d y z, C3d (6zz - 3xx - 3yy))
+            rx += -kC3d * 6.f * x * z * w[12];
+            ry += -kC3d * 6.f * y * z * w[12];
+            rz += kC3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+            // G13 = (-C3c (4zz - 3xx - yy), 2 C3c x y, -8 C3c x z)
+            rx += -kC3c * (4.f * zz - 3.f * xx - yy) * w[13];
+            ry += kC3c * 2.f * x * y * w[13];
+            rz += -kC3c * 8.f * x * z * w[13];
+            // G14 = (2 C3e x z, -2 C3e y z, C3e (xx - yy))
+            rx += kC3e * 2.f * x * z * w[14];
+            ry += -kC3e * 2.f * y * z * w[14];
+            rz += kC3e * (xx - yy) * w[14];
+            // G15 = (-C3a (3xx - 3yy), 6 C3a x y, 0)
+            rx += -kC3a * (3.f * xx - 3.f * yy) * w[15];
+            ry += kC3a * 6.f * x * y * w[15];
+        }
+    }
+    return make_float3(rx, ry, rz);
+}
 
 // K6 for one view: chains d_rec = (d mu_2D, d conic, d o, d rgb) back to the parameters:
 //   conic = A^{-1}:        dL/dA = -A^{-1} G A^{-1}  (G = dL/dconic, off-diagonal split in two)
@@ -337,7 +383,7 @@ struct Acc {
 //   colour:                 dL/dsh_k = Y_k g (where unclamped); dL/dd through the basis gradient,
 //                           projected on the tangent plane and divided by |mu - camera centre|
 template <int DEG>
-__device__ __forceinline__ void adjoint_view(const Params &P, const float *__restrict__ shi, const Geo &G,
+__device__ __forceinline__ void adjoint_view(const Params &P, const float *shi, float *dsh, const Geo &G,
                                              const Cam &k, float4 d0, float4 d1, float4 d2, Acc<DEG> &A) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const float dmx = d0.x, dmy = d0.y, g00 = d0.z, g01 = d0.w, g11 = d1.x;
@@ -348,30 +394,28 @@ __device__ __forceinline__ void adjoint_view(const Params &P, const float *__res
     const float vx = P.m[0] - k.cpos[0], vy = P.m[1] - k.cpos[1], vz = P.m[2] - k.cpos[2];
     const float vinv = rsqrtf(vx * vx + vy * vy + vz * vz);
     const float ux = vx * vinv, uy = vy * vinv, uz = vz * vinv;
-    float Y[K];
-    float3 GY[K];
-    sh_basis<DEG>(ux, uy, uz, Y);
-    sh_basis_grad<DEG>(ux, uy, uz, GY);
-    float raw[3] = {0.5f, 0.5f, 0.5f};
+    float wk[K];  // w_k = gc . sh_k, then dL/dd = sum_k w_k grad Y_k
+    {
+        float Y[K];
+        sh_basis<DEG>(ux, uy, uz, Y);
+        float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) {
-        raw[0] += __ldg(shi + 3 * kk) * Y[kk];
-        raw[1] += __ldg(shi + 3 * kk + 1) * Y[kk];
-        raw[2] += __ldg(shi + 3 * kk + 2) * Y[kk];
-    }
-    float gc[3];
-    for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.f ? drgb[c] : 0.f;
-    float3 gdir = make_float3(0.f, 0.f, 0.f);
+        for (int kk = 0; kk < K; ++kk) {
+            raw[0] += shi[3 * kk] * Y[kk];
+            raw[1] += shi[3 * kk + 1] * Y[kk];
+            raw[2] += shi[3 * kk + 2] * Y[kk];
+        }
+        float gc[3];
+        for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.f ? drgb[c] : 0.f;
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) {
-        const float w = gc[0] * __ldg(shi + 3 * kk) + gc[1] * __ldg(shi + 3 * kk + 1) + gc[2] * __ldg(shi + 3 * kk + 2);
-        gdir.x += w * GY[kk].x;
-        gdir.y += w * GY[kk].y;
-        gdir.z += w * GY[kk].z;
-        A.sh[3 * kk] += Y[kk] * gc[0];
-        A.sh[3 * kk + 1] += Y[kk] * gc[1];
-        A.sh[3 * kk + 2] += Y[kk] * gc[2];
+        for (int kk = 0; kk < K; ++kk) {
+            wk[kk] = gc[0] * shi[3 * kk] + gc[1] * shi[3 * kk + 1] + gc[2] * shi[3 * kk + 2];
+            dsh[3 * kk] += Y[kk] * gc[0];
+            dsh[3 * kk + 1] += Y[kk] * gc[1];
+            dsh[3 * kk + 2] += Y[kk] * gc[2];
+        }
     }
+    const float3 gdir = sh_grad_dot<DEG>(ux, uy, uz, wk);
     const float dd = gdir.x * ux + gdir.y * uy + gdir.z * uz;
     A.mu[0] += (gdir.x - ux * dd) * vinv;
     A.mu[1] += (gdir.y - uy * dd) * vinv;
@@ -458,45 +502,72 @@ __device__ __forceinline__ void adjoint_view(const Params &P, const float *__res
                       qx * gR[6] + qy * gR[7]);
 }
 
+// Shared-memory row stride of one primitive's SH coefficients (odd, so the 32 lanes of a warp
+// reading their own rows hit 32 different banks).
 template <int DEG>
-__global__ void __launch_bounds__(256) project_bwd_kernel(const float *__restrict__ mu, const float *__restrict__ scale,
-                                                          const float *__restrict__ quat,
-                                                          const float *__restrict__ opac,
-                                                          const float *__restrict__ sh, int64_t n, CamSet cs,
-                                                          XprConfig cfg, const float *__restrict__ d_rec,
-                                                          float *__restrict__ gmu, float *__restrict__ gscale,
-                                                          float *__restrict__ gquat, float *__restrict__ gopac,
-                                                          float *__restrict__ gsh) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const Params P = load_params(mu, scale, quat, opac, i);
-    const float *shi = sh + (size_t)i * K * 3;
-    Acc<DEG> A = {};
-    float qinv = 0.f, qn[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int v = 0; v < cs.n_views; ++v) {
-        const Cam k = make_cam(cs.cam[v], cfg);
-        Geo G;
-        geometry(P, k, cfg.cov_dilation, G);
-        if (!footprint(G, P.o, k, cfg).vis) continue;  // invisible in this view: no gradient from it
-        const float4 *D4 = reinterpret_cast<const float4 *>(d_rec + ((size_t)v * n + i) * XPR_REC_FLOATS);
-        adjoint_view<DEG>(P, shi, G, k, __ldg(D4), __ldg(D4 + 1), __ldg(D4 + 2), A);
-        qinv = G.qinv;
-        for (int j = 0; j < 4; ++j) qn[j] = G.qn[j];
+__host__ __device__ constexpr int sh_ld() {
+    return ((DEG + 1) * (DEG + 1) * 3) | 1;
+}
+constexpr int kBwdWarps = 4;
+
+// One thread per primitive; each warp stages its 32 primitives' SH coefficients in shared memory
+// with coalesced loads and accumulates their gradients there, then writes them out coalesced (a
+// thread's own rows are 3K floats apart in global memory).
+template <int DEG>
+__global__ void __launch_bounds__(kBwdWarps * 32, 4) project_bwd_kernel(
+    const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
+    const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
+    const float *__restrict__ d_rec, float *__restrict__ gmu, float *__restrict__ gscale, float *__restrict__ gquat,
+    float *__restrict__ gopac, float *__restrict__ gsh) {
+    constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
+    constexpr int LD = sh_ld<DEG>();
+    extern __shared__ float s_bwd[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * kBwdWarps + w) * 32;
+    if (base >= n) return;
+    const int nv = (int)min((int64_t)32, n - base);
+    float *ssh = s_bwd + (size_t)w * 2 * 32 * LD;
+    float *sdsh = ssh + 32 * LD;
+    const float *gs = sh + base * KC;
+    for (int e = lane; e < nv * KC; e += 32) {
+        const int pi = e / KC;
+        ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
     }
-    // qn = q / |q|:  dL/dq = (dL/dqn - qn (qn . dL/dqn)) / |q|
-    const float dot = A.qn[0] * qn[0] + A.qn[1] * qn[1] + A.qn[2] * qn[2] + A.qn[3] * qn[3];
-    for (int j = 0; j < 3; ++j) {
-        gmu[3 * i + j] = A.mu[j];
-        gscale[3 * i + j] = A.s[j];
+    for (int c = 0; c < KC; ++c) sdsh[lane * LD + c] = 0.f;
+    __syncwarp();
+    const int64_t i = base + lane;
+    if (i < n) {
+        const Params P = load_params(mu, scale, quat, opac, i);
+        Acc<DEG> A = {};
+        float qinv = 0.f, qn[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int v = 0; v < cs.n_views; ++v) {
+            const Cam k = make_cam(cs.cam[v], cfg);
+            Geo G;
+            geometry(P, k, cfg.cov_dilation, G);
+            if (!footprint(G, P.o, k, cfg).vis) continue;  // invisible in this view: no gradient from it
+            const float4 *D4 = reinterpret_cast<const float4 *>(d_rec + ((size_t)v * n + i) * XPR_REC_FLOATS);
+            adjoint_view<DEG>(P, ssh + lane * LD, sdsh + lane * LD, G, k, __ldg(D4), __ldg(D4 + 1), __ldg(D4 + 2),
+                              A);
+            qinv = G.qinv;
+            for (int j = 0; j < 4; ++j) qn[j] = G.qn[j];
+        }
+        // qn = q / |q|:  dL/dq = (dL/dqn - qn (qn . dL/dqn)) / |q|
+        const float dot = A.qn[0] * qn[0] + A.qn[1] * qn[1] + A.qn[2] * qn[2] + A.qn[3] * qn[3];
+        for (int j = 0; j < 3; ++j) {
+            gmu[3 * i + j] = A.mu[j];
+            gscale[3 * i + j] = A.s[j];
+        }
+        reinterpret_cast<float4 *>(gquat)[i] =
+            make_float4((A.qn[0] - qn[0] * dot) * qinv, (A.qn[1] - qn[1] * dot) * qinv,
+                        (A.qn[2] - qn[2] * dot) * qinv, (A.qn[3] - qn[3] * dot) * qinv);
+        gopac[i] = A.o;
     }
-    reinterpret_cast<float4 *>(gquat)[i] =
-        make_float4((A.qn[0] - qn[0] * dot) * qinv, (A.qn[1] - qn[1] * dot) * qinv, (A.qn[2] - qn[2] * dot) * qinv,
-                    (A.qn[3] - qn[3] * dot) * qinv);
-    gopac[i] = A.o;
-    float *gshi = gsh + (size_t)i * K * 3;
-#pragma unroll
-    for (int e = 0; e < K * 3; ++e) gshi[e] = A.sh[e];
+    __syncwarp();
+    float *go = gsh + base * KC;
+    for (int e = lane; e < nv * KC; e += 32) {
+        const int pi = e / KC;
+        go[e] = sdsh[pi * LD + (e - pi * KC)];
+    }
 }
 
 CamSet make_camset(const XprCamera *cams, int n_views) {
@@ -533,12 +604,19 @@ int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams
 int launch_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
                              const float *d_rec, const XprPrimsGrad &g, cudaStream_t st) {
     if (n == 0 || n_views == 0) return XPR_OK;
-    const int tpb = 256;
+    const int tpb = kBwdWarps * 32;
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
-    XPR_DEG_DISPATCH(DEG, project_bwd_kernel<DEG><<<blocks, tpb, 0, st>>>(
-                              p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, d_rec, g.mu, g.scale, g.quat,
-                              g.opacity, g.sh));
+    cudaError_t attr = cudaSuccess;
+    // the shared-memory size is a constant of each instantiation, so every caller sets the same limit
+    XPR_DEG_DISPATCH(DEG, {
+        const size_t smem = (size_t)kBwdWarps * 2 * 32 * sh_ld<DEG>() * sizeof(float);
+        attr = cudaFuncSetAttribute(project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (attr == cudaSuccess)
+            project_bwd_kernel<DEG><<<blocks, tpb, smem, st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg,
+                                                               d_rec, g.mu, g.scale, g.quat, g.opacity, g.sh);
+    });
+    XPR_CUDA_TRY(attr);
     XPR_LAUNCH_CHECK("project_bwd_kernel");
     return XPR_OK;
 }
