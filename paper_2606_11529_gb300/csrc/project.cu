@@ -246,7 +246,7 @@ struct CamSet {
 
 // K1 for one view: writes rec / bbox / tile count of record `out` and returns the cull data.
 template <int DEG>
-__device__ __forceinline__ void project_view(const Params &P, const float *__restrict__ shi, int64_t out,
+__device__ __forceinline__ void project_view(const Params &P, const float *shi, int64_t out,
                                              const XprCamera &cam, const XprConfig &cfg, float *__restrict__ rec,
                                              int4 *__restrict__ bbox, int *__restrict__ tcount, CullData &cd,
                                              int4 &bb, int &area) {
@@ -259,9 +259,9 @@ __device__ __forceinline__ void project_view(const Params &P, const float *__res
     float col[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
-        col[0] += __ldg(shi + 3 * kk) * Y[kk];
-        col[1] += __ldg(shi + 3 * kk + 1) * Y[kk];
-        col[2] += __ldg(shi + 3 * kk + 2) * Y[kk];
+        col[0] += shi[3 * kk] * Y[kk];
+        col[1] += shi[3 * kk + 1] * Y[kk];
+        col[2] += shi[3 * kk + 2] * Y[kk];
     }
     Geo G;
     geometry(P, k, cfg.cov_dilation, G);
@@ -292,26 +292,45 @@ __device__ __forceinline__ void project_view(const Params &P, const float *__res
     }
 }
 
+// Shared-memory row stride of one primitive's SH coefficients (odd, so the 32 lanes of a warp
+// reading their own rows hit 32 different banks).
 template <int DEG>
-__global__ void __launch_bounds__(256) project_fwd_kernel(const float *__restrict__ mu, const float *__restrict__ scale,
-                                                          const float *__restrict__ quat,
-                                                          const float *__restrict__ opac,
-                                                          const float *__restrict__ sh, int64_t n, CamSet cs,
-                                                          XprConfig cfg, float *__restrict__ rec,
-                                                          int4 *__restrict__ bbox, int *__restrict__ tcount,
-                                                          int *__restrict__ isect_count) {
-    constexpr int K = (DEG + 1) * (DEG + 1);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__host__ __device__ constexpr int sh_ld() {
+    return ((DEG + 1) * (DEG + 1) * 3) | 1;
+}
+constexpr int kProjWarps = 4;
+
+// One thread per primitive and all views; each warp first stages its 32 primitives' SH
+// coefficients in shared memory with coalesced loads (a thread's own row is 3K floats long).
+template <int DEG>
+__global__ void __launch_bounds__(kProjWarps * 32) project_fwd_kernel(
+    const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
+    const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
+    float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount, int *__restrict__ isect_count) {
+    constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
+    constexpr int LD = sh_ld<DEG>();
+    extern __shared__ float s_fwd[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * kProjWarps + w) * 32;
+    if (base >= n) return;
+    const int nv = (int)min((int64_t)32, n - base);
+    float *ssh = s_fwd + (size_t)w * 32 * LD;
+    const float *gs = sh + base * KC;
+    for (int e = lane; e < nv * KC; e += 32) {
+        const int pi = e / KC;
+        ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
+    }
+    __syncwarp();
+    const int64_t i = base + lane;
     const bool valid = i < n;
     Params P = {};
     if (valid) P = load_params(mu, scale, quat, opac, i);
-    const float *shi = sh + (size_t)(valid ? i : 0) * K * 3;
     for (int v = 0; v < cs.n_views; ++v) {
         CullData cd = {};
         int4 bb = make_int4(0, 0, 0, 0);
         int area = 0;
         const int64_t out = (int64_t)v * n + i;
-        if (valid) project_view<DEG>(P, shi, out, cs.cam[v], cfg, rec, bbox, tcount, cd, bb, area);
+        if (valid) project_view<DEG>(P, ssh + lane * LD, out, cs.cam[v], cfg, rec, bbox, tcount, cd, bb, area);
         if (isect_count) {  // exact number of kept (primitive, tile) pairs, counted with the binning's cull
             const int cnt = count_kept_tiles(cd, bb, area, make_grid(cs.cam[v], cfg));
             if (valid) isect_count[out] = cnt;
@@ -502,12 +521,6 @@ __device__ __forceinline__ void adjoint_view(const Params &P, const float *shi, 
                       qx * gR[6] + qy * gR[7]);
 }
 
-// Shared-memory row stride of one primitive's SH coefficients (odd, so the 32 lanes of a warp
-// reading their own rows hit 32 different banks).
-template <int DEG>
-__host__ __device__ constexpr int sh_ld() {
-    return ((DEG + 1) * (DEG + 1) * 3) | 1;
-}
 constexpr int kBwdWarps = 4;
 
 // One thread per primitive; each warp stages its 32 primitives' SH coefficients in shared memory
@@ -591,10 +604,11 @@ CamSet make_camset(const XprCamera *cams, int n_views) {
 int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
                              float *rec, int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st) {
     if (n == 0 || n_views == 0) return XPR_OK;
-    const int tpb = 256;
+    const int tpb = kProjWarps * 32;
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
-    XPR_DEG_DISPATCH(DEG, project_fwd_kernel<DEG><<<blocks, tpb, 0, st>>>(
+    XPR_DEG_DISPATCH(DEG, project_fwd_kernel<DEG><<<blocks, tpb,
+                                                     (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
                               p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, rec,
                               reinterpret_cast<int4 *>(bbox), tc, isect_count));
     XPR_LAUNCH_CHECK("project_fwd_kernel");
