@@ -1,8 +1,8 @@
 // Shader stage (Sec. 2 Shader; Sec. 4.3; Algorithm 1; Listing 1 evaluate) and its adjoint.
 //
-// Forward (K4): one thread block per tile; each thread owns two pixels of the tile, (x, y) and
-// (x, y + h/2), so every shared-memory read of a list entry and every warp reduction of the
-// adjoint serves two pixels.  The tile's depth-sorted list is consumed in batches of
+// Forward (K4): one thread block per tile; each thread owns four pixels of the tile,
+// (x, y + q h/4) for q = 0..3, so every shared-memory read of a list entry and every warp
+// reduction of the adjoint serves four pixels.  The tile's depth-sorted list is consumed in batches of
 // `batch` entries staged in shared memory, then each pixel walks the batch front to back:
 //   power = -(c00 dx^2 + 2 c01 dx dy + c11 dy^2)/2  (base-2 form, conic pre-scaled by log2 e)
 //   skip if power > 0;  alpha = min(alpha_max, o 2^power2);  skip if alpha < alpha_t
@@ -14,7 +14,7 @@
 // recomputing T_i = T_{i+1} / (1 - alpha_i) and the colour behind, S (starting at T_final bg):
 //   dL/dc_i = g alpha_i T_i,   dL/dalpha_i = g . (c_i T_i - S_i / (1 - alpha_i))
 // then through alpha = o exp(power) (zero through the clamp) to o, mu_2D and the conic.  The 9
-// per-pixel partial gradients of one entry are summed over the thread's two pixels, over the
+// per-pixel partial gradients of one entry are summed over the thread's four pixels, over the
 // warp with shuffles, over the block in shared memory, and added to global memory with one set
 // of vector atomics per (tile, entry).
 //
@@ -28,7 +28,12 @@ namespace xpr {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kPX = 2;          // pixels per thread: (x, y) and (x, y + h/2)
+// Pixels per thread: (x, y + q h/PX), q = 0..PX-1, with PX = min(4, tile pixels / 32) so that a
+// tile's block is always whole warps (warp-wide shuffles and votes need all 32 lanes).
+template <int TW, int TH>
+__host__ __device__ constexpr int px_per_thread() {
+    return (TW * TH) / 32 >= 4 ? 4 : (TW * TH) / 32;
+}
 constexpr int kMaxBatch = 256;  // largest shared-memory batch (entries)
 
 struct Consts {
@@ -87,56 +92,63 @@ __device__ __forceinline__ void fwd_tile(int gt, const float *__restrict__ rec, 
                                          const int2 *__restrict__ ranges, const Consts &k, float *__restrict__ image,
                                          float *__restrict__ tfin, int *__restrict__ ncon, float4 *s_g, float4 *s_c,
                                          float *s_b) {
+    constexpr int kPX = px_per_thread<TW, TH>();
     constexpr int NT = TW * TH / kPX;
+    constexpr int RS = TH / kPX;  // rows between a thread's pixels
+    static_assert(NT % 32 == 0, "a tile's block must be whole warps");
     const int v = gt / k.T, tile = gt - v * k.T;
     const int tx = tile % k.Wt, ty = tile / k.Wt;
     const int t = threadIdx.x;
-    const int px = tx * TW + t % TW, py0 = ty * TH + t / TW, py1 = py0 + TH / kPX;
-    const bool in0 = px < k.W && py0 < k.H, in1 = px < k.W && py1 < k.H;
+    const int px = tx * TW + t % TW, py = ty * TH + t / TW;
     const int2 rg = ranges[gt];
     const float fx = (float)px;
-    PixelFwd P0 = {(float)py0, 1.f, 0.f, 0.f, 0.f, 0, !in0};
-    PixelFwd P1 = {(float)py1, 1.f, 0.f, 0.f, 0.f, 0, !in1};
+    PixelFwd P[kPX];
+    bool in[kPX];
+    bool all_done = true;
+#pragma unroll
+    for (int q = 0; q < kPX; ++q) {
+        in[q] = px < k.W && py + q * RS < k.H;
+        P[q] = PixelFwd{(float)(py + q * RS), 1.f, 0.f, 0.f, 0.f, 0, !in[q]};
+        all_done &= P[q].done;
+    }
     for (int base = rg.x; base < rg.y; base += k.batch) {
-        if (__syncthreads_and(P0.done && P1.done)) break;
+        if (__syncthreads_and(all_done)) break;
         const int cnt = min(k.batch, rg.y - base);
         for (int e = t; e < cnt; e += NT) stage(rec, vals, base + e, k.n, s_g, s_c, s_b, nullptr, e);
         __syncthreads();
-        if (!(P0.done && P1.done)) {
+        if (!all_done) {
             for (int j = 0; j < cnt; ++j) {
                 const float4 g = s_g[j];
                 const float4 c = s_c[j];
                 const float cb = s_b[j];
                 const float dx = __fsub_rn(fx, g.x);
                 const int pos = base + j - rg.x;
-                if (!P0.done) blend(P0, dx, g, c, cb, pos, k);
-                if (!P1.done) blend(P1, dx, g, c, cb, pos, k);
-                if (P0.done && P1.done) break;
+                all_done = true;
+#pragma unroll
+                for (int q = 0; q < kPX; ++q) {
+                    if (!P[q].done) blend(P[q], dx, g, c, cb, pos, k);
+                    all_done &= P[q].done;
+                }
+                if (all_done) break;
             }
         }
     }
     const int64_t HW = (int64_t)k.W * k.H;
     float *img = image + (int64_t)v * 3 * HW;
-    if (in0) {
-        const int64_t pix = (int64_t)py0 * k.W + px;
-        img[pix] = fmaf(P0.T, k.bg0, P0.r);
-        img[HW + pix] = fmaf(P0.T, k.bg1, P0.g);
-        img[2 * HW + pix] = fmaf(P0.T, k.bg2, P0.b);
-        tfin[v * HW + pix] = P0.T;
-        ncon[v * HW + pix] = P0.last;
-    }
-    if (in1) {
-        const int64_t pix = (int64_t)py1 * k.W + px;
-        img[pix] = fmaf(P1.T, k.bg0, P1.r);
-        img[HW + pix] = fmaf(P1.T, k.bg1, P1.g);
-        img[2 * HW + pix] = fmaf(P1.T, k.bg2, P1.b);
-        tfin[v * HW + pix] = P1.T;
-        ncon[v * HW + pix] = P1.last;
+#pragma unroll
+    for (int q = 0; q < kPX; ++q) {
+        if (!in[q]) continue;
+        const int64_t pix = (int64_t)(py + q * RS) * k.W + px;
+        img[pix] = fmaf(P[q].T, k.bg0, P[q].r);
+        img[HW + pix] = fmaf(P[q].T, k.bg1, P[q].g);
+        img[2 * HW + pix] = fmaf(P[q].T, k.bg2, P[q].b);
+        tfin[v * HW + pix] = P[q].T;
+        ncon[v * HW + pix] = P[q].last;
     }
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / kPX) render_fwd_kernel(const float *__restrict__ rec,
+__global__ void __launch_bounds__(TW *TH / px_per_thread<TW, TH>()) render_fwd_kernel(const float *__restrict__ rec,
                                                                   const uint32_t *__restrict__ vals,
                                                                   const int2 *__restrict__ ranges, Consts k,
                                                                   float *__restrict__ image,
@@ -256,22 +268,31 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
                                          const float *__restrict__ dimg, float *__restrict__ d_rec, float4 *s_g,
                                          float4 *s_c, float *s_b, uint32_t *s_id, float (*s_acc)[kMaxBatch],
                                          int *s_wmax) {
+    constexpr int kPX = px_per_thread<TW, TH>();
     constexpr int NT = TW * TH / kPX;
-    constexpr int NW = NT / 32 > 0 ? NT / 32 : 1;
+    constexpr int NW = NT / 32;
+    constexpr int RS = TH / kPX;
+    static_assert(NT % 32 == 0, "a tile's block must be whole warps");
     const int v = gt / k.T, tile = gt - v * k.T;
     const int tx = tile % k.Wt, ty = tile / k.Wt;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int px = tx * TW + t % TW, py0 = ty * TH + t / TW, py1 = py0 + TH / kPX;
-    const bool in0 = px < k.W && py0 < k.H, in1 = px < k.W && py1 < k.H;
+    const int px = tx * TW + t % TW, py = ty * TH + t / TW;
     const int2 rg = ranges[gt];
     const float fx = (float)px;
     const int64_t HW = (int64_t)k.W * k.H;
     const float *tf = tfin + v * HW;
     const int *nc = ncon + v * HW;
     const float *di = dimg + (int64_t)v * 3 * HW;
-    PixelBwd P0 = load_pixel_bwd(in0, (float)py0, (int64_t)py0 * k.W + px, HW, tf, nc, di, k);
-    PixelBwd P1 = load_pixel_bwd(in1, (float)py1, (int64_t)py1 * k.W + px, HW, tf, nc, di, k);
-    const int wlast = __reduce_max_sync(kFull, max(P0.last, P1.last));
+    PixelBwd P[kPX];
+    int mylast = 0;
+#pragma unroll
+    for (int q = 0; q < kPX; ++q) {
+        const int y = py + q * RS;
+        const bool in = px < k.W && y < k.H;
+        P[q] = load_pixel_bwd(in, (float)y, (int64_t)y * k.W + px, HW, tf, nc, di, k);
+        mylast = max(mylast, P[q].last);
+    }
+    const int wlast = __reduce_max_sync(kFull, mylast);
     if (lane == 0) s_wmax[wid] = wlast;
     __syncthreads();
     int bmax = 0;
@@ -298,8 +319,9 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
             const float4 c = s_c[j];
             const float cb = s_b[j];
             const float dx = __fsub_rn(fx, g.x);
-            bool hit = adjoint(P0, dx, g, c, cb, pos, k, vv);
-            hit |= adjoint(P1, dx, g, c, cb, pos, k, vv);
+            bool hit = false;
+#pragma unroll
+            for (int q = 0; q < kPX; ++q) hit |= adjoint(P[q], dx, g, c, cb, pos, k, vv);
             if (__any_sync(kFull, hit)) {
                 // vv[0..7]: transposed reduce-scatter (9 shuffles); afterwards lane l with l % 4 == 0
                 // holds the warp total of value l / 4.  vv[8]: plain butterfly (5 shuffles).
@@ -330,7 +352,7 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / kPX) render_bwd_kernel(const float *__restrict__ rec,
+__global__ void __launch_bounds__(TW *TH / px_per_thread<TW, TH>()) render_bwd_kernel(const float *__restrict__ rec,
                                                                   const uint32_t *__restrict__ vals,
                                                                   const int2 *__restrict__ ranges, Consts k,
                                                                   const float *__restrict__ tfin,
@@ -407,7 +429,7 @@ int launch_render_fwd_views(const float *rec, int64_t n, const uint32_t *vals, c
     Work w = {worklist, counter, items};
     if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
     XPR_TILE_DISPATCH(TW, TH, {
-        const int threads = TW * TH / kPX;
+        const int threads = TW * TH / px_per_thread<TW, TH>();
         const int grid = worklist ? persistent_grid(render_fwd_kernel<TW, TH>, threads, items) : items;
         render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, image, t_final, n_contrib, w);
     });
@@ -427,7 +449,7 @@ int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_
     Work w = {worklist, counter, items};
     if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
     XPR_TILE_DISPATCH(TW, TH, {
-        const int threads = TW * TH / kPX;
+        const int threads = TW * TH / px_per_thread<TW, TH>();
         const int grid = worklist ? persistent_grid(render_bwd_kernel<TW, TH>, threads, items) : items;
         render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, t_final, n_contrib, d_image, d_rec, w);
     });
