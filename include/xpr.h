@@ -117,7 +117,10 @@ typedef struct XprPrimsGrad {
  * count tc of Sec. 4.2; 0 when invisible).  isect_count[n] int32 (may be
  * NULL): number of tiles of the box that pass the tile cull of xpr_tile_bin,
  * i.e. the exact number of pairs the primitive will emit (the binning then
- * needs no counting pass of its own). */
+ * needs no counting pass of its own).  prims->sh may be NULL: the records'
+ * colours are then left 0 and xpr_project_color fills them later (binning and
+ * sorting read only the geometry, so the SH coefficients can still be on
+ * their way to the device while those stages run). */
 int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
                 int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream);
 
@@ -279,6 +282,15 @@ int xpr_render_bwd_views(const float *rec, int64_t n, int32_t n_views, const uin
                          void *stream); /* d_rec[V*n,12] overwritten */
 int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
                           const XprConfig *cfg, const float *d_rec, const XprPrimsGrad *d_prims, void *stream);
+
+/* xpr_project_color: the view-dependent colour of Listing 1 project (the SH
+ * part of compute_color) for records already projected with prims->sh NULL:
+ * for every visible record v * n + i (rec[.,11] != 0), rec[.,6..8] =
+ * max(0, 0.5 + sum_k sh[i,k,:] Y_k(d)), d = unit vector from camera v's centre
+ * to mu[i]; invisible records are not touched.  mu[n,3], sh[n,K,3] (device);
+ * cams: HOST array of n_views cameras (1..16); rec[n_views*n,12] (device). */
+int xpr_project_color(const float *mu, const float *sh, int64_t n, const XprCamera *cams, int32_t n_views,
+                      const XprConfig *cfg, float *rec, void *stream);
 
 /* ---- Fused bin + sort ---------------------------------------------------------
  * xpr_bin_sorted: Sec. 4.2's replicate / assign tile id / cull followed by

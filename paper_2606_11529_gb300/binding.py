@@ -78,6 +78,8 @@ SIGNATURES = {
                                      ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "xpr_project_bwd_views": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), c_i32,
                                       ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_project_color": (c_i32, [c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), c_i32, ctypes.POINTER(XprConfig),
+                                  c_vp, c_vp]),
     "xpr_bin_sorted_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig)]),
     "xpr_bin_sorted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(XprCamera),
                                ctypes.POINTER(XprConfig), c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz,
@@ -166,10 +168,14 @@ def _dev(t):
 
 
 def _prims(mu, scale, quat, opacity, sh) -> XprPrims:
+    """sh may be None (geometry-only projection)."""
     for name, t in (("mu", mu), ("scale", scale), ("quat", quat), ("opacity", opacity), ("sh", sh)):
+        if t is None and name == "sh":
+            continue
         if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
             raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
-    return XprPrims(mu.data_ptr(), scale.data_ptr(), quat.data_ptr(), opacity.data_ptr(), sh.data_ptr())
+    return XprPrims(mu.data_ptr(), scale.data_ptr(), quat.data_ptr(), opacity.data_ptr(),
+                    None if sh is None else sh.data_ptr())
 
 
 def tiles_of(cam, cfg):
@@ -393,6 +399,18 @@ def xpr_tile_bin_views(rec, bbox, tile_count, isect_count, order, n, n_views, ca
         I = int(got.value)
         return offsets, tiles[:I], vals[:I], I
     raise XprError(XPR_ERR_CAPACITY, "xpr_tile_bin_views", "capacity retry failed")
+
+
+def xpr_project_color(mu, sh, rec, cams, cfg, stream=None):
+    """Fills rec[V*n, 6:9] (colours of visible records) from the SH coefficients; cams: a camera or a list."""
+    L = load()
+    cams = list(cams) if isinstance(cams, (list, tuple)) else [cams]
+    for name, t in (("mu", mu), ("sh", sh), ("rec", rec)):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_project_color(_ptr(mu), _ptr(sh), mu.shape[0], camera_array(cams), len(cams), ctypes.byref(g),
+                               _ptr(rec), _stream(stream)), "xpr_project_color")
 
 
 def binsort_ok(cam, cfg, n_views=1):

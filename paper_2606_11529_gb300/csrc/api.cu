@@ -88,8 +88,7 @@ int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const Xp
     if (s) return s;
     if ((s = check_n(n))) return s;
     if (n == 0) return XPR_OK;
-    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh || !rec || !bbox ||
-        !tile_count)
+    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !rec || !bbox || !tile_count)
         return fail(XPR_ERR_INVALID, "xpr_project: NULL pointer");
     if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(bbox, 16))
         return fail(XPR_ERR_INVALID, "xpr_project: quat, rec and bbox must be 16-byte aligned");
@@ -265,8 +264,7 @@ int xpr_project_views(const XprPrims *prims, int64_t n, const XprCamera *cams, i
     for (int v = 0; v < n_views; ++v)
         if ((s = validate_camera_config(cams + v, cfg))) return s;
     if (n == 0) return XPR_OK;
-    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh || !rec || !bbox ||
-        !tile_count)
+    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !rec || !bbox || !tile_count)
         return fail(XPR_ERR_INVALID, "xpr_project_views: NULL pointer");
     if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(bbox, 16))
         return fail(XPR_ERR_INVALID, "xpr_project_views: quat, rec and bbox must be 16-byte aligned");
@@ -351,6 +349,18 @@ int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cam
     if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_rec, 16))
         return fail(XPR_ERR_INVALID, "xpr_project_bwd_views: quat and d_rec must be 16-byte aligned");
     return launch_project_bwd_views(*prims, n, cams, n_views, *cfg, d_rec, *d_prims, as_stream(stream));
+}
+
+int xpr_project_color(const float *mu, const float *sh, int64_t n, const XprCamera *cams, int32_t n_views,
+                      const XprConfig *cfg, float *rec, void *stream) {
+    int s = check_views(n_views, n);
+    if (s) return s;
+    if (!cams) return fail(XPR_ERR_INVALID, "xpr_project_color: NULL cameras");
+    for (int v = 0; v < n_views; ++v)
+        if ((s = validate_camera_config(cams + v, cfg))) return s;
+    if (n == 0) return XPR_OK;
+    if (!mu || !sh || !rec) return fail(XPR_ERR_INVALID, "xpr_project_color: NULL pointer");
+    return launch_project_color_views(mu, sh, n, cams, n_views, *cfg, rec, as_stream(stream));
 }
 
 size_t xpr_bin_sorted_workspace(int64_t n, int32_t n_views, const XprCamera *cam, const XprConfig *cfg) {

@@ -245,24 +245,32 @@ struct CamSet {
 };
 
 // K1 for one view: writes rec / bbox / tile count of record `out` and returns the cull data.
+// View-dependent colour (before the clamp at 0): 0.5 + sum_k sh_k Y_k(d), d = unit vector from the
+// camera centre to the mean.
 template <int DEG>
-__device__ __forceinline__ void project_view(const Params &P, const float *shi, int64_t out,
-                                             const XprCamera &cam, const XprConfig &cfg, float *__restrict__ rec,
-                                             int4 *__restrict__ bbox, int *__restrict__ tcount, CullData &cd,
-                                             int4 &bb, int &area) {
+__device__ __forceinline__ void sh_colour(const Params &P, const float *shi, const Cam &k, float *col) {
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const Cam k = make_cam(cam, cfg);
     const float vx = P.m[0] - k.cpos[0], vy = P.m[1] - k.cpos[1], vz = P.m[2] - k.cpos[2];
     const float vinv = rsqrtf(vx * vx + vy * vy + vz * vz);
     float Y[K];
     sh_basis<DEG>(vx * vinv, vy * vinv, vz * vinv, Y);
-    float col[3] = {0.5f, 0.5f, 0.5f};
+    col[0] = col[1] = col[2] = 0.5f;
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
         col[0] += shi[3 * kk] * Y[kk];
         col[1] += shi[3 * kk + 1] * Y[kk];
         col[2] += shi[3 * kk + 2] * Y[kk];
     }
+}
+
+template <int DEG>
+__device__ __forceinline__ void project_view(const Params &P, const float *shi, int64_t out,
+                                             const XprCamera &cam, const XprConfig &cfg, float *__restrict__ rec,
+                                             int4 *__restrict__ bbox, int *__restrict__ tcount, CullData &cd,
+                                             int4 &bb, int &area) {
+    const Cam k = make_cam(cam, cfg);
+    float col[3] = {0.f, 0.f, 0.f};
+    if (shi) sh_colour<DEG>(P, shi, k, col);
     Geo G;
     geometry(P, k, cfg.cov_dilation, G);
     const float z = G.mc[2];
@@ -302,12 +310,26 @@ constexpr int kProjWarps = 4;
 
 // One thread per primitive and all views; each warp first stages its 32 primitives' SH
 // coefficients in shared memory with coalesced loads (a thread's own row is 3K floats long).
+// Stages the SH coefficients of a warp's 32 primitives (from base) in shared memory, coalesced.
 template <int DEG>
+__device__ __forceinline__ void stage_sh(const float *__restrict__ sh, int64_t base, int nv, float *ssh) {
+    constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
+    constexpr int LD = sh_ld<DEG>();
+    const int lane = threadIdx.x & 31;
+    const float *gs = sh + base * KC;
+    for (int e = lane; e < nv * KC; e += 32) {
+        const int pi = e / KC;
+        ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
+    }
+    __syncwarp();
+}
+
+// COLOR = false (sh NULL): geometry only, colours left 0 for xpr_project_color to fill.
+template <int DEG, bool COLOR>
 __global__ void __launch_bounds__(kProjWarps * 32) project_fwd_kernel(
     const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
     float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount, int *__restrict__ isect_count) {
-    constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_fwd[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -315,12 +337,7 @@ __global__ void __launch_bounds__(kProjWarps * 32) project_fwd_kernel(
     if (base >= n) return;
     const int nv = (int)min((int64_t)32, n - base);
     float *ssh = s_fwd + (size_t)w * 32 * LD;
-    const float *gs = sh + base * KC;
-    for (int e = lane; e < nv * KC; e += 32) {
-        const int pi = e / KC;
-        ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
-    }
-    __syncwarp();
+    if (COLOR) stage_sh<DEG>(sh, base, nv, ssh);
     const int64_t i = base + lane;
     const bool valid = i < n;
     Params P = {};
@@ -330,11 +347,44 @@ __global__ void __launch_bounds__(kProjWarps * 32) project_fwd_kernel(
         int4 bb = make_int4(0, 0, 0, 0);
         int area = 0;
         const int64_t out = (int64_t)v * n + i;
-        if (valid) project_view<DEG>(P, ssh + lane * LD, out, cs.cam[v], cfg, rec, bbox, tcount, cd, bb, area);
+        if (valid)
+            project_view<DEG>(P, COLOR ? ssh + lane * LD : nullptr, out, cs.cam[v], cfg, rec, bbox, tcount, cd, bb,
+                              area);
         if (isect_count) {  // exact number of kept (primitive, tile) pairs, counted with the binning's cull
             const int cnt = count_kept_tiles(cd, bb, area, make_grid(cs.cam[v], cfg));
             if (valid) isect_count[out] = cnt;
         }
+    }
+}
+
+// The colours of records already projected without them (rec[6..8] of every visible record).
+template <int DEG>
+__global__ void __launch_bounds__(kProjWarps * 32) project_color_kernel(const float *__restrict__ mu,
+                                                                        const float *__restrict__ sh, int64_t n,
+                                                                        CamSet cs, XprConfig cfg,
+                                                                        float *__restrict__ rec) {
+    constexpr int LD = sh_ld<DEG>();
+    extern __shared__ float s_col[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * kProjWarps + w) * 32;
+    if (base >= n) return;
+    const int nv = (int)min((int64_t)32, n - base);
+    float *ssh = s_col + (size_t)w * 32 * LD;
+    stage_sh<DEG>(sh, base, nv, ssh);
+    const int64_t i = base + lane;
+    if (i >= n) return;
+    Params P = {};
+    P.m[0] = mu[3 * i];
+    P.m[1] = mu[3 * i + 1];
+    P.m[2] = mu[3 * i + 2];
+    for (int v = 0; v < cs.n_views; ++v) {
+        float *r = rec + ((size_t)v * n + i) * XPR_REC_FLOATS;
+        if (r[11] == 0.f) continue;  // invisible: colour stays 0
+        float col[3];
+        sh_colour<DEG>(P, ssh + lane * LD, make_cam(cs.cam[v], cfg), col);
+        r[6] = fmaxf(col[0], 0.f);
+        r[7] = fmaxf(col[1], 0.f);
+        r[8] = fmaxf(col[2], 0.f);
     }
 }
 
@@ -607,11 +657,31 @@ int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams
     const int tpb = kProjWarps * 32;
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
-    XPR_DEG_DISPATCH(DEG, project_fwd_kernel<DEG><<<blocks, tpb,
-                                                     (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
-                              p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, rec,
-                              reinterpret_cast<int4 *>(bbox), tc, isect_count));
+    if (p.sh) {
+        XPR_DEG_DISPATCH(DEG, project_fwd_kernel<DEG, true><<<blocks, tpb,
+                                                               (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float),
+                                                               st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs,
+                                                                     cfg, rec, reinterpret_cast<int4 *>(bbox), tc,
+                                                                     isect_count));
+    } else {
+        XPR_DEG_DISPATCH(DEG, project_fwd_kernel<DEG, false><<<blocks, tpb, 0, st>>>(
+                                  p.mu, p.scale, p.quat, p.opacity, nullptr, n, cs, cfg, rec,
+                                  reinterpret_cast<int4 *>(bbox), tc, isect_count));
+    }
     XPR_LAUNCH_CHECK("project_fwd_kernel");
+    return XPR_OK;
+}
+
+int launch_project_color_views(const float *mu, const float *sh, int64_t n, const XprCamera *cams, int n_views,
+                               const XprConfig &cfg, float *rec, cudaStream_t st) {
+    if (n == 0 || n_views == 0) return XPR_OK;
+    const int tpb = kProjWarps * 32;
+    const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
+    const CamSet cs = make_camset(cams, n_views);
+    XPR_DEG_DISPATCH(DEG, project_color_kernel<DEG><<<blocks, tpb,
+                                                       (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
+                              mu, sh, n, cs, cfg, rec));
+    XPR_LAUNCH_CHECK("project_color_kernel");
     return XPR_OK;
 }
 

@@ -46,6 +46,8 @@ int launch_project_bwd(const XprPrims &p, int64_t n, const XprCamera &cam, const
                        const float *d_rec, const XprPrimsGrad &g, cudaStream_t st);
 int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
                              float *rec, int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st);
+int launch_project_color_views(const float *mu, const float *sh, int64_t n, const XprCamera *cams, int n_views,
+                               const XprConfig &cfg, float *rec, cudaStream_t st);
 int launch_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
                              const float *d_rec, const XprPrimsGrad &g, cudaStream_t st);
 int launch_render_fwd_views(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,

@@ -30,6 +30,11 @@ class Workspace:
         self.last_isect = 0
         self.bufs = {}
         self.fused = fused  # xpr_bin_sorted (True) or xpr_tile_bin + xpr_sort_tiles (False)
+        self.sh_events = None  # set by a caller whose SH copy is still in flight (consumed by one forward)
+
+    def take_sh_events(self):
+        ev, self.sh_events = self.sh_events, None
+        return ev
 
     def scratch(self, name, nbytes, device):
         t = self.bufs.get(name)
@@ -97,10 +102,12 @@ class Frame:
 
 
 def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
-                  timers=None, fused: bool = False, keep_sorted_tiles: bool = False) -> Frame:
+                  timers=None, fused: bool = False, keep_sorted_tiles: bool = False, sh_events=None) -> Frame:
     """The forward stages, each one C-ABI call: project, depth order, then either the key path
     (xpr_tile_bin emitting u32 tile ids in depth order + xpr_sort_tiles, the default) or the fused
-    bin + sort (xpr_bin_sorted), then render.  Both give the same sorted lists bit for bit."""
+    bin + sort (xpr_bin_sorted), then render.  Both give the same sorted lists bit for bit.
+    sh_events: events of an SH copy still in flight; then the projection runs without colours,
+    and the stream waits for the events just before xpr_project_color fills them in."""
     L = B.load()
     tm = timers or _NO_TIMERS
     ccam, ccfg = B.make_camera(cam), B.make_config(cfg)
@@ -109,7 +116,9 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     dev = mu.device
     ws = ws or Workspace()
     tm.start("project", stream)
-    out = B.xpr_project(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream, with_isect_count=not fused)
+    deferred = sh_events is not None
+    out = B.xpr_project(mu, scale, quat, opacity, None if deferred else sh, ccam, ccfg, stream=stream,
+                        with_isect_count=not fused)
     rec, bbox, tc = out[:3]
     cnt = out[3] if len(out) > 3 else None
     tm.stop("project", stream)
@@ -140,6 +149,13 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
                                           want_tiles=keep_sorted_tiles)
         tm.stop("sort", stream)
     ws.last_isect = I
+    if deferred:
+        cur = stream if stream is not None else torch.cuda.current_stream()
+        for e in (sh_events if isinstance(sh_events, (list, tuple)) else [sh_events]):
+            cur.wait_event(e)
+        tm.start("color", stream)
+        B.xpr_project_color(mu, sh, rec, ccam, ccfg, stream=stream)
+        tm.stop("color", stream)
     tm.start("render_fwd", stream)
     image, t_final, n_contrib = B.xpr_render_fwd(rec, vs, ranges, ccam, ccfg, stream=stream)
     tm.stop("render_fwd", stream)
@@ -151,7 +167,8 @@ class SplatFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, mu, scale, quat, opacity, sh, cam, cfg, ws, timers):
-        fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, timers=timers, fused=ws.fused)
+        fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, timers=timers, fused=ws.fused,
+                           sh_events=ws.take_sh_events())
         ctx.save_for_backward(mu, scale, quat, opacity, sh, fr.rec, fr.vals_sorted, fr.ranges, fr.t_final,
                               fr.n_contrib)
         ctx.cam, ctx.cfg, ctx.timers = cam, cfg, timers
@@ -174,6 +191,35 @@ class SplatFunction(torch.autograd.Function):
 def render(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, timers: StageTimers | None = None):
     """Differentiable render of one view: returns image [3, H, W]."""
     return SplatFunction.apply(mu, scale, quat, opacity, sh, cam, cfg, ws or Workspace(), timers)
+
+
+class Uploader:
+    """Host -> device copies of pinned parameter tensors on a copy stream, off the compute stream.
+
+    `start(dst, src, after=None)` enqueues the copies (after the compute stream's earlier work, and
+    after the events in `after`) and returns an event that fires when they are done; `upload`
+    does the same and makes the current stream wait.  The splatting forward only needs the SH
+    coefficients for the colours, after binning and sorting: giving it the SH copy's event
+    (``Workspace.sh_events``) lets those stages run while the coefficients are still in flight."""
+
+    def __init__(self):
+        self.stream = torch.cuda.Stream()
+
+    def start(self, dst, src, after=()):
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)  # earlier compute is done with the destination buffers
+        for e in after:
+            self.stream.wait_event(e)
+        with torch.cuda.stream(self.stream):
+            for d, h in zip(dst, src):
+                d.copy_(h, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        return ev
+
+    def upload(self, dst, src):
+        ev = self.start(dst, src)
+        torch.cuda.current_stream().wait_event(ev)
 
 
 def scene_to_device(scene, device="cuda"):

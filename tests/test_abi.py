@@ -119,3 +119,13 @@ def test_bin_sorted_host_checks(lib):
     # every valid camera (width <= 32768, 8x8 tiles: 4096 columns) fits the per-band counters
     widest, cfg8 = _cam_cfg(width=32768, tile_w=8, tile_h=8)
     assert binding.binsort_ok(widest, cfg8) and binding.binsort_ok(cam, cfg)
+
+
+def test_project_color_host_checks(lib):
+    from paper_2606_11529_gb300 import binding
+    cam, cfg = _cam_cfg()
+    cams = (binding.XprCamera * 1)(cam)
+    s = lib.xpr_project_color(None, 256, 10, cams, 1, ctypes.byref(cfg), 256, None)
+    assert s == binding.XPR_ERR_INVALID and b"NULL" in lib.xpr_last_error()
+    s = lib.xpr_project_color(256, 256, 10, cams, 0, ctypes.byref(cfg), 256, None)
+    assert s == binding.XPR_ERR_INVALID

@@ -185,3 +185,31 @@ def test_headline_workload_sampled_pixels_and_gradients(oracle):
     g = oracle.project_bwd(*sc.arrays(), cam, cfg, d_rec)
     for name, p in zip(NAMES, P):
         assert rel_err(p.grad.cpu().numpy(), g[name]) < GRAD_TOL, name
+
+
+def test_deferred_colour_equals_one_pass():
+    # projection without colours while the SH coefficients are still being copied, then
+    # xpr_project_color: the same image bit for bit, and the same gradients
+    sc = scenes.clustered_scene(30_000, seed=11, n_centers=40, width=320, height=180, focal=320.0, sh_degree=3)
+    cam = scenes.pinhole(320, 180, 320.0, scenes.yaw_view(3.0, (0.02, 0.0, 0.05)))
+    cfg = scenes.RenderConfig(sh_degree=3, bg=(0.2, 0.1, 0.0))
+    P = [t.requires_grad_(True) for t in R.scene_to_device(sc)]
+    ref = R.forward_frame(*[p.detach() for p in P], cam, cfg).image
+    host_sh = torch.from_numpy(sc.sh).pin_memory()
+    dev_sh = torch.zeros_like(P[4].detach())
+    up = R.Uploader()
+    ev = up.start([dev_sh], [host_sh])
+    fr = R.forward_frame(*[p.detach() for p in P[:4]], dev_sh, cam, cfg, sh_events=ev)
+    assert torch.equal(fr.image, ref)
+    w = torch.from_numpy(np.random.default_rng(4).normal(size=tuple(ref.shape)).astype(np.float32)).cuda()
+    (R.render(*P, cam, cfg) * w).sum().backward()
+    g_ref = [p.grad.clone() for p in P]
+    for p in P:
+        p.grad = None
+    ws = R.Workspace()
+    with torch.no_grad():
+        P[4].zero_()
+    ws.sh_events = up.start([P[4].detach()], [host_sh])
+    (R.render(*P, cam, cfg, ws) * w).sum().backward()
+    for a, b in zip(g_ref, P):
+        assert rel_err(b.grad.cpu().numpy(), a.cpu().numpy()) < 1e-5
