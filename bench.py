@@ -264,6 +264,14 @@ def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     ptrace = SV.make_trace(n_requests + warmup, rate_hz=200.0, seed=0)
     SV.run_plain(resident, cfg, ptrace, srv)
     plain = SV.latency_stats(ptrace, warmup)
+    # the same comparison at twice the rate, where the queue of the plain path builds up
+    n_hi = max(n_requests // 2, 100)
+    htrace = SV.make_trace(n_hi + warmup // 2, rate_hz=400.0, seed=2)
+    srv.run(htrace)
+    hi = {"rate_hz": 400.0, "requests": n_hi, "server": SV.latency_stats(htrace, warmup // 2)}
+    hptrace = SV.make_trace(n_hi + warmup // 2, rate_hz=400.0, seed=2)
+    SV.run_plain(resident, cfg, hptrace, srv)
+    hi["plain_queue"] = SV.latency_stats(hptrace, warmup // 2)
     n_cap = max(n_requests // 4, 100)
     capped = SV.Server(resident, cfg, pool_bytes=int(cap_gb * 2 ** 30), slots=3)
     capped.calib = srv.calib
@@ -277,7 +285,7 @@ def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
                         "512x512 / 1280x720 / 1920x1080 (f = width), forward only, image delivered to pinned host",
             "requests": n_requests, "warmup_requests": warmup, "slots": 3,
             "p50_ms": ours["p50_ms"], "p99_ms": ours["p99_ms"], "views_per_s": ours["views_per_s"],
-            "server": ours, "plain_queue": plain, "capped_pool": cst,
+            "server": ours, "plain_queue": plain, "capped_pool": cst, "rate_400": hi,
             "resident_gb": round(sum(sum(t.numel() * 4 for t in s) for s in resident) / 2 ** 30, 3),
             "scene_gen_s": round(gen_s, 1)}
 

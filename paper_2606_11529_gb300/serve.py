@@ -255,18 +255,28 @@ class Server:
         return footprint_bytes(n, req.width, req.height, self.n_isect_estimate(req), self.cfg)
 
     def execute(self, batch: list[Request], stream):
+        """One view: the plain per-stage path; several views of one scene and size: one launch per
+        stage for all of them (the batched form).  Both give the same image bit for bit."""
         import torch
         from . import batched as BT
+        from . import render as R
         P = self.scenes[batch[0].scene]
         with torch.cuda.stream(stream):
-            ws = BT.ViewsWorkspace()
-            ws.last_isect = int(sum(self.n_isect_estimate(r) for r in batch) / 1.25)
-            fr = BT.forward_views(*P, [camera_of(r) for r in batch], self.cfg, ws)
-            if self.deliver_host:
-                out = torch.empty(tuple(fr.image.shape), dtype=fr.image.dtype, pin_memory=True)
-                out.copy_(fr.image, non_blocking=True)
+            if len(batch) == 1:
+                ws = R.Workspace()
+                ws.last_isect = int(self.n_isect_estimate(batch[0]) / 1.25)
+                fr = R.forward_frame(*P, camera_of(batch[0]), self.cfg, ws, stream=stream)
+                img = fr.image.unsqueeze(0)
             else:
-                out = fr.image
+                ws = BT.ViewsWorkspace()
+                ws.last_isect = int(sum(self.n_isect_estimate(r) for r in batch) / 1.25)
+                fr = BT.forward_views(*P, [camera_of(r) for r in batch], self.cfg, ws, stream=stream)
+                img = fr.image
+            if self.deliver_host:
+                out = torch.empty(tuple(img.shape), dtype=img.dtype, pin_memory=True)
+                out.copy_(img, non_blocking=True)
+            else:
+                out = img
             stream.synchronize()
         for v, r in enumerate(batch):
             r.image = out[v]
@@ -285,7 +295,7 @@ class Server:
                     batch = self.sched.take_batch(time.perf_counter() - t0)
                     if batch:
                         break
-                    self.cv.wait(0.005)
+                    self.cv.wait(0.0005)
                 if not batch:
                     return
             try:
