@@ -67,6 +67,15 @@ def lib():
         L.oracle_sh_basis.argtypes = [ctypes.c_int, _F64P, _F64P, _F64P]
         L.oracle_cull_one.argtypes = [_F64P, ctypes.c_int, ctypes.c_int, _F64P, _F64P, ctypes.c_int]
         L.oracle_cull_one.restype = ctypes.c_int
+        L.oracle_project_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
+                                        _F64P, _I32P, _I32P, _F64P, _F64P]
+        L.oracle_render_tiles_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _U32P, _I32P, _F64P, _F64P,
+                                             ctypes.c_double, _F64P, _F64P, _I32P, _I32P]
+        L.oracle_render_pixels_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _I32P, ctypes.c_int64, _F64P, _F64P,
+                                              ctypes.c_double, _F64P, _F64P, _I32P]
+        L.oracle_ut_response.argtypes = [_F64P, _F64P]
+        L.oracle_ut_response.restype = ctypes.c_double
+        L.oracle_pixel_ray.argtypes = [ctypes.c_int, ctypes.c_int, _F64P, _F64P]
         L.oracle_abi_version.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -92,10 +101,10 @@ def cam_array(cam) -> np.ndarray:
 
 
 def cfg_array(cfg) -> np.ndarray:
-    """[tile_w, tile_h, alpha_t, alpha_max, t_eps, dilation, clip, sh_degree, bg(3)]."""
+    """[tile_w, tile_h, alpha_t, alpha_max, t_eps, dilation, clip, sh_degree, bg(3), method]."""
     return np.array([cfg.tile_w, cfg.tile_h, _f32v(cfg.alpha_thresh), _f32v(cfg.alpha_max), _f32v(cfg.t_eps),
                      _f32v(cfg.cov_dilation), _f32v(cfg.clip_factor), cfg.sh_degree,
-                     *[_f32v(b) for b in cfg.bg]], np.float64)
+                     *[_f32v(b) for b in cfg.bg], getattr(cfg, "method", 0)], np.float64)
 
 
 def tiles_of(cam, cfg):
@@ -276,6 +285,90 @@ def pipeline_tiled(scene, cam, cfg, delta: float = 0.0):
     out = render_tiles(pr["rec"], vals, ranges, cam, cfg, delta)
     out.update(proj=pr, keys=keys, vals=vals, ranges=ranges)
     return out
+
+
+# --------------------------------------------------------------------------- 3DGUT
+
+def project_ut(mu, scale, quat, opac, sh, cam, cfg):
+    """3DGUT projection (unscented transform).  Returns rec[n,12] (3DGS layout with the UT mean and
+    conic, Mip-Splatting opacity), sd[n,16] (ro_c, M row-major, o', rgb), bbox, tc, pre, cov0."""
+    mu, scale, quat, opac, sh = map(_f64, (mu, scale, quat, opac, sh))
+    n = mu.shape[0]
+    rec = np.zeros((n, 12))
+    sd = np.zeros((n, 16))
+    bbox = np.zeros((n, 4), np.int32)
+    tc = np.zeros(n, np.int32)
+    pre = np.zeros((n, 4))
+    cov0 = np.zeros((n, 3))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_project_ut(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P),
+                            _p(sh, _F64P), _p(ca, _F64P), _p(fa, _F64P), _p(rec, _F64P), _p(sd, _F64P),
+                            _p(bbox, _I32P), _p(tc, _I32P), _p(pre, _F64P), _p(cov0, _F64P))
+    return dict(rec=rec, sd=sd, bbox=bbox, tc=tc, pre=pre, cov0=cov0)
+
+
+def project_ut_scene(scene, cam, cfg):
+    return project_ut(scene.mu, scene.scale, scene.quat, scene.opacity, scene.sh, cam, cfg)
+
+
+def render_tiles_ut(rec, sd, vals, ranges, cam, cfg, delta: float = 0.0):
+    rec, sd = _f64(rec), _f64(sd)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    H, W = cam.height, cam.width
+    image = np.zeros((3, H, W))
+    tfin = np.zeros((H, W))
+    nc = np.zeros((H, W), np.int32)
+    band = np.zeros((H, W), np.int32)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_tiles_ut(rec.shape[0], _p(rec, _F64P), _p(sd, _F64P), _p(vv, _U32P), _p(ranges, _I32P),
+                                 _p(ca, _F64P), _p(fa, _F64P), delta, _p(image, _F64P), _p(tfin, _F64P),
+                                 _p(nc, _I32P), _p(band, _I32P))
+    return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool))
+
+
+def render_pixels_ut(rec, sd, pix, cam, cfg, delta: float = 0.0):
+    """Every visible primitive (depth order) at the listed pixels, no tiles."""
+    rec, sd = _f64(rec), _f64(sd)
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
+    m = pix.shape[0]
+    color = np.zeros((m, 3))
+    tfin = np.zeros(m)
+    band = np.zeros(m, np.int32)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_pixels_ut(rec.shape[0], _p(rec, _F64P), _p(sd, _F64P), _p(pix, _I32P), m, _p(ca, _F64P),
+                                  _p(fa, _F64P), delta, _p(color, _F64P), _p(tfin, _F64P), _p(band, _I32P))
+    return dict(color=color, t_final=tfin, band=band.astype(bool))
+
+
+def ut_response(sd_row, rd) -> float:
+    s, r = _f64(sd_row), _f64(rd)
+    return float(lib().oracle_ut_response(_p(s, _F64P), _p(r, _F64P)))
+
+
+def pixel_ray(x, y, cam):
+    rd = np.zeros(3)
+    ca = cam_array(cam)
+    lib().oracle_pixel_ray(int(x), int(y), _p(ca, _F64P), _p(rd, _F64P))
+    return rd
+
+
+def pipeline_tiled_ut(scene_arrays, cam, cfg, delta: float = 0.0):
+    """FP64 3DGUT pipeline: UT projection -> bin (FP64 cull, ray-offset tile bounds) -> sort ->
+    per-tile ray walk.  scene_arrays = (mu, scale, quat, opacity, sh)."""
+    pr = project_ut(*scene_arrays, cam, cfg)
+    Wt, Ht = tiles_of(cam, cfg)
+    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False)
+    keys, vals, ranges = sort_pairs(keys, vals, Wt * Ht)
+    out = render_tiles_ut(pr["rec"], pr["sd"], vals, ranges, cam, cfg, delta)
+    out.update(proj=pr, keys=keys, vals=vals, ranges=ranges)
+    return out
+
+
+def loss_tiled_ut(scene_arrays, cam, cfg, w):
+    """sum(w * image) of the FP64 3DGUT pipeline."""
+    return float((w * pipeline_tiled_ut(scene_arrays, cam, cfg)["image"]).sum())
 
 
 def loss_brute(scene_arrays, cam, cfg, w):

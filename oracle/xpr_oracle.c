@@ -59,6 +59,7 @@ typedef struct {
     double at, amax, teps, dil, clip;
     int deg;
     double bg[3];
+    int method; /* 0 = 3DGS (EWA), 1 = 3DGUT (unscented transform, ray evaluation) */
 } ocfg;
 
 static ocam read_cam(const double *c) {
@@ -87,6 +88,7 @@ static ocfg read_cfg(const double *c) {
     g.bg[0] = c[8];
     g.bg[1] = c[9];
     g.bg[2] = c[10];
+    g.method = (int)c[11];
     return g;
 }
 
@@ -477,7 +479,7 @@ static rowcull32 rowcull32_make(const float *R) {
  * W - 1): k w + w - 1 >= xa  <=>  k >= ceil((xa + 1) / w) - 1, and k w <= xb
  * <=> k <= floor(xb / w); a span starting right of the image or ending left
  * of it keeps nothing. */
-static int row_tiles_f32(const rowcull32 *r, float y0, float y1, int w, int W, int *ka, int *kb) {
+static int row_tiles_f32(const rowcull32 *r, float y0, float y1, int w, int W, int ext, int *ka, int *kb) {
     if (!r->ok) return 0;
     float lo = INFINITY, hi = -INFINITY;
     if (r->yl >= y0 && r->yl <= y1) lo = r->mx - r->ex;
@@ -501,9 +503,9 @@ static int row_tiles_f32(const rowcull32 *r, float y0, float y1, int w, int W, i
         }
     }
     if (!(lo <= hi)) return 0;
-    if (lo > (float)(W - 1) || hi < 0.0f) return 0;
+    if (lo > (float)(W - 1 + ext) || hi < 0.0f) return 0;
     float iw = 1.0f / (float)w;
-    float t = lo + 1.0f;
+    float t = lo + (float)(1 - ext); /* tile k is kept iff k w + w - 1 + ext >= xa */
     t = t * iw;
     float u = hi * iw;
     t = fmaxf(t, -1.0f);
@@ -513,11 +515,15 @@ static int row_tiles_f32(const rowcull32 *r, float y0, float y1, int w, int W, i
     return *ka <= *kb;
 }
 
+/* 3DGUT (method 1) extends the max bounds by one: its pixel centres sit at +0.5, so tile
+ * [x0, x1] of pixel indices covers [x0, x1 + 1] in the continuous coordinates of its means. */
 static void tile_bounds(int tx, int ty, const ocam *cam, const ocfg *cfg, double *b) {
     int x0 = tx * cfg->tw, y0 = ty * cfg->th;
     int x1 = x0 + cfg->tw - 1, y1 = y0 + cfg->th - 1;
     if (x1 > cam->W - 1) x1 = cam->W - 1;
     if (y1 > cam->H - 1) y1 = cam->H - 1;
+    x1 += cfg->method == 1;
+    y1 += cfg->method == 1;
     b[0] = x0;
     b[1] = y0;
     b[2] = x1;
@@ -538,7 +544,7 @@ int oracle_cull_one(const double *rec, int tx, int ty, const double *camv, const
         for (int k = 0; k < 12; ++k) R[k] = (float)rec[k];
         rowcull32 rc = rowcull32_make(R);
         int ka, kb;
-        if (!row_tiles_f32(&rc, (float)b[1], (float)b[3], cfg.tw, cam.W, &ka, &kb)) return 0;
+        if (!row_tiles_f32(&rc, (float)b[1], (float)b[3], cfg.tw, cam.W, cfg.method == 1, &ka, &kb)) return 0;
         return tx >= ka && tx <= kb;
     }
     return cull_f64(rec[0], rec[1], rec[2], rec[3], rec[4], rec[10], b[0], b[1], b[2], b[3]);
@@ -585,7 +591,7 @@ int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const int
                 const float *R = rec32 + 12 * i;
                 if (ty != row_ty) {  /* one span per tile row */
                     row_ty = ty;
-                    if (!row_tiles_f32(&rc, (float)b[1], (float)b[3], cfg.tw, cam.W, &ka, &kb)) {
+                    if (!row_tiles_f32(&rc, (float)b[1], (float)b[3], cfg.tw, cam.W, cfg.method == 1, &ka, &kb)) {
                         ka = 0;
                         kb = -1;
                     }
@@ -1074,4 +1080,271 @@ void oracle_project_bwd(int64_t n, const double *mu, const double *scale, const 
     }
 }
 
-int oracle_abi_version(void) { return 1; }
+/* ------------------------------------------------------------------------ */
+/* 3DGUT (Appendix "Implementation of XPR-3DGUT"; Listing 3DGUT).           */
+/* Projection by the unscented transform: 2n+1 = 7 sigma points of the 3D    */
+/* Gaussian, X_0 = mu, X_{+-k} = mu +- sqrt(n + lambda) L_k with L = R S    */
+/* (Sigma = L L^T), lambda = alpha^2 (n + kappa) - n, alpha = 1, beta = 2,  */
+/* kappa = 0 (lambda = 0); weights w^m_0 = lambda/(n+lambda) = 0,         */
+/* w^c_0 = w^m_0 + 1 - alpha^2 + beta = 2, w_i = 1/(2(n+lambda)) = 1/6.    */
+/* Each point goes through the pinhole projection; mu_2D = sum w^m_i p_i,    */
+/* Sigma_2D = sum w^c_i (p_i - mu_2D)(p_i - mu_2D)^T, then the low-pass      */
+/* dilation (+ d I) with the Mip-Splatting opacity o' = o sqrt(det_0/det).   */
+/* Pixel centres are at +0.5: the box uses mu_2D - 0.5, the cull extends the */
+/* tiles' max bounds by one (tile_bounds).  Shader data: the camera centre   */
+/* in the Gaussian's canonical frame, ro_c = M (c - mu), M = S^-1 R^T.       */
+/* Evaluation along the pixel ray r(tau) = c + tau d (Eq. for tau_max):     */
+/* d_c = M d, tau_max = -ro_c.d_c / d_c.d_c, and the largest response is     */
+/* G = exp(-|ro_c + tau_max d_c|^2 / 2) = exp(-(|ro_c|^2 - (ro_c.d_c)^2 /   */
+/* d_c.d_c)/2); valid iff G > 0.0113; alpha = min(alpha_max, o' G).         */
+/* Record: the 12-float layout of 3DGS with the UT mean and conic, o', and   */
+/* ln(o'/alpha_t); shader data sd[16] = ro_c[3], M[9] (row-major), o', rgb. */
+/* ------------------------------------------------------------------------ */
+
+#define UT_VALID 0.0113
+
+typedef struct {
+    double mu2d[2], cov0[3], cov[3], conic[3], det0, det, o, ln_thr, ex, ey, pre[4], mc[3], rgb[3], roc[3], M[9];
+    int bbox[4];
+    int tc, visible;
+} oproj_ut;
+
+static void project_ut_one(const double *mu, const double *s, const double *q, double o, const double *sh,
+                           const ocam *cam, const ocfg *cfg, oproj_ut *P) {
+    memset(P, 0, sizeof(*P));
+    const double *V = cam->V;
+    for (int i = 0; i < 3; ++i) P->mc[i] = V[4 * i] * mu[0] + V[4 * i + 1] * mu[1] + V[4 * i + 2] * mu[2] + V[4 * i + 3];
+    double qn[4], qnorm, R[9];
+    quat_rot(q, qn, &qnorm, R);
+    double cp[3];
+    for (int i = 0; i < 3; ++i) cp[i] = -(V[i] * V[3] + V[4 + i] * V[7] + V[8 + i] * V[11]);
+    /* colour as in 3DGS */
+    double v[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
+    double vl = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double dir[3] = {v[0] / vl, v[1] / vl, v[2] / vl};
+    int K = (cfg->deg + 1) * (cfg->deg + 1);
+    double Y[16];
+    oracle_sh_basis(cfg->deg, dir, Y, NULL);
+    for (int c = 0; c < 3; ++c) {
+        double acc = 0.5;
+        for (int k = 0; k < K; ++k) acc += sh[3 * k + c] * Y[k];
+        P->rgb[c] = acc > 0.0 ? acc : 0.0;
+    }
+    /* shader data */
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) P->M[3 * i + j] = R[3 * j + i] / s[i];
+    for (int i = 0; i < 3; ++i)
+        P->roc[i] = P->M[3 * i] * (cp[0] - mu[0]) + P->M[3 * i + 1] * (cp[1] - mu[1]) + P->M[3 * i + 2] * (cp[2] - mu[2]);
+    if (!(P->mc[2] > cam->z_near)) return;
+    /* sigma points through the projection */
+    const double sq3 = sqrt(3.0);
+    double pts[7][2];
+    for (int k = 0; k < 7; ++k) {
+        double X[3];
+        int a = (k - 1) / 2;
+        double sgn = (k == 0) ? 0.0 : ((k % 2) ? 1.0 : -1.0);
+        for (int i = 0; i < 3; ++i) X[i] = mu[i] + (k == 0 ? 0.0 : sgn * sq3 * s[a] * R[3 * i + a]);
+        double pc[3];
+        for (int i = 0; i < 3; ++i) pc[i] = V[4 * i] * X[0] + V[4 * i + 1] * X[1] + V[4 * i + 2] * X[2] + V[4 * i + 3];
+        if (!(pc[2] > cam->z_near)) return; /* a sigma point behind the near plane: footprint undefined */
+        pts[k][0] = cam->fx * pc[0] / pc[2] + cam->cx;
+        pts[k][1] = cam->fy * pc[1] / pc[2] + cam->cy;
+    }
+    const double wm[7] = {0.0, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+    const double wc[7] = {2.0, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+    for (int k = 0; k < 7; ++k) {
+        P->mu2d[0] += wm[k] * pts[k][0];
+        P->mu2d[1] += wm[k] * pts[k][1];
+    }
+    for (int k = 0; k < 7; ++k) {
+        double dx = pts[k][0] - P->mu2d[0], dy = pts[k][1] - P->mu2d[1];
+        P->cov0[0] += wc[k] * dx * dx;
+        P->cov0[1] += wc[k] * dx * dy;
+        P->cov0[2] += wc[k] * dy * dy;
+    }
+    P->det0 = P->cov0[0] * P->cov0[2] - P->cov0[1] * P->cov0[1];
+    P->cov[0] = P->cov0[0] + cfg->dil;
+    P->cov[1] = P->cov0[1];
+    P->cov[2] = P->cov0[2] + cfg->dil;
+    P->det = P->cov[0] * P->cov[2] - P->cov[1] * P->cov[1];
+    if (!(P->det > 0.0)) return;
+    P->o = o * sqrt((P->det0 > 0.0 ? P->det0 : 0.0) / P->det);
+    if (!(P->o > cfg->at)) return; /* strict for 3DGUT (its projection listing), unlike 3DGS */
+    P->conic[0] = P->cov[2] / P->det;
+    P->conic[1] = -P->cov[1] / P->det;
+    P->conic[2] = P->cov[0] / P->det;
+    P->ln_thr = log(P->o / cfg->at);
+    P->ex = sqrt(2.0 * P->ln_thr * P->cov[0]);
+    P->ey = sqrt(2.0 * P->ln_thr * P->cov[2]);
+    double r = P->ex > P->ey ? P->ex : P->ey;
+    int Wt = (cam->W + cfg->tw - 1) / cfg->tw, Ht = (cam->H + cfg->th - 1) / cfg->th;
+    /* the box in pixel-index coordinates: mu_2D - 0.5 (ray offset) */
+    P->pre[0] = (P->mu2d[0] - 0.5 - P->ex) / cfg->tw;
+    P->pre[1] = (P->mu2d[1] - 0.5 - P->ey) / cfg->th;
+    P->pre[2] = (P->mu2d[0] - 0.5 + P->ex) / cfg->tw;
+    P->pre[3] = (P->mu2d[1] - 0.5 + P->ey) / cfg->th;
+    P->bbox[0] = (int)clampd(floor(P->pre[0]), 0.0, (double)Wt);
+    P->bbox[1] = (int)clampd(floor(P->pre[1]), 0.0, (double)Ht);
+    P->bbox[2] = (int)clampd(floor(P->pre[2]) + 1.0, 0.0, (double)Wt);
+    P->bbox[3] = (int)clampd(floor(P->pre[3]) + 1.0, 0.0, (double)Ht);
+    int tc = (P->bbox[2] - P->bbox[0]) * (P->bbox[3] - P->bbox[1]);
+    P->visible = (r > 0.0) && (tc > 0);
+    P->tc = P->visible ? tc : 0;
+    if (!P->visible) memset(P->bbox, 0, sizeof(P->bbox));
+}
+
+/* rec[n*12] (3DGS layout: UT mean, conic, o', rgb, depth, ln(o'/a_t), visible), sd[n*16],
+ * bbox[n*4], tc[n]; pre[n*4] and cov0[n*3] (Sigma_2D before the dilation) may be NULL. */
+void oracle_project_ut(int64_t n, const double *mu, const double *scale, const double *quat, const double *opac,
+                       const double *sh, const double *camv, const double *cfgv, double *rec, double *sd,
+                       int32_t *bbox, int32_t *tc, double *pre, double *cov0) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int K = (cfg.deg + 1) * (cfg.deg + 1);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        oproj_ut P;
+        project_ut_one(mu + 3 * i, scale + 3 * i, quat + 4 * i, opac[i], sh + (int64_t)3 * K * i, &cam, &cfg, &P);
+        double *r = rec + 12 * i, *d = sd + 16 * i;
+        memset(r, 0, 12 * sizeof(double));
+        r[9] = P.mc[2];
+        for (int j = 0; j < 3; ++j) d[j] = P.roc[j];
+        for (int j = 0; j < 9; ++j) d[3 + j] = P.M[j];
+        d[12] = P.visible ? P.o : 0.0;
+        for (int j = 0; j < 3; ++j) d[13 + j] = P.visible ? P.rgb[j] : 0.0;
+        if (P.visible) {
+            r[0] = P.mu2d[0];
+            r[1] = P.mu2d[1];
+            r[2] = P.conic[0];
+            r[3] = P.conic[1];
+            r[4] = P.conic[2];
+            r[5] = P.o;
+            r[6] = P.rgb[0];
+            r[7] = P.rgb[1];
+            r[8] = P.rgb[2];
+            r[10] = P.ln_thr;
+            r[11] = 1.0;
+        }
+        for (int j = 0; j < 4; ++j) bbox[4 * i + j] = P.bbox[j];
+        tc[i] = P.tc;
+        if (pre)
+            for (int j = 0; j < 4; ++j) pre[4 * i + j] = P.visible ? P.pre[j] : 0.0;
+        if (cov0)
+            for (int j = 0; j < 3; ++j) cov0[3 * i + j] = P.cov0[j];
+    }
+}
+
+/* pixel_info: the world-space unit ray direction through the centre (x + 0.5, y + 0.5). */
+static void pixel_ray(double x, double y, const ocam *cam, double *rd) {
+    double dc[3] = {(x + 0.5 - cam->cx) / cam->fx, (y + 0.5 - cam->cy) / cam->fy, 1.0};
+    double nl = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
+    for (int i = 0; i < 3; ++i) dc[i] /= nl;
+    const double *V = cam->V; /* R_c2w = R_w2c^T */
+    for (int i = 0; i < 3; ++i) rd[i] = V[i] * dc[0] + V[4 + i] * dc[1] + V[8 + i] * dc[2];
+}
+
+/* largest response of the Gaussian of shader data S along the ray of direction rd */
+static double ut_response(const double *S, const double *rd) {
+    double dcn[3];
+    for (int i = 0; i < 3; ++i) dcn[i] = S[3 + 3 * i] * rd[0] + S[4 + 3 * i] * rd[1] + S[5 + 3 * i] * rd[2];
+    double a = S[0] * dcn[0] + S[1] * dcn[1] + S[2] * dcn[2];
+    double b = dcn[0] * dcn[0] + dcn[1] * dcn[1] + dcn[2] * dcn[2];
+    double tau = -a / b;
+    double e[3] = {S[0] + tau * dcn[0], S[1] + tau * dcn[1], S[2] + tau * dcn[2]};
+    return exp(-0.5 * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]));
+}
+
+double oracle_ut_response(const double *sd, const double *rd) { return ut_response(sd, rd); }
+
+static int walk_ut(const double *rd, const double *rec, const double *sd, const int64_t *list, int len,
+                   const ocfg *cfg, double delta, double C[3], double *Tout, int *last, int *band) {
+    double T = 1.0;
+    C[0] = C[1] = C[2] = 0.0;
+    int nc = 0, bd = 0;
+    *last = 0;
+    for (int k = 0; k < len; ++k) {
+        const double *S = sd + 16 * list[k];
+        double G = ut_response(S, rd);
+        if (fabs(G - UT_VALID) <= delta * UT_VALID) bd = 1;
+        if (!(G > UT_VALID)) continue;
+        double og = S[12] * G;
+        double alpha = og < cfg->amax ? og : cfg->amax;
+        if (fabs(og - cfg->amax) <= delta * cfg->amax) bd = 1;
+        if (fabs(alpha - cfg->at) <= delta * cfg->at) bd = 1;
+        if (alpha < cfg->at) continue;
+        double tt = T * (1.0 - alpha);
+        if (fabs(tt - cfg->teps) <= delta * cfg->teps) bd = 1;
+        if (tt < cfg->teps) break;
+        for (int c = 0; c < 3; ++c) C[c] += S[13 + c] * alpha * T;
+        T = tt;
+        ++nc;
+        *last = k + 1;
+    }
+    (void)rec;
+    for (int c = 0; c < 3; ++c) C[c] += T * cfg->bg[c];
+    *Tout = T;
+    *band = bd;
+    return nc;
+}
+
+/* Per-tile walk of 3DGUT over given lists (as oracle_render_tiles). */
+void oracle_render_tiles_ut(int64_t n, const double *rec, const double *sd, const uint32_t *vals,
+                            const int32_t *ranges, const double *camv, const double *cfgv, double delta,
+                            double *image, double *tfinal, int32_t *ncontrib, int32_t *band) {
+    (void)n;
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
+    int64_t HW = (int64_t)cam.W * cam.H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < Wt * Ht; ++t) {
+        int tx = t % Wt, ty = t / Wt;
+        int s0 = ranges[2 * t], e0 = ranges[2 * t + 1];
+        int len = e0 - s0;
+        int64_t *list = (int64_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int64_t));
+        for (int k = 0; k < len; ++k) list[k] = vals[s0 + k];
+        for (int yy = 0; yy < cfg.th; ++yy)
+            for (int xx = 0; xx < cfg.tw; ++xx) {
+                int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
+                if (x >= cam.W || y >= cam.H) continue;
+                double rd[3], C[3], T;
+                int last, bd;
+                pixel_ray((double)x, (double)y, &cam, rd);
+                walk_ut(rd, rec, sd, list, len, &cfg, delta, C, &T, &last, &bd);
+                int64_t p = (int64_t)y * cam.W + x;
+                for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
+                tfinal[p] = T;
+                ncontrib[p] = last;
+                band[p] = bd;
+            }
+        free(list);
+    }
+}
+
+/* 3DGUT without tiles: every visible primitive (depth order) at every listed pixel. */
+void oracle_render_pixels_ut(int64_t n, const double *rec, const double *sd, const int32_t *pix, int64_t npix,
+                             const double *camv, const double *cfgv, double delta, double *color, double *tfinal,
+                             int32_t *band) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int64_t *order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t m = depth_order(n, rec, order);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < npix; ++p) {
+        double rd[3], C[3], T;
+        int last, bd;
+        pixel_ray((double)pix[2 * p], (double)pix[2 * p + 1], &cam, rd);
+        walk_ut(rd, rec, sd, order, (int)m, &cfg, delta, C, &T, &last, &bd);
+        for (int c = 0; c < 3; ++c) color[3 * p + c] = C[c];
+        tfinal[p] = T;
+        band[p] = bd;
+    }
+    free(order);
+}
+
+void oracle_pixel_ray(int x, int y, const double *camv, double *rd) {
+    ocam cam = read_cam(camv);
+    pixel_ray((double)x, (double)y, &cam, rd);
+}
+
+int oracle_abi_version(void) { return 2; }

@@ -52,6 +52,7 @@ class RenderConfig:
     sh_degree: int = 0
     bg: tuple = (0.0, 0.0, 0.0)
     batch_depth: int = 0  # 0 = kernel default
+    method: int = 0       # 0 = 3DGS (EWA projection), 1 = 3DGUT (unscented transform + ray evaluation)
 
 
 @dataclass
