@@ -70,7 +70,10 @@ def lib():
         L.oracle_project_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                         _F64P, _I32P, _I32P, _F64P, _F64P]
         L.oracle_render_tiles_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _U32P, _I32P, _F64P, _F64P,
-                                             ctypes.c_double, _F64P, _F64P, _I32P, _I32P]
+                                             ctypes.c_double, _F64P, _F64P, _I32P, _I32P, _U64P]
+        L.oracle_render_bwd_tiles_ut.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_project_ut_bwd.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
+                                            _F64P, _F64P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_render_pixels_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _I32P, ctypes.c_int64, _F64P, _F64P,
                                               ctypes.c_double, _F64P, _F64P, _I32P]
         L.oracle_ut_response.argtypes = [_F64P, _F64P]
@@ -321,11 +324,37 @@ def render_tiles_ut(rec, sd, vals, ranges, cam, cfg, delta: float = 0.0):
     tfin = np.zeros((H, W))
     nc = np.zeros((H, W), np.int32)
     band = np.zeros((H, W), np.int32)
+    psig = np.zeros((H, W), np.uint64)
     ca, fa = cam_array(cam), cfg_array(cfg)
     lib().oracle_render_tiles_ut(rec.shape[0], _p(rec, _F64P), _p(sd, _F64P), _p(vv, _U32P), _p(ranges, _I32P),
                                  _p(ca, _F64P), _p(fa, _F64P), delta, _p(image, _F64P), _p(tfin, _F64P),
-                                 _p(nc, _I32P), _p(band, _I32P))
-    return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool))
+                                 _p(nc, _I32P), _p(band, _I32P), _p(psig, _U64P))
+    return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool), pixel_sig=psig)
+
+
+def render_bwd_tiles_ut(sd, vals, ranges, cam, cfg, d_image):
+    """Adjoint of the per-tile 3DGUT walk: d_sd[n,16] = (dro_c, dM, do', drgb)."""
+    sd, d_image = _f64(sd), _f64(d_image)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    d_sd = np.zeros((sd.shape[0], 16))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_bwd_tiles_ut(sd.shape[0], _p(sd, _F64P), _p(vv, _U32P), _p(ranges, _I32P), _p(ca, _F64P),
+                                     _p(fa, _F64P), _p(d_image, _F64P), _p(d_sd, _F64P))
+    return d_sd
+
+
+def project_ut_bwd(mu, scale, quat, opac, sh, cam, cfg, d_sd):
+    """Adjoint of the 3DGUT projection from d_sd[n,16] to the primitive parameters."""
+    mu, scale, quat, opac, sh, d_sd = map(_f64, (mu, scale, quat, opac, sh, d_sd))
+    n = mu.shape[0]
+    dmu, ds, dq, do, dsh = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 4)), np.zeros(n), np.zeros_like(sh)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_project_ut_bwd(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P),
+                                _p(sh, _F64P), _p(ca, _F64P), _p(fa, _F64P), _p(d_sd, _F64P), _p(dmu, _F64P),
+                                _p(ds, _F64P), _p(dq, _F64P), _p(do, _F64P), _p(dsh, _F64P))
+    return dict(mu=dmu, scale=ds, quat=dq, opacity=do, sh=dsh)
 
 
 def render_pixels_ut(rec, sd, pix, cam, cfg, delta: float = 0.0):
@@ -367,8 +396,24 @@ def pipeline_tiled_ut(scene_arrays, cam, cfg, delta: float = 0.0):
 
 
 def loss_tiled_ut(scene_arrays, cam, cfg, w):
-    """sum(w * image) of the FP64 3DGUT pipeline."""
-    return float((w * pipeline_tiled_ut(scene_arrays, cam, cfg)["image"]).sum())
+    """sum(w * image) of the FP64 3DGUT pipeline and a hash of every decision it took (the tile
+    lists and each pixel's gates), to tell a smooth change from a flipped decision."""
+    import hashlib
+    out = pipeline_tiled_ut(scene_arrays, cam, cfg)
+    h = hashlib.sha1()
+    for a in (out["vals"], out["ranges"], out["pixel_sig"]):
+        h.update(np.ascontiguousarray(a).tobytes())
+    return float((w * out["image"]).sum()), h.hexdigest()
+
+
+def grads_tiled_ut(scene_arrays, cam, cfg, d_image):
+    """Analytic FP64 gradients of sum(d_image * image) of the 3DGUT pipeline."""
+    mu, s, q, o, sh = scene_arrays
+    out = pipeline_tiled_ut(scene_arrays, cam, cfg)
+    d_sd = render_bwd_tiles_ut(out["proj"]["sd"], out["vals"], out["ranges"], cam, cfg, d_image)
+    g = project_ut_bwd(mu, s, q, o, sh, cam, cfg, d_sd)
+    g["d_sd"] = d_sd
+    return g
 
 
 def loss_brute(scene_arrays, cam, cfg, w):

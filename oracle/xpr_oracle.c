@@ -1105,6 +1105,7 @@ void oracle_project_bwd(int64_t n, const double *mu, const double *scale, const 
 
 typedef struct {
     double mu2d[2], cov0[3], cov[3], conic[3], det0, det, o, ln_thr, ex, ey, pre[4], mc[3], rgb[3], roc[3], M[9];
+    double pts[7][2], pc[7][3], R[9], qn[4], qnorm, cp[3], dir[3], vlen, raw[3], mip;
     int bbox[4];
     int tc, visible;
 } oproj_ut;
@@ -1114,20 +1115,21 @@ static void project_ut_one(const double *mu, const double *s, const double *q, d
     memset(P, 0, sizeof(*P));
     const double *V = cam->V;
     for (int i = 0; i < 3; ++i) P->mc[i] = V[4 * i] * mu[0] + V[4 * i + 1] * mu[1] + V[4 * i + 2] * mu[2] + V[4 * i + 3];
-    double qn[4], qnorm, R[9];
-    quat_rot(q, qn, &qnorm, R);
-    double cp[3];
+    double *qn = P->qn, *R = P->R, *cp = P->cp, *dir = P->dir;
+    quat_rot(q, qn, &P->qnorm, R);
     for (int i = 0; i < 3; ++i) cp[i] = -(V[i] * V[3] + V[4 + i] * V[7] + V[8 + i] * V[11]);
     /* colour as in 3DGS */
     double v[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
     double vl = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    double dir[3] = {v[0] / vl, v[1] / vl, v[2] / vl};
+    P->vlen = vl;
+    for (int i = 0; i < 3; ++i) dir[i] = v[i] / vl;
     int K = (cfg->deg + 1) * (cfg->deg + 1);
     double Y[16];
     oracle_sh_basis(cfg->deg, dir, Y, NULL);
     for (int c = 0; c < 3; ++c) {
         double acc = 0.5;
         for (int k = 0; k < K; ++k) acc += sh[3 * k + c] * Y[k];
+        P->raw[c] = acc;
         P->rgb[c] = acc > 0.0 ? acc : 0.0;
     }
     /* shader data */
@@ -1138,13 +1140,13 @@ static void project_ut_one(const double *mu, const double *s, const double *q, d
     if (!(P->mc[2] > cam->z_near)) return;
     /* sigma points through the projection */
     const double sq3 = sqrt(3.0);
-    double pts[7][2];
+    double(*pts)[2] = P->pts;
     for (int k = 0; k < 7; ++k) {
         double X[3];
         int a = (k - 1) / 2;
         double sgn = (k == 0) ? 0.0 : ((k % 2) ? 1.0 : -1.0);
         for (int i = 0; i < 3; ++i) X[i] = mu[i] + (k == 0 ? 0.0 : sgn * sq3 * s[a] * R[3 * i + a]);
-        double pc[3];
+        double *pc = P->pc[k];
         for (int i = 0; i < 3; ++i) pc[i] = V[4 * i] * X[0] + V[4 * i + 1] * X[1] + V[4 * i + 2] * X[2] + V[4 * i + 3];
         if (!(pc[2] > cam->z_near)) return; /* a sigma point behind the near plane: footprint undefined */
         pts[k][0] = cam->fx * pc[0] / pc[2] + cam->cx;
@@ -1168,7 +1170,8 @@ static void project_ut_one(const double *mu, const double *s, const double *q, d
     P->cov[2] = P->cov0[2] + cfg->dil;
     P->det = P->cov[0] * P->cov[2] - P->cov[1] * P->cov[1];
     if (!(P->det > 0.0)) return;
-    P->o = o * sqrt((P->det0 > 0.0 ? P->det0 : 0.0) / P->det);
+    P->mip = sqrt((P->det0 > 0.0 ? P->det0 : 0.0) / P->det);
+    P->o = o * P->mip;
     if (!(P->o > cfg->at)) return; /* strict for 3DGUT (its projection listing), unlike 3DGS */
     P->conic[0] = P->cov[2] / P->det;
     P->conic[1] = -P->cov[1] / P->det;
@@ -1243,28 +1246,44 @@ static void pixel_ray(double x, double y, const ocam *cam, double *rd) {
     for (int i = 0; i < 3; ++i) rd[i] = V[i] * dc[0] + V[4 + i] * dc[1] + V[8 + i] * dc[2];
 }
 
-/* largest response of the Gaussian of shader data S along the ray of direction rd */
-static double ut_response(const double *S, const double *rd) {
+/* largest response of the Gaussian of shader data S along the ray of direction rd; tau (the
+ * maximiser tau_max in the canonical frame's parametrisation) and e = ro_c + tau d_c on request */
+static double ut_response_full(const double *S, const double *rd, double *tau_out, double *e_out) {
     double dcn[3];
     for (int i = 0; i < 3; ++i) dcn[i] = S[3 + 3 * i] * rd[0] + S[4 + 3 * i] * rd[1] + S[5 + 3 * i] * rd[2];
     double a = S[0] * dcn[0] + S[1] * dcn[1] + S[2] * dcn[2];
     double b = dcn[0] * dcn[0] + dcn[1] * dcn[1] + dcn[2] * dcn[2];
     double tau = -a / b;
     double e[3] = {S[0] + tau * dcn[0], S[1] + tau * dcn[1], S[2] + tau * dcn[2]};
+    if (tau_out) *tau_out = tau;
+    if (e_out)
+        for (int i = 0; i < 3; ++i) e_out[i] = e[i];
     return exp(-0.5 * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]));
 }
 
+static double ut_response(const double *S, const double *rd) { return ut_response_full(S, rd, NULL, NULL); }
+
 double oracle_ut_response(const double *sd, const double *rd) { return ut_response(sd, rd); }
 
-static int walk_ut(const double *rd, const double *rec, const double *sd, const int64_t *list, int len,
-                   const ocfg *cfg, double delta, double C[3], double *Tout, int *last, int *band) {
+typedef struct {
+    int64_t idx;
+    double alpha, G, T, tau, e[3];
+    int clamped;
+} contrib_ut;
+
+/* The walk of the 3DGS compositing with the ray response in place of the 2D one.  out (may be
+ * NULL) records the contributors; sig (may be NULL) hashes every decision taken. */
+static int walk_ut(const double *rd, const double *sd, const int64_t *list, int len, const ocfg *cfg, double delta,
+                   double C[3], double *Tout, int *last, int *band, contrib_ut *out, uint64_t *sig) {
     double T = 1.0;
     C[0] = C[1] = C[2] = 0.0;
     int nc = 0, bd = 0;
+    uint64_t h = sig ? *sig : 0;
     *last = 0;
     for (int k = 0; k < len; ++k) {
         const double *S = sd + 16 * list[k];
-        double G = ut_response(S, rd);
+        double tau, e[3];
+        double G = ut_response_full(S, rd, &tau, e);
         if (fabs(G - UT_VALID) <= delta * UT_VALID) bd = 1;
         if (!(G > UT_VALID)) continue;
         double og = S[12] * G;
@@ -1274,23 +1293,36 @@ static int walk_ut(const double *rd, const double *rec, const double *sd, const 
         if (alpha < cfg->at) continue;
         double tt = T * (1.0 - alpha);
         if (fabs(tt - cfg->teps) <= delta * cfg->teps) bd = 1;
-        if (tt < cfg->teps) break;
+        if (tt < cfg->teps) {
+            h = h * 1099511628211ULL ^ 0xffffULL;
+            break;
+        }
+        if (out) {
+            out[nc].idx = list[k];
+            out[nc].alpha = alpha;
+            out[nc].G = G;
+            out[nc].T = T;
+            out[nc].tau = tau;
+            for (int i = 0; i < 3; ++i) out[nc].e[i] = e[i];
+            out[nc].clamped = !(og < cfg->amax);
+        }
+        h = (h ^ (uint64_t)(list[k] + 1)) * 1099511628211ULL;
         for (int c = 0; c < 3; ++c) C[c] += S[13 + c] * alpha * T;
         T = tt;
         ++nc;
         *last = k + 1;
     }
-    (void)rec;
     for (int c = 0; c < 3; ++c) C[c] += T * cfg->bg[c];
     *Tout = T;
     *band = bd;
+    if (sig) *sig = h;
     return nc;
 }
 
 /* Per-tile walk of 3DGUT over given lists (as oracle_render_tiles). */
 void oracle_render_tiles_ut(int64_t n, const double *rec, const double *sd, const uint32_t *vals,
                             const int32_t *ranges, const double *camv, const double *cfgv, double delta,
-                            double *image, double *tfinal, int32_t *ncontrib, int32_t *band) {
+                            double *image, double *tfinal, int32_t *ncontrib, int32_t *band, uint64_t *psig) {
     (void)n;
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
@@ -1309,9 +1341,11 @@ void oracle_render_tiles_ut(int64_t n, const double *rec, const double *sd, cons
                 if (x >= cam.W || y >= cam.H) continue;
                 double rd[3], C[3], T;
                 int last, bd;
+                uint64_t h = 0;
                 pixel_ray((double)x, (double)y, &cam, rd);
-                walk_ut(rd, rec, sd, list, len, &cfg, delta, C, &T, &last, &bd);
+                walk_ut(rd, sd, list, len, &cfg, delta, C, &T, &last, &bd, NULL, &h);
                 int64_t p = (int64_t)y * cam.W + x;
+                if (psig) psig[p] = h;
                 for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
                 tfinal[p] = T;
                 ncontrib[p] = last;
@@ -1334,7 +1368,7 @@ void oracle_render_pixels_ut(int64_t n, const double *rec, const double *sd, con
         double rd[3], C[3], T;
         int last, bd;
         pixel_ray((double)pix[2 * p], (double)pix[2 * p + 1], &cam, rd);
-        walk_ut(rd, rec, sd, order, (int)m, &cfg, delta, C, &T, &last, &bd);
+        walk_ut(rd, sd, order, (int)m, &cfg, delta, C, &T, &last, &bd, NULL, NULL);
         for (int c = 0; c < 3; ++c) color[3 * p + c] = C[c];
         tfinal[p] = T;
         band[p] = bd;
@@ -1347,4 +1381,194 @@ void oracle_pixel_ray(int x, int y, const double *camv, double *rd) {
     pixel_ray((double)x, (double)y, &cam, rd);
 }
 
-int oracle_abi_version(void) { return 2; }
+/* ------------------------------------------------------------------------ */
+/* Adjoint of 3DGUT.  Compositing as in 3DGS (dC/dc_i, dC/da_i with explicit */
+/* suffix sums), then through alpha = o' G (nothing through the clamp) and   */
+/* G = exp(-Q/2), Q = |ro_c|^2 - (ro_c.d_c)^2 / (d_c.d_c), d_c = M d:        */
+/*   dQ/dro_c = 2 e,  dQ/dd_c = 2 tau e,  e = ro_c + tau d_c,                */
+/*   dL/dM_ij = dL/dd_c_i d_j.                                               */
+/* d_sd[n*16] accumulates (dro_c[3], dM[9], do', drgb[3]).                   */
+/* ------------------------------------------------------------------------ */
+
+static void pixel_adjoint_ut(const double *sd, const contrib_ut *cs, int nc, double Tfin, const double *g,
+                             const double *rd, const ocfg *cfg, double *d_sd) {
+    if (nc == 0) return;
+    double *S = (double *)malloc((size_t)nc * 3 * sizeof(double));
+    for (int c = 0; c < 3; ++c) {
+        double acc = Tfin * cfg->bg[c];
+        for (int i = nc - 1; i >= 0; --i) {
+            S[3 * i + c] = acc;
+            acc += sd[16 * cs[i].idx + 13 + c] * cs[i].alpha * cs[i].T;
+        }
+    }
+    for (int i = 0; i < nc; ++i) {
+        const double *Sd = sd + 16 * cs[i].idx;
+        double *D = d_sd + 16 * cs[i].idx;
+        double a = cs[i].alpha, T = cs[i].T;
+        double da = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            D[13 + c] += g[c] * a * T;
+            da += g[c] * (Sd[13 + c] * T - S[3 * i + c] / (1.0 - a));
+        }
+        if (cs[i].clamped) continue;
+        D[12] += da * cs[i].G;
+        double dQ = -0.5 * cs[i].G * (da * Sd[12]); /* dL/dQ = dL/dG dG/dQ */
+        const double *e = cs[i].e;
+        for (int r = 0; r < 3; ++r) {
+            D[r] += 2.0 * dQ * e[r];
+            double ddc = 2.0 * dQ * cs[i].tau * e[r];
+            for (int j = 0; j < 3; ++j) D[3 + 3 * r + j] += ddc * rd[j];
+        }
+    }
+    free(S);
+}
+
+/* Per-tile adjoint over given lists (serial; deterministic). */
+void oracle_render_bwd_tiles_ut(int64_t n, const double *sd, const uint32_t *vals, const int32_t *ranges,
+                                const double *camv, const double *cfgv, const double *d_image, double *d_sd) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
+    int64_t HW = (int64_t)cam.W * cam.H;
+    memset(d_sd, 0, (size_t)n * 16 * sizeof(double));
+    for (int t = 0; t < Wt * Ht; ++t) {
+        int tx = t % Wt, ty = t / Wt;
+        int s0 = ranges[2 * t], e0 = ranges[2 * t + 1];
+        int len = e0 - s0;
+        if (len <= 0) continue;
+        int64_t *list = (int64_t *)malloc((size_t)len * sizeof(int64_t));
+        contrib_ut *cs = (contrib_ut *)malloc((size_t)len * sizeof(contrib_ut));
+        for (int k = 0; k < len; ++k) list[k] = vals[s0 + k];
+        for (int yy = 0; yy < cfg.th; ++yy)
+            for (int xx = 0; xx < cfg.tw; ++xx) {
+                int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
+                if (x >= cam.W || y >= cam.H) continue;
+                int64_t p = (int64_t)y * cam.W + x;
+                double g[3] = {d_image[p], d_image[HW + p], d_image[2 * HW + p]};
+                if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
+                double rd[3], C[3], T;
+                int last, bd;
+                pixel_ray((double)x, (double)y, &cam, rd);
+                int nc = walk_ut(rd, sd, list, len, &cfg, 0.0, C, &T, &last, &bd, cs, NULL);
+                pixel_adjoint_ut(sd, cs, nc, T, g, rd, &cfg, d_sd);
+            }
+        free(cs);
+        free(list);
+    }
+}
+
+/* Adjoint of the 3DGUT projection: d_sd (dro_c, dM, do', drgb) to dmu, dscale, dquat, dopac, dsh.
+ *   rgb: as in 3DGS (SH of the direction from the camera centre);
+ *   ro_c = M (c - mu): dM += dro_c (c - mu)^T, dmu -= M^T dro_c;
+ *   M_ij = R_ji / s_i: ds_i -= sum_j dM_ij M_ij / s_i, dR_ji += dM_ij / s_i;
+ *   o' = o m, m = sqrt(det_0 / det): dopac = do' m, and m depends on Sigma_2D (UT):
+ *     dm/ddet_0 = m / (2 det_0), dm/ddet = -m / (2 det), det_0 = c0 c2 - c1^2,
+ *     det = (c0 + d)(c2 + d) - c1^2;
+ *   Sigma_2D = sum_k wc_k (p_k - mu_2D)(p_k - mu_2D)^T, mu_2D = sum_k wm_k p_k;
+ *   p_k = (fx x_k / z_k + cx, fy y_k / z_k + cy), (x_k, y_k, z_k) = W X_k + t;
+ *   X_k = mu + sgn sqrt(3) s_a R[:, a]: dmu += dX_k, ds_a += sgn sqrt(3) R[:, a].dX_k,
+ *     dR[:, a] += sgn sqrt(3) s_a dX_k;
+ *   R = R(q / |q|) as in 3DGS. */
+void oracle_project_ut_bwd(int64_t n, const double *mu, const double *scale, const double *quat, const double *opac,
+                           const double *sh, const double *camv, const double *cfgv, const double *d_sd,
+                           double *dmu, double *dscale, double *dquat, double *dopac, double *dsh) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int K = (cfg.deg + 1) * (cfg.deg + 1);
+    const double *V = cam.V;
+    const double wm[7] = {0.0, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+    const double wc[7] = {2.0, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
+    const double sq3 = sqrt(3.0);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        oproj_ut P;
+        const double *D = d_sd + 16 * i;
+        const double *s = scale + 3 * i;
+        const double *m_ = mu + 3 * i;
+        const double *shi = sh + (int64_t)3 * K * i;
+        double *gmu = dmu + 3 * i, *gs = dscale + 3 * i, *gq = dquat + 4 * i, *gsh = dsh + (int64_t)3 * K * i;
+        project_ut_one(m_, s, quat + 4 * i, opac[i], shi, &cam, &cfg, &P);
+        memset(gmu, 0, 3 * sizeof(double));
+        memset(gs, 0, 3 * sizeof(double));
+        memset(gq, 0, 4 * sizeof(double));
+        memset(gsh, 0, (size_t)3 * K * sizeof(double));
+        dopac[i] = 0.0;
+        if (!P.visible) continue;
+
+        /* colour */
+        double Y[16], dY[48];
+        oracle_sh_basis(cfg.deg, P.dir, Y, dY);
+        double gdir[3] = {0, 0, 0};
+        for (int c = 0; c < 3; ++c) {
+            if (!(P.raw[c] > 0.0)) continue;
+            double g = D[13 + c];
+            for (int k = 0; k < K; ++k) {
+                gsh[3 * k + c] = Y[k] * g;
+                for (int j = 0; j < 3; ++j) gdir[j] += g * shi[3 * k + c] * dY[3 * k + j];
+            }
+        }
+        double dd = gdir[0] * P.dir[0] + gdir[1] * P.dir[1] + gdir[2] * P.dir[2];
+        for (int j = 0; j < 3; ++j) gmu[j] += (gdir[j] - P.dir[j] * dd) / P.vlen;
+
+        /* ro_c = M (c - mu) */
+        double gM[9];
+        for (int r = 0; r < 3; ++r)
+            for (int j = 0; j < 3; ++j) gM[3 * r + j] = D[3 + 3 * r + j] + D[r] * (P.cp[j] - m_[j]);
+        for (int j = 0; j < 3; ++j) gmu[j] -= P.M[j] * D[0] + P.M[3 + j] * D[1] + P.M[6 + j] * D[2];
+        /* M_ij = R_ji / s_i */
+        double gR[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int r = 0; r < 3; ++r)
+            for (int j = 0; j < 3; ++j) {
+                gs[r] -= gM[3 * r + j] * P.M[3 * r + j] / s[r];
+                gR[3 * j + r] += gM[3 * r + j] / s[r];
+            }
+
+        /* o' = o m */
+        dopac[i] = D[12] * P.mip;
+        double gmip = D[12] * opac[i];
+        double c0 = P.cov0[0], c1 = P.cov0[1], c2 = P.cov0[2], dil = cfg.dil;
+        double kd0 = gmip * P.mip / (2.0 * P.det0), kd = -gmip * P.mip / (2.0 * P.det);
+        double gc0 = kd0 * c2 + kd * (c2 + dil);
+        double gc2 = kd0 * c0 + kd * (c0 + dil);
+        double gc1 = -2.0 * c1 * (kd0 + kd);
+        /* Sigma_2D from the projected sigma points */
+        double gp[7][2], gbar[2] = {0.0, 0.0};
+        for (int k = 0; k < 7; ++k) {
+            double dx = P.pts[k][0] - P.mu2d[0], dy = P.pts[k][1] - P.mu2d[1];
+            gp[k][0] = wc[k] * (2.0 * gc0 * dx + gc1 * dy);
+            gp[k][1] = wc[k] * (gc1 * dx + 2.0 * gc2 * dy);
+            gbar[0] -= gp[k][0];
+            gbar[1] -= gp[k][1];
+        }
+        for (int k = 0; k < 7; ++k) {
+            gp[k][0] += wm[k] * gbar[0];
+            gp[k][1] += wm[k] * gbar[1];
+        }
+        for (int k = 0; k < 7; ++k) {
+            const double *pc = P.pc[k];
+            double z = pc[2];
+            double gpc[3] = {gp[k][0] * cam.fx / z, gp[k][1] * cam.fy / z,
+                             -gp[k][0] * cam.fx * pc[0] / (z * z) - gp[k][1] * cam.fy * pc[1] / (z * z)};
+            double gX[3];
+            for (int j = 0; j < 3; ++j) gX[j] = V[j] * gpc[0] + V[4 + j] * gpc[1] + V[8 + j] * gpc[2];
+            for (int j = 0; j < 3; ++j) gmu[j] += gX[j];
+            if (k == 0) continue;
+            int a = (k - 1) / 2;
+            double sgn = (k % 2) ? 1.0 : -1.0;
+            gs[a] += sgn * sq3 * (P.R[a] * gX[0] + P.R[3 + a] * gX[1] + P.R[6 + a] * gX[2]);
+            for (int j = 0; j < 3; ++j) gR[3 * j + a] += sgn * sq3 * s[a] * gX[j];
+        }
+        double dR[4][9];
+        drot_dq(P.qn, dR);
+        double gqn[4];
+        for (int j = 0; j < 4; ++j) {
+            double acc = 0.0;
+            for (int e = 0; e < 9; ++e) acc += gR[e] * dR[j][e];
+            gqn[j] = acc;
+        }
+        double dotq = gqn[0] * P.qn[0] + gqn[1] * P.qn[1] + gqn[2] * P.qn[2] + gqn[3] * P.qn[3];
+        for (int j = 0; j < 4; ++j) gq[j] = (gqn[j] - P.qn[j] * dotq) / P.qnorm;
+    }
+}
+
+int oracle_abi_version(void) { return 3; }

@@ -254,3 +254,68 @@ def test_ray_response_with_translated_camera(oracle):
         fn = lambda t: 0.5 * (o + t * d - mu) @ Sinv @ (o + t * d - mu)
         best = minimize_scalar(fn, bounds=(0.0, 50.0), method="bounded", options=dict(xatol=1e-12)).fun
         assert oracle.ut_response(pr["sd"][0], d) == pytest.approx(math.exp(-best), rel=1e-7, abs=1e-300)
+
+
+def _tiny_ut_scene(seed, n=6, deg=3):
+    rng = np.random.default_rng(seed)
+    mu = np.stack([rng.uniform(-0.4, 0.4, n), rng.uniform(-0.4, 0.4, n), rng.uniform(2.5, 4.0, n)], 1)
+    s = np.exp(rng.normal(-1.6, 0.3, (n, 3)))
+    q = rng.normal(size=(n, 4))
+    o = 1 / (1 + np.exp(-rng.normal(0.5, 0.8, n)))
+    K = (deg + 1) ** 2
+    sh = rng.normal(0, 0.3, (n, K, 3))
+    sh[:, 0, :] = rng.uniform(0.5, 1.5, (n, 3))  # colours stay away from the max(0, .) kink
+    return [mu, s, q, o, sh]
+
+
+@pytest.mark.parametrize("seed,deg,yaw,tile", [(0, 3, 0.0, 16), (1, 1, 12.0, 8), (2, 0, -8.0, 16)])
+def test_ut_adjoint_matches_central_differences(oracle, seed, deg, yaw, tile):
+    # FP64 central differences of the oracle's own tiled 3DGUT forward; a step that flips any
+    # decision (a tile list, a gate) is left out and must stay rare
+    cam = scenes.pinhole(32, 32, 32.0, scenes.yaw_view(yaw, t=(0.05, -0.03, 0.1)))
+    cfg = _cfg(sh_degree=deg, bg=(0.1, 0.2, 0.3), tile_w=tile, tile_h=tile)
+    P = _tiny_ut_scene(seed, deg=deg)
+    w = np.random.default_rng(100 + seed).normal(size=(3, 32, 32))
+    g = oracle.grads_tiled_ut(P, cam, cfg, w)
+    skipped = total = 0
+    for a, name in enumerate(["mu", "scale", "quat", "opacity", "sh"]):
+        fd = np.zeros_like(P[a], dtype=float)
+        it = np.nditer(P[a], flags=["multi_index"])
+        for _ in it:
+            idx = it.multi_index
+            x0 = P[a][idx]
+            h = 1e-6 * max(abs(x0), 1e-2)
+            Pp = [p.copy() for p in P]
+            Pm = [p.copy() for p in P]
+            Pp[a][idx] = x0 + h
+            Pm[a][idx] = x0 - h
+            lp, sp = oracle.loss_tiled_ut(Pp, cam, cfg, w)
+            lm, sm = oracle.loss_tiled_ut(Pm, cam, cfg, w)
+            total += 1
+            if sp != sm:
+                skipped += 1
+                fd[idx] = g[name][idx]
+                continue
+            fd[idx] = (lp - lm) / (2 * h)
+        err = np.linalg.norm(g[name] - fd) / max(np.linalg.norm(fd), 1e-30)
+        assert err < 1e-5, (name, err)
+    assert skipped <= 0.02 * total
+    assert np.abs(g["mu"]).max() > 0 and np.abs(g["quat"]).max() > 0 and np.abs(g["scale"]).max() > 0
+
+
+def test_ut_single_gaussian_opacity_derivative_closed_form(oracle):
+    # one isotropic Gaussian on the axis, white-free colour c: C = c a, a = o m G, so
+    # dC/do = c m G with m = k / (k + dil), k = (s f / z)^2, G = exp(-|mu x d|^2 / (2 s^2))
+    cam = scenes.pinhole(32, 32, 40.0)
+    cfg = _cfg(tile_w=8, tile_h=8)
+    mu, s, o, c = np.array([0.0, 0.0, 2.0]), 0.1, 0.6, 0.7
+    P = [np.array([mu]), np.array([[s, s, s]]), np.array([[1.0, 0, 0, 0]]), np.array([o]),
+         np.full((1, 1, 3), (c - 0.5) / 0.28209479177387814)]
+    w = np.zeros((3, 32, 32))
+    w[0, 17, 18] = 1.0
+    g = oracle.grads_tiled_ut(P, cam, cfg, w)
+    k = (s * 40.0 / 2.0) ** 2
+    d = oracle.pixel_ray(18, 17, cam)
+    G = math.exp(-np.sum(np.cross(mu, d) ** 2) / (2 * s * s))
+    assert g["opacity"][0] == pytest.approx(c * k / (k + DIL) * G, rel=1e-12)
+    assert g["sh"][0, 0, 0] == pytest.approx(0.28209479177387814 * o * k / (k + DIL) * G, rel=1e-12)
