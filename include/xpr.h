@@ -71,7 +71,13 @@ typedef struct XprConfig {
     int32_t sh_degree;  /* 0..3; K = (sh_degree + 1)^2 coefficients per colour channel */
     float bg[3];        /* background colour added as T_final * bg */
     int32_t batch_depth;/* render: entries staged per shared-memory batch; 0 = kernel default */
+    int32_t method;     /* XPR_METHOD_3DGS (0) or XPR_METHOD_3DGUT (1): selects the tile cull's ray
+                           offset in the binning (xpr_tile_bin*, xpr_bin_sorted) and which projection /
+                           render entry points accept the config (each refuses the other method) */
 } XprConfig;
+
+#define XPR_METHOD_3DGS 0
+#define XPR_METHOD_3DGUT 1
 
 /* 3DGS PrimitiveParams (Appendix, 3DGS implementation), structure of arrays:
  * mu[n,3] world-space means, scale[n,3] (positive, activated), quat[n,4]
@@ -320,6 +326,62 @@ size_t xpr_bin_sorted_workspace(int64_t n, int32_t n_views, const XprCamera *cam
 int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
                    int32_t n_views, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges, uint32_t *vals,
                    int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---- 3DGUT (cfg->method == XPR_METHOD_3DGUT) ------------------------------------
+ * The 3DGUT instance of project / tile_cull / pixel_info / evaluate (Sec. 3
+ * method examples; Appendix, implementation of XPR-3DGUT).  Depth order,
+ * binning and sorting are the 3DGS entry points, called with the same config:
+ * its method field switches the tile cull to the ray-offset bounds (tile max
+ * bounds + 1, pixel centres at +0.5).  The projection / render entry points
+ * above refuse a 3DGUT config and these refuse a 3DGS one (XPR_ERR_INVALID).
+ *
+ * Shader data, 16 floats per record (this library's form of the paper's
+ * p_sd = (o_c, M, o', c), chosen so that float32 evaluation does not cancel):
+ *   [0] p0.x [1] p0.y  projected centre (fx x/z + cx, fy y/z + cy)
+ *   [2..4] A_0 = (z/fx) M W^T e_0   [5..7] A_1 = (z/fy) M W^T e_1
+ *   [8..10] o_c = M (c - mu)   [11] o' (Mip-Splatting opacity)
+ *   [12..14] rgb   [15] |o_c|^2
+ * with M = S^-1 R^T, W the world-to-camera rotation, c the camera centre.
+ * Pixel (x, y) is evaluated on the ray through (x + 0.5, y + 0.5); with
+ * (dx, dy) = (x + 0.5, y + 0.5) - p0, a = dx A_0 + dy A_1, b = a - o_c, the
+ * largest response along the ray is G = exp(-(|a|^2 - (a.b)^2 / |b|^2) / 2),
+ * equal to the paper's exp(-|o_c + tau_max d_c|^2 / 2).  Gradients d_sd use
+ * the same layout (entry 15 stays 0: |o_c|^2 is folded into d o_c). */
+#define XPR_SD_FLOATS 16
+
+/* xpr_project_ut: unscented-transform projection of n primitives.  Seven
+ * sigma points mu, mu +- sqrt(3) s_a R e_a (UT alpha = 1, beta = 2, kappa = 0:
+ * mean weights 0 and 1/6, covariance weights 2 and 1/6) through the pinhole
+ * projection give mu_2D and Sigma_2D; dilation + cov_dilation I; o' = o
+ * sqrt(det_0 / det); conic, extents sqrt(2 ln(o'/a_t) Sigma_2D,xx) (and yy),
+ * tile box of mu_2D - 0.5.  Invisible when a sigma point has camera z <=
+ * z_near, det <= 0, o' <= alpha_thresh, r = 0 or tc = 0.  Outputs rec[n,12]
+ * (3DGS layout: UT mean and conic, o', rgb, depth, ln(o'/a_t), visible),
+ * sd[n,16], bbox[n,4], tile_count[n], isect_count[n] (may be NULL) as
+ * xpr_project.  prims->sh must not be NULL.  rec, sd, bbox, quat 16-byte
+ * aligned. */
+int xpr_project_ut(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
+                   float *sd, int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream);
+
+/* xpr_render_ut_fwd: front-to-back compositing of the sorted lists (as
+ * xpr_render_fwd) with the 3DGUT evaluate: alpha = min(alpha_max, o' G),
+ * valid iff G > 0.0113, skipped if alpha < alpha_thresh.  sd[n,16] from
+ * xpr_project_ut; vals, ranges from xpr_sort_tiles / xpr_bin_sorted;
+ * outputs image[3,H,W], t_final[H,W], n_contrib[H,W].  Tiles of 8 or 16. */
+int xpr_render_ut_fwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                      const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, void *stream);
+
+/* xpr_render_ut_bwd: reverse-order adjoint of xpr_render_ut_fwd.  d_sd[n,16]
+ * is OVERWRITTEN (zeroed, then accumulated with atomics). */
+int xpr_render_ut_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                      const XprConfig *cfg, const float *t_final, const int32_t *n_contrib, const float *d_image,
+                      float *d_sd, void *stream);
+
+/* xpr_project_ut_bwd: adjoint of xpr_project_ut from d_sd[n,16] to the
+ * parameter gradients (OVERWRITTEN; zero for invisible primitives), the
+ * Mip-Splatting factor differentiated through the unscented covariance. */
+int xpr_project_ut_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
+                       const float *d_sd, const XprPrimsGrad *d_prims, void *stream);
 
 /* ---- Misc ------------------------------------------------------------------ */
 const char *xpr_status_string(int status);

@@ -27,7 +27,7 @@ class XprCamera(ctypes.Structure):
 class XprConfig(ctypes.Structure):
     _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("alpha_thresh", c_f32), ("alpha_max", c_f32),
                 ("t_eps", c_f32), ("cov_dilation", c_f32), ("clip_factor", c_f32), ("sh_degree", c_i32),
-                ("bg", c_f32 * 3), ("batch_depth", c_i32)]
+                ("bg", c_f32 * 3), ("batch_depth", c_i32), ("method", c_i32)]
 
 
 class XprPrims(ctypes.Structure):
@@ -39,7 +39,9 @@ class XprPrimsGrad(ctypes.Structure):
 
 
 XPR_OK, XPR_ERR_INVALID, XPR_ERR_CAPACITY, XPR_ERR_CUDA, XPR_ERR_TIMEOUT, XPR_ERR_INTERNAL = range(6)
+XPR_METHOD_3DGS, XPR_METHOD_3DGUT = 0, 1
 REC = 12
+SD = 16  # 3DGUT shader data per record
 
 # (name, restype, argtypes) of every exported entry point
 SIGNATURES = {
@@ -84,6 +86,14 @@ SIGNATURES = {
     "xpr_bin_sorted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(XprCamera),
                                ctypes.POINTER(XprConfig), c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz,
                                c_vp]),
+    "xpr_project_ut": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                               c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_render_ut_fwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                                  c_vp, c_vp, c_vp, c_vp]),
+    "xpr_render_ut_bwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                                  c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_project_ut_bwd": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
+                                   ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
     "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
@@ -156,6 +166,7 @@ def make_config(cfg) -> XprConfig:
     g.sh_degree = int(cfg.sh_degree)
     g.bg[:] = [float(b) for b in cfg.bg]
     g.batch_depth = int(getattr(cfg, "batch_depth", 0))
+    g.method = int(getattr(cfg, "method", XPR_METHOD_3DGS))
     return g
 
 
@@ -505,4 +516,57 @@ def xpr_project_bwd_views(mu, scale, quat, opacity, sh, cams, cfg, d_rec, stream
     g = _as_c(cfg, XprConfig)
     _check(L.xpr_project_bwd_views(ctypes.byref(p), mu.shape[0], camera_array(cams), len(cams), ctypes.byref(g),
                                    _ptr(d_rec), ctypes.byref(gp), _stream(stream)), "xpr_project_bwd_views")
+    return grads
+
+
+# ---------------------------------------------------------------------------------------- 3DGUT
+
+def xpr_project_ut(mu, scale, quat, opacity, sh, cam, cfg, stream=None, with_isect_count=True):
+    """Unscented projection: returns rec[n,12], sd[n,16], bbox[n,4], tile_count[n], isect_count[n] (or None)."""
+    L = load()
+    n = mu.shape[0]
+    dev = mu.device
+    rec = torch.empty((n, REC), dtype=torch.float32, device=dev)
+    sd = torch.empty((n, SD), dtype=torch.float32, device=dev)
+    bbox = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    tc = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev) if with_isect_count else None
+    p = _prims(mu, scale, quat, opacity, sh)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_project_ut(ctypes.byref(p), n, ctypes.byref(c), ctypes.byref(g), _ptr(rec), _ptr(sd), _ptr(bbox),
+                            _ptr(tc), _ptr(cnt), _stream(stream)), "xpr_project_ut")
+    return rec, sd, bbox, tc, cnt
+
+
+def xpr_render_ut_fwd(sd, vals, ranges, cam, cfg, stream=None):
+    L = load()
+    dev = sd.device
+    H, W = int(cam.height), int(cam.width)
+    image = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    t_final = torch.empty((H, W), dtype=torch.float32, device=dev)
+    n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_ut_fwd(_ptr(sd), sd.shape[0], _ptr(vals), _ptr(ranges), ctypes.byref(c), ctypes.byref(g),
+                               _ptr(image), _ptr(t_final), _ptr(n_contrib), _stream(stream)), "xpr_render_ut_fwd")
+    return image, t_final, n_contrib
+
+
+def xpr_render_ut_bwd(sd, vals, ranges, cam, cfg, t_final, n_contrib, d_image, stream=None):
+    L = load()
+    d_sd = torch.empty((sd.shape[0], SD), dtype=torch.float32, device=sd.device)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_ut_bwd(_ptr(sd), sd.shape[0], _ptr(vals), _ptr(ranges), ctypes.byref(c), ctypes.byref(g),
+                               _ptr(t_final), _ptr(n_contrib), _ptr(d_image.contiguous()), _ptr(d_sd),
+                               _stream(stream)), "xpr_render_ut_bwd")
+    return d_sd
+
+
+def xpr_project_ut_bwd(mu, scale, quat, opacity, sh, cam, cfg, d_sd, stream=None):
+    L = load()
+    grads = tuple(torch.empty_like(t) for t in (mu, scale, quat, opacity, sh))
+    p = _prims(mu, scale, quat, opacity, sh)
+    gp = XprPrimsGrad(*[t.data_ptr() for t in grads])
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_project_ut_bwd(ctypes.byref(p), mu.shape[0], ctypes.byref(c), ctypes.byref(g), _ptr(d_sd),
+                                ctypes.byref(gp), _stream(stream)), "xpr_project_ut_bwd")
     return grads

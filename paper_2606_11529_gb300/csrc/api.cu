@@ -50,6 +50,16 @@ int validate_camera_config(const XprCamera *cam, const XprConfig *cfg) {
         return fail(XPR_ERR_INVALID, "need 0 < alpha_thresh <= alpha_max <= 1");
     if (!(cfg->alpha_max < 1.f)) return fail(XPR_ERR_INVALID, "alpha_max must be < 1");
     if (!(cfg->t_eps >= 0.f)) return fail(XPR_ERR_INVALID, "t_eps must be >= 0");
+    if (cfg->method != XPR_METHOD_3DGS && cfg->method != XPR_METHOD_3DGUT)
+        return fail(XPR_ERR_INVALID, "method %d not supported (0 = 3DGS, 1 = 3DGUT)", cfg->method);
+    return XPR_OK;
+}
+
+// Projection and render entry points implement one method each.
+int need_method(const XprConfig *cfg, int method, const char *fn) {
+    if (cfg->method != method)
+        return fail(XPR_ERR_INVALID, "%s implements method %d (%s) but cfg->method is %d", fn, method,
+                    method == XPR_METHOD_3DGS ? "3DGS" : "3DGUT", cfg->method);
     return XPR_OK;
 }
 
@@ -86,6 +96,7 @@ int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const Xp
                 int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_project"))) return s;
     if ((s = check_n(n))) return s;
     if (n == 0) return XPR_OK;
     if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !rec || !bbox || !tile_count)
@@ -209,6 +220,7 @@ int xpr_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int3
                    const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_render_fwd"))) return s;
     if ((s = check_n(n))) return s;
     if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_fwd: NULL pointer");
     if (n > 0 && (!rec || !aligned(rec, 16))) return fail(XPR_ERR_INVALID, "xpr_render_fwd: rec NULL or unaligned");
@@ -220,6 +232,7 @@ int xpr_project_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, cons
                     const float *d_rec, const XprPrimsGrad *d_prims, void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_project_bwd"))) return s;
     if ((s = check_n(n))) return s;
     if (n == 0) return XPR_OK;
     if (!prims || !d_prims || !d_rec || !prims->mu || !prims->scale || !prims->quat || !prims->opacity ||
@@ -235,6 +248,7 @@ int xpr_render_bwd(const float *rec, int64_t n, const uint32_t *vals, const int3
                    float *d_rec, const XprPrims *prims, const XprPrimsGrad *d_prims, void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_render_bwd"))) return s;
     if ((s = check_n(n))) return s;
     if (!ranges || !t_final || !n_contrib || !d_image) return fail(XPR_ERR_INVALID, "xpr_render_bwd: NULL pointer");
     if (n == 0) return XPR_OK;
@@ -263,6 +277,7 @@ int xpr_project_views(const XprPrims *prims, int64_t n, const XprCamera *cams, i
     if (!cams) return fail(XPR_ERR_INVALID, "xpr_project_views: NULL cameras");
     for (int v = 0; v < n_views; ++v)
         if ((s = validate_camera_config(cams + v, cfg))) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_project_views"))) return s;
     if (n == 0) return XPR_OK;
     if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !rec || !bbox || !tile_count)
         return fail(XPR_ERR_INVALID, "xpr_project_views: NULL pointer");
@@ -310,6 +325,7 @@ int xpr_render_fwd_views(const float *rec, int64_t n, int32_t n_views, const uin
                          const int32_t *worklist, int32_t *counter, void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_render_fwd_views"))) return s;
     if ((s = check_views(n_views, n))) return s;
     if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_fwd_views: NULL");
     if (n > 0 && (!rec || !aligned(rec, 16))) return fail(XPR_ERR_INVALID, "xpr_render_fwd_views: rec");
@@ -325,6 +341,7 @@ int xpr_render_bwd_views(const float *rec, int64_t n, int32_t n_views, const uin
                          void *stream) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_render_bwd_views"))) return s;
     if ((s = check_views(n_views, n))) return s;
     if (!ranges || !t_final || !n_contrib || !d_image) return fail(XPR_ERR_INVALID, "xpr_render_bwd_views: NULL");
     if (n == 0) return XPR_OK;
@@ -342,6 +359,7 @@ int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cam
     if (!cams) return fail(XPR_ERR_INVALID, "xpr_project_bwd_views: NULL cameras");
     for (int v = 0; v < n_views; ++v)
         if ((s = validate_camera_config(cams + v, cfg))) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_project_bwd_views"))) return s;
     if (n == 0) return XPR_OK;
     if (!prims || !d_prims || !d_rec || !prims->mu || !prims->scale || !prims->quat || !prims->opacity ||
         !prims->sh || !d_prims->mu || !d_prims->scale || !d_prims->quat || !d_prims->opacity || !d_prims->sh)
@@ -358,6 +376,7 @@ int xpr_project_color(const float *mu, const float *sh, int64_t n, const XprCame
     if (!cams) return fail(XPR_ERR_INVALID, "xpr_project_color: NULL cameras");
     for (int v = 0; v < n_views; ++v)
         if ((s = validate_camera_config(cams + v, cfg))) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_project_color"))) return s;
     if (n == 0) return XPR_OK;
     if (!mu || !sh || !rec) return fail(XPR_ERR_INVALID, "xpr_project_color: NULL pointer");
     return launch_project_color_views(mu, sh, n, cams, n_views, *cfg, rec, as_stream(stream));
@@ -386,6 +405,67 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
         return fail(XPR_ERR_INVALID, "xpr_bin_sorted: rec/bbox must be 16-byte and workspace 256-byte aligned");
     return launch_binsort(rec, bbox, tile_count, order, n, n_views, *cam, *cfg, ranges, vals, capacity, n_isect,
                           workspace, ws_bytes, as_stream(stream));
+}
+
+// ---- 3DGUT --------------------------------------------------------------------------------
+
+int xpr_project_ut(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
+                   float *sd, int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGUT, "xpr_project_ut"))) return s;
+    if ((s = check_n(n))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh || !rec || !sd ||
+        !bbox || !tile_count)
+        return fail(XPR_ERR_INVALID, "xpr_project_ut: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(sd, 16) || !aligned(bbox, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_ut: quat, rec, sd and bbox must be 16-byte aligned");
+    return launch_ut_project_fwd_views(*prims, n, cam, 1, *cfg, rec, sd, bbox, tile_count, isect_count,
+                                       as_stream(stream));
+}
+
+int xpr_render_ut_fwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                      const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGUT, "xpr_render_ut_fwd"))) return s;
+    if ((s = check_n(n))) return s;
+    if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd: NULL pointer");
+    if (n > 0 && (!sd || !aligned(sd, 16))) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd: sd NULL or unaligned");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd: ranges must be 8-byte aligned");
+    return launch_ut_render_fwd(sd, n, vals, ranges, 1, *cam, *cfg, image, t_final, n_contrib, as_stream(stream));
+}
+
+int xpr_render_ut_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                      const XprConfig *cfg, const float *t_final, const int32_t *n_contrib, const float *d_image,
+                      float *d_sd, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGUT, "xpr_render_ut_bwd"))) return s;
+    if ((s = check_n(n))) return s;
+    if (!ranges || !t_final || !n_contrib || !d_image) return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd: NULL pointer");
+    if (n == 0) return XPR_OK;
+    if (!sd || !d_sd || !aligned(sd, 16) || !aligned(d_sd, 16))
+        return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd: sd/d_sd NULL or not 16-byte aligned");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd: ranges must be 8-byte aligned");
+    return launch_ut_render_bwd(sd, n, vals, ranges, 1, *cam, *cfg, t_final, n_contrib, d_image, d_sd,
+                                as_stream(stream));
+}
+
+int xpr_project_ut_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
+                       const float *d_sd, const XprPrimsGrad *d_prims, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGUT, "xpr_project_ut_bwd"))) return s;
+    if ((s = check_n(n))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !d_prims || !d_sd || !prims->mu || !prims->scale || !prims->quat || !prims->opacity ||
+        !prims->sh || !d_prims->mu || !d_prims->scale || !d_prims->quat || !d_prims->opacity || !d_prims->sh)
+        return fail(XPR_ERR_INVALID, "xpr_project_ut_bwd: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_sd, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_ut_bwd: quat and d_sd must be 16-byte aligned");
+    return launch_ut_project_bwd_views(*prims, n, cam, 1, *cfg, d_sd, *d_prims, as_stream(stream));
 }
 
 }  // extern "C"

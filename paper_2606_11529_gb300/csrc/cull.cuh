@@ -18,6 +18,9 @@
 // [k w, k w + w - 1] (the last one clamped to W - 1), so it is kept iff
 // ceil((xa + 1) / w) - 1 <= k <= floor(xb / w), and a span starting right of the image or
 // ending left of it keeps nothing.
+// 3DGUT evaluates pixel (x, y) at its centre (x + 0.5, y + 0.5), and its tile_cull extends the
+// tile's max bounds by one pixel (ray offset): with ext = 1 the tile rows are [y0, y1 + 1], the
+// columns [k w, k w + w - 1 + 1], so k >= ceil(xa / w) - 1, and the image ends at W - 1 + 1.
 #pragma once
 
 #include "xpr_internal.cuh"
@@ -30,6 +33,7 @@ struct CullData {
 
 struct Grid {
     int W, H, tw, th, Wt, Ht;
+    int ext;  // ray offset of the tile's max bounds: 0 (3DGS) or 1 (3DGUT)
 };
 
 constexpr unsigned kFullMask = 0xffffffffu;
@@ -76,7 +80,7 @@ __device__ __forceinline__ CullData shfl_cull(const CullData &d, int src) {
 // Kept tile columns [ka, kb] of tile row ty (unclamped to any box); false if none.
 __device__ __forceinline__ bool row_tiles(const CullData &d, const Grid &g, int ty, int &ka, int &kb) {
     if (!(d.T >= 0.f)) return false;
-    const float y0 = (float)(ty * g.th), y1 = (float)min(ty * g.th + g.th - 1, g.H - 1);
+    const float y0 = (float)(ty * g.th), y1 = (float)(min(ty * g.th + g.th - 1, g.H - 1) + g.ext);
     float lo = __int_as_float(0x7f800000), hi = __int_as_float(0xff800000);
     if (d.yl >= y0 && d.yl <= y1) lo = __fsub_rn(d.mx, d.ex);
     if (d.yr >= y0 && d.yr <= y1) hi = __fadd_rn(d.mx, d.ex);
@@ -94,9 +98,9 @@ __device__ __forceinline__ bool row_tiles(const CullData &d, const Grid &g, int 
         }
     }
     if (!(lo <= hi)) return false;
-    if (lo > (float)(g.W - 1) || hi < 0.f) return false;
+    if (lo > (float)(g.W - 1 + g.ext) || hi < 0.f) return false;
     const float iw = __frcp_rn((float)g.tw);  // exact: the tile width is a power of two
-    float t = __fmul_rn(__fadd_rn(lo, 1.f), iw);
+    float t = __fmul_rn(__fadd_rn(lo, (float)(1 - g.ext)), iw);
     float u = __fmul_rn(hi, iw);
     t = fmaxf(t, -1.f);
     u = fminf(u, (float)(g.W / g.tw + 2));
@@ -148,6 +152,7 @@ __host__ __device__ inline Grid make_grid(const XprCamera &cam, const XprConfig 
     g.th = cfg.tile_h;
     g.Wt = tiles_x(cam, cfg);
     g.Ht = tiles_y(cam, cfg);
+    g.ext = cfg.method == XPR_METHOD_3DGUT ? 1 : 0;
     return g;
 }
 

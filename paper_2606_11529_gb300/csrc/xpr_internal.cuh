@@ -79,6 +79,20 @@ size_t depth_order_workspace_bytes(int64_t n);
 int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
                        cudaStream_t st, int64_t per_view = 0, int n_views = 1);
 
+// 3DGUT (ut.cu)
+int need_method(const XprConfig *cfg, int method, const char *fn);
+int launch_ut_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views,
+                                const XprConfig &cfg, float *rec, float *sd, int32_t *bbox, int32_t *tc,
+                                int32_t *isect_count, cudaStream_t st);
+int launch_ut_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views,
+                                const XprConfig &cfg, const float *d_sd, const XprPrimsGrad &g, cudaStream_t st);
+int launch_ut_render_fwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
+                         const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final,
+                         int32_t *n_contrib, cudaStream_t st);
+int launch_ut_render_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
+                         const XprCamera &cam, const XprConfig &cfg, const float *t_final, const int32_t *n_contrib,
+                         const float *d_image, float *d_sd, cudaStream_t st);
+
 // fused bin + sort (binsort.cu)
 size_t binsort_workspace_bytes(int64_t n, int n_views, const XprCamera &cam, const XprConfig &cfg);
 bool binsort_supported(const XprCamera &cam, const XprConfig &cfg, int n_views);

@@ -1,9 +1,11 @@
-"""3DGS tile-splatting path on the GPU: the plain per-stage calls and the
-``torch.autograd.Function`` that chains them.
+"""Tile-splatting path on the GPU (3DGS, and 3DGUT when ``cfg.method == 1``): the plain
+per-stage calls and the ``torch.autograd.Function`` that chains them.
 
 Forward  = xpr_project -> xpr_depth_order -> xpr_bin_sorted -> xpr_render_fwd
            (or xpr_tile_bin -> xpr_sort_tiles in place of xpr_bin_sorted)
 Backward = xpr_render_bwd (compositing adjoint, then projection adjoint)
+3DGUT    = xpr_project_ut / xpr_render_ut_fwd / xpr_render_ut_bwd + xpr_project_ut_bwd around the
+           same depth order, binning (ray-offset cull) and sort
 
 The Function takes activated parameters (mu, scale, quat, opacity, sh), as in
 the paper's PrimitiveParams, and returns the image [3, H, W].  Gradients are
@@ -99,6 +101,11 @@ class Frame:
     image: torch.Tensor
     t_final: torch.Tensor
     n_contrib: torch.Tensor
+    sd: torch.Tensor | None = None  # 3DGUT shader data [n, 16]
+
+
+def is_ut(cfg) -> bool:
+    return int(getattr(cfg, "method", B.XPR_METHOD_3DGS)) == B.XPR_METHOD_3DGUT
 
 
 def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
@@ -115,12 +122,20 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     n = mu.shape[0]
     dev = mu.device
     ws = ws or Workspace()
+    ut = is_ut(cfg)
+    sd = None
+    deferred = sh_events is not None and not ut
+    if sh_events is not None and ut:  # the unscented projection takes the colours in the same pass
+        _wait_events(stream, sh_events)
     tm.start("project", stream)
-    deferred = sh_events is not None
-    out = B.xpr_project(mu, scale, quat, opacity, None if deferred else sh, ccam, ccfg, stream=stream,
-                        with_isect_count=not fused)
-    rec, bbox, tc = out[:3]
-    cnt = out[3] if len(out) > 3 else None
+    if ut:
+        rec, sd, bbox, tc, cnt = B.xpr_project_ut(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream,
+                                                  with_isect_count=not fused)
+    else:
+        out = B.xpr_project(mu, scale, quat, opacity, None if deferred else sh, ccam, ccfg, stream=stream,
+                            with_isect_count=not fused)
+        rec, bbox, tc = out[:3]
+        cnt = out[3] if len(out) > 3 else None
     tm.stop("project", stream)
     # emit intersections in (depth, index) order so that only tile ids remain to be ordered
     tm.start("depth_order", stream)
@@ -150,16 +165,23 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
         tm.stop("sort", stream)
     ws.last_isect = I
     if deferred:
-        cur = stream if stream is not None else torch.cuda.current_stream()
-        for e in (sh_events if isinstance(sh_events, (list, tuple)) else [sh_events]):
-            cur.wait_event(e)
+        _wait_events(stream, sh_events)
         tm.start("color", stream)
         B.xpr_project_color(mu, sh, rec, ccam, ccfg, stream=stream)
         tm.stop("color", stream)
     tm.start("render_fwd", stream)
-    image, t_final, n_contrib = B.xpr_render_fwd(rec, vs, ranges, ccam, ccfg, stream=stream)
+    if ut:
+        image, t_final, n_contrib = B.xpr_render_ut_fwd(sd, vs, ranges, ccam, ccfg, stream=stream)
+    else:
+        image, t_final, n_contrib = B.xpr_render_fwd(rec, vs, ranges, ccam, ccfg, stream=stream)
     tm.stop("render_fwd", stream)
-    return Frame(rec, bbox, tc, cnt, order, offsets, tiles, vals, I, ks, vs, ranges, image, t_final, n_contrib)
+    return Frame(rec, bbox, tc, cnt, order, offsets, tiles, vals, I, ks, vs, ranges, image, t_final, n_contrib, sd)
+
+
+def _wait_events(stream, events):
+    cur = stream if stream is not None else torch.cuda.current_stream()
+    for e in (events if isinstance(events, (list, tuple)) else [events]):
+        cur.wait_event(e)
 
 
 class SplatFunction(torch.autograd.Function):
@@ -169,21 +191,30 @@ class SplatFunction(torch.autograd.Function):
     def forward(ctx, mu, scale, quat, opacity, sh, cam, cfg, ws, timers):
         fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, timers=timers, fused=ws.fused,
                            sh_events=ws.take_sh_events())
-        ctx.save_for_backward(mu, scale, quat, opacity, sh, fr.rec, fr.vals_sorted, fr.ranges, fr.t_final,
+        # 3DGUT renders from the shader data, 3DGS from the records
+        shade = fr.sd if fr.sd is not None else fr.rec
+        ctx.save_for_backward(mu, scale, quat, opacity, sh, shade, fr.vals_sorted, fr.ranges, fr.t_final,
                               fr.n_contrib)
         ctx.cam, ctx.cfg, ctx.timers = cam, cfg, timers
         return fr.image
 
     @staticmethod
     def backward(ctx, d_image):
-        mu, scale, quat, opacity, sh, rec, vals, ranges, t_final, n_contrib = ctx.saved_tensors
+        mu, scale, quat, opacity, sh, shade, vals, ranges, t_final, n_contrib = ctx.saved_tensors
         tm = ctx.timers or _NO_TIMERS
         ccam, ccfg = B.make_camera(ctx.cam), B.make_config(ctx.cfg)
+        ut = is_ut(ctx.cfg)
         tm.start("render_bwd")
-        d_rec = B.xpr_render_bwd(rec, vals, ranges, ccam, ccfg, t_final, n_contrib, d_image.contiguous())
+        if ut:
+            d_shade = B.xpr_render_ut_bwd(shade, vals, ranges, ccam, ccfg, t_final, n_contrib, d_image.contiguous())
+        else:
+            d_shade = B.xpr_render_bwd(shade, vals, ranges, ccam, ccfg, t_final, n_contrib, d_image.contiguous())
         tm.stop("render_bwd")
         tm.start("project_bwd")
-        grads = B.xpr_project_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_rec)
+        if ut:
+            grads = B.xpr_project_ut_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_shade)
+        else:
+            grads = B.xpr_project_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_shade)
         tm.stop("project_bwd")
         return (*grads, None, None, None, None)
 
