@@ -47,6 +47,9 @@ TRAFFIC_SOURCE = {"render_bwd_kernel<16,16>": "profiles/render_bwd_headline.md",
                   "project_bwd_kernel<3>": "profiles/project_bwd_headline.md",
                   "project_fwd_kernel<3>": "profiles/project_fwd_headline.md"}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# 3DGUT ray evaluation: FP32-pipe operations per (pixel, entry) pair (derivations in the design doc)
+UT_FWD_OPS_PER_PAIR = 31
+UT_BWD_OPS_PER_PAIR = 72
 
 
 def peaks():
@@ -238,6 +241,50 @@ def batched_leg(dev, reps, flush):
             "timing": f"median of {reps} (L2 flushed before each)"}
 
 
+def ut_leg(dev, n, reps, flush):
+    """3DGUT form: the headline scene (1M clustered SH-3 Gaussians, 1920x1080 pinhole) with the
+    unscented projection, ray-offset binning and ray-evaluated compositing, forward + backward
+    through the autograd Function."""
+    import dataclasses
+    import numpy as np
+    import torch
+    from paper_2606_11529_gb300 import render as R
+    from paper_2606_11529_gb300 import scenes
+    sc, cam, cfg = scenes.headline_case(n)
+    cfg = dataclasses.replace(cfg, method=1)
+    P = [t.to(dev).requires_grad_(True) for t in R.scene_to_device(sc)]
+    w = torch.from_numpy(np.random.default_rng(1).normal(size=(3, cam.height, cam.width)).astype(np.float32)).to(dev)
+    ws = R.Workspace()
+
+    def step(timers=None):
+        for p in P:
+            p.grad = None
+        (R.render(*P, cam, cfg, ws, timers) * w).sum().backward()
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ms = _median_ms(step, reps, flush)
+    timers = R.StageTimers()
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        step(timers)
+    st = timers.mean_ms()
+    fr = R.forward_frame(*[p.detach() for p in P], cam, cfg, ws)
+    pairs = int(fr.n_contrib.to(torch.int64).sum().item())
+    alu = peaks()["alu_ops"]
+    roof = {}
+    for name, ops in (("render_fwd", UT_FWD_OPS_PER_PAIR), ("render_bwd", UT_BWD_OPS_PER_PAIR)):
+        ach = pairs * ops / (st[name] * 1e-3)
+        roof[name] = {"kernel": f"ut_{name}_kernel<16,16>", "bound": "alu", "achieved_tops": round(ach / 1e12, 3),
+                      "frac": round(ach / alu, 4)}
+    return {"workload": "3DGUT fwd+bwd, the headline scene (1M SH-3 Gaussians clustered, 1920x1080 pinhole "
+                        "f=1920, 16x16 tiles, seed 0), unscented projection with 7 sigma points",
+            "ms_per_iter": round(ms, 4), "stages_ms": {k: round(v, 4) for k, v in st.items()},
+            "intersections": fr.n_isect, "pairs_blended": pairs, "render_roofline": roof,
+            "timing": f"median of {reps} (L2 flushed before each)"}
+
+
 def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     """Serving form: 16 resident clustered SH-3 scenes (sizes log-uniform in [1e5, 3e6]), Poisson
     arrivals at 200 requests/s, sizes 512x512 / 1280x720 / 1920x1080; the continuous-batching server
@@ -300,6 +347,9 @@ def main():
     ap.add_argument("--n", type=int, default=1_000_000, help="primitive count (default: the headline 1M)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-view batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-ut", action="store_true", help="skip the 3DGUT leg")
+    ap.add_argument("--ut-only", action="store_true",
+                    help="run only the 3DGUT leg and print it as its own JSON line (for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-cap-gb", type=float, default=4.0)
@@ -324,6 +374,13 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     L = B.load()
+
+    if args.ut_only:
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        ut = ut_leg(dev, args.n, max(args.steps, 1), flush)
+        if rank == 0:
+            print(json.dumps({"leg": "3dgut", "ut": ut}))
+        return 0
 
     sc, cam, cfg = scenes.headline_case(args.n)
     host = [torch.from_numpy(a).pin_memory() for a in sc.arrays()]
@@ -467,6 +524,7 @@ def main():
     for _ in range(3):
         key_step()
     key_ms = _median_ms(key_step, args.steps, flush)
+    ut = None if args.no_ut else ut_leg(dev, args.n, max(args.steps, 5), flush)
     batched = None if args.no_batched else batched_leg(dev, max(args.steps // 2, 5), flush)
     serve = None
     if not args.no_serve:
@@ -492,6 +550,7 @@ def main():
             "stages": stages,
             "batched": batched,
             "serve": serve,
+            "ut": ut,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": launches,

@@ -266,7 +266,7 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
                                          const int2 *__restrict__ ranges, const Consts &k,
                                          const float *__restrict__ tfin, const int *__restrict__ ncon,
                                          const float *__restrict__ dimg, float *__restrict__ d_rec, float4 *s_g,
-                                         float4 *s_c, float *s_b, uint32_t *s_id, float (*s_acc)[kMaxBatch],
+                                         float4 *s_c, float *s_b, uint32_t *s_id, float (*s_acc)[kMaxBatch + 1],
                                          int *s_wmax) {
     constexpr int kPX = px_per_thread<TW, TH>();
     constexpr int NT = TW * TH / kPX;
@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(TW *TH / px_per_thread<TW, TH>()) render_bwd_k
     __shared__ float4 s_c[kMaxBatch];
     __shared__ float s_b[kMaxBatch];
     __shared__ uint32_t s_id[kMaxBatch];
-    __shared__ float s_acc[9][kMaxBatch];
+    // rows padded by one float: the 8 lanes adding one entry's values hit 8 different banks
+    __shared__ float s_acc[9][kMaxBatch + 1];
     __shared__ int s_wmax[8];
     if (w.list == nullptr) {
         bwd_tile<TW, TH>(blockIdx.x, rec, vals, ranges, k, tfin, ncon, dimg, d_rec, s_g, s_c, s_b, s_id, s_acc,

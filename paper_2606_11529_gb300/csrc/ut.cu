@@ -390,7 +390,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) ut_project_bwd_kernel(
 
 // ---- ray-evaluated compositing ---------------------------------------------------------------
 constexpr unsigned kFullUt = 0xffffffffu;
-constexpr int kUtBatch = 256;  // list entries staged per shared-memory batch
+constexpr int kUtBatch = 256;     // list entries staged per shared-memory batch (forward)
+constexpr int kUtBwdBatch = 128;  // the adjoint also keeps 16 accumulators per entry: half the batch
 // Pixels per thread: (x, y + q h/PX), q = 0..PX-1, PX = min(4, tile pixels / 32), so that a
 // tile's block is whole warps.
 template <int TW, int TH>
@@ -630,9 +631,10 @@ __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel
     constexpr int kUtPx = ut_px<TW, TH>();
     constexpr int NT = TW * TH / kUtPx, NW = NT / 32, RS = TH / kUtPx;
     static_assert(NT % 32 == 0, "a tile's block must be whole warps");
-    __shared__ float4 s_u0[kUtBatch], s_u1[kUtBatch], s_u2[kUtBatch], s_u3[kUtBatch];
-    __shared__ uint32_t s_id[kUtBatch];
-    __shared__ float s_acc[16][kUtBatch];
+    __shared__ float4 s_u0[kUtBwdBatch], s_u1[kUtBwdBatch], s_u2[kUtBwdBatch], s_u3[kUtBwdBatch];
+    __shared__ uint32_t s_id[kUtBwdBatch];
+    // rows padded by one float: the 16 lanes adding one entry's values hit 16 different banks
+    __shared__ float s_acc[16][kUtBwdBatch + 1];
     __shared__ int s_wmax[NW];
     const UtStage S = {s_u0, s_u1, s_u2, s_u3, s_id};
     const int gt = blockIdx.x;
@@ -673,8 +675,9 @@ __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel
 #pragma unroll
     for (int w = 0; w < NW; ++w) bmax = max(bmax, s_wmax[w]);
 
-    for (int end = rg.x + bmax; end > rg.x; end -= k.batch) {
-        const int start = max(rg.x, end - k.batch);
+    const int batch = min(k.batch, kUtBwdBatch);
+    for (int end = rg.x + bmax; end > rg.x; end -= batch) {
+        const int start = max(rg.x, end - batch);
         const int cnt = end - start;
         __syncthreads();
         for (int e = t; e < cnt; e += NT) {

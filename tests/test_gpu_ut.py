@@ -192,3 +192,47 @@ def test_ut_empty_and_all_invisible():
     empty = [torch.empty((0,) + tuple(x.shape[1:]), device="cuda") for x in R.scene_to_device(sc)]
     fr = R.forward_frame(*empty, cam, cfg)
     assert fr.n_isect == 0 and torch.all(fr.t_final == 1)
+
+
+def test_ut_headline_workload_sampled_tiles(oracle):
+    """1M SH-3 Gaussians, 1920x1080, 16x16 tiles with the 3DGUT path (the benchmarked launch
+    configuration): the pixels of sampled tiles against the oracle walking the GPU's lists for those
+    tiles, and the gradients of a loss on those pixels."""
+    import dataclasses
+    sc, cam, cfg = scenes.headline_case()
+    cfg = dataclasses.replace(cfg, method=1)
+    pr = oracle.project_ut(*sc.arrays(), cam, cfg)
+    o = pr["sd"][:, 12]
+    keep = ~((np.abs(o / A_T - 1.0) < 1e-3) & (o > 0))
+    sc = sc.subset(np.nonzero(keep)[0])
+    pr = oracle.project_ut(*sc.arrays(), cam, cfg)
+    P = [t.clone().requires_grad_(True) for t in R.scene_to_device(sc)]
+    fr = R.forward_frame(*[p.detach() for p in P], cam, cfg)
+    img = R.render(*P, cam, cfg)
+    torch.cuda.synchronize()
+    assert torch.equal(img.detach(), fr.image)
+    ranges = fr.ranges.cpu().numpy()
+    sv = fr.vals_sorted.cpu().numpy().view(np.uint32)
+    lengths = ranges[:, 1] - ranges[:, 0]
+    rng = np.random.default_rng(0)
+    busy = np.nonzero(lengths > np.percentile(lengths, 50))[0]
+    tiles = np.concatenate([rng.choice(busy, 20, replace=False), rng.choice(len(lengths), 4, replace=False)])
+    sub = np.zeros_like(ranges)
+    sub[tiles] = ranges[tiles]
+    ref = oracle.render_tiles_ut(pr["rec"], pr["sd"], sv, sub, cam, cfg, delta=BAND)
+    Wt = (cam.width + 15) // 16
+    mask = np.zeros((cam.height, cam.width), bool)
+    for t in tiles:
+        ty, tx = divmod(int(t), Wt)
+        mask[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+    ok = mask & ~ref["band"]
+    assert ok.sum() > 0.97 * mask.sum()
+    got = fr.image.cpu().numpy()
+    assert np.abs(got[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
+    assert (ref["t_final"][ok] < 0.5).mean() > 0.2  # sampled tiles are not mostly empty
+    w = rng.normal(size=(3, cam.height, cam.width)) * ok[None]
+    (img * dev(w)).sum().backward()
+    d_sd = oracle.render_bwd_tiles_ut(pr["sd"], sv, sub, cam, cfg, w)
+    g = oracle.project_ut_bwd(*sc.arrays(), cam, cfg, d_sd)
+    for name, p in zip(["mu", "scale", "quat", "opacity", "sh"], P):
+        assert rel_err(p.grad.cpu().numpy(), g[name]) < GRAD_TOL, name
