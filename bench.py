@@ -194,10 +194,10 @@ def _median_ms(fn, reps, flush=None):
     return statistics.median(times)
 
 
-def batched_leg(dev, reps, flush):
+def batched_leg(dev, reps, flush, method=0):
     """Batched form: 3M uniform Gaussians seen by 8 pinhole cameras (1600x1064, focal 800, yaw
     -15..+15 degrees), forward + backward of all 8 views; one batched pass (autotuned tile size and
-    batch depth, persistent render grids) against 8 plain single-view passes."""
+    batch depth, persistent render grids) against 8 plain single-view passes.  method 1: 3DGUT."""
     import numpy as np
     import torch
     from paper_2606_11529_gb300 import batched as BT
@@ -205,10 +205,10 @@ def batched_leg(dev, reps, flush):
     from paper_2606_11529_gb300 import scenes
     sc = scenes.uniform_scene(3_000_000, seed=0)
     cams = scenes.multiview_cameras(8, 1600, 1064, 800.0, seed=0)
-    base = scenes.RenderConfig(sh_degree=0)
+    base = scenes.RenderConfig(sh_degree=0, method=method)
     P = [t.to(dev) for t in R.scene_to_device(sc)]
     w = torch.from_numpy(np.random.default_rng(2).normal(size=(8, 3, 1064, 1600)).astype(np.float32)).to(dev)
-    best, table = BT.autotune(P, cams, base, scene_id="uniform-3M", reps=5)
+    best, table = BT.autotune(P, cams, base, scene_id=f"uniform-3M-m{method}", reps=5)
     Pg = [p.detach().requires_grad_(True) for p in P]
     ws = BT.ViewsWorkspace()
 
@@ -232,8 +232,9 @@ def batched_leg(dev, reps, flush):
     tb = _median_ms(batched, reps, flush)
     tp = _median_ms(plain, reps, flush)
     fr = BT.forward_views(*P, cams, best, BT.ViewsWorkspace())
-    return {"workload": "3M uniform SH-0 Gaussians (xy U[-1,1], z U[2,6]), 8 pinhole views 1600x1064 f=800, "
-                        "yaw -15..+15 deg, fwd+bwd of all 8 views, seed 0",
+    what = "3DGUT (unscented projection, ray evaluation)" if method == 1 else "3DGS"
+    return {"workload": f"{what}: 3M uniform SH-0 Gaussians (xy U[-1,1], z U[2,6]), 8 pinhole views 1600x1064 "
+                        "f=800, yaw -15..+15 deg, fwd+bwd of all 8 views, seed 0",
             "ms_batched": round(tb, 3), "ms_plain_8x": round(tp, 3), "speedup": round(tp / tb, 3),
             "intersections": fr.n_isect, "tile": [best.tile_w, best.tile_h], "batch_depth": best.batch_depth,
             "autotune_ms": {f"{k[0]}x{k[1]}/b{k[2]}": (round(v, 3) if v != float("inf") else None)
@@ -526,6 +527,7 @@ def main():
     key_ms = _median_ms(key_step, args.steps, flush)
     ut = None if args.no_ut else ut_leg(dev, args.n, max(args.steps, 5), flush)
     batched = None if args.no_batched else batched_leg(dev, max(args.steps // 2, 5), flush)
+    batched_ut = None if (args.no_batched or args.no_ut) else batched_leg(dev, max(args.steps // 2, 5), flush, 1)
     serve = None
     if not args.no_serve:
         torch.cuda.empty_cache()
@@ -549,6 +551,7 @@ def main():
             "roofline": roof,
             "stages": stages,
             "batched": batched,
+            "batched_3dgut": batched_ut,
             "serve": serve,
             "ut": ut,
             "cpu_baseline": cpu,

@@ -383,6 +383,26 @@ int xpr_render_ut_bwd(const float *sd, int64_t n, const uint32_t *vals, const in
 int xpr_project_ut_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
                        const float *d_sd, const XprPrimsGrad *d_prims, void *stream);
 
+/* 3DGUT, multi-view form (as the 3DGS _views entry points): V <= 16 cameras of
+ * one image size; records and shader data are view-major [V*n, ...]; tile t
+ * of view v is v*T + t in the binning, the sort and ranges[V*T,2]; images
+ * [V,3,H,W].  worklist (may be NULL) / counter: a persistent render grid
+ * taking tiles from xpr_tile_worklist's order through *counter (zeroed by the
+ * call).  d_sd[V*n,16] is OVERWRITTEN; the projection adjoint sums the views'
+ * gradients. */
+int xpr_project_ut_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
+                         const XprConfig *cfg, float *rec, float *sd, int32_t *bbox, int32_t *tile_count,
+                         int32_t *isect_count, void *stream);
+int xpr_render_ut_fwd_views(const float *sd, int64_t n, int32_t n_views, const uint32_t *vals, const int32_t *ranges,
+                            const XprCamera *cam, const XprConfig *cfg, float *image, float *t_final,
+                            int32_t *n_contrib, const int32_t *worklist, int32_t *counter, void *stream);
+int xpr_render_ut_bwd_views(const float *sd, int64_t n, int32_t n_views, const uint32_t *vals, const int32_t *ranges,
+                            const XprCamera *cam, const XprConfig *cfg, const float *t_final,
+                            const int32_t *n_contrib, const float *d_image, float *d_sd, const int32_t *worklist,
+                            int32_t *counter, void *stream);
+int xpr_project_ut_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
+                             const XprConfig *cfg, const float *d_sd, const XprPrimsGrad *d_prims, void *stream);
+
 /* ---- Misc ------------------------------------------------------------------ */
 const char *xpr_status_string(int status);
 const char *xpr_last_error(void); /* message of the last failing call on this host thread */

@@ -40,6 +40,11 @@ class ViewsFrame:
     image: torch.Tensor
     t_final: torch.Tensor
     n_contrib: torch.Tensor
+    sd: torch.Tensor | None = None  # 3DGUT shader data [V*n, 16]
+
+
+def _is_ut(cfg) -> bool:
+    return int(getattr(cfg, "method", B.XPR_METHOD_3DGS)) == B.XPR_METHOD_3DGUT
 
 
 class ViewsWorkspace:
@@ -67,8 +72,14 @@ def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | 
             raise ValueError("all views of one batch must share the image size")
     ccfg = B.make_config(cfg)
     fused = fused and B.binsort_ok(cam0, cfg, V)
-    rec, bbox, tc, cnt = B.xpr_project_views(mu, scale, quat, opacity, sh, cams, ccfg, stream=stream,
-                                             with_isect_count=not fused)
+    ut = _is_ut(cfg)
+    sd = None
+    if ut:
+        rec, sd, bbox, tc, cnt = B.xpr_project_ut_views(mu, scale, quat, opacity, sh, cams, ccfg, stream=stream,
+                                                        with_isect_count=not fused)
+    else:
+        rec, bbox, tc, cnt = B.xpr_project_views(mu, scale, quat, opacity, sh, cams, ccfg, stream=stream,
+                                                 with_isect_count=not fused)
     order = B.xpr_depth_order_views(rec, tc, n, V, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(n * V),
                                                                          dev), stream=stream)
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
@@ -87,8 +98,11 @@ def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | 
     ws.last_isect = I
     wl = B.xpr_tile_worklist(ranges, workspace=ws.scratch("wl", L.xpr_tile_worklist_workspace(nt), dev),
                              stream=stream) if persistent else None
-    image, tfin, ncon = B.xpr_render_fwd_views(rec, n, V, vs, ranges, cam0, ccfg, worklist=wl, stream=stream)
-    return ViewsFrame(rec, tc, I, vs, ranges, wl, image, tfin, ncon)
+    if ut:
+        image, tfin, ncon = B.xpr_render_ut_fwd_views(sd, n, V, vs, ranges, cam0, ccfg, worklist=wl, stream=stream)
+    else:
+        image, tfin, ncon = B.xpr_render_fwd_views(rec, n, V, vs, ranges, cam0, ccfg, worklist=wl, stream=stream)
+    return ViewsFrame(rec, tc, I, vs, ranges, wl, image, tfin, ncon, sd)
 
 
 class MultiViewSplat(torch.autograd.Function):
@@ -97,7 +111,8 @@ class MultiViewSplat(torch.autograd.Function):
     @staticmethod
     def forward(ctx, mu, scale, quat, opacity, sh, cams, cfg, ws, persistent):
         fr = forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws, persistent)
-        ctx.save_for_backward(mu, scale, quat, opacity, sh, fr.rec, fr.vals_sorted, fr.ranges, fr.t_final,
+        shade = fr.sd if fr.sd is not None else fr.rec  # 3DGUT renders from the shader data
+        ctx.save_for_backward(mu, scale, quat, opacity, sh, shade, fr.vals_sorted, fr.ranges, fr.t_final,
                               fr.n_contrib, *(() if fr.worklist is None else (fr.worklist,)))
         ctx.cams, ctx.cfg = cams, cfg
         return fr.image
@@ -105,13 +120,18 @@ class MultiViewSplat(torch.autograd.Function):
     @staticmethod
     def backward(ctx, d_image):
         saved = ctx.saved_tensors
-        mu, scale, quat, opacity, sh, rec, vals, ranges, tfin, ncon = saved[:10]
+        mu, scale, quat, opacity, sh, shade, vals, ranges, tfin, ncon = saved[:10]
         wl = saved[10] if len(saved) > 10 else None
         cams, ccfg = ctx.cams, B.make_config(ctx.cfg)
         n, V = mu.shape[0], len(cams)
-        d_rec = B.xpr_render_bwd_views(rec, n, V, vals, ranges, cams[0], ccfg, tfin, ncon, d_image.contiguous(),
-                                       worklist=wl)
-        grads = B.xpr_project_bwd_views(mu, scale, quat, opacity, sh, cams, ccfg, d_rec)
+        if _is_ut(ctx.cfg):
+            d_sd = B.xpr_render_ut_bwd_views(shade, n, V, vals, ranges, cams[0], ccfg, tfin, ncon,
+                                             d_image.contiguous(), worklist=wl)
+            grads = B.xpr_project_ut_bwd_views(mu, scale, quat, opacity, sh, cams, ccfg, d_sd)
+        else:
+            d_rec = B.xpr_render_bwd_views(shade, n, V, vals, ranges, cams[0], ccfg, tfin, ncon,
+                                           d_image.contiguous(), worklist=wl)
+            grads = B.xpr_project_bwd_views(mu, scale, quat, opacity, sh, cams, ccfg, d_rec)
         return (*grads, None, None, None, None)
 
 
@@ -142,7 +162,8 @@ def autotune(params, cams, cfg, scene_id="scene", backward=True, reps=5, tiles=T
     """Returns (best_cfg, table) where table maps (tile_w, tile_h, batch) -> median ms of one batched
     forward (+ backward) over all `cams` (inf where the batch has more than 2^31 - 1 pairs).
     Results are cached per (device, scene_id, resolution)."""
-    key = (torch.cuda.get_device_name(), scene_id, cams[0].width, cams[0].height, len(cams), backward)
+    key = (torch.cuda.get_device_name(), scene_id, cams[0].width, cams[0].height, len(cams), backward,
+           int(getattr(cfg, "method", 0)))
     if key in _CACHE:
         return _CACHE[key]
     table = {}

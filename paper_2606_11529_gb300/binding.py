@@ -94,6 +94,14 @@ SIGNATURES = {
                                   c_vp, c_vp, c_vp, c_vp, c_vp]),
     "xpr_project_ut_bwd": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
                                    ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_project_ut_views": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), c_i32,
+                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_render_ut_fwd_views": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp, ctypes.POINTER(XprCamera),
+                                        ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_render_ut_bwd_views": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp, ctypes.POINTER(XprCamera),
+                                        ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_project_ut_bwd_views": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), c_i32,
+                                         ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
     "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
@@ -569,4 +577,63 @@ def xpr_project_ut_bwd(mu, scale, quat, opacity, sh, cam, cfg, d_sd, stream=None
     c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
     _check(L.xpr_project_ut_bwd(ctypes.byref(p), mu.shape[0], ctypes.byref(c), ctypes.byref(g), _ptr(d_sd),
                                 ctypes.byref(gp), _stream(stream)), "xpr_project_ut_bwd")
+    return grads
+
+
+def xpr_project_ut_views(mu, scale, quat, opacity, sh, cams, cfg, stream=None, with_isect_count=True):
+    """Returns rec[V*n,12], sd[V*n,16], bbox[V*n,4], tile_count[V*n], isect_count[V*n] (or None)."""
+    L = load()
+    n, V = mu.shape[0], len(cams)
+    dev = mu.device
+    rec = torch.empty((V * n, REC), dtype=torch.float32, device=dev)
+    sd = torch.empty((V * n, SD), dtype=torch.float32, device=dev)
+    bbox = torch.empty((V * n, 4), dtype=torch.int32, device=dev)
+    tc = torch.empty(V * n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(V * n, dtype=torch.int32, device=dev) if with_isect_count else None
+    p = _prims(mu, scale, quat, opacity, sh)
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_project_ut_views(ctypes.byref(p), n, camera_array(cams), V, ctypes.byref(g), _ptr(rec), _ptr(sd),
+                                  _ptr(bbox), _ptr(tc), _ptr(cnt), _stream(stream)), "xpr_project_ut_views")
+    return rec, sd, bbox, tc, cnt
+
+
+def xpr_render_ut_fwd_views(sd, n, n_views, vals, ranges, cam, cfg, worklist=None, counter=None, stream=None):
+    L = load()
+    dev = sd.device
+    H, W = int(cam.height), int(cam.width)
+    image = torch.empty((n_views, 3, H, W), dtype=torch.float32, device=dev)
+    tfin = torch.empty((n_views, H, W), dtype=torch.float32, device=dev)
+    ncon = torch.empty((n_views, H, W), dtype=torch.int32, device=dev)
+    if worklist is not None and counter is None:
+        counter = torch.empty(1, dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_ut_fwd_views(_ptr(sd), n, n_views, _ptr(vals), _ptr(ranges), ctypes.byref(c),
+                                     ctypes.byref(g), _ptr(image), _ptr(tfin), _ptr(ncon), _ptr(worklist),
+                                     _ptr(counter), _stream(stream)), "xpr_render_ut_fwd_views")
+    return image, tfin, ncon
+
+
+def xpr_render_ut_bwd_views(sd, n, n_views, vals, ranges, cam, cfg, t_final, n_contrib, d_image, worklist=None,
+                            counter=None, stream=None):
+    L = load()
+    dev = sd.device
+    d_sd = torch.empty((n * n_views, SD), dtype=torch.float32, device=dev)
+    if worklist is not None and counter is None:
+        counter = torch.empty(1, dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_ut_bwd_views(_ptr(sd), n, n_views, _ptr(vals), _ptr(ranges), ctypes.byref(c),
+                                     ctypes.byref(g), _ptr(t_final), _ptr(n_contrib), _ptr(d_image.contiguous()),
+                                     _ptr(d_sd), _ptr(worklist), _ptr(counter), _stream(stream)),
+           "xpr_render_ut_bwd_views")
+    return d_sd
+
+
+def xpr_project_ut_bwd_views(mu, scale, quat, opacity, sh, cams, cfg, d_sd, stream=None):
+    L = load()
+    grads = tuple(torch.empty_like(t) for t in (mu, scale, quat, opacity, sh))
+    p = _prims(mu, scale, quat, opacity, sh)
+    gp = XprPrimsGrad(*[t.data_ptr() for t in grads])
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_project_ut_bwd_views(ctypes.byref(p), mu.shape[0], camera_array(cams), len(cams), ctypes.byref(g),
+                                      _ptr(d_sd), ctypes.byref(gp), _stream(stream)), "xpr_project_ut_bwd_views")
     return grads

@@ -434,7 +434,8 @@ int xpr_render_ut_fwd(const float *sd, int64_t n, const uint32_t *vals, const in
     if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd: NULL pointer");
     if (n > 0 && (!sd || !aligned(sd, 16))) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd: sd NULL or unaligned");
     if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd: ranges must be 8-byte aligned");
-    return launch_ut_render_fwd(sd, n, vals, ranges, 1, *cam, *cfg, image, t_final, n_contrib, as_stream(stream));
+    return launch_ut_render_fwd(sd, n, vals, ranges, 1, *cam, *cfg, image, t_final, n_contrib, nullptr, nullptr,
+                                as_stream(stream));
 }
 
 int xpr_render_ut_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
@@ -449,8 +450,8 @@ int xpr_render_ut_bwd(const float *sd, int64_t n, const uint32_t *vals, const in
     if (!sd || !d_sd || !aligned(sd, 16) || !aligned(d_sd, 16))
         return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd: sd/d_sd NULL or not 16-byte aligned");
     if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd: ranges must be 8-byte aligned");
-    return launch_ut_render_bwd(sd, n, vals, ranges, 1, *cam, *cfg, t_final, n_contrib, d_image, d_sd,
-                                as_stream(stream));
+    return launch_ut_render_bwd(sd, n, vals, ranges, 1, *cam, *cfg, t_final, n_contrib, d_image, d_sd, nullptr,
+                                nullptr, as_stream(stream));
 }
 
 int xpr_project_ut_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
@@ -466,6 +467,77 @@ int xpr_project_ut_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, c
     if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_sd, 16))
         return fail(XPR_ERR_INVALID, "xpr_project_ut_bwd: quat and d_sd must be 16-byte aligned");
     return launch_ut_project_bwd_views(*prims, n, cam, 1, *cfg, d_sd, *d_prims, as_stream(stream));
+}
+
+// ---- 3DGUT, multi-view form ---------------------------------------------------------------
+
+int xpr_project_ut_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
+                         const XprConfig *cfg, float *rec, float *sd, int32_t *bbox, int32_t *tile_count,
+                         int32_t *isect_count, void *stream) {
+    int s = check_views(n_views, n);
+    if (s) return s;
+    if (!cams) return fail(XPR_ERR_INVALID, "xpr_project_ut_views: NULL cameras");
+    for (int v = 0; v < n_views; ++v)
+        if ((s = validate_camera_config(cams + v, cfg))) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGUT, "xpr_project_ut_views"))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh || !rec || !sd ||
+        !bbox || !tile_count)
+        return fail(XPR_ERR_INVALID, "xpr_project_ut_views: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(sd, 16) || !aligned(bbox, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_ut_views: quat, rec, sd and bbox must be 16-byte aligned");
+    return launch_ut_project_fwd_views(*prims, n, cams, n_views, *cfg, rec, sd, bbox, tile_count, isect_count,
+                                       as_stream(stream));
+}
+
+int xpr_render_ut_fwd_views(const float *sd, int64_t n, int32_t n_views, const uint32_t *vals, const int32_t *ranges,
+                            const XprCamera *cam, const XprConfig *cfg, float *image, float *t_final,
+                            int32_t *n_contrib, const int32_t *worklist, int32_t *counter, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGUT, "xpr_render_ut_fwd_views"))) return s;
+    if ((s = check_views(n_views, n))) return s;
+    if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd_views: NULL");
+    if (n > 0 && (!sd || !aligned(sd, 16))) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd_views: sd");
+    if (worklist && !counter) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd_views: worklist needs a counter");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_ut_fwd_views: ranges must be 8-byte aligned");
+    return launch_ut_render_fwd(sd, n * n_views, vals, ranges, n_views, *cam, *cfg, image, t_final, n_contrib,
+                                worklist, counter, as_stream(stream));
+}
+
+int xpr_render_ut_bwd_views(const float *sd, int64_t n, int32_t n_views, const uint32_t *vals, const int32_t *ranges,
+                            const XprCamera *cam, const XprConfig *cfg, const float *t_final,
+                            const int32_t *n_contrib, const float *d_image, float *d_sd, const int32_t *worklist,
+                            int32_t *counter, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGUT, "xpr_render_ut_bwd_views"))) return s;
+    if ((s = check_views(n_views, n))) return s;
+    if (!ranges || !t_final || !n_contrib || !d_image) return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd_views: NULL");
+    if (n == 0) return XPR_OK;
+    if (!sd || !d_sd || !aligned(sd, 16) || !aligned(d_sd, 16))
+        return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd_views: sd/d_sd NULL or not 16-byte aligned");
+    if (worklist && !counter) return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd_views: worklist needs a counter");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_ut_bwd_views: ranges must be 8-byte aligned");
+    return launch_ut_render_bwd(sd, n * n_views, vals, ranges, n_views, *cam, *cfg, t_final, n_contrib, d_image,
+                                d_sd, worklist, counter, as_stream(stream));
+}
+
+int xpr_project_ut_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
+                             const XprConfig *cfg, const float *d_sd, const XprPrimsGrad *d_prims, void *stream) {
+    int s = check_views(n_views, n);
+    if (s) return s;
+    if (!cams) return fail(XPR_ERR_INVALID, "xpr_project_ut_bwd_views: NULL cameras");
+    for (int v = 0; v < n_views; ++v)
+        if ((s = validate_camera_config(cams + v, cfg))) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGUT, "xpr_project_ut_bwd_views"))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !d_prims || !d_sd || !prims->mu || !prims->scale || !prims->quat || !prims->opacity ||
+        !prims->sh || !d_prims->mu || !d_prims->scale || !d_prims->quat || !d_prims->opacity || !d_prims->sh)
+        return fail(XPR_ERR_INVALID, "xpr_project_ut_bwd_views: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_sd, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_ut_bwd_views: quat and d_sd must be 16-byte aligned");
+    return launch_ut_project_bwd_views(*prims, n, cams, n_views, *cfg, d_sd, *d_prims, as_stream(stream));
 }
 
 }  // extern "C"

@@ -460,16 +460,21 @@ struct UtPixFwd {
     bool done;
 };
 
+struct UtWork {  // persistent scheduling: tiles list[0 .. count) taken through *counter
+    const int *list;
+    int *counter;
+    int count;
+};
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_fwd_kernel(
-    const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, UtConsts k,
-    float *__restrict__ image, float *__restrict__ tfin, int *__restrict__ ncon) {
+__device__ __forceinline__ void ut_fwd_tile(int gt, const float *__restrict__ sd, const uint32_t *__restrict__ vals,
+                                            const int2 *__restrict__ ranges, const UtConsts &k,
+                                            float *__restrict__ image, float *__restrict__ tfin,
+                                            int *__restrict__ ncon, const UtStage &S) {
     constexpr int kUtPx = ut_px<TW, TH>();
     constexpr int NT = TW * TH / kUtPx, RS = TH / kUtPx;
     static_assert(NT % 32 == 0, "a tile's block must be whole warps");
-    __shared__ float4 s_u0[kUtBatch], s_u1[kUtBatch], s_u2[kUtBatch], s_u3[kUtBatch];
-    const UtStage S = {s_u0, s_u1, s_u2, s_u3, nullptr};
-    const int gt = blockIdx.x;
+    const float4 *s_u0 = S.u0, *s_u1 = S.u1, *s_u2 = S.u2, *s_u3 = S.u3;
     const int v = gt / k.T, tile = gt - v * k.T;
     const int tx = tile % k.Wt, ty = tile / k.Wt;
     const int t = threadIdx.x;
@@ -536,6 +541,27 @@ __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_fwd_kernel
         img[2 * HW + pix] = fmaf(P[q].T, k.bg2, P[q].b);
         tfin[v * HW + pix] = P[q].T;
         ncon[v * HW + pix] = P[q].last;
+    }
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_fwd_kernel(
+    const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, UtConsts k,
+    float *__restrict__ image, float *__restrict__ tfin, int *__restrict__ ncon, UtWork w) {
+    __shared__ float4 s_u0[kUtBatch], s_u1[kUtBatch], s_u2[kUtBatch], s_u3[kUtBatch];
+    const UtStage S = {s_u0, s_u1, s_u2, s_u3, nullptr};
+    if (w.list == nullptr) {
+        ut_fwd_tile<TW, TH>(blockIdx.x, sd, vals, ranges, k, image, tfin, ncon, S);
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();  // the previous tile's last reads of shared memory are done
+        if (threadIdx.x == 0) s_item = atomicAdd(w.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= w.count) break;
+        ut_fwd_tile<TW, TH>(w.list[item], sd, vals, ranges, k, image, tfin, ncon, S);
     }
 }
 
@@ -624,20 +650,16 @@ __device__ __forceinline__ bool ut_adjoint(UtPixBwd &P, float cx, const float4 &
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel(
-    const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, UtConsts k,
-    const float *__restrict__ tfin, const int *__restrict__ ncon, const float *__restrict__ dimg,
-    float *__restrict__ d_sd) {
+__device__ __forceinline__ void ut_bwd_tile(int gt, const float *__restrict__ sd, const uint32_t *__restrict__ vals,
+                                            const int2 *__restrict__ ranges, const UtConsts &k,
+                                            const float *__restrict__ tfin, const int *__restrict__ ncon,
+                                            const float *__restrict__ dimg, float *__restrict__ d_sd,
+                                            const UtStage &S, float (*s_acc)[kUtBwdBatch + 1], int *s_wmax) {
     constexpr int kUtPx = ut_px<TW, TH>();
     constexpr int NT = TW * TH / kUtPx, NW = NT / 32, RS = TH / kUtPx;
     static_assert(NT % 32 == 0, "a tile's block must be whole warps");
-    __shared__ float4 s_u0[kUtBwdBatch], s_u1[kUtBwdBatch], s_u2[kUtBwdBatch], s_u3[kUtBwdBatch];
-    __shared__ uint32_t s_id[kUtBwdBatch];
-    // rows padded by one float: the 16 lanes adding one entry's values hit 16 different banks
-    __shared__ float s_acc[16][kUtBwdBatch + 1];
-    __shared__ int s_wmax[NW];
-    const UtStage S = {s_u0, s_u1, s_u2, s_u3, s_id};
-    const int gt = blockIdx.x;
+    const float4 *s_u0 = S.u0, *s_u1 = S.u1, *s_u2 = S.u2, *s_u3 = S.u3;
+    const uint32_t *s_id = S.id;
     const int v = gt / k.T, tile = gt - v * k.T;
     const int tx = tile % k.Wt, ty = tile / k.Wt;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -725,6 +747,33 @@ __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel
     }
 }
 
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel(
+    const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, UtConsts k,
+    const float *__restrict__ tfin, const int *__restrict__ ncon, const float *__restrict__ dimg,
+    float *__restrict__ d_sd, UtWork w) {
+    constexpr int NW = TW * TH / ut_px<TW, TH>() / 32;
+    __shared__ float4 s_u0[kUtBwdBatch], s_u1[kUtBwdBatch], s_u2[kUtBwdBatch], s_u3[kUtBwdBatch];
+    __shared__ uint32_t s_id[kUtBwdBatch];
+    // rows padded by one float: the 16 lanes adding one entry's values hit 16 different banks
+    __shared__ float s_acc[16][kUtBwdBatch + 1];
+    __shared__ int s_wmax[NW];
+    const UtStage S = {s_u0, s_u1, s_u2, s_u3, s_id};
+    if (w.list == nullptr) {
+        ut_bwd_tile<TW, TH>(blockIdx.x, sd, vals, ranges, k, tfin, ncon, dimg, d_sd, S, s_acc, s_wmax);
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        __syncthreads();  // the previous tile's last reads of shared memory are done
+        if (threadIdx.x == 0) s_item = atomicAdd(w.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= w.count) break;
+        ut_bwd_tile<TW, TH>(w.list[item], sd, vals, ranges, k, tfin, ncon, dimg, d_sd, S, s_acc, s_wmax);
+    }
+}
+
 UtConsts make_ut_consts(const XprCamera &cam, const XprConfig &cfg, int64_t n) {
     UtConsts k;
     k.n = (uint32_t)n;
@@ -786,16 +835,31 @@ int launch_ut_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *c
     return XPR_OK;
 }
 
+template <typename KernelT>
+int ut_persistent_grid(KernelT kernel, int threads, int items) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return items;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return items;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return max(1, min(items, sms * per_sm));
+}
+
+// worklist/counter NULL: one block per tile over n_views * T tiles.  Otherwise a persistent grid
+// walks worklist[0 .. n_views * T); *counter is zeroed here.
 int launch_ut_render_fwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
                          const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final,
-                         int32_t *n_contrib, cudaStream_t st) {
+                         int32_t *n_contrib, const int32_t *worklist, int32_t *counter, cudaStream_t st) {
     const UtConsts k = make_ut_consts(cam, cfg, n);
     const int items = n_views * k.T;
     if (items == 0) return XPR_OK;
     const int2 *rg = reinterpret_cast<const int2 *>(ranges);
+    const UtWork w = {worklist, counter, items};
+    if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
     XPR_UT_TILE_DISPATCH(TW, TH, {
-        ut_render_fwd_kernel<TW, TH><<<items, TW * TH / ut_px<TW, TH>(), 0, st>>>(sd, vals, rg, k, image, t_final,
-                                                                               n_contrib);
+        const int threads = TW * TH / ut_px<TW, TH>();
+        const int grid = worklist ? ut_persistent_grid(ut_render_fwd_kernel<TW, TH>, threads, items) : items;
+        ut_render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(sd, vals, rg, k, image, t_final, n_contrib, w);
     });
     XPR_LAUNCH_CHECK("ut_render_fwd_kernel");
     return XPR_OK;
@@ -803,15 +867,20 @@ int launch_ut_render_fwd(const float *sd, int64_t n, const uint32_t *vals, const
 
 int launch_ut_render_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
                          const XprCamera &cam, const XprConfig &cfg, const float *t_final, const int32_t *n_contrib,
-                         const float *d_image, float *d_sd, cudaStream_t st) {
+                         const float *d_image, float *d_sd, const int32_t *worklist, int32_t *counter,
+                         cudaStream_t st) {
     XPR_CUDA_TRY(cudaMemsetAsync(d_sd, 0, (size_t)n * XPR_SD_FLOATS * sizeof(float), st));
     const UtConsts k = make_ut_consts(cam, cfg, n);
     const int items = n_views * k.T;
     if (items == 0) return XPR_OK;
     const int2 *rg = reinterpret_cast<const int2 *>(ranges);
+    const UtWork w = {worklist, counter, items};
+    if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
     XPR_UT_TILE_DISPATCH(TW, TH, {
-        ut_render_bwd_kernel<TW, TH><<<items, TW * TH / ut_px<TW, TH>(), 0, st>>>(sd, vals, rg, k, t_final,
-                                                                               n_contrib, d_image, d_sd);
+        const int threads = TW * TH / ut_px<TW, TH>();
+        const int grid = worklist ? ut_persistent_grid(ut_render_bwd_kernel<TW, TH>, threads, items) : items;
+        ut_render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(sd, vals, rg, k, t_final, n_contrib, d_image, d_sd,
+                                                                 w);
     });
     XPR_LAUNCH_CHECK("ut_render_bwd_kernel");
     return XPR_OK;

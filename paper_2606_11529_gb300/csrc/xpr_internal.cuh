@@ -88,10 +88,11 @@ int launch_ut_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *c
                                 const XprConfig &cfg, const float *d_sd, const XprPrimsGrad &g, cudaStream_t st);
 int launch_ut_render_fwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
                          const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final,
-                         int32_t *n_contrib, cudaStream_t st);
+                         int32_t *n_contrib, const int32_t *worklist, int32_t *counter, cudaStream_t st);
 int launch_ut_render_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
                          const XprCamera &cam, const XprConfig &cfg, const float *t_final, const int32_t *n_contrib,
-                         const float *d_image, float *d_sd, cudaStream_t st);
+                         const float *d_image, float *d_sd, const int32_t *worklist, int32_t *counter,
+                         cudaStream_t st);
 
 // fused bin + sort (binsort.cu)
 size_t binsort_workspace_bytes(int64_t n, int n_views, const XprCamera &cam, const XprConfig &cfg);

@@ -22,11 +22,13 @@ def _views(n_views=3, W=200, H=136, f=200.0):
     return scenes.multiview_cameras(n_views, W, H, f, seed=1)
 
 
-@pytest.mark.parametrize("persistent,tile,deg", [(True, 16, 1), (False, 16, 0), (True, 8, 3)])
-def test_views_equal_single_view_path(persistent, tile, deg):
+@pytest.mark.parametrize("persistent,tile,deg,method", [(True, 16, 1, 0), (False, 16, 0, 0), (True, 8, 3, 0),
+                                                        (True, 16, 1, 1), (False, 8, 0, 1), (True, 8, 3, 1)])
+def test_views_equal_single_view_path(persistent, tile, deg, method):
+    # method 1: 3DGUT, whose single-view path is checked against the oracle in test_gpu_ut.py
     sc = scenes.uniform_scene(8000, seed=2, sh_degree=deg)
     cams = _views()
-    cfg = scenes.RenderConfig(tile_w=tile, tile_h=tile, sh_degree=deg, bg=(0.1, 0.2, 0.3))
+    cfg = scenes.RenderConfig(tile_w=tile, tile_h=tile, sh_degree=deg, bg=(0.1, 0.2, 0.3), method=method)
     P = [t.requires_grad_(True) for t in R.scene_to_device(sc)]
     imgs = BT.render_views(*P, cams, cfg, persistent=persistent)
     w = torch.from_numpy(np.random.default_rng(3).normal(size=tuple(imgs.shape)).astype(np.float32)).cuda()
@@ -74,6 +76,20 @@ def test_batch_depth_does_not_change_the_image():
         if ref is None:
             ref = img
         assert torch.equal(img, ref), bd
+
+
+def test_ut_autotuner_and_worklist():
+    sc = scenes.uniform_scene(20_000, seed=7, sh_degree=1)
+    cams = _views(4)
+    cfg = scenes.RenderConfig(sh_degree=1, method=1)
+    P = list(R.scene_to_device(sc))
+    best, table = BT.autotune(P, cams, cfg, scene_id="ut-test", reps=2, batches=(32, 256))
+    assert best.method == 1 and len(table) == 4 and all(np.isfinite(v) for v in table.values())
+    fr = BT.forward_views(*P, cams, best)
+    ranges = fr.ranges.cpu().numpy()
+    lens = ranges[:, 1] - ranges[:, 0]
+    wl = fr.worklist.cpu().numpy()
+    assert sorted(wl.tolist()) == list(range(len(lens))) and np.all(np.diff(lens[wl]) <= 0)
 
 
 def test_autotuner_picks_a_candidate():
