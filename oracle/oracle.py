@@ -79,6 +79,22 @@ def lib():
         L.oracle_ut_response.argtypes = [_F64P, _F64P]
         L.oracle_ut_response.restype = ctypes.c_double
         L.oracle_pixel_ray.argtypes = [ctypes.c_int, ctypes.c_int, _F64P, _F64P]
+        L.oracle_project_lp.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
+                                        _F64P, _I32P, _I32P, _F64P, _F64P]
+        L.oracle_lp_chord.argtypes = [_F64P, ctypes.c_double, ctypes.c_double]
+        L.oracle_lp_chord.restype = ctypes.c_double
+        L.oracle_lp_keep.argtypes = [_F64P, ctypes.c_int, ctypes.c_int, _F64P, _F64P]
+        L.oracle_lp_keep.restype = ctypes.c_int
+        L.oracle_lp_tile_bound.argtypes = [_F64P, ctypes.c_int, ctypes.c_int, _F64P, _F64P]
+        L.oracle_lp_tile_bound.restype = ctypes.c_double
+        L.oracle_bin_lp.argtypes = [ctypes.c_int64, _F64P, _F64P, _F32P, _F32P, _I32P, _F64P, _F64P, ctypes.c_int,
+                                    _I64P, _I32P, _U64P, _U32P]
+        L.oracle_bin_lp.restype = ctypes.c_int64
+        L.oracle_render_tiles_lp.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, ctypes.c_double,
+                                             _F64P, _F64P, _I32P, _I32P, _U64P]
+        L.oracle_render_bwd_tiles_lp.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_project_lp_bwd.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
+                                            _F64P, _F64P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_abi_version.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -431,6 +447,125 @@ def grads_brute(scene_arrays, cam, cfg, d_image):
     d_rec = render_bwd_brute(pr["rec"], cam, cfg, d_image)
     g = project_bwd(mu, s, q, o, sh, cam, cfg, d_rec)
     g["d_rec"] = d_rec
+    return g
+
+
+# --------------------------------------------------------------------------- LinPrim
+
+def project_lp(mu, scale, quat, opac, sh, cam, cfg):
+    """LinPrim projection.  rec[n,12] (mu_2D, rgb, Euclidean depth, visible), sd[n,16] = (mu_2D,
+    c0, c1, c2 (rows of A^-1), sigma, rgb), bbox, tc, pre, aux[n,12] = (A row-major, ex, ey, camera z)."""
+    mu, scale, quat, opac, sh = map(_f64, (mu, scale, quat, opac, sh))
+    n = mu.shape[0]
+    rec, sd, aux = np.zeros((n, 12)), np.zeros((n, 16)), np.zeros((n, 12))
+    bbox, tc, pre = np.zeros((n, 4), np.int32), np.zeros(n, np.int32), np.zeros((n, 4))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_project_lp(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P), _p(sh, _F64P),
+                            _p(ca, _F64P), _p(fa, _F64P), _p(rec, _F64P), _p(sd, _F64P), _p(bbox, _I32P),
+                            _p(tc, _I32P), _p(pre, _F64P), _p(aux, _F64P))
+    return dict(rec=rec, sd=sd, bbox=bbox, tc=tc, pre=pre, A=aux[:, :9].reshape(-1, 3, 3), ex=aux[:, 9],
+                ey=aux[:, 10], z=aux[:, 11])
+
+
+def lp_chord(sd_row, dX, dY) -> float:
+    return float(lib().oracle_lp_chord(_p(_f64(sd_row), _F64P), float(dX), float(dY)))
+
+
+def lp_keep(sd_row, tx, ty, cam, cfg) -> bool:
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    return bool(lib().oracle_lp_keep(_p(_f64(sd_row), _F64P), tx, ty, _p(ca, _F64P), _p(fa, _F64P)))
+
+
+def lp_tile_bound(sd_row, tx, ty, cam, cfg) -> float:
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    return float(lib().oracle_lp_tile_bound(_p(_f64(sd_row), _F64P), tx, ty, _p(ca, _F64P), _p(fa, _F64P)))
+
+
+def bin_pairs_lp(rec, sd, bbox, cam, cfg, exact32: bool, order=None):
+    """LinPrim replicate + tile ID + cull.  exact32: rec float32 records and sd the kernels'
+    float32 shader data [n,20] (their FP32 decision); else rec/sd the oracle's FP64 ones."""
+    bbox = np.ascontiguousarray(bbox, np.int32)
+    n = bbox.shape[0]
+    od = None if order is None else np.ascontiguousarray(order, np.int64)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    r64 = None if exact32 else _f64(rec)
+    s64 = None if exact32 else _f64(sd)
+    r32 = np.ascontiguousarray(rec, np.float32) if exact32 else None
+    s32 = np.ascontiguousarray(sd, np.float32) if exact32 else None
+    counts = np.zeros(n, np.int32)
+    args = (n, _p(r64, _F64P), _p(s64, _F64P), _p(r32, _F32P), _p(s32, _F32P), _p(bbox, _I32P), _p(ca, _F64P),
+            _p(fa, _F64P), int(exact32), _p(od, _I64P), _p(counts, _I32P))
+    total = lib().oracle_bin_lp(*args, None, None)
+    keys = np.zeros(max(total, 1), np.uint64)
+    vals = np.zeros(max(total, 1), np.uint32)
+    lib().oracle_bin_lp(*args, _p(keys, _U64P), _p(vals, _U32P))
+    return counts, keys[:total].copy(), vals[:total].copy()
+
+
+def render_tiles_lp(sd, vals, ranges, cam, cfg, delta: float = 0.0):
+    sd = _f64(sd)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    H, W = cam.height, cam.width
+    image, tfin = np.zeros((3, H, W)), np.zeros((H, W))
+    nc, band, psig = np.zeros((H, W), np.int32), np.zeros((H, W), np.int32), np.zeros((H, W), np.uint64)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_tiles_lp(sd.shape[0], _p(sd, _F64P), _p(vv, _U32P), _p(ranges, _I32P), _p(ca, _F64P),
+                                 _p(fa, _F64P), delta, _p(image, _F64P), _p(tfin, _F64P), _p(nc, _I32P),
+                                 _p(band, _I32P), _p(psig, _U64P))
+    return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool), pixel_sig=psig)
+
+
+def render_bwd_tiles_lp(sd, vals, ranges, cam, cfg, d_image):
+    sd, d_image = _f64(sd), _f64(d_image)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    d_sd = np.zeros((sd.shape[0], 16))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_bwd_tiles_lp(sd.shape[0], _p(sd, _F64P), _p(vv, _U32P), _p(ranges, _I32P), _p(ca, _F64P),
+                                     _p(fa, _F64P), _p(d_image, _F64P), _p(d_sd, _F64P))
+    return d_sd
+
+
+def project_lp_bwd(mu, scale, quat, opac, sh, cam, cfg, d_sd):
+    mu, scale, quat, opac, sh, d_sd = map(_f64, (mu, scale, quat, opac, sh, d_sd))
+    n = mu.shape[0]
+    dmu, ds, dq, do, dsh = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 4)), np.zeros(n), np.zeros_like(sh)
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_project_lp_bwd(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P),
+                                _p(sh, _F64P), _p(ca, _F64P), _p(fa, _F64P), _p(d_sd, _F64P), _p(dmu, _F64P),
+                                _p(ds, _F64P), _p(dq, _F64P), _p(do, _F64P), _p(dsh, _F64P))
+    return dict(mu=dmu, scale=ds, quat=dq, opacity=do, sh=dsh)
+
+
+def pipeline_tiled_lp(scene_arrays, cam, cfg, delta: float = 0.0):
+    """FP64 LinPrim pipeline: projection -> bin (FP64 per-tile bound) -> sort -> per-tile walk."""
+    pr = project_lp(*scene_arrays, cam, cfg)
+    Wt, Ht = tiles_of(cam, cfg)
+    _, keys, vals = bin_pairs_lp(pr["rec"], pr["sd"], pr["bbox"], cam, cfg, exact32=False)
+    keys, vals, ranges = sort_pairs(keys, vals, Wt * Ht)
+    out = render_tiles_lp(pr["sd"], vals, ranges, cam, cfg, delta)
+    out.update(proj=pr, keys=keys, vals=vals, ranges=ranges)
+    return out
+
+
+def loss_tiled_lp(scene_arrays, cam, cfg, w):
+    import hashlib
+    out = pipeline_tiled_lp(scene_arrays, cam, cfg)
+    h = hashlib.sha1()
+    for a in (out["vals"], out["ranges"], out["pixel_sig"]):
+        h.update(np.ascontiguousarray(a).tobytes())
+    return float((w * out["image"]).sum()), h.hexdigest()
+
+
+def grads_tiled_lp(scene_arrays, cam, cfg, d_image):
+    mu, s, q, o, sh = scene_arrays
+    out = pipeline_tiled_lp(scene_arrays, cam, cfg)
+    d_sd = render_bwd_tiles_lp(out["proj"]["sd"], out["vals"], out["ranges"], cam, cfg, d_image)
+    g = project_lp_bwd(mu, s, q, o, sh, cam, cfg, d_sd)
+    g["d_sd"] = d_sd
     return g
 
 

@@ -1571,4 +1571,611 @@ void oracle_project_ut_bwd(int64_t n, const double *mu, const double *scale, con
     }
 }
 
-int oracle_abi_version(void) { return 3; }
+/* ------------------------------------------------------------------------ */
+/* LinPrim (Appendix, implementation of XPR-LinPrim; Listing LinPrim).       */
+/* Octahedron {x : ||S^-1 R^T (x - mu)||_1 <= 1}, homogeneous density        */
+/*   sigma = -log(1 - 0.99 o) / (2 min s),  o clipped to [0, 0.999].         */
+/* Projection: m_c = W mu + t, d = |m_c|, mu_2D = (fx x/z + cx, fy y/z + cy), */
+/* A = J3 W R diag(s) with J3 the pinhole Jacobian of (x_px, y_px) and a     */
+/* third row d|m_c|/dm_c = m_c / d (Euclidean distance, so tau is depth     */
+/* along the ray); c0, c1, c2 = rows of A^-1; slab normals                   */
+/*   n_i = c0 + e1 c1 + e2 c2, (e1, e2) = (+,+), (+,-), (-,+), (-,-).        */
+/* Extents: the largest pixel offsets of the six vertices, ex = max_k        */
+/* |A_0k|, ey = max_k |A_1k|; the box of mu_2D - 0.5 as 3DGUT; depth = d.    */
+/* Visible iff camera z > z_near, d > z_near, min s > 0, r > 0, tc > 0.      */
+/* Evaluate at (x + 0.5, y + 0.5): slab i bounds tau to [m_i - h_i, m_i +    */
+/* h_i], m_i = -(n_ix dX + n_iy dY) / n_iz, h_i = 1 / |n_iz| (|n_iz| <       */
+/* 1e-10: no bound); dtau = min hi - max lo, alpha = 1 - exp(-sigma dtau)    */
+/* when positive, else 0.  Tile cull: the per-tile bound of Eq.              */
+/* (linprim_tile_cull) over the four pixel-centre corners of the tile.       */
+/* Records: rec[12] with mu_2D [0,1], rgb [6..8], depth d [9], visible [11]; */
+/* sd[16] = mu_2D (2), c0, c1, c2 (9), sigma, rgb (3), 0.                   */
+/* ------------------------------------------------------------------------ */
+
+#define LP_EPS 1e-10
+#define LP_INF 1e10
+static const double LP_E[4][2] = {{1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
+
+typedef struct {
+    double mc[3], d, mu2d[2], J[9], M[9], A[9], Ai[9], n[4][3], ex, ey, sigma, smin, oc, rgb[3], raw[3], dir[3],
+        vlen, qn[4], qnorm, R[9], pre[4];
+    int kmin, oclip, bbox[4], tc, visible, front;
+} oproj_lp;
+
+static double det3(const double *A) {
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* inverse by cofactors; returns the determinant */
+static double inv3(const double *A, double *Ai) {
+    double dt = det3(A);
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) / dt;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) / dt;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) / dt;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) / dt;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) / dt;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) / dt;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) / dt;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) / dt;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) / dt;
+    return dt;
+}
+
+static void project_lp_one(const double *mu, const double *s, const double *q, double o, const double *sh,
+                           const ocam *cam, const ocfg *cfg, oproj_lp *P) {
+    memset(P, 0, sizeof(*P));
+    const double *V = cam->V;
+    for (int i = 0; i < 3; ++i) P->mc[i] = V[4 * i] * mu[0] + V[4 * i + 1] * mu[1] + V[4 * i + 2] * mu[2] + V[4 * i + 3];
+    quat_rot(q, P->qn, &P->qnorm, P->R);
+    double cp[3];
+    for (int i = 0; i < 3; ++i) cp[i] = -(V[i] * V[3] + V[4 + i] * V[7] + V[8 + i] * V[11]);
+    double v[3] = {mu[0] - cp[0], mu[1] - cp[1], mu[2] - cp[2]};
+    P->vlen = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int i = 0; i < 3; ++i) P->dir[i] = v[i] / P->vlen;
+    int K = (cfg->deg + 1) * (cfg->deg + 1);
+    double Y[16];
+    oracle_sh_basis(cfg->deg, P->dir, Y, NULL);
+    for (int c = 0; c < 3; ++c) {
+        double acc = 0.5;
+        for (int k = 0; k < K; ++k) acc += sh[3 * k + c] * Y[k];
+        P->raw[c] = acc;
+        P->rgb[c] = acc > 0.0 ? acc : 0.0;
+    }
+    P->kmin = 0;
+    for (int k = 1; k < 3; ++k)
+        if (s[k] < s[P->kmin]) P->kmin = k;
+    P->smin = s[P->kmin];
+    P->oc = o < 0.0 ? 0.0 : (o > 0.999 ? 0.999 : o);
+    P->oclip = !(o > 0.0 && o < 0.999);
+    P->sigma = -log1p(-0.99 * P->oc) / (2.0 * P->smin);
+    const double x = P->mc[0], y = P->mc[1], z = P->mc[2];
+    P->d = sqrt(x * x + y * y + z * z);
+    P->front = (z > cam->z_near) && (P->d > cam->z_near) && (P->smin > 0.0);
+    if (!P->front) return;
+    P->mu2d[0] = cam->fx * x / z + cam->cx;
+    P->mu2d[1] = cam->fy * y / z + cam->cy;
+    double J[9] = {cam->fx / z, 0.0, -cam->fx * x / (z * z), 0.0, cam->fy / z, -cam->fy * y / (z * z),
+                   x / P->d, y / P->d, z / P->d};
+    memcpy(P->J, J, sizeof(J));
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+            P->M[3 * i + k] = V[4 * i] * P->R[k] + V[4 * i + 1] * P->R[3 + k] + V[4 * i + 2] * P->R[6 + k];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+            P->A[3 * i + k] = (J[3 * i] * P->M[k] + J[3 * i + 1] * P->M[3 + k] + J[3 * i + 2] * P->M[6 + k]) * s[k];
+    inv3(P->A, P->Ai);
+    for (int i = 0; i < 4; ++i)
+        for (int c = 0; c < 3; ++c)
+            P->n[i][c] = P->Ai[c] + LP_E[i][0] * P->Ai[3 + c] + LP_E[i][1] * P->Ai[6 + c];
+    P->ex = fmax(fabs(P->A[0]), fmax(fabs(P->A[1]), fabs(P->A[2])));
+    P->ey = fmax(fabs(P->A[3]), fmax(fabs(P->A[4]), fabs(P->A[5])));
+    double r = P->ex > P->ey ? P->ex : P->ey;
+    int Wt = (cam->W + cfg->tw - 1) / cfg->tw, Ht = (cam->H + cfg->th - 1) / cfg->th;
+    P->pre[0] = (P->mu2d[0] - 0.5 - P->ex) / cfg->tw;
+    P->pre[1] = (P->mu2d[1] - 0.5 - P->ey) / cfg->th;
+    P->pre[2] = (P->mu2d[0] - 0.5 + P->ex) / cfg->tw;
+    P->pre[3] = (P->mu2d[1] - 0.5 + P->ey) / cfg->th;
+    P->bbox[0] = (int)clampd(floor(P->pre[0]), 0.0, (double)Wt);
+    P->bbox[1] = (int)clampd(floor(P->pre[1]), 0.0, (double)Ht);
+    P->bbox[2] = (int)clampd(floor(P->pre[2]) + 1.0, 0.0, (double)Wt);
+    P->bbox[3] = (int)clampd(floor(P->pre[3]) + 1.0, 0.0, (double)Ht);
+    int tc = (P->bbox[2] - P->bbox[0]) * (P->bbox[3] - P->bbox[1]);
+    P->visible = (r > 0.0) && (tc > 0);
+    P->tc = P->visible ? tc : 0;
+    if (!P->visible) memset(P->bbox, 0, sizeof(P->bbox));
+}
+
+void oracle_project_lp(int64_t n, const double *mu, const double *scale, const double *quat, const double *opac,
+                       const double *sh, const double *camv, const double *cfgv, double *rec, double *sd,
+                       int32_t *bbox, int32_t *tc, double *pre, double *aux) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int K = (cfg.deg + 1) * (cfg.deg + 1);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        oproj_lp P;
+        project_lp_one(mu + 3 * i, scale + 3 * i, quat + 4 * i, opac[i], sh + (int64_t)3 * K * i, &cam, &cfg, &P);
+        double *r = rec + 12 * i, *d = sd + 16 * i;
+        memset(r, 0, 12 * sizeof(double));
+        memset(d, 0, 16 * sizeof(double));
+        r[9] = P.d;
+        if (P.visible) {
+            r[0] = P.mu2d[0];
+            r[1] = P.mu2d[1];
+            for (int c = 0; c < 3; ++c) r[6 + c] = P.rgb[c];
+            r[11] = 1.0;
+            d[0] = P.mu2d[0];
+            d[1] = P.mu2d[1];
+            for (int k = 0; k < 9; ++k) d[2 + k] = P.Ai[k];
+            d[11] = P.sigma;
+            for (int c = 0; c < 3; ++c) d[12 + c] = P.rgb[c];
+        }
+        for (int j = 0; j < 4; ++j) bbox[4 * i + j] = P.bbox[j];
+        tc[i] = P.tc;
+        if (pre)
+            for (int j = 0; j < 4; ++j) pre[4 * i + j] = P.visible ? P.pre[j] : 0.0;
+        if (aux) { /* A (9), ex, ey, camera z */
+            for (int k = 0; k < 9; ++k) aux[12 * i + k] = P.A[k];
+            aux[12 * i + 9] = P.ex;
+            aux[12 * i + 10] = P.ey;
+            aux[12 * i + 11] = P.mc[2];
+        }
+    }
+}
+
+/* slab normals of paper-form shader data */
+static void lp_normals(const double *S, double n[4][3]) {
+    for (int i = 0; i < 4; ++i)
+        for (int c = 0; c < 3; ++c) n[i][c] = S[2 + c] + LP_E[i][0] * S[5 + c] + LP_E[i][1] * S[8 + c];
+}
+
+/* chord dtau of the slab intersection at pixel-centre offset (dX, dY); lo / hi receive the binding
+ * slabs (may be NULL) */
+static double lp_chord(const double n[4][3], double dX, double dY, int *lo_i, int *hi_i) {
+    double enter = -INFINITY, exit_ = INFINITY;
+    int li = -1, hj = -1;
+    for (int i = 0; i < 4; ++i) {
+        if (!(fabs(n[i][2]) >= LP_EPS)) continue;
+        double m = -(n[i][0] * dX + n[i][1] * dY) / n[i][2], h = 1.0 / fabs(n[i][2]);
+        if (m - h > enter) {
+            enter = m - h;
+            li = i;
+        }
+        if (m + h < exit_) {
+            exit_ = m + h;
+            hj = i;
+        }
+    }
+    if (lo_i) *lo_i = li;
+    if (hi_i) *hi_i = hj;
+    return (enter < exit_) ? exit_ - enter : 0.0;
+}
+
+double oracle_lp_chord(const double *sd, double dX, double dY) {
+    double n[4][3];
+    lp_normals(sd, n);
+    return lp_chord(n, dX, dY, NULL, NULL);
+}
+
+/* The per-tile bound of Eq. (linprim_tile_cull) at pixel-centre corners X in {x0, x1}, Y in {y0, y1}. */
+static double lp_tile_bound(const double n[4][3], double mx, double my, double x0, double y0, double x1, double y1) {
+    double mc[4][4], half[4];
+    const double cx[4] = {x0, x0, x1, x1}, cy[4] = {y0, y1, y0, y1};
+    for (int i = 0; i < 4; ++i) {
+        int ok = fabs(n[i][2]) >= LP_EPS;
+        double inv = ok ? 1.0 / n[i][2] : 0.0;
+        half[i] = ok ? fabs(inv) : LP_INF;
+        for (int c = 0; c < 4; ++c) mc[i][c] = -inv * (n[i][0] * (cx[c] - mx) + n[i][1] * (cy[c] - my));
+    }
+    double best = INFINITY;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            double g = -INFINITY;
+            for (int c = 0; c < 4; ++c) g = fmax(g, mc[i][c] - mc[j][c]);
+            g += half[i] + half[j];
+            if (g < best) best = g;
+        }
+    return best > 0.0 ? best : 0.0;
+}
+
+/* The kernels' FP32 cull decision on their shader data s32[20]: mu_2D (2), sigma, -log(1 -
+ * alpha_t), then per slab (p, q, h) = (n_x / n_z, n_y / n_z, 1 / |n_z|) (p = q = 0, h = inf when
+ * |n_z| < 1e-10); one correctly rounded IEEE operation per step in this order, no FMA. */
+static int lp_keep_f32(const float *s32, float X0, float Y0, float X1, float Y1) {
+    const float mx = s32[0], my = s32[1], sigma = s32[2], req = s32[3];
+    const float dX[2] = {X0 - mx, X1 - mx}, dY[2] = {Y0 - my, Y1 - my};
+    float m[4][4], h[4];
+    for (int i = 0; i < 4; ++i) {
+        const float p = s32[4 + 3 * i], qq = s32[5 + 3 * i];
+        h[i] = s32[6 + 3 * i];
+        for (int c = 0; c < 4; ++c) {
+            float t = p * dX[c >> 1];
+            float u = qq * dY[c & 1];
+            float w = t + u;
+            m[i][c] = -w;
+        }
+    }
+    float best = INFINITY;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            float g = m[i][0] - m[j][0];
+            for (int c = 1; c < 4; ++c) {
+                float e = m[i][c] - m[j][c];
+                g = fmaxf(g, e);
+            }
+            g = g + h[i];
+            g = g + h[j];
+            best = fminf(best, g);
+        }
+    best = fmaxf(best, 0.0f);
+    float a = sigma * best;
+    return a >= req;
+}
+
+/* tile bounds for LinPrim: the corners' pixel centres (inclusive pixel bounds + 0.5) */
+static void lp_tile_corners(int tx, int ty, const ocam *cam, const ocfg *cfg, double *c) {
+    int x0 = tx * cfg->tw, y0 = ty * cfg->th;
+    int x1 = x0 + cfg->tw - 1, y1 = y0 + cfg->th - 1;
+    if (x1 > cam->W - 1) x1 = cam->W - 1;
+    if (y1 > cam->H - 1) y1 = cam->H - 1;
+    c[0] = x0 + 0.5;
+    c[1] = y0 + 0.5;
+    c[2] = x1 + 0.5;
+    c[3] = y1 + 0.5;
+}
+
+int oracle_lp_keep(const double *sd, int tx, int ty, const double *camv, const double *cfgv) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    double n[4][3], c[4];
+    lp_normals(sd, n);
+    lp_tile_corners(tx, ty, &cam, &cfg, c);
+    double req = -log1p(-cfg.at);
+    return sd[11] * lp_tile_bound(n, sd[0], sd[1], c[0], c[1], c[2], c[3]) >= req;
+}
+
+double oracle_lp_tile_bound(const double *sd, int tx, int ty, const double *camv, const double *cfgv) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    double n[4][3], c[4];
+    lp_normals(sd, n);
+    lp_tile_corners(tx, ty, &cam, &cfg, c);
+    return lp_tile_bound(n, sd[0], sd[1], c[0], c[1], c[2], c[3]);
+}
+
+/* Binning for LinPrim (as oracle_bin): exact32 != 0 takes the FP32 decision on kernel-form shader
+ * data sd32[n*20] and depths from rec32; else the FP64 bound on paper-form sd64[n*16] with rec64. */
+int64_t oracle_bin_lp(int64_t n, const double *rec64, const double *sd64, const float *rec32, const float *sd32,
+                      const int32_t *bbox, const double *camv, const double *cfgv, int exact32,
+                      const int64_t *order, int32_t *counts, uint64_t *keys, uint32_t *vals) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw;
+    double req = -log1p(-cfg.at);
+    int64_t total = 0;
+    for (int64_t pos = 0; pos < n; ++pos) {
+        int64_t i = order ? order[pos] : pos;
+        const int32_t *bb = bbox + 4 * i;
+        int w = bb[2] - bb[0], h = bb[3] - bb[1];
+        int tc = (w > 0 && h > 0) ? w * h : 0;
+        int cnt = 0;
+        double nn[4][3];
+        if (!exact32 && tc > 0) lp_normals(sd64 + 16 * i, nn);
+        for (int r = 0; r < tc; ++r) {
+            int tx = bb[0] + r % w, ty = bb[1] + r / w;
+            double c[4];
+            lp_tile_corners(tx, ty, &cam, &cfg, c);
+            int keep;
+            float depth32;
+            if (exact32) {
+                keep = lp_keep_f32(sd32 + 20 * i, (float)c[0], (float)c[1], (float)c[2], (float)c[3]);
+                depth32 = rec32[12 * i + 9];
+            } else {
+                const double *S = sd64 + 16 * i;
+                keep = S[11] * lp_tile_bound(nn, S[0], S[1], c[0], c[1], c[2], c[3]) >= req;
+                depth32 = (float)rec64[12 * i + 9];
+            }
+            if (!keep) continue;
+            if (keys) {
+                keys[total] = ((uint64_t)(uint32_t)(ty * Wt + tx) << 32) | (uint64_t)f32_bits(depth32);
+                vals[total] = (uint32_t)i;
+            }
+            ++total;
+            ++cnt;
+        }
+        if (counts) counts[pos] = cnt;
+    }
+    return total;
+}
+
+typedef struct {
+    int64_t idx;
+    double alpha, T, dt, e;
+    int clamped, lo, hi;
+    double dX, dY;
+} contrib_lp;
+
+/* the compositing walk of the framework with the LinPrim evaluate (valid = 1) */
+static int walk_lp(double X, double Y, const double *sd, const int64_t *list, int len, const ocfg *cfg, double delta,
+                   double C[3], double *Tout, int *last, int *band, contrib_lp *out, uint64_t *sig) {
+    double T = 1.0;
+    C[0] = C[1] = C[2] = 0.0;
+    int nc = 0, bd = 0;
+    uint64_t hsh = sig ? *sig : 0;
+    *last = 0;
+    for (int k = 0; k < len; ++k) {
+        const double *S = sd + 16 * list[k];
+        double n[4][3];
+        lp_normals(S, n);
+        double dX = X - S[0], dY = Y - S[1];
+        int lo, hi;
+        double dt = lp_chord(n, dX, dY, &lo, &hi);
+        double e = exp(-S[11] * dt);
+        double a0 = dt > 0.0 ? 1.0 - e : 0.0;
+        double alpha = a0 < cfg->amax ? a0 : cfg->amax;
+        if (fabs(a0 - cfg->amax) <= delta * cfg->amax) bd = 1;
+        if (fabs(alpha - cfg->at) <= delta * cfg->at) bd = 1;
+        if (alpha < cfg->at) continue;
+        double tt = T * (1.0 - alpha);
+        if (fabs(tt - cfg->teps) <= delta * cfg->teps) bd = 1;
+        if (tt < cfg->teps) {
+            hsh = hsh * 1099511628211ULL ^ 0xffffULL;
+            break;
+        }
+        if (out) {
+            contrib_lp *c = out + nc;
+            c->idx = list[k];
+            c->alpha = alpha;
+            c->T = T;
+            c->dt = dt;
+            c->e = e;
+            c->clamped = !(a0 < cfg->amax);
+            c->lo = lo;
+            c->hi = hi;
+            c->dX = dX;
+            c->dY = dY;
+        }
+        hsh = (hsh ^ (uint64_t)(list[k] + 1)) * 1099511628211ULL;
+        hsh = (hsh ^ (uint64_t)(4 * lo + hi + 17)) * 1099511628211ULL;
+        for (int c = 0; c < 3; ++c) C[c] += S[12 + c] * alpha * T;
+        T = tt;
+        ++nc;
+        *last = k + 1;
+    }
+    for (int c = 0; c < 3; ++c) C[c] += T * cfg->bg[c];
+    *Tout = T;
+    *band = bd;
+    if (sig) *sig = hsh;
+    return nc;
+}
+
+void oracle_render_tiles_lp(int64_t n, const double *sd, const uint32_t *vals, const int32_t *ranges,
+                            const double *camv, const double *cfgv, double delta, double *image, double *tfinal,
+                            int32_t *ncontrib, int32_t *band, uint64_t *psig) {
+    (void)n;
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
+    int64_t HW = (int64_t)cam.W * cam.H;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < Wt * Ht; ++t) {
+        int tx = t % Wt, ty = t / Wt;
+        int s0 = ranges[2 * t], e0 = ranges[2 * t + 1];
+        int len = e0 - s0;
+        int64_t *list = (int64_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int64_t));
+        for (int k = 0; k < len; ++k) list[k] = vals[s0 + k];
+        for (int yy = 0; yy < cfg.th; ++yy)
+            for (int xx = 0; xx < cfg.tw; ++xx) {
+                int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
+                if (x >= cam.W || y >= cam.H) continue;
+                double C[3], T;
+                int last, bd;
+                uint64_t h = 0;
+                walk_lp(x + 0.5, y + 0.5, sd, list, len, &cfg, delta, C, &T, &last, &bd, NULL, &h);
+                int64_t p = (int64_t)y * cam.W + x;
+                for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
+                tfinal[p] = T;
+                ncontrib[p] = last;
+                band[p] = bd;
+                if (psig) psig[p] = h;
+            }
+        free(list);
+    }
+}
+
+/* Adjoint of the LinPrim walk: dtau = (m_hi + h_hi) - (m_lo - h_lo) for the binding slabs, with
+ * m = -(n_x dX + n_y dY) / n_z and h = 1 / |n_z|:
+ *   dm/dn_x = -dX / n_z, dm/dn_y = -dY / n_z, dm/dn_z = -m / n_z, dh/dn_z = -h / n_z,
+ *   dm/dmu_x = n_x / n_z, dm/dmu_y = n_y / n_z;
+ * alpha = 1 - exp(-sigma dtau): dalpha/dsigma = dtau e, dalpha/ddtau = sigma e (nothing through the
+ * clamp); n_i = c0 + e1 c1 + e2 c2.  d_sd[n*16] in the paper-form layout. */
+static void pixel_adjoint_lp(const double *sd, const contrib_lp *cs, int nc, double Tfin, const double *g,
+                             const ocfg *cfg, double *d_sd) {
+    if (nc == 0) return;
+    double *S = (double *)malloc((size_t)nc * 3 * sizeof(double));
+    for (int c = 0; c < 3; ++c) {
+        double acc = Tfin * cfg->bg[c];
+        for (int i = nc - 1; i >= 0; --i) {
+            S[3 * i + c] = acc;
+            acc += sd[16 * cs[i].idx + 12 + c] * cs[i].alpha * cs[i].T;
+        }
+    }
+    for (int i = 0; i < nc; ++i) {
+        const double *Sd = sd + 16 * cs[i].idx;
+        double *D = d_sd + 16 * cs[i].idx;
+        double a = cs[i].alpha, T = cs[i].T;
+        double da = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            D[12 + c] += g[c] * a * T;
+            da += g[c] * (Sd[12 + c] * T - S[3 * i + c] / (1.0 - a));
+        }
+        if (cs[i].clamped) continue;
+        D[11] += da * cs[i].dt * cs[i].e;
+        double gdt = da * Sd[11] * cs[i].e;
+        double n[4][3];
+        lp_normals(Sd, n);
+        for (int side = 0; side < 2; ++side) {
+            int k = side == 0 ? cs[i].hi : cs[i].lo;
+            double gm = side == 0 ? gdt : -gdt, gh = gdt;
+            const double *nk = n[k];
+            double m = -(nk[0] * cs[i].dX + nk[1] * cs[i].dY) / nk[2], h = 1.0 / fabs(nk[2]);
+            double gn[3] = {gm * (-cs[i].dX / nk[2]), gm * (-cs[i].dY / nk[2]), gm * (-m / nk[2]) + gh * (-h / nk[2])};
+            D[0] += gm * nk[0] / nk[2];
+            D[1] += gm * nk[1] / nk[2];
+            for (int c = 0; c < 3; ++c) {
+                D[2 + c] += gn[c];
+                D[5 + c] += LP_E[k][0] * gn[c];
+                D[8 + c] += LP_E[k][1] * gn[c];
+            }
+        }
+    }
+    free(S);
+}
+
+void oracle_render_bwd_tiles_lp(int64_t n, const double *sd, const uint32_t *vals, const int32_t *ranges,
+                                const double *camv, const double *cfgv, const double *d_image, double *d_sd) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
+    int64_t HW = (int64_t)cam.W * cam.H;
+    memset(d_sd, 0, (size_t)n * 16 * sizeof(double));
+    for (int t = 0; t < Wt * Ht; ++t) {
+        int tx = t % Wt, ty = t / Wt;
+        int s0 = ranges[2 * t], e0 = ranges[2 * t + 1];
+        int len = e0 - s0;
+        if (len <= 0) continue;
+        int64_t *list = (int64_t *)malloc((size_t)len * sizeof(int64_t));
+        contrib_lp *cs = (contrib_lp *)malloc((size_t)len * sizeof(contrib_lp));
+        for (int k = 0; k < len; ++k) list[k] = vals[s0 + k];
+        for (int yy = 0; yy < cfg.th; ++yy)
+            for (int xx = 0; xx < cfg.tw; ++xx) {
+                int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
+                if (x >= cam.W || y >= cam.H) continue;
+                int64_t p = (int64_t)y * cam.W + x;
+                double g[3] = {d_image[p], d_image[HW + p], d_image[2 * HW + p]};
+                if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
+                double C[3], T;
+                int last, bd;
+                int nc = walk_lp(x + 0.5, y + 0.5, sd, list, len, &cfg, 0.0, C, &T, &last, &bd, cs, NULL);
+                pixel_adjoint_lp(sd, cs, nc, T, g, &cfg, d_sd);
+            }
+        free(cs);
+        free(list);
+    }
+}
+
+/* Adjoint of the LinPrim projection from paper-form d_sd (dmu_2D, dc0, dc1, dc2, dsigma, drgb):
+ *   A^-1 rows c_k: dA = -A^-T dA^-1 A^-T;  A = J3 M diag(s), M = W R:
+ *     dJ3 = dA (M diag(s))^T, dM = J3^T dA diag(s), ds_k += sum_i dA_ik (J3 M)_ik, dR = W^T dM;
+ *   J3(m_c): J00 = fx/z, J02 = -fx x/z^2, J11 = fy/z, J12 = -fy y/z^2, J2k = m_c,k / d;
+ *   mu_2D(m_c); m_c = W mu + t;
+ *   sigma = -log(1 - 0.99 o) / (2 s_min): dsigma/do = 0.99 / ((1 - 0.99 o) 2 s_min) (0 where o is
+ *   clipped), dsigma/ds_min = -sigma / s_min;  colour as in 3DGS. */
+void oracle_project_lp_bwd(int64_t n, const double *mu, const double *scale, const double *quat, const double *opac,
+                           const double *sh, const double *camv, const double *cfgv, const double *d_sd,
+                           double *dmu, double *dscale, double *dquat, double *dopac, double *dsh) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int K = (cfg.deg + 1) * (cfg.deg + 1);
+    const double *V = cam.V;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        oproj_lp P;
+        const double *D = d_sd + 16 * i;
+        const double *s = scale + 3 * i;
+        const double *shi = sh + (int64_t)3 * K * i;
+        double *gmu = dmu + 3 * i, *gs = dscale + 3 * i, *gq = dquat + 4 * i, *gsh = dsh + (int64_t)3 * K * i;
+        project_lp_one(mu + 3 * i, s, quat + 4 * i, opac[i], shi, &cam, &cfg, &P);
+        memset(gmu, 0, 3 * sizeof(double));
+        memset(gs, 0, 3 * sizeof(double));
+        memset(gq, 0, 4 * sizeof(double));
+        memset(gsh, 0, (size_t)3 * K * sizeof(double));
+        dopac[i] = 0.0;
+        if (!P.visible) continue;
+        /* colour */
+        double Y[16], dY[48];
+        oracle_sh_basis(cfg.deg, P.dir, Y, dY);
+        double gdir[3] = {0, 0, 0};
+        for (int c = 0; c < 3; ++c) {
+            if (!(P.raw[c] > 0.0)) continue;
+            double g = D[12 + c];
+            for (int k = 0; k < K; ++k) {
+                gsh[3 * k + c] = Y[k] * g;
+                for (int j = 0; j < 3; ++j) gdir[j] += g * shi[3 * k + c] * dY[3 * k + j];
+            }
+        }
+        double dd = gdir[0] * P.dir[0] + gdir[1] * P.dir[1] + gdir[2] * P.dir[2];
+        for (int j = 0; j < 3; ++j) gmu[j] += (gdir[j] - P.dir[j] * dd) / P.vlen;
+        /* sigma */
+        if (!P.oclip) dopac[i] = D[11] * 0.99 / ((1.0 - 0.99 * P.oc) * 2.0 * P.smin);
+        gs[P.kmin] += D[11] * (-P.sigma / P.smin);
+        /* A^-1 -> A */
+        const double *Ai = P.Ai;
+        double G[9], T1[9], dA[9];
+        for (int k = 0; k < 9; ++k) G[k] = D[2 + k];
+        /* dA = -Ai^T G Ai^T */
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += Ai[3 * k + a] * G[3 * k + b];
+                T1[3 * a + b] = acc;
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += T1[3 * a + k] * Ai[3 * b + k];
+                dA[3 * a + b] = -acc;
+            }
+        /* A = J M diag(s) */
+        double JM[9];
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k)
+                JM[3 * a + k] = P.J[3 * a] * P.M[k] + P.J[3 * a + 1] * P.M[3 + k] + P.J[3 * a + 2] * P.M[6 + k];
+        double dJ[9], dM[9];
+        for (int a = 0; a < 3; ++a)
+            for (int l = 0; l < 3; ++l) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += dA[3 * a + k] * P.M[3 * l + k] * s[k];
+                dJ[3 * a + l] = acc;
+            }
+        for (int l = 0; l < 3; ++l)
+            for (int k = 0; k < 3; ++k) {
+                double acc = 0.0;
+                for (int a = 0; a < 3; ++a) acc += P.J[3 * a + l] * dA[3 * a + k];
+                dM[3 * l + k] = acc * s[k];
+            }
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a) gs[k] += dA[3 * a + k] * JM[3 * a + k];
+        double gR[9];
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k) gR[3 * a + k] = V[a] * dM[k] + V[4 + a] * dM[3 + k] + V[8 + a] * dM[6 + k];
+        /* J(m_c) and mu_2D(m_c) */
+        const double x = P.mc[0], y = P.mc[1], z = P.mc[2], d = P.d;
+        double gmc[3] = {0, 0, 0};
+        gmc[2] += dJ[0] * (-cam.fx / (z * z));
+        gmc[0] += dJ[2] * (-cam.fx / (z * z));
+        gmc[2] += dJ[2] * (2.0 * cam.fx * x / (z * z * z));
+        gmc[2] += dJ[4] * (-cam.fy / (z * z));
+        gmc[1] += dJ[5] * (-cam.fy / (z * z));
+        gmc[2] += dJ[5] * (2.0 * cam.fy * y / (z * z * z));
+        for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) gmc[l] += dJ[6 + k] * ((k == l ? 1.0 / d : 0.0) - P.mc[k] * P.mc[l] / (d * d * d));
+        gmc[0] += D[0] * cam.fx / z;
+        gmc[1] += D[1] * cam.fy / z;
+        gmc[2] += -(D[0] * cam.fx * x + D[1] * cam.fy * y) / (z * z);
+        for (int j = 0; j < 3; ++j) gmu[j] += V[j] * gmc[0] + V[4 + j] * gmc[1] + V[8 + j] * gmc[2];
+        double dRq[4][9];
+        drot_dq(P.qn, dRq);
+        double gqn[4];
+        for (int j = 0; j < 4; ++j) {
+            double acc = 0.0;
+            for (int e = 0; e < 9; ++e) acc += gR[e] * dRq[j][e];
+            gqn[j] = acc;
+        }
+        double dotq = gqn[0] * P.qn[0] + gqn[1] * P.qn[1] + gqn[2] * P.qn[2] + gqn[3] * P.qn[3];
+        for (int j = 0; j < 4; ++j) gq[j] = (gqn[j] - P.qn[j] * dotq) / P.qnorm;
+    }
+}
+
+int oracle_abi_version(void) { return 4; }
