@@ -71,13 +71,15 @@ typedef struct XprConfig {
     int32_t sh_degree;  /* 0..3; K = (sh_degree + 1)^2 coefficients per colour channel */
     float bg[3];        /* background colour added as T_final * bg */
     int32_t batch_depth;/* render: entries staged per shared-memory batch; 0 = kernel default */
-    int32_t method;     /* XPR_METHOD_3DGS (0) or XPR_METHOD_3DGUT (1): selects the tile cull's ray
-                           offset in the binning (xpr_tile_bin*, xpr_bin_sorted) and which projection /
-                           render entry points accept the config (each refuses the other method) */
+    int32_t method;     /* XPR_METHOD_3DGS (0), XPR_METHOD_3DGUT (1) or XPR_METHOD_LINPRIM (2): selects
+                           the binning's tile cull (3DGUT: ray-offset bounds; LinPrim: the chord bound
+                           of xpr_tile_bin_lp) and which projection / render entry points accept the
+                           config (each refuses the other methods) */
 } XprConfig;
 
 #define XPR_METHOD_3DGS 0
 #define XPR_METHOD_3DGUT 1
+#define XPR_METHOD_LINPRIM 2
 
 /* 3DGS PrimitiveParams (Appendix, 3DGS implementation), structure of arrays:
  * mu[n,3] world-space means, scale[n,3] (positive, activated), quat[n,4]
@@ -402,6 +404,58 @@ int xpr_render_ut_bwd_views(const float *sd, int64_t n, int32_t n_views, const u
                             int32_t *counter, void *stream);
 int xpr_project_ut_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
                              const XprConfig *cfg, const float *d_sd, const XprPrimsGrad *d_prims, void *stream);
+
+/* ---- LinPrim (cfg->method == XPR_METHOD_LINPRIM) -------------------------------
+ * Octahedra {x : ||S^-1 R^T (x - mu)||_1 <= 1} with homogeneous density (Appendix,
+ * implementation of XPR-LinPrim).  Parameters as XprPrims with scale the three
+ * half-extents and opacity o; sigma = -log(1 - 0.99 clip(o, 0, 0.999)) / (2 min s).
+ * Projection: A = J3 W R diag(s) (J3 = pinhole Jacobian plus the row m_c / |m_c|
+ * of the Euclidean distance), c0, c1, c2 = rows of A^-1, slab normals
+ * n_i = c0 + e1 c1 + e2 c2 for (e1, e2) in (+,+), (+,-), (-,+), (-,-).
+ * Shader data, 20 floats per record (also the cull's data):
+ *   [0] mu_2D.x [1] mu_2D.y [2] sigma [3] -log(1 - alpha_thresh)
+ *   [4 + 3i .. 6 + 3i] slab i: (n_x / n_z, n_y / n_z, 1 / |n_z|) (0, 0, +inf when |n_z| < 1e-10)
+ *   [16..18] rgb [19] 0
+ * Record (rec[12]): mu_2D [0,1], rgb [6..8], Euclidean depth |m_c| [9], visible [11], rest 0;
+ * xpr_depth_order reads it as for 3DGS.  Pixel (x, y) is evaluated at (x + 0.5, y + 0.5):
+ * with (dX, dY) its offset from mu_2D, slab i admits tau in m_i -+ h_i,
+ * m_i = -(p_i dX + q_i dY); dtau = min (m + h) - max (m - h); alpha = 1 - exp(-sigma dtau)
+ * when dtau > 0 (then the framework's clamp, gate and T_eps as for 3DGS).
+ * Gradients d_sd use the shader-data layout ([3] and [19] stay 0). */
+#define XPR_LP_SD_FLOATS 20
+
+/* xpr_project_lp: extents ex = max_k |A_0k|, ey = max_k |A_1k| (the six
+ * vertices), tile box of mu_2D - 0.5 as 3DGUT; visible iff camera z > z_near,
+ * |m_c| > z_near, min s > 0, r > 0, tc > 0.  Outputs rec[n,12], sd[n,20],
+ * bbox[n,4], tile_count[n], isect_count[n] (may be NULL: kept tiles of the
+ * box under xpr_tile_bin_lp's cull).  prims->sh must not be NULL; rec, sd,
+ * bbox, quat 16-byte aligned. */
+int xpr_project_lp(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
+                   float *sd, int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream);
+
+/* xpr_tile_bin_lp: xpr_tile_bin for LinPrim.  The cull keeps a (primitive,
+ * tile) pair iff sigma dtau_upper >= -log(1 - alpha_thresh), dtau_upper the
+ * per-tile chord bound of Eq. (linprim_tile_cull) over the tile's four
+ * pixel-centre corners (inclusive pixel bounds + 0.5), decided in FP32 from
+ * sd with one correctly rounded operation per step.  Arguments, capacity
+ * protocol and outputs as xpr_tile_bin, plus sd[n,20] from xpr_project_lp. */
+int xpr_tile_bin_lp(const float *rec, const float *sd, const int32_t *bbox, const int32_t *tile_count,
+                    const int32_t *isect_count, const int32_t *order, int64_t n, const XprCamera *cam,
+                    const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *tiles, uint32_t *vals,
+                    int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
+
+/* xpr_render_lp_fwd / xpr_render_lp_bwd: compositing of the sorted lists with
+ * the LinPrim evaluate, and its reverse-order adjoint (d_sd[n,20] OVERWRITTEN). */
+int xpr_render_lp_fwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                      const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, void *stream);
+int xpr_render_lp_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                      const XprConfig *cfg, const float *t_final, const int32_t *n_contrib, const float *d_image,
+                      float *d_sd, void *stream);
+
+/* xpr_project_lp_bwd: adjoint of xpr_project_lp from d_sd[n,20] to the
+ * parameter gradients (OVERWRITTEN; zero for invisible primitives). */
+int xpr_project_lp_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
+                       const float *d_sd, const XprPrimsGrad *d_prims, void *stream);
 
 /* ---- Misc ------------------------------------------------------------------ */
 const char *xpr_status_string(int status);

@@ -517,6 +517,25 @@ def render_tiles_lp(sd, vals, ranges, cam, cfg, delta: float = 0.0):
     return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool), pixel_sig=psig)
 
 
+def condition_band_lp(sd, vals, ranges, cam, cfg, eta_px=1e-4, rel=2e-6, tol=5e-5, trials=4, seed=0):
+    """Pixels whose LinPrim image is ill-conditioned at float32 scale: the FP64 image moves by more
+    than ``tol`` when the projected centres are shifted by N(0, eta_px^2) pixels and the slab rows
+    and densities scaled by 1 + N(0, rel^2) (independently per primitive, ``trials`` draws).  Near
+    the silhouette of a face seen almost edge-on the chord is a steep function of the pixel
+    position, so there the rounding of any float32 evaluation decides the value at the 1e-4 level."""
+    sd = _f64(sd)
+    base = render_tiles_lp(sd, vals, ranges, cam, cfg)["image"]
+    rng = np.random.default_rng(seed)
+    worst = np.zeros(base.shape[1:])
+    for _ in range(trials):
+        p = sd.copy()
+        p[:, 0:2] += eta_px * rng.normal(size=(p.shape[0], 2))
+        p[:, 2:12] *= 1 + rel * rng.normal(size=(p.shape[0], 10))
+        img = render_tiles_lp(p, vals, ranges, cam, cfg)["image"]
+        worst = np.maximum(worst, np.abs(img - base).max(0))
+    return worst > tol
+
+
 def render_bwd_tiles_lp(sd, vals, ranges, cam, cfg, d_image):
     sd, d_image = _f64(sd), _f64(d_image)
     vals = np.ascontiguousarray(vals, np.uint32)

@@ -39,9 +39,10 @@ class XprPrimsGrad(ctypes.Structure):
 
 
 XPR_OK, XPR_ERR_INVALID, XPR_ERR_CAPACITY, XPR_ERR_CUDA, XPR_ERR_TIMEOUT, XPR_ERR_INTERNAL = range(6)
-XPR_METHOD_3DGS, XPR_METHOD_3DGUT = 0, 1
+XPR_METHOD_3DGS, XPR_METHOD_3DGUT, XPR_METHOD_LINPRIM = 0, 1, 2
 REC = 12
-SD = 16  # 3DGUT shader data per record
+SD = 16     # 3DGUT shader data per record
+LP_SD = 20  # LinPrim shader data per record
 
 # (name, restype, argtypes) of every exported entry point
 SIGNATURES = {
@@ -102,6 +103,17 @@ SIGNATURES = {
                                         ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "xpr_project_ut_bwd_views": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), c_i32,
                                          ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_project_lp": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                               c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_tile_bin_lp": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera),
+                                ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64),
+                                c_vp, c_sz, c_vp]),
+    "xpr_render_lp_fwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                                  c_vp, c_vp, c_vp, c_vp]),
+    "xpr_render_lp_bwd": (c_i32, [c_vp, c_i64, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                                  c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_project_lp_bwd": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
+                                   ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
     "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
@@ -636,4 +648,86 @@ def xpr_project_ut_bwd_views(mu, scale, quat, opacity, sh, cams, cfg, d_sd, stre
     g = _as_c(cfg, XprConfig)
     _check(L.xpr_project_ut_bwd_views(ctypes.byref(p), mu.shape[0], camera_array(cams), len(cams), ctypes.byref(g),
                                       _ptr(d_sd), ctypes.byref(gp), _stream(stream)), "xpr_project_ut_bwd_views")
+    return grads
+
+
+# ---------------------------------------------------------------------------------------- LinPrim
+
+def xpr_project_lp(mu, scale, quat, opacity, sh, cam, cfg, stream=None, with_isect_count=True):
+    """Returns rec[n,12], sd[n,20], bbox[n,4], tile_count[n], isect_count[n] (or None)."""
+    L = load()
+    n = mu.shape[0]
+    dev = mu.device
+    rec = torch.empty((n, REC), dtype=torch.float32, device=dev)
+    sd = torch.empty((n, LP_SD), dtype=torch.float32, device=dev)
+    bbox = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    tc = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev) if with_isect_count else None
+    p = _prims(mu, scale, quat, opacity, sh)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_project_lp(ctypes.byref(p), n, ctypes.byref(c), ctypes.byref(g), _ptr(rec), _ptr(sd), _ptr(bbox),
+                            _ptr(tc), _ptr(cnt), _stream(stream)), "xpr_project_lp")
+    return rec, sd, bbox, tc, cnt
+
+
+def xpr_tile_bin_lp(rec, sd, bbox, tile_count, cam, cfg, capacity=None, workspace=None, stream=None, order=None,
+                    isect_count=None):
+    """LinPrim binning (tile ids): returns (offsets[n+1], tiles[I] (int32 storage), vals[I], I)."""
+    L = load()
+    n = rec.shape[0]
+    dev = rec.device
+    offsets = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    need = int(L.xpr_tile_bin_workspace(n))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    cap = int(capacity) if capacity is not None else max(4 * n, 1024)
+    tiles = torch.empty(cap, dtype=torch.int32, device=dev)
+    vals = torch.empty(cap, dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    for _ in range(2):
+        got = c_i64(0)
+        s = L.xpr_tile_bin_lp(_ptr(rec), _ptr(sd), _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _ptr(order), n,
+                              ctypes.byref(c), ctypes.byref(g), _ptr(offsets), None, _ptr(tiles), _ptr(vals),
+                              tiles.numel(), ctypes.byref(got), _ptr(workspace), workspace.numel(), _stream(stream))
+        if s == XPR_ERR_CAPACITY and got.value <= 0x7FFFFFFF:
+            tiles = torch.empty(got.value, dtype=torch.int32, device=dev)
+            vals = torch.empty(got.value, dtype=torch.int32, device=dev)
+            continue
+        _check(s, "xpr_tile_bin_lp")
+        I = int(got.value)
+        return offsets, tiles[:I], vals[:I], I
+    raise XprError(XPR_ERR_CAPACITY, "xpr_tile_bin_lp", "capacity retry failed")
+
+
+def xpr_render_lp_fwd(sd, vals, ranges, cam, cfg, stream=None):
+    L = load()
+    dev = sd.device
+    H, W = int(cam.height), int(cam.width)
+    image = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    t_final = torch.empty((H, W), dtype=torch.float32, device=dev)
+    n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_lp_fwd(_ptr(sd), sd.shape[0], _ptr(vals), _ptr(ranges), ctypes.byref(c), ctypes.byref(g),
+                               _ptr(image), _ptr(t_final), _ptr(n_contrib), _stream(stream)), "xpr_render_lp_fwd")
+    return image, t_final, n_contrib
+
+
+def xpr_render_lp_bwd(sd, vals, ranges, cam, cfg, t_final, n_contrib, d_image, stream=None):
+    L = load()
+    d_sd = torch.empty((sd.shape[0], LP_SD), dtype=torch.float32, device=sd.device)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_lp_bwd(_ptr(sd), sd.shape[0], _ptr(vals), _ptr(ranges), ctypes.byref(c), ctypes.byref(g),
+                               _ptr(t_final), _ptr(n_contrib), _ptr(d_image.contiguous()), _ptr(d_sd),
+                               _stream(stream)), "xpr_render_lp_bwd")
+    return d_sd
+
+
+def xpr_project_lp_bwd(mu, scale, quat, opacity, sh, cam, cfg, d_sd, stream=None):
+    L = load()
+    grads = tuple(torch.empty_like(t) for t in (mu, scale, quat, opacity, sh))
+    p = _prims(mu, scale, quat, opacity, sh)
+    gp = XprPrimsGrad(*[t.data_ptr() for t in grads])
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_project_lp_bwd(ctypes.byref(p), mu.shape[0], ctypes.byref(c), ctypes.byref(g), _ptr(d_sd),
+                                ctypes.byref(gp), _stream(stream)), "xpr_project_lp_bwd")
     return grads

@@ -50,8 +50,8 @@ int validate_camera_config(const XprCamera *cam, const XprConfig *cfg) {
         return fail(XPR_ERR_INVALID, "need 0 < alpha_thresh <= alpha_max <= 1");
     if (!(cfg->alpha_max < 1.f)) return fail(XPR_ERR_INVALID, "alpha_max must be < 1");
     if (!(cfg->t_eps >= 0.f)) return fail(XPR_ERR_INVALID, "t_eps must be >= 0");
-    if (cfg->method != XPR_METHOD_3DGS && cfg->method != XPR_METHOD_3DGUT)
-        return fail(XPR_ERR_INVALID, "method %d not supported (0 = 3DGS, 1 = 3DGUT)", cfg->method);
+    if (cfg->method != XPR_METHOD_3DGS && cfg->method != XPR_METHOD_3DGUT && cfg->method != XPR_METHOD_LINPRIM)
+        return fail(XPR_ERR_INVALID, "method %d not supported (0 = 3DGS, 1 = 3DGUT, 2 = LinPrim)", cfg->method);
     return XPR_OK;
 }
 
@@ -59,7 +59,8 @@ int validate_camera_config(const XprCamera *cam, const XprConfig *cfg) {
 int need_method(const XprConfig *cfg, int method, const char *fn) {
     if (cfg->method != method)
         return fail(XPR_ERR_INVALID, "%s implements method %d (%s) but cfg->method is %d", fn, method,
-                    method == XPR_METHOD_3DGS ? "3DGS" : "3DGUT", cfg->method);
+                    method == XPR_METHOD_3DGS ? "3DGS" : (method == XPR_METHOD_3DGUT ? "3DGUT" : "LinPrim"),
+                    cfg->method);
     return XPR_OK;
 }
 
@@ -116,9 +117,14 @@ namespace xpr {
 int tile_bin_impl(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
                   const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *offsets,
                   uint64_t *keys, uint32_t *tiles, uint32_t *vals, int64_t capacity, int64_t *n_isect,
-                  void *workspace, size_t ws_bytes, void *stream, int64_t per_view) {
+                  void *workspace, size_t ws_bytes, void *stream, int64_t per_view, const float *lp_sd = nullptr) {
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
+    // LinPrim culls from its shader data (xpr_tile_bin_lp); the other methods from the records
+    if ((cfg->method == XPR_METHOD_LINPRIM) != (lp_sd != nullptr))
+        return fail(XPR_ERR_INVALID, lp_sd ? "xpr_tile_bin_lp needs cfg->method == LinPrim"
+                                           : "xpr_tile_bin: LinPrim binning is xpr_tile_bin_lp (it needs sd)");
+    if (lp_sd && n > 0 && !aligned(lp_sd, 16)) return fail(XPR_ERR_INVALID, "xpr_tile_bin_lp: sd must be 16-byte aligned");
     if ((s = check_n(n))) return s;
     if (!offsets || !n_isect || (n > 0 && (!rec || !bbox || !tile_count || !workspace)))
         return fail(XPR_ERR_INVALID, "xpr_tile_bin: NULL pointer");
@@ -137,7 +143,11 @@ int tile_bin_impl(const float *rec, const int32_t *bbox, const int32_t *tile_cou
         // per-primitive counts from xpr_project, taken in emission order
         if ((s = launch_exclusive_scan(isect_count, offsets, n, workspace, nullptr, st, order))) return s;
     } else {
-        if ((s = launch_bin_count(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, st))) return s;
+        if (lp_sd) {
+            if ((s = launch_lp_bin_count(lp_sd, bbox, tile_count, order, n, *cam, *cfg, offsets, st))) return s;
+        } else {
+            if ((s = launch_bin_count(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, st))) return s;
+        }
         if ((s = launch_exclusive_scan(offsets, offsets, n, workspace, nullptr, st))) return s;
     }
     const int64_t *tot_dev = scan_total_ptr(workspace, n);
@@ -151,6 +161,9 @@ int tile_bin_impl(const float *rec, const int32_t *bbox, const int32_t *tile_cou
         return fail(XPR_ERR_CAPACITY, "xpr_tile_bin: %lld intersections > capacity %lld", (long long)total,
                     (long long)capacity);
     if (total > 0 && ((!keys && !tiles) || !vals)) return fail(XPR_ERR_INVALID, "xpr_tile_bin: NULL keys/tiles/vals");
+    if (lp_sd)
+        return launch_lp_bin_emit(rec, lp_sd, bbox, tile_count, order, n, *cam, *cfg, offsets, keys, tiles, vals, st,
+                                  per_view);
     return launch_bin_emit(rec, bbox, tile_count, order, n, *cam, *cfg, offsets, keys, tiles, vals, st, per_view);
 }
 }  // namespace xpr
@@ -394,6 +407,8 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
     if ((s = check_views(n_views, n))) return s;
+    if (cfg->method == XPR_METHOD_LINPRIM)
+        return fail(XPR_ERR_INVALID, "xpr_bin_sorted: LinPrim is binned by xpr_tile_bin_lp");
     if (!binsort_supported(*cam, *cfg, n_views))
         return fail(XPR_ERR_INVALID, "xpr_bin_sorted: a %d x %d tile grid (x %d views) exceeds the band limits",
                     tiles_x(*cam, *cfg), tiles_y(*cam, *cfg), n_views);
@@ -538,6 +553,78 @@ int xpr_project_ut_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *
     if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_sd, 16))
         return fail(XPR_ERR_INVALID, "xpr_project_ut_bwd_views: quat and d_sd must be 16-byte aligned");
     return launch_ut_project_bwd_views(*prims, n, cams, n_views, *cfg, d_sd, *d_prims, as_stream(stream));
+}
+
+// ---- LinPrim ------------------------------------------------------------------------------
+
+int xpr_project_lp(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
+                   float *sd, int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_LINPRIM, "xpr_project_lp"))) return s;
+    if ((s = check_n(n))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh || !rec || !sd ||
+        !bbox || !tile_count)
+        return fail(XPR_ERR_INVALID, "xpr_project_lp: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(sd, 16) || !aligned(bbox, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_lp: quat, rec, sd and bbox must be 16-byte aligned");
+    return launch_lp_project_fwd_views(*prims, n, cam, 1, *cfg, rec, sd, bbox, tile_count, isect_count,
+                                       as_stream(stream));
+}
+
+int xpr_tile_bin_lp(const float *rec, const float *sd, const int32_t *bbox, const int32_t *tile_count,
+                    const int32_t *isect_count, const int32_t *order, int64_t n, const XprCamera *cam,
+                    const XprConfig *cfg, int32_t *offsets, uint64_t *keys, uint32_t *tiles, uint32_t *vals,
+                    int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream) {
+    if (n > 0 && !sd) return fail(XPR_ERR_INVALID, "xpr_tile_bin_lp: NULL sd");
+    static const float kNoData = 0.f;  // stands in for sd when n == 0
+    return tile_bin_impl(rec, bbox, tile_count, isect_count, order, n, cam, cfg, offsets, keys, tiles, vals,
+                         capacity, n_isect, workspace, ws_bytes, stream, 0, n > 0 ? sd : &kNoData);
+}
+
+int xpr_render_lp_fwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                      const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_LINPRIM, "xpr_render_lp_fwd"))) return s;
+    if ((s = check_n(n))) return s;
+    if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_lp_fwd: NULL pointer");
+    if (n > 0 && (!sd || !aligned(sd, 16))) return fail(XPR_ERR_INVALID, "xpr_render_lp_fwd: sd NULL or unaligned");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_lp_fwd: ranges must be 8-byte aligned");
+    return launch_lp_render_fwd(sd, n, vals, ranges, 1, *cam, *cfg, image, t_final, n_contrib, nullptr, nullptr,
+                                as_stream(stream));
+}
+
+int xpr_render_lp_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, const XprCamera *cam,
+                      const XprConfig *cfg, const float *t_final, const int32_t *n_contrib, const float *d_image,
+                      float *d_sd, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_LINPRIM, "xpr_render_lp_bwd"))) return s;
+    if ((s = check_n(n))) return s;
+    if (!ranges || !t_final || !n_contrib || !d_image) return fail(XPR_ERR_INVALID, "xpr_render_lp_bwd: NULL pointer");
+    if (n == 0) return XPR_OK;
+    if (!sd || !d_sd || !aligned(sd, 16) || !aligned(d_sd, 16))
+        return fail(XPR_ERR_INVALID, "xpr_render_lp_bwd: sd/d_sd NULL or not 16-byte aligned");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_lp_bwd: ranges must be 8-byte aligned");
+    return launch_lp_render_bwd(sd, n, vals, ranges, 1, *cam, *cfg, t_final, n_contrib, d_image, d_sd, nullptr,
+                                nullptr, as_stream(stream));
+}
+
+int xpr_project_lp_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg,
+                       const float *d_sd, const XprPrimsGrad *d_prims, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_LINPRIM, "xpr_project_lp_bwd"))) return s;
+    if ((s = check_n(n))) return s;
+    if (n == 0) return XPR_OK;
+    if (!prims || !d_prims || !d_sd || !prims->mu || !prims->scale || !prims->quat || !prims->opacity ||
+        !prims->sh || !d_prims->mu || !d_prims->scale || !d_prims->quat || !d_prims->opacity || !d_prims->sh)
+        return fail(XPR_ERR_INVALID, "xpr_project_lp_bwd: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || !aligned(d_sd, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_lp_bwd: quat and d_sd must be 16-byte aligned");
+    return launch_lp_project_bwd_views(*prims, n, cam, 1, *cfg, d_sd, *d_prims, as_stream(stream));
 }
 
 }  // extern "C"

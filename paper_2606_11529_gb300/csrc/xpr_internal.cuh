@@ -94,6 +94,26 @@ int launch_ut_render_bwd(const float *sd, int64_t n, const uint32_t *vals, const
                          const float *d_image, float *d_sd, const int32_t *worklist, int32_t *counter,
                          cudaStream_t st);
 
+// LinPrim (lp.cu)
+int launch_lp_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views,
+                                const XprConfig &cfg, float *rec, float *sd, int32_t *bbox, int32_t *tc,
+                                int32_t *isect_count, cudaStream_t st);
+int launch_lp_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views,
+                                const XprConfig &cfg, const float *d_sd, const XprPrimsGrad &g, cudaStream_t st);
+int launch_lp_bin_count(const float *sd, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
+                        const XprCamera &cam, const XprConfig &cfg, int32_t *counts, cudaStream_t st);
+int launch_lp_bin_emit(const float *rec, const float *sd, const int32_t *bbox, const int32_t *tc,
+                       const int32_t *order, int64_t n, const XprCamera &cam, const XprConfig &cfg,
+                       const int32_t *offsets, uint64_t *keys, uint32_t *tiles, uint32_t *vals, cudaStream_t st,
+                       int64_t per_view);
+int launch_lp_render_fwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
+                         const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final,
+                         int32_t *n_contrib, const int32_t *worklist, int32_t *counter, cudaStream_t st);
+int launch_lp_render_bwd(const float *sd, int64_t n, const uint32_t *vals, const int32_t *ranges, int n_views,
+                         const XprCamera &cam, const XprConfig &cfg, const float *t_final, const int32_t *n_contrib,
+                         const float *d_image, float *d_sd, const int32_t *worklist, int32_t *counter,
+                         cudaStream_t st);
+
 // fused bin + sort (binsort.cu)
 size_t binsort_workspace_bytes(int64_t n, int n_views, const XprCamera &cam, const XprConfig &cfg);
 bool binsort_supported(const XprCamera &cam, const XprConfig &cfg, int n_views);

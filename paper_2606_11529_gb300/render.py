@@ -6,6 +6,8 @@ Forward  = xpr_project -> xpr_depth_order -> xpr_bin_sorted -> xpr_render_fwd
 Backward = xpr_render_bwd (compositing adjoint, then projection adjoint)
 3DGUT    = xpr_project_ut / xpr_render_ut_fwd / xpr_render_ut_bwd + xpr_project_ut_bwd around the
            same depth order, binning (ray-offset cull) and sort
+LinPrim  = xpr_project_lp / xpr_tile_bin_lp (chord-bound cull) / xpr_render_lp_fwd / xpr_render_lp_bwd
+           + xpr_project_lp_bwd around the same depth order and sort (``cfg.method == 2``)
 
 The Function takes activated parameters (mu, scale, quat, opacity, sh), as in
 the paper's PrimitiveParams, and returns the image [3, H, W].  Gradients are
@@ -104,8 +106,16 @@ class Frame:
     sd: torch.Tensor | None = None  # 3DGUT shader data [n, 16]
 
 
+def method_of(cfg) -> int:
+    return int(getattr(cfg, "method", B.XPR_METHOD_3DGS))
+
+
 def is_ut(cfg) -> bool:
-    return int(getattr(cfg, "method", B.XPR_METHOD_3DGS)) == B.XPR_METHOD_3DGUT
+    return method_of(cfg) == B.XPR_METHOD_3DGUT
+
+
+def is_lp(cfg) -> bool:
+    return method_of(cfg) == B.XPR_METHOD_LINPRIM
 
 
 def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
@@ -122,15 +132,18 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     n = mu.shape[0]
     dev = mu.device
     ws = ws or Workspace()
-    ut = is_ut(cfg)
+    ut, lp = is_ut(cfg), is_lp(cfg)
+    fused = fused and not lp  # LinPrim is binned by xpr_tile_bin_lp
     sd = None
-    deferred = sh_events is not None and not ut
-    if sh_events is not None and ut:  # the unscented projection takes the colours in the same pass
+    deferred = sh_events is not None and not (ut or lp)
+    if sh_events is not None and (ut or lp):  # these projections take the colours in the same pass
         _wait_events(stream, sh_events)
     tm.start("project", stream)
     if ut:
         rec, sd, bbox, tc, cnt = B.xpr_project_ut(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream,
                                                   with_isect_count=not fused)
+    elif lp:
+        rec, sd, bbox, tc, cnt = B.xpr_project_lp(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream)
     else:
         out = B.xpr_project(mu, scale, quat, opacity, None if deferred else sh, ccam, ccfg, stream=stream,
                             with_isect_count=not fused)
@@ -155,8 +168,12 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     else:
         bin_ws = ws.scratch("bin", L.xpr_tile_bin_workspace(n), dev)
         tm.start("tile_bin", stream)
-        offsets, tiles, vals, I = B.xpr_tile_bin(rec, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
-                                                 stream=stream, order=order, isect_count=cnt, tile_ids=True)
+        if lp:
+            offsets, tiles, vals, I = B.xpr_tile_bin_lp(rec, sd, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
+                                                        stream=stream, order=order, isect_count=cnt)
+        else:
+            offsets, tiles, vals, I = B.xpr_tile_bin(rec, bbox, tc, ccam, ccfg, capacity=cap, workspace=bin_ws,
+                                                     stream=stream, order=order, isect_count=cnt, tile_ids=True)
         tm.stop("tile_bin", stream)
         sort_ws = ws.scratch("sort", L.xpr_sort_tiles_workspace(I, nt), dev)
         tm.start("sort", stream)
@@ -172,6 +189,8 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     tm.start("render_fwd", stream)
     if ut:
         image, t_final, n_contrib = B.xpr_render_ut_fwd(sd, vs, ranges, ccam, ccfg, stream=stream)
+    elif lp:
+        image, t_final, n_contrib = B.xpr_render_lp_fwd(sd, vs, ranges, ccam, ccfg, stream=stream)
     else:
         image, t_final, n_contrib = B.xpr_render_fwd(rec, vs, ranges, ccam, ccfg, stream=stream)
     tm.stop("render_fwd", stream)
@@ -191,7 +210,7 @@ class SplatFunction(torch.autograd.Function):
     def forward(ctx, mu, scale, quat, opacity, sh, cam, cfg, ws, timers):
         fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, timers=timers, fused=ws.fused,
                            sh_events=ws.take_sh_events())
-        # 3DGUT renders from the shader data, 3DGS from the records
+        # 3DGUT and LinPrim render from the shader data, 3DGS from the records
         shade = fr.sd if fr.sd is not None else fr.rec
         ctx.save_for_backward(mu, scale, quat, opacity, sh, shade, fr.vals_sorted, fr.ranges, fr.t_final,
                               fr.n_contrib)
@@ -203,16 +222,20 @@ class SplatFunction(torch.autograd.Function):
         mu, scale, quat, opacity, sh, shade, vals, ranges, t_final, n_contrib = ctx.saved_tensors
         tm = ctx.timers or _NO_TIMERS
         ccam, ccfg = B.make_camera(ctx.cam), B.make_config(ctx.cfg)
-        ut = is_ut(ctx.cfg)
+        ut, lp = is_ut(ctx.cfg), is_lp(ctx.cfg)
         tm.start("render_bwd")
         if ut:
             d_shade = B.xpr_render_ut_bwd(shade, vals, ranges, ccam, ccfg, t_final, n_contrib, d_image.contiguous())
+        elif lp:
+            d_shade = B.xpr_render_lp_bwd(shade, vals, ranges, ccam, ccfg, t_final, n_contrib, d_image.contiguous())
         else:
             d_shade = B.xpr_render_bwd(shade, vals, ranges, ccam, ccfg, t_final, n_contrib, d_image.contiguous())
         tm.stop("render_bwd")
         tm.start("project_bwd")
         if ut:
             grads = B.xpr_project_ut_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_shade)
+        elif lp:
+            grads = B.xpr_project_lp_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_shade)
         else:
             grads = B.xpr_project_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_shade)
         tm.stop("project_bwd")

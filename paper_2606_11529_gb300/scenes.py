@@ -52,7 +52,8 @@ class RenderConfig:
     sh_degree: int = 0
     bg: tuple = (0.0, 0.0, 0.0)
     batch_depth: int = 0  # 0 = kernel default
-    method: int = 0       # 0 = 3DGS (EWA projection), 1 = 3DGUT (unscented transform + ray evaluation)
+    method: int = 0       # 0 = 3DGS (EWA projection), 1 = 3DGUT (unscented transform + ray evaluation),
+                          # 2 = LinPrim (octahedra, slab intersection)
 
 
 @dataclass
@@ -164,6 +165,13 @@ def headline_case(n: int = 1_000_000, seed: int = 0):
     """1M SH-3 Gaussians in a clustered scene, 1920x1080 pinhole, focal 1920."""
     sc = clustered_scene(n, seed=seed)
     return sc, pinhole(1920, 1080, 1920.0), RenderConfig(sh_degree=3)
+
+
+def linprim_case(n: int = 500_000, seed: int = 0):
+    """LinPrim workload: 500k octahedra drawn as the headline scene (clustered means, half-extents
+    e^N(-3, 0.5), rotations, opacity, SH degree 3) for a 1280x720 pinhole camera, focal 1280."""
+    sc = clustered_scene(n, seed=seed, width=1280, height=720, focal=1280.0)
+    return sc, pinhole(1280, 720, 1280.0), RenderConfig(sh_degree=3, method=2)
 
 
 def multiview_cameras(n_views: int = 8, width: int = 1600, height: int = 1064, focal: float = 800.0,
