@@ -50,6 +50,9 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # 3DGUT ray evaluation: FP32-pipe operations per (pixel, entry) pair (derivations in the design doc)
 UT_FWD_OPS_PER_PAIR = 31
 UT_BWD_OPS_PER_PAIR = 72
+# LinPrim slab intersection: FP32-pipe operations per (pixel, entry) pair (derivations in the design doc)
+LP_FWD_OPS_PER_PAIR = 39
+LP_BWD_OPS_PER_PAIR = 103
 
 
 def peaks():
@@ -286,6 +289,48 @@ def ut_leg(dev, n, reps, flush):
             "timing": f"median of {reps} (L2 flushed before each)"}
 
 
+def lp_leg(dev, reps, flush):
+    """LinPrim form: 500k octahedra drawn as the headline scene (clustered means, half-extents
+    e^N(-3, 0.5), SH degree 3), 1280x720 pinhole f=1280, 16x16 tiles, forward + backward through the
+    autograd Function."""
+    import numpy as np
+    import torch
+    from paper_2606_11529_gb300 import render as R
+    from paper_2606_11529_gb300 import scenes
+    sc, cam, cfg = scenes.linprim_case()
+    P = [t.to(dev).requires_grad_(True) for t in R.scene_to_device(sc)]
+    w = torch.from_numpy(np.random.default_rng(1).normal(size=(3, cam.height, cam.width)).astype(np.float32)).to(dev)
+    ws = R.Workspace()
+
+    def step(timers=None):
+        for p in P:
+            p.grad = None
+        (R.render(*P, cam, cfg, ws, timers) * w).sum().backward()
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ms = _median_ms(step, reps, flush)
+    timers = R.StageTimers()
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        step(timers)
+    st = timers.mean_ms()
+    fr = R.forward_frame(*[p.detach() for p in P], cam, cfg, ws)
+    pairs = int(fr.n_contrib.to(torch.int64).sum().item())
+    alu = peaks()["alu_ops"]
+    roof = {}
+    for name, ops in (("render_fwd", LP_FWD_OPS_PER_PAIR), ("render_bwd", LP_BWD_OPS_PER_PAIR)):
+        ach = pairs * ops / (st[name] * 1e-3)
+        roof[name] = {"kernel": f"lp_{name}_kernel<16,16>", "bound": "alu", "achieved_tops": round(ach / 1e12, 3),
+                      "frac": round(ach / alu, 4)}
+    return {"workload": "LinPrim fwd+bwd: 500k octahedra (clustered means, half-extents e^N(-3,0.5), SH-3), "
+                        "1280x720 pinhole f=1280, 16x16 tiles, seed 0",
+            "ms_per_iter": round(ms, 4), "stages_ms": {k: round(v, 4) for k, v in st.items()},
+            "intersections": fr.n_isect, "pairs_blended": pairs, "render_roofline": roof,
+            "timing": f"median of {reps} (L2 flushed before each)"}
+
+
 def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     """Serving form: 16 resident clustered SH-3 scenes (sizes log-uniform in [1e5, 3e6]), Poisson
     arrivals at 200 requests/s, sizes 512x512 / 1280x720 / 1920x1080; the continuous-batching server
@@ -351,6 +396,9 @@ def main():
     ap.add_argument("--no-ut", action="store_true", help="skip the 3DGUT leg")
     ap.add_argument("--ut-only", action="store_true",
                     help="run only the 3DGUT leg and print it as its own JSON line (for profiling captures)")
+    ap.add_argument("--no-lp", action="store_true", help="skip the LinPrim leg")
+    ap.add_argument("--lp-only", action="store_true",
+                    help="run only the LinPrim leg and print it as its own JSON line (for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-cap-gb", type=float, default=4.0)
@@ -376,11 +424,14 @@ def main():
     dev = torch.device("cuda", local)
     L = B.load()
 
-    if args.ut_only:
+    if args.ut_only or args.lp_only:
         flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-        ut = ut_leg(dev, args.n, max(args.steps, 1), flush)
+        if args.ut_only:
+            out = {"leg": "3dgut", "ut": ut_leg(dev, args.n, max(args.steps, 1), flush)}
+        else:
+            out = {"leg": "linprim", "linprim": lp_leg(dev, max(args.steps, 1), flush)}
         if rank == 0:
-            print(json.dumps({"leg": "3dgut", "ut": ut}))
+            print(json.dumps(out))
         return 0
 
     sc, cam, cfg = scenes.headline_case(args.n)
@@ -526,6 +577,7 @@ def main():
         key_step()
     key_ms = _median_ms(key_step, args.steps, flush)
     ut = None if args.no_ut else ut_leg(dev, args.n, max(args.steps, 5), flush)
+    lp = None if args.no_lp else lp_leg(dev, max(args.steps, 5), flush)
     batched = None if args.no_batched else batched_leg(dev, max(args.steps // 2, 5), flush)
     batched_ut = None if (args.no_batched or args.no_ut) else batched_leg(dev, max(args.steps // 2, 5), flush, 1)
     serve = None
@@ -554,6 +606,7 @@ def main():
             "batched_3dgut": batched_ut,
             "serve": serve,
             "ut": ut,
+            "linprim": lp,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": launches,

@@ -126,15 +126,66 @@ __device__ __forceinline__ void tile_corners(const Grid &g, int tx, int ty, floa
     Y1 = (float)min(ty * g.th + g.th - 1, g.H - 1) + 0.5f;
 }
 
-// kept tiles of box bb (the per-primitive counter of the projection and the binning's count pass)
-__device__ __forceinline__ int lp_count(const float *S, int4 bb, const Grid &g) {
+// The tiles of the warp's 32 boxes (one per lane: area tiles in row-major slots of box bb, cull data
+// S) are walked 32 at a time, flattened over the lanes: lane l tests slot f0 + l of the flattened
+// list with its owner's data (shuffled), so large boxes do not serialise a warp.  Returns the number
+// of kept tiles of the lane's own box.  With EMIT it also writes them, in slot order, at
+// cursor, cursor + 1, ... (never at or past end): a kept slot's position is its owner's cursor plus
+// the kept slots before it in the owner's run of lanes.  Every lane of the warp must call this.
+template <bool EMIT>
+__device__ __forceinline__ int lp_walk(const float *S, int4 bb, int area, const Grid &g, int64_t cursor, int64_t end,
+                                       uint32_t tbase, uint32_t depth_bits, uint32_t id, uint64_t *keys,
+                                       uint32_t *tiles, uint32_t *vals) {
+    const int lane = threadIdx.x & 31;
+    const int incl = warp_incl_scan(area);
+    const int total = __shfl_sync(kFullMask, incl, 31);
+    const int excl = incl - area;
+    const int bw = max(bb.z - bb.x, 1);
     int cnt = 0;
-    for (int ty = bb.y; ty < bb.w; ++ty)
-        for (int tx = bb.x; tx < bb.z; ++tx) {
+    for (int f0 = 0; f0 < total; f0 += 32) {
+        const int f = f0 + lane;
+        const int p = lane_of(incl, f);
+        float T[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) T[c] = __shfl_sync(kFullMask, S[c], p);
+        const int pexcl = __shfl_sync(kFullMask, excl, p);
+        const int pbx = __shfl_sync(kFullMask, bb.x, p), pby = __shfl_sync(kFullMask, bb.y, p);
+        const int pbw = __shfl_sync(kFullMask, bw, p);
+        bool keep = false;
+        int tx = 0, ty = 0;
+        if (f < total) {
+            const int r = f - pexcl, q = r / pbw;
+            ty = pby + q;
+            tx = pbx + (r - q * pbw);
             float X0, Y0, X1, Y1;
             tile_corners(g, tx, ty, X0, Y0, X1, Y1);
-            cnt += lp_keep(S, X0, Y0, X1, Y1) ? 1 : 0;
+            keep = lp_keep(T, X0, Y0, X1, Y1);
         }
+        const unsigned bal = __ballot_sync(kFullMask, keep);
+        if (EMIT) {
+            const int64_t pcur = __shfl_sync(kFullMask, cursor, p);
+            const int64_t pend = __shfl_sync(kFullMask, end, p);
+            const uint32_t ptb = __shfl_sync(kFullMask, tbase, p), pdb = __shfl_sync(kFullMask, depth_bits, p);
+            const uint32_t pid = __shfl_sync(kFullMask, id, p);
+            const int plo = max(pexcl - f0, 0);  // first lane of the owner's run in this step
+            const unsigned before = bal & ((1u << lane) - 1u) & ~((1u << plo) - 1u);
+            const int64_t pos = pcur + __popc(before);
+            if (keep && pos < pend) {
+                const uint32_t t = ptb + (uint32_t)(ty * g.Wt + tx);
+                if (keys) keys[pos] = ((uint64_t)t << 32) | pdb;
+                if (tiles) tiles[pos] = t;
+                vals[pos] = pid;
+            }
+        }
+        // this lane's own run of slots in the step: lanes [lo, hi]
+        const int lo = max(excl - f0, 0), hi = min(incl - 1 - f0, 31);
+        if (area > 0 && lo <= 31 && hi >= 0 && lo <= hi) {
+            const unsigned run = (hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
+            const int k = __popc(bal & run);
+            cnt += k;
+            cursor += k;
+        }
+    }
     return cnt;
 }
 
@@ -153,56 +204,68 @@ __global__ void __launch_bounds__(kProjWarps * 32) lp_project_fwd_kernel(
     float *ssh = s_lpf + (size_t)w * 32 * LD;
     stage_sh<DEG>(sh, base, nv, ssh);
     const int64_t i = base + lane;
-    if (i >= n) return;
-    const Params P = load_params(mu, scale, quat, opac, i);
+    const bool valid = i < n;
+    Params P = {};
+    if (valid) P = load_params(mu, scale, quat, opac, i);
     const float req = -log1pf(-cfg.alpha_thresh);
     for (int v = 0; v < cs.n_views; ++v) {
         const Cam k = make_cam(cs.cam[v], cfg);
         const int64_t out = (int64_t)v * n + i;
-        LpGeo G;
-        lp_geometry(P, k, G);
-        float4 *o4 = reinterpret_cast<float4 *>(rec + (size_t)out * XPR_REC_FLOATS);
-        float4 *s4 = reinterpret_cast<float4 *>(sd + (size_t)out * XPR_LP_SD_FLOATS);
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float S[16] = {};
         int4 bb = make_int4(0, 0, 0, 0);
         int tc = 0;
-        bool vis = false;
-        if (G.front) {
-            const float Wt = (float)((k.width + cfg.tile_w - 1) / cfg.tile_w);
-            const float Ht = (float)((k.height + cfg.tile_h - 1) / cfg.tile_h);
-            const float tw = (float)cfg.tile_w, th = (float)cfg.tile_h;
-            const float bx = G.mx - 0.5f, by = G.my - 0.5f;  // ray offset: pixel centres at +0.5
-            bb.x = (int)fminf(fmaxf(floorf((bx - G.ex) / tw), 0.f), Wt);
-            bb.y = (int)fminf(fmaxf(floorf((by - G.ey) / th), 0.f), Ht);
-            bb.z = (int)fminf(fmaxf(floorf((bx + G.ex) / tw) + 1.f, 0.f), Wt);
-            bb.w = (int)fminf(fmaxf(floorf((by + G.ey) / th) + 1.f, 0.f), Ht);
-            tc = (bb.z - bb.x) * (bb.w - bb.y);
-            vis = (fmaxf(G.ex, G.ey) > 0.f) && (tc > 0);
+        if (valid) {
+            LpGeo G;
+            lp_geometry(P, k, G);
+            float4 *o4 = reinterpret_cast<float4 *>(rec + (size_t)out * XPR_REC_FLOATS);
+            float4 *s4 = reinterpret_cast<float4 *>(sd + (size_t)out * XPR_LP_SD_FLOATS);
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool vis = false;
+            if (G.front) {
+                const float Wt = (float)((k.width + cfg.tile_w - 1) / cfg.tile_w);
+                const float Ht = (float)((k.height + cfg.tile_h - 1) / cfg.tile_h);
+                const float tw = (float)cfg.tile_w, th = (float)cfg.tile_h;
+                const float bx = G.mx - 0.5f, by = G.my - 0.5f;  // ray offset: pixel centres at +0.5
+                bb.x = (int)fminf(fmaxf(floorf((bx - G.ex) / tw), 0.f), Wt);
+                bb.y = (int)fminf(fmaxf(floorf((by - G.ey) / th), 0.f), Ht);
+                bb.z = (int)fminf(fmaxf(floorf((bx + G.ex) / tw) + 1.f, 0.f), Wt);
+                bb.w = (int)fminf(fmaxf(floorf((by + G.ey) / th) + 1.f, 0.f), Ht);
+                tc = (bb.z - bb.x) * (bb.w - bb.y);
+                vis = (fmaxf(G.ex, G.ey) > 0.f) && (tc > 0);
+            }
+            if (!vis) {
+                o4[0] = z4;
+                o4[1] = z4;
+                o4[2] = make_float4(0.f, G.d, 0.f, 0.f);
+                for (int c = 0; c < 5; ++c) s4[c] = z4;
+                bbox[out] = make_int4(0, 0, 0, 0);
+                tcount[out] = 0;
+                bb = make_int4(0, 0, 0, 0);
+                tc = 0;
+            } else {
+                float col[3];
+                sh_colour<DEG>(P, ssh + lane * LD, k, col);
+                for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.f);
+                S[0] = G.mx;
+                S[1] = G.my;
+                S[2] = G.sigma;
+                S[3] = req;
+                for (int q = 0; q < 4; ++q)
+                    for (int c = 0; c < 3; ++c) S[4 + 3 * q + c] = G.pqh[q][c];
+                o4[0] = make_float4(G.mx, G.my, 0.f, 0.f);
+                o4[1] = make_float4(0.f, 0.f, col[0], col[1]);
+                o4[2] = make_float4(col[2], G.d, 0.f, 1.f);
+                for (int c = 0; c < 4; ++c) s4[c] = make_float4(S[4 * c], S[4 * c + 1], S[4 * c + 2], S[4 * c + 3]);
+                s4[4] = make_float4(col[0], col[1], col[2], 0.f);
+                bbox[out] = bb;
+                tcount[out] = tc;
+            }
         }
-        if (!vis) {
-            o4[0] = z4;
-            o4[1] = z4;
-            o4[2] = make_float4(0.f, G.d, 0.f, 0.f);
-            for (int c = 0; c < 5; ++c) s4[c] = z4;
-            bbox[out] = make_int4(0, 0, 0, 0);
-            tcount[out] = 0;
-            if (isect_count) isect_count[out] = 0;
-            continue;
+        if (isect_count) {  // kept tiles, with the binning's cull on the stored values
+            const int cnt = lp_walk<false>(S, bb, tc, make_grid(cs.cam[v], cfg), 0, 0, 0, 0, 0, nullptr, nullptr,
+                                           nullptr);
+            if (valid) isect_count[out] = cnt;
         }
-        float col[3];
-        sh_colour<DEG>(P, ssh + lane * LD, k, col);
-        for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.f);
-        float S[16] = {G.mx, G.my, G.sigma, req};
-        for (int s = 0; s < 4; ++s)
-            for (int c = 0; c < 3; ++c) S[4 + 3 * s + c] = G.pqh[s][c];
-        o4[0] = make_float4(G.mx, G.my, 0.f, 0.f);
-        o4[1] = make_float4(0.f, 0.f, col[0], col[1]);
-        o4[2] = make_float4(col[2], G.d, 0.f, 1.f);
-        for (int c = 0; c < 4; ++c) s4[c] = make_float4(S[4 * c], S[4 * c + 1], S[4 * c + 2], S[4 * c + 3]);
-        s4[4] = make_float4(col[0], col[1], col[2], 0.f);
-        bbox[out] = bb;
-        tcount[out] = tc;
-        if (isect_count) isect_count[out] = lp_count(S, bb, make_grid(cs.cam[v], cfg));
     }
 }
 
@@ -230,56 +293,38 @@ __device__ __forceinline__ int lp_box(const int4 *__restrict__ bbox, const int *
     return (bb.z > bb.x && bb.w > bb.y) ? 1 : 0;
 }
 
-// binning count pass: counts[j] = kept tiles of position j (primitive order[j])
-__global__ void __launch_bounds__(256) lp_bin_count_kernel(const float *__restrict__ sd,
-                                                           const int4 *__restrict__ bbox,
-                                                           const int *__restrict__ tcount,
-                                                           const int *__restrict__ order, int64_t n, Grid g,
-                                                           int32_t *__restrict__ counts) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int64_t i = order ? order[j] : j;
-    int4 bb;
-    int cnt = 0;
-    if (lp_box(bbox, tcount, i, g, bb)) {
-        float S[16];
+// Binning count and emit passes over positions j (primitive order[j]).  Warp w of the grid takes the
+// 32 positions w, w + nw, w + 2 nw, ... (nw warps in all), so every warp gets primitives from all
+// depths (in depth order the near-camera boxes, which hold most pairs, are neighbours).
+template <bool EMIT>
+__global__ void __launch_bounds__(256) lp_bin_kernel(const float *__restrict__ rec, const float *__restrict__ sd,
+                                                     const int4 *__restrict__ bbox, const int *__restrict__ tcount,
+                                                     const int *__restrict__ order, int64_t n, Grid g,
+                                                     int32_t *__restrict__ counts, const int32_t *__restrict__ offsets,
+                                                     uint64_t *__restrict__ keys, uint32_t *__restrict__ tiles,
+                                                     uint32_t *__restrict__ vals, int64_t per_view) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t j = w + (int64_t)lane * nw;
+    const bool valid = j < n;
+    const int64_t i = valid ? (order ? order[j] : j) : 0;
+    int4 bb = make_int4(0, 0, 0, 0);
+    int area = 0;
+    float S[16] = {};
+    if (valid && lp_box(bbox, tcount, i, g, bb)) {
+        area = (bb.z - bb.x) * (bb.w - bb.y);
         lp_load16(sd, i, S);
-        cnt = lp_count(S, bb, g);
     }
-    counts[j] = cnt;
-}
-
-// binning emit pass: the kept tiles of position j, in slot order (rows, then columns), at
-// [offsets[j], offsets[j+1]); tile ids of view v (per_view > 0) are offset by v * Wt * Ht
-__global__ void __launch_bounds__(256) lp_bin_emit_kernel(const float *__restrict__ rec, const float *__restrict__ sd,
-                                                          const int4 *__restrict__ bbox,
-                                                          const int *__restrict__ tcount,
-                                                          const int *__restrict__ order, int64_t n, Grid g,
-                                                          const int32_t *__restrict__ offsets,
-                                                          uint64_t *__restrict__ keys, uint32_t *__restrict__ tiles,
-                                                          uint32_t *__restrict__ vals, int64_t per_view) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int64_t i = order ? order[j] : j;
-    int4 bb;
-    if (!lp_box(bbox, tcount, i, g, bb)) return;
-    float S[16];
-    lp_load16(sd, i, S);
-    const uint32_t depth_bits = __float_as_uint(__ldg(rec + (size_t)i * XPR_REC_FLOATS + 9));
+    if (!EMIT) {
+        const int cnt = lp_walk<false>(S, bb, area, g, 0, 0, 0, 0, 0, nullptr, nullptr, nullptr);
+        if (valid) counts[j] = cnt;
+        return;
+    }
+    const int64_t cur = valid ? offsets[j] : 0, end = valid ? offsets[j + 1] : 0;
+    const uint32_t depth_bits = area > 0 ? __float_as_uint(__ldg(rec + (size_t)i * XPR_REC_FLOATS + 9)) : 0u;
     const uint32_t tbase = per_view > 0 ? (uint32_t)(i / per_view) * (uint32_t)(g.Wt * g.Ht) : 0u;
-    int64_t pos = offsets[j];
-    const int64_t end = offsets[j + 1];
-    for (int ty = bb.y; ty < bb.w; ++ty)
-        for (int tx = bb.x; tx < bb.z; ++tx) {
-            float X0, Y0, X1, Y1;
-            tile_corners(g, tx, ty, X0, Y0, X1, Y1);
-            if (!lp_keep(S, X0, Y0, X1, Y1) || pos >= end) continue;
-            const uint32_t t = tbase + (uint32_t)(ty * g.Wt + tx);
-            if (keys) keys[pos] = ((uint64_t)t << 32) | depth_bits;
-            if (tiles) tiles[pos] = t;
-            vals[pos] = (uint32_t)i;
-            ++pos;
-        }
+    lp_walk<true>(S, bb, area, g, cur, end, tbase, depth_bits, (uint32_t)i, keys, tiles, vals);
 }
 
 // ---- compositing -----------------------------------------------------------------------------
@@ -878,9 +923,11 @@ int launch_lp_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *c
 int launch_lp_bin_count(const float *sd, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                         const XprCamera &cam, const XprConfig &cfg, int32_t *counts, cudaStream_t st) {
     if (n == 0) return XPR_OK;
-    lp_bin_count_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sd, reinterpret_cast<const int4 *>(bbox), tc,
-                                                                     order, n, make_grid(cam, cfg), counts);
-    XPR_LAUNCH_CHECK("lp_bin_count_kernel");
+    const unsigned warps = (unsigned)((n + 31) / 32);
+    lp_bin_kernel<false><<<(warps + 7) / 8, 256, 0, st>>>(nullptr, sd, reinterpret_cast<const int4 *>(bbox), tc, order,
+                                                           n, make_grid(cam, cfg), counts, nullptr, nullptr, nullptr,
+                                                           nullptr, 0);
+    XPR_LAUNCH_CHECK("lp_bin_kernel<count>");
     return XPR_OK;
 }
 
@@ -889,10 +936,11 @@ int launch_lp_bin_emit(const float *rec, const float *sd, const int32_t *bbox, c
                        const int32_t *offsets, uint64_t *keys, uint32_t *tiles, uint32_t *vals, cudaStream_t st,
                        int64_t per_view) {
     if (n == 0) return XPR_OK;
-    lp_bin_emit_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, sd, reinterpret_cast<const int4 *>(bbox), tc,
-                                                                    order, n, make_grid(cam, cfg), offsets, keys,
-                                                                    tiles, vals, per_view);
-    XPR_LAUNCH_CHECK("lp_bin_emit_kernel");
+    const unsigned warps = (unsigned)((n + 31) / 32);
+    lp_bin_kernel<true><<<(warps + 7) / 8, 256, 0, st>>>(rec, sd, reinterpret_cast<const int4 *>(bbox), tc, order, n,
+                                                          make_grid(cam, cfg), nullptr, offsets, keys, tiles, vals,
+                                                          per_view);
+    XPR_LAUNCH_CHECK("lp_bin_kernel<emit>");
     return XPR_OK;
 }
 
