@@ -95,6 +95,10 @@ def lib():
         L.oracle_render_bwd_tiles_lp.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_project_lp_bwd.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                             _F64P, _F64P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_render_tiles_feat.argtypes = [ctypes.c_int64, _F64P, _F64P, ctypes.c_int, ctypes.c_int, _U32P,
+                                               _I32P, _F64P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_render_bwd_tiles_feat.argtypes = [ctypes.c_int64, _F64P, _F64P, ctypes.c_int, ctypes.c_int, _U32P,
+                                                   _I32P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_abi_version.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -585,6 +589,67 @@ def grads_tiled_lp(scene_arrays, cam, cfg, d_image):
     d_sd = render_bwd_tiles_lp(out["proj"]["sd"], out["vals"], out["ranges"], cam, cfg, d_image)
     g = project_lp_bwd(mu, s, q, o, sh, cam, cfg, d_sd)
     g["d_sd"] = d_sd
+    return g
+
+
+# --------------------------------------------------------------------------- rendered features
+
+def _feat_args(rec, feat):
+    rec = _f64(rec)
+    nfeat = 0 if feat is None else int(np.asarray(feat).reshape(rec.shape[0], -1).shape[1])
+    f = np.zeros(1) if nfeat == 0 else _f64(np.asarray(feat).reshape(rec.shape[0], nfeat))
+    return rec, f, nfeat
+
+
+def render_tiles_feat(rec, feat, vals, ranges, cam, cfg, with_depth=False):
+    """3DGS image plus rendered features [nfeat + with_depth, H, W] over given lists: each channel is
+    sum_i f_ic alpha_i T_i (the depth channel's values are the records' depths)."""
+    rec, f, nfeat = _feat_args(rec, feat)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    H, W = cam.height, cam.width
+    nf = nfeat + int(bool(with_depth))
+    image, feats, tfin = np.zeros((3, H, W)), np.zeros((max(nf, 1), H, W)), np.zeros((H, W))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_tiles_feat(rec.shape[0], _p(rec, _F64P), _p(f, _F64P), nfeat, int(bool(with_depth)),
+                                   _p(vv, _U32P), _p(ranges, _I32P), _p(ca, _F64P), _p(fa, _F64P), _p(image, _F64P),
+                                   _p(feats, _F64P), _p(tfin, _F64P))
+    return dict(image=image, features=feats[:nf], t_final=tfin)
+
+
+def render_bwd_tiles_feat(rec, feat, vals, ranges, cam, cfg, d_image, d_features, with_depth=False):
+    """Adjoint of render_tiles_feat: (d_rec[n,12] with the depth gradient in entry 9, d_feat[n,nfeat])."""
+    rec, f, nfeat = _feat_args(rec, feat)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    vv = vals if vals.size else np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    d_image, d_features = _f64(d_image), _f64(d_features)
+    d_rec, d_feat = np.zeros((rec.shape[0], 12)), np.zeros((rec.shape[0], max(nfeat, 1)))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_render_bwd_tiles_feat(rec.shape[0], _p(rec, _F64P), _p(f, _F64P), nfeat, int(bool(with_depth)),
+                                       _p(vv, _U32P), _p(ranges, _I32P), _p(ca, _F64P), _p(fa, _F64P),
+                                       _p(d_image, _F64P), _p(d_features, _F64P), _p(d_rec, _F64P),
+                                       _p(d_feat, _F64P))
+    return d_rec, d_feat[:, :nfeat]
+
+
+def pipeline_tiled_feat(scene_arrays, feat, cam, cfg, with_depth=False):
+    pr = project(*scene_arrays, cam, cfg)
+    Wt, Ht = tiles_of(cam, cfg)
+    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False)
+    keys, vals, ranges = sort_pairs(keys, vals, Wt * Ht)
+    out = render_tiles_feat(pr["rec"], feat, vals, ranges, cam, cfg, with_depth)
+    out.update(proj=pr, vals=vals, ranges=ranges)
+    return out
+
+
+def grads_tiled_feat(scene_arrays, feat, cam, cfg, d_image, d_features, with_depth=False):
+    out = pipeline_tiled_feat(scene_arrays, feat, cam, cfg, with_depth)
+    d_rec, d_feat = render_bwd_tiles_feat(out["proj"]["rec"], feat, out["vals"], out["ranges"], cam, cfg, d_image,
+                                          d_features, with_depth)
+    g = project_bwd(*scene_arrays, cam, cfg, d_rec)
+    g["feat"] = d_feat
     return g
 
 

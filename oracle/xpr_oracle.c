@@ -919,6 +919,136 @@ void oracle_render_bwd_tiles(int64_t n, const double *rec, const uint32_t *vals,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Rendered features (the "rendered feature" class of the design space, e.g. */
+/* depth and semantics): channel c of a pixel is sum_i f_ic alpha_i T_i over */
+/* the same contributors and weights as the colour, with zero background.    */
+/* feat[n*nfeat] are per-primitive feature rows; with_depth appends one      */
+/* channel whose per-primitive value is the record's depth (camera z).       */
+/* ------------------------------------------------------------------------ */
+
+static double feat_value(const double *rec, const double *feat, int nfeat, int64_t i, int c) {
+    return c < nfeat ? feat[(int64_t)nfeat * i + c] : rec[12 * i + 9];
+}
+
+void oracle_render_tiles_feat(int64_t n, const double *rec, const double *feat, int nfeat, int with_depth,
+                              const uint32_t *vals, const int32_t *ranges, const double *camv, const double *cfgv,
+                              double *image, double *features, double *tfinal) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
+    int64_t HW = (int64_t)cam.W * cam.H;
+    int nf = nfeat + (with_depth ? 1 : 0);
+    (void)n;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < Wt * Ht; ++t) {
+        int tx = t % Wt, ty = t / Wt;
+        int s0 = ranges[2 * t], e0 = ranges[2 * t + 1];
+        int len = e0 - s0;
+        int64_t *list = (int64_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(int64_t));
+        contrib_t *cs = (contrib_t *)malloc((size_t)(len > 0 ? len : 1) * sizeof(contrib_t));
+        for (int k = 0; k < len; ++k) list[k] = vals[s0 + k];
+        for (int yy = 0; yy < cfg.th; ++yy)
+            for (int xx = 0; xx < cfg.tw; ++xx) {
+                int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
+                if (x >= cam.W || y >= cam.H) continue;
+                double C[3], T;
+                int last, bd;
+                int nc = walk((double)x, (double)y, rec, list, len, &cfg, 0.0, 0.0, C, &T, &last, &bd, cs, NULL);
+                int64_t p = (int64_t)y * cam.W + x;
+                for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
+                tfinal[p] = T;
+                for (int c = 0; c < nf; ++c) {
+                    double acc = 0.0;
+                    for (int k = 0; k < nc; ++k) acc += feat_value(rec, feat, nfeat, cs[k].idx, c) * cs[k].alpha * cs[k].T;
+                    features[c * HW + p] = acc;
+                }
+            }
+        free(cs);
+        free(list);
+    }
+}
+
+/* Adjoint with features: the compositing adjoint over all channels (3 colours with background, nf
+ * features without), dC/dalpha_i = sum_ch g_ch (v_ich T_i - S_ich / (1 - alpha_i)) with explicit
+ * suffix sums, then through alpha as pixel_adjoint; d_feat[n*nfeat] and, for the depth channel,
+ * d_rec[9] accumulate g alpha_i T_i. */
+void oracle_render_bwd_tiles_feat(int64_t n, const double *rec, const double *feat, int nfeat, int with_depth,
+                                  const uint32_t *vals, const int32_t *ranges, const double *camv, const double *cfgv,
+                                  const double *d_image, const double *d_features, double *d_rec, double *d_feat) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
+    int64_t HW = (int64_t)cam.W * cam.H;
+    int nf = nfeat + (with_depth ? 1 : 0);
+    int nch = 3 + nf;
+    memset(d_rec, 0, (size_t)n * 12 * sizeof(double));
+    if (nfeat > 0) memset(d_feat, 0, (size_t)n * nfeat * sizeof(double));
+    for (int t = 0; t < Wt * Ht; ++t) {
+        int tx = t % Wt, ty = t / Wt;
+        int s0 = ranges[2 * t], e0 = ranges[2 * t + 1];
+        int len = e0 - s0;
+        if (len <= 0) continue;
+        int64_t *list = (int64_t *)malloc((size_t)len * sizeof(int64_t));
+        contrib_t *cs = (contrib_t *)malloc((size_t)len * sizeof(contrib_t));
+        double *S = (double *)malloc((size_t)len * nch * sizeof(double));
+        double *v = (double *)malloc((size_t)len * nch * sizeof(double));
+        double *g = (double *)malloc((size_t)nch * sizeof(double));
+        for (int k = 0; k < len; ++k) list[k] = vals[s0 + k];
+        for (int yy = 0; yy < cfg.th; ++yy)
+            for (int xx = 0; xx < cfg.tw; ++xx) {
+                int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
+                if (x >= cam.W || y >= cam.H) continue;
+                int64_t p = (int64_t)y * cam.W + x;
+                int any = 0;
+                for (int c = 0; c < 3; ++c) any |= (g[c] = d_image[c * HW + p]) != 0.0;
+                for (int c = 0; c < nf; ++c) any |= (g[3 + c] = d_features[c * HW + p]) != 0.0;
+                if (!any) continue;
+                double C[3], T;
+                int last, bd;
+                int nc = walk((double)x, (double)y, rec, list, len, &cfg, 0.0, 0.0, C, &T, &last, &bd, cs, NULL);
+                if (nc == 0) continue;
+                for (int i = 0; i < nc; ++i) {
+                    for (int c = 0; c < 3; ++c) v[nch * i + c] = rec[12 * cs[i].idx + 6 + c];
+                    for (int c = 0; c < nf; ++c) v[nch * i + 3 + c] = feat_value(rec, feat, nfeat, cs[i].idx, c);
+                }
+                for (int c = 0; c < nch; ++c) {
+                    double acc = c < 3 ? T * cfg.bg[c] : 0.0;
+                    for (int i = nc - 1; i >= 0; --i) {
+                        S[nch * i + c] = acc;
+                        acc += v[nch * i + c] * cs[i].alpha * cs[i].T;
+                    }
+                }
+                for (int i = 0; i < nc; ++i) {
+                    const double *R = rec + 12 * cs[i].idx;
+                    double *D = d_rec + 12 * cs[i].idx;
+                    double a = cs[i].alpha, Ti = cs[i].T;
+                    double da = 0.0;
+                    for (int c = 0; c < nch; ++c) da += g[c] * (v[nch * i + c] * Ti - S[nch * i + c] / (1.0 - a));
+                    for (int c = 0; c < 3; ++c) D[6 + c] += g[c] * a * Ti;
+                    for (int c = 0; c < nf; ++c) {
+                        double gv = g[3 + c] * a * Ti;
+                        if (c < nfeat) d_feat[(int64_t)nfeat * cs[i].idx + c] += gv;
+                        else D[9] += gv;
+                    }
+                    if (cs[i].clamped) continue;
+                    D[5] += da * cs[i].G;
+                    double dp = da * a, dx = cs[i].dx, dy = cs[i].dy;
+                    D[2] += dp * (-0.5 * dx * dx);
+                    D[3] += dp * (-dx * dy);
+                    D[4] += dp * (-0.5 * dy * dy);
+                    D[0] += dp * (R[2] * dx + R[3] * dy);
+                    D[1] += dp * (R[3] * dx + R[4] * dy);
+                }
+            }
+        free(g);
+        free(v);
+        free(S);
+        free(cs);
+        free(list);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Adjoint of the projection (Listing 1 project), from screen-space          */
 /* gradients d_rec (dmx, dmy, dc00, dc01, dc11, do, dr, dg, db) to           */
 /* dmu[n*3], dscale[n*3], dquat[n*4], dopac[n], dsh[n*K*3].                  */
@@ -1046,6 +1176,8 @@ void oracle_project_bwd(int64_t n, const double *mu, const double *scale, const 
         } else {
             gmc[2] += gJ[5] * (cam.fy * P.uy / (z * z));
         }
+        /* rendered depth (record entry 9 = camera z) */
+        gmc[2] += D[9];
         /* camera point = W mu + t */
         for (int j = 0; j < 3; ++j) gmu[j] += V[j] * gmc[0] + V[4 + j] * gmc[1] + V[8 + j] * gmc[2];
 
@@ -2178,4 +2310,4 @@ void oracle_project_lp_bwd(int64_t n, const double *mu, const double *scale, con
     }
 }
 
-int oracle_abi_version(void) { return 4; }
+int oracle_abi_version(void) { return 5; }
