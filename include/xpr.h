@@ -111,7 +111,8 @@ typedef struct XprPrimsGrad {
  *   [10] ln(opacity / alpha_thresh)  [11] visible (1.0 or 0.0)
  * conic = Sigma_2D^{-1}.  Invisible primitives have every entry 0 except
  * depth.  The same layout is used for screen-space gradients (d_rec):
- *   [0..1] d mu_2D, [2..4] d conic, [5] d opacity, [6..8] d rgb, rest 0. */
+ *   [0..1] d mu_2D, [2..4] d conic, [5] d opacity, [6..8] d rgb, [9] d depth
+ *   (nonzero only from rendered depth, xpr_render_bwd_feat), rest 0. */
 #define XPR_REC_FLOATS 12
 
 /* ---- Preprocess ----------------------------------------------------------
@@ -328,6 +329,27 @@ size_t xpr_bin_sorted_workspace(int64_t n, int32_t n_views, const XprCamera *cam
 int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
                    int32_t n_views, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges, uint32_t *vals,
                    int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---- Rendered features (3DGS) ----------------------------------------------------
+ * The "rendered feature" class of the design space (depth, semantics): channel c of
+ * pixel p is sum_i f_ic alpha_i T_i over the same contributors and weights as the
+ * colour, with zero background.  feat[n, n_feat] (device, row-major; may be NULL when
+ * n_feat == 0) holds the per-primitive feature rows; with_depth != 0 appends one
+ * channel whose per-primitive value is the record's depth (camera z), i.e. the
+ * expected depth.  1 <= n_feat + with_depth <= 16.
+ * xpr_render_fwd_feat: as xpr_render_fwd (same image bit for bit) plus
+ *   features[n_feat + with_depth, H, W].
+ * xpr_render_bwd_feat: the adjoint for d_image[3,H,W] and d_features[n_feat +
+ *   with_depth, H, W]: d_rec[n,12] (OVERWRITTEN; record layout, the depth
+ *   channel's gradient in entry 9, which xpr_project_bwd takes through camera z)
+ *   and d_feat[n, n_feat] (OVERWRITTEN; may be NULL when n_feat == 0). */
+int xpr_render_fwd_feat(const float *rec, int64_t n, const float *feat, int32_t n_feat, int32_t with_depth,
+                        const uint32_t *vals, const int32_t *ranges, const XprCamera *cam, const XprConfig *cfg,
+                        float *image, float *features, float *t_final, int32_t *n_contrib, void *stream);
+int xpr_render_bwd_feat(const float *rec, int64_t n, const float *feat, int32_t n_feat, int32_t with_depth,
+                        const uint32_t *vals, const int32_t *ranges, const XprCamera *cam, const XprConfig *cfg,
+                        const float *t_final, const int32_t *n_contrib, const float *d_image,
+                        const float *d_features, float *d_rec, float *d_feat, void *stream);
 
 /* ---- 3DGUT (cfg->method == XPR_METHOD_3DGUT) ------------------------------------
  * The 3DGUT instance of project / tile_cull / pixel_info / evaluate (Sec. 3

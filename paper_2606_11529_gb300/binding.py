@@ -114,6 +114,10 @@ SIGNATURES = {
                                   c_vp, c_vp, c_vp, c_vp, c_vp]),
     "xpr_project_lp_bwd": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
                                    ctypes.POINTER(XprConfig), c_vp, ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_render_fwd_feat": (c_i32, [c_vp, c_i64, c_vp, c_i32, c_i32, c_vp, c_vp, ctypes.POINTER(XprCamera),
+                                    ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_render_bwd_feat": (c_i32, [c_vp, c_i64, c_vp, c_i32, c_i32, c_vp, c_vp, ctypes.POINTER(XprCamera),
+                                    ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
@@ -731,3 +735,46 @@ def xpr_project_lp_bwd(mu, scale, quat, opacity, sh, cam, cfg, d_sd, stream=None
     _check(L.xpr_project_lp_bwd(ctypes.byref(p), mu.shape[0], ctypes.byref(c), ctypes.byref(g), _ptr(d_sd),
                                 ctypes.byref(gp), _stream(stream)), "xpr_project_lp_bwd")
     return grads
+
+
+# ---------------------------------------------------------------------------------------- rendered features
+
+def _feat_dims(feat, with_depth):
+    nfeat = 0 if feat is None else int(feat.shape[1])
+    if feat is not None and not (feat.is_cuda and feat.dtype == torch.float32 and feat.is_contiguous()):
+        raise ValueError("feat must be a contiguous float32 CUDA tensor [n, n_feat]")
+    return nfeat, nfeat + (1 if with_depth else 0)
+
+
+def xpr_render_fwd_feat(rec, feat, vals, ranges, cam, cfg, with_depth=False, stream=None):
+    """Returns (image[3,H,W], features[n_feat + with_depth, H, W], t_final, n_contrib)."""
+    L = load()
+    dev = rec.device
+    nfeat, nf = _feat_dims(feat, with_depth)
+    H, W = int(cam.height), int(cam.width)
+    image = torch.empty((3, H, W), dtype=torch.float32, device=dev)
+    features = torch.empty((nf, H, W), dtype=torch.float32, device=dev)
+    t_final = torch.empty((H, W), dtype=torch.float32, device=dev)
+    n_contrib = torch.empty((H, W), dtype=torch.int32, device=dev)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_fwd_feat(_ptr(rec), rec.shape[0], _ptr(feat), nfeat, int(bool(with_depth)), _ptr(vals),
+                                 _ptr(ranges), ctypes.byref(c), ctypes.byref(g), _ptr(image), _ptr(features),
+                                 _ptr(t_final), _ptr(n_contrib), _stream(stream)), "xpr_render_fwd_feat")
+    return image, features, t_final, n_contrib
+
+
+def xpr_render_bwd_feat(rec, feat, vals, ranges, cam, cfg, t_final, n_contrib, d_image, d_features, with_depth=False,
+                        stream=None):
+    """Returns (d_rec[n,12] with the depth gradient in entry 9, d_feat[n, n_feat] or None)."""
+    L = load()
+    n = rec.shape[0]
+    dev = rec.device
+    nfeat, _ = _feat_dims(feat, with_depth)
+    d_rec = torch.empty((n, REC), dtype=torch.float32, device=dev)
+    d_feat = torch.empty((n, nfeat), dtype=torch.float32, device=dev) if nfeat > 0 else None
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_render_bwd_feat(_ptr(rec), n, _ptr(feat), nfeat, int(bool(with_depth)), _ptr(vals), _ptr(ranges),
+                                 ctypes.byref(c), ctypes.byref(g), _ptr(t_final), _ptr(n_contrib),
+                                 _ptr(d_image.contiguous()), _ptr(d_features.contiguous()), _ptr(d_rec), _ptr(d_feat),
+                                 _stream(stream)), "xpr_render_bwd_feat")
+    return d_rec, d_feat

@@ -627,4 +627,49 @@ int xpr_project_lp_bwd(const XprPrims *prims, int64_t n, const XprCamera *cam, c
     return launch_lp_project_bwd_views(*prims, n, cam, 1, *cfg, d_sd, *d_prims, as_stream(stream));
 }
 
+// ---- rendered features ----------------------------------------------------------------------
+
+static int check_feat(const char *fn, int64_t n, const float *feat, int32_t n_feat, int32_t with_depth) {
+    const int nf = n_feat + (with_depth ? 1 : 0);
+    if (n_feat < 0 || nf < 1 || nf > 16)
+        return fail(XPR_ERR_INVALID, "%s: n_feat + with_depth = %d out of range [1, 16]", fn, nf);
+    if (n > 0 && n_feat > 0 && !feat) return fail(XPR_ERR_INVALID, "%s: NULL feat", fn);
+    return XPR_OK;
+}
+
+int xpr_render_fwd_feat(const float *rec, int64_t n, const float *feat, int32_t n_feat, int32_t with_depth,
+                        const uint32_t *vals, const int32_t *ranges, const XprCamera *cam, const XprConfig *cfg,
+                        float *image, float *features, float *t_final, int32_t *n_contrib, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_render_fwd_feat"))) return s;
+    if ((s = check_n(n))) return s;
+    if ((s = check_feat("xpr_render_fwd_feat", n, feat, n_feat, with_depth))) return s;
+    if (!ranges || !image || !features || !t_final || !n_contrib)
+        return fail(XPR_ERR_INVALID, "xpr_render_fwd_feat: NULL pointer");
+    if (n > 0 && (!rec || !aligned(rec, 16))) return fail(XPR_ERR_INVALID, "xpr_render_fwd_feat: rec NULL or unaligned");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_fwd_feat: ranges must be 8-byte aligned");
+    return launch_render_feat_fwd(rec, n, feat, n_feat, with_depth, vals, ranges, *cam, *cfg, image, features,
+                                  t_final, n_contrib, as_stream(stream));
+}
+
+int xpr_render_bwd_feat(const float *rec, int64_t n, const float *feat, int32_t n_feat, int32_t with_depth,
+                        const uint32_t *vals, const int32_t *ranges, const XprCamera *cam, const XprConfig *cfg,
+                        const float *t_final, const int32_t *n_contrib, const float *d_image,
+                        const float *d_features, float *d_rec, float *d_feat, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_render_bwd_feat"))) return s;
+    if ((s = check_n(n))) return s;
+    if ((s = check_feat("xpr_render_bwd_feat", n, feat, n_feat, with_depth))) return s;
+    if (!ranges || !t_final || !n_contrib || !d_image || !d_features)
+        return fail(XPR_ERR_INVALID, "xpr_render_bwd_feat: NULL pointer");
+    if (n == 0) return XPR_OK;
+    if (!rec || !d_rec || !aligned(rec, 16) || !aligned(d_rec, 16))
+        return fail(XPR_ERR_INVALID, "xpr_render_bwd_feat: rec/d_rec NULL or not 16-byte aligned");
+    if (n_feat > 0 && !d_feat) return fail(XPR_ERR_INVALID, "xpr_render_bwd_feat: NULL d_feat");
+    return launch_render_feat_bwd(rec, n, feat, n_feat, with_depth, vals, ranges, *cam, *cfg, t_final, n_contrib,
+                                  d_image, d_features, d_rec, d_feat, as_stream(stream));
+}
+
 }  // extern "C"

@@ -238,6 +238,7 @@ __device__ __forceinline__ void adjoint_view(const Params &P, const float *shi, 
     gmc[0] = dmx * k.fx * iz;
     gmc[1] = dmy * k.fy * iz;
     gmc[2] = -(dmx * k.fx * x + dmy * k.fy * y) * iz2;
+    gmc[2] += d2.y;  // rendered depth (record entry 9 = camera z)
 
     // ---- conic -> Sigma_2D:  dA = -P G P with P = A^{-1} = [[p, q], [q, r]], G = [[g00, h], [h, g11]]
     const float idet = 1.f / G.det;

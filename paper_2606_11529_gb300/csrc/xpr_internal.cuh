@@ -79,6 +79,15 @@ size_t depth_order_workspace_bytes(int64_t n);
 int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
                        cudaStream_t st, int64_t per_view = 0, int n_views = 1);
 
+// rendered features (feat.cu)
+int launch_render_feat_fwd(const float *rec, int64_t n, const float *feat, int nfeat, int depth, const uint32_t *vals,
+                           const int32_t *ranges, const XprCamera &cam, const XprConfig &cfg, float *image,
+                           float *features, float *t_final, int32_t *n_contrib, cudaStream_t st);
+int launch_render_feat_bwd(const float *rec, int64_t n, const float *feat, int nfeat, int depth, const uint32_t *vals,
+                           const int32_t *ranges, const XprCamera &cam, const XprConfig &cfg, const float *t_final,
+                           const int32_t *n_contrib, const float *d_image, const float *d_features, float *d_rec,
+                           float *d_feat, cudaStream_t st);
+
 // 3DGUT (ut.cu)
 int need_method(const XprConfig *cfg, int method, const char *fn);
 int launch_ut_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views,

@@ -119,7 +119,8 @@ def is_lp(cfg) -> bool:
 
 
 def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
-                  timers=None, fused: bool = False, keep_sorted_tiles: bool = False, sh_events=None) -> Frame:
+                  timers=None, fused: bool = False, keep_sorted_tiles: bool = False, sh_events=None,
+                  render: bool = True) -> Frame:
     """The forward stages, each one C-ABI call: project, depth order, then either the key path
     (xpr_tile_bin emitting u32 tile ids in depth order + xpr_sort_tiles, the default) or the fused
     bin + sort (xpr_bin_sorted), then render.  Both give the same sorted lists bit for bit.
@@ -186,6 +187,8 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
         tm.start("color", stream)
         B.xpr_project_color(mu, sh, rec, ccam, ccfg, stream=stream)
         tm.stop("color", stream)
+    if not render:  # the caller composites the lists itself (rendered features)
+        return Frame(rec, bbox, tc, cnt, order, offsets, tiles, vals, I, ks, vs, ranges, None, None, None, sd)
     tm.start("render_fwd", stream)
     if ut:
         image, t_final, n_contrib = B.xpr_render_ut_fwd(sd, vs, ranges, ccam, ccfg, stream=stream)
@@ -240,6 +243,49 @@ class SplatFunction(torch.autograd.Function):
             grads = B.xpr_project_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_shade)
         tm.stop("project_bwd")
         return (*grads, None, None, None, None)
+
+
+class FeatSplatFunction(torch.autograd.Function):
+    """(image, features) = splat with rendered feature channels (3DGS): feat[n, F] per-primitive rows
+    (or None) and, with with_depth, the expected-depth channel; backward gives the five parameter
+    gradients and d feat."""
+
+    @staticmethod
+    def forward(ctx, mu, scale, quat, opacity, sh, feat, cam, cfg, with_depth, ws):
+        fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, render=False)
+        image, features, t_final, n_contrib = B.xpr_render_fwd_feat(fr.rec, feat, fr.vals_sorted, fr.ranges,
+                                                                    B.make_camera(cam), B.make_config(cfg),
+                                                                    with_depth=with_depth)
+        ctx.has_feat = feat is not None
+        ctx.save_for_backward(mu, scale, quat, opacity, sh, *( (feat,) if feat is not None else ()), fr.rec,
+                              fr.vals_sorted, fr.ranges, t_final, n_contrib)
+        ctx.cam, ctx.cfg, ctx.with_depth = cam, cfg, with_depth
+        return image, features
+
+    @staticmethod
+    def backward(ctx, d_image, d_features):
+        saved = list(ctx.saved_tensors)
+        mu, scale, quat, opacity, sh = saved[:5]
+        feat = saved[5] if ctx.has_feat else None
+        rec, vals, ranges, t_final, n_contrib = saved[-5:]
+        ccam, ccfg = B.make_camera(ctx.cam), B.make_config(ctx.cfg)
+        if d_image is None:
+            d_image = torch.zeros((3, ctx.cam.height, ctx.cam.width), dtype=torch.float32, device=mu.device)
+        nf = (0 if feat is None else feat.shape[1]) + int(bool(ctx.with_depth))
+        if d_features is None:
+            d_features = torch.zeros((nf, ctx.cam.height, ctx.cam.width), dtype=torch.float32, device=mu.device)
+        d_rec, d_feat = B.xpr_render_bwd_feat(rec, feat, vals, ranges, ccam, ccfg, t_final, n_contrib,
+                                              d_image.contiguous(), d_features.contiguous(),
+                                              with_depth=ctx.with_depth)
+        grads = B.xpr_project_bwd(mu, scale, quat, opacity, sh, ccam, ccfg, d_rec)
+        return (*grads, d_feat, None, None, None, None)
+
+
+def render_features(mu, scale, quat, opacity, sh, feat, cam, cfg, with_depth: bool = False,
+                    ws: Workspace | None = None):
+    """Differentiable 3DGS render with rendered features: returns (image [3,H,W], features
+    [F + with_depth, H, W]); feat is [n, F] (or None for depth alone)."""
+    return FeatSplatFunction.apply(mu, scale, quat, opacity, sh, feat, cam, cfg, with_depth, ws or Workspace())
 
 
 def render(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, timers: StageTimers | None = None):
