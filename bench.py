@@ -331,6 +331,46 @@ def lp_leg(dev, reps, flush):
             "timing": f"median of {reps} (L2 flushed before each)"}
 
 
+def feat_leg(dev, n, reps, flush):
+    """Rendered features: the headline scene (1M SH-3 Gaussians, 1920x1080) with 8 per-primitive
+    semantic channels and the expected-depth channel composited in the colour's blend loop,
+    forward + backward through render_features, against the plain colour-only step."""
+    import numpy as np
+    import torch
+    from paper_2606_11529_gb300 import render as R
+    from paper_2606_11529_gb300 import scenes
+    sc, cam, cfg = scenes.headline_case(n)
+    P = [t.to(dev).requires_grad_(True) for t in R.scene_to_device(sc)]
+    feat = torch.from_numpy(np.random.default_rng(5).normal(size=(sc.n, 8)).astype(np.float32)).to(dev)
+    feat.requires_grad_(True)
+    rng = np.random.default_rng(6)
+    wi = torch.from_numpy(rng.normal(size=(3, cam.height, cam.width)).astype(np.float32)).to(dev)
+    wf = torch.from_numpy(rng.normal(size=(9, cam.height, cam.width)).astype(np.float32)).to(dev)
+    ws = R.Workspace()
+
+    def step():
+        for p in P + [feat]:
+            p.grad = None
+        img, feats = R.render_features(*P, feat, cam, cfg, with_depth=True, ws=ws)
+        ((img * wi).sum() + (feats * wf).sum()).backward()
+
+    def plain():
+        for p in P:
+            p.grad = None
+        (R.render(*P, cam, cfg, ws) * wi).sum().backward()
+
+    for _ in range(3):
+        step()
+        plain()
+    torch.cuda.synchronize()
+    ms = _median_ms(step, reps, flush)
+    ms_plain = _median_ms(plain, reps, flush)
+    return {"workload": "rendered features: the headline scene (1M SH-3 Gaussians, 1920x1080, 16x16 tiles) with 8 "
+                        "semantic channels + expected depth, fwd+bwd of image and features",
+            "ms_per_iter": round(ms, 4), "ms_colour_only": round(ms_plain, 4),
+            "timing": f"median of {reps} (L2 flushed before each)"}
+
+
 def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     """Serving form: 16 resident clustered SH-3 scenes (sizes log-uniform in [1e5, 3e6]), Poisson
     arrivals at 200 requests/s, sizes 512x512 / 1280x720 / 1920x1080; the continuous-batching server
@@ -397,6 +437,7 @@ def main():
     ap.add_argument("--ut-only", action="store_true",
                     help="run only the 3DGUT leg and print it as its own JSON line (for profiling captures)")
     ap.add_argument("--no-lp", action="store_true", help="skip the LinPrim leg")
+    ap.add_argument("--no-feat", action="store_true", help="skip the rendered-features leg")
     ap.add_argument("--lp-only", action="store_true",
                     help="run only the LinPrim leg and print it as its own JSON line (for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -578,6 +619,7 @@ def main():
     key_ms = _median_ms(key_step, args.steps, flush)
     ut = None if args.no_ut else ut_leg(dev, args.n, max(args.steps, 5), flush)
     lp = None if args.no_lp else lp_leg(dev, max(args.steps, 5), flush)
+    feat = None if args.no_feat else feat_leg(dev, args.n, max(args.steps, 5), flush)
     batched = None if args.no_batched else batched_leg(dev, max(args.steps // 2, 5), flush)
     batched_ut = None if (args.no_batched or args.no_ut) else batched_leg(dev, max(args.steps // 2, 5), flush, 1)
     serve = None
@@ -607,6 +649,7 @@ def main():
             "serve": serve,
             "ut": ut,
             "linprim": lp,
+            "features": feat,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
             "gpu_launches": launches,
