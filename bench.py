@@ -31,7 +31,8 @@ METRIC = "fwd+bwd ms/iter @1M Gaussians 1080p vs plain path; serve p50/p99 ms, v
 UNIT = "ms/iter"
 WORKLOAD = "3DGS fwd+bwd, 1M SH-3 Gaussians clustered (200 centres, spread 0.5, depth 1-20), 1920x1080 pinhole f=1920, 16x16 tiles, seed 0"
 
-# Per-unit algorithmic work of each stage (derivations in the design doc).
+# Per-unit algorithmic work of each stage: bytes a stage must move, or FP32-pipe operations per
+# (pixel, entry) pair counted from the kernels' arithmetic.
 SH_FLOATS = 48
 PARAM_BYTES = 4 * (3 + 3 + 4 + 1 + SH_FLOATS)  # 236 B per primitive
 REC_BYTES = 48
@@ -47,10 +48,10 @@ TRAFFIC_SOURCE = {"render_bwd_kernel<16,16>": "profiles/render_bwd_headline.md",
                   "project_bwd_kernel<3>": "profiles/project_bwd_headline.md",
                   "project_fwd_kernel<3>": "profiles/project_fwd_headline.md"}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# 3DGUT ray evaluation: FP32-pipe operations per (pixel, entry) pair (derivations in the design doc)
+# 3DGUT ray evaluation: FP32-pipe operations per (pixel, entry) pair
 UT_FWD_OPS_PER_PAIR = 31
 UT_BWD_OPS_PER_PAIR = 72
-# LinPrim slab intersection: FP32-pipe operations per (pixel, entry) pair (derivations in the design doc)
+# LinPrim slab intersection: FP32-pipe operations per (pixel, entry) pair
 LP_FWD_OPS_PER_PAIR = 39
 LP_BWD_OPS_PER_PAIR = 103
 

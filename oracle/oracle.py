@@ -99,6 +99,7 @@ def lib():
                                                _I32P, _F64P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_render_bwd_tiles_feat.argtypes = [ctypes.c_int64, _F64P, _F64P, ctypes.c_int, ctypes.c_int, _U32P,
                                                    _I32P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_fisheye_project.argtypes = [_F64P, _F64P, _F64P]
         L.oracle_abi_version.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -117,10 +118,11 @@ def _f32v(v) -> float:
 
 
 def cam_array(cam) -> np.ndarray:
-    """[W, H, fx, fy, cx, cy, V(12), z_near] with float32-rounded values."""
+    """[W, H, fx, fy, cx, cy, V(12), z_near, model, k1..k4] with float32-rounded values."""
     vm = np.asarray(cam.viewmat, np.float32).reshape(12).astype(np.float64)
+    dist = [_f32v(k) for k in getattr(cam, "dist", (0.0, 0.0, 0.0, 0.0))]
     return np.array([cam.width, cam.height, _f32v(cam.fx), _f32v(cam.fy), _f32v(cam.cx), _f32v(cam.cy), *vm,
-                     _f32v(cam.z_near)], np.float64)
+                     _f32v(cam.z_near), int(getattr(cam, "model", 0)), *dist], np.float64)
 
 
 def cfg_array(cfg) -> np.ndarray:
@@ -394,6 +396,17 @@ def render_pixels_ut(rec, sd, pix, cam, cfg, delta: float = 0.0):
 def ut_response(sd_row, rd) -> float:
     s, r = _f64(sd_row), _f64(rd)
     return float(lib().oracle_ut_response(_p(s, _F64P), _p(r, _F64P)))
+
+
+def fisheye_project(pc, cam):
+    """Pixel coordinates of camera-space points pc[m,3] under the camera's fisheye model."""
+    pc = _f64(np.atleast_2d(pc))
+    out = np.zeros((pc.shape[0], 2))
+    ca = cam_array(cam)
+    for i in range(pc.shape[0]):
+        lib().oracle_fisheye_project(_p(np.ascontiguousarray(pc[i]), _F64P), _p(ca, _F64P),
+                                     _p(out[i:i + 1].reshape(2), _F64P))
+    return out
 
 
 def pixel_ray(x, y, cam):

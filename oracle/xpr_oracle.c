@@ -52,6 +52,8 @@ typedef struct {
     double fx, fy, cx, cy;
     double V[12];
     double z_near;
+    int model;    /* 0 pinhole, 1 fisheye (3DGUT) */
+    double k[4];  /* fisheye: theta_d = theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8) */
 } ocam;
 
 typedef struct {
@@ -72,6 +74,8 @@ static ocam read_cam(const double *c) {
     k.cy = c[5];
     for (int i = 0; i < 12; ++i) k.V[i] = c[6 + i];
     k.z_near = c[18];
+    k.model = (int)c[19];
+    for (int i = 0; i < 4; ++i) k.k[i] = c[20 + i];
     return k;
 }
 
@@ -1233,6 +1237,96 @@ void oracle_project_bwd(int64_t n, const double *mu, const double *scale, const 
 /* ln(o'/alpha_t); shader data sd[16] = ro_c[3], M[9] (row-major), o', rgb. */
 /* ------------------------------------------------------------------------ */
 
+/* Fisheye camera (equidistant projection with a radial polynomial; the model of the 3DGUT
+ * configuration of this workload, not printed in the paper): a camera-space point (x, y, z) at angle
+ * theta = atan2(r, z) from the axis, r = sqrt(x^2 + y^2), lands at
+ *   u = fx theta_d x / r + cx,  v = fy theta_d y / r + cy,
+ *   theta_d = theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8)
+ * (u = cx, v = cy on the axis).  The pixel ray inverts theta_d(theta) by Newton's method. */
+static double fish_thetad(const ocam *cam, double th) {
+    double t2 = th * th;
+    return th * (1.0 + t2 * (cam->k[0] + t2 * (cam->k[1] + t2 * (cam->k[2] + t2 * cam->k[3]))));
+}
+
+static void fish_project(const ocam *cam, const double *pc, double *uv) {
+    double r = sqrt(pc[0] * pc[0] + pc[1] * pc[1]);
+    if (r == 0.0) {
+        uv[0] = cam->cx;
+        uv[1] = cam->cy;
+        return;
+    }
+    double th = atan2(r, pc[2]);
+    double s = fish_thetad(cam, th) / r;
+    uv[0] = cam->fx * s * pc[0] + cam->cx;
+    uv[1] = cam->fy * s * pc[1] + cam->cy;
+}
+
+void oracle_fisheye_project(const double *pc, const double *camv, double *uv) {
+    ocam cam = read_cam(camv);
+    fish_project(&cam, pc, uv);
+}
+
+/* d(u, v)/d(x, y, z) of the projection (pinhole or fisheye) as a 2x3 row-major matrix.  Fisheye,
+ * with s = theta_d / r, t = theta_d'(theta) / (r^2 + z^2), K = (t z - s) / r^2:
+ *   du/dx = fx (s + x^2 K), du/dy = fx x y K, du/dz = -fx x t, and v alike (K -> 2 (k1 - 1/3) / z^3
+ *   and s -> 1 / z on the axis). */
+static void proj_jacobian(const ocam *cam, const double *pc, double *J) {
+    double x = pc[0], y = pc[1], z = pc[2];
+    if (cam->model != 1) {
+        J[0] = cam->fx / z;
+        J[1] = 0.0;
+        J[2] = -cam->fx * x / (z * z);
+        J[3] = 0.0;
+        J[4] = cam->fy / z;
+        J[5] = -cam->fy * y / (z * z);
+        return;
+    }
+    double r2 = x * x + y * y, r = sqrt(r2), s, t, K;
+    if (r < 1e-9 * fabs(z)) {
+        s = 1.0 / z;
+        t = 1.0 / (z * z);
+        K = 2.0 * (cam->k[0] - 1.0 / 3.0) / (z * z * z);
+    } else {
+        double th = atan2(r, z), t2 = th * th;
+        double td = fish_thetad(cam, th);
+        double tdp = 1.0 + t2 * (3.0 * cam->k[0] + t2 * (5.0 * cam->k[1] + t2 * (7.0 * cam->k[2] + t2 * 9.0 * cam->k[3])));
+        s = td / r;
+        t = tdp / (r2 + z * z);
+        K = (t * z - s) / r2;
+    }
+    J[0] = cam->fx * (s + x * x * K);
+    J[1] = cam->fx * x * y * K;
+    J[2] = -cam->fx * x * t;
+    J[3] = cam->fy * x * y * K;
+    J[4] = cam->fy * (s + y * y * K);
+    J[5] = -cam->fy * y * t;
+}
+
+/* camera-space unit direction of the fisheye pixel ray through image point (X, Y) */
+static void fish_unproject(const ocam *cam, double X, double Y, double *dc) {
+    double mx = (X - cam->cx) / cam->fx, my = (Y - cam->cy) / cam->fy;
+    double td = sqrt(mx * mx + my * my);
+    if (td == 0.0) {
+        dc[0] = 0.0;
+        dc[1] = 0.0;
+        dc[2] = 1.0;
+        return;
+    }
+    double th = td;
+    for (int it = 0; it < 50; ++it) {
+        double t2 = th * th;
+        double f = fish_thetad(cam, th) - td;
+        double fp = 1.0 + t2 * (3.0 * cam->k[0] + t2 * (5.0 * cam->k[1] + t2 * (7.0 * cam->k[2] + t2 * 9.0 * cam->k[3])));
+        double step = f / fp;
+        th -= step;
+        if (fabs(step) <= 1e-15 * (1.0 + fabs(th))) break;
+    }
+    double st = sin(th);
+    dc[0] = st * mx / td;
+    dc[1] = st * my / td;
+    dc[2] = cos(th);
+}
+
 #define UT_VALID 0.0113
 
 typedef struct {
@@ -1281,8 +1375,12 @@ static void project_ut_one(const double *mu, const double *s, const double *q, d
         double *pc = P->pc[k];
         for (int i = 0; i < 3; ++i) pc[i] = V[4 * i] * X[0] + V[4 * i + 1] * X[1] + V[4 * i + 2] * X[2] + V[4 * i + 3];
         if (!(pc[2] > cam->z_near)) return; /* a sigma point behind the near plane: footprint undefined */
-        pts[k][0] = cam->fx * pc[0] / pc[2] + cam->cx;
-        pts[k][1] = cam->fy * pc[1] / pc[2] + cam->cy;
+        if (cam->model == 1) {
+            fish_project(cam, pc, pts[k]);
+        } else {
+            pts[k][0] = cam->fx * pc[0] / pc[2] + cam->cx;
+            pts[k][1] = cam->fy * pc[1] / pc[2] + cam->cy;
+        }
     }
     const double wm[7] = {0.0, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
     const double wc[7] = {2.0, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6, 1.0 / 6};
@@ -1372,8 +1470,12 @@ void oracle_project_ut(int64_t n, const double *mu, const double *scale, const d
 /* pixel_info: the world-space unit ray direction through the centre (x + 0.5, y + 0.5). */
 static void pixel_ray(double x, double y, const ocam *cam, double *rd) {
     double dc[3] = {(x + 0.5 - cam->cx) / cam->fx, (y + 0.5 - cam->cy) / cam->fy, 1.0};
-    double nl = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
-    for (int i = 0; i < 3; ++i) dc[i] /= nl;
+    if (cam->model == 1) {
+        fish_unproject(cam, x + 0.5, y + 0.5, dc);
+    } else {
+        double nl = sqrt(dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]);
+        for (int i = 0; i < 3; ++i) dc[i] /= nl;
+    }
     const double *V = cam->V; /* R_c2w = R_w2c^T */
     for (int i = 0; i < 3; ++i) rd[i] = V[i] * dc[0] + V[4 + i] * dc[1] + V[8 + i] * dc[2];
 }
@@ -1677,10 +1779,10 @@ void oracle_project_ut_bwd(int64_t n, const double *mu, const double *scale, con
             gp[k][1] += wm[k] * gbar[1];
         }
         for (int k = 0; k < 7; ++k) {
-            const double *pc = P.pc[k];
-            double z = pc[2];
-            double gpc[3] = {gp[k][0] * cam.fx / z, gp[k][1] * cam.fy / z,
-                             -gp[k][0] * cam.fx * pc[0] / (z * z) - gp[k][1] * cam.fy * pc[1] / (z * z)};
+            double Jp[6];
+            proj_jacobian(&cam, P.pc[k], Jp);
+            double gpc[3] = {gp[k][0] * Jp[0] + gp[k][1] * Jp[3], gp[k][0] * Jp[1] + gp[k][1] * Jp[4],
+                             gp[k][0] * Jp[2] + gp[k][1] * Jp[5]};
             double gX[3];
             for (int j = 0; j < 3; ++j) gX[j] = V[j] * gpc[0] + V[4 + j] * gpc[1] + V[8 + j] * gpc[2];
             for (int j = 0; j < 3; ++j) gmu[j] += gX[j];

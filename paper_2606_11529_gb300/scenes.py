@@ -33,15 +33,19 @@ class Camera:
     cy: float
     viewmat: np.ndarray = field(default_factory=lambda: np.hstack([np.eye(3), np.zeros((3, 1))]).astype(np.float32))
     z_near: float = 0.2
+    model: int = 0             # 0 pinhole, 1 fisheye (equidistant with radial polynomial; 3DGUT only)
+    dist: tuple = (0.0, 0.0, 0.0, 0.0)  # fisheye k1..k4: theta_d = theta (1 + k1 th^2 + k2 th^4 + k3 th^6 + k4 th^8)
 
     def as_tuple(self):
         return (self.width, self.height, self.fx, self.fy, self.cx, self.cy,
-                np.asarray(self.viewmat, np.float32).reshape(12), self.z_near)
+                np.asarray(self.viewmat, np.float32).reshape(12), self.z_near, self.model, tuple(self.dist))
 
 
 @dataclass
 class RenderConfig:
-    """Renderer constants.  Defaults are the readings documented in the design doc."""
+    """Renderer constants: tile size, alpha threshold 1/255, alpha clamp 0.99, transmittance stop
+    1e-4, low-pass dilation 0.3, Jacobian clip 1.3 (3DGS), SH degree, background, batch depth and
+    the method (0 3DGS, 1 3DGUT, 2 LinPrim)."""
     tile_w: int = 16
     tile_h: int = 16
     alpha_thresh: float = 1.0 / 255.0
@@ -147,6 +151,17 @@ def pinhole(width: int, height: int, focal: float, viewmat=None, z_near: float =
     vm = np.hstack([np.eye(3), np.zeros((3, 1))]) if viewmat is None else np.asarray(viewmat, np.float64)
     return Camera(width, height, float(focal), float(focal), width / 2.0, height / 2.0,
                   np.ascontiguousarray(vm, np.float32).reshape(3, 4), z_near)
+
+
+def fisheye(width: int, height: int, focal: float, dist=(0.05, -0.01, 0.001, 0.0), viewmat=None,
+            z_near: float = 0.2) -> Camera:
+    """Fisheye camera (equidistant projection with a 4-coefficient radial polynomial), principal point
+    at the image centre: a camera-space point at angle theta from the axis lands at radius
+    focal * theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8) from the principal point."""
+    cam = pinhole(width, height, focal, viewmat, z_near)
+    cam.model = 1
+    cam.dist = tuple(float(k) for k in dist)
+    return cam
 
 
 def yaw_view(yaw_deg: float, t=(0.0, 0.0, 0.0)) -> np.ndarray:

@@ -319,3 +319,103 @@ def test_ut_single_gaussian_opacity_derivative_closed_form(oracle):
     G = math.exp(-np.sum(np.cross(mu, d) ** 2) / (2 * s * s))
     assert g["opacity"][0] == pytest.approx(c * k / (k + DIL) * G, rel=1e-12)
     assert g["sh"][0, 0, 0] == pytest.approx(0.28209479177387814 * o * k / (k + DIL) * G, rel=1e-12)
+
+
+def test_fisheye_equidistant_closed_form(oracle):
+    # k = 0: a point at angle theta from the axis lands at radius f theta from the principal point
+    cam = scenes.fisheye(400, 300, 150.0, dist=(0.0, 0.0, 0.0, 0.0))
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        th, ph = rng.uniform(0, 1.2), rng.uniform(-math.pi, math.pi)
+        d = rng.uniform(0.5, 5)
+        pc = d * np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        uv = oracle.fisheye_project(pc, cam)[0]
+        np.testing.assert_allclose(uv, [200 + 150 * th * math.cos(ph), 150 + 150 * th * math.sin(ph)], atol=1e-10)
+    # the radial polynomial
+    k = (0.05, -0.01, 0.001, 0.0002)
+    cam = scenes.fisheye(400, 300, 150.0, dist=k)
+    th = 0.9
+    uv = oracle.fisheye_project(np.array([math.sin(th), 0.0, math.cos(th)]), cam)[0]
+    kk = [float(np.float32(v)) for v in k]
+    assert uv[0] - 200 == pytest.approx(150 * th * (1 + kk[0] * th ** 2 + kk[1] * th ** 4 + kk[2] * th ** 6 + kk[3] * th ** 8),
+                                        rel=1e-12)
+
+
+def test_fisheye_pixel_ray_projects_back_to_its_pixel(oracle):
+    vm = scenes.yaw_view(12.0, t=(0.1, -0.2, 0.3))
+    cam = scenes.fisheye(320, 240, 110.0, dist=(0.05, -0.01, 0.001, 0.0), viewmat=vm)
+    V = np.asarray(cam.viewmat, np.float64)
+    o = -V[:, :3].T @ V[:, 3]
+    rng = np.random.default_rng(1)
+    for _ in range(60):
+        x, y = int(rng.integers(0, 320)), int(rng.integers(0, 240))
+        d = oracle.pixel_ray(x, y, cam)
+        # (the float32-rounded view rotation is orthonormal to ~1e-7)
+        assert np.linalg.norm(d) == pytest.approx(1.0, abs=1e-6)
+        p = o + rng.uniform(0.5, 8.0) * d
+        pc = V[:, :3] @ p + V[:, 3]
+        np.testing.assert_allclose(oracle.fisheye_project(pc, cam)[0], [x + 0.5, y + 0.5], atol=1e-4)
+    # with the identity view (exact in float32) the round trip is exact to double rounding
+    cam = scenes.fisheye(320, 240, 110.0, dist=(0.05, -0.01, 0.001, 0.0))
+    for _ in range(60):
+        x, y = int(rng.integers(0, 320)), int(rng.integers(0, 240))
+        pc = rng.uniform(0.5, 8.0) * oracle.pixel_ray(x, y, cam)
+        np.testing.assert_allclose(oracle.fisheye_project(pc, cam)[0], [x + 0.5, y + 0.5], atol=1e-9)
+
+
+def test_single_gaussian_image_fisheye(oracle):
+    cam = scenes.fisheye(48, 40, 40.0)
+    cfg = _cfg(tile_w=8, tile_h=8)
+    mu, s, o = np.array([0.35, -0.2, 2.0]), 0.08, 0.9
+    arrs = _one(mu, [s, s, s], o=o)
+    arrs = arrs[:4] + (np.full((1, 1, 3), (0.7 - 0.5) / 0.28209479177387814),)
+    out = oracle.pipeline_tiled_ut(arrs, cam, cfg)
+    op = out["proj"]["rec"][0, 5]
+    img = out["image"][0]
+    checked = 0
+    for py in range(40):
+        for px in range(48):
+            d = oracle.pixel_ray(px, py, cam)
+            g = math.exp(-np.sum(np.cross(mu, d) ** 2) / (2 * s * s))
+            a = min(0.99, op * g)
+            if abs(a - A_T) < 1e-9 or abs(g - 0.0113) < 1e-9:
+                continue
+            inside = out["ranges"][(py // 8) * 6 + px // 8]
+            listed = 0 in out["vals"][inside[0]:inside[1]]
+            ref = 0.7 * a if (listed and g > 0.0113 and a >= A_T) else 0.0
+            assert img[py, px] == pytest.approx(ref, abs=1e-12)
+            checked += 1
+    assert checked > 1800 and img.max() > 0.3
+
+
+def test_ut_adjoint_fisheye_central_differences(oracle):
+    cam = scenes.fisheye(32, 32, 20.0, viewmat=scenes.yaw_view(9.0, t=(0.05, -0.03, 0.1)))
+    cfg = _cfg(sh_degree=1, bg=(0.1, 0.2, 0.3), tile_w=8, tile_h=8)
+    P = _tiny_ut_scene(7, deg=1)
+    P[0][:, :2] *= 2.5  # off-axis, where the fisheye departs from the pinhole
+    w = np.random.default_rng(17).normal(size=(3, 32, 32))
+    g = oracle.grads_tiled_ut(P, cam, cfg, w)
+    skipped = total = 0
+    for a, name in enumerate(["mu", "scale", "quat", "opacity", "sh"]):
+        fd = np.zeros_like(P[a], dtype=float)
+        it = np.nditer(P[a], flags=["multi_index"])
+        for _ in it:
+            idx = it.multi_index
+            x0 = P[a][idx]
+            h = 1e-6 * max(abs(x0), 1e-2)
+            Pp = [p.copy() for p in P]
+            Pm = [p.copy() for p in P]
+            Pp[a][idx] = x0 + h
+            Pm[a][idx] = x0 - h
+            lp, sp = oracle.loss_tiled_ut(Pp, cam, cfg, w)
+            lm, sm = oracle.loss_tiled_ut(Pm, cam, cfg, w)
+            total += 1
+            if sp != sm:
+                skipped += 1
+                fd[idx] = g[name][idx]
+                continue
+            fd[idx] = (lp - lm) / (2 * h)
+        err = np.linalg.norm(g[name] - fd) / max(np.linalg.norm(fd), 1e-30)
+        assert err < 1e-5, (name, err)
+    assert skipped <= 0.03 * total
+    assert np.abs(g["mu"]).max() > 0
