@@ -208,7 +208,9 @@ def batched_leg(dev, reps, flush, method=0):
     from paper_2606_11529_gb300 import render as R
     from paper_2606_11529_gb300 import scenes
     sc = scenes.uniform_scene(3_000_000, seed=0)
-    cams = scenes.multiview_cameras(8, 1600, 1064, 800.0, seed=0)
+    # 3DGUT sees the views through the fisheye of its configuration (it needs no linearisation)
+    cams = scenes.multiview_cameras(8, 1600, 1064, 800.0, seed=0,
+                                    fisheye_dist=scenes.FISHEYE_DIST if method == 1 else None)
     base = scenes.RenderConfig(sh_degree=0, method=method)
     P = [t.to(dev) for t in R.scene_to_device(sc)]
     w = torch.from_numpy(np.random.default_rng(2).normal(size=(8, 3, 1064, 1600)).astype(np.float32)).to(dev)
@@ -237,7 +239,8 @@ def batched_leg(dev, reps, flush, method=0):
     tp = _median_ms(plain, reps, flush)
     fr = BT.forward_views(*P, cams, best, BT.ViewsWorkspace())
     what = "3DGUT (unscented projection, ray evaluation)" if method == 1 else "3DGS"
-    return {"workload": f"{what}: 3M uniform SH-0 Gaussians (xy U[-1,1], z U[2,6]), 8 pinhole views 1600x1064 "
+    lens = ("fisheye (k = 0.05, -0.01, 0.001, 0)" if method == 1 else "pinhole")
+    return {"workload": f"{what}: 3M uniform SH-0 Gaussians (xy U[-1,1], z U[2,6]), 8 {lens} views 1600x1064 "
                         "f=800, yaw -15..+15 deg, fwd+bwd of all 8 views, seed 0",
             "ms_batched": round(tb, 3), "ms_plain_8x": round(tp, 3), "speedup": round(tp / tb, 3),
             "intersections": fr.n_isect, "tile": [best.tile_w, best.tile_h], "batch_depth": best.batch_depth,

@@ -53,7 +53,11 @@ typedef struct XprCamera {
     float fx, fy, cx, cy;
     float viewmat[12];
     float z_near; /* primitives with camera-space z <= z_near are invisible (Listing 1 visibility flag) */
-    int32_t model; /* 0 = pinhole (the only model implemented) */
+    int32_t model; /* 0 = pinhole; 1 = fisheye (3DGUT configs only): a camera-space point at angle
+                      theta = atan2(sqrt(x^2 + y^2), z) from the axis lands at (fx theta_d x / r + cx,
+                      fy theta_d y / r + cy), theta_d = theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6
+                      + k4 theta^8), r = sqrt(x^2 + y^2) */
+    float dist[4]; /* fisheye k1..k4 (ignored for the pinhole) */
 } XprCamera;
 
 /* Renderer constants.  alpha_thresh is the contribution threshold 1/255 of

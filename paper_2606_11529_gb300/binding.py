@@ -21,7 +21,7 @@ c_i32, c_i64, c_f32, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
 
 class XprCamera(ctypes.Structure):
     _fields_ = [("width", c_i32), ("height", c_i32), ("fx", c_f32), ("fy", c_f32), ("cx", c_f32), ("cy", c_f32),
-                ("viewmat", c_f32 * 12), ("z_near", c_f32), ("model", c_i32)]
+                ("viewmat", c_f32 * 12), ("z_near", c_f32), ("model", c_i32), ("dist", c_f32 * 4)]
 
 
 class XprConfig(ctypes.Structure):
@@ -178,7 +178,8 @@ def make_camera(cam) -> XprCamera:
     vm = [float(v) for v in __import__("numpy").asarray(cam.viewmat, dtype="float32").reshape(12)]
     c.viewmat[:] = vm
     c.z_near = float(cam.z_near)
-    c.model = 0
+    c.model = int(getattr(cam, "model", 0))
+    c.dist[:] = [float(k) for k in getattr(cam, "dist", (0.0, 0.0, 0.0, 0.0))]
     return c
 
 

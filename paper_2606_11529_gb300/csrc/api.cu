@@ -40,7 +40,8 @@ int validate_camera_config(const XprCamera *cam, const XprConfig *cfg) {
     if (!cam || !cfg) return fail(XPR_ERR_INVALID, "camera/config pointer is NULL");
     if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
         return fail(XPR_ERR_INVALID, "image size %dx%d out of range [1, 32768]", cam->width, cam->height);
-    if (cam->model != 0) return fail(XPR_ERR_INVALID, "camera model %d not supported (0 = pinhole)", cam->model);
+    if (cam->model != 0 && cam->model != 1)
+        return fail(XPR_ERR_INVALID, "camera model %d not supported (0 = pinhole, 1 = fisheye)", cam->model);
     if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(XPR_ERR_INVALID, "focal lengths must be positive");
     if ((cfg->tile_w != 8 && cfg->tile_w != 16) || (cfg->tile_h != 8 && cfg->tile_h != 16))
         return fail(XPR_ERR_INVALID, "tile size %dx%d not supported (8 or 16 each)", cfg->tile_w, cfg->tile_h);
@@ -52,6 +53,10 @@ int validate_camera_config(const XprCamera *cam, const XprConfig *cfg) {
     if (!(cfg->t_eps >= 0.f)) return fail(XPR_ERR_INVALID, "t_eps must be >= 0");
     if (cfg->method != XPR_METHOD_3DGS && cfg->method != XPR_METHOD_3DGUT && cfg->method != XPR_METHOD_LINPRIM)
         return fail(XPR_ERR_INVALID, "method %d not supported (0 = 3DGS, 1 = 3DGUT, 2 = LinPrim)", cfg->method);
+    if (cam->model == 1 && cfg->method != XPR_METHOD_3DGUT)
+        return fail(XPR_ERR_INVALID, "the fisheye camera needs the 3DGUT method (the others linearise a pinhole)");
+    for (int i = 0; i < 4; ++i)
+        if (!(fabsf(cam->dist[i]) < 1e30f)) return fail(XPR_ERR_INVALID, "fisheye coefficient %d not finite", i);
     return XPR_OK;
 }
 

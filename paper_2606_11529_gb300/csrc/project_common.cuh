@@ -84,6 +84,8 @@ struct Cam {
     float W[9], t[3], cpos[3];
     float fx, fy, cx, cy, limx, limy, z_near;
     int width, height;
+    int model;   // 0 pinhole, 1 fisheye
+    float k[4];  // fisheye radial coefficients
 };
 
 __device__ __forceinline__ Cam make_cam(const XprCamera &c, const XprConfig &g) {
@@ -102,6 +104,8 @@ __device__ __forceinline__ Cam make_cam(const XprCamera &c, const XprConfig &g) 
     k.z_near = c.z_near;
     k.width = c.width;
     k.height = c.height;
+    k.model = c.model;
+    for (int i = 0; i < 4; ++i) k.k[i] = c.dist[i];
     return k;
 }
 

@@ -40,6 +40,65 @@ namespace {
 constexpr float kSqrt3 = 1.7320508075688772f;
 constexpr float kUtValid = 0.0113f;  // validity threshold of the ray response
 
+// Fisheye camera (equidistant projection with a radial polynomial): a camera-space point at angle
+// theta = atan2(r, z) from the axis, r = |(x, y)|, lands at (fx s x + cx, fy s y + cy) with
+// s = theta_d / r, theta_d = theta (1 + k1 theta^2 + k2 theta^4 + k3 theta^6 + k4 theta^8).
+__device__ __forceinline__ float fish_thetad(const float *kk, float th) {
+    const float t2 = th * th;
+    return th * (1.f + t2 * (kk[0] + t2 * (kk[1] + t2 * (kk[2] + t2 * kk[3]))));
+}
+__device__ __forceinline__ float fish_thetad_prime(const float *kk, float th) {
+    const float t2 = th * th;
+    return 1.f + t2 * (3.f * kk[0] + t2 * (5.f * kk[1] + t2 * (7.f * kk[2] + t2 * 9.f * kk[3])));
+}
+
+// projection of a camera-space point to pixels (pinhole or fisheye)
+__device__ __forceinline__ void cam_project(const Cam &k, float x, float y, float z, float &u, float &v) {
+    if (k.model == 1) {
+        const float r = sqrtf(x * x + y * y);
+        const float s = r > 0.f ? fish_thetad(k.k, atan2f(r, z)) / r : 1.f / z;
+        u = k.fx * s * x + k.cx;
+        v = k.fy * s * y + k.cy;
+    } else {
+        u = k.fx * (x / z) + k.cx;
+        v = k.fy * (y / z) + k.cy;
+    }
+}
+
+// d(u, v)/d(x, y, z), 2x3 row-major.  Fisheye, with s = theta_d / r, t = theta_d' / (r^2 + z^2),
+// K = (t z - s) / r^2: du/dx = fx (s + x^2 K), du/dy = fx x y K, du/dz = -fx x t, and v alike
+// (on the axis s -> 1/z, t -> 1/z^2, K -> 2 (k1 - 1/3) / z^3).
+__device__ __forceinline__ void cam_jacobian(const Cam &k, float x, float y, float z, float *J) {
+    if (k.model != 1) {
+        const float iz = 1.f / z;
+        J[0] = k.fx * iz;
+        J[1] = 0.f;
+        J[2] = -k.fx * x * iz * iz;
+        J[3] = 0.f;
+        J[4] = k.fy * iz;
+        J[5] = -k.fy * y * iz * iz;
+        return;
+    }
+    const float r2 = x * x + y * y, r = sqrtf(r2);
+    float s, t, K;
+    if (r < 1e-6f * fabsf(z)) {
+        s = 1.f / z;
+        t = s * s;
+        K = 2.f * (k.k[0] - 1.f / 3.f) * s * s * s;
+    } else {
+        const float th = atan2f(r, z);
+        s = fish_thetad(k.k, th) / r;
+        t = fish_thetad_prime(k.k, th) / (r2 + z * z);
+        K = (t * z - s) / r2;
+    }
+    J[0] = k.fx * (s + x * x * K);
+    J[1] = k.fx * x * y * K;
+    J[2] = -k.fx * x * t;
+    J[3] = k.fy * x * y * K;
+    J[4] = k.fy * (s + y * y * K);
+    J[5] = -k.fy * y * t;
+}
+
 // Forward quantities of the unscented projection (recomputed by the adjoint).
 struct UtGeo {
     float qn[4], qinv;
@@ -76,6 +135,8 @@ __device__ __forceinline__ void ut_geometry(const Params &P, const Cam &k, float
     const float x0 = U.mc[0], y0 = U.mc[1], z0 = U.mc[2];
     U.front = z0 > k.z_near;
     float sx = 0.f, sy = 0.f;
+    float u0 = 0.f, v0 = 0.f;
+    if (k.model == 1) cam_project(k, x0, y0, z0, u0, v0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float h = kSqrt3 * P.s[a];
@@ -87,9 +148,16 @@ __device__ __forceinline__ void ut_geometry(const Params &P, const Cam &k, float
             const float sg = e == 0 ? 1.f : -1.f;
             const float zk = z0 + sg * U.D[a][2];
             U.front = U.front && (zk > k.z_near);
-            const float f = sg / (zk * z0);
-            U.dl[2 * a + e][0] = k.fx * nx * f;
-            U.dl[2 * a + e][1] = k.fy * ny * f;
+            if (k.model == 1) {  // fisheye: difference of the projections
+                float uk, vk;
+                cam_project(k, x0 + sg * U.D[a][0], y0 + sg * U.D[a][1], zk, uk, vk);
+                U.dl[2 * a + e][0] = uk - u0;
+                U.dl[2 * a + e][1] = vk - v0;
+            } else {  // pinhole: the offset in closed form, without cancellation
+                const float f = sg / (zk * z0);
+                U.dl[2 * a + e][0] = k.fx * nx * f;
+                U.dl[2 * a + e][1] = k.fy * ny * f;
+            }
             sx += U.dl[2 * a + e][0];
             sy += U.dl[2 * a + e][1];
         }
@@ -132,8 +200,10 @@ __device__ __forceinline__ UtFootprint ut_footprint(const UtGeo &U, float o, con
     f.cc = a * idet;
     f.lt = logf(f.o / cfg.alpha_thresh);
     const float ex = sqrtf(2.f * f.lt * a), ey = sqrtf(2.f * f.lt * c);
-    f.mx = k.fx * (U.mc[0] / U.mc[2]) + k.cx + U.mo[0];
-    f.my = k.fy * (U.mc[1] / U.mc[2]) + k.cy + U.mo[1];
+    float u0, v0;
+    cam_project(k, U.mc[0], U.mc[1], U.mc[2], u0, v0);
+    f.mx = u0 + U.mo[0];
+    f.my = v0 + U.mo[1];
     const float Wt = (float)((k.width + cfg.tile_w - 1) / cfg.tile_w);
     const float Ht = (float)((k.height + cfg.tile_h - 1) / cfg.tile_h);
     const float tw = (float)cfg.tile_w, th = (float)cfg.tile_h;
@@ -183,9 +253,13 @@ __device__ __forceinline__ void ut_project_view(const Params &P, const float *sh
     o4[1] = make_float4(f.cc, f.o, col[0], col[1]);
     o4[2] = make_float4(col[2], U.mc[2], f.lt, 1.f);
     // shader data
+    // the centre and the canonical images of the pixel axes: in pixels for the pinhole, in normalised
+    // image coordinates (x/z, y/z) for the fisheye, whose pixel rays the render unprojects
     const float z0 = U.mc[2];
-    const float p0x = k.fx * (U.mc[0] / z0) + k.cx, p0y = k.fy * (U.mc[1] / z0) + k.cy;
-    const float s0 = z0 / k.fx, s1 = z0 / k.fy;
+    const bool fish = k.model == 1;
+    const float p0x = fish ? U.mc[0] / z0 : k.fx * (U.mc[0] / z0) + k.cx;
+    const float p0y = fish ? U.mc[1] / z0 : k.fy * (U.mc[1] / z0) + k.cy;
+    const float s0 = fish ? z0 : z0 / k.fx, s1 = fish ? z0 : z0 / k.fy;
     const float vx = k.cpos[0] - P.m[0], vy = k.cpos[1] - P.m[1], vz = k.cpos[2] - P.m[2];
     float roc[3];
     for (int i = 0; i < 3; ++i) roc[i] = U.M[3 * i] * vx + U.M[3 * i + 1] * vy + U.M[3 * i + 2] * vz;
@@ -254,15 +328,17 @@ __device__ __forceinline__ void ut_adjoint_view(const Params &P, const float *sh
 
     const float x0 = U.mc[0], y0 = U.mc[1], z0 = U.mc[2];
     const float iz = 1.f / z0, iz2 = iz * iz;
+    // the shader data's units: pixels (pinhole, scale f) or normalised coordinates (fisheye, scale 1)
+    const float fx = k.model == 1 ? 1.f : k.fx, fy = k.model == 1 ? 1.f : k.fy;
     float gmc[3];
-    // p_0
-    gmc[0] = dp0x * k.fx * iz;
-    gmc[1] = dp0y * k.fy * iz;
-    gmc[2] = -(dp0x * k.fx * x0 + dp0y * k.fy * y0) * iz2;
-    // A_0, A_1
-    const float s0 = z0 / k.fx, s1 = z0 / k.fy;
-    gmc[2] += (dA0[0] * U.Mc[0] + dA0[1] * U.Mc[3] + dA0[2] * U.Mc[6]) / k.fx +
-              (dA1[0] * U.Mc[1] + dA1[1] * U.Mc[4] + dA1[2] * U.Mc[7]) / k.fy;
+    // p_0 = (fx x/z, fy y/z) (+ principal point)
+    gmc[0] = dp0x * fx * iz;
+    gmc[1] = dp0y * fy * iz;
+    gmc[2] = -(dp0x * fx * x0 + dp0y * fy * y0) * iz2;
+    // A_0 = (z / fx) Mc e_0, A_1 = (z / fy) Mc e_1
+    const float s0 = z0 / fx, s1 = z0 / fy;
+    gmc[2] += (dA0[0] * U.Mc[0] + dA0[1] * U.Mc[3] + dA0[2] * U.Mc[6]) / fx +
+              (dA1[0] * U.Mc[1] + dA1[1] * U.Mc[4] + dA1[2] * U.Mc[7]) / fy;
     // Mc = M W^T (columns 0 and 1 only): dM_ik = sum_j dMc_ij W_jk; plus o_c = M (c - mu)
     const float v[3] = {k.cpos[0] - P.m[0], k.cpos[1] - P.m[1], k.cpos[2] - P.m[2]};
     float gM[9];
@@ -311,9 +387,9 @@ __device__ __forceinline__ void ut_adjoint_view(const Params &P, const float *sh
                 sgx += gx;
                 sgy += gy;
                 const float xk = x0 + sg * U.D[a][0], yk = y0 + sg * U.D[a][1], zk = z0 + sg * U.D[a][2];
-                const float izk = 1.f / zk;
-                const float g0 = gx * k.fx * izk, g1 = gy * k.fy * izk;
-                const float g2 = -(g0 * xk + g1 * yk) * izk;
+                float Jk[6];
+                cam_jacobian(k, xk, yk, zk, Jk);
+                const float g0 = gx * Jk[0] + gy * Jk[3], g1 = gx * Jk[1] + gy * Jk[4], g2 = gx * Jk[2] + gy * Jk[5];
                 gmc[0] += g0;
                 gmc[1] += g1;
                 gmc[2] += g2;
@@ -328,10 +404,11 @@ __device__ __forceinline__ void ut_adjoint_view(const Params &P, const float *sh
                 gR[3 * kk + a] += h * (k.W[kk] * gD[0] + k.W[3 + kk] * gD[1] + k.W[6 + kk] * gD[2]);
         }
         // p_0 = proj(m_c) enters every offset with a minus sign
-        const float g0 = -sgx * k.fx * iz, g1 = -sgy * k.fy * iz;
-        gmc[0] += g0;
-        gmc[1] += g1;
-        gmc[2] -= (g0 * x0 + g1 * y0) * iz;
+        float J0[6];
+        cam_jacobian(k, x0, y0, z0, J0);
+        gmc[0] -= sgx * J0[0] + sgy * J0[3];
+        gmc[1] -= sgx * J0[1] + sgy * J0[4];
+        gmc[2] -= sgx * J0[2] + sgy * J0[5];
     }
     for (int j = 0; j < 3; ++j) A.mu[j] += k.W[j] * gmc[0] + k.W[3 + j] * gmc[1] + k.W[6 + j] * gmc[2];
     rotation_adjoint(U.qn, gR, A.qn);
@@ -404,7 +481,37 @@ struct UtConsts {
     uint32_t n;       // records per launch: list entries >= n are ignored
     int batch;
     float at, amax, teps, bg0, bg1, bg2;
+    int model;                 // camera: 0 pinhole, 1 fisheye
+    float fx, fy, cx, cy, k[4];
 };
+
+// The coordinates a pixel is evaluated at: its centre (x + 0.5, y + 0.5) for the pinhole; for the
+// fisheye the normalised image coordinates (d_x / d_z, d_y / d_z) of its ray d, whose angle theta from
+// the axis solves theta_d(theta) = |m|, m = ((x + 0.5 - cx) / fx, (y + 0.5 - cy) / fy) (Newton's
+// method).  Returns false for a ray at 1.5 rad or more from the axis (no finite coordinates).
+template <bool FISH>
+__device__ __forceinline__ bool ut_pixel_coord(const UtConsts &k, int x, int y, float &u, float &v) {
+    const float X = (float)x + 0.5f, Y = (float)y + 0.5f;
+    if (!FISH) {
+        u = X;
+        v = Y;
+        return true;
+    }
+    const float mx = (X - k.cx) / k.fx, my = (Y - k.cy) / k.fy;
+    const float td = sqrtf(mx * mx + my * my);
+    if (td == 0.f) {
+        u = v = 0.f;
+        return true;
+    }
+    float th = td;
+#pragma unroll 1
+    for (int it = 0; it < 10; ++it) th -= (fish_thetad(k.k, th) - td) / fish_thetad_prime(k.k, th);
+    if (!(th < 1.5f && th > 0.f)) return false;
+    const float sc = tanf(th) / td;
+    u = mx * sc;
+    v = my * sc;
+    return true;
+}
 
 // Staged entry: [p0x p0y A0x A0y] [A0z A1x A1y A1z] [o_c o'] [r g b |o_c|^2]
 struct UtStage {
@@ -455,7 +562,7 @@ __device__ __forceinline__ UtEval ut_eval(float cx, float cy, const float4 &u0, 
 }
 
 struct UtPixFwd {
-    float cy, T, r, g, b;
+    float cx, cy, T, r, g, b;
     int last;
     bool done;
 };
@@ -466,7 +573,7 @@ struct UtWork {  // persistent scheduling: tiles list[0 .. count) taken through 
     int count;
 };
 
-template <int TW, int TH>
+template <int TW, int TH, bool FISH>
 __device__ __forceinline__ void ut_fwd_tile(int gt, const float *__restrict__ sd, const uint32_t *__restrict__ vals,
                                             const int2 *__restrict__ ranges, const UtConsts &k,
                                             float *__restrict__ image, float *__restrict__ tfin,
@@ -480,14 +587,15 @@ __device__ __forceinline__ void ut_fwd_tile(int gt, const float *__restrict__ sd
     const int t = threadIdx.x;
     const int px = tx * TW + t % TW, py = ty * TH + t / TW;
     const int2 rg = ranges[gt];
-    const float cx = (float)px + 0.5f;
+    const float col_x = (float)px + 0.5f;  // the pinhole's x coordinate, shared by the thread's pixels
     UtPixFwd P[kUtPx];
     bool in[kUtPx];
     bool all_done = true;
 #pragma unroll
     for (int q = 0; q < kUtPx; ++q) {
         in[q] = px < k.W && py + q * RS < k.H;
-        P[q] = UtPixFwd{(float)(py + q * RS) + 0.5f, 1.f, 0.f, 0.f, 0.f, 0, !in[q]};
+        P[q] = UtPixFwd{0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0, !in[q]};
+        if (in[q] && !ut_pixel_coord<FISH>(k, px, py + q * RS, P[q].cx, P[q].cy)) P[q].done = true;
         all_done &= P[q].done;
     }
     for (int base = rg.x; base < rg.y; base += k.batch) {
@@ -504,7 +612,7 @@ __device__ __forceinline__ void ut_fwd_tile(int gt, const float *__restrict__ sd
                 for (int q = 0; q < kUtPx; ++q) {
                     UtPixFwd &p = P[q];
                     if (!p.done) {
-                        const UtEval ev = ut_eval(cx, p.cy, u0, u1, u2, u3.w);
+                        const UtEval ev = ut_eval(FISH ? p.cx : col_x, p.cy, u0, u1, u2, u3.w);
                         const float G = ex2_approx(__fmul_rn(-0.5f * kLog2e, ev.Q));
                         if (G > kUtValid) {
                             const float og = __fmul_rn(u2.w, G);
@@ -544,14 +652,14 @@ __device__ __forceinline__ void ut_fwd_tile(int gt, const float *__restrict__ sd
     }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool FISH>
 __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_fwd_kernel(
     const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, UtConsts k,
     float *__restrict__ image, float *__restrict__ tfin, int *__restrict__ ncon, UtWork w) {
     __shared__ float4 s_u0[kUtBatch], s_u1[kUtBatch], s_u2[kUtBatch], s_u3[kUtBatch];
     const UtStage S = {s_u0, s_u1, s_u2, s_u3, nullptr};
     if (w.list == nullptr) {
-        ut_fwd_tile<TW, TH>(blockIdx.x, sd, vals, ranges, k, image, tfin, ncon, S);
+        ut_fwd_tile<TW, TH, FISH>(blockIdx.x, sd, vals, ranges, k, image, tfin, ncon, S);
         return;
     }
     __shared__ int s_item;
@@ -561,7 +669,7 @@ __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_fwd_kernel
         __syncthreads();
         const int item = s_item;
         if (item >= w.count) break;
-        ut_fwd_tile<TW, TH>(w.list[item], sd, vals, ranges, k, image, tfin, ncon, S);
+        ut_fwd_tile<TW, TH, FISH>(w.list[item], sd, vals, ranges, k, image, tfin, ncon, S);
     }
 }
 
@@ -598,7 +706,7 @@ __device__ __forceinline__ float reduce_scatter16(const float *v, int lane) {
 }
 
 struct UtPixBwd {
-    float cy, T, g0, g1, g2, S0, S1, S2;
+    float cx, cy, T, g0, g1, g2, S0, S1, S2;
     int last;
 };
 
@@ -649,7 +757,7 @@ __device__ __forceinline__ bool ut_adjoint(UtPixBwd &P, float cx, const float4 &
     return true;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool FISH>
 __device__ __forceinline__ void ut_bwd_tile(int gt, const float *__restrict__ sd, const uint32_t *__restrict__ vals,
                                             const int2 *__restrict__ ranges, const UtConsts &k,
                                             const float *__restrict__ tfin, const int *__restrict__ ncon,
@@ -665,7 +773,7 @@ __device__ __forceinline__ void ut_bwd_tile(int gt, const float *__restrict__ sd
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int px = tx * TW + t % TW, py = ty * TH + t / TW;
     const int2 rg = ranges[gt];
-    const float cx = (float)px + 0.5f;
+    const float col_x = (float)px + 0.5f;  // the pinhole's x coordinate, shared by the thread's pixels
     const int64_t HW = (int64_t)k.W * k.H;
     const float *tf = tfin + v * HW;
     const int *nc = ncon + v * HW;
@@ -677,8 +785,8 @@ __device__ __forceinline__ void ut_bwd_tile(int gt, const float *__restrict__ sd
         const int y = py + q * RS;
         const bool in = px < k.W && y < k.H;
         const int64_t pix = (int64_t)y * k.W + px;
-        P[q] = UtPixBwd{(float)y + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
-        if (in) {
+        P[q] = UtPixBwd{0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        if (in && ut_pixel_coord<FISH>(k, px, y, P[q].cx, P[q].cy)) {
             P[q].T = tf[pix];
             P[q].last = nc[pix];
             P[q].g0 = di[pix];
@@ -717,7 +825,7 @@ __device__ __forceinline__ void ut_bwd_tile(int gt, const float *__restrict__ sd
             const float4 u0 = s_u0[j], u1 = s_u1[j], u2 = s_u2[j], u3 = s_u3[j];
             bool hit = false;
 #pragma unroll
-            for (int q = 0; q < kUtPx; ++q) hit |= ut_adjoint(P[q], cx, u0, u1, u2, u3, pos, k, vv);
+            for (int q = 0; q < kUtPx; ++q) hit |= ut_adjoint(P[q], FISH ? P[q].cx : col_x, u0, u1, u2, u3, pos, k, vv);
             if (__any_sync(kFullUt, hit)) {
                 const float r = reduce_scatter16(vv, lane);
                 if ((lane & 1) == 0) atomicAdd(&s_acc[lane >> 1][j], r);
@@ -747,7 +855,7 @@ __device__ __forceinline__ void ut_bwd_tile(int gt, const float *__restrict__ sd
     }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool FISH>
 __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel(
     const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, UtConsts k,
     const float *__restrict__ tfin, const int *__restrict__ ncon, const float *__restrict__ dimg,
@@ -760,7 +868,7 @@ __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel
     __shared__ int s_wmax[NW];
     const UtStage S = {s_u0, s_u1, s_u2, s_u3, s_id};
     if (w.list == nullptr) {
-        ut_bwd_tile<TW, TH>(blockIdx.x, sd, vals, ranges, k, tfin, ncon, dimg, d_sd, S, s_acc, s_wmax);
+        ut_bwd_tile<TW, TH, FISH>(blockIdx.x, sd, vals, ranges, k, tfin, ncon, dimg, d_sd, S, s_acc, s_wmax);
         return;
     }
     __shared__ int s_item;
@@ -770,7 +878,7 @@ __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel
         __syncthreads();
         const int item = s_item;
         if (item >= w.count) break;
-        ut_bwd_tile<TW, TH>(w.list[item], sd, vals, ranges, k, tfin, ncon, dimg, d_sd, S, s_acc, s_wmax);
+        ut_bwd_tile<TW, TH, FISH>(w.list[item], sd, vals, ranges, k, tfin, ncon, dimg, d_sd, S, s_acc, s_wmax);
     }
 }
 
@@ -788,6 +896,12 @@ UtConsts make_ut_consts(const XprCamera &cam, const XprConfig &cfg, int64_t n) {
     k.bg0 = cfg.bg[0];
     k.bg1 = cfg.bg[1];
     k.bg2 = cfg.bg[2];
+    k.model = cam.model;
+    k.fx = cam.fx;
+    k.fy = cam.fy;
+    k.cx = cam.cx;
+    k.cy = cam.cy;
+    for (int i = 0; i < 4; ++i) k.k[i] = cam.dist[i];
     return k;
 }
 
@@ -856,11 +970,21 @@ int launch_ut_render_fwd(const float *sd, int64_t n, const uint32_t *vals, const
     const int2 *rg = reinterpret_cast<const int2 *>(ranges);
     const UtWork w = {worklist, counter, items};
     if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
-    XPR_UT_TILE_DISPATCH(TW, TH, {
-        const int threads = TW * TH / ut_px<TW, TH>();
-        const int grid = worklist ? ut_persistent_grid(ut_render_fwd_kernel<TW, TH>, threads, items) : items;
-        ut_render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(sd, vals, rg, k, image, t_final, n_contrib, w);
-    });
+    // the camera model is a template argument: the pinhole kernels carry no unprojection code
+    if (cam.model == 1) {
+        XPR_UT_TILE_DISPATCH(TW, TH, {
+            const int threads = TW * TH / ut_px<TW, TH>();
+            const int grid = worklist ? ut_persistent_grid(ut_render_fwd_kernel<TW, TH, true>, threads, items) : items;
+            ut_render_fwd_kernel<TW, TH, true><<<grid, threads, 0, st>>>(sd, vals, rg, k, image, t_final, n_contrib, w);
+        });
+    } else {
+        XPR_UT_TILE_DISPATCH(TW, TH, {
+            const int threads = TW * TH / ut_px<TW, TH>();
+            const int grid = worklist ? ut_persistent_grid(ut_render_fwd_kernel<TW, TH, false>, threads, items) : items;
+            ut_render_fwd_kernel<TW, TH, false><<<grid, threads, 0, st>>>(sd, vals, rg, k, image, t_final, n_contrib,
+                                                                          w);
+        });
+    }
     XPR_LAUNCH_CHECK("ut_render_fwd_kernel");
     return XPR_OK;
 }
@@ -876,12 +1000,21 @@ int launch_ut_render_bwd(const float *sd, int64_t n, const uint32_t *vals, const
     const int2 *rg = reinterpret_cast<const int2 *>(ranges);
     const UtWork w = {worklist, counter, items};
     if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
-    XPR_UT_TILE_DISPATCH(TW, TH, {
-        const int threads = TW * TH / ut_px<TW, TH>();
-        const int grid = worklist ? ut_persistent_grid(ut_render_bwd_kernel<TW, TH>, threads, items) : items;
-        ut_render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(sd, vals, rg, k, t_final, n_contrib, d_image, d_sd,
-                                                                 w);
-    });
+    if (cam.model == 1) {
+        XPR_UT_TILE_DISPATCH(TW, TH, {
+            const int threads = TW * TH / ut_px<TW, TH>();
+            const int grid = worklist ? ut_persistent_grid(ut_render_bwd_kernel<TW, TH, true>, threads, items) : items;
+            ut_render_bwd_kernel<TW, TH, true><<<grid, threads, 0, st>>>(sd, vals, rg, k, t_final, n_contrib, d_image,
+                                                                         d_sd, w);
+        });
+    } else {
+        XPR_UT_TILE_DISPATCH(TW, TH, {
+            const int threads = TW * TH / ut_px<TW, TH>();
+            const int grid = worklist ? ut_persistent_grid(ut_render_bwd_kernel<TW, TH, false>, threads, items) : items;
+            ut_render_bwd_kernel<TW, TH, false><<<grid, threads, 0, st>>>(sd, vals, rg, k, t_final, n_contrib, d_image,
+                                                                          d_sd, w);
+        });
+    }
     XPR_LAUNCH_CHECK("ut_render_bwd_kernel");
     return XPR_OK;
 }

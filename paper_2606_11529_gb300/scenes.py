@@ -190,16 +190,22 @@ def linprim_case(n: int = 500_000, seed: int = 0):
 
 
 def multiview_cameras(n_views: int = 8, width: int = 1600, height: int = 1064, focal: float = 800.0,
-                      seed: int = 0):
-    """``n_views`` pinhole cameras yawed evenly over [-15, +15] degrees and
-    translated by at most 0.1 along each axis."""
+                      seed: int = 0, fisheye_dist=None):
+    """``n_views`` cameras yawed evenly over [-15, +15] degrees and translated by at most 0.1 along
+    each axis: pinhole, or fisheye with radial coefficients ``fisheye_dist`` when given."""
     rng = np.random.default_rng(seed + 7)
     yaws = np.linspace(-15.0, 15.0, n_views) if n_views > 1 else np.zeros(1)
     cams = []
     for y in yaws:
         t = rng.uniform(-0.1, 0.1, size=3)
-        cams.append(pinhole(width, height, focal, yaw_view(float(y), t)))
+        vm = yaw_view(float(y), t)
+        cams.append(pinhole(width, height, focal, vm) if fisheye_dist is None
+                    else fisheye(width, height, focal, fisheye_dist, vm))
     return cams
+
+
+# radial coefficients of the fisheye in the 3DGUT workload
+FISHEYE_DIST = (0.05, -0.01, 0.001, 0.0)
 
 
 def serving_scenes(n_scenes: int = 16, n_min: int = 100_000, n_max: int = 3_000_000, seed: int = 0,

@@ -66,7 +66,8 @@ def _cam_cfg(**over):
     (dict(width=0), b"image size"),
     (dict(sh_degree=4), b"sh_degree"),
     (dict(alpha_max=1.0), b"alpha_max"),
-    (dict(model=1), b"camera model"),
+    (dict(model=2), b"camera model"),
+    (dict(model=1), b"fisheye camera needs the 3DGUT"),
 ])
 def test_invalid_arguments_rejected_on_host(lib, over, frag):
     from paper_2606_11529_gb300 import binding

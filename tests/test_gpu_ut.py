@@ -20,12 +20,13 @@ pytestmark = pytest.mark.gpu
 A_T = float(np.float32(1 / 255))
 
 
-def _ut_case(oracle, deg=0, tile=16, view=False, n=8000, W=256, H=256, seed=0, big_every=0):
+def _ut_case(oracle, deg=0, tile=16, view=False, n=8000, W=256, H=256, seed=0, big_every=0, fish=False):
     sc = scenes.uniform_scene(n, seed=seed, sh_degree=deg)
     if big_every:
         sc.scale[::big_every] *= 12.0
     vm = scenes.yaw_view(4.0, (0.05, -0.02, 0.1)) if view else None
-    cam = scenes.pinhole(W, H, float(W), vm)
+    # the fisheye sees the same scene with a wider field (focal W/2, radial terms of the workload)
+    cam = scenes.fisheye(W, H, W / 2.0, viewmat=vm) if fish else scenes.pinhole(W, H, float(W), vm)
     cfg = scenes.RenderConfig(tile_w=tile, tile_h=tile, sh_degree=deg, method=1)
     pr = oracle.project_ut(*sc.arrays(), cam, cfg)
     o = pr["sd"][:, 12]
@@ -45,10 +46,15 @@ def _oracle_sd_in_kernel_form(pr, sc, cam):
     Mc = M @ W3.T
     z = mc[:, 2]
     out = np.zeros((sc.n, 16))
-    out[:, 0] = cam.fx * mc[:, 0] / z + cam.cx
-    out[:, 1] = cam.fy * mc[:, 1] / z + cam.cy
-    out[:, 2:5] = (z / cam.fx)[:, None] * Mc[:, :, 0]
-    out[:, 5:8] = (z / cam.fy)[:, None] * Mc[:, :, 1]
+    if getattr(cam, "model", 0) == 1:  # fisheye: normalised image coordinates
+        fx = fy = 1.0
+        cx = cy = 0.0
+    else:
+        fx, fy, cx, cy = cam.fx, cam.fy, cam.cx, cam.cy
+    out[:, 0] = fx * mc[:, 0] / z + cx
+    out[:, 1] = fy * mc[:, 1] / z + cy
+    out[:, 2:5] = (z / fx)[:, None] * Mc[:, :, 0]
+    out[:, 5:8] = (z / fy)[:, None] * Mc[:, :, 1]
     out[:, 8:11] = pr["sd"][:, 0:3]
     out[:, 11] = pr["sd"][:, 12]
     out[:, 12:15] = pr["sd"][:, 13:16]
@@ -56,9 +62,10 @@ def _oracle_sd_in_kernel_form(pr, sc, cam):
     return out
 
 
-@pytest.mark.parametrize("deg,tile,view", [(0, 16, False), (3, 8, True), (1, 16, True)])
-def test_ut_project_matches_oracle(oracle, deg, tile, view):
-    sc, cam, cfg, pr = _ut_case(oracle, deg, tile, view)
+@pytest.mark.parametrize("deg,tile,view,fish", [(0, 16, False, False), (3, 8, True, False), (1, 16, True, False),
+                                                (0, 16, False, True), (3, 8, True, True)])
+def test_ut_project_matches_oracle(oracle, deg, tile, view, fish):
+    sc, cam, cfg, pr = _ut_case(oracle, deg, tile, view, fish=fish)
     rec, sd, bbox, tc, cnt = B.xpr_project_ut(*R.scene_to_device(sc), cam, cfg)
     torch.cuda.synchronize()
     rec, sd, bbox, tc, cnt = (x.cpu().numpy() for x in (rec, sd, bbox, tc, cnt))
@@ -81,7 +88,7 @@ def test_ut_project_matches_oracle(oracle, deg, tile, view):
     assert np.all(rec[~vis_g][:, [0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 11]] == 0) and np.all(tc[~vis_g] == 0)
     # shader data against the oracle's quantities in the kernels' form
     want = _oracle_sd_in_kernel_form(pr, sc, cam)
-    np.testing.assert_allclose(sd[both, 0:2], want[both, 0:2], rtol=1e-5, atol=2e-3)
+    np.testing.assert_allclose(sd[both, 0:2], want[both, 0:2], rtol=1e-5, atol=2e-3 if not fish else 2e-6)
     for lo, hi in [(2, 5), (5, 8), (8, 11)]:
         err = np.linalg.norm(sd[both, lo:hi] - want[both, lo:hi], axis=1) / np.linalg.norm(want[both, lo:hi], axis=1)
         assert err.max() < 1e-4, (lo, err.max())
@@ -93,9 +100,10 @@ def test_ut_project_matches_oracle(oracle, deg, tile, view):
     np.testing.assert_array_equal(cnt, counts)
 
 
-@pytest.mark.parametrize("tile,W,H", [(16, 250, 170), (8, 250, 170), (16, 256, 256)])
-def test_ut_tile_lists_bit_exact(oracle, tile, W, H):
-    sc, cam, cfg, pr = _ut_case(oracle, 0, tile, n=12_345, W=W, H=H, big_every=97)
+@pytest.mark.parametrize("tile,W,H,fish", [(16, 250, 170, False), (8, 250, 170, False), (16, 256, 256, False),
+                                           (16, 250, 170, True)])
+def test_ut_tile_lists_bit_exact(oracle, tile, W, H, fish):
+    sc, cam, cfg, pr = _ut_case(oracle, 0, tile, n=12_345, W=W, H=H, big_every=97, fish=fish)
     fr = R.forward_frame(*R.scene_to_device(sc), cam, cfg)
     torch.cuda.synchronize()
     rec32 = fr.rec.cpu().numpy()
@@ -115,10 +123,13 @@ def _gpu_frame(sc, cam, cfg):
     return fr, fr.vals_sorted.cpu().numpy().view(np.uint32), fr.ranges.cpu().numpy()
 
 
-@pytest.mark.parametrize("tile,W,H,bg,deg", [(16, 256, 256, (0, 0, 0), 0), (8, 250, 170, (0.2, 0.5, 1.0), 3),
-                                             (16, 200, 120, (1, 1, 1), 1)])
-def test_ut_render_fwd_matches_oracle(oracle, tile, W, H, bg, deg):
-    sc, cam, cfg, pr = _ut_case(oracle, deg, tile, W=W, H=H, view=deg > 0)
+@pytest.mark.parametrize("tile,W,H,bg,deg,fish", [(16, 256, 256, (0, 0, 0), 0, False),
+                                                  (8, 250, 170, (0.2, 0.5, 1.0), 3, False),
+                                                  (16, 200, 120, (1, 1, 1), 1, False),
+                                                  (16, 256, 256, (0, 0, 0), 0, True),
+                                                  (8, 250, 170, (0.2, 0.5, 1.0), 3, True)])
+def test_ut_render_fwd_matches_oracle(oracle, tile, W, H, bg, deg, fish):
+    sc, cam, cfg, pr = _ut_case(oracle, deg, tile, W=W, H=H, view=deg > 0, fish=fish)
     cfg.bg = bg
     fr, sv, ranges = _gpu_frame(sc, cam, cfg)
     ref = oracle.render_tiles_ut(pr["rec"], pr["sd"], sv, ranges, cam, cfg, delta=BAND)
@@ -131,9 +142,9 @@ def test_ut_render_fwd_matches_oracle(oracle, tile, W, H, bg, deg):
     assert (ref["t_final"] < 0.01).mean() > 0.02  # saturated pixels: early termination exercised
 
 
-@pytest.mark.parametrize("deg,view,tile", [(0, False, 16), (3, True, 8)])
-def test_ut_gradients_match_oracle(oracle, deg, view, tile):
-    sc, cam, cfg, pr = _ut_case(oracle, deg, tile, view, n=6000)
+@pytest.mark.parametrize("deg,view,tile,fish", [(0, False, 16, False), (3, True, 8, False), (1, True, 16, True)])
+def test_ut_gradients_match_oracle(oracle, deg, view, tile, fish):
+    sc, cam, cfg, pr = _ut_case(oracle, deg, tile, view, n=6000, fish=fish)
     cfg.bg = (0.3, 0.1, 0.6)
     fr, sv, ranges = _gpu_frame(sc, cam, cfg)
     ref = oracle.render_tiles_ut(pr["rec"], pr["sd"], sv, ranges, cam, cfg, delta=BAND)
@@ -162,6 +173,15 @@ def test_ut_autograd_matches_direct_calls():
     for p, g in zip(params, direct):
         assert torch.isfinite(p.grad).all()
         assert rel_err(p.grad.cpu().numpy(), g.cpu().numpy()) < 1e-5
+
+
+def test_fisheye_needs_3dgut():
+    sc = scenes.uniform_scene(100, seed=1)
+    t = R.scene_to_device(sc)
+    cam = scenes.fisheye(64, 64, 32.0)
+    with pytest.raises(B.XprError):  # the EWA projection linearises a pinhole
+        B.xpr_project(*t, cam, scenes.RenderConfig(method=0))
+    B.xpr_project_ut(*t, cam, scenes.RenderConfig(method=1))
 
 
 def test_ut_method_is_checked():
