@@ -249,10 +249,10 @@ def batched_leg(dev, reps, flush, method=0):
             "timing": f"median of {reps} (L2 flushed before each)"}
 
 
-def ut_leg(dev, n, reps, flush):
-    """3DGUT form: the headline scene (1M clustered SH-3 Gaussians, 1920x1080 pinhole) with the
-    unscented projection, ray-offset binning and ray-evaluated compositing, forward + backward
-    through the autograd Function."""
+def ut_leg(dev, n, reps, flush, fisheye=False):
+    """3DGUT form: the headline scene (1M clustered SH-3 Gaussians, 1920x1080 pinhole, or the fisheye
+    of the 3DGUT configuration with the same focal length) with the unscented projection, ray-offset
+    binning and ray-evaluated compositing, forward + backward through the autograd Function."""
     import dataclasses
     import numpy as np
     import torch
@@ -260,6 +260,8 @@ def ut_leg(dev, n, reps, flush):
     from paper_2606_11529_gb300 import scenes
     sc, cam, cfg = scenes.headline_case(n)
     cfg = dataclasses.replace(cfg, method=1)
+    if fisheye:
+        cam = scenes.fisheye(cam.width, cam.height, cam.fx, scenes.FISHEYE_DIST)
     P = [t.to(dev).requires_grad_(True) for t in R.scene_to_device(sc)]
     w = torch.from_numpy(np.random.default_rng(1).normal(size=(3, cam.height, cam.width)).astype(np.float32)).to(dev)
     ws = R.Workspace()
@@ -286,8 +288,9 @@ def ut_leg(dev, n, reps, flush):
         ach = pairs * ops / (st[name] * 1e-3)
         roof[name] = {"kernel": f"ut_{name}_kernel<16,16>", "bound": "alu", "achieved_tops": round(ach / 1e12, 3),
                       "frac": round(ach / alu, 4)}
-    return {"workload": "3DGUT fwd+bwd, the headline scene (1M SH-3 Gaussians clustered, 1920x1080 pinhole "
-                        "f=1920, 16x16 tiles, seed 0), unscented projection with 7 sigma points",
+    lens = "fisheye f=1920 (k = 0.05, -0.01, 0.001, 0)" if fisheye else "pinhole f=1920"
+    return {"workload": f"3DGUT fwd+bwd, the headline scene (1M SH-3 Gaussians clustered, 1920x1080 {lens}, "
+                        "16x16 tiles, seed 0), unscented projection with 7 sigma points",
             "ms_per_iter": round(ms, 4), "stages_ms": {k: round(v, 4) for k, v in st.items()},
             "intersections": fr.n_isect, "pairs_blended": pairs, "render_roofline": roof,
             "timing": f"median of {reps} (L2 flushed before each)"}
@@ -442,6 +445,9 @@ def main():
                     help="run only the 3DGUT leg and print it as its own JSON line (for profiling captures)")
     ap.add_argument("--no-lp", action="store_true", help="skip the LinPrim leg")
     ap.add_argument("--no-feat", action="store_true", help="skip the rendered-features leg")
+    ap.add_argument("--feat-only", action="store_true",
+                    help="run only the rendered-features leg and print it as its own JSON line (for profiling)")
+    ap.add_argument("--ut-fisheye", action="store_true", help="with --ut-only: render through the fisheye camera")
     ap.add_argument("--lp-only", action="store_true",
                     help="run only the LinPrim leg and print it as its own JSON line (for profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -469,12 +475,14 @@ def main():
     dev = torch.device("cuda", local)
     L = B.load()
 
-    if args.ut_only or args.lp_only:
+    if args.ut_only or args.lp_only or args.feat_only:
         flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
         if args.ut_only:
-            out = {"leg": "3dgut", "ut": ut_leg(dev, args.n, max(args.steps, 1), flush)}
-        else:
+            out = {"leg": "3dgut", "ut": ut_leg(dev, args.n, max(args.steps, 1), flush, fisheye=args.ut_fisheye)}
+        elif args.lp_only:
             out = {"leg": "linprim", "linprim": lp_leg(dev, max(args.steps, 1), flush)}
+        else:
+            out = {"leg": "features", "features": feat_leg(dev, args.n, max(args.steps, 1), flush)}
         if rank == 0:
             print(json.dumps(out))
         return 0
