@@ -489,6 +489,16 @@ const char *xpr_last_error(void); /* message of the last failing call on this ho
 int xpr_version(void);
 /* Number of kernels this library has launched in the process so far (all threads). */
 unsigned long long xpr_launch_count(void);
+/* xpr_device_check: synchronises the current device, then reads and clears the
+ * error flags that the library's kernels record there instead of faulting.
+ * The sort's chained scan (xpr_sort, xpr_sort_tiles, xpr_depth_order and the
+ * entries built on them) waits on words that earlier blocks publish; each wait
+ * is bounded, and a wait that gives up sets the timeout flag.  A published word
+ * that cannot be right, or an output position outside the buffer (the write is
+ * skipped), sets the consistency flag.  Returns XPR_OK when neither flag was
+ * set since the last call, else XPR_ERR_TIMEOUT or XPR_ERR_INTERNAL (the
+ * results of the calls in between are then unreliable). */
+int xpr_device_check(void);
 
 #ifdef __cplusplus
 }

@@ -122,6 +122,7 @@ SIGNATURES = {
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
     "xpr_launch_count": (ctypes.c_ulonglong, []),
+    "xpr_device_check": (c_i32, []),
 }
 
 _lib = None
@@ -159,6 +160,12 @@ def _check(status: int, fn: str):
     if status != XPR_OK:
         msg = load().xpr_last_error().decode(errors="replace")
         raise XprError(status, fn, msg)
+
+
+def xpr_device_check():
+    """Synchronises the device and raises XprError if a kernel recorded a timed-out wait or an
+    inconsistent intermediate since the last check (the flags are cleared)."""
+    _check(load().xpr_device_check(), "xpr_device_check")
 
 
 def _ptr(t):

@@ -86,6 +86,15 @@ unsigned long long xpr_launch_count(void) { return g_launches.load(std::memory_o
 
 const char *xpr_last_error(void) { return g_err; }
 
+int xpr_device_check(void) {
+    unsigned bits = 0;
+    const int s = sort_device_errors(&bits);
+    if (s != XPR_OK) return s;
+    if (bits & 1u) return fail(XPR_ERR_TIMEOUT, "sort: a look-back wait gave up (flags %u)", bits);
+    if (bits & 2u) return fail(XPR_ERR_INTERNAL, "sort: inconsistent chained-scan word or output position");
+    return XPR_OK;
+}
+
 const char *xpr_status_string(int s) {
     switch (s) {
         case XPR_OK: return "ok";

@@ -144,8 +144,11 @@ def test_sort_tiles_of_depth_ordered_pairs_bit_exact(oracle, tile):
     np.testing.assert_array_equal(rg.cpu().numpy(), ranges)
 
 
-@pytest.mark.parametrize("n,n_tiles", [(1, 1), (2047, 256), (2049, 8160), (100_003, 5000), (300_000, 65536)])
+@pytest.mark.parametrize("n,n_tiles", [(1, 1), (2047, 256), (2049, 8160), (100_003, 5000), (300_000, 65536),
+                                       (5000, 2), (9000, 5), (20_000, 16), (70_000, 31), (70_000, 64),
+                                       (70_000, 100), (50_000, 3000), (10_000, (1 << 20) + 3)])
 def test_sort_tiles_random_stable(oracle, n, n_tiles):
+    # every digit width of a pass (1 .. 8 bits) and one to three passes
     rng = np.random.default_rng(n + 1)
     tiles = rng.integers(0, n_tiles, size=n).astype(np.uint32)
     vals = rng.permutation(n).astype(np.uint32)
@@ -195,6 +198,35 @@ def test_sort_random_keys_stable(oracle, n, n_tiles):
     np.testing.assert_array_equal(host_u32(vs), vals[order])
     _, _, ranges = oracle.sort_pairs(keys, np.arange(n, dtype=np.uint32), n_tiles)
     np.testing.assert_array_equal(rg.cpu().numpy(), ranges)
+
+
+@pytest.mark.parametrize("n", [2_500_003, 9_000_001])
+@pytest.mark.parametrize("skew", ["one_tile", "two_tiles", "runs"])
+def test_sort_tiles_many_blocks_skewed(skew, n):
+    # 2.5M keys (over 600 blocks of the chained scan) and 9M keys (past the chained scan's limit:
+    # the reduce-then-scan offsets): one tile only (every block's count of all but one digit is
+    # zero), two interleaved tiles, and long runs of equal tiles with a ragged tail
+    n_tiles = 8160
+    rng = np.random.default_rng(11)
+    if skew == "one_tile":
+        tiles = np.full(n, 4097, np.uint32)
+    elif skew == "two_tiles":
+        tiles = np.where(rng.random(n) < 0.5, 3, 8159).astype(np.uint32)
+    else:
+        tiles = np.repeat(rng.integers(0, n_tiles, size=n // 1000 + 1), 1000)[:n].astype(np.uint32)
+    vals = np.arange(n, dtype=np.uint32)
+    order = np.argsort(tiles, kind="stable")
+    ts, vs, rg = B.xpr_sort_tiles(dev_i32(tiles), dev_i32(vals), n_tiles)
+    np.testing.assert_array_equal(host_u32(ts), tiles[order])
+    np.testing.assert_array_equal(host_u32(vs), vals[order])
+    counts = np.bincount(tiles, minlength=n_tiles)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    r = rg.cpu().numpy()
+    nz = counts > 0
+    np.testing.assert_array_equal(r[nz, 0], starts[nz])
+    np.testing.assert_array_equal(r[nz, 1], starts[nz] + counts[nz])
+    assert np.all(r[~nz] == 0)
+    B.xpr_device_check()
 
 
 def test_sort_empty():
