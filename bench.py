@@ -37,12 +37,15 @@ SH_FLOATS = 48
 PARAM_BYTES = 4 * (3 + 3 + 4 + 1 + SH_FLOATS)  # 236 B per primitive
 REC_BYTES = 48
 FWD_OPS_PER_PAIR = 16   # FP32-pipe operations per (pixel, entry) pair of the forward walk
-BWD_OPS_PER_PAIR = 45   # FP32-pipe operations per (pixel, entry) pair of the adjoint walk
+# FP32-pipe operations per (pixel, entry) pair of the adjoint walk, counted on a contributing
+# unclamped pair; the colour behind a pixel enters as one scalar (its dot with the loss weight), 6
+# operations fewer than carrying the 3-vector
+BWD_OPS_PER_PAIR = 39
 # stages that are one kernel launch (the render adjoint's bracket also holds the zero-fill of d_rec)
 SINGLE_KERNEL = {"project": "project_fwd_kernel<3>", "render_fwd": "render_fwd_kernel<16,16>",
                  "render_bwd": "render_bwd_kernel<16,16>", "project_bwd": "project_bwd_kernel<3>"}
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel, and where it is
-TRAFFIC = {"render_bwd_kernel<16,16>": 45_115_392, "render_fwd_kernel<16,16>": 10_272_256}  # bytes
+TRAFFIC = {"render_bwd_kernel<16,16>": 45_106_432, "render_fwd_kernel<16,16>": 10_272_256}  # bytes
 TRAFFIC_SOURCE = {"render_bwd_kernel<16,16>": "profiles/render_bwd_headline.md",
                   "render_fwd_kernel<16,16>": "profiles/render_fwd_headline.md",
                   "project_bwd_kernel<3>": "profiles/project_bwd_headline.md",
@@ -50,10 +53,10 @@ TRAFFIC_SOURCE = {"render_bwd_kernel<16,16>": "profiles/render_bwd_headline.md",
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # 3DGUT ray evaluation: FP32-pipe operations per (pixel, entry) pair
 UT_FWD_OPS_PER_PAIR = 31
-UT_BWD_OPS_PER_PAIR = 72
+UT_BWD_OPS_PER_PAIR = 66
 # LinPrim slab intersection: FP32-pipe operations per (pixel, entry) pair
 LP_FWD_OPS_PER_PAIR = 39
-LP_BWD_OPS_PER_PAIR = 103
+LP_BWD_OPS_PER_PAIR = 97
 
 
 def peaks():

@@ -7,7 +7,9 @@
 //
 // Adjoint: the compositing adjoint over all channels, dL/dalpha_i = sum_ch g_ch (v_ich T_i -
 // S_ich / (1 - alpha_i)) with S the suffix sums recomputed back to front (colour channels start at
-// T_final bg, feature channels at 0), then through alpha as the colour-only adjoint; per entry the
+// T_final bg, feature channels at 0); S enters only through B = sum_ch g_ch S_ch, so each pixel
+// carries that scalar (B += (sum_ch g_ch v_ich) alpha_i T_i).  Then through alpha as the colour-only
+// adjoint; per entry the
 // 9 record partials and the NF feature partials are summed over the warp (32-lane reduce-scatter)
 // and the block, then added with atomics: d_rec in the record layout with the depth channel's
 // gradient in entry 9, and d_feat[n, n_feat].
@@ -190,7 +192,7 @@ __device__ __forceinline__ float reduce_scatter32f(const float *v, int lane) {
 
 template <int NF>
 struct FPixBwd {
-    float fy, T, g0, g1, g2, S0, S1, S2, gf[NF], Sf[NF];
+    float fy, T, g0, g1, g2, B, gf[NF];  // B = sum over channels of g . (value behind the entry)
     int last;
 };
 
@@ -206,22 +208,20 @@ __device__ __forceinline__ bool feat_adjoint(FPixBwd<NF> &P, float dx, const flo
     const float og = __fmul_rn(c.y, G);
     const float al = fminf(k.amax, og);
     if (al < k.at) return false;
-    const float inv = __frcp_rn(1.f - al);
+    const float inv = rcp_approx(1.f - al);
     const float Ti = P.T * inv;
     const float w = al * Ti;
     v[6] = fmaf(P.g0, w, v[6]);
     v[7] = fmaf(P.g1, w, v[7]);
     v[8] = fmaf(P.g2, w, v[8]);
-    float dal = P.g0 * (c.z * Ti - P.S0 * inv) + P.g1 * (c.w * Ti - P.S1 * inv) + P.g2 * (cb * Ti - P.S2 * inv);
+    float gc = fmaf(P.g0, c.z, fmaf(P.g1, c.w, P.g2 * cb));
 #pragma unroll
     for (int ch = 0; ch < NF; ++ch) {
-        dal = fmaf(P.gf[ch], f[ch] * Ti - P.Sf[ch] * inv, dal);
-        P.Sf[ch] = fmaf(f[ch], w, P.Sf[ch]);
+        gc = fmaf(P.gf[ch], f[ch], gc);
         v[9 + ch] = fmaf(P.gf[ch], w, v[9 + ch]);
     }
-    P.S0 = fmaf(c.z, w, P.S0);
-    P.S1 = fmaf(c.w, w, P.S1);
-    P.S2 = fmaf(cb, w, P.S2);
+    const float dal = fmaf(gc, Ti, -P.B * inv);
+    P.B = fmaf(gc, w, P.B);
     P.T = Ti;
     if (og < k.amax) {
         const float dp = dal * al;
@@ -271,10 +271,7 @@ __global__ void __launch_bounds__(TW *TH / feat_px<TW, TH, NF>()) render_feat_bw
         P[q].last = 0;
         P[q].g0 = P[q].g1 = P[q].g2 = 0.f;
 #pragma unroll
-        for (int ch = 0; ch < NF; ++ch) {
-            P[q].gf[ch] = (in && ch < nf) ? dfeat_img[ch * HW + pix] : 0.f;
-            P[q].Sf[ch] = 0.f;
-        }
+        for (int ch = 0; ch < NF; ++ch) P[q].gf[ch] = (in && ch < nf) ? dfeat_img[ch * HW + pix] : 0.f;
         if (in) {
             P[q].T = tfin[pix];
             P[q].last = ncon[pix];
@@ -282,9 +279,7 @@ __global__ void __launch_bounds__(TW *TH / feat_px<TW, TH, NF>()) render_feat_bw
             P[q].g1 = dimg[HW + pix];
             P[q].g2 = dimg[2 * HW + pix];
         }
-        P[q].S0 = P[q].T * k.bg0;
-        P[q].S1 = P[q].T * k.bg1;
-        P[q].S2 = P[q].T * k.bg2;
+        P[q].B = P[q].T * fmaf(P[q].g0, k.bg0, fmaf(P[q].g1, k.bg1, P[q].g2 * k.bg2));
         mylast = max(mylast, P[q].last);
     }
     const int wlast = __reduce_max_sync(kFullF, mylast);

@@ -545,7 +545,7 @@ __device__ __forceinline__ float reduce_scatter32(const float *v, int lane) {
 }
 
 struct LpPixBwd {
-    float cy, T, g0, g1, g2, S0, S1, S2;
+    float cy, T, g0, g1, g2, B;  // B = g . (colour behind the current entry)
     int last;
 };
 
@@ -562,17 +562,15 @@ __device__ __forceinline__ bool lp_adjoint(LpPixBwd &P, float cx, const float4 &
     const float a0 = __fsub_rn(1.f, e);
     const float al = fminf(k.amax, a0);
     if (al < k.at) return false;
-    const float inv = __frcp_rn(1.f - al);
+    const float inv = rcp_approx(1.f - al);
     const float Ti = P.T * inv;
     const float w = al * Ti;
     v[17] = fmaf(P.g0, w, v[17]);
     v[18] = fmaf(P.g1, w, v[18]);
     v[19] = fmaf(P.g2, w, v[19]);
-    const float dal = P.g0 * (u4.x * Ti - P.S0 * inv) + P.g1 * (u4.y * Ti - P.S1 * inv) +
-                      P.g2 * (u4.z * Ti - P.S2 * inv);
-    P.S0 = fmaf(u4.x, w, P.S0);
-    P.S1 = fmaf(u4.y, w, P.S1);
-    P.S2 = fmaf(u4.z, w, P.S2);
+    const float gc = fmaf(P.g0, u4.x, fmaf(P.g1, u4.y, P.g2 * u4.z));
+    const float dal = fmaf(gc, Ti, -P.B * inv);
+    P.B = fmaf(gc, w, P.B);
     P.T = Ti;
     if (a0 < k.amax) {
         v[16] = fmaf(dal * ev.dt, e, v[16]);
@@ -615,7 +613,7 @@ __device__ __forceinline__ void lp_bwd_tile(int gt, const float *__restrict__ sd
         const int y = py + q * RS;
         const bool in = px < k.W && y < k.H;
         const int64_t pix = (int64_t)y * k.W + px;
-        P[q] = LpPixBwd{(float)y + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        P[q] = LpPixBwd{(float)y + 0.5f, 1.f, 0.f, 0.f, 0.f, 0.f, 0};
         if (in) {
             P[q].T = tf[pix];
             P[q].last = nc[pix];
@@ -623,9 +621,7 @@ __device__ __forceinline__ void lp_bwd_tile(int gt, const float *__restrict__ sd
             P[q].g1 = di[HW + pix];
             P[q].g2 = di[2 * HW + pix];
         }
-        P[q].S0 = P[q].T * k.bg0;
-        P[q].S1 = P[q].T * k.bg1;
-        P[q].S2 = P[q].T * k.bg2;
+        P[q].B = P[q].T * fmaf(P[q].g0, k.bg0, fmaf(P[q].g1, k.bg1, P[q].g2 * k.bg2));
         mylast = max(mylast, P[q].last);
     }
     const int wlast = __reduce_max_sync(kFullLp, mylast);

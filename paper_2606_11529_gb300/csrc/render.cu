@@ -13,6 +13,7 @@
 // Backward (K5): the same blocks re-walk the list back to front from each pixel's n_contrib,
 // recomputing T_i = T_{i+1} / (1 - alpha_i) and the colour behind, S (starting at T_final bg):
 //   dL/dc_i = g alpha_i T_i,   dL/dalpha_i = g . (c_i T_i - S_i / (1 - alpha_i))
+// S enters only through g . S, so each pixel carries that scalar, B (B += (g . c_i) alpha_i T_i).
 // then through alpha = o exp(power) (zero through the clamp) to o, mu_2D and the conic.  The 9
 // per-pixel partial gradients of one entry are summed over the thread's four pixels, over the
 // warp with shuffles, over the block in shared memory, and added to global memory with one set
@@ -205,7 +206,7 @@ __device__ __forceinline__ float reduce_scatter8(const float *v, int lane) {
 }
 
 struct PixelBwd {
-    float fy, T, g0, g1, g2, S0, S1, S2;
+    float fy, T, g0, g1, g2, B;  // B = g . (colour behind the current entry)
     int last;
 };
 
@@ -221,16 +222,15 @@ __device__ __forceinline__ bool adjoint(PixelBwd &P, float dx, const float4 &g, 
     const float og = __fmul_rn(c.y, G);
     const float al = fminf(k.amax, og);
     if (al < k.at) return false;
-    const float inv = __frcp_rn(1.f - al);
+    const float inv = rcp_approx(1.f - al);
     const float Ti = P.T * inv;
     const float w = al * Ti;
     v[6] = fmaf(P.g0, w, v[6]);
     v[7] = fmaf(P.g1, w, v[7]);
     v[8] = fmaf(P.g2, w, v[8]);
-    const float dal = P.g0 * (c.z * Ti - P.S0 * inv) + P.g1 * (c.w * Ti - P.S1 * inv) + P.g2 * (cb * Ti - P.S2 * inv);
-    P.S0 = fmaf(c.z, w, P.S0);
-    P.S1 = fmaf(c.w, w, P.S1);
-    P.S2 = fmaf(cb, w, P.S2);
+    const float gc = fmaf(P.g0, c.z, fmaf(P.g1, c.w, P.g2 * cb));
+    const float dal = fmaf(gc, Ti, -P.B * inv);
+    P.B = fmaf(gc, w, P.B);
     P.T = Ti;
     if (og < k.amax) {
         const float dp = dal * al;  // dL/dpower (natural log units)
@@ -247,7 +247,7 @@ __device__ __forceinline__ bool adjoint(PixelBwd &P, float dx, const float4 &g, 
 __device__ __forceinline__ PixelBwd load_pixel_bwd(bool inside, float fy, int64_t pix, int64_t HW,
                                                    const float *__restrict__ tfin, const int *__restrict__ ncon,
                                                    const float *__restrict__ dimg, const Consts &k) {
-    PixelBwd P = {fy, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+    PixelBwd P = {fy, 1.f, 0.f, 0.f, 0.f, 0.f, 0};
     if (inside) {
         P.T = tfin[pix];
         P.last = ncon[pix];
@@ -255,9 +255,7 @@ __device__ __forceinline__ PixelBwd load_pixel_bwd(bool inside, float fy, int64_
         P.g1 = dimg[HW + pix];
         P.g2 = dimg[2 * HW + pix];
     }
-    P.S0 = P.T * k.bg0;
-    P.S1 = P.T * k.bg1;
-    P.S2 = P.T * k.bg2;
+    P.B = P.T * fmaf(P.g0, k.bg0, fmaf(P.g1, k.bg1, P.g2 * k.bg2));
     return P;
 }
 

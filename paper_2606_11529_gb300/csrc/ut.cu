@@ -706,7 +706,7 @@ __device__ __forceinline__ float reduce_scatter16(const float *v, int lane) {
 }
 
 struct UtPixBwd {
-    float cx, cy, T, g0, g1, g2, S0, S1, S2;
+    float cx, cy, T, g0, g1, g2, B;  // B = g . (colour behind the current entry)
     int last;
 };
 
@@ -722,17 +722,15 @@ __device__ __forceinline__ bool ut_adjoint(UtPixBwd &P, float cx, const float4 &
     const float og = __fmul_rn(u2.w, G);
     const float al = fminf(k.amax, og);
     if (al < k.at) return false;
-    const float inv = __frcp_rn(1.f - al);
+    const float inv = rcp_approx(1.f - al);
     const float Ti = P.T * inv;
     const float w = al * Ti;
     v[13] = fmaf(P.g0, w, v[13]);
     v[14] = fmaf(P.g1, w, v[14]);
     v[15] = fmaf(P.g2, w, v[15]);
-    const float dal = P.g0 * (u3.x * Ti - P.S0 * inv) + P.g1 * (u3.y * Ti - P.S1 * inv) +
-                      P.g2 * (u3.z * Ti - P.S2 * inv);
-    P.S0 = fmaf(u3.x, w, P.S0);
-    P.S1 = fmaf(u3.y, w, P.S1);
-    P.S2 = fmaf(u3.z, w, P.S2);
+    const float gc = fmaf(P.g0, u3.x, fmaf(P.g1, u3.y, P.g2 * u3.z));
+    const float dal = fmaf(gc, Ti, -P.B * inv);
+    P.B = fmaf(gc, w, P.B);
     P.T = Ti;
     if (og < k.amax) {
         v[12] = fmaf(dal, G, v[12]);
@@ -785,7 +783,7 @@ __device__ __forceinline__ void ut_bwd_tile(int gt, const float *__restrict__ sd
         const int y = py + q * RS;
         const bool in = px < k.W && y < k.H;
         const int64_t pix = (int64_t)y * k.W + px;
-        P[q] = UtPixBwd{0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0};
+        P[q] = UtPixBwd{0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 0};
         if (in && ut_pixel_coord<FISH>(k, px, y, P[q].cx, P[q].cy)) {
             P[q].T = tf[pix];
             P[q].last = nc[pix];
@@ -793,9 +791,7 @@ __device__ __forceinline__ void ut_bwd_tile(int gt, const float *__restrict__ sd
             P[q].g1 = di[HW + pix];
             P[q].g2 = di[2 * HW + pix];
         }
-        P[q].S0 = P[q].T * k.bg0;
-        P[q].S1 = P[q].T * k.bg1;
-        P[q].S2 = P[q].T * k.bg2;
+        P[q].B = P[q].T * fmaf(P[q].g0, k.bg0, fmaf(P[q].g1, k.bg1, P[q].g2 * k.bg2));
         mylast = max(mylast, P[q].last);
     }
     const int wlast = __reduce_max_sync(kFullUt, mylast);

@@ -157,6 +157,13 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// 1/x to about 1 ulp (the hardware reciprocal; x here is 1 - alpha in [1 - alpha_max, 1]).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Staged shading coefficients of one list entry (paper's p_sd with the conic pre-scaled
 // by log2(e) so that exp(power) = 2^(A dx^2 + B dx dy + C dy^2)).
 struct Shade {
