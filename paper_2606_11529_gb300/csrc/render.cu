@@ -36,6 +36,10 @@ __host__ __device__ constexpr int px_per_thread() {
     return (TW * TH) / 32 >= 4 ? 4 : (TW * TH) / 32;
 }
 constexpr int kMaxBatch = 256;  // largest shared-memory batch (entries)
+// The adjoint stages at most kBwdBatch entries: its 9 accumulator rows make a block's shared
+// memory grow 2.3x faster with the batch than the forward's, and at 256 entries shared memory
+// alone held an SM to 11 blocks.
+constexpr int kBwdBatch = 128;
 
 struct Consts {
     int W, H, Wt, T;  // image size, tiles per row, tiles per view
@@ -264,7 +268,7 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
                                          const int2 *__restrict__ ranges, const Consts &k,
                                          const float *__restrict__ tfin, const int *__restrict__ ncon,
                                          const float *__restrict__ dimg, float *__restrict__ d_rec, float4 *s_g,
-                                         float4 *s_c, float *s_b, uint32_t *s_id, float (*s_acc)[kMaxBatch + 1],
+                                         float4 *s_c, float *s_b, uint32_t *s_id, float (*s_acc)[kBwdBatch + 1],
                                          int *s_wmax) {
     constexpr int kPX = px_per_thread<TW, TH>();
     constexpr int NT = TW * TH / kPX;
@@ -357,12 +361,12 @@ __global__ void __launch_bounds__(TW *TH / px_per_thread<TW, TH>()) render_bwd_k
                                                                   const int *__restrict__ ncon,
                                                                   const float *__restrict__ dimg,
                                                                   float *__restrict__ d_rec, Work w) {
-    __shared__ float4 s_g[kMaxBatch];
-    __shared__ float4 s_c[kMaxBatch];
-    __shared__ float s_b[kMaxBatch];
-    __shared__ uint32_t s_id[kMaxBatch];
+    __shared__ float4 s_g[kBwdBatch];
+    __shared__ float4 s_c[kBwdBatch];
+    __shared__ float s_b[kBwdBatch];
+    __shared__ uint32_t s_id[kBwdBatch];
     // rows padded by one float: the 8 lanes adding one entry's values hit 8 different banks
-    __shared__ float s_acc[9][kMaxBatch + 1];
+    __shared__ float s_acc[9][kBwdBatch + 1];
     __shared__ int s_wmax[8];
     if (w.list == nullptr) {
         bwd_tile<TW, TH>(blockIdx.x, rec, vals, ranges, k, tfin, ncon, dimg, d_rec, s_g, s_c, s_b, s_id, s_acc,
@@ -441,7 +445,8 @@ int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_
                             const int32_t *n_contrib, const float *d_image, float *d_rec, int64_t n,
                             const int32_t *worklist, int32_t *counter, cudaStream_t st) {
     XPR_CUDA_TRY(cudaMemsetAsync(d_rec, 0, (size_t)n * XPR_REC_FLOATS * sizeof(float), st));
-    const Consts k = make_consts(cam, cfg, n);
+    Consts k = make_consts(cam, cfg, n);
+    k.batch = min(k.batch, kBwdBatch);
     const int items = n_views * k.T;
     if (items == 0) return XPR_OK;
     const int2 *rg = reinterpret_cast<const int2 *>(ranges);
