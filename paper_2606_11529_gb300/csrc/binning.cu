@@ -54,9 +54,10 @@ __device__ __forceinline__ void put_pair(uint64_t *keys, uint32_t *tiles, uint32
 // [offsets[j], offsets[j+1]) in slot order (the box's rows in order, each row's kept span in
 // order).  The tile rows of the warp's 32 boxes are spread over the lanes 32 at a time: each lane
 // finds its row's kept span (cull.cuh), a warp scan of the span lengths places the rows (each
-// position keeps a running output cursor across steps), and the warp writes the step's pairs 32
-// at a time, a lane finding the row of its pair by a binary search over the scanned lengths, so a
-// row's pairs are written by consecutive lanes to consecutive addresses.
+// position keeps a running output cursor across steps), the non-empty rows are compacted into the
+// warp's shared memory, and the warp writes the step's pairs 32 at a time, a lane finding the row
+// of its pair from one OR-reduction of the rows' end offsets, so a row's pairs are written by
+// consecutive lanes to consecutive addresses.
 // keys (u64 tile << 32 | depth bits) and tiles (u32 tile id) are each written when non-NULL.
 // Records of a multi-view launch are view-major (record i belongs to view i div per_view) and the
 // tile id of a pair is offset by view * tiles_per_view (per_view = 0: a single view).
@@ -67,7 +68,12 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
                                                        const int32_t *__restrict__ offsets,
                                                        uint64_t *__restrict__ keys, uint32_t *__restrict__ tiles,
                                                        uint32_t *__restrict__ vals) {
+    __shared__ int4 s_rows[8][32];  // per warp: the compacted rows of the current step
+    __shared__ uint32_t s_dbs[8][32];
     const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int4 *s_row = s_rows[threadIdx.x >> 5];
+    uint32_t *s_db = s_dbs[threadIdx.x >> 5];
     const int64_t nw = (n + 31) / 32;
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= nw) return;
@@ -106,21 +112,34 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
         const int first = max(excl_p - f0, 0);  // lane of the position's first row in this step
         const int out_row = __shfl_sync(kFullMask, cursor, p) + cx - __shfl_sync(kFullMask, cx, first);
         const int total = __shfl_sync(kFullMask, ci, 31);
-        for (int k0 = 0; k0 < total; k0 += 32) {
-            const int k = k0 + lane;
-            const int r = lane_of(ci, k);
-            const int ka_r = __shfl_sync(kFullMask, ka, r);
-            const int in_r = k - __shfl_sync(kFullMask, cx, r);
-            const int ty_r = __shfl_sync(kFullMask, ty, r);
-            const int o_r = __shfl_sync(kFullMask, out_row, r);
-            const int p_r = __shfl_sync(kFullMask, p, r);
-            const int i_r = __shfl_sync(kFullMask, i, p_r);
-            const uint32_t tb = __shfl_sync(kFullMask, tbase, p_r);
-            const uint32_t db = __shfl_sync(kFullMask, depth_bits, p_r);
-            if (k < total)
-                put_pair(keys, tiles, vals, (int64_t)o_r + in_r, tb + (uint32_t)(ty_r * g.Wt + ka_r + in_r), db,
-                         (uint32_t)i_r);
+        const int i_p = __shfl_sync(kFullMask, i, p);
+        const uint32_t tb_p = __shfl_sync(kFullMask, tbase, p);
+        const uint32_t db_p = __shfl_sync(kFullMask, depth_bits, p);
+        // the step's non-empty rows, compacted in row order: first tile, first output slot,
+        // primitive, index of the row's first pair in the step
+        const unsigned nonempty = __ballot_sync(kFullMask, c > 0);
+        if (c > 0) {
+            const int slot = __popc(nonempty & lt_mask);
+            s_row[slot] = make_int4((int)(tb_p + (uint32_t)(ty * g.Wt + ka)), out_row, i_p, cx);
+            s_db[slot] = db_p;
         }
+        __syncwarp();
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            // pair k lies in the non-empty row whose index is the number of non-empty rows ending
+            // at or before k: those ended before this chunk, plus those whose end (one bit each:
+            // non-empty rows end at distinct places) falls below this lane
+            const int k = k0 + lane;
+            const int e = ci - k0;
+            const unsigned ends = __reduce_or_sync(kFullMask, (c > 0 && e > 0 && e <= 32) ? 1u << (e - 1) : 0u);
+            const int row = __popc(__ballot_sync(kFullMask, c > 0 && e <= 0)) + __popc(ends & lt_mask);
+            if (k < total) {
+                const int4 rr = s_row[row];
+                const int in_r = k - rr.w;
+                put_pair(keys, tiles, vals, (int64_t)rr.y + in_r, (uint32_t)(rr.x + in_r), keys ? s_db[row] : 0u,
+                         (uint32_t)rr.z);
+            }
+        }
+        __syncwarp();  // the next step rewrites this warp's rows
         // advance each position's cursor by its rows' pairs in this step
         const int lo = max(excl - f0, 0), hi = min(incl - 1 - f0, 31);
         const int s_hi = __shfl_sync(kFullMask, ci, max(hi, 0));
