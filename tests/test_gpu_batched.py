@@ -108,3 +108,95 @@ def test_views_reject_mixed_sizes():
     cams = [scenes.pinhole(64, 64, 64.0), scenes.pinhole(80, 64, 64.0)]
     with pytest.raises(ValueError):
         BT.forward_views(*R.scene_to_device(sc), cams, scenes.RenderConfig())
+
+
+A_T = float(np.float32(1 / 255))
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_config3_full_size_two_views_against_oracle(oracle, method):
+    """The batched workload at its full size in the persistent batched launch: 3M uniform SH-0
+    Gaussians, 8 views 1600x1064 f=800 (fisheye for 3DGUT), 16x16 tiles.  Two views against the
+    oracle: 3DGS on sampled pixels walked by brute force over all primitives, 3DGUT on sampled
+    tiles walked by the oracle over the GPU's lists; then the gradients of a loss on those pixels
+    of both views."""
+    sc = scenes.uniform_scene(3_000_000, seed=0)
+    cams = scenes.multiview_cameras(8, 1600, 1064, 800.0, seed=0,
+                                    fisheye_dist=scenes.FISHEYE_DIST if method == 1 else None)
+    cfg = scenes.RenderConfig(sh_degree=0, method=method)
+    views = (0, 5)
+    prs = None
+    if method == 1:
+        # drop primitives whose rescaled opacity sits at the opacity gate in a checked view
+        prs = [oracle.project_ut(*sc.arrays(), cams[v], cfg) for v in views]
+        keep = np.ones(sc.n, bool)
+        for pr in prs:
+            o = pr["sd"][:, 12]
+            keep &= ~((np.abs(o / A_T - 1.0) < 1e-3) & (o > 0))
+        idx = np.nonzero(keep)[0]
+        sc = sc.subset(idx)
+        prs = [{"rec": pr["rec"][idx], "sd": pr["sd"][idx]} for pr in prs]
+    P = [t.clone().requires_grad_(True) for t in R.scene_to_device(sc)]
+    imgs = BT.render_views(*P, cams, cfg)
+    torch.cuda.synchronize()
+    H, W = 1064, 1600
+    rng = np.random.default_rng(0)
+    w = np.zeros((8, 3, H, W))
+    g_ref = {name: 0.0 for name in NAMES}
+    if method == 0:
+        for v in views:
+            pr = oracle.project_scene(sc, cams[v], cfg)
+            pix = np.stack([rng.integers(0, W, 256), rng.integers(0, H, 256)], 1)
+            ref = oracle.render_pixels(pr["rec"], pix, cfg, delta=BAND, dz=1e-6)
+            got = imgs[v].detach().cpu().numpy()[:, pix[:, 1], pix[:, 0]].T
+            ok = ~ref["band"]
+            # a pixel of this dense uniform scene blends hundreds of primitives, so two successive
+            # contributors with depths within 1e-6 (whose order may differ between float32 and
+            # float64 depths) are common: about 40% of the sampled pixels are set aside for that
+            assert ok.mean() > 0.5
+            assert np.abs(got[ok] - ref["color"][ok]).max() <= IMG_TOL, v
+            assert (ref["t_final"] < 0.5).mean() > 0.2  # sampled pixels are not mostly empty
+            use = pix[ok][:96]
+            w[v][:, use[:, 1], use[:, 0]] = rng.normal(size=(3, len(use)))
+            g = oracle.project_bwd(*sc.arrays(), cams[v], cfg, oracle.render_bwd_brute(pr["rec"], cams[v], cfg, w[v]))
+            for name in NAMES:
+                g_ref[name] = g_ref[name] + g[name]
+    else:
+        fr = BT.forward_views(*[p.detach() for p in P], cams, cfg)
+        Wt, Ht = (W + 15) // 16, (H + 15) // 16
+        T = Wt * Ht
+        ranges = fr.ranges.cpu().numpy()
+        sv = fr.vals_sorted.cpu().numpy().view(np.uint32).astype(np.int64)
+        for v, pr in zip(views, prs):
+            rv = ranges[v * T:(v + 1) * T]
+            lengths = rv[:, 1] - rv[:, 0]
+            busy = np.nonzero(lengths > np.percentile(lengths, 50))[0]
+            tiles = np.concatenate([rng.choice(busy, 12, replace=False), rng.choice(T, 3, replace=False)])
+            # the sampled tiles' lists, with the records renumbered within the view
+            sub = np.zeros((T, 2), np.int32)
+            parts, at = [], 0
+            for t in tiles:
+                seg = sv[rv[t, 0]:rv[t, 1]] - v * sc.n
+                assert seg.size == 0 or (seg.min() >= 0 and seg.max() < sc.n)
+                sub[t] = (at, at + seg.size)
+                parts.append(seg)
+                at += seg.size
+            vals_v = np.concatenate(parts).astype(np.uint32) if at else np.zeros(0, np.uint32)
+            ref = oracle.render_tiles_ut(pr["rec"], pr["sd"], vals_v, sub, cams[v], cfg, delta=BAND)
+            mask = np.zeros((H, W), bool)
+            for t in tiles:
+                ty, tx = divmod(int(t), Wt)
+                mask[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
+            ok = mask & ~ref["band"]
+            assert ok.sum() > 0.97 * mask.sum()
+            got = imgs[v].detach().cpu().numpy()
+            assert np.abs(got[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL, v
+            assert (ref["t_final"][ok] < 0.5).mean() > 0.2
+            w[v] = rng.normal(size=(3, H, W)) * ok[None]
+            d_sd = oracle.render_bwd_tiles_ut(pr["sd"], vals_v, sub, cams[v], cfg, w[v])
+            g = oracle.project_ut_bwd(*sc.arrays(), cams[v], cfg, d_sd)
+            for name in NAMES:
+                g_ref[name] = g_ref[name] + g[name]
+    (imgs * dev(w)).sum().backward()
+    for name, p in zip(NAMES, P):
+        assert rel_err(p.grad.cpu().numpy(), g_ref[name]) < GRAD_TOL, name
