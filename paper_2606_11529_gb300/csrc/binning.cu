@@ -326,14 +326,14 @@ int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *
     const size_t a = ((size_t)n * 8 + 255) / 256 * 256, b = ((size_t)n * 4 + 255) / 256 * 256;
     char *p = reinterpret_cast<char *>(ws);
     uint64_t *keys = reinterpret_cast<uint64_t *>(p);
-    uint64_t *keys_sorted = reinterpret_cast<uint64_t *>(p + a);
     uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
-    int32_t *ranges = reinterpret_cast<int32_t *>(p + 2 * a + b);  // n_views int2 (unused by the caller)
     void *sort_ws = p + 2 * a + b + 256;
     depth_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, tc, n, per_view, keys, vals);
     XPR_LAUNCH_CHECK("depth_key_kernel");
-    // the sort's "tile" is the view: keys (view << 32 | depth bits) sort over 32 + ceil(log2 views) bits
-    return launch_sort(keys, vals, n, n_views, 0, keys_sorted, reinterpret_cast<uint32_t *>(order), ranges, sort_ws,
+    // the sort's "tile" is the view: keys (view << 32 | depth bits) sort over 32 + ceil(log2 views) bits;
+    // only the order is wanted (no sorted keys, which lets the sort use `keys` as scratch, and no
+    // per-view ranges)
+    return launch_sort(keys, vals, n, n_views, 0, nullptr, reinterpret_cast<uint32_t *>(order), nullptr, sort_ws,
                        sort_workspace_bytes(n, n_views), st);
 }
 

@@ -685,11 +685,12 @@ int launch_chained_bits(int nbits, A... a) {
     }
 }
 
-// Sorts (kin, vin) by key bits [begin_bit, end_bit) into (kout, vout), then finds tile ranges.
+// Sorts (kin, vin) by key bits [begin_bit, end_bit) into (kout, vout), then finds tile ranges
+// (ranges NULL: none are wanted).
 template <typename K>
 int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit, int end_bit,
                K *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {
-    XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(int32_t), st));
+    if (ranges) XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(int32_t), st));
     if (n == 0) return XPR_OK;
     if (n > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "sort: more than 2^31 - 1 keys");
     if (ws_bytes < workspace_bytes<K>(n))
@@ -719,6 +720,7 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
             XPR_CUDA_TRY(cudaMemcpyAsync(keys_out, keys_in, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, st));
         XPR_CUDA_TRY(cudaMemcpyAsync(vals_out, vals_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
         // nothing to sort by (a single tile): one pass over the keys finds the bounds
+        if (!rg) return XPR_OK;
         const int64_t nthreads = (n + kRangeItems - 1) / kRangeItems;
         tile_ranges_kernel<K><<<(unsigned)((nthreads + 255) / 256), 256, 0, st>>>(
             keys_in, n, (uint32_t)n_tiles, rg, is_aligned16(keys_in));
@@ -726,8 +728,10 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
         return XPR_OK;
     }
     const unsigned tgrid = (unsigned)((n_tiles + 255) / 256);
-    init_ranges_kernel<<<tgrid, 256, 0, st>>>(rg, n_tiles);
-    XPR_LAUNCH_CHECK("init_ranges_kernel");
+    if (rg) {
+        init_ranges_kernel<<<tgrid, 256, 0, st>>>(rg, n_tiles);
+        XPR_LAUNCH_CHECK("init_ranges_kernel");
+    }
     if (chained) {
         int dev = 0, sms = 0;
         XPR_CUDA_TRY(cudaGetDevice(&dev));
@@ -782,8 +786,10 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
         src_k = dst_k;
         src_v = dst_v;
     }
-    fix_empty_ranges_kernel<<<tgrid, 256, 0, st>>>(rg, n_tiles);
-    XPR_LAUNCH_CHECK("fix_empty_ranges_kernel");
+    if (rg) {
+        fix_empty_ranges_kernel<<<tgrid, 256, 0, st>>>(rg, n_tiles);
+        XPR_LAUNCH_CHECK("fix_empty_ranges_kernel");
+    }
     return XPR_OK;
 }
 
