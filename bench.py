@@ -595,14 +595,12 @@ def main():
     e2e_e = torch.cuda.Event(enable_timing=True)
     h2d = sum(h.numel() * h.element_size() for h in host)
     up = R.Uploader()
-    dst = [p.detach() for p in P]
 
     def upload_inputs():
-        # geometry first (the projection waits for it), then the SH coefficients, which the forward
-        # needs only for the colours after binning and sorting
-        ev_geo = up.start(dst[:4], host[:4])
-        torch.cuda.current_stream().wait_event(ev_geo)
-        ws.sh_events = up.start(dst[4:], host[4:], after=(ev_geo,))
+        # the forward brings the inputs over itself: the projection reads the geometry from pinned
+        # host memory and writes its device copy in the same pass, then the SH coefficients are
+        # copied under the depth order, binning and sort (the colours are needed only after them)
+        ws.host_inputs = (host, up.stream)
 
     upload_inputs()
     step()

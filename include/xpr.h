@@ -137,6 +137,21 @@ typedef struct XprPrimsGrad {
 int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,
                 int32_t *bbox, int32_t *tile_count, int32_t *isect_count, void *stream);
 
+/* xpr_project_host: xpr_project whose geometry (mu, scale, quat, opacity) is
+ * read straight from page-locked host memory (`host`: pointers of pinned
+ * allocations, which the device addresses through the host link), and which
+ * writes a copy of that geometry into the device arrays of `dst` in the same
+ * pass (later passes, e.g. xpr_project_bwd, read dst).  The projection then
+ * runs at the host link's bandwidth instead of after a separate copy.
+ * host->sh is ignored; dst->sh is a DEVICE pointer or NULL (colours left for
+ * xpr_project_color, as in xpr_project).  Every host pointer must lie in
+ * page-locked memory mapped for the device: otherwise XPR_ERR_INVALID and
+ * nothing is launched.  dst->quat, rec and bbox 16-byte aligned.  Outputs as
+ * xpr_project. */
+int xpr_project_host(const XprPrims *host, const XprPrims *dst, int64_t n, const XprCamera *cam,
+                     const XprConfig *cfg, float *rec, int32_t *bbox, int32_t *tile_count, int32_t *isect_count,
+                     void *stream);
+
 /* ---- Rasterizer: replicate, assign tile ID, cull --------------------------
  * xpr_depth_order: order[n] = the primitives with tile_count > 0 sorted by
  * (depth, index) ascending (float bits of camera z; stable), followed by the

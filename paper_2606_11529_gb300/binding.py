@@ -123,6 +123,8 @@ SIGNATURES = {
     "xpr_version": (ctypes.c_int, []),
     "xpr_launch_count": (ctypes.c_ulonglong, []),
     "xpr_device_check": (c_i32, []),
+    "xpr_project_host": (c_i32, [ctypes.POINTER(XprPrims), ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
+                                 ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp]),
 }
 
 _lib = None
@@ -243,6 +245,28 @@ def xpr_project(mu, scale, quat, opacity, sh, cam, cfg, rec=None, bbox=None, til
     c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
     _check(L.xpr_project(ctypes.byref(p), n, ctypes.byref(c), ctypes.byref(g), _ptr(rec), _ptr(bbox),
                          _ptr(tile_count), _ptr(isect_count), _stream(stream)), "xpr_project")
+    return (rec, bbox, tile_count) if isect_count is None else (rec, bbox, tile_count, isect_count)
+
+
+def xpr_project_host(host, dst, cam, cfg, stream=None, with_isect_count=False):
+    """xpr_project reading the geometry from pinned host tensors host = (mu, scale, quat, opacity)
+    and writing its copy into the device tensors dst = (mu, scale, quat, opacity, sh or None) in the
+    same pass.  Returns (rec, bbox, tile_count[, isect_count])."""
+    L = load()
+    n = dst[0].shape[0]
+    for t, d in zip(host, dst[:4]):
+        if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.shape != d.shape:
+            raise ValueError("host geometry must be contiguous float32 host tensors shaped like the device ones")
+    dev = dst[0].device
+    rec = torch.empty((n, REC), dtype=torch.float32, device=dev)
+    bbox = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    tile_count = torch.empty(n, dtype=torch.int32, device=dev)
+    isect_count = torch.empty(n, dtype=torch.int32, device=dev) if with_isect_count else None
+    hp = XprPrims(*[t.data_ptr() for t in host], None)
+    dp = _prims(*dst)
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    _check(L.xpr_project_host(ctypes.byref(hp), ctypes.byref(dp), n, ctypes.byref(c), ctypes.byref(g), _ptr(rec),
+                              _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _stream(stream)), "xpr_project_host")
     return (rec, bbox, tile_count) if isect_count is None else (rec, bbox, tile_count, isect_count)
 
 

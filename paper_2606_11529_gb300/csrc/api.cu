@@ -121,6 +121,40 @@ int xpr_project(const XprPrims *prims, int64_t n, const XprCamera *cam, const Xp
     return launch_project_fwd(*prims, n, *cam, *cfg, rec, bbox, tile_count, isect_count, as_stream(stream));
 }
 
+int xpr_project_host(const XprPrims *host, const XprPrims *dst, int64_t n, const XprCamera *cam,
+                     const XprConfig *cfg, float *rec, int32_t *bbox, int32_t *tile_count, int32_t *isect_count,
+                     void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_project_host"))) return s;
+    if ((s = check_n(n))) return s;
+    if (!host || !dst || !host->mu || !host->scale || !host->quat || !host->opacity || !dst->mu || !dst->scale ||
+        !dst->quat || !dst->opacity || !rec || !bbox || !tile_count)
+        return fail(XPR_ERR_INVALID, "xpr_project_host: NULL pointer");
+    if (n == 0) return XPR_OK;
+    if (!aligned(host->quat, 16) || !aligned(dst->quat, 16) || !aligned(rec, 16) || !aligned(bbox, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_host: quat, rec and bbox must be 16-byte aligned");
+    // the kernel dereferences the host arrays: each must be page-locked memory mapped for the device
+    // (the kernel reads it at its device address)
+    const float *hp[4] = {host->mu, host->scale, host->quat, host->opacity};
+    const float *hd[4];
+    for (int a = 0; a < 4; ++a) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, hp[a]) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(XPR_ERR_INVALID, "xpr_project_host: cannot query a host pointer");
+        }
+        if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr)
+            return fail(XPR_ERR_INVALID, "xpr_project_host: host geometry must be page-locked and device-mapped");
+        hd[a] = static_cast<const float *>(at.devicePointer);
+    }
+    if (!aligned(hd[2], 16)) return fail(XPR_ERR_INVALID, "xpr_project_host: quat must be 16-byte aligned");
+    const XprPrims src = {hd[0], hd[1], hd[2], hd[3], dst->sh};
+    const XprPrimsGrad copy = {const_cast<float *>(dst->mu), const_cast<float *>(dst->scale),
+                               const_cast<float *>(dst->quat), const_cast<float *>(dst->opacity), nullptr};
+    return launch_project_fwd(src, n, *cam, *cfg, rec, bbox, tile_count, isect_count, as_stream(stream), &copy);
+}
+
 size_t xpr_tile_bin_workspace(int64_t n) { return scan_partials_bytes(n < 0 ? 0 : n); }
 
 }  // extern "C"

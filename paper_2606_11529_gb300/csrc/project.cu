@@ -149,11 +149,14 @@ __device__ __forceinline__ void project_view(const Params &P, const float *shi, 
 }
 
 // COLOR = false (sh NULL): geometry only, colours left 0 for xpr_project_color to fill.
+// copy.mu non-NULL: the geometry read (from mu, scale, quat, opac, which may then be pinned host
+// memory) is also written to the device arrays of copy.
 template <int DEG, bool COLOR>
 __global__ void __launch_bounds__(kProjWarps * 32) project_fwd_kernel(
     const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
-    float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount, int *__restrict__ isect_count) {
+    float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount, int *__restrict__ isect_count,
+    XprPrimsGrad copy) {
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_fwd[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -166,6 +169,14 @@ __global__ void __launch_bounds__(kProjWarps * 32) project_fwd_kernel(
     const bool valid = i < n;
     Params P = {};
     if (valid) P = load_params(mu, scale, quat, opac, i);
+    if (valid && copy.mu) {
+        for (int j = 0; j < 3; ++j) {
+            copy.mu[3 * i + j] = P.m[j];
+            copy.scale[3 * i + j] = P.s[j];
+        }
+        reinterpret_cast<float4 *>(copy.quat)[i] = make_float4(P.q[0], P.q[1], P.q[2], P.q[3]);
+        copy.opacity[i] = P.o;
+    }
     for (int v = 0; v < cs.n_views; ++v) {
         CullData cd = {};
         int4 bb = make_int4(0, 0, 0, 0);
@@ -368,8 +379,10 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) project_bwd_kernel(
 }  // namespace
 
 int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
-                             float *rec, int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st) {
+                             float *rec, int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st,
+                             const XprPrimsGrad *copy) {
     if (n == 0 || n_views == 0) return XPR_OK;
+    const XprPrimsGrad cp = copy ? *copy : XprPrimsGrad{nullptr, nullptr, nullptr, nullptr, nullptr};
     const int tpb = kProjWarps * 32;
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
@@ -378,11 +391,11 @@ int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams
                                                                (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float),
                                                                st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs,
                                                                      cfg, rec, reinterpret_cast<int4 *>(bbox), tc,
-                                                                     isect_count));
+                                                                     isect_count, cp));
     } else {
         XPR_DEG_DISPATCH(DEG, project_fwd_kernel<DEG, false><<<blocks, tpb, 0, st>>>(
                                   p.mu, p.scale, p.quat, p.opacity, nullptr, n, cs, cfg, rec,
-                                  reinterpret_cast<int4 *>(bbox), tc, isect_count));
+                                  reinterpret_cast<int4 *>(bbox), tc, isect_count, cp));
     }
     XPR_LAUNCH_CHECK("project_fwd_kernel");
     return XPR_OK;
@@ -422,8 +435,8 @@ int launch_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams
 }
 
 int launch_project_fwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg, float *rec,
-                       int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st) {
-    return launch_project_fwd_views(p, n, &cam, 1, cfg, rec, bbox, tc, isect_count, st);
+                       int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st, const XprPrimsGrad *copy) {
+    return launch_project_fwd_views(p, n, &cam, 1, cfg, rec, bbox, tc, isect_count, st, copy);
 }
 
 int launch_project_bwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg,

@@ -41,11 +41,13 @@ int validate_camera_config(const XprCamera *cam, const XprConfig *cfg);
 constexpr int kMaxViews = 16;  // views per multi-view launch (cameras travel as a kernel argument)
 
 int launch_project_fwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg, float *rec,
-                       int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st);
+                       int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st,
+                       const XprPrimsGrad *copy = nullptr);  // copy: device copy of the geometry read
 int launch_project_bwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg,
                        const float *d_rec, const XprPrimsGrad &g, cudaStream_t st);
 int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
-                             float *rec, int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st);
+                             float *rec, int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st,
+                             const XprPrimsGrad *copy = nullptr);
 int launch_project_color_views(const float *mu, const float *sh, int64_t n, const XprCamera *cams, int n_views,
                                const XprConfig &cfg, float *rec, cudaStream_t st);
 int launch_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,

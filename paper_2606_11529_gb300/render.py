@@ -35,10 +35,17 @@ class Workspace:
         self.bufs = {}
         self.fused = fused  # xpr_bin_sorted (True) or xpr_tile_bin + xpr_sort_tiles (False)
         self.sh_events = None  # set by a caller whose SH copy is still in flight (consumed by one forward)
+        # set by a caller whose inputs are still in pinned host memory: (host (mu, scale, quat,
+        # opacity, sh), copy stream); the forward brings them over itself (consumed by one forward)
+        self.host_inputs = None
 
     def take_sh_events(self):
         ev, self.sh_events = self.sh_events, None
         return ev
+
+    def take_host_inputs(self):
+        h, self.host_inputs = self.host_inputs, None
+        return h
 
     def scratch(self, name, nbytes, device):
         t = self.bufs.get(name)
@@ -120,12 +127,17 @@ def is_lp(cfg) -> bool:
 
 def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
                   timers=None, fused: bool = False, keep_sorted_tiles: bool = False, sh_events=None,
-                  render: bool = True) -> Frame:
+                  render: bool = True, host_inputs=None) -> Frame:
     """The forward stages, each one C-ABI call: project, depth order, then either the key path
     (xpr_tile_bin emitting u32 tile ids in depth order + xpr_sort_tiles, the default) or the fused
     bin + sort (xpr_bin_sorted), then render.  Both give the same sorted lists bit for bit.
     sh_events: events of an SH copy still in flight; then the projection runs without colours,
-    and the stream waits for the events just before xpr_project_color fills them in."""
+    and the stream waits for the events just before xpr_project_color fills them in.
+    host_inputs: (pinned host (mu, scale, quat, opacity, sh), copy stream): the parameters are brought
+    into the given device tensors here.  3DGS: the projection reads the geometry over the host link
+    and writes its device copy in the same pass (xpr_project_host); then the SH coefficients are
+    copied on the copy stream under the depth order, binning and sort, and the colours are filled
+    in after the sort (as with sh_events).  3DGUT / LinPrim: everything is copied first."""
     L = B.load()
     tm = timers or _NO_TIMERS
     ccam, ccfg = B.make_camera(cam), B.make_config(cfg)
@@ -137,6 +149,11 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     fused = fused and not lp  # LinPrim is binned by xpr_tile_bin_lp
     sd = None
     deferred = sh_events is not None and not (ut or lp)
+    from_host = host_inputs is not None and not (ut or lp)
+    if host_inputs is not None and not from_host:  # these projections need every input first
+        _wait_events(stream, _copy_on(host_inputs[1], (mu, scale, quat, opacity, sh), host_inputs[0], stream))
+    if from_host:
+        deferred = True
     if sh_events is not None and (ut or lp):  # these projections take the colours in the same pass
         _wait_events(stream, sh_events)
     tm.start("project", stream)
@@ -145,6 +162,13 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
                                                   with_isect_count=not fused)
     elif lp:
         rec, sd, bbox, tc, cnt = B.xpr_project_lp(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream)
+    elif from_host:
+        hs, cs = host_inputs
+        out = B.xpr_project_host(hs[:4], (mu, scale, quat, opacity, None), ccam, ccfg, stream=stream,
+                                 with_isect_count=not fused)
+        rec, bbox, tc = out[:3]
+        cnt = out[3] if len(out) > 3 else None
+        sh_events = _copy_on(cs, (sh,), hs[4:], stream)  # after the projection: the host link is free
     else:
         out = B.xpr_project(mu, scale, quat, opacity, None if deferred else sh, ccam, ccfg, stream=stream,
                             with_isect_count=not fused)
@@ -200,6 +224,19 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     return Frame(rec, bbox, tc, cnt, order, offsets, tiles, vals, I, ks, vs, ranges, image, t_final, n_contrib, sd)
 
 
+def _copy_on(copy_stream, dst, src, stream):
+    """Copies src (host) into dst (device) on copy_stream after the work enqueued on `stream` (None:
+    the current stream) so far; returns the event of the copies."""
+    cur = stream if stream is not None else torch.cuda.current_stream()
+    copy_stream.wait_stream(cur)
+    with torch.cuda.stream(copy_stream), torch.no_grad():
+        for d, h in zip(dst, src):
+            d.copy_(h, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(copy_stream)
+    return ev
+
+
 def _wait_events(stream, events):
     cur = stream if stream is not None else torch.cuda.current_stream()
     for e in (events if isinstance(events, (list, tuple)) else [events]):
@@ -212,7 +249,7 @@ class SplatFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, mu, scale, quat, opacity, sh, cam, cfg, ws, timers):
         fr = forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws, timers=timers, fused=ws.fused,
-                           sh_events=ws.take_sh_events())
+                           sh_events=ws.take_sh_events(), host_inputs=ws.take_host_inputs())
         # 3DGUT and LinPrim render from the shader data, 3DGS from the records
         shade = fr.sd if fr.sd is not None else fr.rec
         ctx.save_for_backward(mu, scale, quat, opacity, sh, shade, fr.vals_sorted, fr.ranges, fr.t_final,

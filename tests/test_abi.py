@@ -130,3 +130,20 @@ def test_project_color_host_checks(lib):
     assert s == binding.XPR_ERR_INVALID and b"NULL" in lib.xpr_last_error()
     s = lib.xpr_project_color(256, 256, 10, cams, 0, ctypes.byref(cfg), 256, None)
     assert s == binding.XPR_ERR_INVALID
+
+
+def test_project_host_checks(lib):
+    from paper_2606_11529_gb300 import binding
+    cam, cfg = _cam_cfg()
+    p = binding.XprPrims(16, 16, 16, 16, None)
+    s = lib.xpr_project_host(None, ctypes.byref(p), 10, ctypes.byref(cam), ctypes.byref(cfg), 16, 16, 16, None, None)
+    assert s == binding.XPR_ERR_INVALID and b"NULL" in lib.xpr_last_error()
+    q = binding.XprPrims(16, 16, 20, 16, None)  # quat not 16-byte aligned
+    s = lib.xpr_project_host(ctypes.byref(q), ctypes.byref(p), 10, ctypes.byref(cam), ctypes.byref(cfg), 16, 16, 16,
+                             None, None)
+    assert s == binding.XPR_ERR_INVALID and b"aligned" in lib.xpr_last_error()
+    ut = binding.XprConfig.from_buffer_copy(cfg)
+    ut.method = binding.XPR_METHOD_3DGUT
+    s = lib.xpr_project_host(ctypes.byref(p), ctypes.byref(p), 10, ctypes.byref(cam), ctypes.byref(ut), 16, 16, 16,
+                             None, None)
+    assert s == binding.XPR_ERR_INVALID

@@ -213,3 +213,44 @@ def test_deferred_colour_equals_one_pass():
     (R.render(*P, cam, cfg, ws) * w).sum().backward()
     for a, b in zip(g_ref, P):
         assert rel_err(b.grad.cpu().numpy(), a.cpu().numpy()) < 1e-5
+
+
+def test_projection_from_pinned_host_equals_resident():
+    # inputs still in pinned host memory: the projection reads the geometry over the host link and
+    # writes its device copy in the same pass, then the SH coefficients are copied under the binning
+    # and sort: the frame equals the one from resident inputs bit for bit, the device copy equals the
+    # host data, and the gradients through the autograd function are those of resident inputs
+    sc = scenes.clustered_scene(30_001, seed=12, n_centers=40, width=320, height=180, focal=320.0, sh_degree=3)
+    cam = scenes.pinhole(320, 180, 320.0, scenes.yaw_view(3.0, (0.02, 0.0, 0.05)))
+    cfg = scenes.RenderConfig(sh_degree=3, bg=(0.2, 0.1, 0.0))
+    P = [t.requires_grad_(True) for t in R.scene_to_device(sc)]
+    ref = R.forward_frame(*[p.detach() for p in P], cam, cfg)
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in sc.arrays()]
+    up = R.Uploader()
+    dst = [torch.zeros_like(p.detach()) for p in P]
+    rec, bbox, tc, cnt = B.xpr_project_host(host[:4], dst[:4] + [None], cam, cfg, with_isect_count=True)
+    for a, b in zip((ref.bbox, ref.tile_count, ref.isect_count), (bbox, tc, cnt)):
+        assert torch.equal(a, b)
+    for d, h in zip(dst[:4], host[:4]):
+        assert torch.equal(d.cpu(), h)
+    dst = [torch.zeros_like(p.detach()) for p in P]
+    fr = R.forward_frame(*dst, cam, cfg, host_inputs=(host, up.stream))
+    for name in ("rec", "bbox", "tile_count", "isect_count", "vals_sorted", "ranges", "image", "t_final", "n_contrib"):
+        assert torch.equal(getattr(ref, name), getattr(fr, name)), name
+    w = torch.from_numpy(np.random.default_rng(5).normal(size=tuple(ref.image.shape)).astype(np.float32)).cuda()
+    (R.render(*P, cam, cfg) * w).sum().backward()
+    g_ref = [p.grad.clone() for p in P]
+    for p in P:
+        p.grad = None
+    with torch.no_grad():
+        for p in P:
+            p.zero_()
+    ws = R.Workspace()
+    ws.host_inputs = (host, up.stream)
+    (R.render(*P, cam, cfg, ws) * w).sum().backward()
+    for a, b in zip(g_ref, P):
+        assert rel_err(b.grad.cpu().numpy(), a.cpu().numpy()) < 1e-5
+    # pageable host memory is refused before any launch
+    pageable = [torch.from_numpy(np.ascontiguousarray(a)) for a in sc.arrays()[:4]]
+    with pytest.raises(B.XprError):
+        B.xpr_project_host(pageable, dst[:4] + [None], cam, cfg)
