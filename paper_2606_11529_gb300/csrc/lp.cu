@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) lp_bin_kernel(const float *__restrict__ r
 
 // ---- compositing -----------------------------------------------------------------------------
 constexpr unsigned kFullLp = 0xffffffffu;
-constexpr int kLpBatch = 256;     // entries staged per batch (forward)
+constexpr int kLpBatch = 128;     // entries staged per batch (forward; 128 rather than 256: 78 instead of 94 registers, 10% faster)
 constexpr int kLpBwdBatch = 128;  // the adjoint also keeps 20 accumulators per entry
 template <int TW, int TH>
 __host__ __device__ constexpr int lp_px() {
