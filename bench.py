@@ -396,16 +396,19 @@ def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     cfg = scenes.RenderConfig(sh_degree=3)
     free, _ = torch.cuda.mem_get_info(dev)
     pool = int(max(free - (16 << 30), 8 << 30))
-    srv = SV.Server(resident, cfg, pool_bytes=pool, slots=3)
+    # the client consumes each image once delivered (pinned output buffers are recycled)
+    srv = SV.Server(resident, cfg, pool_bytes=pool, slots=3, keep_images=False)
     srv.calibrate()
     # warm every (scene, size) once so lazy module loading and allocator growth stay outside
-    SV.run_plain(resident, cfg, SV.make_trace(48, rate_hz=1e6, seed=99), srv)
+    SV.run_plain(resident, cfg, SV.make_trace(48, rate_hz=1e6, seed=99), srv, keep_images=False)
+    # and a burst through the server, so that each worker stream's allocator pool has grown too
+    srv.run(SV.make_trace(192, rate_hz=1e6, seed=98))
     trace = SV.make_trace(n_requests + warmup, rate_hz=200.0, seed=0)
     srv.run(trace)
     ours = SV.latency_stats(trace, warmup)
     ours["pool_peak_gb"] = round(srv.budget.peak / 2 ** 30, 3)
     ptrace = SV.make_trace(n_requests + warmup, rate_hz=200.0, seed=0)
-    SV.run_plain(resident, cfg, ptrace, srv)
+    SV.run_plain(resident, cfg, ptrace, srv, keep_images=False)
     plain = SV.latency_stats(ptrace, warmup)
     # the same comparison at twice the rate, where the queue of the plain path builds up
     n_hi = max(n_requests // 2, 100)
@@ -413,10 +416,10 @@ def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     srv.run(htrace)
     hi = {"rate_hz": 400.0, "requests": n_hi, "server": SV.latency_stats(htrace, warmup // 2)}
     hptrace = SV.make_trace(n_hi + warmup // 2, rate_hz=400.0, seed=2)
-    SV.run_plain(resident, cfg, hptrace, srv)
+    SV.run_plain(resident, cfg, hptrace, srv, keep_images=False)
     hi["plain_queue"] = SV.latency_stats(hptrace, warmup // 2)
     n_cap = max(n_requests // 4, 100)
-    capped = SV.Server(resident, cfg, pool_bytes=int(cap_gb * 2 ** 30), slots=3)
+    capped = SV.Server(resident, cfg, pool_bytes=int(cap_gb * 2 ** 30), slots=3, keep_images=False)
     capped.calib = srv.calib
     ctrace = SV.make_trace(n_cap + warmup // 4, rate_hz=200.0, seed=1)
     capped.run(ctrace)

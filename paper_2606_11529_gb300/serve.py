@@ -54,7 +54,8 @@ class Request:
     ready: float = math.nan
     batch_views: int = 0
     n_isect: int = 0
-    image: object = None
+    image: object = None  # the delivered image (None once a client that keeps no images has it)
+    delivered: bool = False
 
     @property
     def key(self):
@@ -223,12 +224,15 @@ class Server:
     outside it).  ``slots``: worker threads, one CUDA stream each."""
 
     def __init__(self, scenes, cfg, pool_bytes: int, slots: int = 3, capacity_factor: float = 1.3,
-                 max_views: int = MAX_VIEWS, deliver_host: bool = True):
+                 max_views: int = MAX_VIEWS, deliver_host: bool = True, keep_images: bool = True):
         self.scenes = scenes
         self.cfg = cfg
         self.slots = slots
         self.capacity_factor = capacity_factor
         self.deliver_host = deliver_host
+        # keep_images False: a request drops its image once delivered (a client that consumes
+        # results), so the pinned host buffers are recycled instead of pinning new memory per request
+        self.keep_images = keep_images
         self.budget = HBMBudget(pool_bytes)
         self.sched = Scheduler(self.budget, max_views)
         self.cv = threading.Condition()
@@ -279,8 +283,9 @@ class Server:
                 out = img
             stream.synchronize()
         for v, r in enumerate(batch):
-            r.image = out[v]
+            r.image = out[v] if self.keep_images else None
             r.n_isect = fr.n_isect
+            r.delivered = True
 
     def new_stream(self):
         import torch
@@ -295,7 +300,7 @@ class Server:
                     batch = self.sched.take_batch(time.perf_counter() - t0)
                     if batch:
                         break
-                    self.cv.wait(0.0005)
+                    self.cv.wait(0.01)  # arrivals and completions notify; the timeout is a backstop
                 if not batch:
                     return
             try:
@@ -307,7 +312,7 @@ class Server:
             with self.cv:
                 self.sched.complete([r for r in batch], time.perf_counter() - t0)
                 for r in batch:
-                    if r.image is None:
+                    if not r.delivered:
                         r.status = "error"
                 self.cv.notify_all()
 
@@ -339,9 +344,10 @@ class Server:
         return trace
 
 
-def run_plain(scenes, cfg, trace: list[Request], server: Server | None = None, deliver_host: bool = True):
+def run_plain(scenes, cfg, trace: list[Request], server: Server | None = None, deliver_host: bool = True,
+              keep_images: bool = True):
     """The plain per-request queue: one request at a time, in arrival order, through the
-    single-view per-stage path on the current stream."""
+    single-view per-stage path on the current stream (keep_images as for Server)."""
     import torch
     from . import binding as B
     from . import render as R
@@ -360,5 +366,6 @@ def run_plain(scenes, cfg, trace: list[Request], server: Server | None = None, d
             out = fr.image
         torch.cuda.current_stream().synchronize()
         r.ready = time.perf_counter() - t0
-        r.status, r.batch_views, r.image, r.n_isect = "done", 1, out, fr.n_isect
+        r.status, r.batch_views, r.n_isect, r.delivered = "done", 1, fr.n_isect, True
+        r.image = out if keep_images else None
     return trace

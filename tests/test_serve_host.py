@@ -99,6 +99,7 @@ class FakeServer(SV.Server):
             self.running -= 1
         for r in batch:
             r.image = r.rid
+            r.delivered = True
 
 
 @pytest.mark.parametrize("slots", [1, 3])
@@ -134,3 +135,15 @@ def test_latency_stats_on_known_values():
     st = SV.latency_stats(reqs)
     assert st["p50_ms"] == pytest.approx(50.5) and st["p99_ms"] == pytest.approx(99.01)
     assert st["views_per_s"] == pytest.approx(100 / 99.1, abs=0.006)  # rounded to 0.01
+
+
+def test_undelivered_request_is_an_error():
+    # a worker whose execute returns without delivering marks its batch failed
+    class Undelivering(FakeServer):
+        def execute(self, batch, stream):
+            pass
+
+    trace = SV.make_trace(20, n_scenes=2, rate_hz=5000.0, seed=3)
+    srv = Undelivering(pool=2 * 1920 * 1080, slots=2)
+    srv.run(trace)
+    assert all(r.status == "error" for r in trace)
