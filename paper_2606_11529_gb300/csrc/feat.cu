@@ -21,11 +21,12 @@ namespace {
 constexpr unsigned kFullF = 0xffffffffu;
 constexpr int kFeatBatch = 128;
 
-// pixels per thread: fewer as the channels grow (each pixel keeps NF accumulators), and no more
-// than a whole-warp block allows
+// pixels per thread: 4 up to 2 channels, else 2 (each pixel keeps NF values; at one pixel per
+// thread the 16-channel adjoint's per-entry warp reduction served only 32 pixels and ran 1.33 ms on
+// the headline against 0.97 ms at two), and no more than a whole-warp block allows
 template <int TW, int TH, int NF>
 __host__ __device__ constexpr int feat_px() {
-    constexpr int want = NF <= 2 ? 4 : (NF <= 8 ? 2 : 1);
+    constexpr int want = NF <= 2 ? 4 : 2;
     constexpr int cap = (TW * TH) / 32 >= 4 ? 4 : (TW * TH) / 32;
     return want < cap ? want : cap;
 }
