@@ -367,6 +367,7 @@ FeatConsts make_feat_consts(const XprCamera &cam, const XprConfig &cfg, int64_t 
     else if ((nf) <= 2) { constexpr int NFV = 2; __VA_ARGS__; }      \
     else if ((nf) <= 4) { constexpr int NFV = 4; __VA_ARGS__; }      \
     else if ((nf) <= 8) { constexpr int NFV = 8; __VA_ARGS__; }      \
+    else if ((nf) <= 12) { constexpr int NFV = 12; __VA_ARGS__; }    \
     else { constexpr int NFV = 16; __VA_ARGS__; }
 
 #define XPR_FEAT_TILE_DISPATCH(TWV, THV, ...)                                                     \

@@ -21,7 +21,7 @@ def _case(tile=16, n=8000, W=256, H=256, deg=1, seed=0):
 
 
 @pytest.mark.parametrize("nfeat,depth,tile", [(0, True, 16), (3, True, 8), (8, False, 16), (15, True, 16),
-                                              (2, False, 8)])
+                                              (2, False, 8), (10, True, 8), (12, False, 16)])
 def test_features_match_oracle(oracle, nfeat, depth, tile):
     sc, cam, cfg = _case(tile, W=250, H=170)
     pr = oracle.project_scene(sc, cam, cfg)
