@@ -3,8 +3,9 @@
 //
 // Keys are either u64 (tile << 32 | depth bits; xpr_sort) or u32 tile ids (xpr_sort_tiles, for
 // pairs emitted in depth order, where a stable sort by tile alone gives the (tile, depth) order).
-// Each 8-bit pass ranks blocks of 4096 keys stably (warp w owns a contiguous run of 512 keys
-// visited in index order; lanes with equal digits are found with one ballot per digit bit), places
+// Each 8-bit pass ranks blocks of keys stably (4096 keys, 16 per thread, in the chained scan; 3072,
+// 12 per thread, in reduce-then-scan; warp w owns a contiguous run of 32 x keys-per-thread visited
+// in index order; lanes with equal digits are found with one ballot per digit bit), places
 // every key at its rank in a block-local sorted copy in shared memory, and writes the copy out in
 // order, so consecutive threads write consecutive addresses of one digit's run.  The global start
 // of each (block, digit) run comes from one of two schemes:
