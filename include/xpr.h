@@ -514,6 +514,13 @@ unsigned long long xpr_launch_count(void);
  * set since the last call, else XPR_ERR_TIMEOUT or XPR_ERR_INTERNAL (the
  * results of the calls in between are then unreliable). */
 int xpr_device_check(void);
+/* xpr_selftest_wait: exercises the bounded wait of the sort's chained scan
+ * against words that nothing publishes.  `zeroed` is a device buffer of at
+ * least 512 uint32 whose first 256 are zero; one block of 256 threads looks
+ * back at them, gives up after `polls` polls each (1..2^20) and records the
+ * timeout, so the next xpr_device_check returns XPR_ERR_TIMEOUT.  Words
+ * 256..511 receive the (short) counts.  The device stays usable. */
+int xpr_selftest_wait(uint32_t *zeroed, int32_t polls, void *stream);
 
 #ifdef __cplusplus
 }

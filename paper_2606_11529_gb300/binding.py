@@ -123,6 +123,7 @@ SIGNATURES = {
     "xpr_version": (ctypes.c_int, []),
     "xpr_launch_count": (ctypes.c_ulonglong, []),
     "xpr_device_check": (c_i32, []),
+    "xpr_selftest_wait": (c_i32, [c_vp, c_i32, c_vp]),
     "xpr_project_host": (c_i32, [ctypes.POINTER(XprPrims), ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
                                  ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp]),
 }
@@ -168,6 +169,14 @@ def xpr_device_check():
     """Synchronises the device and raises XprError if a kernel recorded a timed-out wait or an
     inconsistent intermediate since the last check (the flags are cleared)."""
     _check(load().xpr_device_check(), "xpr_device_check")
+
+
+def xpr_selftest_wait(polls=1000, stream=None):
+    """Runs the sort's bounded look-back wait against words nothing publishes (see xpr.h); returns
+    the 256 counts it ended with.  The timeout is then reported by xpr_device_check."""
+    z = torch.zeros(512, dtype=torch.int32, device="cuda")
+    _check(load().xpr_selftest_wait(_ptr(z), int(polls), _stream(stream)), "xpr_selftest_wait")
+    return z[256:]
 
 
 def _ptr(t):

@@ -86,6 +86,12 @@ unsigned long long xpr_launch_count(void) { return g_launches.load(std::memory_o
 
 const char *xpr_last_error(void) { return g_err; }
 
+int xpr_selftest_wait(uint32_t *zeroed, int32_t polls, void *stream) {
+    if (!zeroed) return fail(XPR_ERR_INVALID, "xpr_selftest_wait: NULL buffer");
+    if (polls < 1 || polls > (1 << 20)) return fail(XPR_ERR_INVALID, "xpr_selftest_wait: polls must be in [1, 2^20]");
+    return lookback_selftest(zeroed, polls, as_stream(stream));
+}
+
 int xpr_device_check(void) {
     unsigned bits = 0;
     const int s = sort_device_errors(&bits);

@@ -274,6 +274,62 @@ __global__ void __launch_bounds__(kRadix) colapply_kernel(int32_t *__restrict__ 
 }
 
 
+// The count of digit d0 in all blocks before block b > 0 of a chained-scan pass: a word not yet
+// published is polled alone; after each step over published counts the window of words read at
+// once grows (1, 4, 16), so that one round trip walks up to kLook blocks.  A word still unpublished
+// after max_polls polls sets the timeout flag and ends the walk (the count is then short); walking
+// past block 0, which always publishes its running total, sets the consistency flag.
+__device__ __forceinline__ uint32_t lookback(const uint32_t *status, int b, int d0, int max_polls) {
+    uint32_t excl = 0;
+    int j = b - 1, polls = 0, win = 1;
+    for (;;) {
+        uint32_t wv[kLook];
+#pragma unroll
+        for (int q = 0; q < kLook; ++q)
+            wv[q] = (q < win && j - q >= 0) ? ld_relaxed(status + (size_t)(j - q) * kRadix + d0) : 0u;
+        int adv = 0;
+        bool stop = false, found = false;
+#pragma unroll
+        for (int q = 0; q < kLook; ++q) {
+            if (!stop) {
+                const uint32_t sw = wv[q];
+                if (sw == 0u) {
+                    stop = true;  // not yet published (or outside the window)
+                } else if (sw & kPrefixFlag) {
+                    excl += sw & ~kPrefixFlag;
+                    stop = found = true;
+                } else {
+                    excl += sw - 1u;
+                    ++adv;
+                }
+            }
+        }
+        if (found) return excl;
+        j -= adv;
+        if (j < 0) {
+            atomicOr(&g_sort_errors, 2u);
+            return excl;
+        }
+        if (adv == 0) {
+            if (++polls >= max_polls) {
+                atomicOr(&g_sort_errors, 1u);
+                return excl;
+            }
+            __nanosleep(64);
+            win = 1;
+        } else {
+            polls = 0;
+            win = min(4 * win, kLook);
+        }
+    }
+}
+
+// Self-test of the bounded wait: every thread looks back from block 1 at block 0's words, which
+// the caller has zeroed and nothing publishes, so each wait runs out after max_polls polls.
+__global__ void lookback_selftest_kernel(const uint32_t *status, int max_polls, uint32_t *out) {
+    out[threadIdx.x] = lookback(status, 1, (int)threadIdx.x, max_polls);
+}
+
 // Exclusive scan over the block's 256 threads of two ints at once (one per digit); totals unused.
 __device__ __forceinline__ void digit_scan2(int a, int b, int &ea, int &eb, int2 *s_wsum) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -397,53 +453,10 @@ __global__ void __launch_bounds__(kThreads)
             s_val[pos] = kHoldVals ? vreg[kHoldVals ? r : 0] : vb[idx];
         }
     }
-    // look back (after the placement, so that the blocks before this one have had time to publish):
-    // the digit's count in all blocks before this one.  A word not yet published is polled alone;
-    // after each step over published counts the window of words read at once grows (1, 4, 16), so
-    // that one round trip walks up to kLook blocks.
+    // look back (after the placement, so that the blocks before this one have had time to publish)
     uint32_t excl = 0;
     if (b > 0) {
-        int j = b - 1, polls = 0, win = 1;
-        for (;;) {
-            uint32_t wv[kLook];
-#pragma unroll
-            for (int q = 0; q < kLook; ++q)
-                wv[q] = (q < win && j - q >= 0) ? ld_relaxed(status + (size_t)(j - q) * kRadix + d0) : 0u;
-            int adv = 0;
-            bool stop = false, found = false;
-#pragma unroll
-            for (int q = 0; q < kLook; ++q) {
-                if (!stop) {
-                    const uint32_t sw = wv[q];
-                    if (sw == 0u) {
-                        stop = true;  // not yet published (or outside the window)
-                    } else if (sw & kPrefixFlag) {
-                        excl += sw & ~kPrefixFlag;
-                        stop = found = true;
-                    } else {
-                        excl += sw - 1u;
-                        ++adv;
-                    }
-                }
-            }
-            if (found) break;
-            j -= adv;
-            if (j < 0) {  // block 0 always publishes a running total
-                atomicOr(&g_sort_errors, 2u);
-                break;
-            }
-            if (adv == 0) {
-                if (++polls >= kWaitPolls) {
-                    atomicOr(&g_sort_errors, 1u);
-                    break;
-                }
-                __nanosleep(64);
-                win = 1;
-            } else {
-                polls = 0;
-                win = min(4 * win, kLook);
-            }
-        }
+        excl = lookback(status, b, d0, kWaitPolls);
         st_relaxed(my, kPrefixFlag | (excl + (uint32_t)tot));
     }
     s_gofs[d0] = (int64_t)gstart + excl - start;
@@ -805,6 +818,12 @@ __global__ void worklist_keys_kernel(const int2 *__restrict__ ranges, int n_tile
 }
 
 }  // namespace
+
+int lookback_selftest(uint32_t *zeroed, int max_polls, cudaStream_t st) {
+    lookback_selftest_kernel<<<1, kRadix, 0, st>>>(zeroed, max_polls, zeroed + kRadix);
+    XPR_LAUNCH_CHECK("lookback_selftest_kernel");
+    return XPR_OK;
+}
 
 int sort_device_errors(unsigned *bits) {
     unsigned v = 0;

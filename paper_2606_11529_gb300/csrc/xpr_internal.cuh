@@ -137,6 +137,7 @@ int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int
                 uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st);
 size_t sort_tiles_workspace_bytes(int64_t n, int32_t n_tiles);
 int sort_device_errors(unsigned *bits);  // synchronises; reads and clears the sort's device flags
+int lookback_selftest(uint32_t *zeroed, int max_polls, cudaStream_t st);  // see xpr_selftest_wait
 int launch_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles,
                       uint32_t *tiles_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes,
                       cudaStream_t st);

@@ -147,3 +147,10 @@ def test_project_host_checks(lib):
     s = lib.xpr_project_host(ctypes.byref(p), ctypes.byref(p), 10, ctypes.byref(cam), ctypes.byref(ut), 16, 16, 16,
                              None, None)
     assert s == binding.XPR_ERR_INVALID
+
+
+def test_selftest_wait_host_checks(lib):
+    from paper_2606_11529_gb300 import binding
+    assert lib.xpr_selftest_wait(None, 10, None) == binding.XPR_ERR_INVALID
+    for polls in (0, (1 << 20) + 1):
+        assert lib.xpr_selftest_wait(16, polls, None) == binding.XPR_ERR_INVALID

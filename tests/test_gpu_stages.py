@@ -288,3 +288,23 @@ def test_project_bwd_matches_oracle(oracle):
         got = B.xpr_project_bwd(*R.scene_to_device(sc), cam, cfg, dev(d_rec))
         for name, g in zip(["mu", "scale", "quat", "opacity", "sh"], got):
             assert rel_err(g.cpu().numpy(), ref[name]) < GRAD_TOL, (deg, name)
+
+
+def test_sort_wait_timeout_is_reported_and_the_device_stays_usable():
+    # the chained scan's look-back wait, run against words that nothing publishes, gives up after
+    # its poll limit and records a timeout that xpr_device_check reports (once); a sort right after
+    # is still exact
+    B.xpr_device_check()
+    counts = B.xpr_selftest_wait(polls=2000)
+    torch.cuda.synchronize()
+    with pytest.raises(B.XprError) as e:
+        B.xpr_device_check()
+    assert e.value.status == B.XPR_ERR_TIMEOUT
+    assert torch.all(counts == 0)
+    B.xpr_device_check()  # the flag was cleared by the first check
+    rng = np.random.default_rng(5)
+    tiles = rng.integers(0, 300, size=50_000).astype(np.uint32)
+    vals = np.arange(50_000, dtype=np.uint32)
+    order = np.argsort(tiles, kind="stable")
+    _, vs, _ = B.xpr_sort_tiles(dev_i32(tiles), dev_i32(vals), 300)
+    np.testing.assert_array_equal(host_u32(vs), vals[order])
