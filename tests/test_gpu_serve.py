@@ -74,3 +74,21 @@ def test_plain_queue_matches(resident):
     trace = SV.make_trace(20, n_scenes=len(resident), rate_hz=3000.0, seed=8, resolutions=RES)
     SV.run_plain(resident, cfg, trace)
     _check_identical(resident, cfg, trace)
+
+
+def test_served_equals_alone_at_the_serving_workload_size():
+    # the serving workload's sizes: its smallest and largest scenes (clustered SH-3, about 1.9e5 and
+    # 2.8e6 Gaussians) at 512x512, 1280x720 and 1920x1080, three worker streams, requests arriving
+    # together: every image equals the same request rendered alone, bit for bit
+    import math
+    import numpy as np
+    rng = np.random.default_rng(1000)
+    sizes = np.exp(rng.uniform(math.log(100_000), math.log(3_000_000), size=16)).astype(np.int64)
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes))]
+    resident = [R.scene_to_device(scenes.clustered_scene(int(sizes[k]), seed=k)) for k in pick]
+    cfg = scenes.RenderConfig(sh_degree=3)
+    trace = SV.make_trace(18, n_scenes=2, rate_hz=1e5, seed=6)
+    srv = SV.Server(resident, cfg, pool_bytes=24 << 30, slots=3)
+    srv.run(trace)
+    _check_identical(resident, cfg, trace)
+    assert {(r.width, r.height) for r in trace} == set(SV.RESOLUTIONS)
