@@ -19,6 +19,18 @@ import numpy as np
 from . import oracle as O
 
 
+def covering(bb, tx, ty, Wt: int, Ht: int):
+    """Mask of the primitives whose tile box [x0, x1) x [y0, y1) (bb rows) holds at least one of the
+    tiles (tx[i], ty[i]): a summed-area table of the sampled-tile mask answers it per primitive."""
+    sat = np.zeros((Ht + 1, Wt + 1), np.int64)
+    sat[ty + 1, tx + 1] = 1
+    sat = sat.cumsum(0).cumsum(1)
+    x0, y0 = np.clip(bb[:, 0], 0, Wt), np.clip(bb[:, 1], 0, Ht)
+    x1, y1 = np.clip(bb[:, 2], 0, Wt), np.clip(bb[:, 3], 0, Ht)
+    inside = sat[y1, x1] - sat[y0, x1] - sat[y1, x0] + sat[y0, x0]
+    return (x1 > x0) & (y1 > y0) & (inside > 0)
+
+
 def estimate_fwd_bwd_seconds(scene, cam, cfg, prim_frac: float = 0.1, n_tiles: int = 48, seed: int = 0):
     rng = np.random.default_rng(seed)
     n = scene.n
@@ -44,9 +56,7 @@ def estimate_fwd_bwd_seconds(scene, cam, cfg, prim_frac: float = 0.1, n_tiles: i
     full = O.project_scene(scene, cam, cfg)
     bb = full["bbox"]
     tx, ty = tiles % Wt, tiles // Wt
-    cover = np.zeros(n, bool)
-    for x, y in zip(tx, ty):
-        cover |= (bb[:, 0] <= x) & (x < bb[:, 2]) & (bb[:, 1] <= y) & (y < bb[:, 3])
+    cover = covering(bb, tx, ty, Wt, Ht)
     idx = np.nonzero(cover)[0]
     rec_c = full["rec"][idx]
     _, k2, v2 = O.bin_pairs(rec_c, bb[idx], cam, cfg, exact32=False)
