@@ -158,11 +158,11 @@ def run_reference(args):
     from paper_2606_11529_gb300 import scenes
     sc, cam, cfg = scenes.headline_case()
     for _ in range(args.warmup):
-        baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=0.02, n_tiles=8, seed=123)
+        baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=0.05, n_tiles=512, seed=123)
     ests, meas = [], 0.0
     desc = ""
     for k in range(args.steps):
-        est, m, desc = baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=0.02, n_tiles=8, seed=k)
+        est, m, desc = baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=0.05, n_tiles=512, seed=k)
         ests.append(est)
         meas += m
     ms = 1000.0 * statistics.mean(ests)
