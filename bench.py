@@ -183,6 +183,7 @@ def cpu_baseline_leg():
     from paper_2606_11529_gb300 import scenes
     sc, cam, cfg = scenes.headline_case()
     est, meas, desc = baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=1.0, n_tiles=1 << 30, seed=0)
+    baseline.release_lists()
     return {"value": 1000.0 * est, "unit": UNIT, "cores": baseline.threads(), "kind": "oracle", "sample": desc}
 
 

@@ -34,6 +34,11 @@ def _full_lists(scene, cam, cfg, T: int):
     return _lists["rec"], _lists["vals"], _lists["ranges"]
 
 
+def release_lists() -> None:
+    """Drops the cached full-scene lists (several hundred MB of host memory on a 1M scene)."""
+    _lists.clear()
+
+
 def estimate_fwd_bwd_seconds(scene, cam, cfg, prim_frac: float = 0.1, n_tiles: int = 48, seed: int = 0):
     rng = np.random.default_rng(seed)
     n = scene.n
