@@ -81,7 +81,9 @@ def estimate_fwd_bwd_seconds(scene, cam, cfg, prim_frac: float = 0.1, n_tiles: i
     measured = t_proj + t_bin + t_render + t_pbwd
     desc = (f"oracle (FP64, C) on a bounded sample: project+bin+sort+project-adjoint of {m} of {n} primitives "
             f"(x{n / m:.1f}), per-tile compositing fwd+adjoint on {len(tiles)} of {T} tiles (x{T / len(tiles):.1f}); "
-            f"{measured:.1f} s measured, extrapolated to one full fwd+bwd; projection and forward compositing "
+            f"{measured:.1f} s measured, "
+            f"{'the whole workload' if m == n and len(tiles) == T else 'extrapolated to one full fwd+bwd'}; "
+            f"projection and forward compositing "
             f"use OpenMP, binning/sort/adjoint compositing are serial")
     return est, measured, desc
 
