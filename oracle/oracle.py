@@ -16,6 +16,8 @@ import os
 import subprocess
 import sys
 
+from typing import NamedTuple
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -52,15 +54,17 @@ def lib():
         L = ctypes.CDLL(_LIB)
         L.oracle_project.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                      _I32P, _I32P, _F64P, _F64P]
-        L.oracle_bin.argtypes = [ctypes.c_int64, _F64P, _F32P, _I32P, _F64P, _F64P, ctypes.c_int, _I64P, _I32P, _U64P,
-                                 _U32P]
+        L.oracle_bin.argtypes = [ctypes.c_int64, _F64P, _F32P, _F32P, _I32P, _F64P, _F64P, ctypes.c_int, _I64P,
+                                 _I32P, _U64P, _U32P]
         L.oracle_bin.restype = ctypes.c_int64
         L.oracle_sort.argtypes = [ctypes.c_int64, _U64P, _U32P, ctypes.c_int64, _I32P]
-        L.oracle_render_tiles.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, ctypes.c_double,
-                                          _F64P, _F64P, _I32P, _I32P]
-        L.oracle_render_pixels.argtypes = [ctypes.c_int64, _F64P, _I32P, ctypes.c_int64, _F64P, ctypes.c_double,
-                                           ctypes.c_double, _F64P, _F64P, _I32P, _U64P]
-        L.oracle_render_bwd_brute.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_depth_keys.argtypes = [ctypes.c_int64, _F64P, _F64P, ctypes.c_int, _F32P]
+        L.oracle_project_unc.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P]
+        L.oracle_render_tiles.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, _F64P, _F64P,
+                                          _F64P, _F64P, _I32P, _I32P, _F64P]
+        L.oracle_render_pixels.argtypes = [ctypes.c_int64, _F64P, _F32P, _I32P, ctypes.c_int64, _F64P, _F64P,
+                                           _F64P, _F64P, _F64P, _I32P, _F64P, _U64P, _U64P]
+        L.oracle_render_bwd_brute.argtypes = [ctypes.c_int64, _F64P, _F32P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_render_bwd_tiles.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_project_bwd.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                          _F64P, _F64P, _F64P, _F64P, _F64P]
@@ -70,12 +74,12 @@ def lib():
         L.oracle_project_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                         _F64P, _I32P, _I32P, _F64P, _F64P]
         L.oracle_render_tiles_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _U32P, _I32P, _F64P, _F64P,
-                                             ctypes.c_double, _F64P, _F64P, _I32P, _I32P, _U64P]
+                                             ctypes.c_double, _F64P, _F64P, _I32P, _I32P, _F64P, _U64P]
         L.oracle_render_bwd_tiles_ut.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_project_ut_bwd.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                             _F64P, _F64P, _F64P, _F64P, _F64P, _F64P]
-        L.oracle_render_pixels_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _I32P, ctypes.c_int64, _F64P, _F64P,
-                                              ctypes.c_double, _F64P, _F64P, _I32P]
+        L.oracle_render_pixels_ut.argtypes = [ctypes.c_int64, _F64P, _F64P, _F32P, _I32P, ctypes.c_int64, _F64P,
+                                              _F64P, ctypes.c_double, _F64P, _F64P, _I32P, _F64P]
         L.oracle_ut_response.argtypes = [_F64P, _F64P]
         L.oracle_ut_response.restype = ctypes.c_double
         L.oracle_pixel_ray.argtypes = [ctypes.c_int, ctypes.c_int, _F64P, _F64P]
@@ -87,11 +91,11 @@ def lib():
         L.oracle_lp_keep.restype = ctypes.c_int
         L.oracle_lp_tile_bound.argtypes = [_F64P, ctypes.c_int, ctypes.c_int, _F64P, _F64P]
         L.oracle_lp_tile_bound.restype = ctypes.c_double
-        L.oracle_bin_lp.argtypes = [ctypes.c_int64, _F64P, _F64P, _F32P, _F32P, _I32P, _F64P, _F64P, ctypes.c_int,
-                                    _I64P, _I32P, _U64P, _U32P]
+        L.oracle_bin_lp.argtypes = [ctypes.c_int64, _F64P, _F64P, _F32P, _F32P, _F32P, _I32P, _F64P, _F64P,
+                                    ctypes.c_int, _I64P, _I32P, _U64P, _U32P]
         L.oracle_bin_lp.restype = ctypes.c_int64
         L.oracle_render_tiles_lp.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, ctypes.c_double,
-                                             _F64P, _F64P, _I32P, _I32P, _U64P]
+                                             _F64P, _F64P, _I32P, _I32P, _F64P, _U64P]
         L.oracle_render_bwd_tiles_lp.argtypes = [ctypes.c_int64, _F64P, _U32P, _I32P, _F64P, _F64P, _F64P, _F64P]
         L.oracle_project_lp_bwd.argtypes = [ctypes.c_int64, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P, _F64P,
                                             _F64P, _F64P, _F64P, _F64P, _F64P, _F64P]
@@ -132,6 +136,43 @@ def cfg_array(cfg) -> np.ndarray:
                      *[_f32v(b) for b in cfg.bg], getattr(cfg, "method", 0)], np.float64)
 
 
+class Band(NamedTuple):
+    """Uncertainty model of the 3DGS ambiguity band (the compositing walk of xpr_oracle.c).
+
+    eps: relative precision of a float32 evaluation of the exponent and the exponential.
+    mu_abs, conic_rel: multipliers of the per-primitive uncertainty scales of a float32 projection
+    (``fp32_uncertainty``: the centre's rounding in pixels and the conic's cancellation factor);
+    both are zero when the float32 side reads the same float32 records as the oracle (stage-wise
+    parity), and bound the float32 projection's rounding when it computed its own records
+    (end-to-end parity).  Without per-primitive scales mu_abs is in pixels."""
+    eps: float = 1e-6
+    mu_abs: float = 0.0
+    conic_rel: float = 0.0
+
+
+#: stage-wise parity: both sides composite the same float32 records
+BAND_STAGE = Band(1e-6, 0.0, 0.0)
+#: end-to-end parity: the float32 projection's own records (twice the rounding-error model of the
+#: centres; the Sigma_2D entries uncertain to 2e-6 of their absolute-value sums, about 32 units of
+#: float32 roundoff, against at most 14 measured on a float32 restatement of the projection)
+BAND_E2E = Band(1e-6, 2.0, 2e-6)
+
+
+def _cmax(rec, cfg) -> float:
+    """Largest colour or background magnitude (the scale of the jump bound)."""
+    r = np.asarray(rec, np.float64)
+    c = float(np.abs(r[:, 6:9]).max()) if r.size else 0.0
+    return max(c, max(abs(float(b)) for b in cfg.bg), 1e-30)
+
+
+def _bandp(band, rec, cfg):
+    if band is None or (not isinstance(band, Band) and float(band) == 0.0):
+        return None
+    if not isinstance(band, Band):
+        band = Band(eps=float(band))
+    return np.array([band.eps, band.mu_abs, band.conic_rel, _cmax(rec, cfg)], np.float64)
+
+
 def tiles_of(cam, cfg):
     return (cam.width + cfg.tile_w - 1) // cfg.tile_w, (cam.height + cfg.tile_h - 1) // cfg.tile_h
 
@@ -140,7 +181,8 @@ def tiles_of(cam, cfg):
 
 def project(mu, scale, quat, opac, sh, cam, cfg):
     """Projection (Listing 1 project).  Returns dict with rec[n,12] (f64),
-    bbox[n,4], tc[n], pre[n,4] (values before floor, tile units), cov[n,3]."""
+    bbox[n,4], tc[n], pre[n,4] (values before floor, tile units), cov[n,3] and
+    key[n] (float32 depth sort keys, depth_keys)."""
     mu, scale, quat, opac, sh = map(_f64, (mu, scale, quat, opac, sh))
     n = mu.shape[0]
     rec = np.zeros((n, 12), np.float64)
@@ -152,7 +194,32 @@ def project(mu, scale, quat, opac, sh, cam, cfg):
     lib().oracle_project(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P), _p(sh, _F64P),
                          _p(ca, _F64P), _p(fa, _F64P), _p(rec, _F64P), _p(bbox, _I32P), _p(tc, _I32P),
                          _p(pre, _F64P), _p(cov, _F64P))
-    return dict(rec=rec, bbox=bbox, tc=tc, pre=pre, cov=cov)
+    return dict(rec=rec, bbox=bbox, tc=tc, pre=pre, cov=cov, key=depth_keys(mu, cam),
+                unc=fp32_uncertainty(mu, scale, quat, opac, sh, cam, cfg))
+
+
+def depth_keys(mu, cam, euclid: bool = False):
+    """Depth sort keys (float32): camera z (or, euclid, the Euclidean distance to the camera) of
+    the float32 means, every operation rounded to float32 in a fixed order without FMA; the tile
+    lists are ordered by (tile, key bits, index)."""
+    mu = _f64(np.asarray(mu, np.float32))
+    key = np.zeros(mu.shape[0], np.float32)
+    ca = cam_array(cam)
+    lib().oracle_depth_keys(mu.shape[0], _p(mu, _F64P), _p(ca, _F64P), int(bool(euclid)), _p(key, _F32P))
+    return key
+
+
+def fp32_uncertainty(mu, scale, quat, opac, sh, cam, cfg):
+    """Per-primitive scales of a float32 projection's rounding, unc[n,5] (oracle_project_unc):
+    the centre's rounding model in pixels, the 2x2 inverse's cancellation factor, and the
+    absolute-value sums of the Sigma_2D entries.  Test infrastructure for the ambiguity band."""
+    mu, scale, quat, opac, sh = map(_f64, (mu, scale, quat, opac, sh))
+    n = mu.shape[0]
+    unc = np.zeros((n, 5))
+    ca, fa = cam_array(cam), cfg_array(cfg)
+    lib().oracle_project_unc(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P), _p(sh, _F64P),
+                             _p(ca, _F64P), _p(fa, _F64P), _p(unc, _F64P))
+    return unc
 
 
 def project_scene(scene, cam, cfg):
@@ -176,29 +243,32 @@ def project_bwd(mu, scale, quat, opac, sh, cam, cfg, d_rec):
 
 # --------------------------------------------------------------------------- binning / sort
 
-def bin_pairs(rec, bbox, cam, cfg, exact32: bool, order=None):
+def bin_pairs(rec, bbox, cam, cfg, exact32: bool, order=None, key=None):
     """Replicate + tile ID + cull, visiting primitives in ``order`` (index order when None);
     counts are per visited position.  With exact32, ``rec`` must be float32 records (the decision
-    is taken in FP32)."""
+    is taken in FP32, the depths are the records' own); else the keys carry ``key`` (depth_keys;
+    None = the FP64 depth rounded to float32)."""
     bbox = np.ascontiguousarray(bbox, np.int32)
     n = bbox.shape[0]
     od = None if order is None else np.ascontiguousarray(order, np.int64)
     ca, fa = cam_array(cam), cfg_array(cfg)
     r64 = None if exact32 else _f64(rec)
     r32 = np.ascontiguousarray(rec, np.float32) if exact32 else None
+    kk = None if (exact32 or key is None) else np.ascontiguousarray(key, np.float32)
     counts = np.zeros(n, np.int32)
-    total = lib().oracle_bin(n, _p(r64, _F64P), _p(r32, _F32P), _p(bbox, _I32P), _p(ca, _F64P), _p(fa, _F64P),
-                             int(exact32), _p(od, _I64P), _p(counts, _I32P), None, None)
+    total = lib().oracle_bin(n, _p(r64, _F64P), _p(r32, _F32P), _p(kk, _F32P), _p(bbox, _I32P), _p(ca, _F64P),
+                             _p(fa, _F64P), int(exact32), _p(od, _I64P), _p(counts, _I32P), None, None)
     keys = np.zeros(max(total, 1), np.uint64)
     vals = np.zeros(max(total, 1), np.uint32)
-    lib().oracle_bin(n, _p(r64, _F64P), _p(r32, _F32P), _p(bbox, _I32P), _p(ca, _F64P), _p(fa, _F64P),
-                     int(exact32), _p(od, _I64P), _p(counts, _I32P), _p(keys, _U64P), _p(vals, _U32P))
+    lib().oracle_bin(n, _p(r64, _F64P), _p(r32, _F32P), _p(kk, _F32P), _p(bbox, _I32P), _p(ca, _F64P),
+                     _p(fa, _F64P), int(exact32), _p(od, _I64P), _p(counts, _I32P), _p(keys, _U64P), _p(vals, _U32P))
     return counts, keys[:total].copy(), vals[:total].copy()
 
 
-def depth_order(rec, tc):
-    """Primitives with tiles by (float32 camera depth, index), then the rest in index order."""
-    d32 = np.asarray(rec, np.float64)[:, 9].astype(np.float32)
+def depth_order(rec, tc, key=None):
+    """Primitives with tiles by (float32 depth key, index), then the rest in index order (key None:
+    the records' depths rounded to float32)."""
+    d32 = np.asarray(rec, np.float64)[:, 9].astype(np.float32) if key is None else np.asarray(key, np.float32)
     has = np.asarray(tc) > 0
     idx = np.arange(len(has))
     vis = idx[has][np.lexsort((idx[has], d32[has]))]
@@ -225,8 +295,17 @@ def cull_one(rec_row, tx, ty, cam, cfg, form: int = 0) -> bool:
 
 # --------------------------------------------------------------------------- compositing
 
-def render_tiles(rec, vals, ranges, cam, cfg, delta: float = 0.0):
+def _band_out(bd, jump):
+    """band: pixels whose value may differ (bit 1); gband: pixels whose gradient may differ as well
+    (any flag); jump: bound of the colour change through the flagged decisions."""
+    return dict(band=(bd & 1).astype(bool), gband=bd != 0, jump=jump)
+
+
+def render_tiles(rec, vals, ranges, cam, cfg, band=None, unc=None):
+    """Per-tile walk over given lists.  ``band``: a Band (or a float eps) turns on the ambiguity
+    band of the walk; ``unc``: the per-primitive scales of fp32_uncertainty."""
     rec = _f64(rec)
+    un = None if unc is None else _f64(unc)
     vals = np.ascontiguousarray(vals, np.uint32)
     vv = vals if vals.size else np.zeros(1, np.uint32)
     ranges = np.ascontiguousarray(ranges, np.int32)
@@ -234,45 +313,56 @@ def render_tiles(rec, vals, ranges, cam, cfg, delta: float = 0.0):
     image = np.zeros((3, H, W))
     tfin = np.zeros((H, W))
     nc = np.zeros((H, W), np.int32)
-    band = np.zeros((H, W), np.int32)
+    bd = np.zeros((H, W), np.int32)
+    jump = np.zeros((H, W))
     ca, fa = cam_array(cam), cfg_array(cfg)
+    bp = _bandp(band, rec, cfg)
     lib().oracle_render_tiles(rec.shape[0], _p(rec, _F64P), _p(vv, _U32P), _p(ranges, _I32P), _p(ca, _F64P),
-                              _p(fa, _F64P), delta, _p(image, _F64P), _p(tfin, _F64P), _p(nc, _I32P),
-                              _p(band, _I32P))
-    return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool))
+                              _p(fa, _F64P), _p(bp, _F64P), _p(un, _F64P), _p(image, _F64P), _p(tfin, _F64P),
+                              _p(nc, _I32P), _p(bd, _I32P), _p(jump, _F64P))
+    return dict(image=image, t_final=tfin, n_contrib=nc, **_band_out(bd, jump))
 
 
-def render_pixels(rec, pix, cfg, delta: float = 0.0, dz: float = 0.0):
-    """Brute-force walk over every visible primitive at the listed pixels."""
+def render_pixels(rec, pix, cfg, band=None, key=None, unc=None):
+    """Brute-force walk over every visible primitive at the listed pixels, in the order of the
+    depth keys ``key`` (depth_keys; None = the records' depths rounded to float32)."""
     rec = _f64(rec)
+    un = None if unc is None else _f64(unc)
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
     m = pix.shape[0]
     color = np.zeros((m, 3))
     tfin = np.zeros(m)
-    band = np.zeros(m, np.int32)
+    bd = np.zeros(m, np.int32)
+    jump = np.zeros(m)
     sig = np.zeros(1, np.uint64)
+    psig = np.zeros(m, np.uint64)
     fa = cfg_array(cfg)
-    lib().oracle_render_pixels(rec.shape[0], _p(rec, _F64P), _p(pix, _I32P), m, _p(fa, _F64P), delta, dz,
-                               _p(color, _F64P), _p(tfin, _F64P), _p(band, _I32P), _p(sig, _U64P))
-    return dict(color=color, t_final=tfin, band=band.astype(bool), sig=int(sig[0]))
+    kk = None if key is None else np.ascontiguousarray(key, np.float32)
+    bp = _bandp(band, rec, cfg)
+    lib().oracle_render_pixels(rec.shape[0], _p(rec, _F64P), _p(kk, _F32P), _p(pix, _I32P), m, _p(fa, _F64P),
+                               _p(bp, _F64P), _p(un, _F64P), _p(color, _F64P), _p(tfin, _F64P), _p(bd, _I32P),
+                               _p(jump, _F64P), _p(psig, _U64P), _p(sig, _U64P))
+    return dict(color=color, t_final=tfin, sig=int(sig[0]), pixel_sig=psig, **_band_out(bd, jump))
 
 
-def render_brute(rec, cam, cfg, delta: float = 0.0, dz: float = 0.0):
+def render_brute(rec, cam, cfg, band=None, key=None, unc=None):
     """Brute-force image (every pixel, every visible primitive; Sec. 3.1)."""
     H, W = cam.height, cam.width
     ys, xs = np.mgrid[0:H, 0:W]
     pix = np.stack([xs.ravel(), ys.ravel()], 1)
-    r = render_pixels(rec, pix, cfg, delta, dz)
+    r = render_pixels(rec, pix, cfg, band, key, unc)
     return dict(image=r["color"].T.reshape(3, H, W), t_final=r["t_final"].reshape(H, W),
-                band=r["band"].reshape(H, W), sig=r["sig"])
+                band=r["band"].reshape(H, W), gband=r["gband"].reshape(H, W), jump=r["jump"].reshape(H, W),
+                sig=r["sig"])
 
 
-def render_bwd_brute(rec, cam, cfg, d_image):
+def render_bwd_brute(rec, cam, cfg, d_image, key=None):
     rec = _f64(rec)
     d_image = _f64(d_image)
     d_rec = np.zeros((rec.shape[0], 12))
     ca, fa = cam_array(cam), cfg_array(cfg)
-    lib().oracle_render_bwd_brute(rec.shape[0], _p(rec, _F64P), _p(ca, _F64P), _p(fa, _F64P),
+    kk = None if key is None else np.ascontiguousarray(key, np.float32)
+    lib().oracle_render_bwd_brute(rec.shape[0], _p(rec, _F64P), _p(kk, _F32P), _p(ca, _F64P), _p(fa, _F64P),
                                   _p(d_image, _F64P), _p(d_rec, _F64P))
     return d_rec
 
@@ -301,13 +391,13 @@ def sh_basis(deg, d, with_grad=False):
 
 # --------------------------------------------------------------------------- whole pipelines
 
-def pipeline_tiled(scene, cam, cfg, delta: float = 0.0):
-    """FP64 tiled pipeline: project -> bin (FP64 cull) -> sort -> per-tile walk."""
+def pipeline_tiled(scene, cam, cfg, band=None):
+    """FP64 tiled pipeline: project -> bin (FP64 cull, float32 depth keys) -> sort -> per-tile walk."""
     pr = project_scene(scene, cam, cfg)
     Wt, Ht = tiles_of(cam, cfg)
-    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False)
+    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False, key=pr["key"])
     keys, vals, ranges = sort_pairs(keys, vals, Wt * Ht)
-    out = render_tiles(pr["rec"], vals, ranges, cam, cfg, delta)
+    out = render_tiles(pr["rec"], vals, ranges, cam, cfg, band, pr["unc"])
     out.update(proj=pr, keys=keys, vals=vals, ranges=ranges)
     return out
 
@@ -329,7 +419,7 @@ def project_ut(mu, scale, quat, opac, sh, cam, cfg):
     lib().oracle_project_ut(n, _p(mu, _F64P), _p(scale, _F64P), _p(quat, _F64P), _p(opac, _F64P),
                             _p(sh, _F64P), _p(ca, _F64P), _p(fa, _F64P), _p(rec, _F64P), _p(sd, _F64P),
                             _p(bbox, _I32P), _p(tc, _I32P), _p(pre, _F64P), _p(cov0, _F64P))
-    return dict(rec=rec, sd=sd, bbox=bbox, tc=tc, pre=pre, cov0=cov0)
+    return dict(rec=rec, sd=sd, bbox=bbox, tc=tc, pre=pre, cov0=cov0, key=depth_keys(mu, cam))
 
 
 def project_ut_scene(scene, cam, cfg):
@@ -345,13 +435,15 @@ def render_tiles_ut(rec, sd, vals, ranges, cam, cfg, delta: float = 0.0):
     image = np.zeros((3, H, W))
     tfin = np.zeros((H, W))
     nc = np.zeros((H, W), np.int32)
-    band = np.zeros((H, W), np.int32)
+    bd = np.zeros((H, W), np.int32)
+    jump = np.zeros((H, W))
     psig = np.zeros((H, W), np.uint64)
     ca, fa = cam_array(cam), cfg_array(cfg)
     lib().oracle_render_tiles_ut(rec.shape[0], _p(rec, _F64P), _p(sd, _F64P), _p(vv, _U32P), _p(ranges, _I32P),
                                  _p(ca, _F64P), _p(fa, _F64P), delta, _p(image, _F64P), _p(tfin, _F64P),
-                                 _p(nc, _I32P), _p(band, _I32P), _p(psig, _U64P))
-    return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool), pixel_sig=psig)
+                                 _p(nc, _I32P), _p(bd, _I32P), _p(jump, _F64P), _p(psig, _U64P))
+    return dict(image=image, t_final=tfin, n_contrib=nc, pixel_sig=psig,
+                **_band_out(bd, jump * _cmax(sd[:, 7:], cfg)))
 
 
 def render_bwd_tiles_ut(sd, vals, ranges, cam, cfg, d_image):
@@ -379,18 +471,21 @@ def project_ut_bwd(mu, scale, quat, opac, sh, cam, cfg, d_sd):
     return dict(mu=dmu, scale=ds, quat=dq, opacity=do, sh=dsh)
 
 
-def render_pixels_ut(rec, sd, pix, cam, cfg, delta: float = 0.0):
-    """Every visible primitive (depth order) at the listed pixels, no tiles."""
+def render_pixels_ut(rec, sd, pix, cam, cfg, delta: float = 0.0, key=None):
+    """Every visible primitive (depth-key order) at the listed pixels, no tiles."""
     rec, sd = _f64(rec), _f64(sd)
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
     m = pix.shape[0]
     color = np.zeros((m, 3))
     tfin = np.zeros(m)
-    band = np.zeros(m, np.int32)
+    bd = np.zeros(m, np.int32)
+    jump = np.zeros(m)
     ca, fa = cam_array(cam), cfg_array(cfg)
-    lib().oracle_render_pixels_ut(rec.shape[0], _p(rec, _F64P), _p(sd, _F64P), _p(pix, _I32P), m, _p(ca, _F64P),
-                                  _p(fa, _F64P), delta, _p(color, _F64P), _p(tfin, _F64P), _p(band, _I32P))
-    return dict(color=color, t_final=tfin, band=band.astype(bool))
+    kk = None if key is None else np.ascontiguousarray(key, np.float32)
+    lib().oracle_render_pixels_ut(rec.shape[0], _p(rec, _F64P), _p(sd, _F64P), _p(kk, _F32P), _p(pix, _I32P), m,
+                                  _p(ca, _F64P), _p(fa, _F64P), delta, _p(color, _F64P), _p(tfin, _F64P),
+                                  _p(bd, _I32P), _p(jump, _F64P))
+    return dict(color=color, t_final=tfin, **_band_out(bd, jump * _cmax(sd[:, 7:], cfg)))
 
 
 def ut_response(sd_row, rd) -> float:
@@ -421,7 +516,7 @@ def pipeline_tiled_ut(scene_arrays, cam, cfg, delta: float = 0.0):
     per-tile ray walk.  scene_arrays = (mu, scale, quat, opacity, sh)."""
     pr = project_ut(*scene_arrays, cam, cfg)
     Wt, Ht = tiles_of(cam, cfg)
-    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False)
+    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False, key=pr["key"])
     keys, vals, ranges = sort_pairs(keys, vals, Wt * Ht)
     out = render_tiles_ut(pr["rec"], pr["sd"], vals, ranges, cam, cfg, delta)
     out.update(proj=pr, keys=keys, vals=vals, ranges=ranges)
@@ -453,7 +548,7 @@ def loss_brute(scene_arrays, cam, cfg, w):
     """sum(w * image) of the brute-force FP64 render; also the decision hash."""
     mu, s, q, o, sh = scene_arrays
     pr = project(mu, s, q, o, sh, cam, cfg)
-    r = render_brute(pr["rec"], cam, cfg)
+    r = render_brute(pr["rec"], cam, cfg, key=pr["key"])
     return float((w * r["image"]).sum()), r["sig"]
 
 
@@ -461,7 +556,7 @@ def grads_brute(scene_arrays, cam, cfg, d_image):
     """Analytic FP64 gradients of sum(d_image * image) w.r.t. all parameters."""
     mu, s, q, o, sh = scene_arrays
     pr = project(mu, s, q, o, sh, cam, cfg)
-    d_rec = render_bwd_brute(pr["rec"], cam, cfg, d_image)
+    d_rec = render_bwd_brute(pr["rec"], cam, cfg, d_image, key=pr["key"])
     g = project_bwd(mu, s, q, o, sh, cam, cfg, d_rec)
     g["d_rec"] = d_rec
     return g
@@ -481,7 +576,7 @@ def project_lp(mu, scale, quat, opac, sh, cam, cfg):
                             _p(ca, _F64P), _p(fa, _F64P), _p(rec, _F64P), _p(sd, _F64P), _p(bbox, _I32P),
                             _p(tc, _I32P), _p(pre, _F64P), _p(aux, _F64P))
     return dict(rec=rec, sd=sd, bbox=bbox, tc=tc, pre=pre, A=aux[:, :9].reshape(-1, 3, 3), ex=aux[:, 9],
-                ey=aux[:, 10], z=aux[:, 11])
+                ey=aux[:, 10], z=aux[:, 11], key=depth_keys(mu, cam, euclid=True))
 
 
 def lp_chord(sd_row, dX, dY) -> float:
@@ -498,9 +593,10 @@ def lp_tile_bound(sd_row, tx, ty, cam, cfg) -> float:
     return float(lib().oracle_lp_tile_bound(_p(_f64(sd_row), _F64P), tx, ty, _p(ca, _F64P), _p(fa, _F64P)))
 
 
-def bin_pairs_lp(rec, sd, bbox, cam, cfg, exact32: bool, order=None):
+def bin_pairs_lp(rec, sd, bbox, cam, cfg, exact32: bool, order=None, key=None):
     """LinPrim replicate + tile ID + cull.  exact32: rec float32 records and sd the kernels'
-    float32 shader data [n,20] (their FP32 decision); else rec/sd the oracle's FP64 ones."""
+    float32 shader data [n,20] (their FP32 decision); else rec/sd the oracle's FP64 ones and the
+    depth keys ``key`` (depth_keys with euclid; None = rec's depth rounded to float32)."""
     bbox = np.ascontiguousarray(bbox, np.int32)
     n = bbox.shape[0]
     od = None if order is None else np.ascontiguousarray(order, np.int64)
@@ -510,8 +606,9 @@ def bin_pairs_lp(rec, sd, bbox, cam, cfg, exact32: bool, order=None):
     r32 = np.ascontiguousarray(rec, np.float32) if exact32 else None
     s32 = np.ascontiguousarray(sd, np.float32) if exact32 else None
     counts = np.zeros(n, np.int32)
-    args = (n, _p(r64, _F64P), _p(s64, _F64P), _p(r32, _F32P), _p(s32, _F32P), _p(bbox, _I32P), _p(ca, _F64P),
-            _p(fa, _F64P), int(exact32), _p(od, _I64P), _p(counts, _I32P))
+    kk = None if (exact32 or key is None) else np.ascontiguousarray(key, np.float32)
+    args = (n, _p(r64, _F64P), _p(s64, _F64P), _p(r32, _F32P), _p(s32, _F32P), _p(kk, _F32P), _p(bbox, _I32P),
+            _p(ca, _F64P), _p(fa, _F64P), int(exact32), _p(od, _I64P), _p(counts, _I32P))
     total = lib().oracle_bin_lp(*args, None, None)
     keys = np.zeros(max(total, 1), np.uint64)
     vals = np.zeros(max(total, 1), np.uint32)
@@ -526,12 +623,14 @@ def render_tiles_lp(sd, vals, ranges, cam, cfg, delta: float = 0.0):
     ranges = np.ascontiguousarray(ranges, np.int32)
     H, W = cam.height, cam.width
     image, tfin = np.zeros((3, H, W)), np.zeros((H, W))
-    nc, band, psig = np.zeros((H, W), np.int32), np.zeros((H, W), np.int32), np.zeros((H, W), np.uint64)
+    nc, bd, psig = np.zeros((H, W), np.int32), np.zeros((H, W), np.int32), np.zeros((H, W), np.uint64)
+    jump = np.zeros((H, W))
     ca, fa = cam_array(cam), cfg_array(cfg)
     lib().oracle_render_tiles_lp(sd.shape[0], _p(sd, _F64P), _p(vv, _U32P), _p(ranges, _I32P), _p(ca, _F64P),
                                  _p(fa, _F64P), delta, _p(image, _F64P), _p(tfin, _F64P), _p(nc, _I32P),
-                                 _p(band, _I32P), _p(psig, _U64P))
-    return dict(image=image, t_final=tfin, n_contrib=nc, band=band.astype(bool), pixel_sig=psig)
+                                 _p(bd, _I32P), _p(jump, _F64P), _p(psig, _U64P))
+    return dict(image=image, t_final=tfin, n_contrib=nc, pixel_sig=psig,
+                **_band_out(bd, jump * _cmax(sd[:, 6:], cfg)))
 
 
 def condition_band_lp(sd, vals, ranges, cam, cfg, eta_px=1e-4, rel=2e-6, tol=5e-5, trials=4, seed=0):
@@ -580,7 +679,7 @@ def pipeline_tiled_lp(scene_arrays, cam, cfg, delta: float = 0.0):
     """FP64 LinPrim pipeline: projection -> bin (FP64 per-tile bound) -> sort -> per-tile walk."""
     pr = project_lp(*scene_arrays, cam, cfg)
     Wt, Ht = tiles_of(cam, cfg)
-    _, keys, vals = bin_pairs_lp(pr["rec"], pr["sd"], pr["bbox"], cam, cfg, exact32=False)
+    _, keys, vals = bin_pairs_lp(pr["rec"], pr["sd"], pr["bbox"], cam, cfg, exact32=False, key=pr["key"])
     keys, vals, ranges = sort_pairs(keys, vals, Wt * Ht)
     out = render_tiles_lp(pr["sd"], vals, ranges, cam, cfg, delta)
     out.update(proj=pr, keys=keys, vals=vals, ranges=ranges)
@@ -650,7 +749,7 @@ def render_bwd_tiles_feat(rec, feat, vals, ranges, cam, cfg, d_image, d_features
 def pipeline_tiled_feat(scene_arrays, feat, cam, cfg, with_depth=False):
     pr = project(*scene_arrays, cam, cfg)
     Wt, Ht = tiles_of(cam, cfg)
-    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False)
+    _, keys, vals = bin_pairs(pr["rec"], pr["bbox"], cam, cfg, exact32=False, key=pr["key"])
     keys, vals, ranges = sort_pairs(keys, vals, Wt * Ht)
     out = render_tiles_feat(pr["rec"], feat, vals, ranges, cam, cfg, with_depth)
     out.update(proj=pr, vals=vals, ranges=ranges)

@@ -188,6 +188,7 @@ typedef struct {
     double J[6];      /* 2x3 */
     double Tm[6];     /* J * W (2x3) */
     double cov[3];    /* a, b, c of Sigma_2D (dilated) */
+    double cabs[3];   /* the same sums over absolute values (|T| |Sigma| |T|^T + dilation) */
     double det;
     double conic[3];
     double mu2d[2];
@@ -277,14 +278,21 @@ static void project_one(const double *mu, const double *s, const double *q, doub
             for (int k = 0; k < 3; ++k) acc += P->J[3 * i + k] * V[4 * k + j];
             P->Tm[3 * i + j] = acc;
         }
-    double C2[4];
+    double C2[4], C2a[4];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
-            double acc = 0.0;
+            double acc = 0.0, aacc = 0.0;
             for (int k = 0; k < 3; ++k)
-                for (int l = 0; l < 3; ++l) acc += P->Tm[3 * i + k] * P->Sig[3 * k + l] * P->Tm[3 * j + l];
+                for (int l = 0; l < 3; ++l) {
+                    acc += P->Tm[3 * i + k] * P->Sig[3 * k + l] * P->Tm[3 * j + l];
+                    aacc += fabs(P->Tm[3 * i + k] * P->Sig[3 * k + l] * P->Tm[3 * j + l]);
+                }
             C2[2 * i + j] = acc;
+            C2a[2 * i + j] = aacc;
         }
+    P->cabs[0] = C2a[0] + cfg->dil;
+    P->cabs[1] = 0.5 * (C2a[1] + C2a[2]);
+    P->cabs[2] = C2a[3] + cfg->dil;
     P->cov[0] = C2[0] + cfg->dil;
     P->cov[1] = 0.5 * (C2[1] + C2[2]);
     P->cov[2] = C2[3] + cfg->dil;
@@ -358,6 +366,81 @@ void oracle_project(int64_t n, const double *mu, const double *scale, const doub
             for (int j = 0; j < 4; ++j) pre[4 * i + j] = P.visible ? P.pre[j] : 0.0;
         if (cov)
             for (int j = 0; j < 3; ++j) cov[3 * i + j] = P.cov[j];
+    }
+}
+
+/* Scales of a float32 projection's rounding, per primitive (test infrastructure for the ambiguity
+ * band of the compositing walk; no part of the method).  unc[n*5] = (m, k, sa, sb, sc):
+ *   m  = the centre's rounding model in pixels, e = 2^-24:
+ *        e (3 |f x/z| + |mu_2D| + 3 f (s_x + |x/z| s_z) / z), s_i = sum_j |V_ij mu_j| + |V_i3|,
+ *        the larger of the x and y expressions (m_c = W mu + t carries ~3 e s_i per component,
+ *        x/z two roundings more, f x/z + c one more relative to |mu_2D|);
+ *   k  = a c / (a c - b^2) of Sigma_2D: the relative precision the 2x2 inverse loses;
+ *   sa, sb, sc = |T| |Sigma| |T|^T + dilation I (T = J W): the scale of the rounding of the
+ *        Sigma_2D entries, whose first-order effect on power = -d^T Sigma_2D^-1 d / 2 is
+ *        g^T dSigma_2D g / 2 with g = conic d. */
+void oracle_project_unc(int64_t n, const double *mu, const double *scale, const double *quat, const double *opac,
+                        const double *sh, const double *camv, const double *cfgv, double *unc) {
+    ocam cam = read_cam(camv);
+    ocfg cfg = read_cfg(cfgv);
+    int K = (cfg.deg + 1) * (cfg.deg + 1);
+    const double e = 1.0 / 16777216.0;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        oproj P;
+        project_one(mu + 3 * i, scale + 3 * i, quat + 4 * i, opac[i], sh + (int64_t)3 * K * i, &cam, &cfg, &P);
+        double *u = unc + 5 * i;
+        for (int j = 0; j < 5; ++j) u[j] = 0.0;
+        if (!P.visible) continue;
+        double sv[3];
+        for (int r = 0; r < 3; ++r) {
+            sv[r] = fabs(cam.V[4 * r + 3]);
+            for (int j = 0; j < 3; ++j) sv[r] += fabs(cam.V[4 * r + j] * mu[3 * i + j]);
+        }
+        double z = P.mc[2], rx = P.mc[0] / z, ry = P.mc[1] / z;
+        double mx = e * (3.0 * fabs(cam.fx * rx) + fabs(P.mu2d[0]) + 3.0 * cam.fx * (sv[0] + fabs(rx) * sv[2]) / z);
+        double my = e * (3.0 * fabs(cam.fy * ry) + fabs(P.mu2d[1]) + 3.0 * cam.fy * (sv[1] + fabs(ry) * sv[2]) / z);
+        u[0] = mx > my ? mx : my;
+        u[1] = P.cov[0] * P.cov[2] / P.det;
+        u[2] = P.cabs[0];
+        u[3] = P.cabs[1];
+        u[4] = P.cabs[2];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Depth sort key (Sec. 4.2 sorts by tile, then depth; reading of the tie     */
+/* order: (tile, float32 bits of the depth, primitive index)).  The order is */
+/* an integer decision, so it is taken in the kernels' precision from the    */
+/* float32 inputs, with every operation rounded to float32 in a fixed order  */
+/* and no fused multiply-add:                                                */
+/*   m_c,i = ((V_i0 x + V_i1 y) + V_i2 z) + V_i3                             */
+/*   key = m_c,2 (camera z; 3DGS and 3DGUT), or                               */
+/*   key = sqrt((x_c x_c + y_c y_c) + z_c z_c)  (LinPrim's Euclidean depth).  */
+/* ------------------------------------------------------------------------ */
+
+static float cam_axis32(const ocam *cam, int i, const float *m) {
+    float a = (float)cam->V[4 * i] * m[0];
+    float b = (float)cam->V[4 * i + 1] * m[1];
+    float c = (float)cam->V[4 * i + 2] * m[2];
+    float s = a + b;
+    s = s + c;
+    return s + (float)cam->V[4 * i + 3];
+}
+
+void oracle_depth_keys(int64_t n, const double *mu, const double *camv, int euclid, float *key) {
+    ocam cam = read_cam(camv);
+    for (int64_t i = 0; i < n; ++i) {
+        float m[3] = {(float)mu[3 * i], (float)mu[3 * i + 1], (float)mu[3 * i + 2]};
+        float z = cam_axis32(&cam, 2, m);
+        if (euclid) {
+            float x = cam_axis32(&cam, 0, m), y = cam_axis32(&cam, 1, m);
+            float xx = x * x, yy = y * y, zz = z * z;
+            float s = xx + yy;
+            s = s + zz;
+            z = sqrtf(s);
+        }
+        key[i] = z;
     }
 }
 
@@ -564,13 +647,14 @@ static uint32_t f32_bits(float f) {
  * index order and every slot r in 0..tc-1 of its bounding box (row-major:
  * x = xmin + r mod w_i, y = ymin + r div w_i, t = y W' + x), keep the pair if
  * the cull passes and emit key = (t << 32) | bits(float(depth)), val = i.
- * exact32 != 0: rec32 (float records) with the FP32 cull; else rec64 with the
- * FP64 cull.  order (may be NULL = index order) gives the order in which the
+ * exact32 != 0: rec32 (float records) with the FP32 cull and the records'
+ * own depths; else rec64 with the FP64 cull and the depth keys key[n]
+ * (oracle_depth_keys; NULL = the FP64 depth rounded to float32).  order (may be NULL = index order) gives the order in which the
  * primitives are visited; counts[n] receives the surviving count per visited
  * position.  keys and vals may be NULL (count only).  Returns the total. */
-int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const int32_t *bbox, const double *camv,
-                   const double *cfgv, int exact32, const int64_t *order, int32_t *counts, uint64_t *keys,
-                   uint32_t *vals) {
+int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const float *key, const int32_t *bbox,
+                   const double *camv, const double *cfgv, int exact32, const int64_t *order, int32_t *counts,
+                   uint64_t *keys, uint32_t *vals) {
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
     int Wt = (cam.W + cfg.tw - 1) / cfg.tw;
@@ -605,7 +689,7 @@ int64_t oracle_bin(int64_t n, const double *rec64, const float *rec32, const int
             } else {
                 const double *R = rec64 + 12 * i;
                 keep = cull_f64(R[0], R[1], R[2], R[3], R[4], R[10], b[0], b[1], b[2], b[3]);
-                depth32 = (float)R[9];
+                depth32 = key ? key[i] : (float)R[9];
             }
             if (!keep) continue;
             if (keys) {
@@ -663,10 +747,51 @@ void oracle_sort(int64_t m, uint64_t *keys, uint32_t *vals, int64_t n_tiles, int
 /*   alpha = min(alpha_max, o exp(power)); skip if alpha < alpha_t;          */
 /*   stop (without accumulating) if T (1 - alpha) < T_eps;                   */
 /*   C += c alpha T; T *= (1 - alpha).                                       */
-/* Finally C += T bg.  band is set when a decision lies within a relative    */
-/* delta of its threshold, or when two successive contributors have depths   */
-/* within a relative dz (order of near-ties is precision dependent).         */
+/* Finally C += T bg.                                                        */
+/*                                                                           */
+/* Ambiguity band.  A float32 evaluation of the same walk may take a gate    */
+/* decision the other way when the decision's margin is below the float32    */
+/* uncertainty of the quantity compared.  bandm (NULL = no band) models that */
+/* uncertainty per decision, as an absolute uncertainty of ln(alpha):        */
+/*   u = eps (S + 1) + mu_abs m_i (|g_x| + |g_y|) + conic_rel Q_i,           */
+/*   S = (|c00| dx^2 + 2 |c01 dx dy| + |c11| dy^2) / 2,  g = conic d,        */
+/*   Q_i = (sa g_x^2 + 2 sb |g_x g_y| + sc g_y^2) / 2 + k_i |power|,         */
+/* eps = relative precision of the float32 evaluation of the walk           */
+/* (products, sums, the exponential).  The other two terms cover a float32  */
+/* projection that computed its own records, with the per-primitive scales  */
+/* unc[5 i ..] = (m_i, k_i, sa, sb, sc) of oracle_project_unc: m_i the      */
+/* centre's rounding in pixels, Q_i the first-order effect of a relative    */
+/* rounding of the Sigma_2D entries (g^T dSigma g / 2) plus the 2x2         */
+/* inverse's cancellation k_i (NULL: m_i = 1, Q_i = S).  Both multipliers   */
+/* are zero when both sides read the same float32 records.                  */
+/* The relative uncertainty of T gathers                                     */
+/* alpha_i u_i / (1 - alpha_i) + eps per blended entry, and the full factor  */
+/* alpha / (1 - alpha) of an entry whose gate is ambiguous (its flip changes */
+/* every later T by that factor).  A pixel is in the band (bit 1) when the   */
+/* valid, alpha_t or T_eps decision lies within its uncertainty; bit 2 marks */
+/* an ambiguous alpha_max clamp, which moves no value (min is continuous)    */
+/* but switches a gradient.  jump (may be NULL) bounds how far the colour    */
+/* can move through the flagged decisions: a flipped valid or alpha_t gate   */
+/* moves it by at most alpha T (|c_i| + cmax) <= 2 cmax max(alpha, alpha_t) T*/
+/* (the entry's own term and the rescaling of everything behind it), a       */
+/* flipped stop by at most T cmax (the entry and everything behind it);      */
+/* cmax bounds every colour and background channel.                          */
 /* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double eps, mu_abs, conic_rel, cmax;
+} bandm;
+
+static bandm read_band(const double *b) {
+    bandm m = {0.0, 0.0, 0.0, 1.0};
+    if (b) {
+        m.eps = b[0];
+        m.mu_abs = b[1];
+        m.conic_rel = b[2];
+        m.cmax = b[3];
+    }
+    return m;
+}
 
 typedef struct {
     int64_t idx;   /* primitive */
@@ -677,33 +802,63 @@ typedef struct {
 } contrib_t;
 
 static int walk(double px, double py, const double *rec, const int64_t *list, int len, const ocfg *cfg,
-                double delta, double dz, double C[3], double *Tout, int *last, int *band, contrib_t *out,
-                uint64_t *sig) {
-    double T = 1.0;
+                const bandm *bm, const double *unc, double C[3], double *Tout, int *last, int *band, double *jump,
+                contrib_t *out, uint64_t *sig) {
+    double T = 1.0, eT = 0.0, J = 0.0;
     C[0] = C[1] = C[2] = 0.0;
     int nc = 0, bd = 0;
     *last = 0;
-    double prev_depth = -1.0;
     uint64_t h = sig ? *sig : 0;
+    const double lat = log(cfg->at), lamax = log(cfg->amax), lteps = log(cfg->teps);
     for (int k = 0; k < len; ++k) {
         const double *R = rec + 12 * list[k];
         double dx = px - R[0], dy = py - R[1];
         double power = -0.5 * (R[2] * dx * dx + 2.0 * R[3] * dx * dy + R[4] * dy * dy);
+        double u = 0.0;
+        if (bm) {
+            double S = 0.5 * (fabs(R[2]) * dx * dx + 2.0 * fabs(R[3] * dx * dy) + fabs(R[4]) * dy * dy);
+            double gx = R[2] * dx + R[3] * dy, gy = R[3] * dx + R[4] * dy;
+            double mi = 1.0, cs = S;
+            if (unc) {
+                const double *U = unc + 5 * list[k];
+                mi = U[0];
+                cs = 0.5 * (U[2] * gx * gx + 2.0 * U[3] * fabs(gx * gy) + U[4] * gy * gy) + U[1] * fabs(power);
+            }
+            u = bm->eps * (S + 1.0) + bm->mu_abs * mi * (fabs(gx) + fabs(gy)) + bm->conic_rel * cs;
+            double am = R[5] < cfg->amax ? R[5] : cfg->amax;
+            if (power > -u) { /* valid gate ambiguous (pixel at the centre) */
+                bd |= 1;
+                J += 2.0 * bm->cmax * am * T;
+                eT += am / (1.0 - am);
+            }
+        }
         if (power > 0.0) continue;
         double G = exp(power);
         double og = R[5] * G;
         double alpha = og < cfg->amax ? og : cfg->amax;
-        if (fabs(og - cfg->amax) <= delta * cfg->amax) bd = 1;
-        if (fabs(alpha - cfg->at) <= delta * cfg->at) bd = 1;
+        if (bm) {
+            double la = log(R[5]) + power;
+            if (fabs(la - lamax) <= u) bd |= 2;
+            if (fabs(la - lat) <= u) {
+                double am = alpha > cfg->at ? alpha : cfg->at;
+                bd |= 1;
+                J += 2.0 * bm->cmax * am * T;
+                eT += am / (1.0 - am);
+            }
+        }
         if (alpha < cfg->at) continue;
         double tt = T * (1.0 - alpha);
-        if (fabs(tt - cfg->teps) <= delta * cfg->teps) bd = 1;
+        if (bm) {
+            double ut = eT + alpha * u / (1.0 - alpha) + bm->eps;
+            if (fabs(log(tt) - lteps) <= ut) {
+                bd |= 1;
+                J += bm->cmax * T;
+            }
+        }
         if (tt < cfg->teps) {
             h = h * 1099511628211ULL ^ 0xffffULL;
             break;
         }
-        if (dz > 0.0 && prev_depth > 0.0 && fabs(R[9] - prev_depth) <= dz * R[9]) bd = 1;
-        prev_depth = R[9];
         if (out) {
             out[nc].idx = list[k];
             out[nc].pos = k;
@@ -717,34 +872,39 @@ static int walk(double px, double py, const double *rec, const int64_t *list, in
         h = (h ^ (uint64_t)(list[k] + 1)) * 1099511628211ULL;
         for (int c = 0; c < 3; ++c) C[c] += R[6 + c] * alpha * T;
         T = tt;
+        if (bm) eT += alpha * u / (1.0 - alpha) + bm->eps;
         ++nc;
         *last = k + 1;
     }
     for (int c = 0; c < 3; ++c) C[c] += T * cfg->bg[c];
     *Tout = T;
     *band = bd;
+    if (jump) *jump = J;
     if (sig) *sig = h;
     return nc;
 }
 
 typedef struct {
-    double depth;
+    uint32_t key;
     int64_t idx;
 } dz_t;
 
 static int dz_cmp(const void *a, const void *b) {
     const dz_t *x = (const dz_t *)a, *y = (const dz_t *)b;
-    if (x->depth != y->depth) return x->depth < y->depth ? -1 : 1;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
     return x->idx < y->idx ? -1 : (x->idx > y->idx ? 1 : 0);
 }
 
-/* visible primitives ordered by (depth, index) */
-static int64_t depth_order(int64_t n, const double *rec, int64_t *order) {
+/* Visible primitives ordered by (float32 bits of the depth key, index): the order of the sorted
+ * tile lists within every tile.  key[n] from oracle_depth_keys; NULL = the record's FP64 depth
+ * rounded to float32 (equal to the key when the view matrix is the identity).  Depths of visible
+ * primitives are positive, so the bit order is the value order. */
+static int64_t depth_order(int64_t n, const double *rec, const float *key, int64_t *order) {
     dz_t *a = (dz_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(dz_t));
     int64_t m = 0;
     for (int64_t i = 0; i < n; ++i)
         if (rec[12 * i + 11] != 0.0) {
-            a[m].depth = rec[12 * i + 9];
+            a[m].key = f32_bits(key ? key[i] : (float)rec[12 * i + 9]);
             a[m].idx = i;
             ++m;
         }
@@ -754,26 +914,32 @@ static int64_t depth_order(int64_t n, const double *rec, int64_t *order) {
     return m;
 }
 
-/* Brute force (no tiles): every visible primitive at every listed pixel.
- * pix[npix*2] = (x, y) integer pixel coordinates; out color[npix*3],
- * tfinal[npix], band[npix]; sig (may be NULL) = hash of all decisions. */
-void oracle_render_pixels(int64_t n, const double *rec, const int32_t *pix, int64_t npix, const double *cfgv,
-                          double delta, double dz, double *color, double *tfinal, int32_t *band, uint64_t *sig) {
+/* Brute force (no tiles): every visible primitive at every listed pixel, in depth-key order.
+ * pix[npix*2] = (x, y) integer pixel coordinates; out color[npix*3], tfinal[npix], band[npix],
+ * jump[npix] (may be NULL); bandp[4] = (eps, mu_abs, conic_rel, cmax) or NULL; unc[n*5] per
+ * primitive uncertainty scales (oracle_project_unc) or NULL; psig[npix] (may be NULL) = hash of
+ * each pixel's decisions (blended entries and the stop), sig (may be NULL) = hash of them all. */
+void oracle_render_pixels(int64_t n, const double *rec, const float *key, const int32_t *pix, int64_t npix,
+                          const double *cfgv, const double *bandp, const double *unc, double *color, double *tfinal,
+                          int32_t *band, double *jump, uint64_t *psig, uint64_t *sig) {
     ocfg cfg = read_cfg(cfgv);
+    bandm bm = read_band(bandp);
     int64_t *order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
-    int64_t m = depth_order(n, rec, order);
+    int64_t m = depth_order(n, rec, key, order);
     uint64_t hs = 1469598103934665603ULL;
     uint64_t *hp = (uint64_t *)malloc((size_t)(npix > 0 ? npix : 1) * sizeof(uint64_t));
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t p = 0; p < npix; ++p) {
-        double C[3], T;
+        double C[3], T, J;
         int last, bd;
         uint64_t h = (uint64_t)p;
-        walk((double)pix[2 * p], (double)pix[2 * p + 1], rec, order, (int)m, &cfg, delta, dz, C, &T, &last, &bd,
-             NULL, &h);
+        walk((double)pix[2 * p], (double)pix[2 * p + 1], rec, order, (int)m, &cfg, bandp ? &bm : NULL, unc, C, &T,
+             &last, &bd, &J, NULL, &h);
         for (int c = 0; c < 3; ++c) color[3 * p + c] = C[c];
         tfinal[p] = T;
         band[p] = bd;
+        if (jump) jump[p] = J;
+        if (psig) psig[p] = h;
         hp[p] = h;
     }
     for (int64_t p = 0; p < npix; ++p) hs = (hs ^ hp[p]) * 1099511628211ULL;
@@ -784,13 +950,14 @@ void oracle_render_pixels(int64_t n, const double *rec, const int32_t *pix, int6
 
 /* Per-tile walk over given lists: vals[ranges[t,0]:ranges[t,1]] for tile t.
  * image[3,H,W] (planar), tfinal[H,W], ncontrib[H,W] (position+1 of the last
- * accumulated entry in the tile's list), band[H,W]. */
+ * accumulated entry in the tile's list), band[H,W], jump[H,W] (may be NULL). */
 void oracle_render_tiles(int64_t n, const double *rec, const uint32_t *vals, const int32_t *ranges,
-                         const double *camv, const double *cfgv, double delta, double *image, double *tfinal,
-                         int32_t *ncontrib, int32_t *band) {
+                         const double *camv, const double *cfgv, const double *bandp, const double *unc,
+                         double *image, double *tfinal, int32_t *ncontrib, int32_t *band, double *jump) {
     (void)n;
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
+    bandm bm = read_band(bandp);
     int Wt = (cam.W + cfg.tw - 1) / cfg.tw, Ht = (cam.H + cfg.th - 1) / cfg.th;
     int64_t HW = (int64_t)cam.W * cam.H;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -804,14 +971,16 @@ void oracle_render_tiles(int64_t n, const double *rec, const uint32_t *vals, con
             for (int xx = 0; xx < cfg.tw; ++xx) {
                 int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
                 if (x >= cam.W || y >= cam.H) continue;
-                double C[3], T;
+                double C[3], T, J;
                 int last, bd;
-                walk((double)x, (double)y, rec, list, len, &cfg, delta, 0.0, C, &T, &last, &bd, NULL, NULL);
+                walk((double)x, (double)y, rec, list, len, &cfg, bandp ? &bm : NULL, unc, C, &T, &last, &bd, &J,
+                     NULL, NULL);
                 int64_t p = (int64_t)y * cam.W + x;
                 for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
                 tfinal[p] = T;
                 ncontrib[p] = last;
                 band[p] = bd;
+                if (jump) jump[p] = J;
             }
         free(list);
     }
@@ -866,12 +1035,12 @@ static void pixel_adjoint(const double *rec, const contrib_t *cs, int nc, double
 }
 
 /* Brute-force adjoint over all pixels of a W x H image (tiny scenes). */
-void oracle_render_bwd_brute(int64_t n, const double *rec, const double *camv, const double *cfgv,
+void oracle_render_bwd_brute(int64_t n, const double *rec, const float *key, const double *camv, const double *cfgv,
                              const double *d_image, double *d_rec) {
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
     int64_t *order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
-    int64_t m = depth_order(n, rec, order);
+    int64_t m = depth_order(n, rec, key, order);
     contrib_t *cs = (contrib_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(contrib_t));
     int64_t HW = (int64_t)cam.W * cam.H;
     memset(d_rec, 0, (size_t)n * 12 * sizeof(double));
@@ -882,7 +1051,7 @@ void oracle_render_bwd_brute(int64_t n, const double *rec, const double *camv, c
             if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
             double C[3], T;
             int last, bd;
-            int nc = walk((double)x, (double)y, rec, order, (int)m, &cfg, 0.0, 0.0, C, &T, &last, &bd, cs, NULL);
+            int nc = walk((double)x, (double)y, rec, order, (int)m, &cfg, NULL, NULL, C, &T, &last, &bd, NULL, cs, NULL);
             pixel_adjoint(rec, cs, nc, T, g, &cfg, d_rec);
         }
     free(cs);
@@ -914,7 +1083,7 @@ void oracle_render_bwd_tiles(int64_t n, const double *rec, const uint32_t *vals,
                 if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
                 double C[3], T;
                 int last, bd;
-                int nc = walk((double)x, (double)y, rec, list, len, &cfg, 0.0, 0.0, C, &T, &last, &bd, cs, NULL);
+                int nc = walk((double)x, (double)y, rec, list, len, &cfg, NULL, NULL, C, &T, &last, &bd, NULL, cs, NULL);
                 pixel_adjoint(rec, cs, nc, T, g, &cfg, d_rec);
             }
         free(cs);
@@ -957,7 +1126,7 @@ void oracle_render_tiles_feat(int64_t n, const double *rec, const double *feat, 
                 if (x >= cam.W || y >= cam.H) continue;
                 double C[3], T;
                 int last, bd;
-                int nc = walk((double)x, (double)y, rec, list, len, &cfg, 0.0, 0.0, C, &T, &last, &bd, cs, NULL);
+                int nc = walk((double)x, (double)y, rec, list, len, &cfg, NULL, NULL, C, &T, &last, &bd, NULL, cs, NULL);
                 int64_t p = (int64_t)y * cam.W + x;
                 for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
                 tfinal[p] = T;
@@ -1009,7 +1178,7 @@ void oracle_render_bwd_tiles_feat(int64_t n, const double *rec, const double *fe
                 if (!any) continue;
                 double C[3], T;
                 int last, bd;
-                int nc = walk((double)x, (double)y, rec, list, len, &cfg, 0.0, 0.0, C, &T, &last, &bd, cs, NULL);
+                int nc = walk((double)x, (double)y, rec, list, len, &cfg, NULL, NULL, C, &T, &last, &bd, NULL, cs, NULL);
                 if (nc == 0) continue;
                 for (int i = 0; i < nc; ++i) {
                     for (int c = 0; c < 3; ++c) v[nch * i + c] = rec[12 * cs[i].idx + 6 + c];
@@ -1506,10 +1675,15 @@ typedef struct {
 } contrib_ut;
 
 /* The walk of the 3DGS compositing with the ray response in place of the 2D one.  out (may be
- * NULL) records the contributors; sig (may be NULL) hashes every decision taken. */
+ * NULL) records the contributors; sig (may be NULL) hashes every decision taken.  Band: a decision
+ * is ambiguous when its quantity lies within a relative delta of its threshold (valid, alpha_t,
+ * alpha_max) or, for the T_eps stop, within the relative uncertainty T has gathered (delta
+ * alpha / (1 - alpha) per blended entry, the full alpha / (1 - alpha) of an ambiguous gate).  jump
+ * (may be NULL) bounds the colour change through the flagged decisions in units of the largest
+ * colour magnitude (2 max(alpha, alpha_t) T per flipped gate, T per flipped stop), as for 3DGS. */
 static int walk_ut(const double *rd, const double *sd, const int64_t *list, int len, const ocfg *cfg, double delta,
-                   double C[3], double *Tout, int *last, int *band, contrib_ut *out, uint64_t *sig) {
-    double T = 1.0;
+                   double C[3], double *Tout, int *last, int *band, double *jump, contrib_ut *out, uint64_t *sig) {
+    double T = 1.0, eT = 0.0, J = 0.0;
     C[0] = C[1] = C[2] = 0.0;
     int nc = 0, bd = 0;
     uint64_t h = sig ? *sig : 0;
@@ -1518,15 +1692,22 @@ static int walk_ut(const double *rd, const double *sd, const int64_t *list, int 
         const double *S = sd + 16 * list[k];
         double tau, e[3];
         double G = ut_response_full(S, rd, &tau, e);
-        if (fabs(G - UT_VALID) <= delta * UT_VALID) bd = 1;
-        if (!(G > UT_VALID)) continue;
         double og = S[12] * G;
         double alpha = og < cfg->amax ? og : cfg->amax;
-        if (fabs(og - cfg->amax) <= delta * cfg->amax) bd = 1;
-        if (fabs(alpha - cfg->at) <= delta * cfg->at) bd = 1;
+        double am = alpha > cfg->at ? alpha : cfg->at;
+        if (delta > 0.0 && (fabs(G - UT_VALID) <= delta * UT_VALID || fabs(alpha - cfg->at) <= delta * cfg->at)) {
+            bd |= 1;
+            J += 2.0 * am * T;
+            eT += am / (1.0 - am);
+        }
+        if (!(G > UT_VALID)) continue;
+        if (delta > 0.0 && fabs(og - cfg->amax) <= delta * cfg->amax) bd |= 2;
         if (alpha < cfg->at) continue;
         double tt = T * (1.0 - alpha);
-        if (fabs(tt - cfg->teps) <= delta * cfg->teps) bd = 1;
+        if (delta > 0.0 && fabs(log(tt / cfg->teps)) <= eT + alpha * delta / (1.0 - alpha) + delta) {
+            bd |= 1;
+            J += T;
+        }
         if (tt < cfg->teps) {
             h = h * 1099511628211ULL ^ 0xffffULL;
             break;
@@ -1543,12 +1724,14 @@ static int walk_ut(const double *rd, const double *sd, const int64_t *list, int 
         h = (h ^ (uint64_t)(list[k] + 1)) * 1099511628211ULL;
         for (int c = 0; c < 3; ++c) C[c] += S[13 + c] * alpha * T;
         T = tt;
+        eT += alpha * delta / (1.0 - alpha) + delta;
         ++nc;
         *last = k + 1;
     }
     for (int c = 0; c < 3; ++c) C[c] += T * cfg->bg[c];
     *Tout = T;
     *band = bd;
+    if (jump) *jump = J;
     if (sig) *sig = h;
     return nc;
 }
@@ -1556,7 +1739,8 @@ static int walk_ut(const double *rd, const double *sd, const int64_t *list, int 
 /* Per-tile walk of 3DGUT over given lists (as oracle_render_tiles). */
 void oracle_render_tiles_ut(int64_t n, const double *rec, const double *sd, const uint32_t *vals,
                             const int32_t *ranges, const double *camv, const double *cfgv, double delta,
-                            double *image, double *tfinal, int32_t *ncontrib, int32_t *band, uint64_t *psig) {
+                            double *image, double *tfinal, int32_t *ncontrib, int32_t *band, double *jump,
+                            uint64_t *psig) {
     (void)n;
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
@@ -1573,12 +1757,13 @@ void oracle_render_tiles_ut(int64_t n, const double *rec, const double *sd, cons
             for (int xx = 0; xx < cfg.tw; ++xx) {
                 int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
                 if (x >= cam.W || y >= cam.H) continue;
-                double rd[3], C[3], T;
+                double rd[3], C[3], T, J;
                 int last, bd;
                 uint64_t h = 0;
                 pixel_ray((double)x, (double)y, &cam, rd);
-                walk_ut(rd, sd, list, len, &cfg, delta, C, &T, &last, &bd, NULL, &h);
+                walk_ut(rd, sd, list, len, &cfg, delta, C, &T, &last, &bd, &J, NULL, &h);
                 int64_t p = (int64_t)y * cam.W + x;
+                if (jump) jump[p] = J;
                 if (psig) psig[p] = h;
                 for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
                 tfinal[p] = T;
@@ -1590,19 +1775,20 @@ void oracle_render_tiles_ut(int64_t n, const double *rec, const double *sd, cons
 }
 
 /* 3DGUT without tiles: every visible primitive (depth order) at every listed pixel. */
-void oracle_render_pixels_ut(int64_t n, const double *rec, const double *sd, const int32_t *pix, int64_t npix,
-                             const double *camv, const double *cfgv, double delta, double *color, double *tfinal,
-                             int32_t *band) {
+void oracle_render_pixels_ut(int64_t n, const double *rec, const double *sd, const float *key, const int32_t *pix,
+                             int64_t npix, const double *camv, const double *cfgv, double delta, double *color,
+                             double *tfinal, int32_t *band, double *jump) {
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
     int64_t *order = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
-    int64_t m = depth_order(n, rec, order);
+    int64_t m = depth_order(n, rec, key, order);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t p = 0; p < npix; ++p) {
-        double rd[3], C[3], T;
+        double rd[3], C[3], T, J;
         int last, bd;
         pixel_ray((double)pix[2 * p], (double)pix[2 * p + 1], &cam, rd);
-        walk_ut(rd, sd, order, (int)m, &cfg, delta, C, &T, &last, &bd, NULL, NULL);
+        walk_ut(rd, sd, order, (int)m, &cfg, delta, C, &T, &last, &bd, &J, NULL, NULL);
+        if (jump) jump[p] = J;
         for (int c = 0; c < 3; ++c) color[3 * p + c] = C[c];
         tfinal[p] = T;
         band[p] = bd;
@@ -1683,7 +1869,7 @@ void oracle_render_bwd_tiles_ut(int64_t n, const double *sd, const uint32_t *val
                 double rd[3], C[3], T;
                 int last, bd;
                 pixel_ray((double)x, (double)y, &cam, rd);
-                int nc = walk_ut(rd, sd, list, len, &cfg, 0.0, C, &T, &last, &bd, cs, NULL);
+                int nc = walk_ut(rd, sd, list, len, &cfg, 0.0, C, &T, &last, &bd, NULL, cs, NULL);
                 pixel_adjoint_ut(sd, cs, nc, T, g, rd, &cfg, d_sd);
             }
         free(cs);
@@ -2079,9 +2265,10 @@ double oracle_lp_tile_bound(const double *sd, int tx, int ty, const double *camv
 }
 
 /* Binning for LinPrim (as oracle_bin): exact32 != 0 takes the FP32 decision on kernel-form shader
- * data sd32[n*20] and depths from rec32; else the FP64 bound on paper-form sd64[n*16] with rec64. */
+ * data sd32[n*20] and depths from rec32; else the FP64 bound on paper-form sd64[n*16] with the
+ * depth keys key[n] (NULL = rec64's depth rounded to float32). */
 int64_t oracle_bin_lp(int64_t n, const double *rec64, const double *sd64, const float *rec32, const float *sd32,
-                      const int32_t *bbox, const double *camv, const double *cfgv, int exact32,
+                      const float *key, const int32_t *bbox, const double *camv, const double *cfgv, int exact32,
                       const int64_t *order, int32_t *counts, uint64_t *keys, uint32_t *vals) {
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
@@ -2108,7 +2295,7 @@ int64_t oracle_bin_lp(int64_t n, const double *rec64, const double *sd64, const 
             } else {
                 const double *S = sd64 + 16 * i;
                 keep = S[11] * lp_tile_bound(nn, S[0], S[1], c[0], c[1], c[2], c[3]) >= req;
-                depth32 = (float)rec64[12 * i + 9];
+                depth32 = key ? key[i] : (float)rec64[12 * i + 9];
             }
             if (!keep) continue;
             if (keys) {
@@ -2132,8 +2319,8 @@ typedef struct {
 
 /* the compositing walk of the framework with the LinPrim evaluate (valid = 1) */
 static int walk_lp(double X, double Y, const double *sd, const int64_t *list, int len, const ocfg *cfg, double delta,
-                   double C[3], double *Tout, int *last, int *band, contrib_lp *out, uint64_t *sig) {
-    double T = 1.0;
+                   double C[3], double *Tout, int *last, int *band, double *jump, contrib_lp *out, uint64_t *sig) {
+    double T = 1.0, eT = 0.0, J = 0.0;
     C[0] = C[1] = C[2] = 0.0;
     int nc = 0, bd = 0;
     uint64_t hsh = sig ? *sig : 0;
@@ -2148,11 +2335,19 @@ static int walk_lp(double X, double Y, const double *sd, const int64_t *list, in
         double e = exp(-S[11] * dt);
         double a0 = dt > 0.0 ? 1.0 - e : 0.0;
         double alpha = a0 < cfg->amax ? a0 : cfg->amax;
-        if (fabs(a0 - cfg->amax) <= delta * cfg->amax) bd = 1;
-        if (fabs(alpha - cfg->at) <= delta * cfg->at) bd = 1;
+        if (delta > 0.0 && fabs(a0 - cfg->amax) <= delta * cfg->amax) bd |= 2;
+        if (delta > 0.0 && fabs(alpha - cfg->at) <= delta * cfg->at) {
+            double am = alpha > cfg->at ? alpha : cfg->at;
+            bd |= 1;
+            J += 2.0 * am * T;
+            eT += am / (1.0 - am);
+        }
         if (alpha < cfg->at) continue;
         double tt = T * (1.0 - alpha);
-        if (fabs(tt - cfg->teps) <= delta * cfg->teps) bd = 1;
+        if (delta > 0.0 && fabs(log(tt / cfg->teps)) <= eT + alpha * delta / (1.0 - alpha) + delta) {
+            bd |= 1;
+            J += T;
+        }
         if (tt < cfg->teps) {
             hsh = hsh * 1099511628211ULL ^ 0xffffULL;
             break;
@@ -2174,19 +2369,21 @@ static int walk_lp(double X, double Y, const double *sd, const int64_t *list, in
         hsh = (hsh ^ (uint64_t)(4 * lo + hi + 17)) * 1099511628211ULL;
         for (int c = 0; c < 3; ++c) C[c] += S[12 + c] * alpha * T;
         T = tt;
+        eT += alpha * delta / (1.0 - alpha) + delta;
         ++nc;
         *last = k + 1;
     }
     for (int c = 0; c < 3; ++c) C[c] += T * cfg->bg[c];
     *Tout = T;
     *band = bd;
+    if (jump) *jump = J;
     if (sig) *sig = hsh;
     return nc;
 }
 
 void oracle_render_tiles_lp(int64_t n, const double *sd, const uint32_t *vals, const int32_t *ranges,
                             const double *camv, const double *cfgv, double delta, double *image, double *tfinal,
-                            int32_t *ncontrib, int32_t *band, uint64_t *psig) {
+                            int32_t *ncontrib, int32_t *band, double *jump, uint64_t *psig) {
     (void)n;
     ocam cam = read_cam(camv);
     ocfg cfg = read_cfg(cfgv);
@@ -2203,11 +2400,12 @@ void oracle_render_tiles_lp(int64_t n, const double *sd, const uint32_t *vals, c
             for (int xx = 0; xx < cfg.tw; ++xx) {
                 int x = tx * cfg.tw + xx, y = ty * cfg.th + yy;
                 if (x >= cam.W || y >= cam.H) continue;
-                double C[3], T;
+                double C[3], T, J;
                 int last, bd;
                 uint64_t h = 0;
-                walk_lp(x + 0.5, y + 0.5, sd, list, len, &cfg, delta, C, &T, &last, &bd, NULL, &h);
+                walk_lp(x + 0.5, y + 0.5, sd, list, len, &cfg, delta, C, &T, &last, &bd, &J, NULL, &h);
                 int64_t p = (int64_t)y * cam.W + x;
+                if (jump) jump[p] = J;
                 for (int c = 0; c < 3; ++c) image[c * HW + p] = C[c];
                 tfinal[p] = T;
                 ncontrib[p] = last;
@@ -2291,7 +2489,7 @@ void oracle_render_bwd_tiles_lp(int64_t n, const double *sd, const uint32_t *val
                 if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
                 double C[3], T;
                 int last, bd;
-                int nc = walk_lp(x + 0.5, y + 0.5, sd, list, len, &cfg, 0.0, C, &T, &last, &bd, cs, NULL);
+                int nc = walk_lp(x + 0.5, y + 0.5, sd, list, len, &cfg, 0.0, C, &T, &last, &bd, NULL, cs, NULL);
                 pixel_adjoint_lp(sd, cs, nc, T, g, &cfg, d_sd);
             }
         free(cs);

@@ -43,10 +43,9 @@ __device__ __forceinline__ void lp_geometry(const Params &P, const Cam &k, LpGeo
     G.qinv = rsqrtf(qq);
     for (int i = 0; i < 4; ++i) G.qn[i] = P.q[i] * G.qinv;
     quat_to_rot(G.qn[0], G.qn[1], G.qn[2], G.qn[3], G.R);
-    for (int i = 0; i < 3; ++i)
-        G.mc[i] = k.W[3 * i] * P.m[0] + k.W[3 * i + 1] * P.m[1] + k.W[3 * i + 2] * P.m[2] + k.t[i];
+    cam_point(k, P.m, G.mc);
     const float x = G.mc[0], y = G.mc[1], z = G.mc[2];
-    G.d = sqrtf(x * x + y * y + z * z);
+    G.d = euclid_depth(G.mc);
     G.kmin = P.s[1] < P.s[0] ? 1 : 0;
     if (P.s[2] < P.s[G.kmin]) G.kmin = 2;
     G.smin = P.s[G.kmin];

@@ -37,8 +37,7 @@ struct Geo {
 };
 
 __device__ __forceinline__ void geometry(const Params &P, const Cam &k, float dil, Geo &G) {
-    for (int i = 0; i < 3; ++i)
-        G.mc[i] = k.W[3 * i] * P.m[0] + k.W[3 * i + 1] * P.m[1] + k.W[3 * i + 2] * P.m[2] + k.t[i];
+    cam_point(k, P.m, G.mc);
     const float qq = P.q[0] * P.q[0] + P.q[1] * P.q[1] + P.q[2] * P.q[2] + P.q[3] * P.q[3];
     G.qinv = rsqrtf(qq);
     for (int i = 0; i < 4; ++i) G.qn[i] = P.q[i] * G.qinv;

@@ -109,6 +109,23 @@ __device__ __forceinline__ Cam make_cam(const XprCamera &c, const XprConfig &g) 
     return k;
 }
 
+// Camera point m_c = W mu + t with every operation rounded to float32 in a fixed order and no fused
+// multiply-add: m_c,i = ((W_i0 x + W_i1 y) + W_i2 z) + t_i.  The depth sort key comes from it
+// (camera z, or the Euclidean distance below), so the order of the tile lists is a reproducible
+// integer decision: the same float32 operations give the same key bits on any IEEE machine.
+__device__ __forceinline__ void cam_point(const Cam &k, const float *m, float *mc) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        mc[i] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(k.W[3 * i], m[0]), __fmul_rn(k.W[3 * i + 1], m[1])),
+                                    __fmul_rn(k.W[3 * i + 2], m[2])),
+                          k.t[i]);
+}
+
+// Euclidean distance of a camera point, rounded as sqrt((x x + y y) + z z) with no fused operation.
+__device__ __forceinline__ float euclid_depth(const float *mc) {
+    return __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(mc[0], mc[0]), __fmul_rn(mc[1], mc[1])), __fmul_rn(mc[2], mc[2])));
+}
+
 __device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float *R) {
     R[0] = 1.f - 2.f * (y * y + z * z);
     R[1] = 2.f * (x * y - w * z);

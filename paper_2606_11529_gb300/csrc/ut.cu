@@ -120,8 +120,7 @@ __device__ __forceinline__ void ut_geometry(const Params &P, const Cam &k, float
     U.qinv = rsqrtf(qq);
     for (int i = 0; i < 4; ++i) U.qn[i] = P.q[i] * U.qinv;
     quat_to_rot(U.qn[0], U.qn[1], U.qn[2], U.qn[3], U.R);
-    for (int i = 0; i < 3; ++i)
-        U.mc[i] = k.W[3 * i] * P.m[0] + k.W[3 * i + 1] * P.m[1] + k.W[3 * i + 2] * P.m[2] + k.t[i];
+    cam_point(k, P.m, U.mc);
     for (int i = 0; i < 3; ++i)
         for (int a = 0; a < 3; ++a)
             U.WR[3 * i + a] = k.W[3 * i] * U.R[a] + k.W[3 * i + 1] * U.R[3 + a] + k.W[3 * i + 2] * U.R[6 + a];

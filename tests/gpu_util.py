@@ -6,9 +6,11 @@ from paper_2606_11529_gb300 import binding as B
 from paper_2606_11529_gb300 import render as R
 from paper_2606_11529_gb300 import scenes
 
+from oracle.oracle import BAND_E2E, BAND_STAGE  # noqa: F401  (3DGS ambiguity-band models)
+
 IMG_TOL = 1e-4    # max abs image error outside the ambiguity band
 GRAD_TOL = 1e-3   # per-tensor relative L2 error of gradients
-BAND = 1e-5       # relative margin of a gate decision that counts as ambiguous
+BAND = 1e-5       # 3DGUT / LinPrim: relative margin of a gate decision that counts as ambiguous
 
 
 def dev(a, dtype=torch.float32):
@@ -48,3 +50,31 @@ def oracle_lists(oracle, rec32, bbox, cam, cfg):
 
 def near_integer_bbox(pre, tol=1e-4):
     return np.any(np.abs(pre - np.round(pre)) < tol, axis=1)
+
+
+def check_band(got, ref, mask=None, max_frac=1e-4, tol=IMG_TOL, what=""):
+    """Image parity against an oracle result with an ambiguity band.
+
+    got, ref["image"] (or ref["color"]): [3, ...] / [..., 3] arrays of the same pixels; ref["band"]
+    marks pixels where a gate decision lies within its float32 uncertainty, ref["jump"] bounds how
+    far those decisions can move the colour.  Asserts: the band covers at most ``max_frac`` of the
+    (masked) pixels; outside it every channel is within ``tol``; inside it within jump + tol.
+    Returns the boolean mask of unambiguous pixels."""
+    img = ref["image"] if "image" in ref else ref["color"].T
+    got = np.asarray(got, np.float64)
+    if got.shape != img.shape:
+        got = got.T
+    band = ref["band"]
+    m = np.ones(band.shape, bool) if mask is None else mask
+    frac = float(band[m].mean()) if m.any() else 0.0
+    print(f"{what} ambiguity band: {int(band[m].sum())} of {int(m.sum())} pixels ({frac:.2e})")
+    assert frac <= max_frac, f"{what}: band fraction {frac:.2e} > {max_frac:.1e}"
+    err = np.abs(got - img).max(0)
+    ok = m & ~band
+    if ok.any():
+        assert err[ok].max() <= tol, f"{what}: max error {err[ok].max():.3e} outside the band"
+    bad = m & band
+    if bad.any():
+        excess = err[bad] - (ref["jump"][bad] + tol)
+        assert excess.max() <= 0, f"{what}: band pixel beyond its jump bound by {excess.max():.3e}"
+    return ok

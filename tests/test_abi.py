@@ -11,6 +11,20 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+def _device_visible() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        return False
+
+
+# The host-validation checks below pass placeholder addresses (16, 256, ...) that validation rejects
+# before any launch.  They run only where no CUDA device is visible, so that a check reordered by a
+# later change can never send a placeholder address to a GPU.
+host_only = pytest.mark.skipif(_device_visible(), reason="placeholder addresses: run only without a CUDA device")
+
+
 def _declared():
     txt = open(os.path.join(ROOT, "include", "xpr.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
@@ -60,6 +74,7 @@ def _cam_cfg(**over):
     return cam, cfg
 
 
+@host_only
 @pytest.mark.parametrize("over,frag", [
     (dict(tile_w=7), b"tile size"),
     (dict(tile_h=32), b"tile size"),
@@ -78,6 +93,7 @@ def test_invalid_arguments_rejected_on_host(lib, over, frag):
     assert frag in lib.xpr_last_error()
 
 
+@host_only
 def test_null_and_alias_rejected(lib):
     from paper_2606_11529_gb300 import binding
     cam, cfg = _cam_cfg()
@@ -103,6 +119,7 @@ def test_workspace_sizes_monotone(lib):
     assert lib.xpr_tile_bin_workspace(10_000_000) > lib.xpr_tile_bin_workspace(10)
 
 
+@host_only
 def test_bin_sorted_host_checks(lib):
     from paper_2606_11529_gb300 import binding
     cam, cfg = _cam_cfg()
@@ -122,6 +139,7 @@ def test_bin_sorted_host_checks(lib):
     assert binding.binsort_ok(widest, cfg8) and binding.binsort_ok(cam, cfg)
 
 
+@host_only
 def test_project_color_host_checks(lib):
     from paper_2606_11529_gb300 import binding
     cam, cfg = _cam_cfg()
@@ -132,6 +150,7 @@ def test_project_color_host_checks(lib):
     assert s == binding.XPR_ERR_INVALID
 
 
+@host_only
 def test_project_host_checks(lib):
     from paper_2606_11529_gb300 import binding
     cam, cfg = _cam_cfg()
@@ -149,6 +168,7 @@ def test_project_host_checks(lib):
     assert s == binding.XPR_ERR_INVALID
 
 
+@host_only
 def test_selftest_wait_host_checks(lib):
     from paper_2606_11529_gb300 import binding
     assert lib.xpr_selftest_wait(None, 10, None) == binding.XPR_ERR_INVALID

@@ -11,7 +11,7 @@ from paper_2606_11529_gb300 import binding as B
 from paper_2606_11529_gb300 import render as R
 from paper_2606_11529_gb300 import scenes
 
-from gpu_util import BAND, GRAD_TOL, IMG_TOL, dev, rel_err
+from gpu_util import BAND, BAND_E2E, GRAD_TOL, check_band, dev, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -52,10 +52,8 @@ def test_one_view_against_oracle(oracle):
     cams = _views(2)
     cfg = scenes.RenderConfig(sh_degree=3)
     imgs = BT.forward_views(*R.scene_to_device(sc), cams, cfg).image
-    ref = oracle.pipeline_tiled(sc, cams[1], cfg, delta=BAND)
-    ok = ~ref["band"]
-    assert ok.mean() > 0.99
-    assert np.abs(imgs[1].cpu().numpy()[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
+    ref = oracle.pipeline_tiled(sc, cams[1], cfg, band=BAND_E2E)
+    check_band(imgs[1].cpu().numpy(), ref, max_frac=1e-2, what="batched view 1")
 
 
 def test_worklist_is_descending_permutation():
@@ -147,18 +145,20 @@ def test_config3_full_size_two_views_against_oracle(oracle, method):
         for v in views:
             pr = oracle.project_scene(sc, cams[v], cfg)
             pix = np.stack([rng.integers(0, W, 256), rng.integers(0, H, 256)], 1)
-            ref = oracle.render_pixels(pr["rec"], pix, cfg, delta=BAND, dz=1e-6)
+            # brute force in the kernels' order (float32 depth keys of the rotated, translated
+            # views, computed in the same fixed float32 operation order)
+            ref = oracle.render_pixels(pr["rec"], pix, cfg, band=BAND_E2E, key=pr["key"], unc=pr["unc"])
             got = imgs[v].detach().cpu().numpy()[:, pix[:, 1], pix[:, 0]].T
-            ok = ~ref["band"]
-            # a pixel of this dense uniform scene blends hundreds of primitives, so two successive
-            # contributors with depths within 1e-6 (whose order may differ between float32 and
-            # float64 depths) are common: about 40% of the sampled pixels are set aside for that
-            assert ok.mean() > 0.5
-            assert np.abs(got[ok] - ref["color"][ok]).max() <= IMG_TOL, v
+            # a pixel of this dense scene evaluates hundreds of primitives, so a gate decision within
+            # the float32 uncertainty of the kernels' projection is more frequent here (0.8% of the
+            # sampled pixels of view 5)
+            ok = check_band(got, ref, max_frac=3e-2, what=f"3M / 1600x1064 view {v}")
+            ok &= ~ref["gband"]
             assert (ref["t_final"] < 0.5).mean() > 0.2  # sampled pixels are not mostly empty
             use = pix[ok][:96]
             w[v][:, use[:, 1], use[:, 0]] = rng.normal(size=(3, len(use)))
-            g = oracle.project_bwd(*sc.arrays(), cams[v], cfg, oracle.render_bwd_brute(pr["rec"], cams[v], cfg, w[v]))
+            d_rec = oracle.render_bwd_brute(pr["rec"], cams[v], cfg, w[v], key=pr["key"])
+            g = oracle.project_bwd(*sc.arrays(), cams[v], cfg, d_rec)
             for name in NAMES:
                 g_ref[name] = g_ref[name] + g[name]
     else:
@@ -187,10 +187,9 @@ def test_config3_full_size_two_views_against_oracle(oracle, method):
             for t in tiles:
                 ty, tx = divmod(int(t), Wt)
                 mask[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
-            ok = mask & ~ref["band"]
-            assert ok.sum() > 0.97 * mask.sum()
             got = imgs[v].detach().cpu().numpy()
-            assert np.abs(got[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL, v
+            ok = check_band(got, ref, mask=mask, max_frac=3e-2, what=f"3DGUT view {v} sampled tiles")
+            ok &= ~ref["gband"]
             assert (ref["t_final"][ok] < 0.5).mean() > 0.2
             w[v] = rng.normal(size=(3, H, W)) * ok[None]
             d_sd = oracle.render_bwd_tiles_ut(pr["sd"], vals_v, sub, cams[v], cfg, w[v])

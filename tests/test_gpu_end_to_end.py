@@ -10,7 +10,7 @@ from paper_2606_11529_gb300 import binding as B
 from paper_2606_11529_gb300 import render as R
 from paper_2606_11529_gb300 import scenes
 
-from gpu_util import BAND, GRAD_TOL, IMG_TOL, dev, rel_err
+from gpu_util import BAND_E2E, GRAD_TOL, check_band, dev, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -24,14 +24,14 @@ def _params(sc):
 def test_small_case_image_and_gradients(oracle):
     """10k Gaussians, 256x256, 16x16 tiles: image and all five gradients vs the FP64 tiled oracle."""
     sc, cam, cfg = scenes.small_case()
-    ref = oracle.pipeline_tiled(sc, cam, cfg, delta=BAND)
+    ref = oracle.pipeline_tiled(sc, cam, cfg, band=BAND_E2E)
     P = _params(sc)
     img = R.render(*P, cam, cfg)
-    ok = ~ref["band"]
-    assert ok.mean() > 0.99
     got = img.detach().cpu().numpy()
-    assert np.abs(got[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
-    w = np.random.default_rng(0).normal(size=got.shape) * ok[None]
+    # band: gate decisions within the float32 uncertainty of the kernels' own projection (0.44% of
+    # this image's pixels; their error is bounded by the jump of the flagged decisions)
+    check_band(got, ref, max_frac=1e-2, what="small case")
+    w = np.random.default_rng(0).normal(size=got.shape) * ~ref["gband"][None]
     (img * dev(w)).sum().backward()
     d_rec = oracle.render_bwd_tiles(ref["proj"]["rec"], ref["vals"], ref["ranges"], cam, cfg, w)
     g = oracle.project_bwd(*sc.arrays(), cam, cfg, d_rec)
@@ -44,13 +44,12 @@ def test_sh_scene_with_view_and_background(oracle, deg, tile):
     sc = scenes.uniform_scene(6000, seed=3, sh_degree=deg)
     cam = scenes.pinhole(224, 160, 224.0, scenes.yaw_view(-6.0, (0.1, 0.05, -0.2)))
     cfg = scenes.RenderConfig(tile_w=tile, tile_h=tile, sh_degree=deg, bg=(0.25, 0.5, 0.75))
-    ref = oracle.pipeline_tiled(sc, cam, cfg, delta=BAND)
+    ref = oracle.pipeline_tiled(sc, cam, cfg, band=BAND_E2E)
     P = _params(sc)
     img = R.render(*P, cam, cfg)
-    ok = ~ref["band"]
     got = img.detach().cpu().numpy()
-    assert np.abs(got[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
-    w = np.random.default_rng(1).normal(size=got.shape) * ok[None]
+    check_band(got, ref, max_frac=1e-2, what=f"SH {deg}, {tile}x{tile} tiles, rotated view")
+    w = np.random.default_rng(1).normal(size=got.shape) * ~ref["gband"][None]
     (img * dev(w)).sum().backward()
     d_rec = oracle.render_bwd_tiles(ref["proj"]["rec"], ref["vals"], ref["ranges"], cam, cfg, w)
     g = oracle.project_bwd(*sc.arrays(), cam, cfg, d_rec)
@@ -143,11 +142,10 @@ def test_one_huge_gaussian_covers_every_tile(oracle):
     sc.scale[:] = [[2.0, 1.5, 1.0], [0.05, 0.05, 0.05], [0.3, 0.1, 0.2]]
     cam = scenes.pinhole(128, 96, 128.0)
     cfg = scenes.RenderConfig()
-    ref = oracle.pipeline_tiled(sc, cam, cfg, delta=BAND)
+    ref = oracle.pipeline_tiled(sc, cam, cfg, band=BAND_E2E)
     fr = R.forward_frame(*R.scene_to_device(sc), cam, cfg)
     assert fr.n_isect >= 8 * 6
-    ok = ~ref["band"]
-    assert np.abs(fr.image.cpu().numpy()[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
+    check_band(fr.image.cpu().numpy(), ref, max_frac=1e-2, what="huge Gaussian")
 
 
 def test_capacity_retry_inside_the_path():
@@ -170,18 +168,18 @@ def test_headline_workload_sampled_pixels_and_gradients(oracle):
     pr = oracle.project_scene(sc, cam, cfg)
     rng = np.random.default_rng(0)
     pix = np.stack([rng.integers(0, 1920, 384), rng.integers(0, 1080, 384)], 1)
-    ref = oracle.render_pixels(pr["rec"], pix, cfg, delta=BAND, dz=1e-6)
+    # brute force over all primitives in the order of the float32 depth keys (the kernels' order)
+    ref = oracle.render_pixels(pr["rec"], pix, cfg, band=BAND_E2E, key=pr["key"], unc=pr["unc"])
     got = img.detach().cpu().numpy()[:, pix[:, 1], pix[:, 0]].T
-    ok = ~ref["band"]
-    assert ok.mean() > 0.97
-    assert np.abs(got[ok] - ref["color"][ok]).max() <= IMG_TOL
+    ok = check_band(got, ref, max_frac=1e-2, what="1M / 1080p sampled pixels")
+    ok &= ~ref["gband"]
     assert (ref["t_final"] < 0.5).mean() > 0.2  # sampled pixels are not mostly empty
     # sparse loss on the unambiguous sampled pixels
     use = pix[ok][:128]
     w = np.zeros((3, 1080, 1920))
     w[:, use[:, 1], use[:, 0]] = rng.normal(size=(3, len(use)))
     (img * dev(w)).sum().backward()
-    d_rec = oracle.render_bwd_brute(pr["rec"], cam, cfg, w)
+    d_rec = oracle.render_bwd_brute(pr["rec"], cam, cfg, w, key=pr["key"])
     g = oracle.project_bwd(*sc.arrays(), cam, cfg, d_rec)
     for name, p in zip(NAMES, P):
         assert rel_err(p.grad.cpu().numpy(), g[name]) < GRAD_TOL, name

@@ -8,7 +8,7 @@ from paper_2606_11529_gb300 import binding as B
 from paper_2606_11529_gb300 import render as R
 from paper_2606_11529_gb300 import scenes
 
-from gpu_util import BAND, GRAD_TOL, IMG_TOL, dev, dev_i32, oracle_lists, rel_err
+from gpu_util import BAND_E2E, BAND_STAGE, GRAD_TOL, IMG_TOL, dev, dev_i32, oracle_lists, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -29,14 +29,14 @@ def test_features_match_oracle(oracle, nfeat, depth, tile):
     *_, sv, ranges = oracle_lists(oracle, rec32, pr["bbox"], cam, cfg)
     feat = np.random.default_rng(nfeat).normal(size=(sc.n, nfeat)).astype(np.float32) if nfeat else None
     ref = oracle.render_tiles_feat(rec32, feat, sv, ranges, cam, cfg, with_depth=depth)
-    band = oracle.render_tiles(rec32.astype(np.float64), sv, ranges, cam, cfg, delta=BAND)["band"]
+    band = oracle.render_tiles(rec32.astype(np.float64), sv, ranges, cam, cfg, band=BAND_STAGE)["gband"]
     rec_d, sv_d, rg_d = dev(rec32), dev_i32(sv), dev_i32(ranges)
     img, feats, tf, nc = B.xpr_render_fwd_feat(rec_d, None if feat is None else dev(feat), sv_d, rg_d, cam, cfg,
                                                with_depth=depth)
     img0, _, _ = B.xpr_render_fwd(rec_d, sv_d, rg_d, cam, cfg)
     assert torch.equal(img, img0)  # the colour is the plain compositing, bit for bit
     ok = ~band
-    assert ok.mean() > 0.99
+    assert band.mean() <= 3e-3  # decisions within the float32 precision of the walk itself
     got = feats.cpu().numpy()
     assert got.shape[0] == nfeat + int(depth)
     for c in range(got.shape[0]):
@@ -66,8 +66,8 @@ def test_feature_autograd_against_oracle(oracle):
     img, feats = R.render_features(*P, f, cam, cfg, with_depth=True)
     pr = oracle.project_scene(sc, cam, cfg)
     ref_img = oracle.render_tiles(pr["rec"], *oracle_lists(oracle, pr["rec"].astype(np.float32), pr["bbox"], cam,
-                                                           cfg)[4:], cam, cfg, delta=BAND)
-    ok = ~ref_img["band"]
+                                                           cfg)[4:], cam, cfg, band=BAND_E2E, unc=pr["unc"])
+    ok = ~ref_img["gband"]
     wi = np.random.default_rng(4).normal(size=(3, cam.height, cam.width)) * ok[None]
     wf = np.random.default_rng(5).normal(size=(5, cam.height, cam.width)) * ok[None]
     ((img * dev(wi)).sum() + (feats * dev(wf)).sum()).backward()
@@ -114,14 +114,14 @@ def test_features_headline_sampled_tiles(oracle):
     sub[tiles] = ranges[tiles]
     rec32 = fr.rec.cpu().numpy()
     ref = oracle.render_tiles_feat(rec32, feat, sv, sub, cam, cfg, with_depth=True)
-    band = oracle.render_tiles(rec32.astype(np.float64), sv, sub, cam, cfg, delta=BAND)["band"]
+    band = oracle.render_tiles(rec32.astype(np.float64), sv, sub, cam, cfg, band=BAND_STAGE)["gband"]
     Wt = (cam.width + 15) // 16
     mask = np.zeros((cam.height, cam.width), bool)
     for t in tiles:
         ty, tx = divmod(int(t), Wt)
         mask[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
     ok = mask & ~band
-    assert ok.sum() > 0.97 * mask.sum()
+    assert band[mask].mean() <= 1e-2
     got = feats.cpu().numpy()
     for c in range(9):
         scale = max(1.0, np.abs(ref["features"][c][ok]).max())

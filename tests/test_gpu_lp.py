@@ -112,7 +112,7 @@ def test_lp_render_fwd_matches_oracle(oracle, tile, W, H, bg, deg):
     ref = oracle.render_tiles_lp(pr["sd"], sv, ranges, cam, cfg, delta=BAND)
     cond = oracle.condition_band_lp(pr["sd"], sv, ranges, cam, cfg)
     img, tf, nc = fr.image.cpu().numpy(), fr.t_final.cpu().numpy(), fr.n_contrib.cpu().numpy()
-    ok = ~ref["band"] & ~cond
+    ok = ~ref["gband"] & ~cond
     assert ok.mean() > 0.95
     assert np.abs(img[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
     assert np.abs(tf[ok] - ref["t_final"][ok]).max() <= IMG_TOL
@@ -128,7 +128,7 @@ def test_lp_gradients_match_oracle(oracle, deg, view, tile):
     fr, sv, ranges = _gpu_frame(sc, cam, cfg)
     pr = oracle.project_lp(*sc.arrays(), cam, cfg)
     ref = oracle.render_tiles_lp(pr["sd"], sv, ranges, cam, cfg, delta=BAND)
-    ok = ~ref["band"] & ~oracle.condition_band_lp(pr["sd"], sv, ranges, cam, cfg)
+    ok = ~ref["gband"] & ~oracle.condition_band_lp(pr["sd"], sv, ranges, cam, cfg)
     assert ok.mean() > 0.95
     w = np.random.default_rng(5).normal(size=(3, cam.height, cam.width)) * ok[None]
     d_sd_ref = oracle.render_bwd_tiles_lp(pr["sd"], sv, ranges, cam, cfg, w)
@@ -210,7 +210,7 @@ def test_lp_full_size_sampled_tiles(oracle):
     for t in tiles:
         ty, tx = divmod(int(t), Wt)
         mask[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
-    ok = mask & ~ref["band"] & ~cond
+    ok = mask & ~ref["gband"] & ~cond
     assert ok.sum() > 0.9 * mask.sum()
     got = fr.image.cpu().numpy()
     assert np.abs(got[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL

@@ -11,8 +11,8 @@ from paper_2606_11529_gb300 import binding as B
 from paper_2606_11529_gb300 import render as R
 from paper_2606_11529_gb300 import scenes
 
-from gpu_util import (BAND, GRAD_TOL, IMG_TOL, dev, dev_i32, dev_i64, host_u32, host_u64, near_integer_bbox,
-                      oracle_lists, rel_err)
+from gpu_util import (BAND_STAGE, GRAD_TOL, IMG_TOL, check_band, dev, dev_i32, dev_i64, host_u32, host_u64,
+                      near_integer_bbox, oracle_lists, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -248,12 +248,12 @@ def test_render_fwd_matches_oracle(oracle, tile, W, H, bg):
     sc, cam, cfg = _case(0, tile, W=W, H=H)
     cfg.bg = bg
     rec32, sv, ranges = _stage_inputs(oracle, sc, cam, cfg)
-    ref = oracle.render_tiles(rec32.astype(np.float64), sv, ranges, cam, cfg, delta=BAND)
+    ref = oracle.render_tiles(rec32.astype(np.float64), sv, ranges, cam, cfg, band=BAND_STAGE)
     img, tf, nc = B.xpr_render_fwd(dev(rec32), dev_i32(sv), dev_i32(ranges), cam, cfg)
     img, tf, nc = img.cpu().numpy(), tf.cpu().numpy(), nc.cpu().numpy()
-    ok = ~ref["band"]
-    assert ok.mean() > 0.995
-    assert np.abs(img[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
+    # both sides composite the same float32 records: the band holds only the decisions within the
+    # float32 precision of the walk itself (about 1e-3 of the pixels of this dense scene)
+    ok = check_band(img, ref, max_frac=3e-3, what=f"render fwd {W}x{H}")
     assert np.abs(tf[ok] - ref["t_final"][ok]).max() <= IMG_TOL
     assert (nc[ok] != ref["n_contrib"][ok]).mean() <= 1e-4
     assert (ref["t_final"] < 0.01).mean() > 0.05  # some pixels saturate (early termination exercised)
@@ -264,8 +264,8 @@ def test_render_bwd_matches_oracle(oracle):
     cfg.bg = (0.3, 0.1, 0.6)
     rec32, sv, ranges = _stage_inputs(oracle, sc, cam, cfg)
     rec64 = rec32.astype(np.float64)
-    ref = oracle.render_tiles(rec64, sv, ranges, cam, cfg, delta=BAND)
-    w = np.random.default_rng(5).normal(size=(3, cam.height, cam.width)) * ~ref["band"][None]
+    ref = oracle.render_tiles(rec64, sv, ranges, cam, cfg, band=BAND_STAGE)
+    w = np.random.default_rng(5).normal(size=(3, cam.height, cam.width)) * ~ref["gband"][None]
     d_ref = oracle.render_bwd_tiles(rec64, sv, ranges, cam, cfg, w)
     rec_d, sv_d, rg_d = dev(rec32), dev_i32(sv), dev_i32(ranges)
     _, tf, nc = B.xpr_render_fwd(rec_d, sv_d, rg_d, cam, cfg)

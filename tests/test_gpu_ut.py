@@ -13,7 +13,7 @@ from paper_2606_11529_gb300 import binding as B
 from paper_2606_11529_gb300 import render as R
 from paper_2606_11529_gb300 import scenes
 
-from gpu_util import BAND, GRAD_TOL, IMG_TOL, dev, dev_i32, near_integer_bbox, oracle_lists, rel_err
+from gpu_util import BAND, GRAD_TOL, IMG_TOL, check_band, dev, dev_i32, near_integer_bbox, oracle_lists, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -134,9 +134,7 @@ def test_ut_render_fwd_matches_oracle(oracle, tile, W, H, bg, deg, fish):
     fr, sv, ranges = _gpu_frame(sc, cam, cfg)
     ref = oracle.render_tiles_ut(pr["rec"], pr["sd"], sv, ranges, cam, cfg, delta=BAND)
     img, tf, nc = fr.image.cpu().numpy(), fr.t_final.cpu().numpy(), fr.n_contrib.cpu().numpy()
-    ok = ~ref["band"]
-    assert ok.mean() > 0.99
-    assert np.abs(img[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
+    ok = check_band(img, ref, max_frac=1e-2, what=f"3DGUT fwd {W}x{H}")
     assert np.abs(tf[ok] - ref["t_final"][ok]).max() <= IMG_TOL
     assert (nc[ok] != ref["n_contrib"][ok]).mean() <= 1e-3
     assert (ref["t_final"] < 0.01).mean() > 0.02  # saturated pixels: early termination exercised
@@ -148,7 +146,7 @@ def test_ut_gradients_match_oracle(oracle, deg, view, tile, fish):
     cfg.bg = (0.3, 0.1, 0.6)
     fr, sv, ranges = _gpu_frame(sc, cam, cfg)
     ref = oracle.render_tiles_ut(pr["rec"], pr["sd"], sv, ranges, cam, cfg, delta=BAND)
-    w = np.random.default_rng(5).normal(size=(3, cam.height, cam.width)) * ~ref["band"][None]
+    w = np.random.default_rng(5).normal(size=(3, cam.height, cam.width)) * ~ref["gband"][None]
     d_sd_ref = oracle.render_bwd_tiles_ut(pr["sd"], sv, ranges, cam, cfg, w)
     g_ref = oracle.project_ut_bwd(*sc.arrays(), cam, cfg, d_sd_ref)
     d_sd = B.xpr_render_ut_bwd(fr.sd, fr.vals_sorted, fr.ranges, cam, cfg, fr.t_final, fr.n_contrib, dev(w))
@@ -245,10 +243,9 @@ def test_ut_headline_workload_sampled_tiles(oracle):
     for t in tiles:
         ty, tx = divmod(int(t), Wt)
         mask[ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16] = True
-    ok = mask & ~ref["band"]
-    assert ok.sum() > 0.97 * mask.sum()
     got = fr.image.cpu().numpy()
-    assert np.abs(got[:, ok] - ref["image"][:, ok]).max() <= IMG_TOL
+    ok = check_band(got, ref, mask=mask, max_frac=3e-2, what="3DGUT 1M / 1080p sampled tiles")
+    ok &= ~ref["gband"]
     assert (ref["t_final"][ok] < 0.5).mean() > 0.2  # sampled tiles are not mostly empty
     w = rng.normal(size=(3, cam.height, cam.width)) * ok[None]
     (img * dev(w)).sum().backward()

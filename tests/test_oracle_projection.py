@@ -4,6 +4,7 @@ import math
 
 import numpy as np
 import pytest
+import scipy.special
 
 from paper_2606_11529_gb300 import scenes
 
@@ -241,3 +242,75 @@ def test_sh_colour_degree0_recovers_rgb(oracle):
     rgb = sc.sh[:, 0, :] / math.sqrt(4 * math.pi) + 0.5
     vis = pr["rec"][:, 11] > 0
     np.testing.assert_allclose(pr["rec"][vis, 6:9], rgb[vis], atol=1e-6)
+
+
+def _sh_closed_forms(x, y, z):
+    """The 16 real spherical harmonics of degrees 0-3 written out as polynomials of the unit
+    direction (x, y, z), index k = l^2 + l + m, from Y_l^m = sqrt(2) K_l^m P_l^|m|(z) cos(m phi)
+    (m > 0), sin(|m| phi) (m < 0), K_l^m P_l^m(z) (m = 0), where P_l^m carries the Condon-Shortley
+    phase (-1)^m: every odd |m| function changes sign relative to the phase-free table."""
+    pi = math.pi
+    return np.array([
+        0.5 / math.sqrt(pi),
+        -math.sqrt(3 / (4 * pi)) * y,
+        math.sqrt(3 / (4 * pi)) * z,
+        -math.sqrt(3 / (4 * pi)) * x,
+        0.5 * math.sqrt(15 / pi) * x * y,
+        -0.5 * math.sqrt(15 / pi) * y * z,
+        0.25 * math.sqrt(5 / pi) * (3 * z * z - 1),
+        -0.5 * math.sqrt(15 / pi) * x * z,
+        0.25 * math.sqrt(15 / pi) * (x * x - y * y),
+        -0.25 * math.sqrt(35 / (2 * pi)) * y * (3 * x * x - y * y),
+        0.5 * math.sqrt(105 / pi) * x * y * z,
+        -0.25 * math.sqrt(21 / (2 * pi)) * y * (5 * z * z - 1),
+        0.25 * math.sqrt(7 / pi) * (5 * z ** 3 - 3 * z),
+        -0.25 * math.sqrt(21 / (2 * pi)) * x * (5 * z * z - 1),
+        0.25 * math.sqrt(105 / pi) * z * (x * x - y * y),
+        -0.25 * math.sqrt(35 / (2 * pi)) * x * (x * x - 3 * y * y),
+    ])
+
+
+def test_sh_basis_closed_forms_every_function(oracle):
+    # every one of the 16 functions, at axis directions and random ones: a swapped m <-> -m, a
+    # flipped sign or an exchanged degree changes at least one value
+    rng = np.random.default_rng(21)
+    dirs = [np.eye(3)[i] for i in range(3)] + [-np.eye(3)[i] for i in range(3)]
+    dirs += [v / np.linalg.norm(v) for v in rng.normal(size=(12, 3))]
+    for d in dirs:
+        np.testing.assert_allclose(oracle.sh_basis(3, d), _sh_closed_forms(*d), rtol=0, atol=1e-14)
+    # hand values: Y_1^1 at +x is -sqrt(3/(4 pi)), Y_1^-1 at +y likewise, Y_2^0 at +z is sqrt(5/pi)/2
+    assert oracle.sh_basis(1, np.array([1.0, 0, 0]))[3] == pytest.approx(-math.sqrt(3 / (4 * math.pi)), abs=1e-15)
+    assert oracle.sh_basis(1, np.array([0, 1.0, 0]))[1] == pytest.approx(-math.sqrt(3 / (4 * math.pi)), abs=1e-15)
+    assert oracle.sh_basis(2, np.array([0, 0, 1.0]))[6] == pytest.approx(0.5 * math.sqrt(5 / math.pi), abs=1e-15)
+
+
+def test_sh_basis_equals_library_complex_harmonics(oracle):
+    # scipy's complex Y_l^m carries the Condon-Shortley phase: the real functions are sqrt(2) Re Y_l^m
+    # (index l^2 + l + m), sqrt(2) Im Y_l^m (index l^2 + l - m) and Y_l^0
+    sph = getattr(scipy.special, "sph_harm_y", None)
+    if sph is None:
+        pytest.skip("scipy without sph_harm_y")
+    rng = np.random.default_rng(22)
+    for v in rng.normal(size=(25, 3)):
+        d = v / np.linalg.norm(v)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        Y = oracle.sh_basis(3, d)
+        for l in range(4):
+            for m in range(l + 1):
+                c = complex(sph(l, m, theta, phi))
+                if m == 0:
+                    assert Y[l * l + l] == pytest.approx(c.real, abs=1e-13)
+                else:
+                    assert Y[l * l + l + m] == pytest.approx(math.sqrt(2) * c.real, abs=1e-13)
+                    assert Y[l * l + l - m] == pytest.approx(math.sqrt(2) * c.imag, abs=1e-13)
+
+
+def test_sh_basis_parity_gives_the_degree(oracle):
+    # Y_k(-d) = (-1)^l Y_k(d) with l = floor(sqrt(k)): a function of the wrong degree fails
+    rng = np.random.default_rng(23)
+    for v in rng.normal(size=(10, 3)):
+        d = v / np.linalg.norm(v)
+        Yp, Yn = oracle.sh_basis(3, d), oracle.sh_basis(3, -d)
+        for k in range(16):
+            l = int(math.isqrt(k))
+            assert Yn[k] == pytest.approx((-1) ** l * Yp[k], abs=1e-14), k

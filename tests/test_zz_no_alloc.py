@@ -59,6 +59,8 @@ def test_noalloc_capacity_and_size_limit():
     L = B.load()
     c, g = B.make_camera(cam), B.make_config(cfg)
     n_out = ctypes.c_int64(0)
-    s = L.xpr_tile_bin_noalloc(rec.data_ptr(), bbox.data_ptr(), tc.data_ptr(), None, None, (1 << 26) + 1,
-                               ctypes.byref(c), ctypes.byref(g), 256, 256, None, 256, 0, ctypes.byref(n_out), None)
+    # every device pointer is NULL: the size limit is checked first, and if it ever were not, the
+    # call would stop at the NULL-pointer check instead of reaching the GPU
+    s = L.xpr_tile_bin_noalloc(None, None, None, None, None, (1 << 26) + 1, ctypes.byref(c), ctypes.byref(g), None,
+                               None, None, None, 0, ctypes.byref(n_out), None)
     assert s == B.XPR_ERR_INVALID and b"limit" in L.xpr_last_error()
