@@ -44,19 +44,30 @@ BWD_OPS_PER_PAIR = 39
 # stages that are one kernel launch (the render adjoint's bracket also holds the zero-fill of d_rec)
 SINGLE_KERNEL = {"project": "project_fwd_kernel<3>", "render_fwd": "render_fwd_kernel<16,16>",
                  "render_bwd": "render_bwd_kernel<16,16>", "project_bwd": "project_bwd_kernel<3>"}
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernel, and where it is
-TRAFFIC = {"render_bwd_kernel<16,16>": 45_103_616, "render_fwd_kernel<16,16>": 10_272_256}  # bytes
-TRAFFIC_SOURCE = {"render_bwd_kernel<16,16>": "profiles/render_bwd_headline.md",
-                  "render_fwd_kernel<16,16>": "profiles/render_fwd_headline.md",
-                  "project_bwd_kernel<3>": "profiles/project_bwd_headline.md",
-                  "project_fwd_kernel<3>": "profiles/project_fwd_headline.md"}
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture, the profile summary that
+# holds it, and the sha256 (first 16 hex digits) of the kernel's source file when it was captured:
+# the figure is reported only while that source is unchanged (null once the kernel has changed).
+TRAFFIC = {}
+FP32_LANES = 128  # FP32 lanes per SM (4 partitions x 32)
+DEFAULT_SM_MHZ = 2070.0  # maximum SM clock, used when no clock sample exists
 # 3DGUT ray evaluation: FP32-pipe operations per (pixel, entry) pair
 UT_FWD_OPS_PER_PAIR = 31
 UT_BWD_OPS_PER_PAIR = 66
 # LinPrim slab intersection: FP32-pipe operations per (pixel, entry) pair
 LP_FWD_OPS_PER_PAIR = 39
 LP_BWD_OPS_PER_PAIR = 97
+
+
+# SM count read from the device and the SM clock the ALU peak is taken at (the median sampled
+# under load in the timed region once known)
+_ALU = {"sms": None, "mhz": DEFAULT_SM_MHZ, "mhz_source": "maximum SM clock (no sample yet)"}
+
+
+def set_alu_peak(dev, sm_mhz=None, source=None):
+    import torch
+    _ALU["sms"] = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    if sm_mhz:
+        _ALU["mhz"], _ALU["mhz_source"] = float(sm_mhz), source or "median sampled SM clock in the timed region"
 
 
 def peaks():
@@ -67,8 +78,27 @@ def peaks():
         p = {"hbm_gbs": float(j["hbm_gbs"]), "source": "measured"}
     except Exception:
         pass
-    p["alu_ops"] = SMS * FP32_LANES * SM_MAX_MHZ * 1e6  # FP32 lane-ops/s at the maximum SM clock
+    sms = _ALU["sms"] or 152
+    # FP32 lane-ops/s (an FMA counted as one operation): SMs x 128 lanes x SM clock
+    p["alu_ops"] = sms * FP32_LANES * _ALU["mhz"] * 1e6
+    p["alu_desc"] = (f"{sms} SMs (device properties) x {FP32_LANES} FP32 lanes x {_ALU['mhz']:.0f} MHz "
+                     f"({_ALU['mhz_source']}), FP32 lane-ops/s, derived")
     return p
+
+
+def traffic_of(kernel):
+    """ncu DRAM bytes per launch of ``kernel`` if its source is unchanged since the capture."""
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if t is None:
+        return None, None
+    nbytes, profile, src, sha = t
+    try:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            cur = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None, None
+    return (nbytes, profile) if cur == sha else (None, None)
 
 
 # --------------------------------------------------------------------------- clocks
@@ -149,6 +179,12 @@ class ClockSampler:
                 "samples": len(sel), "scope": scope}
 
 
+def workload_config(sc, cam, cfg):
+    """The workload's description, the same dict on both arms."""
+    return {"workload": WORKLOAD, "primitives": sc.n, "sh_degree": cfg.sh_degree,
+            "resolution": [cam.width, cam.height], "tile": [cfg.tile_w, cfg.tile_h]}
+
+
 # --------------------------------------------------------------------------- reference arm (oracle on CPU)
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -157,20 +193,22 @@ def run_reference(args):
     from oracle import baseline
     from paper_2606_11529_gb300 import scenes
     sc, cam, cfg = scenes.headline_case()
+    # every step is one whole forward + backward of the workload (all primitives, all tiles), timed
+    # on the host cores as the oracle stands: nothing is sampled or extrapolated
     for _ in range(args.warmup):
-        baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=0.05, n_tiles=512, seed=123)
-    ests, meas = [], 0.0
+        baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=1.0, n_tiles=1 << 30, seed=0)
+    ests = []
     desc = ""
     for k in range(args.steps):
-        est, m, desc = baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=0.05, n_tiles=512, seed=k)
+        est, m, desc = baseline.estimate_fwd_bwd_seconds(sc, cam, cfg, prim_frac=1.0, n_tiles=1 << 30, seed=k)
         ests.append(est)
-        meas += m
+    baseline.release_lists()
     ms = 1000.0 * statistics.mean(ests)
     cores = baseline.threads()
     out = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD},
+           "config": workload_config(sc, cam, cfg),
            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
            "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -481,6 +519,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     L = B.load()
+    set_alu_peak(dev)
 
     if args.ut_only or args.lp_only or args.feat_only:
         flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -533,6 +572,8 @@ def main():
     wall = time.perf_counter() - t_wall
     clocks.mark(t_epoch0, time.time())
     clk = clocks.stop()
+    if clk.get("sm_mhz"):
+        set_alu_peak(dev, clk["sm_mhz"])
     launches = int(L.xpr_launch_count() - launches0)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
@@ -549,22 +590,30 @@ def main():
     pairs = int(fr.n_contrib.to(torch.int64).sum().item())
     I = fr.n_isect
     n = sc.n
-    passes = math.ceil(max(1, (fr.ranges.shape[0] - 1).bit_length()) / 8)  # tile bits only (depth-ordered input)
+    T = int(fr.ranges.shape[0])
+    passes = math.ceil(max(1, (T - 1).bit_length()) / 8)  # tile bits only (depth-ordered input)
     pk = peaks()
+    # Algorithmic bytes per stage (what the method must move, the per-unit figures of the design
+    # notes); "impl" is what the implementation moves when it differs.
     work = {
-        "project": ("hbm", n * (PARAM_BYTES + REC_BYTES + 16 + 4)),
-        "depth_order": ("hbm", n * (4 + 4 + 4) + 4 * n * 24),  # key build + 4 passes over 12-byte pairs
-        # fused bin + sort: read order, box, tile count and record per primitive; write one u32 per
-        # kept pair and one [start, end) per tile
-        "bin_sort": ("hbm", n * (4 + 16 + 4 + REC_BYTES) + I * 4 + fr.ranges.shape[0] * 8),
-        "tile_bin": ("hbm", n * 2 * (REC_BYTES + 16 + 4) + n * 4 + I * 12),
-        "sort": ("hbm", passes * 24 * I),
-        "render_fwd": ("alu", pairs * FWD_OPS_PER_PAIR),
-        "render_bwd": ("alu", pairs * BWD_OPS_PER_PAIR),
-        "project_bwd": ("hbm", n * (2 * PARAM_BYTES + REC_BYTES)),
+        "project": ("hbm", n * (PARAM_BYTES + REC_BYTES + 16 + 4), None),
+        # one radix pass over (key, index) pairs: read the depth and tile count, read + write 8 B
+        # pairs, write the order
+        "depth_order": ("hbm", n * (8 + 16 + 4), None),
+        # bin: read each primitive's record, box and count, write 12 B per kept pair (u64 key + u32
+        # value) and the offsets
+        "tile_bin": ("hbm", n * (REC_BYTES + 16 + 4 + 4) + I * 12, None),
+        # sort: one read and one write of 12 B per kept pair (the lower bound of one pass)
+        "sort": ("hbm", 24 * I, {"passes": passes, "bytes": passes * 16 * I + passes * 4 * I}),
+        # fused bin + sort: the bin's reads plus one write of the sorted lists (4 B per kept pair) and
+        # the tile ranges
+        "bin_sort": ("hbm", n * (REC_BYTES + 16 + 4 + 4) + I * 4 + T * 8, None),
+        "render_fwd": ("alu", pairs * FWD_OPS_PER_PAIR, None),
+        "render_bwd": ("alu", pairs * BWD_OPS_PER_PAIR, None),
+        "project_bwd": ("hbm", n * (2 * PARAM_BYTES + REC_BYTES), None),
     }
     stages = {}
-    for name, (bound, amount) in work.items():
+    for name, (bound, amount, impl) in work.items():
         t = stage_ms.get(name)
         if not t:
             continue
@@ -572,6 +621,10 @@ def main():
             ach = amount / (t * 1e-3) / 1e9
             stages[name] = {"ms": round(t, 4), "bound": "hbm", "achieved_gbs": round(ach, 1),
                             "frac": round(ach / pk["hbm_gbs"], 4)}
+            if impl:
+                ib = impl["bytes"] / (t * 1e-3) / 1e9
+                stages[name]["impl"] = {"passes": impl["passes"], "bytes": impl["bytes"], "gbs": round(ib, 1),
+                                        "frac": round(ib / pk["hbm_gbs"], 4)}
         else:
             ach = amount / (t * 1e-3)
             stages[name] = {"ms": round(t, 4), "bound": "alu", "achieved_tops": round(ach / 1e12, 3),
@@ -581,7 +634,7 @@ def main():
     dom = max(single, key=lambda k: single[k]["ms"])
     d = stages[dom]
     kname = SINGLE_KERNEL[dom]
-    traffic = TRAFFIC.get(kname)
+    traffic, traffic_src = traffic_of(kname)
     if d["bound"] == "hbm":
         roof = {"kernel": kname, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": d["frac"], "traffic": traffic,
@@ -589,10 +642,9 @@ def main():
     else:
         roof = {"kernel": kname, "bound": "alu", "achieved": d["achieved_tops"],
                 "peak": round(pk["alu_ops"] / 1e12, 2), "unit": "TOP/s", "frac": d["frac"], "traffic": traffic,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (FP32 lane-ops/s), derived"}
+                "peak_source": pk["alu_desc"], "sms": _ALU["sms"], "peak_sm_mhz": _ALU["mhz"]}
     roof["timing"] = "CUDA events around the C-ABI call on the launching stream, mean over the timed steps"
-    if traffic is not None:
-        roof["traffic_source"] = TRAFFIC_SOURCE[kname]
+    roof["traffic_source"] = traffic_src or "null: no ncu capture of the kernel's current source"
 
     # end to end through the public API: pinned H2D of the step's inputs, fwd+bwd, D2H of the loss
     e2e_s = torch.cuda.Event(enable_timing=True)
@@ -617,10 +669,39 @@ def main():
     e2e_e.record()
     torch.cuda.synchronize()
     e2e_ms = e2e_s.elapsed_time(e2e_e) / args.steps
+
+    # the same, also bringing every output back: the image and all five parameter gradients copied
+    # into pinned host buffers inside each step (for a caller whose optimiser runs on the host)
+    img_host = torch.empty((3, cam.height, cam.width), dtype=torch.float32).pin_memory()
+    grad_host = [torch.empty_like(h).pin_memory() for h in host]
+    d2h_full = img_host.numel() * 4 + sum(g.numel() * 4 for g in grad_host)
+
+    def step_out():
+        for p in P:
+            p.grad = None
+        img = R.render(*P, cam, cfg, ws)
+        loss = (img * w).sum()
+        loss.backward()
+        img_host.copy_(img.detach(), non_blocking=True)
+        for g, p in zip(grad_host, P):
+            g.copy_(p.grad, non_blocking=True)
+        return loss
+
+    upload_inputs()
+    step_out()
+    torch.cuda.synchronize()
+    e2e_s.record()
+    for k in range(args.steps):
+        upload_inputs()
+        loss = step_out()
+        _ = loss.item()
+    e2e_e.record()
+    torch.cuda.synchronize()
+    e2e_full_ms = e2e_s.elapsed_time(e2e_e) / args.steps
     if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
+        t = torch.tensor([e2e_ms, e2e_full_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms, e2e_full_ms = float(t[0].item()), float(t[1].item())
 
     del fr
     # the same step with the fused bin + sort (xpr_bin_sorted in place of xpr_tile_bin + xpr_sort_tiles)
@@ -653,12 +734,12 @@ def main():
             "metric": METRIC, "value": round(ms, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "primitives": n, "resolution": [cam.width, cam.height],
-                       "tile": [cfg.tile_w, cfg.tile_h], "intersections": I, "pairs_blended": pairs,
-                       "views_per_s_total": round(world * 1000.0 / ms, 2),
-                       "fused_bin_sort_path_ms": round(key_ms, 4),
-                       "l2": "flushed between steps (256 MB write outside the timed events)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": workload_config(sc, cam, cfg),
+            "workload_stats": {"intersections": I, "pairs_blended": pairs,
+                               "views_per_s_total": round(world * 1000.0 / ms, 2),
+                               "fused_bin_sort_path_ms": round(key_ms, 4)},
+            "l2": "flushed between steps (256 MB write outside the timed events)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "roofline": roof,
             "stages": stages,
             "batched": batched,
@@ -668,7 +749,12 @@ def main():
             "linprim": lp,
             "features": feat,
             "cpu_baseline": cpu,
-            "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
+            "e2e": {"value": round(e2e_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4,
+                    "note": "the gradients stay on the device (for an on-device optimiser); only the loss is read back",
+                    "with_outputs_d2h": {"value": round(e2e_full_ms, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                                         "d2h_bytes_per_step": d2h_full + 4,
+                                         "note": "image and all five parameter gradients copied to pinned host "
+                                                 "memory inside each step"}},
             "gpu_launches": launches,
             "clocks": clk,
             "wall_s": round(wall, 3),

@@ -123,9 +123,9 @@ def test_workspace_sizes_monotone(lib):
 def test_bin_sorted_host_checks(lib):
     from paper_2606_11529_gb300 import binding
     cam, cfg = _cam_cfg()
-    ws = lib.xpr_bin_sorted_workspace(1000, 1, ctypes.byref(cam), ctypes.byref(cfg))
-    assert ws > 1000 * 8
-    assert lib.xpr_bin_sorted_workspace(1000, 3, ctypes.byref(cam), ctypes.byref(cfg)) > ws
+    ws = lib.xpr_bin_sorted_workspace(100_000, 1, ctypes.byref(cam), ctypes.byref(cfg))
+    assert ws > 0
+    assert lib.xpr_bin_sorted_workspace(100_000, 3, ctypes.byref(cam), ctypes.byref(cfg)) > ws
     assert lib.xpr_bin_sorted_workspace(1000, 17, ctypes.byref(cam), ctypes.byref(cfg)) == 0
     n = ctypes.c_int64(0)
     s = lib.xpr_bin_sorted(256, 256, 256, 256, 10, 1, ctypes.byref(cam), ctypes.byref(cfg), None, 256, 100,
@@ -174,3 +174,21 @@ def test_selftest_wait_host_checks(lib):
     assert lib.xpr_selftest_wait(None, 10, None) == binding.XPR_ERR_INVALID
     for polls in (0, (1 << 20) + 1):
         assert lib.xpr_selftest_wait(16, polls, None) == binding.XPR_ERR_INVALID
+
+
+@host_only
+def test_items_host_checks(lib):
+    # offsets that are not the running sums, or too many items, are refused before any device work
+    from paper_2606_11529_gb300 import binding, scenes
+    cfg = binding.make_config(scenes.RenderConfig())
+    cams = [scenes.pinhole(64, 48, 64.0), scenes.pinhole(32, 32, 32.0)]
+    lay = binding.ItemLayout([0, 100], [100, 50], cams, cfg)
+    assert lay.R == 128 + 64 and lay.S == 4 * 3 + 2 * 2 and lay.pixels == 64 * 48 + 32 * 32
+    assert lib.xpr_bin_sorted_items_workspace(lay.carr, lay.arr, 2, ctypes.byref(cfg)) > 0
+    lay.arr[1].rec_offset = 100  # not padded to a multiple of 32
+    assert lib.xpr_bin_sorted_items_workspace(lay.carr, lay.arr, 2, ctypes.byref(cfg)) == 0
+    p = binding.XprPrims(None, None, None, None, None)
+    s = lib.xpr_project_items(ctypes.byref(p), lay.carr, lay.arr, 2, ctypes.byref(cfg), None, None, None, None)
+    assert s == binding.XPR_ERR_INVALID and b"running sums" in lib.xpr_last_error()
+    s = lib.xpr_project_items(ctypes.byref(p), lay.carr, lay.arr, 17, ctypes.byref(cfg), None, None, None, None)
+    assert s == binding.XPR_ERR_INVALID
