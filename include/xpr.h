@@ -119,6 +119,27 @@ typedef struct XprPrimsGrad {
  *   (nonzero only from rendered depth, xpr_render_bwd_feat), rest 0. */
 #define XPR_REC_FLOATS 12
 
+/* One item of a multi-scene launch: a scene (a range of primitives of the
+ * concatenated parameter arrays) seen by one camera.  Items are listed in
+ * order; every offset is the previous item's plus its size:
+ *   prim_offset, n: the scene's primitives [prim_offset, prim_offset + n) of
+ *     the concatenated XprPrims arrays (several items may name one scene);
+ *   rec_offset: the item's first record; records are item-major and each
+ *     item's block is padded to a multiple of 32 records (item k + 1 starts at
+ *     rec_offset + ceil(n / 32) 32), the padding records being invisible;
+ *   tile_offset: the item's first global tile id (item k + 1 starts at
+ *     tile_offset + tiles_x tiles_y of item k's camera);
+ *   pix_offset: the item's first pixel in the per-pixel buffers (t_final,
+ *     n_contrib: pix_offset + W H of the next; image planes [3, H, W] at
+ *     3 pix_offset floats). */
+typedef struct XprItem {
+    int64_t prim_offset;
+    int64_t n;
+    int64_t rec_offset;
+    int64_t tile_offset;
+    int64_t pix_offset;
+} XprItem;
+
 /* ---- Preprocess ----------------------------------------------------------
  * xpr_project: Listing 1 project for n primitives (Sec. 4.1 Preprocess):
  * camera-space mean, Sigma = R S S^T R^T, EWA footprint Sigma_2D = J W Sigma
@@ -311,6 +332,49 @@ int xpr_render_bwd_views(const float *rec, int64_t n, int32_t n_views, const uin
 int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cams, int32_t n_views,
                           const XprConfig *cfg, const float *d_rec, const XprPrimsGrad *d_prims, void *stream);
 
+/* ---- Multi-scene batched form (3DGS) -------------------------------------------
+ * K items (1 <= K <= 16), each a (scene, camera) pair with its own primitive
+ * count and image size (XprItem), run through one launch per stage; per item
+ * the result is exactly what the single-view calls compute for that scene and
+ * camera (records, sorted lists, image, gradients), so a batch can mix scenes
+ * of uneven size and requests of different resolutions (the paper's
+ * trip-count binning, Sec. 4.3, made dynamic over all items' tiles).
+ * cams, items: HOST arrays of K entries; R = the records of all items
+ * (the last rec_offset + its padded size).
+ *   xpr_project_items: rec[R,12], bbox[R,4], tile_count[R] (padding records
+ *     invisible, tile count 0);
+ *   xpr_depth_order_items: order[R]: each item's records by (depth key,
+ *     index), those without tiles last, item k's at [rec_offset, + padded n);
+ *     workspace: xpr_depth_order_workspace(R);
+ *   xpr_bin_sorted_items: as xpr_bin_sorted over all items: ranges[S,2] for
+ *     S = the last tile_offset + its tiles, vals[capacity], *n_isect (HOST);
+ *     synchronises the stream once; workspace: xpr_bin_sorted_items_workspace;
+ *   xpr_render_fwd_items / xpr_render_bwd_items: as the _views calls with a
+ *     work list over all S tiles (xpr_tile_worklist) or NULL (one block per
+ *     tile); d_rec[R,12] overwritten;
+ *   xpr_project_bwd_items: d_prims (concatenated layout) OVERWRITTEN with the
+ *     sum over items of each scene primitive's gradient. */
+int xpr_project_items(const XprPrims *prims, const XprCamera *cams, const XprItem *items, int32_t n_items,
+                      const XprConfig *cfg, float *rec, int32_t *bbox, int32_t *tile_count, void *stream);
+int xpr_depth_order_items(const float *rec, const int32_t *tile_count, const XprItem *items, int32_t n_items,
+                          int32_t *order, void *workspace, size_t ws_bytes, void *stream);
+size_t xpr_bin_sorted_items_workspace(const XprCamera *cams, const XprItem *items, int32_t n_items,
+                                      const XprConfig *cfg);
+int xpr_bin_sorted_items(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order,
+                         const XprCamera *cams, const XprItem *items, int32_t n_items, const XprConfig *cfg,
+                         int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect, void *workspace,
+                         size_t ws_bytes, void *stream);
+int xpr_render_fwd_items(const float *rec, const uint32_t *vals, const int32_t *ranges, const XprCamera *cams,
+                         const XprItem *items, int32_t n_items, const XprConfig *cfg, float *image, float *t_final,
+                         int32_t *n_contrib, const int32_t *worklist, int32_t *counter, void *stream);
+int xpr_render_bwd_items(const float *rec, const uint32_t *vals, const int32_t *ranges, const XprCamera *cams,
+                         const XprItem *items, int32_t n_items, const XprConfig *cfg, const float *t_final,
+                         const int32_t *n_contrib, const float *d_image, float *d_rec, const int32_t *worklist,
+                         int32_t *counter, void *stream);
+int xpr_project_bwd_items(const XprPrims *prims, int64_t n_prims, const XprCamera *cams, const XprItem *items,
+                          int32_t n_items, const XprConfig *cfg, const float *d_rec, const XprPrimsGrad *d_prims,
+                          void *stream);
+
 /* xpr_project_color: the view-dependent colour of Listing 1 project (the SH
  * part of compute_color) for records already projected with prims->sh NULL:
  * for every visible record v * n + i (rec[.,11] != 0), rec[.,6..8] =
@@ -338,12 +402,13 @@ int xpr_project_color(const float *mu, const float *sh, int64_t n, const XprCame
  *     for I pairs); call again with capacity >= I.
  * The call synchronises the stream once (to read I).  It does a counting pass,
  * a prefix over a (chunk x tile) count matrix and a writing pass; every tile's
- * segment is [start, end) of vals.  Tile rows are walked in bands of
- * BR = max(1, min(8, 2048 / tiles_x)) rows; grids with more than 6400 tile
- * columns or more than 2048 bands over all views are rejected with
- * XPR_ERR_INVALID (use xpr_tile_bin + xpr_sort_tiles for them).  workspace
- * (device, 256-byte aligned, caller-owned): xpr_bin_sorted_workspace(n, V,
- * cam, cfg) bytes, 0 for invalid arguments. */
+ * segment is [start, end) of vals.  The passes walk the emission positions in
+ * chunks, 8 tile rows per thread block, each row's kept span of tile columns
+ * from the row form of the cull; grids with more than 4096 tile columns are
+ * rejected with XPR_ERR_INVALID (use xpr_tile_bin + xpr_sort_tiles for them).
+ * workspace (device, 256-byte aligned, caller-owned):
+ * xpr_bin_sorted_workspace(n, V, cam, cfg) bytes (the count matrix holds at
+ * most 16M entries), 0 for invalid arguments. */
 size_t xpr_bin_sorted_workspace(int64_t n, int32_t n_views, const XprCamera *cam, const XprConfig *cfg);
 int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
                    int32_t n_views, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges, uint32_t *vals,

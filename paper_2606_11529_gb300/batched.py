@@ -191,3 +191,95 @@ def autotune(params, cams, cfg, scene_id="scene", backward=True, reps=5, tiles=T
     out = (dataclasses.replace(cfg, tile_w=best[0], tile_h=best[1], batch_depth=best[2]), table)
     _CACHE[key] = out
     return out
+
+
+# ------------------------------------------------------------------------------------------- scenes
+
+@dataclasses.dataclass
+class ItemsFrame:
+    layout: "B.ItemLayout"
+    rec: torch.Tensor
+    tile_count: torch.Tensor
+    n_isect: int
+    vals_sorted: torch.Tensor
+    ranges: torch.Tensor
+    worklist: torch.Tensor | None
+    image: torch.Tensor      # flat: item k's planes [3, H, W] at 3 pix_offset[k]
+    t_final: torch.Tensor    # flat: item k's [H, W] at pix_offset[k]
+    n_contrib: torch.Tensor
+
+    def images(self):
+        return self.layout.images(self.image)
+
+
+class SceneSet:
+    """Scenes of any size held as one set of concatenated parameter arrays (the batch's primitive
+    space): scene s owns primitives [offsets[s], offsets[s] + counts[s])."""
+
+    def __init__(self, scenes):
+        scenes = [tuple(t.contiguous() for t in s) for s in scenes]
+        self.counts = [int(s[0].shape[0]) for s in scenes]
+        self.offsets = [0]
+        for c in self.counts[:-1]:
+            self.offsets.append(self.offsets[-1] + c)
+        self.params = [torch.cat([s[j] for s in scenes]) for j in range(5)]
+
+    def views(self):
+        """Per-scene (mu, scale, quat, opacity, sh) tensors: contiguous slices of the set."""
+        return [tuple(t[o:o + n] for t in self.params) for o, n in zip(self.offsets, self.counts)]
+
+    def layout(self, scene_of_item, cams, cfg) -> "B.ItemLayout":
+        return B.ItemLayout([self.offsets[s] for s in scene_of_item], [self.counts[s] for s in scene_of_item], cams, cfg)
+
+
+def forward_items(mu, scale, quat, opacity, sh, layout, cfg, ws: ViewsWorkspace | None = None, persistent=True,
+                  stream=None) -> ItemsFrame:
+    """K (scene, camera) items of uneven scene and image sizes through one launch per stage (3DGS):
+    projection, depth order, fused bin + sort, work list over every item's tiles, render."""
+    L = B.load()
+    ws = ws or ViewsWorkspace()
+    dev = mu.device
+    ccfg = B.make_config(cfg)
+    rec, bbox, tc = B.xpr_project_items(mu, scale, quat, opacity, sh, layout, ccfg, stream=stream)
+    order = B.xpr_depth_order_items(rec, tc, layout, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(
+        layout.R), dev), stream=stream)
+    cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
+    ranges, vs, I = B.xpr_bin_sorted_items(rec, bbox, tc, order, layout, ccfg, capacity=cap,
+                                           workspace=ws.scratch("binsort", B.bin_sorted_items_workspace_bytes(
+                                               layout, ccfg), dev), stream=stream)
+    ws.last_isect = I
+    wl = B.xpr_tile_worklist(ranges, workspace=ws.scratch("wl", L.xpr_tile_worklist_workspace(layout.S), dev),
+                             stream=stream) if persistent else None
+    image, tfin, ncon = B.xpr_render_fwd_items(rec, vs, ranges, layout, ccfg, worklist=wl, stream=stream)
+    return ItemsFrame(layout, rec, tc, I, vs, ranges, wl, image, tfin, ncon)
+
+
+class MultiSceneSplat(torch.autograd.Function):
+    """Flat images of K (scene, camera) items; backward sums each scene primitive's gradient over
+    the items that see it."""
+
+    @staticmethod
+    def forward(ctx, mu, scale, quat, opacity, sh, layout, cfg, ws, persistent):
+        fr = forward_items(mu, scale, quat, opacity, sh, layout, cfg, ws, persistent)
+        ctx.save_for_backward(mu, scale, quat, opacity, sh, fr.rec, fr.vals_sorted, fr.ranges, fr.t_final,
+                              fr.n_contrib, *(() if fr.worklist is None else (fr.worklist,)))
+        ctx.layout, ctx.cfg = layout, cfg
+        return fr.image
+
+    @staticmethod
+    def backward(ctx, d_image):
+        saved = ctx.saved_tensors
+        mu, scale, quat, opacity, sh, rec, vals, ranges, tfin, ncon = saved[:10]
+        wl = saved[10] if len(saved) > 10 else None
+        ccfg = B.make_config(ctx.cfg)
+        d_rec = B.xpr_render_bwd_items(rec, vals, ranges, ctx.layout, ccfg, tfin, ncon, d_image.contiguous(),
+                                       worklist=wl)
+        grads = B.xpr_project_bwd_items(mu, scale, quat, opacity, sh, ctx.layout, ccfg, d_rec)
+        return (*grads, None, None, None, None)
+
+
+def render_items(mu, scale, quat, opacity, sh, layout, cfg, ws: ViewsWorkspace | None = None, persistent=True):
+    """Differentiable render of a multi-scene batch: returns the per-item images [3, H_k, W_k]
+    (views of one flat output)."""
+    flat = MultiSceneSplat.apply(mu, scale, quat, opacity, sh, layout, cfg, ws or ViewsWorkspace(), persistent)
+    return layout.images(flat)

@@ -38,6 +38,11 @@ class XprPrimsGrad(ctypes.Structure):
     _fields_ = [("mu", c_vp), ("scale", c_vp), ("quat", c_vp), ("opacity", c_vp), ("sh", c_vp)]
 
 
+class XprItem(ctypes.Structure):
+    _fields_ = [("prim_offset", c_i64), ("n", c_i64), ("rec_offset", c_i64), ("tile_offset", c_i64),
+                ("pix_offset", c_i64)]
+
+
 XPR_OK, XPR_ERR_INVALID, XPR_ERR_CAPACITY, XPR_ERR_CUDA, XPR_ERR_TIMEOUT, XPR_ERR_INTERNAL = range(6)
 XPR_METHOD_3DGS, XPR_METHOD_3DGUT, XPR_METHOD_LINPRIM = 0, 1, 2
 REC = 12
@@ -118,6 +123,21 @@ SIGNATURES = {
                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp]),
     "xpr_render_bwd_feat": (c_i32, [c_vp, c_i64, c_vp, c_i32, c_i32, c_vp, c_vp, ctypes.POINTER(XprCamera),
                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_project_items": (c_i32, [ctypes.POINTER(XprPrims), ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem), c_i32,
+                                  ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp]),
+    "xpr_depth_order_items": (c_i32, [c_vp, c_vp, ctypes.POINTER(XprItem), c_i32, c_vp, c_vp, c_sz, c_vp]),
+    "xpr_bin_sorted_items_workspace": (c_sz, [ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem), c_i32,
+                                              ctypes.POINTER(XprConfig)]),
+    "xpr_bin_sorted_items": (c_i32, [c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem),
+                                     c_i32, ctypes.POINTER(XprConfig), c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp,
+                                     c_sz, c_vp]),
+    "xpr_render_fwd_items": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem), c_i32,
+                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_render_bwd_items": (c_i32, [c_vp, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem), c_i32,
+                                     ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "xpr_project_bwd_items": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
+                                      ctypes.POINTER(XprItem), c_i32, ctypes.POINTER(XprConfig), c_vp,
+                                      ctypes.POINTER(XprPrimsGrad), c_vp]),
     "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
@@ -490,11 +510,10 @@ def xpr_project_color(mu, sh, rec, cams, cfg, stream=None):
 
 
 def binsort_ok(cam, cfg, n_views=1):
-    """Whether xpr_bin_sorted takes this grid: at most 6400 tile columns (its per-band counters)
-    and at most 2048 bands of 8 (or 2048 // columns) tile rows over all views."""
+    """Whether xpr_bin_sorted takes this grid: at most 4096 tile columns (its per-row cursors in
+    shared memory) and 1..16 views."""
     Wt, Ht = tiles_of(cam, cfg)
-    br = max(1, min(8, 2048 // Wt))
-    return Wt <= 6400 and Ht < 32768 and n_views * ((Ht + br - 1) // br) <= 2048
+    return Wt <= 4096 and 1 <= n_views <= 16
 
 
 def bin_sorted_workspace_bytes(n, n_views, cam, cfg):
@@ -581,6 +600,138 @@ def xpr_project_bwd_views(mu, scale, quat, opacity, sh, cams, cfg, d_rec, stream
     g = _as_c(cfg, XprConfig)
     _check(L.xpr_project_bwd_views(ctypes.byref(p), mu.shape[0], camera_array(cams), len(cams), ctypes.byref(g),
                                    _ptr(d_rec), ctypes.byref(gp), _stream(stream)), "xpr_project_bwd_views")
+    return grads
+
+
+# ---------------------------------------------------------------------------------------- multi-scene items
+
+class ItemLayout:
+    """Offsets of a multi-scene batch (XprItem): item k = (scene of primitives [prim_offset,
+    prim_offset + n), camera k).  Records are item-major in blocks padded to 32, tiles and pixels
+    follow item order."""
+
+    def __init__(self, prim_offsets, counts, cams, cfg):
+        self.cams = list(cams)
+        K = len(self.cams)
+        if not 1 <= K <= 16:
+            raise ValueError(f"{K} items: a batch holds 1..16")
+        self.arr = (XprItem * K)()
+        rec = tile = pix = 0
+        self.rec_offsets, self.tile_offsets, self.pix_offsets, self.shapes = [], [], [], []
+        for k, (p0, n, cam) in enumerate(zip(prim_offsets, counts, self.cams)):
+            Wt, Ht = tiles_of(cam, cfg)
+            self.arr[k] = XprItem(int(p0), int(n), rec, tile, pix)
+            self.rec_offsets.append(rec)
+            self.tile_offsets.append(tile)
+            self.pix_offsets.append(pix)
+            self.shapes.append((int(cam.height), int(cam.width)))
+            rec += (int(n) + 31) // 32 * 32
+            tile += Wt * Ht
+            pix += int(cam.width) * int(cam.height)
+        self.K, self.R, self.S, self.pixels = K, rec, tile, pix
+        self.carr = camera_array(self.cams)
+
+    def images(self, flat):
+        """Per-item [3, H, W] views of a flat image buffer."""
+        return [flat[3 * p0:3 * p0 + 3 * h * w].view(3, h, w) for p0, (h, w) in zip(self.pix_offsets, self.shapes)]
+
+    def planes(self, flat):
+        """Per-item [H, W] views of a flat per-pixel buffer."""
+        return [flat[p0:p0 + h * w].view(h, w) for p0, (h, w) in zip(self.pix_offsets, self.shapes)]
+
+
+def xpr_project_items(mu, scale, quat, opacity, sh, layout, cfg, stream=None):
+    L = load()
+    dev = mu.device
+    rec = torch.empty((layout.R, REC), dtype=torch.float32, device=dev)
+    bbox = torch.empty((layout.R, 4), dtype=torch.int32, device=dev)
+    tc = torch.empty(layout.R, dtype=torch.int32, device=dev)
+    p = _prims(mu, scale, quat, opacity, sh)
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_project_items(ctypes.byref(p), layout.carr, layout.arr, layout.K, ctypes.byref(g), _ptr(rec),
+                               _ptr(bbox), _ptr(tc), _stream(stream)), "xpr_project_items")
+    return rec, bbox, tc
+
+
+def xpr_depth_order_items(rec, tile_count, layout, workspace=None, stream=None):
+    L = load()
+    order = torch.empty(layout.R, dtype=torch.int32, device=rec.device)
+    need = int(L.xpr_depth_order_workspace(layout.R))
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=rec.device)
+    _check(L.xpr_depth_order_items(_ptr(rec), _ptr(tile_count), layout.arr, layout.K, _ptr(order), _ptr(workspace),
+                                   workspace.numel(), _stream(stream)), "xpr_depth_order_items")
+    return order
+
+
+def bin_sorted_items_workspace_bytes(layout, cfg):
+    g = _as_c(cfg, XprConfig)
+    return int(load().xpr_bin_sorted_items_workspace(layout.carr, layout.arr, layout.K, ctypes.byref(g)))
+
+
+def xpr_bin_sorted_items(rec, bbox, tile_count, order, layout, cfg, capacity=None, workspace=None, stream=None):
+    """Fused bin + sort over all items: (ranges[S,2], vals[I] (int32 storage), I)."""
+    L = load()
+    dev = rec.device
+    g = _as_c(cfg, XprConfig)
+    ranges = torch.empty((max(layout.S, 1), 2), dtype=torch.int32, device=dev)[:layout.S]
+    need = bin_sorted_items_workspace_bytes(layout, g)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    cap = int(capacity) if capacity is not None else max(4 * layout.R, 1024)
+    vals = torch.empty(cap, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        got = c_i64(0)
+        s = L.xpr_bin_sorted_items(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(order), layout.carr, layout.arr,
+                                   layout.K, ctypes.byref(g), _ptr(ranges), _ptr(vals), vals.numel(),
+                                   ctypes.byref(got), _ptr(workspace), workspace.numel(), _stream(stream))
+        if s == XPR_ERR_CAPACITY and got.value <= 0x7FFFFFFF:
+            vals = torch.empty(max(got.value, 1), dtype=torch.int32, device=dev)
+            continue
+        _check(s, "xpr_bin_sorted_items")
+        I = int(got.value)
+        return ranges, vals[:I], I
+    raise XprError(XPR_ERR_CAPACITY, "xpr_bin_sorted_items", "capacity retry failed")
+
+
+def xpr_render_fwd_items(rec, vals, ranges, layout, cfg, worklist=None, counter=None, stream=None):
+    """Flat outputs: image[3 * pixels] (item k's planes at 3 pix_offset), t_final[pixels], n_contrib[pixels]."""
+    L = load()
+    dev = rec.device
+    image = torch.empty(3 * layout.pixels, dtype=torch.float32, device=dev)
+    tfin = torch.empty(layout.pixels, dtype=torch.float32, device=dev)
+    ncon = torch.empty(layout.pixels, dtype=torch.int32, device=dev)
+    if worklist is not None and counter is None:
+        counter = torch.empty(1, dtype=torch.int32, device=dev)
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_render_fwd_items(_ptr(rec), _ptr(vals), _ptr(ranges), layout.carr, layout.arr, layout.K,
+                                  ctypes.byref(g), _ptr(image), _ptr(tfin), _ptr(ncon), _ptr(worklist), _ptr(counter),
+                                  _stream(stream)), "xpr_render_fwd_items")
+    return image, tfin, ncon
+
+
+def xpr_render_bwd_items(rec, vals, ranges, layout, cfg, t_final, n_contrib, d_image, worklist=None, counter=None,
+                         stream=None):
+    L = load()
+    dev = rec.device
+    d_rec = torch.empty((layout.R, REC), dtype=torch.float32, device=dev)
+    if worklist is not None and counter is None:
+        counter = torch.empty(1, dtype=torch.int32, device=dev)
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_render_bwd_items(_ptr(rec), _ptr(vals), _ptr(ranges), layout.carr, layout.arr, layout.K,
+                                  ctypes.byref(g), _ptr(t_final), _ptr(n_contrib), _ptr(d_image.contiguous()),
+                                  _ptr(d_rec), _ptr(worklist), _ptr(counter), _stream(stream)), "xpr_render_bwd_items")
+    return d_rec
+
+
+def xpr_project_bwd_items(mu, scale, quat, opacity, sh, layout, cfg, d_rec, stream=None):
+    L = load()
+    grads = tuple(torch.empty_like(t) for t in (mu, scale, quat, opacity, sh))
+    p = _prims(mu, scale, quat, opacity, sh)
+    gp = XprPrimsGrad(*[t.data_ptr() for t in grads])
+    g = _as_c(cfg, XprConfig)
+    _check(L.xpr_project_bwd_items(ctypes.byref(p), mu.shape[0], layout.carr, layout.arr, layout.K, ctypes.byref(g),
+                                   _ptr(d_rec), ctypes.byref(gp), _stream(stream)), "xpr_project_bwd_items")
     return grads
 
 

@@ -74,6 +74,41 @@ static int check_n(int64_t n) {
     return XPR_OK;
 }
 
+int make_item_table(const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg, ItemTable &t,
+                    int64_t *n_records, const char *fn) {
+    if (n_items < 1 || n_items > kMaxItems)
+        return fail(XPR_ERR_INVALID, "%s: item count %d out of range [1, %d]", fn, n_items, kMaxItems);
+    if (!cams || !items) return fail(XPR_ERR_INVALID, "%s: NULL cameras or items", fn);
+    memset(&t, 0, sizeof(t));
+    t.count = n_items;
+    int64_t rec = 0, tile = 0, pix = 0;
+    for (int k = 0; k < n_items; ++k) {
+        int s = validate_camera_config(cams + k, &cfg);
+        if (s) return s;
+        const XprItem &it = items[k];
+        if (it.n < 0 || it.prim_offset < 0)
+            return fail(XPR_ERR_INVALID, "%s: item %d has a negative primitive range", fn, k);
+        if (it.rec_offset != rec || it.tile_offset != tile || it.pix_offset != pix)
+            return fail(XPR_ERR_INVALID, "%s: item %d offsets (%lld, %lld, %lld) are not the running sums "
+                        "(%lld, %lld, %lld)", fn, k, (long long)it.rec_offset, (long long)it.tile_offset,
+                        (long long)it.pix_offset, (long long)rec, (long long)tile, (long long)pix);
+        t.W[k] = cams[k].width;
+        t.H[k] = cams[k].height;
+        t.Wt[k] = tiles_x(cams[k], cfg);
+        t.tile0[k] = tile;
+        t.pix0[k] = pix;
+        rec += (it.n + 31) / 32 * 32;
+        tile += (int64_t)tiles_x(cams[k], cfg) * tiles_y(cams[k], cfg);
+        pix += (int64_t)cams[k].width * cams[k].height;
+    }
+    t.tile0[n_items] = tile;
+    if (rec > 0x7fffffffLL || tile > 0x7fffffffLL)
+        return fail(XPR_ERR_INVALID, "%s: %lld records or %lld tiles exceed 2^31-1", fn, (long long)rec,
+                    (long long)tile);
+    if (n_records) *n_records = rec;
+    return XPR_OK;
+}
+
 }  // namespace xpr
 
 using namespace xpr;
@@ -436,6 +471,131 @@ int xpr_project_bwd_views(const XprPrims *prims, int64_t n, const XprCamera *cam
     return launch_project_bwd_views(*prims, n, cams, n_views, *cfg, d_rec, *d_prims, as_stream(stream));
 }
 
+// ---- multi-scene batched form (items) ------------------------------------------------------
+
+
+int xpr_project_items(const XprPrims *prims, const XprCamera *cams, const XprItem *items, int32_t n_items,
+                      const XprConfig *cfg, float *rec, int32_t *bbox, int32_t *tile_count, void *stream) {
+    if (!cfg) return fail(XPR_ERR_INVALID, "xpr_project_items: NULL config");
+    ItemTable t;
+    int64_t R = 0;
+    int s = make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_project_items");
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_project_items"))) return s;
+    if (R == 0) return XPR_OK;
+    if (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh || !rec || !bbox ||
+        !tile_count)
+        return fail(XPR_ERR_INVALID, "xpr_project_items: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(rec, 16) || !aligned(bbox, 16))
+        return fail(XPR_ERR_INVALID, "xpr_project_items: quat, rec and bbox must be 16-byte aligned");
+    return launch_project_items(*prims, cams, items, n_items, *cfg, rec, bbox, tile_count, as_stream(stream));
+}
+
+int xpr_depth_order_items(const float *rec, const int32_t *tile_count, const XprItem *items, int32_t n_items,
+                          int32_t *order, void *workspace, size_t ws_bytes, void *stream) {
+    if (n_items < 1 || n_items > kMaxItems || !items)
+        return fail(XPR_ERR_INVALID, "xpr_depth_order_items: item count %d out of range [1, %d]", n_items, kMaxItems);
+    int64_t rec_end = 0;
+    for (int k = 0; k < n_items; ++k) {
+        if (items[k].n < 0 || items[k].rec_offset != rec_end)
+            return fail(XPR_ERR_INVALID, "xpr_depth_order_items: item %d record block is not the running sum", k);
+        rec_end += (items[k].n + 31) / 32 * 32;
+    }
+    if (rec_end == 0) return XPR_OK;
+    if (rec_end > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "xpr_depth_order_items: too many records");
+    if (!rec || !tile_count || !order || !workspace) return fail(XPR_ERR_INVALID, "xpr_depth_order_items: NULL");
+    if (!aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_depth_order_items: workspace alignment");
+    return launch_depth_order_items(rec, tile_count, items, n_items, order, workspace, ws_bytes, as_stream(stream));
+}
+
+size_t xpr_bin_sorted_items_workspace(const XprCamera *cams, const XprItem *items, int32_t n_items,
+                                      const XprConfig *cfg) {
+    ItemTable t;
+    if (!cfg || make_item_table(cams, items, n_items, *cfg, t, nullptr, "xpr_bin_sorted_items_workspace") != XPR_OK)
+        return 0;
+    return binsort_items_workspace_bytes(cams, items, n_items, *cfg);
+}
+
+int xpr_bin_sorted_items(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order,
+                         const XprCamera *cams, const XprItem *items, int32_t n_items, const XprConfig *cfg,
+                         int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect, void *workspace,
+                         size_t ws_bytes, void *stream) {
+    if (!cfg) return fail(XPR_ERR_INVALID, "xpr_bin_sorted_items: NULL config");
+    ItemTable t;
+    int64_t R = 0;
+    int s = make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_bin_sorted_items");
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_bin_sorted_items"))) return s;
+    if (!binsort_items_supported(cams, n_items, *cfg))
+        return fail(XPR_ERR_INVALID, "xpr_bin_sorted_items: a camera has more than 4096 tile columns");
+    if (!ranges || !n_isect) return fail(XPR_ERR_INVALID, "xpr_bin_sorted_items: NULL ranges or n_isect");
+    if (capacity < 0) return fail(XPR_ERR_INVALID, "xpr_bin_sorted_items: negative capacity");
+    if (R > 0 && (!rec || !bbox || !tile_count || !order || !workspace))
+        return fail(XPR_ERR_INVALID, "xpr_bin_sorted_items: NULL pointer");
+    if (R > 0 && (!aligned(rec, 16) || !aligned(bbox, 16) || !aligned(workspace, 256)))
+        return fail(XPR_ERR_INVALID, "xpr_bin_sorted_items: rec/bbox 16-byte and workspace 256-byte alignment");
+    return launch_binsort_items(rec, bbox, tile_count, order, cams, items, n_items, *cfg, ranges, vals, capacity,
+                                n_isect, workspace, ws_bytes, as_stream(stream));
+}
+
+int xpr_render_fwd_items(const float *rec, const uint32_t *vals, const int32_t *ranges, const XprCamera *cams,
+                         const XprItem *items, int32_t n_items, const XprConfig *cfg, float *image, float *t_final,
+                         int32_t *n_contrib, const int32_t *worklist, int32_t *counter, void *stream) {
+    if (!cfg) return fail(XPR_ERR_INVALID, "xpr_render_fwd_items: NULL config");
+    ItemTable t;
+    int64_t R = 0;
+    int s = make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_render_fwd_items");
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_render_fwd_items"))) return s;
+    if (!ranges || !image || !t_final || !n_contrib) return fail(XPR_ERR_INVALID, "xpr_render_fwd_items: NULL");
+    if (R > 0 && (!rec || !aligned(rec, 16))) return fail(XPR_ERR_INVALID, "xpr_render_fwd_items: rec");
+    if (worklist && !counter) return fail(XPR_ERR_INVALID, "xpr_render_fwd_items: worklist needs a counter");
+    if (!aligned(ranges, 8)) return fail(XPR_ERR_INVALID, "xpr_render_fwd_items: ranges must be 8-byte aligned");
+    return launch_render_fwd_items(rec, R, vals, ranges, t, *cfg, image, t_final, n_contrib, worklist, counter,
+                                   as_stream(stream));
+}
+
+int xpr_render_bwd_items(const float *rec, const uint32_t *vals, const int32_t *ranges, const XprCamera *cams,
+                         const XprItem *items, int32_t n_items, const XprConfig *cfg, const float *t_final,
+                         const int32_t *n_contrib, const float *d_image, float *d_rec, const int32_t *worklist,
+                         int32_t *counter, void *stream) {
+    if (!cfg) return fail(XPR_ERR_INVALID, "xpr_render_bwd_items: NULL config");
+    ItemTable t;
+    int64_t R = 0;
+    int s = make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_render_bwd_items");
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_render_bwd_items"))) return s;
+    if (!ranges || !t_final || !n_contrib || !d_image) return fail(XPR_ERR_INVALID, "xpr_render_bwd_items: NULL");
+    if (R == 0) return XPR_OK;
+    if (!rec || !d_rec || !aligned(rec, 16) || !aligned(d_rec, 16))
+        return fail(XPR_ERR_INVALID, "xpr_render_bwd_items: rec/d_rec NULL or not 16-byte aligned");
+    if (worklist && !counter) return fail(XPR_ERR_INVALID, "xpr_render_bwd_items: worklist needs a counter");
+    return launch_render_bwd_items(rec, R, vals, ranges, t, *cfg, t_final, n_contrib, d_image, d_rec, worklist,
+                                   counter, as_stream(stream));
+}
+
+int xpr_project_bwd_items(const XprPrims *prims, int64_t n_prims, const XprCamera *cams, const XprItem *items,
+                          int32_t n_items, const XprConfig *cfg, const float *d_rec, const XprPrimsGrad *d_prims,
+                          void *stream) {
+    if (!cfg) return fail(XPR_ERR_INVALID, "xpr_project_bwd_items: NULL config");
+    ItemTable t;
+    int64_t R = 0;
+    int s = make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_project_bwd_items");
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_project_bwd_items"))) return s;
+    for (int k = 0; k < n_items; ++k)
+        if (items[k].prim_offset + items[k].n > n_prims)
+            return fail(XPR_ERR_INVALID, "xpr_project_bwd_items: item %d reaches past the %lld primitives", k,
+                        (long long)n_prims);
+    if (n_prims == 0) return XPR_OK;
+    if (!prims || !d_prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh ||
+        !d_prims->mu || !d_prims->scale || !d_prims->quat || !d_prims->opacity || !d_prims->sh || (R > 0 && !d_rec))
+        return fail(XPR_ERR_INVALID, "xpr_project_bwd_items: NULL pointer");
+    if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || (d_rec && !aligned(d_rec, 16)))
+        return fail(XPR_ERR_INVALID, "xpr_project_bwd_items: quat and d_rec must be 16-byte aligned");
+    return launch_project_bwd_items(*prims, n_prims, cams, items, n_items, *cfg, d_rec, *d_prims, as_stream(stream));
+}
+
 int xpr_project_color(const float *mu, const float *sh, int64_t n, const XprCamera *cams, int32_t n_views,
                       const XprConfig *cfg, float *rec, void *stream) {
     int s = check_views(n_views, n);
@@ -464,7 +624,7 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
     if (cfg->method == XPR_METHOD_LINPRIM)
         return fail(XPR_ERR_INVALID, "xpr_bin_sorted: LinPrim is binned by xpr_tile_bin_lp");
     if (!binsort_supported(*cam, *cfg, n_views))
-        return fail(XPR_ERR_INVALID, "xpr_bin_sorted: a %d x %d tile grid (x %d views) exceeds the band limits",
+        return fail(XPR_ERR_INVALID, "xpr_bin_sorted: a %d x %d tile grid (x %d views) has more than 4096 tile columns",
                     tiles_x(*cam, *cfg), tiles_y(*cam, *cfg), n_views);
     if (!ranges || !n_isect) return fail(XPR_ERR_INVALID, "xpr_bin_sorted: NULL ranges or n_isect");
     if (capacity < 0) return fail(XPR_ERR_INVALID, "xpr_bin_sorted: negative capacity");

@@ -162,6 +162,23 @@ __global__ void depth_key_kernel(const float *__restrict__ rec, const int *__res
     vals[i] = (uint32_t)i;
 }
 
+// Multi-scene items: the item of record i (its block [rec0[k], rec0[k + 1])) goes in bits 32..
+struct KeyItems {
+    int count;
+    int64_t rec0[kMaxItems + 1];
+};
+
+__global__ void depth_key_items_kernel(const float *__restrict__ rec, const int *__restrict__ tcount, KeyItems ki,
+                                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ki.rec0[ki.count]) return;
+    int k = 0;
+    while (k + 1 < ki.count && i >= ki.rec0[k + 1]) ++k;
+    const uint64_t d = tcount[i] > 0 ? (uint64_t)__float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]) : 0xffffffffull;
+    keys[i] = ((uint64_t)k << 32) | d;
+    vals[i] = (uint32_t)i;
+}
+
 // ---- device-wide exclusive scan (three phases: block reduce, scan of block sums, block scan) ----
 // Item j is in[gather[j]] when gather is non-NULL, else in[j].
 constexpr int kScanThreads = 512;
@@ -335,6 +352,29 @@ int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *
     // per-view ranges)
     return launch_sort(keys, vals, n, n_views, 0, nullptr, reinterpret_cast<uint32_t *>(order), nullptr, sort_ws,
                        sort_workspace_bytes(n, n_views), st);
+}
+
+int launch_depth_order_items(const float *rec, const int32_t *tc, const XprItem *items, int n_items, int32_t *order,
+                             void *ws, size_t ws_bytes, cudaStream_t st) {
+    KeyItems ki;
+    memset(&ki, 0, sizeof(ki));
+    ki.count = n_items;
+    for (int k = 0; k < n_items; ++k) ki.rec0[k] = items[k].rec_offset;
+    const int64_t R = items[n_items - 1].rec_offset + (items[n_items - 1].n + 31) / 32 * 32;
+    ki.rec0[n_items] = R;
+    if (R == 0) return XPR_OK;
+    if (ws_bytes < depth_order_workspace_bytes(R))
+        return fail(XPR_ERR_INVALID, "xpr_depth_order_items: workspace %zu < %zu bytes", ws_bytes,
+                    depth_order_workspace_bytes(R));
+    const size_t a = ((size_t)R * 8 + 255) / 256 * 256, b = ((size_t)R * 4 + 255) / 256 * 256;
+    char *p = reinterpret_cast<char *>(ws);
+    uint64_t *keys = reinterpret_cast<uint64_t *>(p);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
+    void *sort_ws = p + 2 * a + b + 256;
+    depth_key_items_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(rec, tc, ki, keys, vals);
+    XPR_LAUNCH_CHECK("depth_key_items_kernel");
+    return launch_sort(keys, vals, R, n_items, 0, nullptr, reinterpret_cast<uint32_t *>(order), nullptr, sort_ws,
+                       sort_workspace_bytes(R, n_items), st);
 }
 
 }  // namespace xpr

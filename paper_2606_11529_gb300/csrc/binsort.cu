@@ -1,562 +1,449 @@
 // Rasterizer, both halves fused (Sec. 4.2 "Replicate, Assign tile ID, Cull" + "Sort and identify
-// bounds"): the per-tile lists are built directly in their sorted order, with no key array and no
-// radix passes.
+// bounds"): the per-tile lists are written directly in their sorted order, with no key array and
+// no radix pass.
 //
 // Input: the records in emission (depth) order, order[] from xpr_depth_order.  Wanted: for every
 // tile, the kept records in that order, i.e. a stable counting sort of the (record, tile) pairs by
-// tile.  The pairs of one record fall on distinct tiles, so a warp that walks records one after
-// another can rank pairs with private per-tile counters and no conflict resolution:
+// tile.  The cull of Listing 1 tile_cull keeps, in each tile row, one contiguous span of tile
+// columns (cull.cuh, row form), so the work is organised by tile rows:
 //
-//   * tile rows are grouped into bands of BR rows; a work unit is (band, range of consecutive
-//     emission positions) and owns one counter per tile of its band in shared memory;
-//   * the unit's warp walks its positions in order; for each record whose box meets the band, the
-//     lanes take the box's band slots 32 at a time (all on different tiles), apply the exact FP32
-//     cull of cull.cuh and bump the counter of each kept tile;
-//   * count pass: the counters are stored as the unit's row of a (unit x band tile) matrix; then
-//     for each tile, an exclusive prefix over the tiles before it and over the band's units before
-//     this one turns each entry into the output position of the unit's first pair on that tile,
-//     and gives the tile ranges [start, end) directly;
-//   * emit pass: the same walk with the counters started at those positions writes
-//     vals[counter++] = record index.
-// Within a tile, units come in position order and a unit's pairs in walk order, so the result is
-// the (tile, depth, index) order of the key sort, bit for bit, with the same kept set.
-//
-// Work balance.  The cost of a walk is about (band slots + a per-record overhead) summed over the
-// records met, and it is very uneven: near the camera one record covers hundreds of tiles.  So the
-// positions are first cut into chunks of Q positions; for every (band, chunk) the cost is summed;
-// a work quantum E is chosen on the device from the total so that the units fit a fixed budget;
-// and each (band, chunk) becomes floor(cost / E) + 1 units, cut where its running cost crosses a
-// multiple of E.  A unit therefore walks at most Q positions and about E slots.  Each band's
-// units are padded to a multiple of 32 (empty units) so the column prefix works on 32-row
-// segments that never straddle two bands.
+//   * the emission positions of a view are cut into chunks of P positions; a block serves one
+//     (view, chunk, group of 8 tile rows), one warp per tile row;
+//   * the block scans its chunk's positions 1024 at a time: every warp takes 128 consecutive
+//     positions and appends each record whose box meets one of the group's rows to a queue per
+//     (warp, row), in position order;
+//   * the row's warp then takes the queues of warps 0..7 in turn (that is, position order), 32
+//     records at a time: each lane computes its record's kept span [ka, kb] in the row;
+//   * count pass: a difference array per row (+1 at ka, -1 at kb + 1) gives, after the chunk, the
+//     number of kept pairs of every tile of the row in this chunk: one row of a (chunk x tile)
+//     count matrix per view;
+//   * the matrix is prefix-summed down each tile's column (over the chunks) and across the tiles:
+//     each entry becomes the output position of the chunk's first pair on that tile, and the tile
+//     ranges [start, end) follow;
+//   * emit pass: the same walk with per-row cursors loaded from the matrix; the 32 records' spans
+//     are flattened over the lanes 32 pairs at a time, and a pair's rank among the step's pairs on
+//     the same tile is the number of lower lanes with the same tile (__match_any_sync): lanes hold
+//     the pairs in record order and a record has at most one pair per tile, so those are exactly
+//     the earlier records' pairs.  vals[cursor + rank] = record, and the last of them advances the
+//     cursor.
+// Within a tile, chunks come in position order and a chunk's pairs in record order, so the lists
+// are the (tile, depth, index) order of the key sort, bit for bit, with the same kept set.
+#include <algorithm>
+
 #include "cull.cuh"
 
 namespace xpr {
 namespace {
 
-constexpr int kUnitWarps = 8;     // warps (units) per walk block
+constexpr int kRows = 8;                 // tile rows per block: one warp each
+constexpr int kRound = 1024;             // positions scanned per round (128 per warp)
+constexpr int kPerWarp = kRound / kRows;
+constexpr int kSegChunks = 32;           // chunks per segment of the column prefix
+constexpr int64_t kMinChunk = kRound;  // positions per chunk, at least
 constexpr int kColThreads = 256;
-constexpr int kSeg = 32;          // units per column-scan segment (and band padding granule)
-constexpr int kKappa = 32;        // per-record cost of a walk, in slot units
-constexpr int kMinQuantum = 2048; // smallest work quantum E, in slot units
-constexpr int kMaxBandCols = 6400;
-constexpr int kWalkSmemMax = kUnitWarps * kMaxBandCols * 4;  // 204800 B: one band row per warp
-constexpr int kPlanThreads = 1024;
-constexpr int kMaxBands = 2048;   // views x bands taken (the unit budget is sized for it)
+constexpr int kMaxCols = 4096;           // tile columns (a 32768-pixel row in 8-pixel tiles)
+constexpr int64_t kMatrixEntries = int64_t(16) << 20;  // count-matrix budget (64 MB)
 
-struct Shape {
-    int64_t n;       // records per view
-    int V;           // views
+// One item of the walk: a view of the single- / multi-view calls, or a (scene, camera) item of
+// the multi-scene call.  Its positions are order[pos0, pos0 + n), its tiles the global ids
+// [tile0, tile0 + T), its count matrix mat[mat0 ..] of nc rows by T, its segment sums
+// part[part0 ..] of nseg rows by T, and its blocks of the walk grid [blk0, blk0 + nc ng).
+struct BItem {
     Grid g;
-    int BR;          // tile rows per band
-    int nb;          // bands per view
-    int bt;          // band row stride of the matrix: BR * Wt
-    int T1;          // tiles per view
-    int64_t Q;       // positions per chunk
-    int npc;         // chunks per view
-    int max_units;   // unit budget (matrix rows)
+    int T, nc, ng, nseg, blk0;
+    int64_t n, pos0, tile0, mat0, part0;
 };
 
-Shape make_shape(int64_t n, int V, const XprCamera &cam, const XprConfig &cfg) {
-    Shape s;
-    s.n = n;
-    s.V = V;
-    s.g = make_grid(cam, cfg);
-    s.BR = max(1, min(8, 2048 / s.g.Wt));
-    s.nb = (s.g.Ht + s.BR - 1) / s.BR;
-    s.bt = s.BR * s.g.Wt;
-    s.T1 = s.g.Wt * s.g.Ht;
-    s.max_units = 12288 * min(V, 4);
-    // at most half the budget goes to the one-unit-per-(band, chunk) minimum
-    const int64_t vb = (int64_t)V * s.nb;
-    int64_t npc_cap = max((int64_t)1, (int64_t)(s.max_units / 2) / vb);
-    int64_t Q = max((int64_t)4096, (n + npc_cap - 1) / npc_cap);
-    Q = (Q + 31) / 32 * 32;
-    s.Q = Q;
-    s.npc = (int)((n + Q - 1) / Q);
-    // the band padding can add up to kSeg - 1 units per band
-    s.max_units += (int)(vb * kSeg);
+struct Shape {
+    int K;          // items
+    int64_t P;      // positions per chunk (a multiple of kRound)
+    int blocks;     // walk blocks over all items
+    int max_T, max_nseg;
+    int64_t S;      // tiles over all items
+    int64_t mat_entries, part_entries;
+    BItem it[kMaxItems];
+};
+
+// grids[k], n[k], pos0[k], tile0[k] for k < K; tile0 must be the running sum of the grids' tiles.
+Shape make_shape(int K, const Grid *grids, const int64_t *n, const int64_t *pos0) {
+    Shape s = {};
+    s.K = K;
+    // the smallest chunk of at least kMinChunk positions whose count matrix fits the budget (longer
+    // per-(chunk, tile) segments keep the scattered writes of the emit pass to fewer partial sectors)
+    int64_t P = kMinChunk;
+    for (;;) {
+        int64_t e = 0;
+        for (int k = 0; k < K; ++k)
+            e += std::max<int64_t>(1, (n[k] + P - 1) / P) * (int64_t)grids[k].Wt * grids[k].Ht;
+        if (e <= kMatrixEntries || P >= (int64_t(1) << 40)) break;
+        P += kRound;
+    }
+    s.P = P;
+    int64_t tile0 = 0, mat0 = 0, part0 = 0;
+    int blk0 = 0;
+    for (int k = 0; k < K; ++k) {
+        BItem &b = s.it[k];
+        b.g = grids[k];
+        b.T = b.g.Wt * b.g.Ht;
+        b.n = n[k];
+        b.pos0 = pos0[k];
+        b.nc = (int)std::max<int64_t>(1, (n[k] + P - 1) / P);
+        b.ng = (b.g.Ht + kRows - 1) / kRows;
+        b.nseg = (b.nc + kSegChunks - 1) / kSegChunks;
+        b.tile0 = tile0;
+        b.mat0 = mat0;
+        b.part0 = part0;
+        b.blk0 = blk0;
+        tile0 += b.T;
+        mat0 += (int64_t)b.nc * b.T;
+        part0 += (int64_t)b.nseg * b.T;
+        blk0 += b.nc * b.ng;
+        s.max_T = std::max(s.max_T, b.T);
+        s.max_nseg = std::max(s.max_nseg, b.nseg);
+    }
+    s.blocks = blk0;
+    s.S = tile0;
+    s.mat_entries = mat0;
+    s.part_entries = part0;
     return s;
 }
 
-inline size_t al256(size_t b) { return (b + 255) / 256 * 256; }
-
-struct Plan {
-    unsigned long long h_total;  // sum of all (band, chunk) costs
-    long long quantum;           // work quantum E
-    long long units;             // units in use (a multiple of kSeg)
-    long long pad;
-};
+Shape make_views_shape(int64_t n, int V, const XprCamera &cam, const XprConfig &cfg) {
+    Grid grids[kMaxItems];
+    int64_t nn[kMaxItems], p0[kMaxItems];
+    for (int v = 0; v < V; ++v) {
+        grids[v] = make_grid(cam, cfg);
+        nn[v] = n;
+        p0[v] = (int64_t)v * n;
+    }
+    return make_shape(V, grids, nn, p0);
+}
 
 struct Ws {
-    int2 *box;        // [V n] packed boxes in emission order
-    int32_t *cost;    // [V nb npc] (band, chunk) cost sums, band-major
-    int32_t *lofs;    // [V nb npc] first unit of a (band, chunk) within its band
-    int32_t *bandu;   // [V nb] units per band (padded), then the first unit of each band
-    int4 *desc;       // [max_units] (band, chunk, sub-unit, sub-units); chunk -1: padding
-    int32_t *ustart;  // [max_units] first position of sub-unit s >= 1
-    Plan *plan;
-    int32_t *mat;     // [max_units][bt] counts, then first output positions
-    int32_t *part;    // [max_units / kSeg][bt] segment sums, then segment prefixes
-    int32_t *tot;     // [V T1] tile totals
-    int32_t *start;   // [V T1 + 1] tile starts
-    void *scan_tiles; // scan partials over V T1 entries
-    void *scan_bands; // scan partials over V nb entries
+    int32_t *mat;    // count matrix: counts, then first output positions
+    int32_t *part;   // segment sums, then segment bases
+    int32_t *tot;    // [S + 1]: tile totals, then tile starts
+    void *scan;      // scan partials of S entries
 };
 
 size_t carve(const Shape &s, void *base, Ws *w) {
-    const int64_t nr = s.n * s.V, nt = (int64_t)s.T1 * s.V, vb = (int64_t)s.V * s.nb;
-    const int64_t ncost = vb * s.npc;
-    size_t off = 0;
-    char *p = reinterpret_cast<char *>(base);
-    auto take = [&](size_t bytes) {
-        char *q = p ? p + off : nullptr;
-        off += al256(bytes);
-        return q;
-    };
-    char *a = take((size_t)nr * sizeof(int2));
-    char *b = take((size_t)ncost * 4);
-    char *c = take((size_t)ncost * 4);
-    char *d = take((size_t)(vb + 1) * 4);
-    char *e = take((size_t)s.max_units * sizeof(int4));
-    char *f = take((size_t)s.max_units * 4);
-    char *g = take(sizeof(Plan));
-    char *h = take((size_t)s.max_units * s.bt * 4);
-    char *i = take((size_t)(s.max_units / kSeg) * s.bt * 4);
-    char *j = take((size_t)nt * 4);
-    char *k = take((size_t)(nt + 1) * 4);
-    char *l = take(scan_partials_bytes(nt));
-    char *m = take(scan_partials_bytes(vb));
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_mat = up((size_t)s.mat_entries * sizeof(int32_t));
+    const size_t b_part = up((size_t)s.part_entries * sizeof(int32_t));
+    const size_t b_tot = up(((size_t)s.S + 1) * sizeof(int32_t));
+    const size_t b_scan = up(scan_partials_bytes(s.S));
     if (w) {
-        w->box = reinterpret_cast<int2 *>(a);
-        w->cost = reinterpret_cast<int32_t *>(b);
-        w->lofs = reinterpret_cast<int32_t *>(c);
-        w->bandu = reinterpret_cast<int32_t *>(d);
-        w->desc = reinterpret_cast<int4 *>(e);
-        w->ustart = reinterpret_cast<int32_t *>(f);
-        w->plan = reinterpret_cast<Plan *>(g);
-        w->mat = reinterpret_cast<int32_t *>(h);
-        w->part = reinterpret_cast<int32_t *>(i);
-        w->tot = reinterpret_cast<int32_t *>(j);
-        w->start = reinterpret_cast<int32_t *>(k);
-        w->scan_tiles = l;
-        w->scan_bands = m;
+        char *p = reinterpret_cast<char *>(base);
+        w->mat = reinterpret_cast<int32_t *>(p);
+        p += b_mat;
+        w->part = reinterpret_cast<int32_t *>(p);
+        p += b_part;
+        w->tot = reinterpret_cast<int32_t *>(p);
+        p += b_tot;
+        w->scan = p;
     }
-    return off;
+    return b_mat + b_part + b_tot + b_scan;
 }
 
-// ---------------------------------------------------------------------------------------------
-// box[j] = the tile box of record order[j], clamped to the grid, packed x0 | x1 << 16, y0 | y1 << 16
-// (empty when the record has no tiles).
-__global__ void gather_box_kernel(const int4 *__restrict__ bbox, const int32_t *__restrict__ tcount,
-                                  const int32_t *__restrict__ order, int64_t nr, Grid g, int2 *__restrict__ box) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nr) return;
-    const int i = order[j];
-    int2 out = make_int2(0, 0);
-    if (tcount[i] > 0) {
-        int4 bb = bbox[i];
-        bb.x = max(bb.x, 0);
-        bb.y = max(bb.y, 0);
-        bb.z = min(bb.z, g.Wt);
-        bb.w = min(bb.w, g.Ht);
-        if (bb.z > bb.x && bb.w > bb.y) out = make_int2(bb.x | (bb.z << 16), bb.y | (bb.w << 16));
-    }
-    box[j] = out;
+__device__ __forceinline__ int box_rows(const int4 *__restrict__ bbox, const int32_t *__restrict__ tc, int i,
+                                        const Grid &g, int4 &bb) {
+    bb = make_int4(0, 0, 0, 0);
+    if (tc[i] <= 0) return 0;
+    bb = bbox[i];
+    bb.x = max(bb.x, 0);  // never leave the tile grid, whatever the caller's boxes say
+    bb.y = max(bb.y, 0);
+    bb.z = min(bb.z, g.Wt);
+    bb.w = min(bb.w, g.Ht);
+    return (bb.z > bb.x && bb.w > bb.y) ? 1 : 0;
 }
 
-struct Box {
-    int x0, x1, y0, y1;
-};
-
-__device__ __forceinline__ Box unpack(int2 b) {
-    return Box{b.x & 0xffff, b.x >> 16, b.y & 0xffff, b.y >> 16};
-}
-
-// Walk cost of a box on band rows [r0, r1): its slots there plus the per-record overhead (0 if
-// the box misses the band or is empty).
-__device__ __forceinline__ int band_cost(const Box &b, int r0, int r1) {
-    const int y0 = max(b.y0, r0), y1 = min(b.y1, r1);
-    return (b.x1 > b.x0 && y1 > y0) ? (y1 - y0) * (b.x1 - b.x0) + kKappa : 0;
-}
-
-// One warp per (view, chunk): the walk cost of each band over the chunk's positions.
-__global__ void __launch_bounds__(256) chunk_cost_kernel(const int2 *__restrict__ box, Shape s,
-                                                         int32_t *__restrict__ cost, Plan *__restrict__ plan) {
-    extern __shared__ int32_t s_acc[];  // [8 warps][nb]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t wid = (int64_t)blockIdx.x * 8 + warp;
-    if (wid >= (int64_t)s.V * s.npc) return;
-    const int64_t v = wid / s.npc, pc = wid - v * s.npc;
-    int32_t *acc = s_acc + warp * s.nb;
-    for (int b = lane; b < s.nb; b += 32) acc[b] = 0;
-    __syncwarp();
-    const int64_t jb = v * s.n + pc * s.Q, je = v * s.n + min((pc + 1) * s.Q, s.n);
-    for (int64_t j0 = jb; j0 < je; j0 += 32) {
-        const int64_t j = j0 + lane;
-        const Box b = j < je ? unpack(box[j]) : Box{0, 0, 0, 0};
-        const bool has = b.x1 > b.x0;
-        const int blo = __reduce_min_sync(kFullMask, has ? (unsigned)(b.y0 / s.BR) : 0x7fffffffu);
-        const int bhi = (int)__reduce_max_sync(kFullMask, has ? (unsigned)((b.y1 - 1) / s.BR) : 0u);
-        for (int band = blo; band <= bhi; ++band) {
-            const int c = band_cost(b, band * s.BR, min(band * s.BR + s.BR, s.g.Ht));
-            const int sum = (int)__reduce_add_sync(kFullMask, (unsigned)c);
-            if (lane == 0) acc[band] += sum;
-        }
-    }
-    __syncwarp();
-    unsigned long long mine = 0;
-    for (int b = lane; b < s.nb; b += 32) {
-        cost[((int64_t)v * s.nb + b) * s.npc + pc] = acc[b];
-        mine += (unsigned long long)acc[b];
-    }
-    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(kFullMask, mine, o);
-    if (lane == 0) atomicAdd(&plan->h_total, mine);
-}
-
-__device__ __forceinline__ long long plan_quantum(const Plan *plan, const Shape &s) {
-    const long long vb = (long long)s.V * s.nb;
-    const long long avail = (long long)s.max_units - vb * kSeg - vb * s.npc;  // > 0 by the shape
-    const long long q = ((long long)plan->h_total + avail - 1) / (avail > 0 ? avail : 1);
-    return q > kMinQuantum ? q : kMinQuantum;
-}
-
-// One block per band: units of each (band, chunk) = floor(cost / E) + 1, their first unit within
-// the band (block-wide exclusive scan), and the band's unit count padded to a multiple of kSeg.
-__global__ void __launch_bounds__(kPlanThreads) plan_band_kernel(const int32_t *__restrict__ cost, Shape s,
-                                                                 const Plan *__restrict__ plan,
-                                                                 int32_t *__restrict__ lofs,
-                                                                 int32_t *__restrict__ bandu) {
-    __shared__ int s_warp[kPlanThreads / 32];
-    __shared__ int s_carry;
-    const int64_t vb = blockIdx.x;
-    const long long E = plan_quantum(plan, s);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < s.npc; base += kPlanThreads) {
-        const int pc = base + threadIdx.x;
-        const int u = pc < s.npc ? (int)(cost[vb * s.npc + pc] / E) + 1 : 0;
-        int x = u;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFullMask, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-            int w = s_warp[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFullMask, w, o);
-                if (lane >= o) w += y;
-            }
-            s_warp[lane] = w;
-        }
-        __syncthreads();
-        const int excl = s_carry + (wid > 0 ? s_warp[wid - 1] : 0) + x - u;
-        if (pc < s.npc) lofs[vb * s.npc + pc] = excl;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += s_warp[kPlanThreads / 32 - 1];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) bandu[vb] = (s_carry + kSeg - 1) / kSeg * kSeg;
-}
-
-// One block per band (after the band scan turned bandu into first units): unit descriptors.
-__global__ void __launch_bounds__(256) describe_units_kernel(const int32_t *__restrict__ cost,
-                                                             const int32_t *__restrict__ lofs,
-                                                             const int32_t *__restrict__ bandfirst, Shape s,
-                                                             Plan *__restrict__ plan, int4 *__restrict__ desc) {
-    const int vb = blockIdx.x;
-    const long long E = plan_quantum(plan, s);
-    const int first = bandfirst[vb], last = bandfirst[vb + 1];
-    const int used = s.npc > 0 ? lofs[(int64_t)vb * s.npc + s.npc - 1] +
-                                     (int)(cost[(int64_t)vb * s.npc + s.npc - 1] / E) + 1
-                               : 0;
-    for (int pc = threadIdx.x; pc < s.npc; pc += blockDim.x) {
-        const int nsub = (int)(cost[(int64_t)vb * s.npc + pc] / E) + 1;
-        const int u0 = first + lofs[(int64_t)vb * s.npc + pc];
-        for (int k = 0; k < nsub; ++k) desc[u0 + k] = make_int4(vb, pc, k, nsub);
-    }
-    for (int u = first + used + threadIdx.x; u < last; u += blockDim.x) desc[u] = make_int4(vb, -1, 0, 0);
-    if (vb == (int)gridDim.x - 1 && threadIdx.x == 0) {
-        plan->quantum = E;
-        plan->units = last;
-    }
-}
-
-// One warp per (view, chunk): where each (band, chunk)'s sub-units s >= 1 begin, i.e. the first
-// position after the running cost crosses s * E.
-__global__ void __launch_bounds__(256) cut_units_kernel(const int2 *__restrict__ box, Shape s,
-                                                        const int32_t *__restrict__ lofs,
-                                                        const int32_t *__restrict__ bandfirst,
-                                                        const int32_t *__restrict__ cost,
-                                                        const Plan *__restrict__ plan,
-                                                        int32_t *__restrict__ ustart) {
-    extern __shared__ int32_t s_run[];  // [8 warps][nb] running cost
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t wid = (int64_t)blockIdx.x * 8 + warp;
-    if (wid >= (int64_t)s.V * s.npc) return;
-    const int64_t v = wid / s.npc, pc = wid - v * s.npc;
-    const long long E = plan->quantum;
-    int32_t *run = s_run + warp * s.nb;
-    for (int b = lane; b < s.nb; b += 32) run[b] = 0;
-    __syncwarp();
-    const int64_t jv = v * s.n;
-    const int64_t jb = jv + pc * s.Q, je = jv + min((pc + 1) * s.Q, s.n);
-    for (int64_t j0 = jb; j0 < je; j0 += 32) {
-        const int64_t j = j0 + lane;
-        const Box b = j < je ? unpack(box[j]) : Box{0, 0, 0, 0};
-        const bool has = b.x1 > b.x0;
-        const int blo = __reduce_min_sync(kFullMask, has ? (unsigned)(b.y0 / s.BR) : 0x7fffffffu);
-        const int bhi = (int)__reduce_max_sync(kFullMask, has ? (unsigned)((b.y1 - 1) / s.BR) : 0u);
-        for (int band = blo; band <= bhi; ++band) {
-            const int c = band_cost(b, band * s.BR, min(band * s.BR + s.BR, s.g.Ht));
-            int incl = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFullMask, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int r = run[band];
-            __syncwarp();
-            if (c > 0) {
-                const long long lo = (long long)(r + incl - c) / E, hi = (long long)(r + incl) / E;
-                if (hi > lo) {
-                    const int64_t vbi = v * s.nb + band;
-                    const int u0 = bandfirst[vbi] + lofs[vbi * s.npc + pc];
-                    const int nsub = (int)(cost[vbi * s.npc + pc] / E) + 1;
-                    for (long long k = lo + 1; k <= hi && k < nsub; ++k) ustart[u0 + k] = (int32_t)(j + 1 - jv);
-                }
-            }
-            if (lane == 31) run[band] = r + incl;
-            __syncwarp();
-        }
-    }
-}
-
-// One warp per unit; EMIT = false counts, EMIT = true writes.
+// One (item, chunk, row group) per block, kRows warps.  EMIT = false: count pass (writes the
+// chunk's row of counts for the group's rows); EMIT = true: writes vals from the cursors in mat.
 template <bool EMIT>
-__global__ void __launch_bounds__(kUnitWarps * 32) walk_kernel(const float *__restrict__ rec,
-                                                               const int32_t *__restrict__ order,
-                                                               const int2 *__restrict__ box, Shape s,
-                                                               const int4 *__restrict__ desc,
-                                                               const int32_t *__restrict__ ustart,
-                                                               const Plan *__restrict__ plan,
-                                                               int32_t *__restrict__ mat,
-                                                               uint32_t *__restrict__ vals) {
-    extern __shared__ int32_t s_ctr[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t u = (int64_t)blockIdx.x * kUnitWarps + warp;
-    if (u >= plan->units) return;
-    const int4 d = desc[u];  // (view * nb + band, chunk or -1, sub-unit, sub-units)
-    const int v = d.x / s.nb, band = d.x - v * s.nb;
-    const int Wt = s.g.Wt;
-    const int r0 = band * s.BR, r1 = min(r0 + s.BR, s.g.Ht);
-    const int band_tiles = (r1 - r0) * Wt;
-    int32_t *ctr = s_ctr + warp * s.bt;
-    int32_t *mrow = mat + u * s.bt;
-    for (int k = lane; k < band_tiles; k += 32) ctr[k] = EMIT ? mrow[k] : 0;
-    __syncwarp();
-    if (d.y >= 0) {
-        const int64_t jv = (int64_t)v * s.n;
-        const int64_t cs = (int64_t)d.y * s.Q, ce = min(cs + s.Q, s.n);
-        // sub-unit bounds lie in [cs, ce] by construction; the clamps keep every read in the chunk
-        const int64_t ub = d.z == 0 ? cs : min(max((int64_t)ustart[u], cs), ce);
-        const int64_t ue = d.z == d.w - 1 ? ce : min(max((int64_t)ustart[u + 1], ub), ce);
-        const int64_t jb = jv + ub, je = jv + ue;
-        for (int64_t j0 = jb; j0 < je; j0 += 32) {
-            const int64_t j = j0 + lane;
-            Box b = Box{0, 0, 0, 0};
-            int i = 0;
-            if (j < je) {
-                b = unpack(box[j]);
-                i = order[j];
+__global__ void __launch_bounds__(kRows * 32) rowband_kernel(const float *__restrict__ rec,
+                                                             const int4 *__restrict__ bbox,
+                                                             const int32_t *__restrict__ tc,
+                                                             const int32_t *__restrict__ order, Shape s,
+                                                             int32_t *__restrict__ mat, uint32_t *__restrict__ vals,
+                                                             int64_t limit) {
+    __shared__ int32_t s_q[kRows][kRows][kPerWarp];  // [scanning warp][row] record queue
+    __shared__ int32_t s_qn[kRows][kRows];
+    extern __shared__ int32_t s_cols[];              // [row][Wt + 1]: difference array / cursors
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    int k = 0;
+    while (k + 1 < s.K && (int)blockIdx.x >= s.it[k + 1].blk0) ++k;
+    const BItem &it = s.it[k];
+    const Grid &g = it.g;
+    const int local = (int)blockIdx.x - it.blk0;
+    const int c = local / it.ng, g_idx = local - c * it.ng;
+    const int row0 = g_idx * kRows;
+    const int ty = row0 + wid;
+    const bool has_row = ty < g.Ht;
+    const int stride = g.Wt + 1;
+    int32_t *cols = s_cols + wid * stride;
+    int32_t *mrow = mat + it.mat0 + (int64_t)c * it.T + (int64_t)ty * g.Wt;
+    for (int x = lane; x < stride; x += 32) cols[x] = (EMIT && has_row && x < g.Wt) ? mrow[x] : 0;
+    const int64_t p_begin = (int64_t)c * s.P, p_end = min(p_begin + s.P, it.n);
+    const int32_t *ord = order + it.pos0;
+    for (int64_t r0 = p_begin; r0 < p_end; r0 += kRound) {
+        // scan: warp wid appends the records of positions [r0 + 128 wid, + 128) meeting each row
+        int qn[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) qn[r] = 0;
+#pragma unroll 1
+        for (int itr = 0; itr < kPerWarp / 32; ++itr) {
+            const int64_t p = r0 + wid * kPerWarp + itr * 32 + lane;
+            int i = 0, has = 0;
+            int4 bb = make_int4(0, 0, 0, 0);
+            if (p < p_end) {
+                i = ord[p];
+                has = box_rows(bbox, tc, i, g, bb);
             }
-            const bool hit = b.x1 > b.x0 && b.y0 < r1 && b.y1 > r0;
-            unsigned m = __ballot_sync(kFullMask, hit);
-            if (!m) continue;
-            CullData cd = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1.f};
-            if (hit) cd = load_cull(rec, i);
-            while (m) {
-                const int src = __ffs(m) - 1;
-                m &= m - 1;
-                const CullData e = shfl_cull(cd, src);
-                const int is = __shfl_sync(kFullMask, i, src);
-                const int x0 = __shfl_sync(kFullMask, b.x0, src), x1 = __shfl_sync(kFullMask, b.x1, src);
-                const int y0 = max(__shfl_sync(kFullMask, b.y0, src), r0);
-                const int y1 = min(__shfl_sync(kFullMask, b.y1, src), r1);
-                const int bw = x1 - x0, area = (y1 - y0) * bw;
-                SlotWalk sw(x0, y0, bw, lane);
-                for (int r = 0; r < area; r += 32) {
-                    if (r + lane < area && keep_tile(e, s.g, sw.tx, sw.ty)) {
-                        const int k = (sw.ty - r0) * Wt + sw.tx;  // distinct across the lanes of one step
-                        const int c = ctr[k];
-                        ctr[k] = c + 1;
-                        if (EMIT) vals[c] = (uint32_t)is;
-                    }
-                    sw.step();
-                }
-                __syncwarp();  // the next record's lanes read what this one's lanes wrote
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const bool meets = has && row0 + r >= bb.y && row0 + r < bb.w;
+                const unsigned m = __ballot_sync(kFullMask, meets);
+                if (meets) s_q[wid][r][qn[r] + __popc(m & lt_mask)] = i;
+                qn[r] += __popc(m);
             }
         }
+        if (lane == 0)
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) s_qn[wid][r] = qn[r];
+        __syncthreads();
+        if (has_row) {
+            // this row's queue is the scanning warps' sub-queues in order (position order): entry e
+            // is sub-queue w's entry e - start[w]
+            int qstart[kRows + 1];
+            qstart[0] = 0;
+#pragma unroll
+            for (int w = 0; w < kRows; ++w) qstart[w + 1] = qstart[w] + s_qn[w][wid];
+            const int cnt = qstart[kRows];
+            for (int e0 = 0; e0 < cnt; e0 += 32) {
+                const int e = e0 + lane;
+                int i = 0, ka = 0, kb = -1, span = 0;
+                if (e < cnt) {
+                    int w = 0, off = 0;
+#pragma unroll
+                    for (int q = 1; q < kRows; ++q)
+                        if (e >= qstart[q]) {
+                            w = q;
+                            off = qstart[q];
+                        }
+                    i = s_q[w][wid][e - off];
+                    const int4 bb = bbox[i];
+                    const CullData d = load_cull(rec, i);
+                    span = row_span_in_box(d, g, ty, max(bb.x, 0), min(bb.z, g.Wt), ka, kb);
+                }
+                if (!EMIT) {
+                    if (span > 0) {
+                        atomicAdd(cols + ka, 1);
+                        atomicAdd(cols + kb + 1, -1);
+                    }
+                    continue;
+                }
+                const int incl = warp_incl_scan(span);
+                const int excl = incl - span;
+                const int total = __shfl_sync(kFullMask, incl, 31);
+                for (int k0 = 0; k0 < total; k0 += 32) {
+                    const int kk = k0 + lane;
+                    const int sl = lane_of(incl, min(kk, total - 1));  // lane holding pair kk's record
+                    const int tx = __shfl_sync(kFullMask, ka, sl) + (kk - __shfl_sync(kFullMask, excl, sl));
+                    const int rid = __shfl_sync(kFullMask, i, sl);
+                    const unsigned act = __ballot_sync(kFullMask, kk < total);
+                    int base = 0, before = 0;
+                    bool last = false;
+                    if (kk < total) {
+                        const unsigned peers = __match_any_sync(act, tx);
+                        before = __popc(peers & lt_mask);
+                        last = (peers >> lane) == 1u;  // no higher lane on this tile
+                        base = cols[tx];
+                    }
+                    __syncwarp();
+                    if (kk < total) {
+                        const int64_t at = (int64_t)base + before;
+                        if (at < limit) vals[at] = (uint32_t)rid;  // limit: the pair count (defensive)
+                        if (last) cols[tx] = base + before + 1;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();  // the next round rewrites the queues
     }
-    if (!EMIT) {
+    if (!EMIT && has_row) {
+        // prefix of the difference array: the chunk's pairs on each tile of the row
         __syncwarp();
-        for (int k = lane; k < band_tiles; k += 32) mrow[k] = ctr[k];
+        int carry = 0;
+        for (int x0 = 0; x0 < g.Wt; x0 += 32) {
+            const int x = x0 + lane;
+            const int dv = x < g.Wt ? cols[x] : 0;
+            const int sc = warp_incl_scan(dv) + carry;
+            if (x < g.Wt) mrow[x] = sc;
+            carry = __shfl_sync(kFullMask, sc, 31);
+        }
     }
 }
 
-__device__ __forceinline__ int band_tiles_of(const Shape &s, int vb) {
-    const int band = vb % s.nb;
-    const int r0 = band * s.BR, r1 = min(r0 + s.BR, s.g.Ht);
-    return (r1 - r0) * s.g.Wt;
-}
-
-// part[seg][k] = sum of column k over the kSeg units of segment seg (a segment lies in one band).
-__global__ void __launch_bounds__(kColThreads) colsum_kernel(const int32_t *__restrict__ mat, Shape s,
-                                                             const int4 *__restrict__ desc,
-                                                             const Plan *__restrict__ plan,
-                                                             int32_t *__restrict__ part) {
-    const int64_t seg = blockIdx.y;
-    if (seg * kSeg >= plan->units) return;
-    const int k = blockIdx.x * kColThreads + threadIdx.x;
-    if (k >= band_tiles_of(s, desc[seg * kSeg].x)) return;
-    const int32_t *m = mat + seg * kSeg * (int64_t)s.bt + k;
+// part[seg][t] of item z = sum of the counts of the segment's chunks on tile t.
+__global__ void __launch_bounds__(kColThreads) col_part_kernel(const int32_t *__restrict__ mat, Shape s,
+                                                               int32_t *__restrict__ part) {
+    const BItem &it = s.it[blockIdx.z];
+    const int t = blockIdx.x * kColThreads + threadIdx.x;
+    const int seg = blockIdx.y;
+    if (t >= it.T || seg >= it.nseg) return;
+    const int c0 = seg * kSegChunks, nc = min(kSegChunks, it.nc - c0);
+    const int32_t *m = mat + it.mat0 + (int64_t)c0 * it.T + t;
     int sum = 0;
-#pragma unroll 8
-    for (int r = 0; r < kSeg; ++r) sum += m[(int64_t)r * s.bt];
-    part[seg * (int64_t)s.bt + k] = sum;
+#pragma unroll
+    for (int c = 0; c < kSegChunks; ++c) sum += c < nc ? m[(int64_t)c * it.T] : 0;
+    part[it.part0 + (int64_t)seg * it.T + t] = sum;
 }
 
-// Per band and column: exclusive prefix over the band's segments (in place) and the tile total.
-__global__ void __launch_bounds__(kColThreads) segscan_kernel(int32_t *__restrict__ part, Shape s,
-                                                              const int32_t *__restrict__ bandfirst,
+// Per tile: exclusive prefix over the segments (in place) and the tile's total.
+__global__ void __launch_bounds__(kColThreads) col_seg_kernel(int32_t *__restrict__ part, Shape s,
                                                               int32_t *__restrict__ tot) {
-    const int vb = blockIdx.y;
-    const int k = blockIdx.x * kColThreads + threadIdx.x;
-    if (k >= band_tiles_of(s, vb)) return;
-    const int64_t g0 = bandfirst[vb] / kSeg, g1 = bandfirst[vb + 1] / kSeg;
+    const BItem &it = s.it[blockIdx.y];
+    const int t = blockIdx.x * kColThreads + threadIdx.x;
+    if (t >= it.T) return;
+    int32_t *p = part + it.part0 + t;
     int run = 0;
-    for (int64_t g = g0; g < g1; ++g) {
-        int32_t *p = part + g * (int64_t)s.bt + k;
+    for (int seg = 0; seg < it.nseg; ++seg, p += it.T) {
         const int x = *p;
         *p = run;
         run += x;
     }
-    const int v = vb / s.nb, band = vb - v * s.nb;
-    tot[(int64_t)v * s.T1 + (int64_t)band * s.BR * s.g.Wt + k] = run;
+    tot[it.tile0 + t] = run;
 }
 
-// Matrix entries -> first output position of the (unit, tile); a band's first segment also
-// writes the tile ranges (an empty tile gets [0, 0), as from the key sort's segment search).
-__global__ void __launch_bounds__(kColThreads) apply_kernel(int32_t *__restrict__ mat, const int32_t *__restrict__ part,
-                                                            const int32_t *__restrict__ start, Shape s,
-                                                            const int4 *__restrict__ desc,
-                                                            const int32_t *__restrict__ bandfirst,
-                                                            const Plan *__restrict__ plan, int2 *__restrict__ ranges) {
-    const int64_t seg = blockIdx.y;
-    if (seg * kSeg >= plan->units) return;
-    const int vb = desc[seg * kSeg].x;
-    const int k = blockIdx.x * kColThreads + threadIdx.x;
-    if (k >= band_tiles_of(s, vb)) return;
-    const int v = vb / s.nb, band = vb - v * s.nb;
-    const int64_t gt = (int64_t)v * s.T1 + (int64_t)band * s.BR * s.g.Wt + k;
-    if (seg * kSeg == bandfirst[vb]) {
+// Counts -> output position of each (chunk, tile)'s first pair; the first segment also writes the
+// tile ranges (an empty tile gets [0, 0), as from the key sort's segment search).
+__global__ void __launch_bounds__(kColThreads) col_apply_kernel(int32_t *__restrict__ mat,
+                                                                const int32_t *__restrict__ part,
+                                                                const int32_t *__restrict__ start, Shape s,
+                                                                int2 *__restrict__ ranges) {
+    const BItem &it = s.it[blockIdx.z];
+    const int t = blockIdx.x * kColThreads + threadIdx.x;
+    const int seg = blockIdx.y;
+    if (t >= it.T || seg >= it.nseg) return;
+    const int64_t gt = it.tile0 + t;
+    if (seg == 0) {
         const int a = start[gt], b = start[gt + 1];
         ranges[gt] = b > a ? make_int2(a, b) : make_int2(0, 0);
     }
-    int run = start[gt] + part[seg * (int64_t)s.bt + k];
-    int32_t *m = mat + seg * kSeg * (int64_t)s.bt + k;
-    for (int r = 0; r < kSeg; ++r) {
-        const int x = m[(int64_t)r * s.bt];
-        m[(int64_t)r * s.bt] = run;
-        run += x;
+    const int c0 = seg * kSegChunks, nc = min(kSegChunks, it.nc - c0);
+    int run = start[gt] + part[it.part0 + (int64_t)seg * it.T + t];
+    int32_t *m = mat + it.mat0 + (int64_t)c0 * it.T + t;
+    int x[kSegChunks];  // all loads issued before the first store (they do not wait on each other)
+#pragma unroll
+    for (int c = 0; c < kSegChunks; ++c) x[c] = c < nc ? m[(int64_t)c * it.T] : 0;
+#pragma unroll
+    for (int c = 0; c < kSegChunks; ++c) {
+        if (c < nc) m[(int64_t)c * it.T] = run;
+        run += x[c];
     }
+}
+
+int run_binsort(const Shape &s, const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order,
+                int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect, void *ws, size_t ws_bytes,
+                cudaStream_t st, const char *fn) {
+    Ws w;
+    const size_t need = carve(s, ws, &w);
+    if (ws_bytes < need) return fail(XPR_ERR_INVALID, "%s: workspace %zu < %zu bytes", fn, ws_bytes, need);
+    if (s.mat_entries > 0x7fffffffLL || s.S > 0x7fffffffLL || s.blocks < 0)
+        return fail(XPR_ERR_INVALID, "%s: too many tiles", fn);
+    *n_isect = 0;
+    bool any = false;
+    int max_wt = 0;
+    for (int k = 0; k < s.K; ++k) {
+        any |= s.it[k].n > 0;
+        max_wt = std::max(max_wt, s.it[k].g.Wt);
+    }
+    if (!any || s.S == 0) {
+        if (s.S) XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)s.S * 2 * sizeof(int32_t), st));
+        return XPR_OK;
+    }
+    // One fixed limit for every call: concurrent callers (other host threads, other grid sizes) must
+    // never lower it below what a launch in flight on another stream was checked against.
+    const int smem_max = kRows * (kMaxCols + 1) * (int)sizeof(int32_t);
+    XPR_CUDA_TRY(cudaFuncSetAttribute(rowband_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+    XPR_CUDA_TRY(cudaFuncSetAttribute(rowband_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+    const size_t smem = (size_t)kRows * (max_wt + 1) * sizeof(int32_t);
+    const int4 *bb4 = reinterpret_cast<const int4 *>(bbox);
+    rowband_kernel<false><<<(unsigned)s.blocks, kRows * 32, smem, st>>>(rec, bb4, tc, order, s, w.mat, nullptr, 0);
+    XPR_LAUNCH_CHECK("rowband_kernel<count>");
+    const dim3 cgrid((unsigned)((s.max_T + kColThreads - 1) / kColThreads), (unsigned)s.max_nseg, (unsigned)s.K);
+    col_part_kernel<<<cgrid, kColThreads, 0, st>>>(w.mat, s, w.part);
+    XPR_LAUNCH_CHECK("col_part_kernel");
+    col_seg_kernel<<<dim3(cgrid.x, (unsigned)s.K), kColThreads, 0, st>>>(w.part, s, w.tot);
+    XPR_LAUNCH_CHECK("col_seg_kernel");
+    int r = launch_exclusive_scan(w.tot, w.tot, s.S, w.scan, nullptr, st);
+    if (r) return r;
+    col_apply_kernel<<<cgrid, kColThreads, 0, st>>>(w.mat, w.part, w.tot, s, reinterpret_cast<int2 *>(ranges));
+    XPR_LAUNCH_CHECK("col_apply_kernel");
+    int64_t total = 0;
+    XPR_CUDA_TRY(cudaMemcpyAsync(&total, scan_total_ptr(w.scan, s.S), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    XPR_CUDA_TRY(cudaStreamSynchronize(st));
+    *n_isect = total;
+    if (total > 0x7fffffffLL)
+        return fail(XPR_ERR_CAPACITY, "%s: %lld intersections exceed 2^31-1", fn, (long long)total);
+    if (total > capacity)
+        return fail(XPR_ERR_CAPACITY, "%s: %lld intersections > capacity %lld", fn, (long long)total,
+                    (long long)capacity);
+    if (total == 0) return XPR_OK;
+    if (!vals) return fail(XPR_ERR_INVALID, "%s: NULL vals", fn);
+    rowband_kernel<true><<<(unsigned)s.blocks, kRows * 32, smem, st>>>(rec, bb4, tc, order, s, w.mat, vals, total);
+    XPR_LAUNCH_CHECK("rowband_kernel<emit>");
+    return XPR_OK;
 }
 
 }  // namespace
 
 size_t binsort_workspace_bytes(int64_t n, int n_views, const XprCamera &cam, const XprConfig &cfg) {
-    return carve(make_shape(n, n_views, cam, cfg), nullptr, nullptr);
+    return carve(make_views_shape(n, n_views, cam, cfg), nullptr, nullptr);
 }
 
 bool binsort_supported(const XprCamera &cam, const XprConfig &cfg, int n_views) {
     const Grid g = make_grid(cam, cfg);
-    // packed 16-bit box coordinates; one band row of counters per warp fits (<= 200 KB per block);
-    // the unit budget holds at least two units per (band, chunk) for every band of every view
-    if (g.Wt > kMaxBandCols || g.Ht >= 32768) return false;
-    const int BR = max(1, min(8, 2048 / g.Wt));
-    return (int64_t)n_views * ((g.Ht + BR - 1) / BR) <= kMaxBands;
+    return g.Wt <= kMaxCols && n_views >= 1 && n_views <= kMaxViews;
 }
 
 int launch_binsort(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                    int n_views, const XprCamera &cam, const XprConfig &cfg, int32_t *ranges, uint32_t *vals,
                    int64_t capacity, int64_t *n_isect, void *ws, size_t ws_bytes, cudaStream_t st) {
-    const Shape s = make_shape(n, n_views, cam, cfg);
-    Ws w;
-    const size_t need = carve(s, ws, &w);
-    if (ws_bytes < need) return fail(XPR_ERR_INVALID, "xpr_bin_sorted: workspace %zu < %zu bytes", ws_bytes, need);
-    const int64_t nr = n * n_views, nt = (int64_t)s.T1 * n_views, vb = (int64_t)n_views * s.nb;
-    if ((int64_t)s.Q * (s.bt + kKappa) > 0x7fffffffLL)
-        return fail(XPR_ERR_INVALID, "xpr_bin_sorted: %lld records per view are too many", (long long)n);
-    *n_isect = 0;
-    if (nr == 0) {
-        XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)nt * 2 * sizeof(int32_t), st));
-        return XPR_OK;
+    if (n > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "xpr_bin_sorted: %lld records per view", (long long)n);
+    return run_binsort(make_views_shape(n, n_views, cam, cfg), rec, bbox, tc, order, ranges, vals, capacity, n_isect,
+                       ws, ws_bytes, st, "xpr_bin_sorted");
+}
+
+static Shape items_shape(const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg) {
+    Grid grids[kMaxItems];
+    int64_t nn[kMaxItems], p0[kMaxItems];
+    for (int k = 0; k < n_items; ++k) {
+        grids[k] = make_grid(cams[k], cfg);
+        nn[k] = items[k].n;
+        p0[k] = items[k].rec_offset;
     }
-    const size_t smem = (size_t)kUnitWarps * s.bt * sizeof(int32_t);
-    if (smem > (size_t)kWalkSmemMax) return fail(XPR_ERR_INVALID, "xpr_bin_sorted: %zu bytes of counters", smem);
-    // One fixed limit for every call: concurrent callers (other host threads, other grid sizes) must
-    // never lower it below what a launch in flight on another stream was checked against.
-    XPR_CUDA_TRY(cudaFuncSetAttribute(walk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWalkSmemMax));
-    XPR_CUDA_TRY(cudaFuncSetAttribute(walk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWalkSmemMax));
-    XPR_CUDA_TRY(cudaMemsetAsync(w.plan, 0, sizeof(Plan), st));
+    return make_shape(n_items, grids, nn, p0);
+}
 
-    gather_box_kernel<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(reinterpret_cast<const int4 *>(bbox), tc, order,
-                                                                     nr, s.g, w.box);
-    XPR_LAUNCH_CHECK("gather_box_kernel");
-    const unsigned chunk_blocks = (unsigned)(((int64_t)n_views * s.npc + 7) / 8);
-    const size_t band_smem = (size_t)8 * s.nb * sizeof(int32_t);
-    chunk_cost_kernel<<<chunk_blocks, 256, band_smem, st>>>(w.box, s, w.cost, w.plan);
-    XPR_LAUNCH_CHECK("chunk_cost_kernel");
-    plan_band_kernel<<<(unsigned)vb, kPlanThreads, 0, st>>>(w.cost, s, w.plan, w.lofs, w.bandu);
-    XPR_LAUNCH_CHECK("plan_band_kernel");
-    int r = launch_exclusive_scan(w.bandu, w.bandu, vb, w.scan_bands, nullptr, st);
-    if (r) return r;
-    describe_units_kernel<<<(unsigned)vb, 256, 0, st>>>(w.cost, w.lofs, w.bandu, s, w.plan, w.desc);
-    XPR_LAUNCH_CHECK("describe_units_kernel");
-    cut_units_kernel<<<chunk_blocks, 256, band_smem, st>>>(w.box, s, w.lofs, w.bandu, w.cost, w.plan, w.ustart);
-    XPR_LAUNCH_CHECK("cut_units_kernel");
+size_t binsort_items_workspace_bytes(const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg) {
+    return carve(items_shape(cams, items, n_items, cfg), nullptr, nullptr);
+}
 
-    const unsigned walk_blocks = (unsigned)(s.max_units / kUnitWarps);
-    walk_kernel<false><<<walk_blocks, kUnitWarps * 32, smem, st>>>(rec, order, w.box, s, w.desc, w.ustart, w.plan,
-                                                                   w.mat, nullptr);
-    XPR_LAUNCH_CHECK("walk_kernel<count>");
-    const dim3 cgrid((unsigned)((s.bt + kColThreads - 1) / kColThreads), (unsigned)(s.max_units / kSeg));
-    colsum_kernel<<<cgrid, kColThreads, 0, st>>>(w.mat, s, w.desc, w.plan, w.part);
-    XPR_LAUNCH_CHECK("colsum_kernel");
-    segscan_kernel<<<dim3(cgrid.x, (unsigned)vb), kColThreads, 0, st>>>(w.part, s, w.bandu, w.tot);
-    XPR_LAUNCH_CHECK("segscan_kernel");
-    if ((r = launch_exclusive_scan(w.tot, w.start, nt, w.scan_tiles, nullptr, st))) return r;
-    apply_kernel<<<cgrid, kColThreads, 0, st>>>(w.mat, w.part, w.start, s, w.desc, w.bandu, w.plan,
-                                                reinterpret_cast<int2 *>(ranges));
-    XPR_LAUNCH_CHECK("apply_kernel");
-    int64_t total = 0;
-    XPR_CUDA_TRY(cudaMemcpyAsync(&total, scan_total_ptr(w.scan_tiles, nt), sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                 st));
-    XPR_CUDA_TRY(cudaStreamSynchronize(st));
-    *n_isect = total;
-    if (total > 0x7fffffffLL)
-        return fail(XPR_ERR_CAPACITY, "xpr_bin_sorted: %lld intersections exceed 2^31-1", (long long)total);
-    if (total > capacity)
-        return fail(XPR_ERR_CAPACITY, "xpr_bin_sorted: %lld intersections > capacity %lld", (long long)total,
-                    (long long)capacity);
-    if (total == 0) return XPR_OK;
-    if (!vals) return fail(XPR_ERR_INVALID, "xpr_bin_sorted: NULL vals");
-    walk_kernel<true><<<walk_blocks, kUnitWarps * 32, smem, st>>>(rec, order, w.box, s, w.desc, w.ustart, w.plan,
-                                                                  w.mat, vals);
-    XPR_LAUNCH_CHECK("walk_kernel<emit>");
-    return XPR_OK;
+bool binsort_items_supported(const XprCamera *cams, int n_items, const XprConfig &cfg) {
+    for (int k = 0; k < n_items; ++k)
+        if (make_grid(cams[k], cfg).Wt > kMaxCols) return false;
+    return true;
+}
+
+int launch_binsort_items(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order,
+                         const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg,
+                         int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect, void *ws,
+                         size_t ws_bytes, cudaStream_t st) {
+    return run_binsort(items_shape(cams, items, n_items, cfg), rec, bbox, tc, order, ranges, vals, capacity, n_isect,
+                       ws, ws_bytes, st, "xpr_bin_sorted_items");
 }
 
 }  // namespace xpr

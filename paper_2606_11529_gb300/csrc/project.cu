@@ -375,7 +375,171 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) project_bwd_kernel(
     }
 }
 
+// ---- multi-scene items: item k projects primitives [prim0, prim0 + n) of the concatenated arrays
+// with camera k into its records [rec0, rec0 + n) (a block of whole warps: rec0 is a multiple of 32).
+struct ItemSet {
+    int count;
+    int64_t rec0[kMaxItems + 1];  // first record of each item, then the total
+    int64_t prim0[kMaxItems];
+    int64_t n[kMaxItems];
+    XprCamera cam[kMaxItems];
+};
+
+__device__ __forceinline__ int item_of_record(const ItemSet &is, int64_t r) {
+    int k = 0;
+#pragma unroll 1
+    while (k + 1 < is.count && r >= is.rec0[k + 1]) ++k;
+    return k;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjWarps * 32) project_items_kernel(
+    const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
+    const float *__restrict__ opac, const float *__restrict__ sh, ItemSet is, XprConfig cfg,
+    float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount) {
+    constexpr int LD = sh_ld<DEG>();
+    extern __shared__ float s_fwd[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * kProjWarps + w) * 32;  // first record of the warp
+    if (base >= is.rec0[is.count]) return;
+    const int k = item_of_record(is, base);  // warp-uniform: items start at multiples of 32
+    const int64_t local = base - is.rec0[k];
+    const int nv = (int)max((int64_t)0, min((int64_t)32, is.n[k] - local));
+    const int64_t r = base + lane;
+    if (nv == 0) {  // padding records of the item's block: invisible
+        float4 *o4 = reinterpret_cast<float4 *>(rec + (size_t)r * XPR_REC_FLOATS);
+        o4[0] = o4[1] = o4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        bbox[r] = make_int4(0, 0, 0, 0);
+        tcount[r] = 0;
+        return;
+    }
+    const int64_t p0 = is.prim0[k] + local;
+    float *ssh = s_fwd + (size_t)w * 32 * LD;
+    stage_sh<DEG>(sh, p0, nv, ssh);
+    if (lane >= nv) {
+        float4 *o4 = reinterpret_cast<float4 *>(rec + (size_t)r * XPR_REC_FLOATS);
+        o4[0] = o4[1] = o4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        bbox[r] = make_int4(0, 0, 0, 0);
+        tcount[r] = 0;
+        return;
+    }
+    const Params P = load_params(mu, scale, quat, opac, p0 + lane);
+    CullData cd;
+    int4 bb;
+    int area;
+    project_view<DEG>(P, ssh + lane * LD, r, is.cam[k], cfg, rec, bbox, tcount, cd, bb, area);
+}
+
+// Adjoint of the items' projection: each record's gradient is added (atomically: several items
+// may view one scene) into its scene primitive's entries of the concatenated gradient arrays.
+template <int DEG>
+__global__ void __launch_bounds__(kBwdWarps * 32) project_bwd_items_kernel(
+    const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
+    const float *__restrict__ opac, const float *__restrict__ sh, ItemSet is, XprConfig cfg,
+    const float *__restrict__ d_rec, float *__restrict__ gmu, float *__restrict__ gscale, float *__restrict__ gquat,
+    float *__restrict__ gopac, float *__restrict__ gsh) {
+    constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
+    constexpr int LD = sh_ld<DEG>();
+    extern __shared__ float s_bwd[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * kBwdWarps + w) * 32;
+    if (base >= is.rec0[is.count]) return;
+    const int k = item_of_record(is, base);
+    const int64_t local = base - is.rec0[k];
+    const int nv = (int)max((int64_t)0, min((int64_t)32, is.n[k] - local));
+    if (nv == 0) return;
+    const int64_t p0 = is.prim0[k] + local;
+    float *ssh = s_bwd + (size_t)w * 2 * 32 * LD;
+    float *sdsh = ssh + 32 * LD;
+    stage_sh<DEG>(sh, p0, nv, ssh);
+    for (int c = 0; c < KC; ++c) sdsh[lane * LD + c] = 0.f;
+    __syncwarp();
+    if (lane < nv) {
+        const int64_t i = p0 + lane, r = base + lane;
+        const Params P = load_params(mu, scale, quat, opac, i);
+        const Cam kc = make_cam(is.cam[k], cfg);
+        Geo G;
+        geometry(P, kc, cfg.cov_dilation, G);
+        if (footprint(G, P.o, kc, cfg).vis) {
+            Acc<DEG> A = {};
+            const float4 *D4 = reinterpret_cast<const float4 *>(d_rec + (size_t)r * XPR_REC_FLOATS);
+            adjoint_view<DEG>(P, ssh + lane * LD, sdsh + lane * LD, G, kc, __ldg(D4), __ldg(D4 + 1), __ldg(D4 + 2), A);
+            const float dot = A.qn[0] * G.qn[0] + A.qn[1] * G.qn[1] + A.qn[2] * G.qn[2] + A.qn[3] * G.qn[3];
+            for (int j = 0; j < 3; ++j) {
+                atomicAdd(gmu + 3 * i + j, A.mu[j]);
+                atomicAdd(gscale + 3 * i + j, A.s[j]);
+            }
+            for (int j = 0; j < 4; ++j) atomicAdd(gquat + 4 * i + j, (A.qn[j] - G.qn[j] * dot) * G.qinv);
+            atomicAdd(gopac + i, A.o);
+        }
+    }
+    __syncwarp();
+    float *go = gsh + p0 * KC;
+    for (int e = lane; e < nv * KC; e += 32) {
+        const int pi = e / KC;
+        const float x = sdsh[pi * LD + (e - pi * KC)];
+        if (x != 0.f) atomicAdd(go + e, x);
+    }
+}
+
+ItemSet make_itemset(const XprCamera *cams, const XprItem *items, int n_items) {
+    ItemSet is;
+    memset(&is, 0, sizeof(is));
+    is.count = n_items;
+    for (int k = 0; k < n_items; ++k) {
+        is.rec0[k] = items[k].rec_offset;
+        is.prim0[k] = items[k].prim_offset;
+        is.n[k] = items[k].n;
+        is.cam[k] = cams[k];
+    }
+    is.rec0[n_items] = items[n_items - 1].rec_offset + (items[n_items - 1].n + 31) / 32 * 32;
+    return is;
+}
+
 }  // namespace
+
+int launch_project_items(const XprPrims &p, const XprCamera *cams, const XprItem *items, int n_items,
+                         const XprConfig &cfg, float *rec, int32_t *bbox, int32_t *tc, cudaStream_t st) {
+    const ItemSet is = make_itemset(cams, items, n_items);
+    const int64_t R = is.rec0[n_items];
+    if (R == 0) return XPR_OK;
+    const int tpb = kProjWarps * 32;
+    const unsigned blocks = (unsigned)((R + tpb - 1) / tpb);
+    XPR_DEG_DISPATCH(DEG, project_items_kernel<DEG><<<blocks, tpb,
+                                                       (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
+                              p.mu, p.scale, p.quat, p.opacity, p.sh, is, cfg, rec, reinterpret_cast<int4 *>(bbox),
+                              tc));
+    XPR_LAUNCH_CHECK("project_items_kernel");
+    return XPR_OK;
+}
+
+int launch_project_bwd_items(const XprPrims &p, int64_t n_prims, const XprCamera *cams, const XprItem *items,
+                             int n_items, const XprConfig &cfg, const float *d_rec, const XprPrimsGrad &g,
+                             cudaStream_t st) {
+    const int K = (cfg.sh_degree + 1) * (cfg.sh_degree + 1);
+    XPR_CUDA_TRY(cudaMemsetAsync(g.mu, 0, (size_t)n_prims * 3 * sizeof(float), st));
+    XPR_CUDA_TRY(cudaMemsetAsync(g.scale, 0, (size_t)n_prims * 3 * sizeof(float), st));
+    XPR_CUDA_TRY(cudaMemsetAsync(g.quat, 0, (size_t)n_prims * 4 * sizeof(float), st));
+    XPR_CUDA_TRY(cudaMemsetAsync(g.opacity, 0, (size_t)n_prims * sizeof(float), st));
+    XPR_CUDA_TRY(cudaMemsetAsync(g.sh, 0, (size_t)n_prims * K * 3 * sizeof(float), st));
+    const ItemSet is = make_itemset(cams, items, n_items);
+    const int64_t R = is.rec0[n_items];
+    if (R == 0) return XPR_OK;
+    const int tpb = kBwdWarps * 32;
+    const unsigned blocks = (unsigned)((R + tpb - 1) / tpb);
+    cudaError_t attr = cudaSuccess;
+    XPR_DEG_DISPATCH(DEG, {
+        const size_t smem = (size_t)kBwdWarps * 2 * 32 * sh_ld<DEG>() * sizeof(float);
+        attr = cudaFuncSetAttribute(project_bwd_items_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+        if (attr == cudaSuccess)
+            project_bwd_items_kernel<DEG><<<blocks, tpb, smem, st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, is, cfg,
+                                                                     d_rec, g.mu, g.scale, g.quat, g.opacity, g.sh);
+    });
+    XPR_CUDA_TRY(attr);
+    XPR_LAUNCH_CHECK("project_bwd_items_kernel");
+    return XPR_OK;
+}
 
 int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams, int n_views, const XprConfig &cfg,
                              float *rec, int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st,

@@ -46,7 +46,35 @@ struct Consts {
     uint32_t n;       // number of records: list entries >= n are ignored
     int batch;        // entries staged per batch, 1 .. kMaxBatch
     float at, amax, teps, bg0, bg1, bg2;
+    ItemTable it;     // multi-scene launch: per-item grids (it.count 0: uniform views)
 };
+
+// Where global tile gt lies: its item (or view), tile index within it, the item's image size and
+// tiles per row, and its first pixel in the per-pixel buffers.
+struct TileLoc {
+    int v, tile, W, H, Wt;
+    int64_t pix0;
+};
+
+__device__ __forceinline__ TileLoc locate(int gt, const Consts &k) {
+    TileLoc l;
+    if (k.it.count > 0) {
+        l.v = item_of_tile(k.it, gt);
+        l.tile = (int)(gt - k.it.tile0[l.v]);
+        l.W = k.it.W[l.v];
+        l.H = k.it.H[l.v];
+        l.Wt = k.it.Wt[l.v];
+        l.pix0 = k.it.pix0[l.v];
+    } else {
+        l.v = gt / k.T;
+        l.tile = gt - l.v * k.T;
+        l.W = k.W;
+        l.H = k.H;
+        l.Wt = k.Wt;
+        l.pix0 = (int64_t)l.v * k.W * k.H;
+    }
+    return l;
+}
 
 struct Work {  // persistent scheduling: tiles list[0 .. count) taken through *counter
     const int *list;
@@ -101,8 +129,8 @@ __device__ __forceinline__ void fwd_tile(int gt, const float *__restrict__ rec, 
     constexpr int NT = TW * TH / kPX;
     constexpr int RS = TH / kPX;  // rows between a thread's pixels
     static_assert(NT % 32 == 0, "a tile's block must be whole warps");
-    const int v = gt / k.T, tile = gt - v * k.T;
-    const int tx = tile % k.Wt, ty = tile / k.Wt;
+    const TileLoc L = locate(gt, k);
+    const int tx = L.tile % L.Wt, ty = L.tile / L.Wt;
     const int t = threadIdx.x;
     const int px = tx * TW + t % TW, py = ty * TH + t / TW;
     const int2 rg = ranges[gt];
@@ -112,7 +140,7 @@ __device__ __forceinline__ void fwd_tile(int gt, const float *__restrict__ rec, 
     bool all_done = true;
 #pragma unroll
     for (int q = 0; q < kPX; ++q) {
-        in[q] = px < k.W && py + q * RS < k.H;
+        in[q] = px < L.W && py + q * RS < L.H;
         P[q] = PixelFwd{(float)(py + q * RS), 1.f, 0.f, 0.f, 0.f, 0, !in[q]};
         all_done &= P[q].done;
     }
@@ -138,17 +166,17 @@ __device__ __forceinline__ void fwd_tile(int gt, const float *__restrict__ rec, 
             }
         }
     }
-    const int64_t HW = (int64_t)k.W * k.H;
-    float *img = image + (int64_t)v * 3 * HW;
+    const int64_t HW = (int64_t)L.W * L.H;
+    float *img = image + 3 * L.pix0;
 #pragma unroll
     for (int q = 0; q < kPX; ++q) {
         if (!in[q]) continue;
-        const int64_t pix = (int64_t)(py + q * RS) * k.W + px;
+        const int64_t pix = (int64_t)(py + q * RS) * L.W + px;
         img[pix] = fmaf(P[q].T, k.bg0, P[q].r);
         img[HW + pix] = fmaf(P[q].T, k.bg1, P[q].g);
         img[2 * HW + pix] = fmaf(P[q].T, k.bg2, P[q].b);
-        tfin[v * HW + pix] = P[q].T;
-        ncon[v * HW + pix] = P[q].last;
+        tfin[L.pix0 + pix] = P[q].T;
+        ncon[L.pix0 + pix] = P[q].last;
     }
 }
 
@@ -275,23 +303,23 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
     constexpr int NW = NT / 32;
     constexpr int RS = TH / kPX;
     static_assert(NT % 32 == 0, "a tile's block must be whole warps");
-    const int v = gt / k.T, tile = gt - v * k.T;
-    const int tx = tile % k.Wt, ty = tile / k.Wt;
+    const TileLoc L = locate(gt, k);
+    const int tx = L.tile % L.Wt, ty = L.tile / L.Wt;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const int px = tx * TW + t % TW, py = ty * TH + t / TW;
     const int2 rg = ranges[gt];
     const float fx = (float)px;
-    const int64_t HW = (int64_t)k.W * k.H;
-    const float *tf = tfin + v * HW;
-    const int *nc = ncon + v * HW;
-    const float *di = dimg + (int64_t)v * 3 * HW;
+    const int64_t HW = (int64_t)L.W * L.H;
+    const float *tf = tfin + L.pix0;
+    const int *nc = ncon + L.pix0;
+    const float *di = dimg + 3 * L.pix0;
     PixelBwd P[kPX];
     int mylast = 0;
 #pragma unroll
     for (int q = 0; q < kPX; ++q) {
         const int y = py + q * RS;
-        const bool in = px < k.W && y < k.H;
-        P[q] = load_pixel_bwd(in, (float)y, (int64_t)y * k.W + px, HW, tf, nc, di, k);
+        const bool in = px < L.W && y < L.H;
+        P[q] = load_pixel_bwd(in, (float)y, (int64_t)y * L.W + px, HW, tf, nc, di, k);
         mylast = max(mylast, P[q].last);
     }
     const int wlast = __reduce_max_sync(kFull, mylast);
@@ -399,6 +427,7 @@ Consts make_consts(const XprCamera &cam, const XprConfig &cfg, int64_t n) {
     k.bg0 = cfg.bg[0];
     k.bg1 = cfg.bg[1];
     k.bg2 = cfg.bg[2];
+    k.it.count = 0;
     return k;
 }
 
@@ -455,6 +484,57 @@ int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_
     XPR_TILE_DISPATCH(TW, TH, {
         const int threads = TW * TH / px_per_thread<TW, TH>();
         const int grid = worklist ? persistent_grid(render_bwd_kernel<TW, TH>, threads, items) : items;
+        render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, t_final, n_contrib, d_image, d_rec, w);
+    });
+    XPR_LAUNCH_CHECK("render_bwd_kernel");
+    return XPR_OK;
+}
+
+// Multi-scene launches: the tiles of every item in one grid (a persistent one over worklist when
+// given); records are the items' concatenated blocks (n_rec in all).
+int launch_render_fwd_items(const float *rec, int64_t n_rec, const uint32_t *vals, const int32_t *ranges,
+                            const ItemTable &it, const XprConfig &cfg, float *image, float *t_final,
+                            int32_t *n_contrib, const int32_t *worklist, int32_t *counter, cudaStream_t st) {
+    XprCamera dummy = {};
+    dummy.width = it.W[0];
+    dummy.height = it.H[0];
+    Consts k = make_consts(dummy, cfg, n_rec);
+    k.it = it;
+    const int64_t items = it.tile0[it.count];
+    if (items == 0) return XPR_OK;
+    if (items > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "xpr_render_fwd_items: too many tiles");
+    const int2 *rg = reinterpret_cast<const int2 *>(ranges);
+    Work w = {worklist, counter, (int)items};
+    if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
+    XPR_TILE_DISPATCH(TW, TH, {
+        const int threads = TW * TH / px_per_thread<TW, TH>();
+        const int grid = worklist ? persistent_grid(render_fwd_kernel<TW, TH>, threads, (int)items) : (int)items;
+        render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, image, t_final, n_contrib, w);
+    });
+    XPR_LAUNCH_CHECK("render_fwd_kernel");
+    return XPR_OK;
+}
+
+int launch_render_bwd_items(const float *rec, int64_t n_rec, const uint32_t *vals, const int32_t *ranges,
+                            const ItemTable &it, const XprConfig &cfg, const float *t_final,
+                            const int32_t *n_contrib, const float *d_image, float *d_rec, const int32_t *worklist,
+                            int32_t *counter, cudaStream_t st) {
+    XPR_CUDA_TRY(cudaMemsetAsync(d_rec, 0, (size_t)n_rec * XPR_REC_FLOATS * sizeof(float), st));
+    XprCamera dummy = {};
+    dummy.width = it.W[0];
+    dummy.height = it.H[0];
+    Consts k = make_consts(dummy, cfg, n_rec);
+    k.it = it;
+    k.batch = min(k.batch, kBwdBatch);
+    const int64_t items = it.tile0[it.count];
+    if (items == 0) return XPR_OK;
+    if (items > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "xpr_render_bwd_items: too many tiles");
+    const int2 *rg = reinterpret_cast<const int2 *>(ranges);
+    Work w = {worklist, counter, (int)items};
+    if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
+    XPR_TILE_DISPATCH(TW, TH, {
+        const int threads = TW * TH / px_per_thread<TW, TH>();
+        const int grid = worklist ? persistent_grid(render_bwd_kernel<TW, TH>, threads, (int)items) : (int)items;
         render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, t_final, n_contrib, d_image, d_rec, w);
     });
     XPR_LAUNCH_CHECK("render_bwd_kernel");

@@ -39,6 +39,31 @@ int validate_camera_config(const XprCamera *cam, const XprConfig *cfg);
 
 // ---- launch helpers implemented per translation unit -------------------------------------
 constexpr int kMaxViews = 16;  // views per multi-view launch (cameras travel as a kernel argument)
+constexpr int kMaxItems = 16;  // (scene, camera) items per multi-scene launch
+
+// Per-item tile grids and image placement of a multi-scene launch (count 0: the uniform views of
+// one camera size).  Item k owns global tiles [tile0[k], tile0[k + 1]) and the pixels
+// [pix0[k], pix0[k] + W[k] H[k]) of the per-pixel buffers (its image planes at 3 pix0[k]).
+struct ItemTable {
+    int count;
+    int W[kMaxItems], H[kMaxItems], Wt[kMaxItems];
+    int64_t tile0[kMaxItems + 1];
+    int64_t pix0[kMaxItems];
+};
+
+// Checks a host item array against its cameras and config (offsets contiguous and in order,
+// records aligned to 32) and fills the table; returns an XprStatus.
+int make_item_table(const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg,
+                    ItemTable &t, int64_t *n_records, const char *fn);
+#ifdef __CUDACC__
+// The item holding global tile gt (tile0 is increasing; at most kMaxItems items).
+__device__ __forceinline__ int item_of_tile(const ItemTable &t, int64_t gt) {
+    int k = 0;
+#pragma unroll 1
+    while (k + 1 < t.count && gt >= t.tile0[k + 1]) ++k;
+    return k;
+}
+#endif
 
 int launch_project_fwd(const XprPrims &p, int64_t n, const XprCamera &cam, const XprConfig &cfg, float *rec,
                        int32_t *bbox, int32_t *tc, int32_t *isect_count, cudaStream_t st,
@@ -59,6 +84,20 @@ int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_
                             const XprCamera &cam, const XprConfig &cfg, const float *t_final,
                             const int32_t *n_contrib, const float *d_image, float *d_rec, int64_t n,
                             const int32_t *worklist, int32_t *counter, cudaStream_t st);
+int launch_project_items(const XprPrims &p, const XprCamera *cams, const XprItem *items, int n_items,
+                         const XprConfig &cfg, float *rec, int32_t *bbox, int32_t *tc, cudaStream_t st);
+int launch_project_bwd_items(const XprPrims &p, int64_t n_prims, const XprCamera *cams, const XprItem *items,
+                             int n_items, const XprConfig &cfg, const float *d_rec, const XprPrimsGrad &g,
+                             cudaStream_t st);
+int launch_depth_order_items(const float *rec, const int32_t *tc, const XprItem *items, int n_items, int32_t *order,
+                             void *ws, size_t ws_bytes, cudaStream_t st);
+int launch_render_fwd_items(const float *rec, int64_t n_rec, const uint32_t *vals, const int32_t *ranges,
+                            const ItemTable &it, const XprConfig &cfg, float *image, float *t_final,
+                            int32_t *n_contrib, const int32_t *worklist, int32_t *counter, cudaStream_t st);
+int launch_render_bwd_items(const float *rec, int64_t n_rec, const uint32_t *vals, const int32_t *ranges,
+                            const ItemTable &it, const XprConfig &cfg, const float *t_final,
+                            const int32_t *n_contrib, const float *d_image, float *d_rec, const int32_t *worklist,
+                            int32_t *counter, cudaStream_t st);
 // tiles sorted by descending list length (ranges[t,1] - ranges[t,0]), for persistent scheduling
 size_t worklist_workspace_bytes(int32_t n_tiles);
 int launch_tile_worklist(const int32_t *ranges, int32_t n_tiles, int32_t *worklist, void *ws, size_t ws_bytes,
@@ -131,6 +170,13 @@ bool binsort_supported(const XprCamera &cam, const XprConfig &cfg, int n_views);
 int launch_binsort(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                    int n_views, const XprCamera &cam, const XprConfig &cfg, int32_t *ranges, uint32_t *vals,
                    int64_t capacity, int64_t *n_isect, void *ws, size_t ws_bytes, cudaStream_t st);
+
+size_t binsort_items_workspace_bytes(const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg);
+bool binsort_items_supported(const XprCamera *cams, int n_items, const XprConfig &cfg);
+int launch_binsort_items(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order,
+                         const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg,
+                         int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect, void *ws,
+                         size_t ws_bytes, cudaStream_t st);
 
 size_t sort_workspace_bytes(int64_t n, int32_t n_tiles);
 int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,

@@ -10,13 +10,18 @@ module is the request loop around the same forward stages:
   fits in the pool that the in-flight requests have not reserved; admission is
   FIFO, so a large request is not starved by smaller ones behind it, and a
   request larger than the whole pool is rejected;
-* ``slots`` worker threads each own a CUDA stream; a free worker takes the
-  oldest admitted request together with any other admitted requests for the
-  same scene and image size (up to 16 views) and renders them as one
-  multi-view batch (one launch per stage); so several batches are in flight at
-  once, on different streams;
-* a request is ready when its image has reached pinned host memory; the
-  worker then frees its reservation and admits what now fits.
+* one host thread runs the loop: it takes arrivals as they come, and whenever
+  one of ``slots`` CUDA streams is free and requests are admitted, it takes the
+  oldest admitted requests, whatever their scene and image size (up to 16), and
+  launches them as one multi-scene batch (one launch per stage for all of them,
+  the tiles of every request in one persistent work list), then copies the
+  images to pinned host memory and records an event; so several batches are in
+  flight at once, on different streams, and a request arriving while the GPU is
+  busy joins the next batch instead of queueing behind single renders;
+* the loop polls the batches' events; a request is ready when its image has
+  reached pinned host memory; its reservation is then freed and what now fits
+  is admitted.  One thread with no hand-off between threads keeps the dispatch
+  latency of an isolated request at the plain path's.
 
 The plain baseline renders the same trace one request at a time, in arrival
 order, through the per-stage single-view path.
@@ -29,7 +34,6 @@ from __future__ import annotations
 import collections
 import dataclasses
 import math
-import threading
 import time
 
 import numpy as np
@@ -145,18 +149,12 @@ class Scheduler:
             self.admitted.append(r)
 
     def take_batch(self, now: float) -> list[Request]:
-        """The oldest admitted request and the next admitted ones with the same scene and size."""
+        """The oldest admitted requests, any scene and size, up to max_views of them."""
         if not self.admitted:
             return []
-        head = self.admitted.popleft()
-        batch, rest = [head], collections.deque()
-        while self.admitted:
-            r = self.admitted.popleft()
-            if r.key == head.key and len(batch) < self.max_views:
-                batch.append(r)
-            else:
-                rest.append(r)
-        self.admitted = rest
+        batch = []
+        while self.admitted and len(batch) < self.max_views:
+            batch.append(self.admitted.popleft())
         for r in batch:
             r.status, r.start, r.batch_views = "running", now, len(batch)
         self.in_flight += 1
@@ -189,6 +187,23 @@ def latency_stats(reqs: list[Request], warmup: int = 0) -> dict:
 
 # ------------------------------------------------------------------------------------------ device side
 
+def footprint_bytes_items(n_prims: int, width: int, height: int, n_isect: int, cfg) -> int:
+    """Device working memory of one request rendered as an item of a multi-scene batch: records,
+    boxes, counts and depth order of its padded record block, the depth-order scratch, the fused
+    bin + sort's count matrix and scans, the pair buffer at the capacity asked for, the tile ranges
+    and work list, and the image planes."""
+    from . import binding as B
+    L = B.load()
+    R = (n_prims + 31) // 32 * 32
+    tw, th = int(cfg.tile_w), int(cfg.tile_h)
+    nt = ((width + tw - 1) // tw) * ((height + th - 1) // th)
+    cap = int(n_isect * 1.25) + 1024
+    chunks = max(1, (n_prims + 4095) // 4096)
+    binsort = chunks * nt * 4 + (chunks // 32 + 1) * nt * 4 + (nt + 1) * 4 + 4096
+    return int(R * (12 * 4 + 16 + 4 + 4) + int(L.xpr_depth_order_workspace(R)) + binsort + cap * 4 +
+               int(L.xpr_tile_worklist_workspace(nt)) + nt * 12 + width * height * (3 * 4 + 4 + 4))
+
+
 def footprint_bytes(n_prims: int, width: int, height: int, n_isect: int, cfg, n_views: int = 1) -> int:
     """Device working memory of one forward of ``n_views`` views (every buffer the stages
     allocate: records, bounding boxes, counts, depth order, offsets, the pair buffers at the
@@ -219,13 +234,18 @@ def _wait_until(t_abs: float):
 class Server:
     """Continuous-batching renderer over resident scenes (see the module docstring).
 
-    ``scenes``: list of (mu, scale, quat, opacity, sh) device tensors, one tuple per scene.
-    ``pool_bytes``: working-memory pool for the in-flight requests (the resident scenes are
-    outside it).  ``slots``: worker threads, one CUDA stream each."""
+    ``scenes``: a ``batched.SceneSet`` (the resident scenes as one concatenated parameter set; its
+    ``views()`` are the per-scene tensors), or a list of per-scene (mu, scale, quat, opacity, sh)
+    tuples, concatenated here.  ``pool_bytes``: working-memory pool for the in-flight requests
+    (the resident scenes are outside it).  ``slots``: batches in flight, one CUDA stream each."""
 
-    def __init__(self, scenes, cfg, pool_bytes: int, slots: int = 3, capacity_factor: float = 1.3,
+    def __init__(self, scenes, cfg, pool_bytes: int, slots: int = 2, capacity_factor: float = 1.3,
                  max_views: int = MAX_VIEWS, deliver_host: bool = True, keep_images: bool = True):
-        self.scenes = scenes
+        if scenes is not None and not hasattr(scenes, "views") and len(scenes) and scenes[0] is not None:
+            from . import batched as BT
+            scenes = BT.SceneSet(scenes)
+        self.scene_set = scenes if hasattr(scenes, "views") else None
+        self.scenes = self.scene_set.views() if self.scene_set is not None else scenes
         self.cfg = cfg
         self.slots = slots
         self.capacity_factor = capacity_factor
@@ -235,10 +255,10 @@ class Server:
         self.keep_images = keep_images
         self.budget = HBMBudget(pool_bytes)
         self.sched = Scheduler(self.budget, max_views)
-        self.cv = threading.Condition()
         self.calib = {}
         self.errors = []
-        self._stop = False
+        self._ws = {}
+        self._pinned = {}
 
     # intersections at the canonical pose of each (scene, size): the admission estimate
     def calibrate(self, resolutions=RESOLUTIONS):
@@ -256,65 +276,57 @@ class Server:
 
     def estimate(self, req: Request) -> int:
         n = int(self.scenes[req.scene][0].shape[0])
-        return footprint_bytes(n, req.width, req.height, self.n_isect_estimate(req), self.cfg)
-
-    def execute(self, batch: list[Request], stream):
-        """One view: the plain per-stage path; several views of one scene and size: one launch per
-        stage for all of them (the batched form).  Both give the same image bit for bit."""
-        import torch
-        from . import batched as BT
-        from . import render as R
-        P = self.scenes[batch[0].scene]
-        with torch.cuda.stream(stream):
-            if len(batch) == 1:
-                ws = R.Workspace()
-                ws.last_isect = int(self.n_isect_estimate(batch[0]) / 1.25)
-                fr = R.forward_frame(*P, camera_of(batch[0]), self.cfg, ws, stream=stream)
-                img = fr.image.unsqueeze(0)
-            else:
-                ws = BT.ViewsWorkspace()
-                ws.last_isect = int(sum(self.n_isect_estimate(r) for r in batch) / 1.25)
-                fr = BT.forward_views(*P, [camera_of(r) for r in batch], self.cfg, ws, stream=stream)
-                img = fr.image
-            if self.deliver_host:
-                out = torch.empty(tuple(img.shape), dtype=img.dtype, pin_memory=True)
-                out.copy_(img, non_blocking=True)
-            else:
-                out = img
-            stream.synchronize()
-        for v, r in enumerate(batch):
-            r.image = out[v] if self.keep_images else None
-            r.n_isect = fr.n_isect
-            r.delivered = True
+        return footprint_bytes_items(n, req.width, req.height, self.n_isect_estimate(req), self.cfg)
 
     def new_stream(self):
         import torch
         return torch.cuda.Stream()
 
-    def _worker(self, t0: float):
-        stream = self.new_stream()
-        while True:
-            with self.cv:
-                batch = []
-                while not self._stop:
-                    batch = self.sched.take_batch(time.perf_counter() - t0)
-                    if batch:
-                        break
-                    self.cv.wait(0.01)  # arrivals and completions notify; the timeout is a backstop
-                if not batch:
-                    return
-            try:
-                self.execute(batch, stream)
-            except Exception as e:  # recorded and re-raised by run()
-                self.errors.append(e)
-                for r in batch:
-                    r.status = "error"
-            with self.cv:
-                self.sched.complete([r for r in batch], time.perf_counter() - t0)
-                for r in batch:
-                    if not r.delivered:
-                        r.status = "error"
-                self.cv.notify_all()
+    def _pinned_buffer(self, stream, nfloats):
+        import torch
+        key = id(stream)
+        buf = self._pinned.get(key)
+        if buf is None or buf.numel() < nfloats:
+            buf = torch.empty(int(nfloats), dtype=torch.float32).pin_memory()
+            self._pinned[key] = buf
+        return buf[:nfloats]
+
+    def launch(self, batch: list[Request], stream):
+        """Enqueues one multi-scene batch on ``stream`` (projection, depth order, fused bin + sort,
+        persistent render over every request's tiles, copy of the images to pinned host memory) and
+        returns the pending handle.  The fused bin + sort reads the pair count back, so this call
+        returns once the binning is done; the render and the copy run on."""
+        import torch
+        from . import batched as BT
+        ss = self.scene_set
+        cams = [camera_of(r) for r in batch]
+        layout = ss.layout([r.scene for r in batch], cams, self.cfg)
+        ws = self._ws.get(id(stream))
+        if ws is None:
+            ws = self._ws[id(stream)] = BT.ViewsWorkspace()
+        ws.last_isect = int(sum(self.n_isect_estimate(r) for r in batch) / 1.25)
+        with torch.cuda.stream(stream):
+            fr = BT.forward_items(*ss.params, layout, self.cfg, ws, stream=stream)
+            if self.deliver_host:
+                out = self._pinned_buffer(stream, fr.image.numel()) if not self.keep_images else \
+                    torch.empty(fr.image.numel(), dtype=torch.float32, pin_memory=True)
+                out.copy_(fr.image, non_blocking=True)
+            else:
+                out = fr.image
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return ev, out, layout, fr.n_isect
+
+    def is_done(self, handle) -> bool:
+        return handle[0].query()
+
+    def finish(self, batch: list[Request], handle):
+        _, out, layout, n_isect = handle
+        imgs = layout.images(out)
+        for r, im in zip(batch, imgs):
+            r.image = im if self.keep_images else None
+            r.n_isect = n_isect
+            r.delivered = True
 
     def run(self, trace: list[Request]) -> list[Request]:
         """Replays ``trace`` open-loop against the wall clock; returns it with times filled in."""
@@ -322,23 +334,56 @@ class Server:
             self.calibrate(sorted({(r.width, r.height) for r in trace}))
         for r in trace:
             r.nbytes = self.estimate(r)
-        self._stop = False
+        streams = [self.new_stream() for _ in range(self.slots)]
+        free = list(range(self.slots))
+        inflight = []  # (batch, handle, stream index)
         t0 = time.perf_counter()
-        workers = [threading.Thread(target=self._worker, args=(t0,), daemon=True) for _ in range(self.slots)]
-        for w in workers:
-            w.start()
-        for r in trace:
-            _wait_until(t0 + r.arrival)
-            with self.cv:
-                self.sched.arrive(r, time.perf_counter() - t0)
-                self.cv.notify_all()
-        with self.cv:
-            while not self.sched.idle() and not self.errors:
-                self.cv.wait(0.01)
-            self._stop = True
-            self.cv.notify_all()
-        for w in workers:
-            w.join()
+        nxt = 0
+        while True:
+            now = time.perf_counter() - t0
+            # completions (in launch order per stream; any order across streams)
+            still = []
+            for batch, handle, si in inflight:
+                if self.is_done(handle):
+                    try:
+                        self.finish(batch, handle)
+                    except Exception as e:  # recorded and re-raised below
+                        self.errors.append(e)
+                    now = time.perf_counter() - t0
+                    self.sched.complete(batch, now)
+                    for r in batch:
+                        if not r.delivered:
+                            r.status = "error"
+                    free.append(si)
+                else:
+                    still.append((batch, handle, si))
+            inflight = still
+            # arrivals
+            while nxt < len(trace) and trace[nxt].arrival <= now:
+                self.sched.arrive(trace[nxt], now)
+                nxt += 1
+            # dispatch: every free stream takes the oldest admitted requests
+            while free and self.sched.admitted and not self.errors:
+                batch = self.sched.take_batch(time.perf_counter() - t0)
+                si = free.pop(0)
+                try:
+                    inflight.append((batch, self.launch(batch, streams[si]), si))
+                except Exception as e:
+                    self.errors.append(e)
+                    self.sched.complete(batch, time.perf_counter() - t0)
+                    for r in batch:
+                        r.status = "error"
+                    free.append(si)
+            if self.errors and not inflight:
+                break
+            if nxt >= len(trace) and self.sched.idle():
+                break
+            if not inflight and not self.sched.admitted and nxt < len(trace):
+                # idle until the next arrival (sleep, then spin the last 0.3 ms)
+                wake = t0 + trace[nxt].arrival
+                d = wake - time.perf_counter()
+                if d > 3e-4:
+                    time.sleep(d - 3e-4)
         if self.errors:
             raise self.errors[0]
         return trace

@@ -1,7 +1,6 @@
 """Host logic of the serving form, without a GPU: the Poisson trace, footprint
-accounting, FIFO admission, batch formation, and the threaded continuous-batching
-loop driven by a fake executor (a sleep standing in for the render)."""
-import threading
+accounting, FIFO admission, batch formation, and the single-thread dispatch loop
+driven by a fake executor (a deadline standing in for the render)."""
 import time
 
 import numpy as np
@@ -58,30 +57,30 @@ def test_too_large_is_rejected():
     assert r.status == "rejected" and s.rejected == 1 and s.idle()
 
 
-def test_batches_group_same_scene_and_size_in_order():
+def test_batches_take_the_oldest_admitted_of_any_scene_and_size():
     s = SV.Scheduler(SV.HBMBudget(10 ** 9), max_views=3)
     keys = [(0, 512), (1, 512), (0, 512), (0, 1280), (0, 512), (0, 512), (1, 512)]
     for i, (sc, w) in enumerate(keys):
         s.arrive(_req(i, scene=sc, w=w, h=w), 0.0)
     b1 = s.take_batch(0.0)
-    assert [r.rid for r in b1] == [0, 2, 4]  # capped at max_views, oldest first
+    assert [r.rid for r in b1] == [0, 1, 2]  # capped at max_views, oldest first, scenes and sizes mixed
     assert all(r.batch_views == 3 and r.status == "running" for r in b1)
-    assert [r.rid for r in s.admitted] == [1, 3, 5, 6]
+    assert [r.rid for r in s.admitted] == [3, 4, 5, 6]
     b2 = s.take_batch(0.0)
-    assert [r.rid for r in b2] == [1, 6]
+    assert [r.rid for r in b2] == [3, 4, 5]
     assert s.in_flight == 2
 
 
 class FakeServer(SV.Server):
-    """Server whose render is a sleep proportional to the pixel count."""
+    """Server whose batch "runs" for a time proportional to its pixel count (no device)."""
 
     def __init__(self, pool, slots, service_s=0.002, **kw):
         super().__init__(scenes=[None] * 4, cfg=None, pool_bytes=pool, slots=slots, **kw)
         self.service_s = service_s
         self.calib = {"fake": 1}
-        self.lock = threading.Lock()
         self.running = 0
         self.max_running = 0
+        self.batches = []
 
     def estimate(self, req):
         return req.width * req.height  # bytes ~ pixels
@@ -89,21 +88,28 @@ class FakeServer(SV.Server):
     def new_stream(self):
         return None
 
-    def execute(self, batch, stream):
-        with self.lock:
-            self.running += 1
-            self.max_running = max(self.max_running, self.running)
-            assert self.budget.used <= self.budget.capacity
-        time.sleep(self.service_s * batch[0].width * batch[0].height / 512 ** 2)
-        with self.lock:
+    def launch(self, batch, stream):
+        assert self.budget.used <= self.budget.capacity
+        self.running += 1
+        self.max_running = max(self.max_running, self.running)
+        self.batches.append(len(batch))
+        pixels = sum(r.width * r.height for r in batch)
+        return time.perf_counter() + self.service_s * pixels / 512 ** 2
+
+    def is_done(self, handle):
+        done = time.perf_counter() >= handle
+        if done:
             self.running -= 1
+        return done
+
+    def finish(self, batch, handle):
         for r in batch:
             r.image = r.rid
             r.delivered = True
 
 
 @pytest.mark.parametrize("slots", [1, 3])
-def test_threaded_loop_completes_everything(slots):
+def test_dispatch_loop_completes_everything(slots):
     trace = SV.make_trace(300, n_scenes=4, rate_hz=2000.0, seed=1)
     srv = FakeServer(pool=2 * 1920 * 1080, slots=slots)
     srv.run(trace)
@@ -114,6 +120,7 @@ def test_threaded_loop_completes_everything(slots):
         assert r.arrival <= r.admitted <= r.start <= r.ready
     st = SV.latency_stats(trace, warmup=20)
     assert st["completed"] == 280 and st["p50_ms"] <= st["p99_ms"]
+    assert max(srv.batches) > 1  # requests that arrive while the streams are busy are batched
 
 
 def test_pool_gates_concurrency():
@@ -138,9 +145,9 @@ def test_latency_stats_on_known_values():
 
 
 def test_undelivered_request_is_an_error():
-    # a worker whose execute returns without delivering marks its batch failed
+    # a batch that completes without delivering its images is marked failed
     class Undelivering(FakeServer):
-        def execute(self, batch, stream):
+        def finish(self, batch, handle):
             pass
 
     trace = SV.make_trace(20, n_scenes=2, rate_hz=5000.0, seed=3)
