@@ -425,23 +425,27 @@ def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     arrivals at 200 requests/s, sizes 512x512 / 1280x720 / 1920x1080; the continuous-batching server
     against the plain one-at-a-time queue on the same trace, then the server under a small pool."""
     import torch
+    from paper_2606_11529_gb300 import batched as BT
     from paper_2606_11529_gb300 import render as R
     from paper_2606_11529_gb300 import scenes
     from paper_2606_11529_gb300 import serve as SV
     t0 = time.perf_counter()
-    resident = [tuple(t.to(dev) for t in R.scene_to_device(s))
-                for s in scenes.serving_scenes(16, seed=0, scale_down=scale_down)]
+    # the resident scenes as one concatenated parameter set; both paths read its per-scene views
+    sset = BT.SceneSet([tuple(t.to(dev) for t in R.scene_to_device(s))
+                        for s in scenes.serving_scenes(16, seed=0, scale_down=scale_down)])
+    resident = sset.views()
     gen_s = time.perf_counter() - t0
     cfg = scenes.RenderConfig(sh_degree=3)
     free, _ = torch.cuda.mem_get_info(dev)
     pool = int(max(free - (16 << 30), 8 << 30))
     # the client consumes each image once delivered (pinned output buffers are recycled)
-    srv = SV.Server(resident, cfg, pool_bytes=pool, slots=3, keep_images=False)
+    srv = SV.Server(sset, cfg, pool_bytes=pool, slots=2, keep_images=False)
     srv.calibrate()
     # warm every (scene, size) once so lazy module loading and allocator growth stay outside
     SV.run_plain(resident, cfg, SV.make_trace(48, rate_hz=1e6, seed=99), srv, keep_images=False)
-    # and a burst through the server, so that each worker stream's allocator pool has grown too
+    # and a burst through the server, so that each stream's allocator pool has grown too
     srv.run(SV.make_trace(192, rate_hz=1e6, seed=98))
+    srv.run(SV.make_trace(192, rate_hz=2000.0, seed=97))
     trace = SV.make_trace(n_requests + warmup, rate_hz=200.0, seed=0)
     srv.run(trace)
     ours = SV.latency_stats(trace, warmup)
@@ -458,7 +462,7 @@ def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     SV.run_plain(resident, cfg, hptrace, srv, keep_images=False)
     hi["plain_queue"] = SV.latency_stats(hptrace, warmup // 2)
     n_cap = max(n_requests // 4, 100)
-    capped = SV.Server(resident, cfg, pool_bytes=int(cap_gb * 2 ** 30), slots=3, keep_images=False)
+    capped = SV.Server(sset, cfg, pool_bytes=int(cap_gb * 2 ** 30), slots=2, keep_images=False)
     capped.calib = srv.calib
     ctrace = SV.make_trace(n_cap + warmup // 4, rate_hz=200.0, seed=1)
     capped.run(ctrace)
@@ -468,7 +472,7 @@ def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     return {"workload": f"16 resident clustered SH-3 scenes ({sum(scene_prims)} Gaussians, "
                         f"{min(scene_prims)}-{max(scene_prims)} per scene), Poisson 200 req/s, "
                         "512x512 / 1280x720 / 1920x1080 (f = width), forward only, image delivered to pinned host",
-            "requests": n_requests, "warmup_requests": warmup, "slots": 3,
+            "requests": n_requests, "warmup_requests": warmup, "slots": 2,
             "p50_ms": ours["p50_ms"], "p99_ms": ours["p99_ms"], "views_per_s": ours["views_per_s"],
             "server": ours, "plain_queue": plain, "capped_pool": cst, "rate_400": hi,
             "resident_gb": round(sum(sum(t.numel() * 4 for t in s) for s in resident) / 2 ** 30, 3),
@@ -534,6 +538,11 @@ def main():
         return 0
 
     sc, cam, cfg = scenes.headline_case(args.n)
+    if world > 1:
+        # view-parallel training step: rank r renders view r of the step (the headline camera turned
+        # by r degrees), then one packed NCCL all-reduce sums the primitive gradients over the ranks
+        cam = scenes.pinhole(cam.width, cam.height, cam.fx, scenes.yaw_view(float(rank)))
+    from paper_2606_11529_gb300 import parallel as PL
     host = [torch.from_numpy(a).pin_memory() for a in sc.arrays()]
     P = [h.to(dev).requires_grad_(True) for h in host]
     w = torch.from_numpy(np.random.default_rng(1).normal(size=(3, cam.height, cam.width)).astype(np.float32)).to(dev)
@@ -546,6 +555,8 @@ def main():
         img = R.render(*P, cam, cfg, ws, timers)
         loss = (img * w).sum()
         loss.backward()
+        if world > 1:
+            PL.allreduce_sum([p.grad for p in P])
         return loss
 
     clocks = ClockSampler(local)
@@ -682,6 +693,8 @@ def main():
         img = R.render(*P, cam, cfg, ws)
         loss = (img * w).sum()
         loss.backward()
+        if world > 1:
+            PL.allreduce_sum([p.grad for p in P])
         img_host.copy_(img.detach(), non_blocking=True)
         for g, p in zip(grad_host, P):
             g.copy_(p.grad, non_blocking=True)
@@ -739,7 +752,9 @@ def main():
                                "views_per_s_total": round(world * 1000.0 / ms, 2),
                                "fused_bin_sort_path_ms": round(key_ms, 4)},
             "l2": "flushed between steps (256 MB write outside the timed events)",
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "parallelism": (f"view-parallel x{world}: one view per rank, one packed NCCL all-reduce of the "
+                            f"{sum(p.numel() for p in P) * 4 // 2 ** 20} MB of gradients per step") if world > 1
+            else "single GPU",
             "roofline": roof,
             "stages": stages,
             "batched": batched,
