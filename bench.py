@@ -291,6 +291,58 @@ def batched_leg(dev, reps, flush, method=0):
             "timing": f"median of {reps} (L2 flushed before each)"}
 
 
+def scenes_leg(dev, reps, flush):
+    """Multi-scene batched form: 4 clustered SH-3 scenes of uneven size (drawn as the serving
+    workload's) seen by 2 cameras each at different resolutions (8 items), forward + backward of all
+    8 in one launch per stage, against 8 plain single-view passes."""
+    import numpy as np
+    import torch
+    from paper_2606_11529_gb300 import batched as BT
+    from paper_2606_11529_gb300 import render as R
+    from paper_2606_11529_gb300 import scenes
+    from paper_2606_11529_gb300 import serve as SV
+    scs = scenes.serving_scenes(16, seed=0)[:4]
+    cfg = scenes.RenderConfig(sh_degree=3)
+    sset = BT.SceneSet([tuple(t.to(dev) for t in R.scene_to_device(s)) for s in scs])
+    res = [(1920, 1080), (512, 512), (1280, 720), (1920, 1080), (512, 512), (1280, 720), (1280, 720), (512, 512)]
+    soi = [0, 0, 1, 1, 2, 2, 3, 3]
+    cams = [scenes.pinhole(w, h, float(w), scenes.yaw_view(3.0 * (k - 4), (0.01 * k, 0.0, 0.0)))
+            for k, (w, h) in enumerate(res)]
+    layout = sset.layout(soi, cams, cfg)
+    rng = np.random.default_rng(4)
+    wts = [torch.from_numpy(rng.normal(size=(3, h, w)).astype(np.float32)).to(dev) for (w, h) in res]
+    P = [p.detach().requires_grad_(True) for p in sset.params]
+    views = [tuple(t[o:o + n] for t in P) for o, n in zip(sset.offsets, sset.counts)]
+    ws = BT.ViewsWorkspace()
+
+    def batched():
+        for p in P:
+            p.grad = None
+        imgs = BT.render_items(*P, layout, cfg, ws)
+        sum((im * w).sum() for im, w in zip(imgs, wts)).backward()
+
+    wss = [R.Workspace() for _ in cams]
+
+    def plain():
+        for p in P:
+            p.grad = None
+        for k, (s_, cam) in enumerate(zip(soi, cams)):
+            (R.render(*views[s_], cam, cfg, wss[k]) * wts[k]).sum().backward()
+
+    for _ in range(3):
+        batched()
+        plain()
+    torch.cuda.synchronize()
+    tb = _median_ms(batched, reps, flush)
+    tp = _median_ms(plain, reps, flush)
+    fr = BT.forward_items(*sset.params, layout, cfg, BT.ViewsWorkspace())
+    return {"workload": f"4 clustered SH-3 scenes of uneven size ({', '.join(str(c) for c in sset.counts)} Gaussians), "
+                        "2 cameras each at 1920x1080 / 512x512 / 1280x720 (f = width): 8 (scene, camera) items, "
+                        "fwd+bwd of all 8, seed 0",
+            "ms_batched": round(tb, 3), "ms_plain_8x": round(tp, 3), "speedup": round(tp / tb, 3),
+            "intersections": fr.n_isect, "timing": f"median of {reps} (L2 flushed before each)"}
+
+
 def ut_leg(dev, n, reps, flush, fisheye=False):
     """3DGUT form: the headline scene (1M clustered SH-3 Gaussians, 1920x1080 pinhole, or the fisheye
     of the 3DGUT configuration with the same focal length) with the unscented projection, ray-offset
@@ -499,6 +551,8 @@ def main():
     ap.add_argument("--ut-fisheye", action="store_true", help="with --ut-only: render through the fisheye camera")
     ap.add_argument("--lp-only", action="store_true",
                     help="run only the LinPrim leg and print it as its own JSON line (for profiling captures)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving leg and print it as its own JSON line")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-cap-gb", type=float, default=4.0)
@@ -524,6 +578,13 @@ def main():
     dev = torch.device("cuda", local)
     L = B.load()
     set_alu_peak(dev)
+
+    if args.serve_only:
+        out = {"leg": "serve", "serve": serve_leg(dev, args.serve_requests, args.serve_warmup, args.serve_cap_gb,
+                                                  args.serve_scale_down)}
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
 
     if args.ut_only or args.lp_only or args.feat_only:
         flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
@@ -733,6 +794,7 @@ def main():
     feat = None if args.no_feat else feat_leg(dev, args.n, max(args.steps, 5), flush)
     batched = None if args.no_batched else batched_leg(dev, max(args.steps // 2, 5), flush)
     batched_ut = None if (args.no_batched or args.no_ut) else batched_leg(dev, max(args.steps // 2, 5), flush, 1)
+    batched_scenes = None if args.no_batched else scenes_leg(dev, max(args.steps // 2, 5), flush)
     serve = None
     if not args.no_serve:
         torch.cuda.empty_cache()
@@ -759,6 +821,7 @@ def main():
             "stages": stages,
             "batched": batched,
             "batched_3dgut": batched_ut,
+            "batched_scenes": batched_scenes,
             "serve": serve,
             "ut": ut,
             "linprim": lp,

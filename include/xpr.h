@@ -375,6 +375,23 @@ int xpr_project_bwd_items(const XprPrims *prims, int64_t n_prims, const XprCamer
                           int32_t n_items, const XprConfig *cfg, const float *d_rec, const XprPrimsGrad *d_prims,
                           void *stream);
 
+/* xpr_forward_items: the whole forward of a multi-scene batch in one call (the
+ * serving runtime's entry point): xpr_project_items, xpr_depth_order_items,
+ * xpr_bin_sorted_items, xpr_tile_worklist and xpr_render_fwd_items with the
+ * work list, every intermediate carved from one caller-owned workspace
+ * (device, 256-byte aligned) of xpr_forward_items_workspace(cams, items, K,
+ * cfg, capacity) bytes, where capacity is the room for intersection pairs.
+ * Outputs as xpr_render_fwd_items: image[3 * pixels], t_final[pixels],
+ * n_contrib[pixels] (device).  *n_isect (HOST) receives the pair count; if it
+ * exceeds capacity the call returns XPR_ERR_CAPACITY before rendering (call
+ * again with a workspace sized for at least that many pairs).  Synchronises
+ * the stream once (the pair count). */
+size_t xpr_forward_items_workspace(const XprCamera *cams, const XprItem *items, int32_t n_items, const XprConfig *cfg,
+                                   int64_t capacity);
+int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprItem *items, int32_t n_items,
+                      const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, int64_t capacity,
+                      int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
+
 /* xpr_project_color: the view-dependent colour of Listing 1 project (the SH
  * part of compute_color) for records already projected with prims->sh NULL:
  * for every visible record v * n + i (rec[.,11] != 0), rec[.,6..8] =

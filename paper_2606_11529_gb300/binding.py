@@ -138,6 +138,11 @@ SIGNATURES = {
     "xpr_project_bwd_items": (c_i32, [ctypes.POINTER(XprPrims), c_i64, ctypes.POINTER(XprCamera),
                                       ctypes.POINTER(XprItem), c_i32, ctypes.POINTER(XprConfig), c_vp,
                                       ctypes.POINTER(XprPrimsGrad), c_vp]),
+    "xpr_forward_items_workspace": (c_sz, [ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem), c_i32,
+                                           ctypes.POINTER(XprConfig), c_i64]),
+    "xpr_forward_items": (c_i32, [ctypes.POINTER(XprPrims), ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem), c_i32,
+                                  ctypes.POINTER(XprConfig), c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz,
+                                  c_vp]),
     "xpr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "xpr_last_error": (ctypes.c_char_p, []),
     "xpr_version": (ctypes.c_int, []),
@@ -733,6 +738,37 @@ def xpr_project_bwd_items(mu, scale, quat, opacity, sh, layout, cfg, d_rec, stre
     _check(L.xpr_project_bwd_items(ctypes.byref(p), mu.shape[0], layout.carr, layout.arr, layout.K, ctypes.byref(g),
                                    _ptr(d_rec), ctypes.byref(gp), _stream(stream)), "xpr_project_bwd_items")
     return grads
+
+
+def xpr_forward_items(mu, scale, quat, opacity, sh, layout, cfg, capacity, workspace=None, out=None, stream=None):
+    """The whole forward of a multi-scene batch in one C call.  Returns (image, t_final, n_contrib,
+    n_isect, workspace) with flat per-pixel outputs (``layout.images``); ``workspace`` (uint8,
+    grown here when too small, to be passed again) holds every intermediate.  On a capacity
+    shortfall the call is repeated once with room for the reported pair count."""
+    L = load()
+    dev = mu.device
+    g = _as_c(cfg, XprConfig)
+    p = _prims(mu, scale, quat, opacity, sh)
+    if out is None:
+        out = (torch.empty(3 * layout.pixels, dtype=torch.float32, device=dev),
+               torch.empty(layout.pixels, dtype=torch.float32, device=dev),
+               torch.empty(layout.pixels, dtype=torch.int32, device=dev))
+    image, tfin, ncon = out
+    cap = int(capacity)
+    for _ in range(2):
+        need = int(L.xpr_forward_items_workspace(layout.carr, layout.arr, layout.K, ctypes.byref(g), cap))
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+        got = c_i64(0)
+        s = L.xpr_forward_items(ctypes.byref(p), layout.carr, layout.arr, layout.K, ctypes.byref(g), _ptr(image),
+                                _ptr(tfin), _ptr(ncon), cap, ctypes.byref(got), _ptr(workspace), workspace.numel(),
+                                _stream(stream))
+        if s == XPR_ERR_CAPACITY and got.value <= 0x7FFFFFFF:
+            cap = int(got.value * 1.25) + 1024
+            continue
+        _check(s, "xpr_forward_items")
+        return image, tfin, ncon, int(got.value), workspace
+    raise XprError(XPR_ERR_CAPACITY, "xpr_forward_items", "capacity retry failed")
 
 
 # ---------------------------------------------------------------------------------------- 3DGUT

@@ -5,6 +5,8 @@
 
 #include <atomic>
 
+#include <algorithm>
+
 #include "xpr_internal.cuh"
 
 namespace xpr {
@@ -594,6 +596,99 @@ int xpr_project_bwd_items(const XprPrims *prims, int64_t n_prims, const XprCamer
     if (!aligned(prims->quat, 16) || !aligned(d_prims->quat, 16) || (d_rec && !aligned(d_rec, 16)))
         return fail(XPR_ERR_INVALID, "xpr_project_bwd_items: quat and d_rec must be 16-byte aligned");
     return launch_project_bwd_items(*prims, n_prims, cams, items, n_items, *cfg, d_rec, *d_prims, as_stream(stream));
+}
+
+// Workspace layout of xpr_forward_items (every part 256-byte aligned).
+struct FwdItemsWs {
+    size_t rec, bbox, tc, order, depth, binsort, vals, ranges, worklist, wl_ws, counter, total;
+};
+
+static FwdItemsWs fwd_items_layout(const XprCamera *cams, const XprItem *items, int32_t n_items, const XprConfig &cfg,
+                                   int64_t R, int64_t S, int64_t capacity) {
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    FwdItemsWs w;
+    size_t o = 0;
+    w.rec = o;
+    o += up((size_t)R * XPR_REC_FLOATS * 4);
+    w.bbox = o;
+    o += up((size_t)R * 16);
+    w.tc = o;
+    o += up((size_t)R * 4);
+    w.order = o;
+    o += up((size_t)R * 4);
+    w.depth = o;
+    o += up(depth_order_workspace_bytes(R));
+    w.binsort = o;
+    o += up(binsort_items_workspace_bytes(cams, items, n_items, cfg));
+    w.vals = o;
+    o += up((size_t)std::max<int64_t>(capacity, 1) * 4);
+    w.ranges = o;
+    o += up((size_t)S * 8);
+    w.worklist = o;
+    o += up((size_t)S * 4);
+    w.wl_ws = o;
+    o += up(worklist_workspace_bytes((int32_t)S));
+    w.counter = o;
+    o += 256;
+    w.total = o;
+    return w;
+}
+
+size_t xpr_forward_items_workspace(const XprCamera *cams, const XprItem *items, int32_t n_items, const XprConfig *cfg,
+                                   int64_t capacity) {
+    ItemTable t;
+    int64_t R = 0;
+    if (!cfg || capacity < 0 ||
+        make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_forward_items_workspace") != XPR_OK)
+        return 0;
+    return fwd_items_layout(cams, items, n_items, *cfg, R, t.tile0[n_items], capacity).total;
+}
+
+int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprItem *items, int32_t n_items,
+                      const XprConfig *cfg, float *image, float *t_final, int32_t *n_contrib, int64_t capacity,
+                      int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream) {
+    if (!cfg) return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL config");
+    ItemTable t;
+    int64_t R = 0;
+    int s = make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_forward_items");
+    if (s) return s;
+    if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_forward_items"))) return s;
+    if (!binsort_items_supported(cams, n_items, *cfg))
+        return fail(XPR_ERR_INVALID, "xpr_forward_items: a camera has more than 4096 tile columns");
+    if (!n_isect || capacity < 0) return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL n_isect or negative capacity");
+    const int64_t S = t.tile0[n_items];
+    if (!image || !t_final || !n_contrib || !workspace)
+        return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL output or workspace");
+    if (R > 0 && (!prims || !prims->mu || !prims->scale || !prims->quat || !prims->opacity || !prims->sh))
+        return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL primitive array");
+    if (R > 0 && !aligned(prims->quat, 16)) return fail(XPR_ERR_INVALID, "xpr_forward_items: quat alignment");
+    if (!aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_forward_items: workspace must be 256-byte aligned");
+    const FwdItemsWs L = fwd_items_layout(cams, items, n_items, *cfg, R, S, capacity);
+    if (ws_bytes < L.total)
+        return fail(XPR_ERR_INVALID, "xpr_forward_items: workspace %zu < %zu bytes", ws_bytes, L.total);
+    char *w = reinterpret_cast<char *>(workspace);
+    float *rec = reinterpret_cast<float *>(w + L.rec);
+    int32_t *bbox = reinterpret_cast<int32_t *>(w + L.bbox);
+    int32_t *tc = reinterpret_cast<int32_t *>(w + L.tc);
+    int32_t *order = reinterpret_cast<int32_t *>(w + L.order);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(w + L.vals);
+    int32_t *ranges = reinterpret_cast<int32_t *>(w + L.ranges);
+    int32_t *wl = reinterpret_cast<int32_t *>(w + L.worklist);
+    int32_t *counter = reinterpret_cast<int32_t *>(w + L.counter);
+    cudaStream_t st = as_stream(stream);
+    *n_isect = 0;
+    if (R > 0) {
+        if ((s = launch_project_items(*prims, cams, items, n_items, *cfg, rec, bbox, tc, st))) return s;
+        if ((s = launch_depth_order_items(rec, tc, items, n_items, order, w + L.depth,
+                                          depth_order_workspace_bytes(R), st)))
+            return s;
+    }
+    if ((s = launch_binsort_items(rec, bbox, tc, order, cams, items, n_items, *cfg, ranges, vals, capacity, n_isect,
+                                  w + L.binsort, binsort_items_workspace_bytes(cams, items, n_items, *cfg), st)))
+        return s;
+    if ((s = launch_tile_worklist(ranges, (int32_t)S, wl, w + L.wl_ws, worklist_workspace_bytes((int32_t)S), st)))
+        return s;
+    return launch_render_fwd_items(rec, R, vals, ranges, t, *cfg, image, t_final, n_contrib, wl, counter, st);
 }
 
 int xpr_project_color(const float *mu, const float *sh, int64_t n, const XprCamera *cams, int32_t n_views,

@@ -259,6 +259,10 @@ class Server:
         self.errors = []
         self._ws = {}
         self._pinned = {}
+        self._ccfg = None
+        if cfg is not None:
+            from . import binding as B
+            self._ccfg = B.make_config(cfg)
 
     # intersections at the canonical pose of each (scene, size): the admission estimate
     def calibrate(self, resolutions=RESOLUTIONS):
@@ -292,30 +296,31 @@ class Server:
         return buf[:nfloats]
 
     def launch(self, batch: list[Request], stream):
-        """Enqueues one multi-scene batch on ``stream`` (projection, depth order, fused bin + sort,
-        persistent render over every request's tiles, copy of the images to pinned host memory) and
-        returns the pending handle.  The fused bin + sort reads the pair count back, so this call
-        returns once the binning is done; the render and the copy run on."""
+        """Enqueues one multi-scene batch on ``stream`` through one native call (projection, depth
+        order, fused bin + sort, persistent render over every request's tiles), then the copy of
+        the images to pinned host memory, and returns the pending handle.  The native call reads
+        the pair count back, so it returns once the binning is done; the render and the copy run
+        on."""
         import torch
-        from . import batched as BT
+        from . import binding as B
         ss = self.scene_set
         cams = [camera_of(r) for r in batch]
-        layout = ss.layout([r.scene for r in batch], cams, self.cfg)
-        ws = self._ws.get(id(stream))
-        if ws is None:
-            ws = self._ws[id(stream)] = BT.ViewsWorkspace()
-        ws.last_isect = int(sum(self.n_isect_estimate(r) for r in batch) / 1.25)
+        layout = ss.layout([r.scene for r in batch], cams, self._ccfg)
+        key = id(stream)
+        cap = sum(self.n_isect_estimate(r) for r in batch)
         with torch.cuda.stream(stream):
-            fr = BT.forward_items(*ss.params, layout, self.cfg, ws, stream=stream)
+            image, _, _, n_isect, ws = B.xpr_forward_items(*ss.params, layout, self._ccfg, cap,
+                                                           workspace=self._ws.get(key), stream=stream)
+            self._ws[key] = ws
             if self.deliver_host:
-                out = self._pinned_buffer(stream, fr.image.numel()) if not self.keep_images else \
-                    torch.empty(fr.image.numel(), dtype=torch.float32, pin_memory=True)
-                out.copy_(fr.image, non_blocking=True)
+                out = self._pinned_buffer(stream, image.numel()) if not self.keep_images else \
+                    torch.empty(image.numel(), dtype=torch.float32, pin_memory=True)
+                out.copy_(image, non_blocking=True)
             else:
-                out = fr.image
+                out = image
             ev = torch.cuda.Event()
             ev.record(stream)
-        return ev, out, layout, fr.n_isect
+        return ev, out, layout, n_isect
 
     def is_done(self, handle) -> bool:
         return handle[0].query()

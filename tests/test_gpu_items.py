@@ -117,3 +117,17 @@ def test_items_reject_inconsistent_offsets():
     with pytest.raises(B.XprError) as e:
         B.xpr_project_items(*ss.params, layout, B.make_config(cfg))
     assert e.value.status == B.XPR_ERR_INVALID
+
+
+def test_native_forward_equals_staged_calls():
+    # xpr_forward_items (one call, every intermediate in one workspace) gives the staged path's
+    # outputs bit for bit, including after a capacity retry
+    scs, cams, soi = _batch()
+    cfg = scenes.RenderConfig(sh_degree=3, bg=(0.3, 0.2, 0.1))
+    ss = BT.SceneSet([R.scene_to_device(s) for s in scs])
+    layout = ss.layout(soi, cams, cfg)
+    ref = BT.forward_items(*ss.params, layout, cfg)
+    for cap in (ref.n_isect + 7, 16):
+        img, tf, nc, I, ws = B.xpr_forward_items(*ss.params, layout, B.make_config(cfg), cap)
+        assert I == ref.n_isect
+        assert torch.equal(img, ref.image) and torch.equal(tf, ref.t_final) and torch.equal(nc, ref.n_contrib)
