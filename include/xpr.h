@@ -376,9 +376,14 @@ int xpr_project_bwd_items(const XprPrims *prims, int64_t n_prims, const XprCamer
                           void *stream);
 
 /* xpr_forward_items: the whole forward of a multi-scene batch in one call (the
- * serving runtime's entry point): xpr_project_items, xpr_depth_order_items,
- * xpr_bin_sorted_items, xpr_tile_worklist and xpr_render_fwd_items with the
- * work list, every intermediate carved from one caller-owned workspace
+ * serving runtime's entry point): the items' projection with the exact
+ * kept-tile counts, xpr_depth_order_items, the offsets scan and the emission
+ * of (global tile id, record) pairs in depth order (as xpr_tile_bin, each
+ * record on its item's grid), xpr_sort_tiles over all items' tiles,
+ * xpr_tile_worklist and xpr_render_fwd_items with the work list (one block
+ * per tile for a single item; the same lists and images as the staged
+ * calls), every intermediate carved from one
+ * caller-owned workspace
  * (device, 256-byte aligned) of xpr_forward_items_workspace(cams, items, K,
  * cfg, capacity) bytes, where capacity is the room for intersection pairs.
  * Outputs as xpr_render_fwd_items: image[3 * pixels], t_final[pixels],

@@ -600,36 +600,35 @@ int xpr_project_bwd_items(const XprPrims *prims, int64_t n_prims, const XprCamer
 
 // Workspace layout of xpr_forward_items (every part 256-byte aligned).
 struct FwdItemsWs {
-    size_t rec, bbox, tc, order, depth, binsort, vals, ranges, worklist, wl_ws, counter, total;
+    size_t rec, bbox, tc, isect, order, depth, offsets, scan, tiles, vals_in, vals, sort, ranges, worklist, wl_ws,
+        counter, total;
 };
 
-static FwdItemsWs fwd_items_layout(const XprCamera *cams, const XprItem *items, int32_t n_items, const XprConfig &cfg,
-                                   int64_t R, int64_t S, int64_t capacity) {
+static FwdItemsWs fwd_items_layout(int64_t R, int64_t S, int64_t capacity) {
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t cap = (size_t)std::max<int64_t>(capacity, 1);
     FwdItemsWs w;
     size_t o = 0;
-    w.rec = o;
-    o += up((size_t)R * XPR_REC_FLOATS * 4);
-    w.bbox = o;
-    o += up((size_t)R * 16);
-    w.tc = o;
-    o += up((size_t)R * 4);
-    w.order = o;
-    o += up((size_t)R * 4);
-    w.depth = o;
-    o += up(depth_order_workspace_bytes(R));
-    w.binsort = o;
-    o += up(binsort_items_workspace_bytes(cams, items, n_items, cfg));
-    w.vals = o;
-    o += up((size_t)std::max<int64_t>(capacity, 1) * 4);
-    w.ranges = o;
-    o += up((size_t)S * 8);
-    w.worklist = o;
-    o += up((size_t)S * 4);
-    w.wl_ws = o;
-    o += up(worklist_workspace_bytes((int32_t)S));
-    w.counter = o;
-    o += 256;
+    auto take = [&](size_t &field, size_t bytes) {
+        field = o;
+        o += up(bytes);
+    };
+    take(w.rec, (size_t)R * XPR_REC_FLOATS * 4);
+    take(w.bbox, (size_t)R * 16);
+    take(w.tc, (size_t)R * 4);
+    take(w.isect, (size_t)R * 4);
+    take(w.order, (size_t)R * 4);
+    take(w.depth, depth_order_workspace_bytes(R));
+    take(w.offsets, ((size_t)R + 1) * 4);
+    take(w.scan, scan_partials_bytes(R));
+    take(w.tiles, cap * 4);
+    take(w.vals_in, cap * 4);
+    take(w.vals, cap * 4);
+    take(w.sort, sort_tiles_workspace_bytes((int64_t)cap, (int32_t)S));
+    take(w.ranges, (size_t)S * 8);
+    take(w.worklist, (size_t)S * 4);
+    take(w.wl_ws, worklist_workspace_bytes((int32_t)S));
+    take(w.counter, 256);
     w.total = o;
     return w;
 }
@@ -638,10 +637,10 @@ size_t xpr_forward_items_workspace(const XprCamera *cams, const XprItem *items, 
                                    int64_t capacity) {
     ItemTable t;
     int64_t R = 0;
-    if (!cfg || capacity < 0 ||
+    if (!cfg || capacity < 0 || capacity > 0x7fffffffLL ||
         make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_forward_items_workspace") != XPR_OK)
         return 0;
-    return fwd_items_layout(cams, items, n_items, *cfg, R, t.tile0[n_items], capacity).total;
+    return fwd_items_layout(R, t.tile0[n_items], capacity).total;
 }
 
 int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprItem *items, int32_t n_items,
@@ -653,9 +652,8 @@ int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprIte
     int s = make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_forward_items");
     if (s) return s;
     if ((s = need_method(cfg, XPR_METHOD_3DGS, "xpr_forward_items"))) return s;
-    if (!binsort_items_supported(cams, n_items, *cfg))
-        return fail(XPR_ERR_INVALID, "xpr_forward_items: a camera has more than 4096 tile columns");
-    if (!n_isect || capacity < 0) return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL n_isect or negative capacity");
+    if (!n_isect || capacity < 0 || capacity > 0x7fffffffLL)
+        return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL n_isect or capacity out of range");
     const int64_t S = t.tile0[n_items];
     if (!image || !t_final || !n_contrib || !workspace)
         return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL output or workspace");
@@ -663,29 +661,52 @@ int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprIte
         return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL primitive array");
     if (R > 0 && !aligned(prims->quat, 16)) return fail(XPR_ERR_INVALID, "xpr_forward_items: quat alignment");
     if (!aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_forward_items: workspace must be 256-byte aligned");
-    const FwdItemsWs L = fwd_items_layout(cams, items, n_items, *cfg, R, S, capacity);
+    const FwdItemsWs L = fwd_items_layout(R, S, capacity);
     if (ws_bytes < L.total)
         return fail(XPR_ERR_INVALID, "xpr_forward_items: workspace %zu < %zu bytes", ws_bytes, L.total);
     char *w = reinterpret_cast<char *>(workspace);
     float *rec = reinterpret_cast<float *>(w + L.rec);
     int32_t *bbox = reinterpret_cast<int32_t *>(w + L.bbox);
     int32_t *tc = reinterpret_cast<int32_t *>(w + L.tc);
+    int32_t *isect = reinterpret_cast<int32_t *>(w + L.isect);
     int32_t *order = reinterpret_cast<int32_t *>(w + L.order);
+    int32_t *offsets = reinterpret_cast<int32_t *>(w + L.offsets);
+    uint32_t *tiles = reinterpret_cast<uint32_t *>(w + L.tiles);
+    uint32_t *vals_in = reinterpret_cast<uint32_t *>(w + L.vals_in);
     uint32_t *vals = reinterpret_cast<uint32_t *>(w + L.vals);
     int32_t *ranges = reinterpret_cast<int32_t *>(w + L.ranges);
     int32_t *wl = reinterpret_cast<int32_t *>(w + L.worklist);
     int32_t *counter = reinterpret_cast<int32_t *>(w + L.counter);
     cudaStream_t st = as_stream(stream);
     *n_isect = 0;
+    int64_t total = 0;
     if (R > 0) {
-        if ((s = launch_project_items(*prims, cams, items, n_items, *cfg, rec, bbox, tc, st))) return s;
+        // projection with the exact kept-tile counts, depth order per item, offsets in that order
+        if ((s = launch_project_items(*prims, cams, items, n_items, *cfg, rec, bbox, tc, st, isect))) return s;
         if ((s = launch_depth_order_items(rec, tc, items, n_items, order, w + L.depth,
                                           depth_order_workspace_bytes(R), st)))
             return s;
+        if ((s = launch_exclusive_scan(isect, offsets, R, w + L.scan, nullptr, st, order))) return s;
+        XPR_CUDA_TRY(cudaMemcpyAsync(&total, scan_total_ptr(w + L.scan, R), sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                     st));
+        XPR_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    if ((s = launch_binsort_items(rec, bbox, tc, order, cams, items, n_items, *cfg, ranges, vals, capacity, n_isect,
-                                  w + L.binsort, binsort_items_workspace_bytes(cams, items, n_items, *cfg), st)))
+    *n_isect = total;
+    if (total > 0x7fffffffLL)
+        return fail(XPR_ERR_CAPACITY, "xpr_forward_items: %lld intersections exceed 2^31-1", (long long)total);
+    if (total > capacity)
+        return fail(XPR_ERR_CAPACITY, "xpr_forward_items: %lld intersections > capacity %lld", (long long)total,
+                    (long long)capacity);
+    // pairs in depth order with global tile ids, then a stable sort by tile (the key path)
+    if (total > 0 &&
+        (s = launch_bin_emit_items(rec, bbox, tc, order, cams, items, n_items, *cfg, offsets, tiles, vals_in, st)))
         return s;
+    if ((s = launch_sort_tiles(tiles, vals_in, total, (int32_t)S, nullptr, vals, ranges, w + L.sort,
+                               sort_tiles_workspace_bytes(std::max<int64_t>(capacity, 1), (int32_t)S), st)))
+        return s;
+    if (n_items == 1)  // one item: one block per tile (nothing to balance across items)
+        return launch_render_fwd_items(rec, R, vals, ranges, t, *cfg, image, t_final, n_contrib, nullptr, nullptr,
+                                       st);
     if ((s = launch_tile_worklist(ranges, (int32_t)S, wl, w + L.wl_ws, worklist_workspace_bytes((int32_t)S), st)))
         return s;
     return launch_render_fwd_items(rec, R, vals, ranges, t, *cfg, image, t_final, n_contrib, wl, counter, st);

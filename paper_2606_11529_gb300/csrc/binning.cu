@@ -61,10 +61,21 @@ __device__ __forceinline__ void put_pair(uint64_t *keys, uint32_t *tiles, uint32
 // keys (u64 tile << 32 | depth bits) and tiles (u32 tile id) are each written when non-NULL.
 // Records of a multi-view launch are view-major (record i belongs to view i div per_view) and the
 // tile id of a pair is offset by view * tiles_per_view (per_view = 0: a single view).
+// ITEMS: records of a multi-scene launch; record i belongs to the item k whose block
+// [rec0[k], rec0[k + 1]) holds it, is binned on item k's tile grid and its tile ids are offset by
+// tile0[k] (each lane's grid travels with its rows through the shuffles).
+struct BinItems {
+    int count;
+    int64_t rec0[kMaxItems + 1];
+    int64_t tile0[kMaxItems];
+    int W[kMaxItems], H[kMaxItems], Wt[kMaxItems], Ht[kMaxItems];
+};
+
+template <bool ITEMS>
 __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
                                                        const int *__restrict__ tcount,
                                                        const int *__restrict__ order, int64_t n, Grid g,
-                                                       int64_t per_view, int tiles_per_view,
+                                                       int64_t per_view, int tiles_per_view, BinItems bi,
                                                        const int32_t *__restrict__ offsets,
                                                        uint64_t *__restrict__ keys, uint32_t *__restrict__ tiles,
                                                        uint32_t *__restrict__ vals) {
@@ -83,14 +94,26 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
     CullData d = {};
     uint32_t depth_bits = 0, tbase = 0;
     int cursor = 0;  // next output slot of this lane's position
+    Grid gl = g;     // this lane's tile grid (its item's, for ITEMS)
     if (j < n) {
         i = order ? order[j] : (int)j;
         cursor = offsets[j];
-        area = box_of(bbox, tcount, i, g, bb);
+        int k = 0;
+        if (ITEMS) {
+            while (k + 1 < bi.count && (int64_t)i >= bi.rec0[k + 1]) ++k;
+            gl.W = bi.W[k];
+            gl.H = bi.H[k];
+            gl.Wt = bi.Wt[k];
+            gl.Ht = bi.Ht[k];
+        }
+        area = box_of(bbox, tcount, i, gl, bb);
         if (area > 0) {
             d = load_cull(rec, i);
             depth_bits = __float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]);
-            tbase = per_view ? (uint32_t)(i / per_view) * (uint32_t)tiles_per_view : 0u;
+            if (ITEMS)
+                tbase = (uint32_t)bi.tile0[k];
+            else
+                tbase = per_view ? (uint32_t)(i / per_view) * (uint32_t)tiles_per_view : 0u;
         }
     }
     const int h = area > 0 ? bb.w - bb.y : 0;
@@ -104,8 +127,14 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
         const int excl_p = __shfl_sync(kFullMask, excl, p);
         const int ty = __shfl_sync(kFullMask, bb.y, p) + f - excl_p;
         const int x0 = __shfl_sync(kFullMask, bb.x, p), x1 = __shfl_sync(kFullMask, bb.z, p);
+        Grid ge = g;
+        if (ITEMS) {
+            ge.W = __shfl_sync(kFullMask, gl.W, p);
+            ge.H = __shfl_sync(kFullMask, gl.H, p);
+            ge.Wt = __shfl_sync(kFullMask, gl.Wt, p);
+        }
         int ka = 0, kb = -1;
-        const int c = f < rows ? row_span_in_box(e, g, ty, x0, x1, ka, kb) : 0;
+        const int c = f < rows ? row_span_in_box(e, ge, ty, x0, x1, ka, kb) : 0;
         const int ci = warp_incl_scan(c);
         const int cx = ci - c;
         // output slot of this row's first pair: the position's cursor plus its earlier rows here
@@ -120,7 +149,7 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
         const unsigned nonempty = __ballot_sync(kFullMask, c > 0);
         if (c > 0) {
             const int slot = __popc(nonempty & lt_mask);
-            s_row[slot] = make_int4((int)(tb_p + (uint32_t)(ty * g.Wt + ka)), out_row, i_p, cx);
+            s_row[slot] = make_int4((int)(tb_p + (uint32_t)(ty * ge.Wt + ka)), out_row, i_p, cx);
             s_db[slot] = db_p;
         }
         __syncwarp();
@@ -321,10 +350,41 @@ int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, co
     if (n == 0) return XPR_OK;
     const int tpb = 256;
     const int64_t warps = (n + 31) / 32;
-    bin_emit_kernel<<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, st>>>(
+    BinItems bi;
+    memset(&bi, 0, sizeof(bi));
+    bin_emit_kernel<false><<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, st>>>(
         rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg), per_view,
-        tiles_x(cam, cfg) * tiles_y(cam, cfg), offsets, keys, tiles, vals);
+        tiles_x(cam, cfg) * tiles_y(cam, cfg), bi, offsets, keys, tiles, vals);
     XPR_LAUNCH_CHECK("bin_emit_kernel");
+    return XPR_OK;
+}
+
+// Multi-scene items: every position of order[R] binned on its record's item grid; tile ids global.
+int launch_bin_emit_items(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order,
+                          const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg,
+                          const int32_t *offsets, uint32_t *tiles, uint32_t *vals, cudaStream_t st) {
+    BinItems bi;
+    memset(&bi, 0, sizeof(bi));
+    bi.count = n_items;
+    int64_t tile = 0;
+    for (int k = 0; k < n_items; ++k) {
+        bi.rec0[k] = items[k].rec_offset;
+        bi.tile0[k] = tile;
+        bi.W[k] = cams[k].width;
+        bi.H[k] = cams[k].height;
+        bi.Wt[k] = tiles_x(cams[k], cfg);
+        bi.Ht[k] = tiles_y(cams[k], cfg);
+        tile += (int64_t)bi.Wt[k] * bi.Ht[k];
+    }
+    const int64_t R = items[n_items - 1].rec_offset + (items[n_items - 1].n + 31) / 32 * 32;
+    bi.rec0[n_items] = R;
+    if (R == 0) return XPR_OK;
+    const int tpb = 256;
+    const int64_t warps = (R + 31) / 32;
+    bin_emit_kernel<true><<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, st>>>(
+        rec, reinterpret_cast<const int4 *>(bbox), tc, order, R, make_grid(cams[0], cfg), 0, 0, bi, offsets, nullptr,
+        tiles, vals);
+    XPR_LAUNCH_CHECK("bin_emit_kernel<items>");
     return XPR_OK;
 }
 

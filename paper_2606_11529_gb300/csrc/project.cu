@@ -396,7 +396,7 @@ template <int DEG>
 __global__ void __launch_bounds__(kProjWarps * 32) project_items_kernel(
     const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
     const float *__restrict__ opac, const float *__restrict__ sh, ItemSet is, XprConfig cfg,
-    float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount) {
+    float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount, int *__restrict__ isect_count) {
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_fwd[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -406,28 +406,25 @@ __global__ void __launch_bounds__(kProjWarps * 32) project_items_kernel(
     const int64_t local = base - is.rec0[k];
     const int nv = (int)max((int64_t)0, min((int64_t)32, is.n[k] - local));
     const int64_t r = base + lane;
-    if (nv == 0) {  // padding records of the item's block: invisible
-        float4 *o4 = reinterpret_cast<float4 *>(rec + (size_t)r * XPR_REC_FLOATS);
-        o4[0] = o4[1] = o4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
-        bbox[r] = make_int4(0, 0, 0, 0);
-        tcount[r] = 0;
-        return;
-    }
     const int64_t p0 = is.prim0[k] + local;
     float *ssh = s_fwd + (size_t)w * 32 * LD;
-    stage_sh<DEG>(sh, p0, nv, ssh);
-    if (lane >= nv) {
+    if (nv > 0) stage_sh<DEG>(sh, p0, nv, ssh);
+    CullData cd = {};
+    int4 bb = make_int4(0, 0, 0, 0);
+    int area = 0;
+    if (lane < nv) {
+        const Params P = load_params(mu, scale, quat, opac, p0 + lane);
+        project_view<DEG>(P, ssh + lane * LD, r, is.cam[k], cfg, rec, bbox, tcount, cd, bb, area);
+    } else {  // padding records of the item's block: invisible
         float4 *o4 = reinterpret_cast<float4 *>(rec + (size_t)r * XPR_REC_FLOATS);
         o4[0] = o4[1] = o4[2] = make_float4(0.f, 0.f, 0.f, 0.f);
         bbox[r] = make_int4(0, 0, 0, 0);
         tcount[r] = 0;
-        return;
     }
-    const Params P = load_params(mu, scale, quat, opac, p0 + lane);
-    CullData cd;
-    int4 bb;
-    int area;
-    project_view<DEG>(P, ssh + lane * LD, r, is.cam[k], cfg, rec, bbox, tcount, cd, bb, area);
+    if (isect_count) {  // exact kept (primitive, tile) pairs with the binning's cull (warp-wide)
+        const int cnt = count_kept_tiles(cd, bb, area, make_grid(is.cam[k], cfg));
+        isect_count[r] = cnt;
+    }
 }
 
 // Adjoint of the items' projection: each record's gradient is added (atomically: several items
@@ -499,7 +496,8 @@ ItemSet make_itemset(const XprCamera *cams, const XprItem *items, int n_items) {
 }  // namespace
 
 int launch_project_items(const XprPrims &p, const XprCamera *cams, const XprItem *items, int n_items,
-                         const XprConfig &cfg, float *rec, int32_t *bbox, int32_t *tc, cudaStream_t st) {
+                         const XprConfig &cfg, float *rec, int32_t *bbox, int32_t *tc, cudaStream_t st,
+                         int32_t *isect_count) {
     const ItemSet is = make_itemset(cams, items, n_items);
     const int64_t R = is.rec0[n_items];
     if (R == 0) return XPR_OK;
@@ -508,7 +506,7 @@ int launch_project_items(const XprPrims &p, const XprCamera *cams, const XprItem
     XPR_DEG_DISPATCH(DEG, project_items_kernel<DEG><<<blocks, tpb,
                                                        (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
                               p.mu, p.scale, p.quat, p.opacity, p.sh, is, cfg, rec, reinterpret_cast<int4 *>(bbox),
-                              tc));
+                              tc, isect_count));
     XPR_LAUNCH_CHECK("project_items_kernel");
     return XPR_OK;
 }

@@ -29,11 +29,26 @@ namespace xpr {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-// Pixels per thread: (x, y + q h/PX), q = 0..PX-1, with PX = min(4, tile pixels / 32) so that a
-// tile's block is always whole warps (warp-wide shuffles and votes need all 32 lanes).
+// Pixels per thread: (x, y + q h/PX), q = 0..PX-1, with PX = min(cap, tile pixels / 32) so that a
+// tile's block is always whole warps (warp-wide shuffles and votes need all 32 lanes).  The caps
+// of the forward and the adjoint are compile-time constants.
+#ifndef XPR_FWD_PX
+#define XPR_FWD_PX 4
+#endif
+#ifndef XPR_BWD_PX
+#define XPR_BWD_PX 4
+#endif
+template <int TW, int TH, int CAP>
+__host__ __device__ constexpr int px_cap() {
+    return (TW * TH) / 32 >= CAP ? CAP : (TW * TH) / 32;
+}
 template <int TW, int TH>
-__host__ __device__ constexpr int px_per_thread() {
-    return (TW * TH) / 32 >= 4 ? 4 : (TW * TH) / 32;
+__host__ __device__ constexpr int fwd_px() {
+    return px_cap<TW, TH, XPR_FWD_PX>();
+}
+template <int TW, int TH>
+__host__ __device__ constexpr int bwd_px() {
+    return px_cap<TW, TH, XPR_BWD_PX>();
 }
 constexpr int kMaxBatch = 256;  // largest shared-memory batch (entries)
 // The adjoint stages at most kBwdBatch entries: its 9 accumulator rows make a block's shared
@@ -125,7 +140,7 @@ __device__ __forceinline__ void fwd_tile(int gt, const float *__restrict__ rec, 
                                          const int2 *__restrict__ ranges, const Consts &k, float *__restrict__ image,
                                          float *__restrict__ tfin, int *__restrict__ ncon, float4 *s_g, float4 *s_c,
                                          float *s_b) {
-    constexpr int kPX = px_per_thread<TW, TH>();
+    constexpr int kPX = fwd_px<TW, TH>();
     constexpr int NT = TW * TH / kPX;
     constexpr int RS = TH / kPX;  // rows between a thread's pixels
     static_assert(NT % 32 == 0, "a tile's block must be whole warps");
@@ -181,7 +196,7 @@ __device__ __forceinline__ void fwd_tile(int gt, const float *__restrict__ rec, 
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / px_per_thread<TW, TH>()) render_fwd_kernel(const float *__restrict__ rec,
+__global__ void __launch_bounds__(TW *TH / fwd_px<TW, TH>()) render_fwd_kernel(const float *__restrict__ rec,
                                                                   const uint32_t *__restrict__ vals,
                                                                   const int2 *__restrict__ ranges, Consts k,
                                                                   float *__restrict__ image,
@@ -298,7 +313,7 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
                                          const float *__restrict__ dimg, float *__restrict__ d_rec, float4 *s_g,
                                          float4 *s_c, float *s_b, uint32_t *s_id, float (*s_acc)[kBwdBatch + 1],
                                          int *s_wmax) {
-    constexpr int kPX = px_per_thread<TW, TH>();
+    constexpr int kPX = bwd_px<TW, TH>();
     constexpr int NT = TW * TH / kPX;
     constexpr int NW = NT / 32;
     constexpr int RS = TH / kPX;
@@ -382,7 +397,7 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / px_per_thread<TW, TH>()) render_bwd_kernel(const float *__restrict__ rec,
+__global__ void __launch_bounds__(TW *TH / bwd_px<TW, TH>()) render_bwd_kernel(const float *__restrict__ rec,
                                                                   const uint32_t *__restrict__ vals,
                                                                   const int2 *__restrict__ ranges, Consts k,
                                                                   const float *__restrict__ tfin,
@@ -461,7 +476,7 @@ int launch_render_fwd_views(const float *rec, int64_t n, const uint32_t *vals, c
     Work w = {worklist, counter, items};
     if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
     XPR_TILE_DISPATCH(TW, TH, {
-        const int threads = TW * TH / px_per_thread<TW, TH>();
+        const int threads = TW * TH / fwd_px<TW, TH>();
         const int grid = worklist ? persistent_grid(render_fwd_kernel<TW, TH>, threads, items) : items;
         render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, image, t_final, n_contrib, w);
     });
@@ -482,7 +497,7 @@ int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_
     Work w = {worklist, counter, items};
     if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
     XPR_TILE_DISPATCH(TW, TH, {
-        const int threads = TW * TH / px_per_thread<TW, TH>();
+        const int threads = TW * TH / bwd_px<TW, TH>();
         const int grid = worklist ? persistent_grid(render_bwd_kernel<TW, TH>, threads, items) : items;
         render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, t_final, n_contrib, d_image, d_rec, w);
     });
@@ -507,7 +522,7 @@ int launch_render_fwd_items(const float *rec, int64_t n_rec, const uint32_t *val
     Work w = {worklist, counter, (int)items};
     if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
     XPR_TILE_DISPATCH(TW, TH, {
-        const int threads = TW * TH / px_per_thread<TW, TH>();
+        const int threads = TW * TH / fwd_px<TW, TH>();
         const int grid = worklist ? persistent_grid(render_fwd_kernel<TW, TH>, threads, (int)items) : (int)items;
         render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, image, t_final, n_contrib, w);
     });
@@ -533,7 +548,7 @@ int launch_render_bwd_items(const float *rec, int64_t n_rec, const uint32_t *val
     Work w = {worklist, counter, (int)items};
     if (worklist) XPR_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
     XPR_TILE_DISPATCH(TW, TH, {
-        const int threads = TW * TH / px_per_thread<TW, TH>();
+        const int threads = TW * TH / bwd_px<TW, TH>();
         const int grid = worklist ? persistent_grid(render_bwd_kernel<TW, TH>, threads, (int)items) : (int)items;
         render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, t_final, n_contrib, d_image, d_rec, w);
     });

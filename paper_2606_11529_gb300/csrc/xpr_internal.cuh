@@ -85,7 +85,11 @@ int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_
                             const int32_t *n_contrib, const float *d_image, float *d_rec, int64_t n,
                             const int32_t *worklist, int32_t *counter, cudaStream_t st);
 int launch_project_items(const XprPrims &p, const XprCamera *cams, const XprItem *items, int n_items,
-                         const XprConfig &cfg, float *rec, int32_t *bbox, int32_t *tc, cudaStream_t st);
+                         const XprConfig &cfg, float *rec, int32_t *bbox, int32_t *tc, cudaStream_t st,
+                         int32_t *isect_count = nullptr);
+int launch_bin_emit_items(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order,
+                          const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg,
+                          const int32_t *offsets, uint32_t *tiles, uint32_t *vals, cudaStream_t st);
 int launch_project_bwd_items(const XprPrims &p, int64_t n_prims, const XprCamera *cams, const XprItem *items,
                              int n_items, const XprConfig &cfg, const float *d_rec, const XprPrimsGrad &g,
                              cudaStream_t st);
