@@ -524,7 +524,7 @@ def serve_leg(dev, n_requests, warmup, cap_gb, scale_down):
     return {"workload": f"16 resident clustered SH-3 scenes ({sum(scene_prims)} Gaussians, "
                         f"{min(scene_prims)}-{max(scene_prims)} per scene), Poisson 200 req/s, "
                         "512x512 / 1280x720 / 1920x1080 (f = width), forward only, image delivered to pinned host",
-            "requests": n_requests, "warmup_requests": warmup, "slots": 2,
+            "requests": n_requests, "warmup_requests": warmup, "slots": 2, "batch_cost_cap": 2.0,
             "p50_ms": ours["p50_ms"], "p99_ms": ours["p99_ms"], "views_per_s": ours["views_per_s"],
             "server": ours, "plain_queue": plain, "capped_pool": cst, "rate_400": hi,
             "resident_gb": round(sum(sum(t.numel() * 4 for t in s) for s in resident) / 2 ** 30, 3),

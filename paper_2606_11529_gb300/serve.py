@@ -12,8 +12,10 @@ module is the request loop around the same forward stages:
   request larger than the whole pool is rejected;
 * one host thread runs the loop: it takes arrivals as they come, and whenever
   one of ``slots`` CUDA streams is free and requests are admitted, it takes the
-  oldest admitted requests, whatever their scene and image size (up to 16), and
-  launches them as one multi-scene batch (one launch per stage for all of them,
+  oldest admitted request and the admitted requests after it, whatever their
+  scene and image size (up to 16, while the batch's summed footprint stays
+  within ``batch_cost_cap`` times the oldest one's, so that a small request is
+  not held back by a large one), and launches them as one multi-scene batch (one launch per stage for all of them,
   the tiles of every request in one persistent work list), then copies the
   images to pinned host memory and records an event; so several batches are in
   flight at once, on different streams, and a request arriving while the GPU is
@@ -125,9 +127,13 @@ class Scheduler:
     """FIFO admission by footprint and batch formation.  Not thread-safe by itself: the server
     calls it under one lock."""
 
-    def __init__(self, budget: HBMBudget, max_views: int = MAX_VIEWS):
+    def __init__(self, budget: HBMBudget, max_views: int = MAX_VIEWS, batch_cost_cap: float | None = None):
         self.budget = budget
         self.max_views = max_views
+        # None: a batch takes the oldest admitted requests up to max_views; a number c: requests
+        # join the oldest one only while the batch's summed footprint (the cost proxy) stays within
+        # c times the oldest request's, so that small requests are not held back by large ones
+        self.batch_cost_cap = batch_cost_cap
         self.pending = collections.deque()  # arrived, not yet admitted (FIFO)
         self.admitted = collections.deque()  # admitted, not yet taken by a worker (FIFO)
         self.in_flight = 0
@@ -152,8 +158,13 @@ class Scheduler:
         """The oldest admitted requests, any scene and size, up to max_views of them."""
         if not self.admitted:
             return []
-        batch = []
+        batch = [self.admitted.popleft()]
+        cap = None if self.batch_cost_cap is None else self.batch_cost_cap * max(batch[0].nbytes, 1)
+        cost = batch[0].nbytes
         while self.admitted and len(batch) < self.max_views:
+            if cap is not None and cost + self.admitted[0].nbytes > cap:
+                break
+            cost += self.admitted[0].nbytes
             batch.append(self.admitted.popleft())
         for r in batch:
             r.status, r.start, r.batch_views = "running", now, len(batch)
@@ -240,7 +251,8 @@ class Server:
     (the resident scenes are outside it).  ``slots``: batches in flight, one CUDA stream each."""
 
     def __init__(self, scenes, cfg, pool_bytes: int, slots: int = 2, capacity_factor: float = 1.3,
-                 max_views: int = MAX_VIEWS, deliver_host: bool = True, keep_images: bool = True):
+                 max_views: int = MAX_VIEWS, deliver_host: bool = True, keep_images: bool = True,
+                 batch_cost_cap: float | None = 2.0):
         if scenes is not None and not hasattr(scenes, "views") and len(scenes) and scenes[0] is not None:
             from . import batched as BT
             scenes = BT.SceneSet(scenes)
@@ -254,7 +266,7 @@ class Server:
         # results), so the pinned host buffers are recycled instead of pinning new memory per request
         self.keep_images = keep_images
         self.budget = HBMBudget(pool_bytes)
-        self.sched = Scheduler(self.budget, max_views)
+        self.sched = Scheduler(self.budget, max_views, batch_cost_cap)
         self.calib = {}
         self.errors = []
         self._ws = {}

@@ -154,3 +154,15 @@ def test_undelivered_request_is_an_error():
     srv = Undelivering(pool=2 * 1920 * 1080, slots=2)
     srv.run(trace)
     assert all(r.status == "error" for r in trace)
+
+
+def test_cost_capped_batches_keep_small_requests_apart_from_large():
+    s = SV.Scheduler(SV.HBMBudget(10 ** 9), max_views=8, batch_cost_cap=2.0)
+    for i, nb in enumerate([10, 5, 5, 100, 4, 4]):
+        s.arrive(_req(i, nbytes=nb), 0.0)
+    assert [r.rid for r in s.take_batch(0.0)] == [0, 1, 2]     # 10 + 5 + 5 <= 2 x 10
+    assert [r.rid for r in s.take_batch(0.0)] == [3, 4, 5]     # a large head takes the small ones along
+    s = SV.Scheduler(SV.HBMBudget(10 ** 9), max_views=8, batch_cost_cap=1.0)
+    for i, nb in enumerate([10, 5, 5]):
+        s.arrive(_req(i, nbytes=nb), 0.0)
+    assert [r.rid for r in s.take_batch(0.0)] == [0]           # cap 1: one request per batch
