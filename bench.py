@@ -259,7 +259,8 @@ def batched_leg(dev, reps, flush, method=0):
     base = scenes.RenderConfig(sh_degree=0, method=method)
     P = [t.to(dev) for t in R.scene_to_device(sc)]
     w = torch.from_numpy(np.random.default_rng(2).normal(size=(8, 3, 1064, 1600)).astype(np.float32)).to(dev)
-    best, table = BT.autotune(P, cams, base, scene_id=f"uniform-3M-m{method}", reps=5)
+    chunks = {}
+    best, table = BT.autotune(P, cams, base, scene_id=f"uniform-3M-m{method}", reps=5, chunks=chunks)
     Pg = [p.detach().requires_grad_(True) for p in P]
     ws = BT.ViewsWorkspace()
 
@@ -282,15 +283,19 @@ def batched_leg(dev, reps, flush, method=0):
     torch.cuda.synchronize()
     tb = _median_ms(batched, reps, flush)
     tp = _median_ms(plain, reps, flush)
-    fr = BT.forward_views(*P, cams, best, BT.ViewsWorkspace())
+    # pairs of the chosen setting, summed over the view chunks it runs in
+    n_isect = sum(BT.forward_views(*P, part, best, BT.ViewsWorkspace()).n_isect
+                  for part in BT.view_chunks(cams, ws.chunks))
     what = "3DGUT (unscented projection, ray evaluation)" if method == 1 else "3DGS"
     lens = ("fisheye (k = 0.05, -0.01, 0.001, 0)" if method == 1 else "pinhole")
     return {"workload": f"{what}: 3M uniform SH-0 Gaussians (xy U[-1,1], z U[2,6]), 8 {lens} views 1600x1064 "
                         "f=800, yaw -15..+15 deg, fwd+bwd of all 8 views, seed 0",
             "ms_batched": round(tb, 3), "ms_plain_8x": round(tp, 3), "speedup": round(tp / tb, 3),
-            "intersections": fr.n_isect, "tile": [best.tile_w, best.tile_h], "batch_depth": best.batch_depth,
+            "intersections": n_isect, "tile": [best.tile_w, best.tile_h], "batch_depth": best.batch_depth,
+            "view_chunks": ws.chunks,
             "autotune_ms": {f"{k[0]}x{k[1]}/b{k[2]}": (round(v, 3) if v != float("inf") else None)
                             for k, v in table.items()},
+            "autotune_view_chunks": {f"{k[0]}x{k[1]}/b{k[2]}": c for k, c in chunks.items()},
             "timing": f"median of {reps} (L2 flushed before each)"}
 
 

@@ -51,6 +51,9 @@ class ViewsWorkspace:
     def __init__(self):
         self.last_isect = 0
         self.bufs = {}
+        # consecutive view chunks a batch of these views is split into (grown when one batch would
+        # hold more than 2^31 - 1 pairs, the limit of the 32-bit pair index)
+        self.chunks = 1
 
     def scratch(self, name, nbytes, device):
         t = self.bufs.get(name)
@@ -135,9 +138,39 @@ class MultiViewSplat(torch.autograd.Function):
         return (*grads, None, None, None, None)
 
 
+def view_chunks(cams, k):
+    """``cams`` split into ``k`` consecutive chunks of near-equal size (none empty)."""
+    cams = list(cams)
+    k = max(1, min(int(k), len(cams)))
+    q, m = divmod(len(cams), k)
+    out, o = [], 0
+    for i in range(k):
+        c = q + (1 if i < m else 0)
+        out.append(cams[o:o + c])
+        o += c
+    return out
+
+
 def render_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | None = None, persistent=True):
-    """Differentiable render of V views in one launch per stage: returns images [V, 3, H, W]."""
-    return MultiViewSplat.apply(mu, scale, quat, opacity, sh, list(cams), cfg, ws or ViewsWorkspace(), persistent)
+    """Differentiable render of V views in one launch per stage: returns images [V, 3, H, W].
+
+    When one batch of the V views would hold more than 2^31 - 1 (tile, primitive) pairs (the pair
+    index is 32-bit), the views run as consecutive chunks, each one batch (the chunk count is
+    doubled until every chunk fits and kept in ``ws`` for the next call); a single view above the
+    limit raises."""
+    ws = ws or ViewsWorkspace()
+    cams = list(cams)
+    while True:
+        parts = view_chunks(cams, ws.chunks)
+        try:
+            imgs = [MultiViewSplat.apply(mu, scale, quat, opacity, sh, part, cfg, ws, persistent) for part in parts]
+        except B.XprError as e:
+            if e.status != B.XPR_ERR_CAPACITY or len(parts) >= len(cams):
+                raise
+            ws.chunks = min(2 * len(parts), len(cams))
+            ws.last_isect = 0
+            continue
+        return imgs[0] if len(imgs) == 1 else torch.cat(imgs)
 
 
 # ------------------------------------------------------------------------------------------- autotuner
@@ -158,15 +191,19 @@ def _time_ms(fn, reps):
 
 
 def autotune(params, cams, cfg, scene_id="scene", backward=True, reps=5, tiles=TILE_CANDIDATES,
-             batches=BATCH_CANDIDATES):
+             batches=BATCH_CANDIDATES, chunks=None):
     """Returns (best_cfg, table) where table maps (tile_w, tile_h, batch) -> median ms of one batched
-    forward (+ backward) over all `cams` (inf where the batch has more than 2^31 - 1 pairs).
-    Results are cached per (device, scene_id, resolution)."""
+    forward (+ backward) over all `cams` (a candidate whose batch exceeds 2^31 - 1 pairs runs the
+    views in chunks, as `render_views` does; inf only where a single view exceeds it).  ``chunks``
+    (a dict, optional) receives the chunk count each candidate ran with.  Results are cached per
+    (device, scene_id, resolution)."""
     key = (torch.cuda.get_device_name(), scene_id, cams[0].width, cams[0].height, len(cams), backward,
            int(getattr(cfg, "method", 0)))
     if key in _CACHE:
-        return _CACHE[key]
-    table = {}
+        if chunks is not None:
+            chunks.update(_CACHE[key][2])
+        return _CACHE[key][:2]
+    table, nchunks = {}, {}
     d_img = None
     for tw, th in tiles:
         for bd in batches:
@@ -184,13 +221,16 @@ def autotune(params, cams, cfg, scene_id="scene", backward=True, reps=5, tiles=T
             except B.XprError as e:
                 if e.status != B.XPR_ERR_CAPACITY:
                     raise
-                table[(tw, th, bd)] = math.inf  # more than 2^31 - 1 pairs: this tile size does not fit
+                table[(tw, th, bd)] = math.inf  # a single view above 2^31 - 1 pairs: this tile size does not fit
                 continue
             table[(tw, th, bd)] = _time_ms(run, reps)
+            nchunks[(tw, th, bd)] = ws.chunks
     best = min(table, key=table.get)
-    out = (dataclasses.replace(cfg, tile_w=best[0], tile_h=best[1], batch_depth=best[2]), table)
+    out = (dataclasses.replace(cfg, tile_w=best[0], tile_h=best[1], batch_depth=best[2]), table, nchunks)
     _CACHE[key] = out
-    return out
+    if chunks is not None:
+        chunks.update(nchunks)
+    return out[:2]
 
 
 # ------------------------------------------------------------------------------------------- scenes

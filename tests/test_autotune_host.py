@@ -70,3 +70,45 @@ def test_other_errors_propagate(monkeypatch):
     params, cams, cfg = _inputs()
     with pytest.raises(B.XprError):
         batched.autotune(params, cams, cfg, scene_id="s")
+
+
+def test_view_chunks_partition():
+    cams = list(range(8))
+    assert batched.view_chunks(cams, 1) == [cams]
+    assert batched.view_chunks(cams, 3) == [[0, 1, 2], [3, 4, 5], [6, 7]]
+    assert batched.view_chunks(cams, 20) == [[c] for c in cams]
+    assert sum(batched.view_chunks(cams, 5), []) == cams
+
+
+def _fake_splat(monkeypatch, max_views, calls):
+    """MultiViewSplat stand-in: a batch of more than ``max_views`` views is over the pair limit."""
+
+    class Fake:
+        @staticmethod
+        def apply(mu, scale, quat, opacity, sh, part, cfg, ws, persistent):
+            calls.append(list(part))
+            if len(part) > max_views:
+                raise B.XprError(B.XPR_ERR_CAPACITY, "xpr_tile_bin_views", "more than 2^31 - 1 pairs")
+            return torch.stack([torch.full((3, 2, 2), float(c)) for c in part])
+
+    monkeypatch.setattr(batched, "MultiViewSplat", Fake)
+
+
+def test_render_views_splits_views_over_the_pair_limit(monkeypatch):
+    calls = []
+    _fake_splat(monkeypatch, 3, calls)
+    ws = batched.ViewsWorkspace()
+    params = [torch.zeros(1) for _ in range(5)]
+    img = batched.render_views(*params, list(range(8)), None, ws)
+    # 8 views fail, 2 x 4 fail on the first chunk, 4 x 2 fit; images in view order
+    assert ws.chunks == 4
+    assert img[:, 0, 0, 0].tolist() == [float(c) for c in range(8)]
+    n = len(calls)
+    batched.render_views(*params, list(range(8)), None, ws)
+    assert calls[n:] == [[0, 1], [2, 3], [4, 5], [6, 7]]  # the chunk count is kept
+
+
+def test_render_views_raises_when_one_view_is_over_the_limit(monkeypatch):
+    _fake_splat(monkeypatch, 0, [])
+    with pytest.raises(B.XprError):
+        batched.render_views(*[torch.zeros(1) for _ in range(5)], list(range(4)), None, batched.ViewsWorkspace())

@@ -47,6 +47,29 @@ def test_views_equal_single_view_path(persistent, tile, deg, method):
         assert rel_err(gm.cpu().numpy(), gs.cpu().numpy()) < 1e-5, name
 
 
+@pytest.mark.parametrize("method", [0, 1])
+def test_view_chunks_equal_one_batch(method):
+    # the chunked form (used when one batch would exceed 2^31 - 1 pairs) forced on a small case:
+    # images bit-identical to one batch, gradients equal up to the order of the per-view sums
+    sc = scenes.uniform_scene(6000, seed=9, sh_degree=1)
+    cams = _views(5)
+    cfg = scenes.RenderConfig(sh_degree=1, method=method)
+    out = []
+    for k in (1, 2, 5):
+        P = [t.requires_grad_(True) for t in R.scene_to_device(sc)]
+        ws = BT.ViewsWorkspace()
+        ws.chunks = k
+        imgs = BT.render_views(*P, cams, cfg, ws)
+        assert ws.chunks == k
+        w = torch.from_numpy(np.random.default_rng(3).normal(size=tuple(imgs.shape)).astype(np.float32)).cuda()
+        (imgs * w).sum().backward()
+        out.append((imgs.detach(), [p.grad.clone() for p in P]))
+    for imgs, grads in out[1:]:
+        assert torch.equal(imgs, out[0][0])
+        for name, g, g0 in zip(NAMES, grads, out[0][1]):
+            assert rel_err(g.cpu().numpy(), g0.cpu().numpy()) < 1e-5, name
+
+
 def test_one_view_against_oracle(oracle):
     sc = scenes.uniform_scene(6000, seed=4, sh_degree=3)
     cams = _views(2)
