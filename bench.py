@@ -36,11 +36,17 @@ WORKLOAD = "3DGS fwd+bwd, 1M SH-3 Gaussians clustered (200 centres, spread 0.5, 
 SH_FLOATS = 48
 PARAM_BYTES = 4 * (3 + 3 + 4 + 1 + SH_FLOATS)  # 236 B per primitive
 REC_BYTES = 48
-FWD_OPS_PER_PAIR = 16   # FP32-pipe operations per (pixel, entry) pair of the forward walk
-# FP32-pipe operations per (pixel, entry) pair of the adjoint walk, counted on a contributing
-# unclamped pair; the colour behind a pixel enters as one scalar (its dot with the loss weight), 6
-# operations fewer than carrying the 3-vector
+# FP32-pipe operations per (pixel, entry) pair of the method's compositing arithmetic written per
+# pair (power from the pixel offset, alpha, gates, blend; the adjoint counted on a contributing
+# unclamped pair with the colour behind a pixel as one scalar): the algorithmic work of the render
+# stages.
+FWD_OPS_PER_PAIR = 16
 BWD_OPS_PER_PAIR = 39
+# What the kernels execute per pair after factoring the power by pixel column (A dx^2 and B dx once
+# per entry and column) and, in the adjoint, applying the mean partials' conic factors once per
+# (tile, entry): forward 12 + 4 per column of 4 pixels, adjoint 28 + 4 per column of 8 pixels.
+FWD_EXEC_OPS_PER_PAIR = 13.0
+BWD_EXEC_OPS_PER_PAIR = 28.5
 # stages that are one kernel launch (the render adjoint's bracket also holds the zero-fill of d_rec)
 SINGLE_KERNEL = {"project": "project_fwd_kernel<3>", "render_fwd": "render_fwd_kernel<16,16>",
                  "render_bwd": "render_bwd_kernel<16,16>", "project_bwd": "project_bwd_kernel<3>"}
@@ -688,8 +694,8 @@ def main():
         # fused bin + sort: the bin's reads plus one write of the sorted lists (4 B per kept pair) and
         # the tile ranges
         "bin_sort": ("hbm", n * (REC_BYTES + 16 + 4 + 4) + I * 4 + T * 8, None),
-        "render_fwd": ("alu", pairs * FWD_OPS_PER_PAIR, None),
-        "render_bwd": ("alu", pairs * BWD_OPS_PER_PAIR, None),
+        "render_fwd": ("alu", pairs * FWD_OPS_PER_PAIR, {"ops_per_pair": FWD_EXEC_OPS_PER_PAIR}),
+        "render_bwd": ("alu", pairs * BWD_OPS_PER_PAIR, {"ops_per_pair": BWD_EXEC_OPS_PER_PAIR}),
         "project_bwd": ("hbm", n * (2 * PARAM_BYTES + REC_BYTES), None),
     }
     stages = {}
@@ -709,6 +715,10 @@ def main():
             ach = amount / (t * 1e-3)
             stages[name] = {"ms": round(t, 4), "bound": "alu", "achieved_tops": round(ach / 1e12, 3),
                             "frac": round(ach / pk["alu_ops"], 4)}
+            if impl:
+                ex = pairs * impl["ops_per_pair"] / (t * 1e-3)
+                stages[name]["executed"] = {"ops_per_pair": impl["ops_per_pair"], "tops": round(ex / 1e12, 3),
+                                            "frac": round(ex / pk["alu_ops"], 4)}
     # roofline of the dominant kernel: the largest stage that is a single kernel launch
     single = {k: v for k, v in stages.items() if k in SINGLE_KERNEL}
     dom = max(single, key=lambda k: single[k]["ms"])
@@ -723,6 +733,8 @@ def main():
         roof = {"kernel": kname, "bound": "alu", "achieved": d["achieved_tops"],
                 "peak": round(pk["alu_ops"] / 1e12, 2), "unit": "TOP/s", "frac": d["frac"], "traffic": traffic,
                 "peak_source": pk["alu_desc"], "sms": _ALU["sms"], "peak_sm_mhz": _ALU["mhz"]}
+        if "executed" in d:
+            roof["executed"] = d["executed"]
     roof["timing"] = "CUDA events around the C-ABI call on the launching stream, mean over the timed steps"
     roof["traffic_source"] = traffic_src or "null: no ncu capture of the kernel's current source"
 

@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(TW *TH / feat_px<TW, TH, NF>()) render_feat_fw
                 const float4 c = s_c[j];
                 const float cb = s_b[j];
                 const float dx = __fsub_rn(fx, g.x);
+                const ColTerms ct = column_terms(g.z, g.w, dx);
                 const int pos = base + j - rg.x;
                 all_done = true;
 #pragma unroll
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(TW *TH / feat_px<TW, TH, NF>()) render_feat_fw
                     FPixFwd<NF> &p = P[q];
                     if (!p.done) {
                         const float dy = __fsub_rn(p.fy, g.y);
-                        const float pw = eval_power2(g.z, g.w, c.x, dx, dy);
+                        const float pw = eval_power2(ct, c.x, dy);
                         if (pw <= 0.f) {
                             const float og = __fmul_rn(c.y, ex2_approx(pw));
                             const float al = fminf(k.amax, og);
@@ -199,11 +200,12 @@ struct FPixBwd {
 
 // partials into v[32]: v[0..8] as the colour-only adjoint (base-2 form), v[9 + c] dL/df_c
 template <int NF>
-__device__ __forceinline__ bool feat_adjoint(FPixBwd<NF> &P, float dx, const float4 &g, const float4 &c, float cb,
-                                             const float *f, int pos, const FeatConsts &k, float *v) {
+__device__ __forceinline__ bool feat_adjoint(FPixBwd<NF> &P, float dx, const ColTerms &ct, const float4 &g,
+                                             const float4 &c, float cb, const float *f, int pos, const FeatConsts &k,
+                                             float *v) {
     if (pos >= P.last) return false;
     const float dy = __fsub_rn(P.fy, g.y);
-    const float p = eval_power2(g.z, g.w, c.x, dx, dy);
+    const float p = eval_power2(ct, c.x, dy);
     if (p > 0.f) return false;
     const float G = ex2_approx(p);
     const float og = __fmul_rn(c.y, G);
@@ -312,9 +314,10 @@ __global__ void __launch_bounds__(TW *TH / feat_px<TW, TH, NF>()) render_feat_bw
 #pragma unroll
             for (int ch = 0; ch < NF; ++ch) f[ch] = s_f[j][ch];
             const float dx = __fsub_rn(fx, g.x);
+            const ColTerms ct = column_terms(g.z, g.w, dx);
             bool hit = false;
 #pragma unroll
-            for (int q = 0; q < PX; ++q) hit |= feat_adjoint<NF>(P[q], dx, g, c, cb, f, pos, k, vv);
+            for (int q = 0; q < PX; ++q) hit |= feat_adjoint<NF>(P[q], dx, ct, g, c, cb, f, pos, k, vv);
             if (__any_sync(kFullF, hit)) {
                 const float r = reduce_scatter32f(vv, lane);
                 if (lane < NV) atomicAdd(&s_acc[lane][j], r);

@@ -232,14 +232,54 @@ __global__ void __launch_bounds__(kProjWarps * 32) project_color_kernel(const fl
 //   R(q/|q|):               explicit partials of the rotation matrix
 //   colour:                 dL/dsh_k = Y_k g (where unclamped); dL/dd through the basis gradient,
 //                           projected on the tangent plane and divided by |mu - camera centre|
+// colour_adjoint with dL/dsh written instead of added; dsh may be the staged row shi itself (each
+// coefficient's gradient is written after that coefficient's last read).
 template <int DEG>
+__device__ __forceinline__ void colour_adjoint_set(const Params &P, const float *shi, float *dsh, const Cam &k,
+                                                   const float *drgb, float *gmu) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const float vx = P.m[0] - k.cpos[0], vy = P.m[1] - k.cpos[1], vz = P.m[2] - k.cpos[2];
+    const float vinv = rsqrtf(vx * vx + vy * vy + vz * vz);
+    const float ux = vx * vinv, uy = vy * vinv, uz = vz * vinv;
+    float wk[K];
+    {
+        float Y[K];
+        sh_basis<DEG>(ux, uy, uz, Y);
+        float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            raw[0] += shi[3 * kk] * Y[kk];
+            raw[1] += shi[3 * kk + 1] * Y[kk];
+            raw[2] += shi[3 * kk + 2] * Y[kk];
+        }
+        float gc[3];
+        for (int c = 0; c < 3; ++c) gc[c] = raw[c] > 0.f ? drgb[c] : 0.f;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            wk[kk] = gc[0] * shi[3 * kk] + gc[1] * shi[3 * kk + 1] + gc[2] * shi[3 * kk + 2];
+            dsh[3 * kk] = Y[kk] * gc[0];
+            dsh[3 * kk + 1] = Y[kk] * gc[1];
+            dsh[3 * kk + 2] = Y[kk] * gc[2];
+        }
+    }
+    const float3 gdir = sh_grad_dot<DEG>(ux, uy, uz, wk);
+    const float dd = gdir.x * ux + gdir.y * uy + gdir.z * uz;
+    gmu[0] += (gdir.x - ux * dd) * vinv;
+    gmu[1] += (gdir.y - uy * dd) * vinv;
+    gmu[2] += (gdir.z - uz * dd) * vinv;
+}
+
+template <int DEG, bool SET = false>
 __device__ __forceinline__ void adjoint_view(const Params &P, const float *shi, float *dsh, const Geo &G,
                                              const Cam &k, float4 d0, float4 d1, float4 d2, Acc<DEG> &A) {
     const float dmx = d0.x, dmy = d0.y, g00 = d0.z, g01 = d0.w, g11 = d1.x;
     const float drgb[3] = {d1.z, d1.w, d2.x};
     A.o += d1.y;
 
-    colour_adjoint<DEG>(P, shi, dsh, k, drgb, A.mu);
+    if (SET)
+        colour_adjoint_set<DEG>(P, shi, dsh, k, drgb, A.mu);
+    else
+        colour_adjoint<DEG>(P, shi, dsh, k, drgb, A.mu);
 
     // ---- mu_2D
     const float x = G.mc[0], y = G.mc[1], z = G.mc[2];
@@ -316,10 +356,13 @@ __device__ __forceinline__ void adjoint_view(const Params &P, const float *shi, 
 }
 
 // One thread per primitive; each warp stages its 32 primitives' SH coefficients in shared memory
-// with coalesced loads and accumulates their gradients there, then writes them out coalesced (a
-// thread's own rows are 3K floats apart in global memory).
+// with coalesced 16-byte loads (all of a lane's loads issued before its first store) and
+// accumulates their gradients there, then writes them out coalesced (a thread's own rows are 3K
+// floats apart in global memory).  With one view the gradient overwrites the thread's own staged
+// row after its last read, so a warp holds one row buffer (6.3 KB at degree 3) instead of two;
+// with at most 96 registers, 5 blocks (20 warps) fit an SM.
 template <int DEG>
-__global__ void __launch_bounds__(kBwdWarps * 32, 4) project_bwd_kernel(
+__global__ void __launch_bounds__(kBwdWarps * 32, 5) project_bwd_kernel(
     const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
     const float *__restrict__ d_rec, float *__restrict__ gmu, float *__restrict__ gscale, float *__restrict__ gquat,
@@ -331,31 +374,66 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) project_bwd_kernel(
     const int64_t base = ((int64_t)blockIdx.x * kBwdWarps + w) * 32;
     if (base >= n) return;
     const int nv = (int)min((int64_t)32, n - base);
-    float *ssh = s_bwd + (size_t)w * 2 * 32 * LD;
-    float *sdsh = ssh + 32 * LD;
+    const bool one = cs.n_views == 1;  // one row buffer: the gradient overwrites the staged row
+    float *ssh = s_bwd + (size_t)w * (one ? 1 : 2) * 32 * LD;
+    float *sdsh = one ? ssh : ssh + 32 * LD;
     const float *gs = sh + base * KC;
-    for (int e = lane; e < nv * KC; e += 32) {
-        const int pi = e / KC;
-        ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
-    }
-    for (int c = 0; c < KC; ++c) sdsh[lane * LD + c] = 0.f;
-    __syncwarp();
     const int64_t i = base + lane;
+    Params P = {};
+    if (i < n) P = load_params(mu, scale, quat, opac, i);
+    constexpr int F4 = 8 * KC;              // float4 of a full warp's rows (32 KC floats)
+    constexpr int PER = (F4 + 31) / 32;      // per lane
+    if (nv == 32 && ((reinterpret_cast<uintptr_t>(gs) & 15) == 0)) {
+        float4 r[PER];
+#pragma unroll
+        for (int it = 0; it < PER; ++it) {
+            const int u = lane + 32 * it;
+            if (u < F4) r[it] = __ldg(reinterpret_cast<const float4 *>(gs) + u);
+        }
+#pragma unroll
+        for (int it = 0; it < PER; ++it) {
+            const int u = lane + 32 * it;
+            if (u < F4) {
+                const float vals[4] = {r[it].x, r[it].y, r[it].z, r[it].w};
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int e = 4 * u + c4;
+                    const int pi = e / KC;
+                    ssh[pi * LD + (e - pi * KC)] = vals[c4];
+                }
+            }
+        }
+    } else {
+        for (int e = lane; e < nv * KC; e += 32) {
+            const int pi = e / KC;
+            ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
+        }
+    }
+    if (!one)
+        for (int c = 0; c < KC; ++c) sdsh[lane * LD + c] = 0.f;
+    __syncwarp();
     if (i < n) {
-        const Params P = load_params(mu, scale, quat, opac, i);
         Acc<DEG> A = {};
         float qinv = 0.f, qn[4] = {0.f, 0.f, 0.f, 0.f};
+        bool wrote = false;  // one view: the row holds the SH gradient instead of the coefficients
         for (int v = 0; v < cs.n_views; ++v) {
             const Cam k = make_cam(cs.cam[v], cfg);
             Geo G;
             geometry(P, k, cfg.cov_dilation, G);
             if (!footprint(G, P.o, k, cfg).vis) continue;  // invisible in this view: no gradient from it
             const float4 *D4 = reinterpret_cast<const float4 *>(d_rec + ((size_t)v * n + i) * XPR_REC_FLOATS);
-            adjoint_view<DEG>(P, ssh + lane * LD, sdsh + lane * LD, G, k, __ldg(D4), __ldg(D4 + 1), __ldg(D4 + 2),
-                              A);
+            if (one)
+                adjoint_view<DEG, true>(P, ssh + lane * LD, sdsh + lane * LD, G, k, __ldg(D4), __ldg(D4 + 1),
+                                        __ldg(D4 + 2), A);
+            else
+                adjoint_view<DEG>(P, ssh + lane * LD, sdsh + lane * LD, G, k, __ldg(D4), __ldg(D4 + 1), __ldg(D4 + 2),
+                                  A);
+            wrote = true;
             qinv = G.qinv;
             for (int j = 0; j < 4; ++j) qn[j] = G.qn[j];
         }
+        if (one && !wrote)  // invisible: the staged coefficients become a zero gradient
+            for (int c = 0; c < KC; ++c) sdsh[lane * LD + c] = 0.f;
         // qn = q / |q|:  dL/dq = (dL/dqn - qn (qn . dL/dqn)) / |q|
         const float dot = A.qn[0] * qn[0] + A.qn[1] * qn[1] + A.qn[2] * qn[2] + A.qn[3] * qn[3];
         for (int j = 0; j < 3; ++j) {
@@ -369,9 +447,26 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) project_bwd_kernel(
     }
     __syncwarp();
     float *go = gsh + base * KC;
-    for (int e = lane; e < nv * KC; e += 32) {
-        const int pi = e / KC;
-        go[e] = sdsh[pi * LD + (e - pi * KC)];
+    if (nv == 32 && ((reinterpret_cast<uintptr_t>(go) & 15) == 0)) {
+#pragma unroll
+        for (int it = 0; it < PER; ++it) {
+            const int u = lane + 32 * it;
+            if (u < F4) {
+                float vals[4];
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int e = 4 * u + c4;
+                    const int pi = e / KC;
+                    vals[c4] = sdsh[pi * LD + (e - pi * KC)];
+                }
+                reinterpret_cast<float4 *>(go)[u] = make_float4(vals[0], vals[1], vals[2], vals[3]);
+            }
+        }
+    } else {
+        for (int e = lane; e < nv * KC; e += 32) {
+            const int pi = e / KC;
+            go[e] = sdsh[pi * LD + (e - pi * KC)];
+        }
     }
 }
 
@@ -586,9 +681,10 @@ int launch_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams
     XPR_DEG_DISPATCH(DEG, {
         const size_t smem = (size_t)kBwdWarps * 2 * 32 * sh_ld<DEG>() * sizeof(float);
         attr = cudaFuncSetAttribute(project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // one view: one row buffer per warp (half the limit)
         if (attr == cudaSuccess)
-            project_bwd_kernel<DEG><<<blocks, tpb, smem, st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg,
-                                                               d_rec, g.mu, g.scale, g.quat, g.opacity, g.sh);
+            project_bwd_kernel<DEG><<<blocks, tpb, n_views == 1 ? smem / 2 : smem, st>>>(
+                p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, d_rec, g.mu, g.scale, g.quat, g.opacity, g.sh);
     });
     XPR_CUDA_TRY(attr);
     XPR_LAUNCH_CHECK("project_bwd_kernel");

@@ -1,12 +1,15 @@
 // Shader stage (Sec. 2 Shader; Sec. 4.3; Algorithm 1; Listing 1 evaluate) and its adjoint.
 //
-// Forward (K4): one thread block per tile; each thread owns four pixels of the tile,
-// (x, y + q h/4) for q = 0..3, so every shared-memory read of a list entry and every warp
-// reduction of the adjoint serves four pixels.  The tile's depth-sorted list is consumed in batches of
-// `batch` entries staged in shared memory, then each pixel walks the batch front to back:
+// Forward (K4): one thread block per tile; each thread owns PX pixels of one pixel column of the
+// tile (4 in the forward, 8 in the adjoint on 16x16 tiles), so every shared-memory read of a list
+// entry, the column factors of the power and every warp reduction of the adjoint serve PX pixels.
+// The tile's depth-sorted list is consumed in batches of `batch` entries staged in shared memory,
+// then each pixel walks the batch front to back:
 //   power = -(c00 dx^2 + 2 c01 dx dy + c11 dy^2)/2  (base-2 form, conic pre-scaled by log2 e)
 //   skip if power > 0;  alpha = min(alpha_max, o 2^power2);  skip if alpha < alpha_t
 //   stop if T (1 - alpha) < t_eps (that entry is not blended);  C += c alpha T;  T *= 1 - alpha
+// The gates are predicates and the state updates selects (a pixel an entry does not reach adds
+// zeros), so a warp runs one straight path per entry.
 // A block stops loading batches as soon as every pixel has terminated (__syncthreads_and), which
 // replaces the paper's fixed trip counts and per-bin batch boundaries with a dynamic exit.
 //
@@ -14,10 +17,12 @@
 // recomputing T_i = T_{i+1} / (1 - alpha_i) and the colour behind, S (starting at T_final bg):
 //   dL/dc_i = g alpha_i T_i,   dL/dalpha_i = g . (c_i T_i - S_i / (1 - alpha_i))
 // S enters only through g . S, so each pixel carries that scalar, B (B += (g . c_i) alpha_i T_i).
-// then through alpha = o exp(power) (zero through the clamp) to o, mu_2D and the conic.  The 9
-// per-pixel partial gradients of one entry are summed over the thread's four pixels, over the
-// warp with shuffles, over the block in shared memory, and added to global memory with one set
-// of vector atomics per (tile, entry).
+// then through alpha = o exp(power) (zero through the clamp) to o, mu_2D and the conic.  The
+// mean's partials d power / d mu_2D = -(2A dx + B dy, B dx + 2C dy) are linear in (dx, dy) with
+// per-entry factors, so a pixel accumulates only dp dx and dp dy (with dp dx^2, dp dx dy, dp dy^2
+// for the conic) and the factors are applied once per (tile, entry).  The 9 per-pixel partials
+// of one entry are summed over the thread's pixels, over the warp with shuffles, over the block
+// in shared memory, and added to global memory with one set of vector atomics per (tile, entry).
 //
 // Views: tile gt of a multi-view launch is tile gt mod T of view gt div T (T tiles per view, all
 // views of one size); images are [views, 3, H, W].  Scheduling: one block per tile, or a
@@ -31,12 +36,13 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 // Pixels per thread: (x, y + q h/PX), q = 0..PX-1, with PX = min(cap, tile pixels / 32) so that a
 // tile's block is always whole warps (warp-wide shuffles and votes need all 32 lanes).  The caps
-// of the forward and the adjoint are compile-time constants.
+// of the forward (4) and the adjoint (8: one warp per 16x16 tile, each warp reduction serving 8
+// pixels) are compile-time constants.
 #ifndef XPR_FWD_PX
 #define XPR_FWD_PX 4
 #endif
 #ifndef XPR_BWD_PX
-#define XPR_BWD_PX 4
+#define XPR_BWD_PX 8
 #endif
 template <int TW, int TH, int CAP>
 __host__ __device__ constexpr int px_cap() {
@@ -113,26 +119,25 @@ struct PixelFwd {
     bool done;
 };
 
-// Blends entry (g, c, cb) at list position pos into pixel P (front to back).
-__device__ __forceinline__ void blend(PixelFwd &P, float dx, const float4 &g, const float4 &c, float cb, int pos,
-                                      const Consts &k) {
+// Blends entry (g, c, cb) at list position pos into pixel P (front to back).  Branch-free: the
+// gates become predicates and the state updates selects, so a warp runs one straight path.
+__device__ __forceinline__ void blend(PixelFwd &P, const ColTerms &ct, const float4 &g, const float4 &c, float cb,
+                                      int pos, const Consts &k) {
     const float dy = __fsub_rn(P.fy, g.y);
-    const float p = eval_power2(g.z, g.w, c.x, dx, dy);
-    if (p > 0.f) return;
-    const float og = __fmul_rn(c.y, ex2_approx(p));
+    const float p = eval_power2(ct, c.x, dy);
+    const float og = __fmul_rn(c.y, ex2_approx(fminf(p, 0.f)));
     const float al = fminf(k.amax, og);
-    if (al < k.at) return;
+    const bool live = !P.done && p <= 0.f && al >= k.at;
     const float tt = __fmul_rn(P.T, __fsub_rn(1.f, al));
-    if (tt < k.teps) {
-        P.done = true;
-        return;
-    }
-    const float w = al * P.T;
+    const bool stop = live && tt < k.teps;
+    const bool take = live && !stop;
+    const float w = take ? al * P.T : 0.f;
     P.r = fmaf(c.z, w, P.r);
     P.g = fmaf(c.w, w, P.g);
     P.b = fmaf(cb, w, P.b);
-    P.T = tt;
-    P.last = pos + 1;
+    P.T = take ? tt : P.T;
+    P.last = take ? pos + 1 : P.last;
+    P.done = P.done || stop;
 }
 
 template <int TW, int TH>
@@ -170,11 +175,12 @@ __device__ __forceinline__ void fwd_tile(int gt, const float *__restrict__ rec, 
                 const float4 c = s_c[j];
                 const float cb = s_b[j];
                 const float dx = __fsub_rn(fx, g.x);
+                const ColTerms ct = column_terms(g.z, g.w, dx);
                 const int pos = base + j - rg.x;
                 all_done = true;
 #pragma unroll
                 for (int q = 0; q < kPX; ++q) {
-                    if (!P[q].done) blend(P[q], dx, g, c, cb, pos, k);
+                    blend(P[q], ct, g, c, cb, pos, k);
                     all_done &= P[q].done;
                 }
                 if (all_done) break;
@@ -258,37 +264,36 @@ struct PixelBwd {
 };
 
 // Adds pixel P's partial gradients for the entry at list position pos (back to front) into v[9]:
-// v = [qx dp, qy dp, dp dx^2, dp dx dy, dp dy^2, dL/do, dL/dr, dL/dg, dL/db] in the base-2 form.
-__device__ __forceinline__ bool adjoint(PixelBwd &P, float dx, const float4 &g, const float4 &c, float cb, int pos,
-                                        const Consts &k, float *v) {
-    if (pos >= P.last) return false;
+// v = [dp dx, dp dy, dp dx^2, dp dx dy, dp dy^2, dL/do, dL/dr, dL/dg, dL/db]; the conic factors of
+// d power / d mu_2D (2A dx + B dy, B dx + 2C dy in the base-2 form) are applied at the flush.
+// Branch-free: a pixel the entry does not reach adds zeros and keeps its state.
+__device__ __forceinline__ bool adjoint(PixelBwd &P, float dx, const ColTerms &ct, const float4 &g, const float4 &c,
+                                        float cb, int pos, const Consts &k, float *v) {
     const float dy = __fsub_rn(P.fy, g.y);
-    const float p = eval_power2(g.z, g.w, c.x, dx, dy);
-    if (p > 0.f) return false;
-    const float G = ex2_approx(p);
+    const float p = eval_power2(ct, c.x, dy);
+    const float G = ex2_approx(fminf(p, 0.f));
     const float og = __fmul_rn(c.y, G);
     const float al = fminf(k.amax, og);
-    if (al < k.at) return false;
+    const bool live = pos < P.last && p <= 0.f && al >= k.at;
     const float inv = rcp_approx(1.f - al);
     const float Ti = P.T * inv;
-    const float w = al * Ti;
+    const float w = live ? al * Ti : 0.f;
     v[6] = fmaf(P.g0, w, v[6]);
     v[7] = fmaf(P.g1, w, v[7]);
     v[8] = fmaf(P.g2, w, v[8]);
     const float gc = fmaf(P.g0, c.z, fmaf(P.g1, c.w, P.g2 * cb));
-    const float dal = fmaf(gc, Ti, -P.B * inv);
+    const float dal = (live && og < k.amax) ? fmaf(gc, Ti, -P.B * inv) : 0.f;
     P.B = fmaf(gc, w, P.B);
-    P.T = Ti;
-    if (og < k.amax) {
-        const float dp = dal * al;  // dL/dpower (natural log units)
-        v[5] = fmaf(dal, G, v[5]);
-        v[0] = fmaf(dp, fmaf(2.f * g.z, dx, g.w * dy), v[0]);
-        v[1] = fmaf(dp, fmaf(g.w, dx, 2.f * c.x * dy), v[1]);
-        v[2] = fmaf(dp * dx, dx, v[2]);
-        v[3] = fmaf(dp * dx, dy, v[3]);
-        v[4] = fmaf(dp * dy, dy, v[4]);
-    }
-    return true;
+    P.T = live ? Ti : P.T;
+    const float dp = dal * al;  // dL/dpower (natural log units)
+    v[5] = fmaf(dal, G, v[5]);
+    const float dpx = dp * dx, dpy = dp * dy;
+    v[0] += dpx;
+    v[1] += dpy;
+    v[2] = fmaf(dpx, dx, v[2]);
+    v[3] = fmaf(dpx, dy, v[3]);
+    v[4] = fmaf(dpy, dy, v[4]);
+    return live;
 }
 
 __device__ __forceinline__ PixelBwd load_pixel_bwd(bool inside, float fy, int64_t pix, int64_t HW,
@@ -364,9 +369,10 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
             const float4 c = s_c[j];
             const float cb = s_b[j];
             const float dx = __fsub_rn(fx, g.x);
+            const ColTerms ct = column_terms(g.z, g.w, dx);
             bool hit = false;
 #pragma unroll
-            for (int q = 0; q < kPX; ++q) hit |= adjoint(P[q], dx, g, c, cb, pos, k, vv);
+            for (int q = 0; q < kPX; ++q) hit |= adjoint(P[q], dx, ct, g, c, cb, pos, k, vv);
             if (__any_sync(kFull, hit)) {
                 // vv[0..7]: transposed reduce-scatter (9 shuffles); afterwards lane l with l % 4 == 0
                 // holds the warp total of value l / 4.  vv[8]: plain butterfly (5 shuffles).
@@ -388,7 +394,9 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
             if (any && s_id[e] < k.n) {
                 // record layout: [dmx, dmy, dc00, dc01] [dc11, do, dr, dg] [db, 0, 0, 0]; vector atomics
                 float4 *d = reinterpret_cast<float4 *>(d_rec + (size_t)s_id[e] * XPR_REC_FLOATS);
-                atomicAdd(d, make_float4(-kLn2 * a[0], -kLn2 * a[1], -0.5f * a[2], -a[3]));
+                const float A2 = 2.f * s_g[e].z, Bc = s_g[e].w, C2 = 2.f * s_c[e].x;
+                const float qx = fmaf(A2, a[0], Bc * a[1]), qy = fmaf(Bc, a[0], C2 * a[1]);
+                atomicAdd(d, make_float4(-kLn2 * qx, -kLn2 * qy, -0.5f * a[2], -a[3]));
                 atomicAdd(d + 1, make_float4(-0.5f * a[4], a[5], a[6], a[7]));
                 atomicAdd(reinterpret_cast<float *>(d + 2), a[8]);
             }

@@ -239,12 +239,18 @@ __device__ __forceinline__ Shade load_shade(const float *__restrict__ rec, uint3
     return s;
 }
 
-// Listing 1 evaluate in base-2 form.  Every operation is an explicit IEEE intrinsic so
-// the forward and the backward kernels compute bit-identical powers and alphas.
-__device__ __forceinline__ float eval_power2(float A, float B, float C, float dx, float dy) {
-    float t = __fmaf_rn(A, dx, __fmul_rn(B, dy));  // A dx + B dy
-    float u = __fmul_rn(__fmul_rn(C, dy), dy);     // C dy^2
-    return __fmaf_rn(t, dx, u);                    // A dx^2 + B dx dy + C dy^2
+// Listing 1 evaluate in base-2 form, p = A dx^2 + B dx dy + C dy^2, factored by pixel column: a
+// thread's pixels share one column, so A dx^2 and B dx are formed once per (entry, column) and each
+// pixel adds (C dy + B dx) dy with two fused multiply-adds.  Every operation is an explicit IEEE
+// intrinsic so the forward and the backward kernels compute bit-identical powers and alphas.
+struct ColTerms {
+    float adx2, bdx;  // A dx^2, B dx
+};
+__device__ __forceinline__ ColTerms column_terms(float A, float B, float dx) {
+    return ColTerms{__fmul_rn(__fmul_rn(A, dx), dx), __fmul_rn(B, dx)};
+}
+__device__ __forceinline__ float eval_power2(const ColTerms &t, float C, float dy) {
+    return __fmaf_rn(__fmaf_rn(C, dy, t.bdx), dy, t.adx2);
 }
 #endif
 
