@@ -377,38 +377,10 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 5) project_bwd_kernel(
     const bool one = cs.n_views == 1;  // one row buffer: the gradient overwrites the staged row
     float *ssh = s_bwd + (size_t)w * (one ? 1 : 2) * 32 * LD;
     float *sdsh = one ? ssh : ssh + 32 * LD;
-    const float *gs = sh + base * KC;
     const int64_t i = base + lane;
     Params P = {};
     if (i < n) P = load_params(mu, scale, quat, opac, i);
-    constexpr int F4 = 8 * KC;              // float4 of a full warp's rows (32 KC floats)
-    constexpr int PER = (F4 + 31) / 32;      // per lane
-    if (nv == 32 && ((reinterpret_cast<uintptr_t>(gs) & 15) == 0)) {
-        float4 r[PER];
-#pragma unroll
-        for (int it = 0; it < PER; ++it) {
-            const int u = lane + 32 * it;
-            if (u < F4) r[it] = __ldg(reinterpret_cast<const float4 *>(gs) + u);
-        }
-#pragma unroll
-        for (int it = 0; it < PER; ++it) {
-            const int u = lane + 32 * it;
-            if (u < F4) {
-                const float vals[4] = {r[it].x, r[it].y, r[it].z, r[it].w};
-#pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    const int e = 4 * u + c4;
-                    const int pi = e / KC;
-                    ssh[pi * LD + (e - pi * KC)] = vals[c4];
-                }
-            }
-        }
-    } else {
-        for (int e = lane; e < nv * KC; e += 32) {
-            const int pi = e / KC;
-            ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
-        }
-    }
+    stage_sh<DEG>(sh, base, nv, ssh);
     if (!one)
         for (int c = 0; c < KC; ++c) sdsh[lane * LD + c] = 0.f;
     __syncwarp();
@@ -446,28 +418,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 5) project_bwd_kernel(
         gopac[i] = A.o;
     }
     __syncwarp();
-    float *go = gsh + base * KC;
-    if (nv == 32 && ((reinterpret_cast<uintptr_t>(go) & 15) == 0)) {
-#pragma unroll
-        for (int it = 0; it < PER; ++it) {
-            const int u = lane + 32 * it;
-            if (u < F4) {
-                float vals[4];
-#pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) {
-                    const int e = 4 * u + c4;
-                    const int pi = e / KC;
-                    vals[c4] = sdsh[pi * LD + (e - pi * KC)];
-                }
-                reinterpret_cast<float4 *>(go)[u] = make_float4(vals[0], vals[1], vals[2], vals[3]);
-            }
-        }
-    } else {
-        for (int e = lane; e < nv * KC; e += 32) {
-            const int pi = e / KC;
-            go[e] = sdsh[pi * LD + (e - pi * KC)];
-        }
-    }
+    write_sh_rows<DEG>(sdsh, nv, gsh + base * KC);
 }
 
 // ---- multi-scene items: item k projects primitives [prim0, prim0 + n) of the concatenated arrays

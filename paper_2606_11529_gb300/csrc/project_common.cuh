@@ -193,17 +193,75 @@ constexpr int kProjWarps = 4;
 // One thread per primitive and all views; each warp first stages its 32 primitives' SH
 // coefficients in shared memory with coalesced loads (a thread's own row is 3K floats long).
 // Stages the SH coefficients of a warp's 32 primitives (from base) in shared memory, coalesced.
+// A full warp whose rows start on a 16-byte boundary loads them as float4, every load of a lane
+// issued before its first shared-memory store (12 loads in flight per lane at degree 3).
 template <int DEG>
 __device__ __forceinline__ void stage_sh(const float *__restrict__ sh, int64_t base, int nv, float *ssh) {
     constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
     constexpr int LD = sh_ld<DEG>();
+    constexpr int F4 = 8 * KC;          // float4 of a full warp's rows (32 KC floats)
+    constexpr int PER = (F4 + 31) / 32;  // per lane
     const int lane = threadIdx.x & 31;
     const float *gs = sh + base * KC;
-    for (int e = lane; e < nv * KC; e += 32) {
-        const int pi = e / KC;
-        ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
+    if (nv == 32 && (reinterpret_cast<uintptr_t>(gs) & 15) == 0) {
+        float4 r[PER];
+#pragma unroll
+        for (int it = 0; it < PER; ++it) {
+            const int u = lane + 32 * it;
+            if (u < F4) r[it] = __ldg(reinterpret_cast<const float4 *>(gs) + u);
+        }
+#pragma unroll
+        for (int it = 0; it < PER; ++it) {
+            const int u = lane + 32 * it;
+            if (u < F4) {
+                const float v4[4] = {r[it].x, r[it].y, r[it].z, r[it].w};
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int e = 4 * u + c4;
+                    const int pi = e / KC;
+                    ssh[pi * LD + (e - pi * KC)] = v4[c4];
+                }
+            }
+        }
+    } else {
+        for (int e = lane; e < nv * KC; e += 32) {
+            const int pi = e / KC;
+            ssh[pi * LD + (e - pi * KC)] = __ldg(gs + e);
+        }
     }
     __syncwarp();
+}
+
+// Writes the staged rows of a warp's nv primitives (row stride LD in shared memory) to the
+// contiguous rows at go, coalesced (float4 stores for a full warp on a 16-byte boundary).
+template <int DEG>
+__device__ __forceinline__ void write_sh_rows(const float *ssh, int nv, float *__restrict__ go) {
+    constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
+    constexpr int LD = sh_ld<DEG>();
+    constexpr int F4 = 8 * KC;
+    constexpr int PER = (F4 + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    if (nv == 32 && (reinterpret_cast<uintptr_t>(go) & 15) == 0) {
+#pragma unroll
+        for (int it = 0; it < PER; ++it) {
+            const int u = lane + 32 * it;
+            if (u < F4) {
+                float v4[4];
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int e = 4 * u + c4;
+                    const int pi = e / KC;
+                    v4[c4] = ssh[pi * LD + (e - pi * KC)];
+                }
+                reinterpret_cast<float4 *>(go)[u] = make_float4(v4[0], v4[1], v4[2], v4[3]);
+            }
+        }
+    } else {
+        for (int e = lane; e < nv * KC; e += 32) {
+            const int pi = e / KC;
+            go[e] = ssh[pi * LD + (e - pi * KC)];
+        }
+    }
 }
 
 // Sum over k of w_k grad Y_k (the partials of sh_basis_grad, folded into the sum term by term so

@@ -8,8 +8,9 @@
 //   power = -(c00 dx^2 + 2 c01 dx dy + c11 dy^2)/2  (base-2 form, conic pre-scaled by log2 e)
 //   skip if power > 0;  alpha = min(alpha_max, o 2^power2);  skip if alpha < alpha_t
 //   stop if T (1 - alpha) < t_eps (that entry is not blended);  C += c alpha T;  T *= 1 - alpha
-// The gates are predicates and the state updates selects (a pixel an entry does not reach adds
-// zeros), so a warp runs one straight path per entry.
+// Every pixel evaluates every entry with no early exit: the gates are predicates (the forward's
+// blend a predicated block, the adjoint's updates selects that add zeros for a pixel the entry
+// does not reach), so a warp runs one straight path per entry.
 // A block stops loading batches as soon as every pixel has terminated (__syncthreads_and), which
 // replaces the paper's fixed trip counts and per-bin batch boundaries with a dynamic exit.
 //
@@ -119,24 +120,27 @@ struct PixelFwd {
     bool done;
 };
 
-// Blends entry (g, c, cb) at list position pos into pixel P (front to back).  Branch-free: the
-// gates become predicates and the state updates selects, so a warp runs one straight path.
+// Blends entry (g, c, cb) at list position pos into pixel P (front to back).  No early exit: the
+// gates are predicates and the blend a predicated block.  2^p needs no guard: for the
+// positive-definite conic of a kept record p <= 0 up to rounding, and a non-finite value could
+// only reach alpha, which the p <= 0 gate then discards.
 __device__ __forceinline__ void blend(PixelFwd &P, const ColTerms &ct, const float4 &g, const float4 &c, float cb,
                                       int pos, const Consts &k) {
     const float dy = __fsub_rn(P.fy, g.y);
     const float p = eval_power2(ct, c.x, dy);
-    const float og = __fmul_rn(c.y, ex2_approx(fminf(p, 0.f)));
+    const float og = __fmul_rn(c.y, ex2_approx(p));
     const float al = fminf(k.amax, og);
     const bool live = !P.done && p <= 0.f && al >= k.at;
     const float tt = __fmul_rn(P.T, __fsub_rn(1.f, al));
     const bool stop = live && tt < k.teps;
-    const bool take = live && !stop;
-    const float w = take ? al * P.T : 0.f;
-    P.r = fmaf(c.z, w, P.r);
-    P.g = fmaf(c.w, w, P.g);
-    P.b = fmaf(cb, w, P.b);
-    P.T = take ? tt : P.T;
-    P.last = take ? pos + 1 : P.last;
+    if (live && !stop) {
+        const float w = al * P.T;
+        P.r = fmaf(c.z, w, P.r);
+        P.g = fmaf(c.w, w, P.g);
+        P.b = fmaf(cb, w, P.b);
+        P.T = tt;
+        P.last = pos + 1;
+    }
     P.done = P.done || stop;
 }
 
@@ -266,7 +270,9 @@ struct PixelBwd {
 // Adds pixel P's partial gradients for the entry at list position pos (back to front) into v[9]:
 // v = [dp dx, dp dy, dp dx^2, dp dx dy, dp dy^2, dL/do, dL/dr, dL/dg, dL/db]; the conic factors of
 // d power / d mu_2D (2A dx + B dy, B dx + 2C dy in the base-2 form) are applied at the flush.
-// Branch-free: a pixel the entry does not reach adds zeros and keeps its state.
+// Branch-free: a pixel the entry does not reach adds zeros and keeps its state (selects; a
+// predicated block measured slower here).  2^min(p, 0) keeps G finite for the products with
+// the selected zeros.
 __device__ __forceinline__ bool adjoint(PixelBwd &P, float dx, const ColTerms &ct, const float4 &g, const float4 &c,
                                         float cb, int pos, const Consts &k, float *v) {
     const float dy = __fsub_rn(P.fy, g.y);
@@ -378,8 +384,13 @@ __device__ __forceinline__ void bwd_tile(int gt, const float *__restrict__ rec, 
                 // holds the warp total of value l / 4.  vv[8]: plain butterfly (5 shuffles).
                 const float s8 = warp_sum(vv[8]);
                 const float r7 = reduce_scatter8(vv, lane);
-                if ((lane & 3) == 0) atomicAdd(&s_acc[lane >> 2][j], r7);
-                if (lane == 0) atomicAdd(&s_acc[8][j], s8);
+                if (NW == 1) {  // one warp per tile: each slot is written once
+                    if ((lane & 3) == 0) s_acc[lane >> 2][j] = r7;
+                    if (lane == 0) s_acc[8][j] = s8;
+                } else {
+                    if ((lane & 3) == 0) atomicAdd(&s_acc[lane >> 2][j], r7);
+                    if (lane == 0) atomicAdd(&s_acc[8][j], s8);
+                }
             }
         }
         __syncthreads();
