@@ -407,6 +407,22 @@ __device__ __forceinline__ LpEval lp_eval(float cx, float cy, const float4 &u0, 
     return r;
 }
 
+// The forward needs only the chord: enter = max_i (m_i - h_i), exit = min_i (m_i + h_i), with the
+// same operations as lp_eval.
+__device__ __forceinline__ float lp_chord(float cx, float cy, const float4 &u0, const float4 &u1, const float4 &u2,
+                                          const float4 &u3) {
+    const float dX = __fsub_rn(cx, u0.x), dY = __fsub_rn(cy, u0.y);
+    const float p[4] = {u1.x, u1.w, u2.z, u3.y}, q[4] = {u1.y, u2.x, u2.w, u3.z}, h[4] = {u1.z, u2.y, u3.x, u3.w};
+    float enter = __int_as_float(0xff800000), exit_ = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float m = -__fmaf_rn(p[i], dX, __fmul_rn(q[i], dY));
+        enter = fmaxf(enter, __fsub_rn(m, h[i]));
+        exit_ = fminf(exit_, __fadd_rn(m, h[i]));
+    }
+    return enter < exit_ ? __fsub_rn(exit_, enter) : 0.f;
+}
+
 struct LpPixFwd {
     float cy, T, r, g, b;
     int last;
@@ -443,33 +459,28 @@ __device__ __forceinline__ void lp_fwd_tile(int gt, const float *__restrict__ sd
         __syncthreads();
         if (!all_done) {
             for (int j = 0; j < cnt; ++j) {
-                const float4 u0 = S.u0[j], u1 = S.u1[j], u2 = S.u2[j], u3 = S.u3[j];
+                const float4 u0 = S.u0[j], u1 = S.u1[j], u2 = S.u2[j], u3 = S.u3[j], c = S.u4[j];
+                const float ks = -kLog2e * u0.z;
                 const int pos = base + j - rg.x;
                 all_done = true;
 #pragma unroll
                 for (int q = 0; q < PX; ++q) {
                     LpPixFwd &p = P[q];
-                    if (!p.done) {
-                        const LpEval ev = lp_eval(cx, p.cy, u0, u1, u2, u3);
-                        if (ev.dt > 0.f) {
-                            const float a0 = __fsub_rn(1.f, ex2_approx(__fmul_rn(-kLog2e * u0.z, ev.dt)));
-                            const float al = fminf(k.amax, a0);
-                            if (al >= k.at) {
-                                const float tt = __fmul_rn(p.T, __fsub_rn(1.f, al));
-                                if (tt < k.teps) {
-                                    p.done = true;
-                                } else {
-                                    const float4 c = S.u4[j];
-                                    const float w = al * p.T;
-                                    p.r = fmaf(c.x, w, p.r);
-                                    p.g = fmaf(c.y, w, p.g);
-                                    p.b = fmaf(c.z, w, p.b);
-                                    p.T = tt;
-                                    p.last = pos + 1;
-                                }
-                            }
-                        }
+                    const float dt = lp_chord(cx, p.cy, u0, u1, u2, u3);
+                    const float a0 = __fsub_rn(1.f, ex2_approx(__fmul_rn(ks, dt)));
+                    const float al = fminf(k.amax, a0);
+                    const bool live = !p.done && dt > 0.f && al >= k.at;
+                    const float tt = __fmul_rn(p.T, __fsub_rn(1.f, al));
+                    const bool stop = live && tt < k.teps;
+                    if (live && !stop) {
+                        const float w = al * p.T;
+                        p.r = fmaf(c.x, w, p.r);
+                        p.g = fmaf(c.y, w, p.g);
+                        p.b = fmaf(c.z, w, p.b);
+                        p.T = tt;
+                        p.last = pos + 1;
                     }
+                    p.done = p.done || stop;
                     all_done &= p.done;
                 }
                 if (all_done) break;
