@@ -115,30 +115,26 @@ __global__ void __launch_bounds__(TW *TH / feat_px<TW, TH, NF>()) render_feat_fw
                 all_done = true;
 #pragma unroll
                 for (int q = 0; q < PX; ++q) {
+                    // the colour forward's gates and blend (render.cu), so the image is identical
                     FPixFwd<NF> &p = P[q];
-                    if (!p.done) {
-                        const float dy = __fsub_rn(p.fy, g.y);
-                        const float pw = eval_power2(ct, c.x, dy);
-                        if (pw <= 0.f) {
-                            const float og = __fmul_rn(c.y, ex2_approx(pw));
-                            const float al = fminf(k.amax, og);
-                            if (al >= k.at) {
-                                const float tt = __fmul_rn(p.T, __fsub_rn(1.f, al));
-                                if (tt < k.teps) {
-                                    p.done = true;
-                                } else {
-                                    const float w = al * p.T;
-                                    p.r = fmaf(c.z, w, p.r);
-                                    p.g = fmaf(c.w, w, p.g);
-                                    p.b = fmaf(cb, w, p.b);
+                    const float dy = __fsub_rn(p.fy, g.y);
+                    const float pw = eval_power2(ct, c.x, dy);
+                    const float og = __fmul_rn(c.y, ex2_approx(pw));
+                    const float al = fminf(k.amax, og);
+                    const bool live = !p.done && pw <= 0.f && al >= k.at;
+                    const float tt = __fmul_rn(p.T, __fsub_rn(1.f, al));
+                    const bool stop = live && tt < k.teps;
+                    if (live && !stop) {
+                        const float w = al * p.T;
+                        p.r = fmaf(c.z, w, p.r);
+                        p.g = fmaf(c.w, w, p.g);
+                        p.b = fmaf(cb, w, p.b);
 #pragma unroll
-                                    for (int ch = 0; ch < NF; ++ch) p.f[ch] = fmaf(s_f[j][ch], w, p.f[ch]);
-                                    p.T = tt;
-                                    p.last = pos + 1;
-                                }
-                            }
-                        }
+                        for (int ch = 0; ch < NF; ++ch) p.f[ch] = fmaf(s_f[j][ch], w, p.f[ch]);
+                        p.T = tt;
+                        p.last = pos + 1;
                     }
+                    p.done = p.done || stop;
                     all_done &= p.done;
                 }
                 if (all_done) break;
