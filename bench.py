@@ -798,17 +798,25 @@ def main():
         e2e_ms, e2e_full_ms = float(t[0].item()), float(t[1].item())
 
     del fr
-    # the same step with the fused bin + sort (xpr_bin_sorted in place of xpr_tile_bin + xpr_sort_tiles)
-    ws_key = R.Workspace(fused=True)
+    # the same step with the other binning paths in place of xpr_bin_rows: the fused bin + sort
+    # (xpr_bin_sorted) and the key path (xpr_tile_bin + xpr_sort_tiles, with its stage times)
+    ws_fused, ws_key = R.Workspace(fused=True), R.Workspace(rows=False)
 
-    def key_step():
+    def alt_step(wsx, t=None):
         for p in P:
             p.grad = None
-        (R.render(*P, cam, cfg, ws_key) * w).sum().backward()
+        (R.render(*P, cam, cfg, wsx, t) * w).sum().backward()
 
     for _ in range(3):
-        key_step()
-    key_ms = _median_ms(key_step, args.steps, flush)
+        alt_step(ws_fused)
+        alt_step(ws_key)
+    fused_ms = _median_ms(lambda: alt_step(ws_fused), args.steps, flush)
+    key_ms = _median_ms(lambda: alt_step(ws_key), args.steps, flush)
+    key_timers = R.StageTimers()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        alt_step(ws_key, key_timers)
+    key_stages = {k: round(v, 4) for k, v in key_timers.mean_ms().items()}
     ut = None if args.no_ut else ut_leg(dev, args.n, max(args.steps, 5), flush)
     lp = None if args.no_lp else lp_leg(dev, max(args.steps, 5), flush)
     feat = None if args.no_feat else feat_leg(dev, args.n, max(args.steps, 5), flush)
@@ -832,7 +840,8 @@ def main():
             "config": workload_config(sc, cam, cfg),
             "workload_stats": {"intersections": I, "pairs_blended": pairs,
                                "views_per_s_total": round(world * 1000.0 / ms, 2),
-                               "fused_bin_sort_path_ms": round(key_ms, 4)},
+                               "fused_bin_sort_path_ms": round(fused_ms, 4), "key_path_ms": round(key_ms, 4),
+                               "key_path_stages_ms": key_stages},
             "l2": "flushed between steps (256 MB write outside the timed events)",
             "parallelism": (f"view-parallel x{world}: one view per rank, one packed NCCL all-reduce of the "
                             f"{sum(p.numel() for p in P) * 4 // 2 ** 20} MB of gradients per step") if world > 1

@@ -18,7 +18,8 @@
  *     of launched kernels.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *     enqueued asynchronously on it; entry points that must return a count to
- *     the host (xpr_tile_bin, xpr_bin_sorted) synchronise that stream.
+ *     the host (xpr_tile_bin, xpr_bin_sorted, xpr_bin_rows) synchronise that
+ *     stream.
  *   - Floating-point arrays are IEEE float32, row-major, densely packed.
  *   - Return value: an XprStatus.  On error nothing is guaranteed about the
  *     output buffers; xpr_last_error() describes the failure.
@@ -435,6 +436,41 @@ size_t xpr_bin_sorted_workspace(int64_t n, int32_t n_views, const XprCamera *cam
 int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *order, int64_t n,
                    int32_t n_views, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges, uint32_t *vals,
                    int64_t capacity, int64_t *n_isect, void *workspace, size_t ws_bytes, void *stream);
+
+/* ---- Bin + sort by tile rows ------------------------------------------------
+ * xpr_bin_rows: Sec. 4.2's replicate / assign tile id / cull and "sort and
+ * identify bounds" for one view whose tile grid has at most 128 columns and
+ * 128 rows, with one radix pass over the pairs: the row form of the cull gives
+ * every primitive one span of kept tile columns per row of its box; the spans
+ * (about seven pairs each on the headline workload) are sorted by row in depth
+ * order, expanded into pairs grouped by row, and one stable pass over the
+ * pairs' column groups them by tile.  The result is bit-identical to
+ * xpr_tile_bin in the same order followed by xpr_sort_tiles: the same kept
+ * pairs (same FP32 cull), each tile's list in emission order.
+ *   rec, bbox, tile_count: from xpr_project (n records of one view);
+ *   isect_count[n] (device, may be NULL): the kept tile counts from
+ *     xpr_project; with them the call reads both totals back at once;
+ *   order[n]: the emission order, from xpr_depth_order;
+ *   ranges[T,2] (int32, device): OVERWRITTEN, [0, 0) for a tile with no pairs;
+ *   vals[capacity] (u32, device): record indices, tile-major, in emission order
+ *     within a tile;
+ *   *n_isect, *n_spans (HOST): the kept pairs I and the span slots S (one per
+ *     row of every box).  If I > capacity or workspace_bytes is below
+ *     xpr_bin_rows_workspace(n, S, I, cam, cfg), the call returns
+ *     XPR_ERR_CAPACITY with both counts set and without writing vals or
+ *     ranges; call again with enough of both.
+ * The call synchronises the stream once with isect_count (twice without).
+ * Grids with more than 128 tile columns or rows are rejected with
+ * XPR_ERR_INVALID (use xpr_tile_bin + xpr_sort_tiles for them).
+ * workspace (device, 256-byte aligned, caller-owned):
+ * xpr_bin_rows_workspace(n, S, I, cam, cfg) bytes (0 for invalid arguments);
+ * with S = I = 0 it is the least size that lets the call report the counts. */
+size_t xpr_bin_rows_workspace(int64_t n, int64_t n_spans, int64_t n_isect, const XprCamera *cam,
+                              const XprConfig *cfg);
+int xpr_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                 const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges,
+                 uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *workspace,
+                 size_t workspace_bytes, void *stream);
 
 /* ---- Rendered features (3DGS) ----------------------------------------------------
  * The "rendered feature" class of the design space (depth, semantics): channel c of

@@ -89,6 +89,9 @@ SIGNATURES = {
     "xpr_project_color": (c_i32, [c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), c_i32, ctypes.POINTER(XprConfig),
                                   c_vp, c_vp]),
     "xpr_bin_sorted_workspace": (c_sz, [c_i64, c_i32, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig)]),
+    "xpr_bin_rows_workspace": (c_sz, [c_i64, c_i64, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig)]),
+    "xpr_bin_rows": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
+                             c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
     "xpr_bin_sorted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(XprCamera),
                                ctypes.POINTER(XprConfig), c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz,
                                c_vp]),
@@ -553,6 +556,52 @@ def xpr_bin_sorted(rec, bbox, tile_count, order, n, cam, cfg, n_views=1, capacit
         I = int(got.value)
         return ranges, vals[:I], I
     raise XprError(XPR_ERR_CAPACITY, "xpr_bin_sorted", "capacity retry failed")
+
+
+def bin_rows_ok(cam, cfg) -> bool:
+    """xpr_bin_rows takes one view of at most 128 x 128 tiles (3DGS and 3DGUT)."""
+    Wt, Ht = tiles_of(cam, cfg)
+    return Wt <= 128 and Ht <= 128 and int(getattr(cfg, "method", XPR_METHOD_3DGS)) != XPR_METHOD_LINPRIM
+
+
+def bin_rows_workspace_bytes(n, n_spans, n_isect, cam, cfg):
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    return int(load().xpr_bin_rows_workspace(int(n), int(n_spans), int(n_isect), ctypes.byref(c), ctypes.byref(g)))
+
+
+def xpr_bin_rows(rec, bbox, tile_count, order, n, cam, cfg, isect_count=None, capacity=None, workspace=None,
+                 stream=None):
+    """Bin + sort by tile rows: returns (ranges[T,2], vals[I] (record indices, int32 storage), I, S,
+    workspace), S the span slots.  ``capacity``: initial size of vals; ``workspace``: initial
+    scratch.  On XPR_ERR_CAPACITY either is re-allocated to the reported counts and the call repeated;
+    the workspace returned is the one used (keep it for the next call)."""
+    L = load()
+    dev = rec.device
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    Wt, Ht = tiles_of(cam, cfg)
+    ranges = torch.empty((Wt * Ht, 2), dtype=torch.int32, device=dev)
+    cap = int(capacity) if capacity is not None else max(4 * n, 1024)
+    vals = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    need = bin_rows_workspace_bytes(n, 0, 0, cam, cfg)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        got_i, got_s = c_i64(0), c_i64(0)
+        s = L.xpr_bin_rows(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _ptr(order), n,
+                           ctypes.byref(c), ctypes.byref(g), _ptr(ranges), _ptr(vals), vals.numel(),
+                           ctypes.byref(got_i), ctypes.byref(got_s), _ptr(workspace), workspace.numel(),
+                           _stream(stream))
+        if s == XPR_ERR_CAPACITY and got_i.value <= 0x7FFFFFFF and got_s.value <= 0x7FFFFFFF:
+            if got_i.value > vals.numel():
+                vals = torch.empty(got_i.value, dtype=torch.int32, device=dev)
+            need = bin_rows_workspace_bytes(n, got_s.value, got_i.value, cam, cfg)
+            if workspace.numel() < need:
+                workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+            continue
+        _check(s, "xpr_bin_rows")
+        I = int(got_i.value)
+        return ranges, vals[:I], I, int(got_s.value), workspace
+    raise XprError(XPR_ERR_CAPACITY, "xpr_bin_rows", "capacity retry failed")
 
 
 def xpr_tile_worklist(ranges, workspace=None, stream=None):

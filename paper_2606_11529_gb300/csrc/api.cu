@@ -752,6 +752,33 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
                           workspace, ws_bytes, as_stream(stream));
 }
 
+size_t xpr_bin_rows_workspace(int64_t n, int64_t n_spans, int64_t n_isect, const XprCamera *cam,
+                              const XprConfig *cfg) {
+    if (validate_camera_config(cam, cfg) != XPR_OK || n < 0 || n_spans < 0 || n_isect < 0 ||
+        !bin_rows_supported(*cam, *cfg))
+        return 0;
+    return bin_rows_workspace_bytes(n, n_spans, n_isect, *cam, *cfg);
+}
+
+int xpr_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                 const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges,
+                 uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *workspace,
+                 size_t ws_bytes, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_n(n))) return s;
+    if (cfg->method == XPR_METHOD_LINPRIM)
+        return fail(XPR_ERR_INVALID, "xpr_bin_rows: LinPrim is binned by xpr_tile_bin_lp");
+    if (!ranges || !n_isect || !n_spans) return fail(XPR_ERR_INVALID, "xpr_bin_rows: NULL ranges, n_isect or n_spans");
+    if (capacity < 0) return fail(XPR_ERR_INVALID, "xpr_bin_rows: negative capacity");
+    if (n > 0 && (!rec || !bbox || !tile_count || !order || !workspace || (capacity > 0 && !vals)))
+        return fail(XPR_ERR_INVALID, "xpr_bin_rows: NULL pointer");
+    if (n > 0 && (!aligned(rec, 16) || !aligned(bbox, 16) || !aligned(workspace, 256)))
+        return fail(XPR_ERR_INVALID, "xpr_bin_rows: rec/bbox must be 16-byte and workspace 256-byte aligned");
+    return launch_bin_rows(rec, bbox, tile_count, isect_count, order, n, *cam, *cfg, ranges, vals, capacity, n_isect,
+                           n_spans, workspace, ws_bytes, as_stream(stream));
+}
+
 // ---- 3DGUT --------------------------------------------------------------------------------
 
 int xpr_project_ut(const XprPrims *prims, int64_t n, const XprCamera *cam, const XprConfig *cfg, float *rec,

@@ -10,19 +10,6 @@
 namespace xpr {
 namespace {
 
-__device__ __forceinline__ int box_of(const int4 *__restrict__ bbox, const int *__restrict__ tcount, int i,
-                                      const Grid &g, int4 &bb) {
-    bb = make_int4(0, 0, 0, 0);
-    if (tcount[i] <= 0) return 0;
-    bb = bbox[i];
-    bb.x = max(bb.x, 0);  // never leave the tile grid, whatever the caller's boxes say
-    bb.y = max(bb.y, 0);
-    bb.z = min(bb.z, g.Wt);
-    bb.w = min(bb.w, g.Ht);
-    const int w = bb.z - bb.x, h = bb.w - bb.y;
-    return (w > 0 && h > 0) ? w * h : 0;
-}
-
 // Count pass (used when the caller has no per-primitive counts): counts[j] = kept tiles of position j.
 __global__ void __launch_bounds__(256) bin_count_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
                                                         const int *__restrict__ tcount,

@@ -1,0 +1,287 @@
+// Rasterizer first half by rows (Sec. 4.2: Replicate, Assign tile ID, Cull, Sort and identify bounds)
+// for one view whose tile grid has at most 128 columns and 128 rows.
+//
+// The tile cull in row form (cull.cuh) gives, for every primitive and every tile row of its box, one
+// interval [ka, kb] of kept tile columns: a span.  The per-tile lists are built from spans:
+//   1. span slots: each position j of the depth order owns one slot per row of its box (offsets by
+//      a scan of the box heights in depth order); the emit kernel writes each slot as a 4-byte key
+//      (its tile row, or 255 for a row with no kept tile, in bits 0-7; the first kept column in
+//      bits 8-14; the number of kept tiles in bits 15-22) and its primitive as the value;
+//   2. one stable radix pass over the span slots by the row bits, moving key and value: spans
+//      grouped by row, each row's spans in depth order (the empty rows last);
+//   3. an exclusive scan of the span lengths in that order gives every span its first pair, and
+//      the expansion writes the pairs of each span contiguously: tile code (tx << 7) | ty and the
+//      primitive, so the pairs are grouped by tile row, in depth order inside every row (every
+//      read of these passes is a coalesced one of the sorted spans);
+//   4. one stable radix pass over the pairs by the code's column bits [7, 14): the pairs end
+//      grouped by (column, row), i.e. by tile, and inside every tile still in depth order, which is
+//      the tile-major depth-sorted list of Sec. 4.2 with one radix pass over the pairs instead of
+//      two (the rows were sorted on the spans, about seven pairs each here).
+// The tile ranges are found in the code order (column-major over a 128-row grid) and permuted to
+// the row-major tile ids the render uses.  The result is identical, list for list, to the depth-
+// ordered emission followed by the stable sort of the tile ids.
+#include "cull.cuh"
+
+namespace xpr {
+namespace {
+
+constexpr uint32_t kRowNone = 255;  // key of a span slot whose box row keeps no tile: sorted last
+constexpr int kMaxRowGrid = 128;    // tile columns and rows: 7 bits each in the pair's tile code
+
+__global__ void box_rows_kernel(const int4 *__restrict__ bbox, const int *__restrict__ tcount, int64_t n, Grid g,
+                                int32_t *__restrict__ rows) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 bb;
+    rows[i] = box_of(bbox, tcount, (int)i, g, bb) > 0 ? bb.w - bb.y : 0;
+}
+
+// Warp w takes the positions w, w + nw, ... (interleaved over the depth order, as the pair
+// emission does) and flattens their box rows over its lanes; each row's span goes to its slot.
+__global__ void __launch_bounds__(256) span_emit_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
+                                                        const int *__restrict__ tcount,
+                                                        const int *__restrict__ order, int64_t n, Grid g,
+                                                        const int32_t *__restrict__ slot0,
+                                                        uint32_t *__restrict__ span_key,
+                                                        uint32_t *__restrict__ span_prim) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (n + 31) / 32;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= nw) return;
+    const int64_t j = w + (int64_t)lane * nw;
+    int i = 0, area = 0, base = 0;
+    int4 bb = make_int4(0, 0, 0, 0);
+    CullData d = {};
+    if (j < n) {
+        i = order[j];
+        base = slot0[j];
+        area = box_of(bbox, tcount, i, g, bb);
+        if (area > 0) d = load_cull(rec, i);
+    }
+    const int h = area > 0 ? bb.w - bb.y : 0;
+    const int incl = warp_incl_scan(h);
+    const int rows = __shfl_sync(kFullMask, incl, 31);
+    const int excl = incl - h;
+    for (int f0 = 0; f0 < rows; f0 += 32) {
+        const int f = f0 + lane;
+        const int p = lane_of(incl, f);
+        const CullData e = shfl_cull(d, p);
+        const int excl_p = __shfl_sync(kFullMask, excl, p);
+        const int ty = __shfl_sync(kFullMask, bb.y, p) + f - excl_p;
+        const int x0 = __shfl_sync(kFullMask, bb.x, p), x1 = __shfl_sync(kFullMask, bb.z, p);
+        const int base_p = __shfl_sync(kFullMask, base, p), i_p = __shfl_sync(kFullMask, i, p);
+        if (f < rows) {
+            int ka = 0, kb = -1;
+            const int c = row_span_in_box(e, g, ty, x0, x1, ka, kb);
+            const int64_t s = (int64_t)base_p + (f - excl_p);
+            span_key[s] = c > 0 ? ((uint32_t)c << 15) | ((uint32_t)ka << 8) | (uint32_t)ty : kRowNone;
+            span_prim[s] = (uint32_t)i_p;
+        }
+    }
+}
+
+// Warp w takes the sorted spans [32 w, 32 w + 32): their pairs are contiguous from the first span's
+// offset, and the warp writes them 32 at a time, lane k writing pair k of the warp's flattened list
+// (its span found from the ends of the non-empty spans, which are distinct).
+__global__ void __launch_bounds__(256) span_expand_kernel(const uint32_t *__restrict__ skey,
+                                                          const uint32_t *__restrict__ sprim, int64_t ns,
+                                                          const int32_t *__restrict__ pair0, int64_t capacity,
+                                                          uint32_t *__restrict__ codes, uint32_t *__restrict__ vals) {
+    __shared__ uint2 s_sp[8][32];  // per warp: the non-empty spans' (first code, primitive)
+    __shared__ int s_x[8][32];     // and the index of their first pair in the warp's list
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t q0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wl) * 32;
+    if (q0 >= ns) return;
+    const int64_t q = q0 + lane;
+    int len = 0;
+    uint32_t code0 = 0, prim = 0;
+    if (q < ns) {
+        const uint32_t key = skey[q];
+        len = (int)(key >> 15);
+        if (len > 0) {
+            code0 = (((key >> 8) & 0x7fu) << 7) | (key & 0x7fu);  // first kept column, row
+            prim = sprim[q];
+        }
+    }
+    const int64_t base = pair0[q0];
+    const int incl = warp_incl_scan(len);
+    const int total = __shfl_sync(kFullMask, incl, 31);
+    const unsigned nonempty = __ballot_sync(kFullMask, len > 0);
+    if (len > 0) {
+        const int slot = __popc(nonempty & lt_mask);
+        s_sp[wl][slot] = make_uint2(code0, prim);
+        s_x[wl][slot] = incl - len;
+    }
+    __syncwarp();
+    for (int k0 = 0; k0 < total; k0 += 32) {
+        const int k = k0 + lane;
+        const int e = incl - k0;
+        const unsigned ends = __reduce_or_sync(kFullMask, (len > 0 && e > 0 && e <= 32) ? 1u << (e - 1) : 0u);
+        const int sp = __popc(__ballot_sync(kFullMask, len > 0 && e <= 0)) + __popc(ends & lt_mask);
+        if (k < total) {
+            const uint2 r = s_sp[wl][sp];
+            const int64_t pos = base + k;
+            if (pos < capacity) {
+                codes[pos] = r.x + ((uint32_t)(k - s_x[wl][sp]) << 7);
+                vals[pos] = r.y;
+            }
+        }
+    }
+}
+
+__global__ void span_len_kernel(const uint32_t *__restrict__ skey, int64_t ns, int32_t *__restrict__ len) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < ns) len[q] = (int32_t)(skey[q] >> 15);
+}
+
+// ranges[ty Wt + tx] = the range found for tile code (tx << 7) | ty
+__global__ void permute_ranges_kernel(const int2 *__restrict__ by_code, int Wt, int Ht, int2 *__restrict__ ranges) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Wt * Ht) return;
+    const int tx = t % Wt, ty = t / Wt;
+    ranges[t] = by_code[(tx << 7) | ty];
+}
+
+size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
+
+struct RowsLayout {
+    size_t rows, slot0, part_n, isect_out, totals;           // depend on n only
+    size_t key, prim, skey, sprim, len, pair0, part_s;       // on the span slots
+    size_t sort_ws, codes, pvals, by_code;                   // on the pairs
+    size_t total;
+};
+
+RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, int Wt) {
+    RowsLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align_up(bytes);
+        return at;
+    };
+    L.rows = take((size_t)n * 4);
+    L.slot0 = take((size_t)(n + 1) * 4);
+    L.part_n = take(scan_partials_bytes(n));
+    L.isect_out = take((size_t)(n + 1) * 4);
+    L.totals = take(4 * sizeof(int64_t));
+    L.key = take((size_t)ns * 4);
+    L.prim = take((size_t)ns * 4);
+    L.skey = take((size_t)ns * 4);
+    L.sprim = take((size_t)ns * 4);
+    L.len = take((size_t)ns * 4);
+    L.pair0 = take((size_t)(ns + 1) * 4);
+    L.part_s = take(scan_partials_bytes(ns));
+    const size_t sws = sort_tiles_workspace_bytes(ns, 256), pws = sort_tiles_workspace_bytes(ni, Wt * kMaxRowGrid);
+    L.sort_ws = take(sws > pws ? sws : pws);  // the span sort, then the pair sort
+    L.codes = take((size_t)ni * 4);
+    L.pvals = take((size_t)ni * 4);
+    L.by_code = take((size_t)Wt * kMaxRowGrid * 8);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+bool bin_rows_supported(const XprCamera &cam, const XprConfig &cfg) {
+    return tiles_x(cam, cfg) <= kMaxRowGrid && tiles_y(cam, cfg) <= kMaxRowGrid;
+}
+
+size_t bin_rows_workspace_bytes(int64_t n, int64_t n_spans, int64_t n_isect, const XprCamera &cam,
+                                const XprConfig &cfg) {
+    return rows_layout(n, n_spans, n_isect, tiles_x(cam, cfg)).total;
+}
+
+// order: the depth order of the n records; isect_count (NULL: none): their kept tile counts, whose
+// total is read back with the span count (one synchronisation) so that both capacities are checked
+// before any span is written.  Returns XPR_ERR_CAPACITY (n_isect, n_spans set, nothing written)
+// when vals holds fewer than n_isect pairs or the workspace is below bin_rows_workspace_bytes.
+int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *isect_count,
+                    const int32_t *order, int64_t n, const XprCamera &cam, const XprConfig &cfg, int32_t *ranges,
+                    uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *ws, size_t ws_bytes,
+                    cudaStream_t st) {
+    const Grid g = make_grid(cam, cfg);
+    const int Wt = g.Wt, Ht = g.Ht, T = Wt * Ht;
+    if (!bin_rows_supported(cam, cfg))
+        return fail(XPR_ERR_INVALID, "xpr_bin_rows: a %d x %d tile grid has more than 128 tile columns or rows", Wt,
+                    Ht);
+    *n_isect = 0;
+    *n_spans = 0;
+    if (n == 0) {
+        if (T > 0) XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)T * 8, st));
+        return XPR_OK;
+    }
+    const RowsLayout L0 = rows_layout(n, 0, 0, Wt);
+    if (ws_bytes < L0.total) return fail(XPR_ERR_INVALID, "xpr_bin_rows: workspace %zu < %zu bytes", ws_bytes, L0.total);
+    char *p = reinterpret_cast<char *>(ws);
+    int32_t *rows = reinterpret_cast<int32_t *>(p + L0.rows);
+    int32_t *slot0 = reinterpret_cast<int32_t *>(p + L0.slot0);
+    int64_t *tot = reinterpret_cast<int64_t *>(p + L0.totals);
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    box_rows_kernel<<<nb, 256, 0, st>>>(reinterpret_cast<const int4 *>(bbox), tc, n, g, rows);
+    XPR_LAUNCH_CHECK("box_rows_kernel");
+    int s = launch_exclusive_scan(rows, slot0, n, p + L0.part_n, tot, st, order);
+    if (s != XPR_OK) return s;
+    if (isect_count) {
+        s = launch_exclusive_scan(isect_count, reinterpret_cast<int32_t *>(p + L0.isect_out), n, p + L0.part_n,
+                                  tot + 1, st);
+        if (s != XPR_OK) return s;
+    }
+    int64_t h_tot[2] = {0, -1};
+    XPR_CUDA_TRY(cudaMemcpyAsync(h_tot, tot, (isect_count ? 2 : 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    XPR_CUDA_TRY(cudaStreamSynchronize(st));
+    const int64_t ns = h_tot[0];
+    if (ns > 0x7fffffffLL || h_tot[1] > 0x7fffffffLL)
+        return fail(XPR_ERR_CAPACITY, "xpr_bin_rows: more than 2^31 - 1 spans or pairs");
+    *n_spans = ns;
+    // without the kept counts the pair total is known only once the spans exist: the span phase
+    // is checked here (its regions do not depend on the pair count) and the pair phase after
+    int64_t ni = isect_count ? h_tot[1] : 0;
+    if (isect_count) *n_isect = ni;
+    const RowsLayout L = rows_layout(n, ns, ni, Wt);
+    if ((isect_count && ni > capacity) || ws_bytes < L.total) return XPR_ERR_CAPACITY;
+    uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
+    uint32_t *skey = reinterpret_cast<uint32_t *>(p + L.skey), *sprim = reinterpret_cast<uint32_t *>(p + L.sprim);
+    int32_t *len = reinterpret_cast<int32_t *>(p + L.len);
+    int32_t *pair0 = reinterpret_cast<int32_t *>(p + L.pair0);
+    const int64_t warps = (n + 31) / 32;
+    span_emit_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, g, slot0, key, prim);
+    XPR_LAUNCH_CHECK("span_emit_kernel");
+    s = launch_sort_u32_bits(key, prim, ns, 256, 0, 8, skey, sprim, nullptr, p + L.sort_ws,
+                             sort_tiles_workspace_bytes(ns, 256), st);
+    if (s != XPR_OK) return s;
+    if (ns > 0) {
+        span_len_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(skey, ns, len);
+        XPR_LAUNCH_CHECK("span_len_kernel");
+    }
+    s = launch_exclusive_scan(len, pair0, ns, p + L.part_s, tot + 2, st);
+    if (s != XPR_OK) return s;
+    if (!isect_count) {
+        XPR_CUDA_TRY(cudaMemcpyAsync(&ni, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        XPR_CUDA_TRY(cudaStreamSynchronize(st));
+        *n_isect = ni;
+        if (ni > capacity || ws_bytes < rows_layout(n, ns, ni, Wt).total) return XPR_ERR_CAPACITY;
+    }
+    const RowsLayout LP = rows_layout(n, ns, ni, Wt);
+    uint32_t *codes = reinterpret_cast<uint32_t *>(p + LP.codes), *pvals = reinterpret_cast<uint32_t *>(p + LP.pvals);
+    const int64_t swarps = (ns + 31) / 32;
+    if (ns > 0) {
+        span_expand_kernel<<<(unsigned)((swarps * 32 + 255) / 256), 256, 0, st>>>(skey, sprim, ns, pair0, ni, codes,
+                                                                                  pvals);
+        XPR_LAUNCH_CHECK("span_expand_kernel");
+    }
+    int2 *by_code = reinterpret_cast<int2 *>(p + LP.by_code);
+    int colbits = 0;
+    while ((1 << colbits) < Wt) ++colbits;
+    s = launch_sort_u32_bits(codes, pvals, ni, Wt * kMaxRowGrid, 7, 7 + colbits, nullptr, vals,
+                             reinterpret_cast<int32_t *>(by_code), p + LP.sort_ws,
+                             sort_tiles_workspace_bytes(ni, Wt * kMaxRowGrid), st);
+    if (s != XPR_OK) return s;
+    permute_ranges_kernel<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(by_code, Wt, Ht,
+                                                                        reinterpret_cast<int2 *>(ranges));
+    XPR_LAUNCH_CHECK("permute_ranges_kernel");
+    return XPR_OK;
+}
+
+}  // namespace xpr

@@ -156,6 +156,21 @@ __host__ __device__ inline Grid make_grid(const XprCamera &cam, const XprConfig 
     return g;
 }
 
+// Tile box of primitive i clamped to the grid (all zero when its tile count is 0); returns its
+// number of tiles (0 for an empty box).
+__device__ __forceinline__ int box_of(const int4 *__restrict__ bbox, const int *__restrict__ tcount, int i,
+                                      const Grid &g, int4 &bb) {
+    bb = make_int4(0, 0, 0, 0);
+    if (tcount[i] <= 0) return 0;
+    bb = bbox[i];
+    bb.x = max(bb.x, 0);  // never leave the tile grid, whatever the caller's boxes say
+    bb.y = max(bb.y, 0);
+    bb.z = min(bb.z, g.Wt);
+    bb.w = min(bb.w, g.Ht);
+    const int w = bb.z - bb.x, h = bb.w - bb.y;
+    return (w > 0 && h > 0) ? w * h : 0;
+}
+
 // Rows of the 32 boxes of a warp (one per lane) are processed flattened over the lanes: with
 // incl = inclusive prefix over lanes of the boxes' row counts, flattened row f belongs to the
 // first lane whose incl exceeds f (a binary search by shuffles; incl is non-decreasing).

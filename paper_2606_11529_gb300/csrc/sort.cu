@@ -885,4 +885,11 @@ int launch_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t
                                 vals_out, ranges, ws, ws_bytes, st);
 }
 
+int launch_sort_u32_bits(const uint32_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
+                         int end_bit, uint32_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws,
+                         size_t ws_bytes, cudaStream_t st) {
+    return radix_sort<uint32_t>(keys_in, vals_in, n, n_tiles, begin_bit, end_bit, keys_out, vals_out, ranges, ws,
+                                ws_bytes, st);
+}
+
 }  // namespace xpr

@@ -120,6 +120,14 @@ int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, c
 int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                     const XprCamera &cam, const XprConfig &cfg, const int32_t *offsets, uint64_t *keys,
                     uint32_t *tiles, uint32_t *vals, cudaStream_t st, int64_t per_view = 0);
+// binning and tile sort by rows (binrows.cu): one view, at most 128 tile columns and rows
+bool bin_rows_supported(const XprCamera &cam, const XprConfig &cfg);
+size_t bin_rows_workspace_bytes(int64_t n, int64_t n_spans, int64_t n_isect, const XprCamera &cam,
+                                const XprConfig &cfg);
+int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *isect_count,
+                    const int32_t *order, int64_t n, const XprCamera &cam, const XprConfig &cfg, int32_t *ranges,
+                    uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *ws, size_t ws_bytes,
+                    cudaStream_t st);
 size_t depth_order_workspace_bytes(int64_t n);
 int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
                        cudaStream_t st, int64_t per_view = 0, int n_views = 1);
@@ -191,6 +199,11 @@ int lookback_selftest(uint32_t *zeroed, int max_polls, cudaStream_t st);  // see
 int launch_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles,
                       uint32_t *tiles_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes,
                       cudaStream_t st);
+// stable sort of 4-byte keys by bits [begin_bit, end_bit) (workspace: sort_tiles_workspace_bytes(n, .));
+// ranges (NULL: none) are those of the whole key values, 0 .. n_tiles - 1
+int launch_sort_u32_bits(const uint32_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
+                         int end_bit, uint32_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws,
+                         size_t ws_bytes, cudaStream_t st);
 
 int launch_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges,
                       const XprCamera &cam, const XprConfig &cfg, float *image, float *t_final, int32_t *n_contrib,

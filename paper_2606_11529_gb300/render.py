@@ -30,10 +30,13 @@ class Workspace:
     xpr_tile_bin) and the transient scratch of xpr_tile_bin / xpr_sort.  Per-frame outputs are
     fresh tensors from PyTorch's caching allocator, so a Frame stays valid after later calls."""
 
-    def __init__(self, fused: bool = False):
+    def __init__(self, fused: bool = False, rows: bool = True):
         self.last_isect = 0
+        self.last_spans = 0
         self.bufs = {}
         self.fused = fused  # xpr_bin_sorted (True) or xpr_tile_bin + xpr_sort_tiles (False)
+        # with fused False: xpr_bin_rows where the grid allows it (True), else the key path
+        self.rows = rows
         self.sh_events = None  # set by a caller whose SH copy is still in flight (consumed by one forward)
         # set by a caller whose inputs are still in pinned host memory: (host (mu, scale, quat,
         # opacity, sh), copy stream); the forward brings them over itself (consumed by one forward)
@@ -128,9 +131,11 @@ def is_lp(cfg) -> bool:
 def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None = None, stream=None,
                   timers=None, fused: bool = False, keep_sorted_tiles: bool = False, sh_events=None,
                   render: bool = True, host_inputs=None) -> Frame:
-    """The forward stages, each one C-ABI call: project, depth order, then either the key path
-    (xpr_tile_bin emitting u32 tile ids in depth order + xpr_sort_tiles, the default) or the fused
-    bin + sort (xpr_bin_sorted), then render.  Both give the same sorted lists bit for bit.
+    """The forward stages, each one C-ABI call: project, depth order, then the binning and tile sort:
+    by tile rows (xpr_bin_rows, the default where the grid has at most 128 x 128 tiles), the key
+    path (xpr_tile_bin emitting u32 tile ids in depth order + xpr_sort_tiles: larger grids, LinPrim,
+    or keep_sorted_tiles) or the fused bin + sort (xpr_bin_sorted); then render.  All give the same
+    sorted lists bit for bit.
     sh_events: events of an SH copy still in flight; then the projection runs without colours,
     and the stream waits for the events just before xpr_project_color fills them in.
     host_inputs: (pinned host (mu, scale, quat, opacity, sh), copy stream): the parameters are brought
@@ -147,6 +152,7 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     ws = ws or Workspace()
     ut, lp = is_ut(cfg), is_lp(cfg)
     fused = fused and not lp  # LinPrim is binned by xpr_tile_bin_lp
+    rows = not fused and not keep_sorted_tiles and getattr(ws, "rows", True) and B.bin_rows_ok(cam, cfg)
     sd = None
     deferred = sh_events is not None and not (ut or lp)
     from_host = host_inputs is not None and not (ut or lp)
@@ -189,6 +195,16 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
         ranges, vs, I = B.xpr_bin_sorted(rec, bbox, tc, order, n, ccam, ccfg, capacity=cap, workspace=bs_ws,
                                          stream=stream)
         tm.stop("bin_sort", stream)
+        offsets = tiles = vals = ks = None
+    elif rows:
+        need = B.bin_rows_workspace_bytes(n, int(ws.last_spans * 1.25) + 1024, cap, ccam, ccfg)
+        rows_ws = ws.scratch("rows", need, dev)
+        tm.start("bin_sort", stream)
+        ranges, vs, I, S, used = B.xpr_bin_rows(rec, bbox, tc, order, n, ccam, ccfg, isect_count=cnt, capacity=cap,
+                                                workspace=rows_ws, stream=stream)
+        tm.stop("bin_sort", stream)
+        ws.bufs["rows"] = used
+        ws.last_spans = S
         offsets = tiles = vals = ks = None
     else:
         bin_ws = ws.scratch("bin", L.xpr_tile_bin_workspace(n), dev)

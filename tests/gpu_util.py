@@ -78,3 +78,25 @@ def check_band(got, ref, mask=None, max_frac=1e-4, tol=IMG_TOL, what=""):
         excess = err[bad] - (ref["jump"][bad] + tol)
         assert excess.max() <= 0, f"{what}: band pixel beyond its jump bound by {excess.max():.3e}"
     return ok
+
+
+def tile_lists_row_major(vals, ranges):
+    """The sorted record indices re-gathered tile by tile in row-major tile order, and the list
+    lengths (layout-independent: the ranges locate each tile's segment)."""
+    import torch
+    v = torch.as_tensor(vals).cuda().to(torch.int64)
+    r = torch.as_tensor(ranges).cuda().to(torch.int64)
+    lens = r[:, 1] - r[:, 0]
+    total = int(lens.sum().item())
+    starts_out = torch.cumsum(lens, 0) - lens
+    idx = torch.repeat_interleave(r[:, 0] - starts_out, lens) + torch.arange(total, device="cuda")
+    return v[idx], lens
+
+
+def assert_same_tile_lists(v_a, r_a, v_b, r_b):
+    """Every tile's list (record indices in order) is the same in both (vals, ranges) pairs."""
+    import torch
+    a, la = tile_lists_row_major(v_a, r_a)
+    b, lb = tile_lists_row_major(v_b, r_b)
+    assert torch.equal(la, lb), "tile list lengths differ"
+    assert torch.equal(a, b), "tile lists differ"

@@ -57,7 +57,7 @@ def test_bin_sorted_equals_key_path_on_gpu_records(tile):
     cfg = scenes.RenderConfig(tile_w=tile, tile_h=tile, sh_degree=1)
     P = R.scene_to_device(sc)
     a = R.forward_frame(*P, cam, cfg, fused=True)
-    b = R.forward_frame(*P, cam, cfg, fused=False)
+    b = R.forward_frame(*P, cam, cfg, R.Workspace(rows=False), fused=False)
     assert a.n_isect == b.n_isect > 100_000
     assert torch.equal(a.vals_sorted, b.vals_sorted) and torch.equal(a.ranges, b.ranges)
     assert torch.equal(a.image, b.image)
