@@ -444,16 +444,17 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
  * every primitive one span of kept tile columns per row of its box; the spans
  * (about seven pairs each on the headline workload) are sorted by row in depth
  * order, expanded into pairs grouped by row, and one stable pass over the
- * pairs' column groups them by tile.  The result is bit-identical to
+ * pairs' column groups them by tile.  Every tile's list is bit-identical to
  * xpr_tile_bin in the same order followed by xpr_sort_tiles: the same kept
- * pairs (same FP32 cull), each tile's list in emission order.
+ * pairs (same FP32 cull), each tile's list in emission order; the tiles'
+ * segments lie in column-major tile order (the ranges locate them).
  *   rec, bbox, tile_count: from xpr_project (n records of one view);
  *   isect_count[n] (device, may be NULL): the kept tile counts from
  *     xpr_project; with them the call reads both totals back at once;
  *   order[n]: the emission order, from xpr_depth_order;
  *   ranges[T,2] (int32, device): OVERWRITTEN, [0, 0) for a tile with no pairs;
- *   vals[capacity] (u32, device): record indices, tile-major, in emission order
- *     within a tile;
+ *   vals[capacity] (u32, device): record indices, each tile's list contiguous
+ *     and in emission order;
  *   *n_isect, *n_spans (HOST): the kept pairs I and the span slots S (one per
  *     row of every box).  If I > capacity or workspace_bytes is below
  *     xpr_bin_rows_workspace(n, S, I, cam, cfg), the call returns
