@@ -378,12 +378,15 @@ int xpr_project_bwd_items(const XprPrims *prims, int64_t n_prims, const XprCamer
 
 /* xpr_forward_items: the whole forward of a multi-scene batch in one call (the
  * serving runtime's entry point): the items' projection with the exact
- * kept-tile counts, xpr_depth_order_items, the offsets scan and the emission
- * of (global tile id, record) pairs in depth order (as xpr_tile_bin, each
- * record on its item's grid), xpr_sort_tiles over all items' tiles,
- * xpr_tile_worklist and xpr_render_fwd_items with the work list (one block
- * per tile for a single item; the same lists and images as the staged
- * calls), every intermediate carved from one
+ * kept-tile counts, xpr_depth_order_items, the binning and tile sort by rows
+ * of xpr_bin_rows_items when every item's grid has at most 128 x 128 tiles
+ * (else, or when the span slots outgrow the workspace's room for
+ * capacity / 2 + R of them, the offsets scan, the emission of (global tile
+ * id, record) pairs in depth order as xpr_tile_bin, and xpr_sort_tiles over
+ * all items' tiles: the same lists either way), xpr_tile_worklist and
+ * xpr_render_fwd_items with the work list (one block per tile for a single
+ * item; the same lists and images as the staged calls), every intermediate
+ * carved from one
  * caller-owned workspace
  * (device, 256-byte aligned) of xpr_forward_items_workspace(cams, items, K,
  * cfg, capacity) bytes, where capacity is the room for intersection pairs.
@@ -472,6 +475,35 @@ int xpr_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tile_coun
                  const int32_t *order, int64_t n, const XprCamera *cam, const XprConfig *cfg, int32_t *ranges,
                  uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *workspace,
                  size_t workspace_bytes, void *stream);
+
+/* xpr_bin_rows_views / xpr_bin_rows_items: xpr_bin_rows over a batch (the
+ * multi-view and multi-scene forms, Sec. 4.3), every grid at most 128 x 128
+ * tiles: each view's or item's lists are bit-identical to xpr_tile_bin_views
+ * (or the items' emission) followed by xpr_sort_tiles over all S tiles.  The
+ * spans carry their item, the pass over the pairs groups them by (column, row,
+ * item), and the tiles' segments lie in that order (the ranges locate them).
+ *   _views: V = n_views (1..16) views of n primitives, records view-major
+ *     (rec[V*n,12] ... from xpr_project_views, isect_count[V*n] or NULL,
+ *     order[V*n] from xpr_depth_order_views); ranges[V*T,2];
+ *   _items: K items (1..16; cams and items HOST arrays as in
+ *     xpr_project_items), R records from xpr_project_items (isect_count[R] or
+ *     NULL), order[R] from xpr_depth_order_items; ranges[S,2], S = the last
+ *     tile_offset + its tiles.
+ * Counts, capacity protocol, synchronisation and errors as xpr_bin_rows (the
+ * workspace functions take the same batch description; 0 for invalid
+ * arguments). */
+size_t xpr_bin_rows_views_workspace(int64_t n, int32_t n_views, int64_t n_spans, int64_t n_isect,
+                                    const XprCamera *cam, const XprConfig *cfg);
+int xpr_bin_rows_views(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                       const int32_t *order, int64_t n, int32_t n_views, const XprCamera *cam, const XprConfig *cfg,
+                       int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans,
+                       void *workspace, size_t workspace_bytes, void *stream);
+size_t xpr_bin_rows_items_workspace(const XprCamera *cams, const XprItem *items, int32_t n_items,
+                                    const XprConfig *cfg, int64_t n_spans, int64_t n_isect);
+int xpr_bin_rows_items(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                       const int32_t *order, const XprCamera *cams, const XprItem *items, int32_t n_items,
+                       const XprConfig *cfg, int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                       int64_t *n_spans, void *workspace, size_t workspace_bytes, void *stream);
 
 /* ---- Rendered features (3DGS) ----------------------------------------------------
  * The "rendered feature" class of the design space (depth, semantics): channel c of

@@ -64,7 +64,11 @@ class ViewsWorkspace:
 
 
 def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | None = None, persistent=True,
-                  stream=None, fused=False) -> ViewsFrame:
+                  stream=None, fused=False, rows=True) -> ViewsFrame:
+    """Projection, depth order, binning and tile sort, work list and render of V views.  The binning
+    and tile sort is the rows form (`xpr_bin_rows_views`) where every view's grid has at most 128 x
+    128 tiles (``rows``), else the fused counting sort (``fused``) or the key path (tile ids, then
+    the tile sort); every form gives the same lists."""
     L = B.load()
     ws = ws or ViewsWorkspace()
     n, V = mu.shape[0], len(cams)
@@ -74,7 +78,8 @@ def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | 
         if (c.width, c.height) != (cam0.width, cam0.height):
             raise ValueError("all views of one batch must share the image size")
     ccfg = B.make_config(cfg)
-    fused = fused and B.binsort_ok(cam0, cfg, V)
+    rows = rows and B.bin_rows_ok(cam0, cfg)
+    fused = fused and not rows and B.binsort_ok(cam0, cfg, V)
     ut = _is_ut(cfg)
     sd = None
     if ut:
@@ -88,7 +93,11 @@ def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | 
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
     Wt, Ht = B.tiles_of(cam0, cfg)
     nt = V * Wt * Ht
-    if fused:
+    if rows:
+        ranges, vs, I, _, ws.bufs["rows"] = B.xpr_bin_rows_views(rec, bbox, tc, order, n, V, cam0, ccfg,
+                                                                 isect_count=cnt, capacity=cap,
+                                                                 workspace=ws.bufs.get("rows"), stream=stream)
+    elif fused:
         ranges, vs, I = B.xpr_bin_sorted(rec, bbox, tc, order, n, cam0, ccfg, n_views=V, capacity=cap,
                                          workspace=ws.scratch("binsort", B.bin_sorted_workspace_bytes(
                                              n, V, cam0, ccfg), dev), stream=stream)
@@ -273,9 +282,11 @@ class SceneSet:
 
 
 def forward_items(mu, scale, quat, opacity, sh, layout, cfg, ws: ViewsWorkspace | None = None, persistent=True,
-                  stream=None) -> ItemsFrame:
+                  stream=None, rows=True) -> ItemsFrame:
     """K (scene, camera) items of uneven scene and image sizes through one launch per stage (3DGS):
-    projection, depth order, fused bin + sort, work list over every item's tiles, render."""
+    projection, depth order, binning and tile sort (by rows where every item's grid has at most 128
+    x 128 tiles and ``rows``, else the fused counting sort: the same lists), work list over every
+    item's tiles, render."""
     L = B.load()
     ws = ws or ViewsWorkspace()
     dev = mu.device
@@ -284,9 +295,13 @@ def forward_items(mu, scale, quat, opacity, sh, layout, cfg, ws: ViewsWorkspace 
     order = B.xpr_depth_order_items(rec, tc, layout, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(
         layout.R), dev), stream=stream)
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
-    ranges, vs, I = B.xpr_bin_sorted_items(rec, bbox, tc, order, layout, ccfg, capacity=cap,
-                                           workspace=ws.scratch("binsort", B.bin_sorted_items_workspace_bytes(
-                                               layout, ccfg), dev), stream=stream)
+    if rows and B.bin_rows_items_ok(layout, cfg):
+        ranges, vs, I, _, ws.bufs["rows"] = B.xpr_bin_rows_items(rec, bbox, tc, order, layout, ccfg, capacity=cap,
+                                                                 workspace=ws.bufs.get("rows"), stream=stream)
+    else:
+        ranges, vs, I = B.xpr_bin_sorted_items(rec, bbox, tc, order, layout, ccfg, capacity=cap,
+                                               workspace=ws.scratch("binsort", B.bin_sorted_items_workspace_bytes(
+                                                   layout, ccfg), dev), stream=stream)
     ws.last_isect = I
     wl = B.xpr_tile_worklist(ranges, workspace=ws.scratch("wl", L.xpr_tile_worklist_workspace(layout.S), dev),
                              stream=stream) if persistent else None

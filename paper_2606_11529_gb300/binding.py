@@ -92,6 +92,16 @@ SIGNATURES = {
     "xpr_bin_rows_workspace": (c_sz, [c_i64, c_i64, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig)]),
     "xpr_bin_rows": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(XprCamera), ctypes.POINTER(XprConfig),
                              c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
+    "xpr_bin_rows_views_workspace": (c_sz, [c_i64, c_i32, c_i64, c_i64, ctypes.POINTER(XprCamera),
+                                            ctypes.POINTER(XprConfig)]),
+    "xpr_bin_rows_views": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(XprCamera),
+                                   ctypes.POINTER(XprConfig), c_vp, c_vp, c_i64, ctypes.POINTER(c_i64),
+                                   ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
+    "xpr_bin_rows_items_workspace": (c_sz, [ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem), c_i32,
+                                            ctypes.POINTER(XprConfig), c_i64, c_i64]),
+    "xpr_bin_rows_items": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, ctypes.POINTER(XprCamera), ctypes.POINTER(XprItem),
+                                   c_i32, ctypes.POINTER(XprConfig), c_vp, c_vp, c_i64, ctypes.POINTER(c_i64),
+                                   ctypes.POINTER(c_i64), c_vp, c_sz, c_vp]),
     "xpr_bin_sorted": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(XprCamera),
                                ctypes.POINTER(XprConfig), c_vp, c_vp, c_i64, ctypes.POINTER(c_i64), c_vp, c_sz,
                                c_vp]),
@@ -559,14 +569,57 @@ def xpr_bin_sorted(rec, bbox, tile_count, order, n, cam, cfg, n_views=1, capacit
 
 
 def bin_rows_ok(cam, cfg) -> bool:
-    """xpr_bin_rows takes one view of at most 128 x 128 tiles (3DGS and 3DGUT)."""
+    """The rows binning takes grids of at most 128 x 128 tiles (3DGS and 3DGUT; one view, the views
+    of one camera, or items whose every camera fits)."""
     Wt, Ht = tiles_of(cam, cfg)
     return Wt <= 128 and Ht <= 128 and int(getattr(cfg, "method", XPR_METHOD_3DGS)) != XPR_METHOD_LINPRIM
+
+
+def bin_rows_items_ok(layout, cfg) -> bool:
+    return all(bin_rows_ok(c, cfg) for c in layout.cams)
 
 
 def bin_rows_workspace_bytes(n, n_spans, n_isect, cam, cfg):
     c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
     return int(load().xpr_bin_rows_workspace(int(n), int(n_spans), int(n_isect), ctypes.byref(c), ctypes.byref(g)))
+
+
+def bin_rows_views_workspace_bytes(n, n_views, n_spans, n_isect, cam, cfg):
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    return int(load().xpr_bin_rows_views_workspace(int(n), int(n_views), int(n_spans), int(n_isect), ctypes.byref(c),
+                                                   ctypes.byref(g)))
+
+
+def bin_rows_items_workspace_bytes(layout, n_spans, n_isect, cfg):
+    g = _as_c(cfg, XprConfig)
+    return int(load().xpr_bin_rows_items_workspace(layout.carr, layout.arr, layout.K, ctypes.byref(g), int(n_spans),
+                                                   int(n_isect)))
+
+
+def _bin_rows_retry(name, call, need, n_tiles, dev, cap, workspace):
+    """The capacity protocol of the rows binning calls: call(ranges, vals, workspace, got_i, got_s) runs
+    the C entry, need(S, I) gives the workspace it wants.  On XPR_ERR_CAPACITY vals and the workspace
+    are re-allocated to the reported counts and the call repeated; returns (ranges, vals[:I], I, S,
+    workspace)."""
+    ranges = torch.empty((max(n_tiles, 1), 2), dtype=torch.int32, device=dev)[:n_tiles]
+    vals = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    n0 = need(0, 0)
+    if workspace is None or workspace.numel() < n0:
+        workspace = torch.empty(max(n0, 256), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        got_i, got_s = c_i64(0), c_i64(0)
+        s = call(ranges, vals, workspace, got_i, got_s)
+        if s == XPR_ERR_CAPACITY and got_i.value <= 0x7FFFFFFF and got_s.value <= 0x7FFFFFFF:
+            if got_i.value > vals.numel():
+                vals = torch.empty(got_i.value, dtype=torch.int32, device=dev)
+            n1 = need(got_s.value, got_i.value)
+            if workspace.numel() < n1:
+                workspace = torch.empty(n1, dtype=torch.uint8, device=dev)
+            continue
+        _check(s, name)
+        I = int(got_i.value)
+        return ranges, vals[:I], I, int(got_s.value), workspace
+    raise XprError(XPR_ERR_CAPACITY, name, "capacity retry failed")
 
 
 def xpr_bin_rows(rec, bbox, tile_count, order, n, cam, cfg, isect_count=None, capacity=None, workspace=None,
@@ -576,32 +629,54 @@ def xpr_bin_rows(rec, bbox, tile_count, order, n, cam, cfg, isect_count=None, ca
     scratch.  On XPR_ERR_CAPACITY either is re-allocated to the reported counts and the call repeated;
     the workspace returned is the one used (keep it for the next call)."""
     L = load()
-    dev = rec.device
     c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
     Wt, Ht = tiles_of(cam, cfg)
-    ranges = torch.empty((Wt * Ht, 2), dtype=torch.int32, device=dev)
     cap = int(capacity) if capacity is not None else max(4 * n, 1024)
-    vals = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
-    need = bin_rows_workspace_bytes(n, 0, 0, cam, cfg)
-    if workspace is None or workspace.numel() < need:
-        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
-    for _ in range(3):
-        got_i, got_s = c_i64(0), c_i64(0)
-        s = L.xpr_bin_rows(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _ptr(order), n,
-                           ctypes.byref(c), ctypes.byref(g), _ptr(ranges), _ptr(vals), vals.numel(),
-                           ctypes.byref(got_i), ctypes.byref(got_s), _ptr(workspace), workspace.numel(),
-                           _stream(stream))
-        if s == XPR_ERR_CAPACITY and got_i.value <= 0x7FFFFFFF and got_s.value <= 0x7FFFFFFF:
-            if got_i.value > vals.numel():
-                vals = torch.empty(got_i.value, dtype=torch.int32, device=dev)
-            need = bin_rows_workspace_bytes(n, got_s.value, got_i.value, cam, cfg)
-            if workspace.numel() < need:
-                workspace = torch.empty(need, dtype=torch.uint8, device=dev)
-            continue
-        _check(s, "xpr_bin_rows")
-        I = int(got_i.value)
-        return ranges, vals[:I], I, int(got_s.value), workspace
-    raise XprError(XPR_ERR_CAPACITY, "xpr_bin_rows", "capacity retry failed")
+
+    def call(ranges, vals, ws, gi, gs):
+        return L.xpr_bin_rows(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _ptr(order), n,
+                              ctypes.byref(c), ctypes.byref(g), _ptr(ranges), _ptr(vals), vals.numel(),
+                              ctypes.byref(gi), ctypes.byref(gs), _ptr(ws), ws.numel(), _stream(stream))
+
+    return _bin_rows_retry("xpr_bin_rows", call, lambda S, I: bin_rows_workspace_bytes(n, S, I, cam, cfg), Wt * Ht,
+                           rec.device, cap, workspace)
+
+
+def xpr_bin_rows_views(rec, bbox, tile_count, order, n, n_views, cam, cfg, isect_count=None, capacity=None,
+                       workspace=None, stream=None):
+    """xpr_bin_rows over V views of one camera (records view-major): ranges[V*T,2], the rest as
+    xpr_bin_rows."""
+    L = load()
+    c, g = _as_c(cam, XprCamera), _as_c(cfg, XprConfig)
+    Wt, Ht = tiles_of(cam, cfg)
+    cap = int(capacity) if capacity is not None else max(4 * n * n_views, 1024)
+
+    def call(ranges, vals, ws, gi, gs):
+        return L.xpr_bin_rows_views(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _ptr(order), n,
+                                    n_views, ctypes.byref(c), ctypes.byref(g), _ptr(ranges), _ptr(vals), vals.numel(),
+                                    ctypes.byref(gi), ctypes.byref(gs), _ptr(ws), ws.numel(), _stream(stream))
+
+    return _bin_rows_retry("xpr_bin_rows_views", call,
+                           lambda S, I: bin_rows_views_workspace_bytes(n, n_views, S, I, cam, cfg),
+                           n_views * Wt * Ht, rec.device, cap, workspace)
+
+
+def xpr_bin_rows_items(rec, bbox, tile_count, order, layout, cfg, isect_count=None, capacity=None, workspace=None,
+                       stream=None):
+    """xpr_bin_rows over the items of a multi-scene batch: ranges[S,2] over all items' tiles, the rest
+    as xpr_bin_rows."""
+    L = load()
+    g = _as_c(cfg, XprConfig)
+    cap = int(capacity) if capacity is not None else max(4 * layout.R, 1024)
+
+    def call(ranges, vals, ws, gi, gs):
+        return L.xpr_bin_rows_items(_ptr(rec), _ptr(bbox), _ptr(tile_count), _ptr(isect_count), _ptr(order),
+                                    layout.carr, layout.arr, layout.K, ctypes.byref(g), _ptr(ranges), _ptr(vals),
+                                    vals.numel(), ctypes.byref(gi), ctypes.byref(gs), _ptr(ws), ws.numel(),
+                                    _stream(stream))
+
+    return _bin_rows_retry("xpr_bin_rows_items", call, lambda S, I: bin_rows_items_workspace_bytes(layout, S, I, g),
+                           layout.S, rec.device, cap, workspace)
 
 
 def xpr_tile_worklist(ranges, workspace=None, stream=None):

@@ -598,20 +598,25 @@ int xpr_project_bwd_items(const XprPrims *prims, int64_t n_prims, const XprCamer
     return launch_project_bwd_items(*prims, n_prims, cams, items, n_items, *cfg, d_rec, *d_prims, as_stream(stream));
 }
 
-// Workspace layout of xpr_forward_items (every part 256-byte aligned).
+// Workspace layout of xpr_forward_items (every part 256-byte aligned).  The binning's scratch is
+// one region: the rows binning's workspace with room for cap / 2 + R span slots (the spans hold
+// from about three to nine pairs each on the serving workloads), else, or when the spans outgrow
+// that room, the key path's offsets, scan partials, tile ids, values and sort scratch.
 struct FwdItemsWs {
-    size_t rec, bbox, tc, isect, order, depth, offsets, scan, tiles, vals_in, vals, sort, ranges, worklist, wl_ws,
-        counter, total;
+    size_t rec, bbox, tc, isect, order, depth, vals, ranges, worklist, wl_ws, counter, bin, total;
+    size_t bin_bytes;
+    size_t k_offsets, k_scan, k_tiles, k_vals_in, k_sort;  // the key path, inside the bin region
 };
 
-static FwdItemsWs fwd_items_layout(int64_t R, int64_t S, int64_t capacity) {
-    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+static FwdItemsWs fwd_items_layout(int64_t R, int64_t S, int64_t capacity, const RowItems *rows) {
     const size_t cap = (size_t)std::max<int64_t>(capacity, 1);
     FwdItemsWs w;
     size_t o = 0;
     auto take = [&](size_t &field, size_t bytes) {
         field = o;
-        o += up(bytes);
+        o += up256(bytes);
     };
     take(w.rec, (size_t)R * XPR_REC_FLOATS * 4);
     take(w.bbox, (size_t)R * 16);
@@ -619,16 +624,25 @@ static FwdItemsWs fwd_items_layout(int64_t R, int64_t S, int64_t capacity) {
     take(w.isect, (size_t)R * 4);
     take(w.order, (size_t)R * 4);
     take(w.depth, depth_order_workspace_bytes(R));
-    take(w.offsets, ((size_t)R + 1) * 4);
-    take(w.scan, scan_partials_bytes(R));
-    take(w.tiles, cap * 4);
-    take(w.vals_in, cap * 4);
     take(w.vals, cap * 4);
-    take(w.sort, sort_tiles_workspace_bytes((int64_t)cap, (int32_t)S));
     take(w.ranges, (size_t)S * 8);
     take(w.worklist, (size_t)S * 4);
     take(w.wl_ws, worklist_workspace_bytes((int32_t)S));
     take(w.counter, 256);
+    size_t k = 0;
+    w.k_offsets = k;
+    k += up256(((size_t)R + 1) * 4);
+    w.k_scan = k;
+    k += up256(scan_partials_bytes(R));
+    w.k_tiles = k;
+    k += up256(cap * 4);
+    w.k_vals_in = k;
+    k += up256(cap * 4);
+    w.k_sort = k;
+    k += up256(sort_tiles_workspace_bytes((int64_t)cap, (int32_t)S));
+    if (rows) k = std::max(k, bin_rows_workspace_bytes(R, (int64_t)cap / 2 + R, (int64_t)cap, *rows));
+    w.bin_bytes = k;
+    take(w.bin, k);
     w.total = o;
     return w;
 }
@@ -640,7 +654,8 @@ size_t xpr_forward_items_workspace(const XprCamera *cams, const XprItem *items, 
     if (!cfg || capacity < 0 || capacity > 0x7fffffffLL ||
         make_item_table(cams, items, n_items, *cfg, t, &R, "xpr_forward_items_workspace") != XPR_OK)
         return 0;
-    return fwd_items_layout(R, t.tile0[n_items], capacity).total;
+    const RowItems rt = row_items_items(cams, items, n_items, *cfg);
+    return fwd_items_layout(R, t.tile0[n_items], capacity, bin_rows_supported(rt) ? &rt : nullptr).total;
 }
 
 int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprItem *items, int32_t n_items,
@@ -661,7 +676,9 @@ int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprIte
         return fail(XPR_ERR_INVALID, "xpr_forward_items: NULL primitive array");
     if (R > 0 && !aligned(prims->quat, 16)) return fail(XPR_ERR_INVALID, "xpr_forward_items: quat alignment");
     if (!aligned(workspace, 256)) return fail(XPR_ERR_INVALID, "xpr_forward_items: workspace must be 256-byte aligned");
-    const FwdItemsWs L = fwd_items_layout(R, S, capacity);
+    const RowItems rt = row_items_items(cams, items, n_items, *cfg);
+    const bool by_rows = bin_rows_supported(rt);
+    const FwdItemsWs L = fwd_items_layout(R, S, capacity, by_rows ? &rt : nullptr);
     if (ws_bytes < L.total)
         return fail(XPR_ERR_INVALID, "xpr_forward_items: workspace %zu < %zu bytes", ws_bytes, L.total);
     char *w = reinterpret_cast<char *>(workspace);
@@ -670,40 +687,60 @@ int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprIte
     int32_t *tc = reinterpret_cast<int32_t *>(w + L.tc);
     int32_t *isect = reinterpret_cast<int32_t *>(w + L.isect);
     int32_t *order = reinterpret_cast<int32_t *>(w + L.order);
-    int32_t *offsets = reinterpret_cast<int32_t *>(w + L.offsets);
-    uint32_t *tiles = reinterpret_cast<uint32_t *>(w + L.tiles);
-    uint32_t *vals_in = reinterpret_cast<uint32_t *>(w + L.vals_in);
     uint32_t *vals = reinterpret_cast<uint32_t *>(w + L.vals);
     int32_t *ranges = reinterpret_cast<int32_t *>(w + L.ranges);
     int32_t *wl = reinterpret_cast<int32_t *>(w + L.worklist);
     int32_t *counter = reinterpret_cast<int32_t *>(w + L.counter);
+    char *bin = w + L.bin;
     cudaStream_t st = as_stream(stream);
     *n_isect = 0;
     int64_t total = 0;
+    bool binned = false;
     if (R > 0) {
-        // projection with the exact kept-tile counts, depth order per item, offsets in that order
+        // projection with the exact kept-tile counts, depth order per item
         if ((s = launch_project_items(*prims, cams, items, n_items, *cfg, rec, bbox, tc, st, isect))) return s;
         if ((s = launch_depth_order_items(rec, tc, items, n_items, order, w + L.depth,
                                           depth_order_workspace_bytes(R), st)))
             return s;
-        if ((s = launch_exclusive_scan(isect, offsets, R, w + L.scan, nullptr, st, order))) return s;
-        XPR_CUDA_TRY(cudaMemcpyAsync(&total, scan_total_ptr(w + L.scan, R), sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                     st));
-        XPR_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    *n_isect = total;
-    if (total > 0x7fffffffLL)
-        return fail(XPR_ERR_CAPACITY, "xpr_forward_items: %lld intersections exceed 2^31-1", (long long)total);
-    if (total > capacity)
-        return fail(XPR_ERR_CAPACITY, "xpr_forward_items: %lld intersections > capacity %lld", (long long)total,
-                    (long long)capacity);
-    // pairs in depth order with global tile ids, then a stable sort by tile (the key path)
-    if (total > 0 &&
-        (s = launch_bin_emit_items(rec, bbox, tc, order, cams, items, n_items, *cfg, offsets, tiles, vals_in, st)))
-        return s;
-    if ((s = launch_sort_tiles(tiles, vals_in, total, (int32_t)S, nullptr, vals, ranges, w + L.sort,
-                               sort_tiles_workspace_bytes(std::max<int64_t>(capacity, 1), (int32_t)S), st)))
-        return s;
+    if (R > 0 && by_rows) {
+        // binning and tile sort by rows (one synchronisation: the span and pair totals)
+        int64_t spans = 0;
+        s = launch_bin_rows(rec, bbox, tc, isect, order, R, rt, *cfg, ranges, vals, capacity, &total, &spans, bin,
+                            L.bin_bytes, st);
+        *n_isect = total;
+        if (s == XPR_OK) binned = true;
+        else if (s != XPR_ERR_CAPACITY) return s;
+        else if (total > capacity)
+            return fail(XPR_ERR_CAPACITY, "xpr_forward_items: %lld intersections > capacity %lld", (long long)total,
+                        (long long)capacity);
+        // else the spans outgrew their room: the key path below gives the same lists
+    }
+    if (!binned) {
+        int32_t *offsets = reinterpret_cast<int32_t *>(bin + L.k_offsets);
+        uint32_t *tiles = reinterpret_cast<uint32_t *>(bin + L.k_tiles);
+        uint32_t *vals_in = reinterpret_cast<uint32_t *>(bin + L.k_vals_in);
+        total = 0;
+        if (R > 0) {
+            if ((s = launch_exclusive_scan(isect, offsets, R, bin + L.k_scan, nullptr, st, order))) return s;
+            XPR_CUDA_TRY(cudaMemcpyAsync(&total, scan_total_ptr(bin + L.k_scan, R), sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, st));
+            XPR_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        *n_isect = total;
+        if (total > 0x7fffffffLL)
+            return fail(XPR_ERR_CAPACITY, "xpr_forward_items: %lld intersections exceed 2^31-1", (long long)total);
+        if (total > capacity)
+            return fail(XPR_ERR_CAPACITY, "xpr_forward_items: %lld intersections > capacity %lld", (long long)total,
+                        (long long)capacity);
+        // pairs in depth order with global tile ids, then a stable sort by tile (the key path)
+        if (total > 0 &&
+            (s = launch_bin_emit_items(rec, bbox, tc, order, cams, items, n_items, *cfg, offsets, tiles, vals_in, st)))
+            return s;
+        if ((s = launch_sort_tiles(tiles, vals_in, total, (int32_t)S, nullptr, vals, ranges, bin + L.k_sort,
+                                   sort_tiles_workspace_bytes(std::max<int64_t>(capacity, 1), (int32_t)S), st)))
+            return s;
+    }
     if (n_items == 1)  // one item: one block per tile (nothing to balance across items)
         return launch_render_fwd_items(rec, R, vals, ranges, t, *cfg, image, t_final, n_contrib, nullptr, nullptr,
                                        st);
@@ -754,10 +791,25 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
 
 size_t xpr_bin_rows_workspace(int64_t n, int64_t n_spans, int64_t n_isect, const XprCamera *cam,
                               const XprConfig *cfg) {
-    if (validate_camera_config(cam, cfg) != XPR_OK || n < 0 || n_spans < 0 || n_isect < 0 ||
-        !bin_rows_supported(*cam, *cfg))
-        return 0;
-    return bin_rows_workspace_bytes(n, n_spans, n_isect, *cam, *cfg);
+    return xpr_bin_rows_views_workspace(n, 1, n_spans, n_isect, cam, cfg);
+}
+
+// Shared argument checks and launch of the three rows binning entries (n_rec records, table t).
+static int bin_rows_call(const char *fn, const float *rec, const int32_t *bbox, const int32_t *tile_count,
+                         const int32_t *isect_count, const int32_t *order, int64_t n_rec, const RowItems &t,
+                         const XprConfig *cfg, int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                         int64_t *n_spans, void *workspace, size_t ws_bytes, void *stream) {
+    if (cfg->method == XPR_METHOD_LINPRIM) return fail(XPR_ERR_INVALID, "%s: LinPrim is binned by xpr_tile_bin_lp", fn);
+    if (!bin_rows_supported(t))
+        return fail(XPR_ERR_INVALID, "%s: a tile grid has more than 128 tile columns or rows", fn);
+    if (!ranges || !n_isect || !n_spans) return fail(XPR_ERR_INVALID, "%s: NULL ranges, n_isect or n_spans", fn);
+    if (capacity < 0) return fail(XPR_ERR_INVALID, "%s: negative capacity", fn);
+    if (n_rec > 0 && (!rec || !bbox || !tile_count || !order || !workspace || (capacity > 0 && !vals)))
+        return fail(XPR_ERR_INVALID, "%s: NULL pointer", fn);
+    if (n_rec > 0 && (!aligned(rec, 16) || !aligned(bbox, 16) || !aligned(workspace, 256)))
+        return fail(XPR_ERR_INVALID, "%s: rec/bbox must be 16-byte and workspace 256-byte aligned", fn);
+    return launch_bin_rows(rec, bbox, tile_count, isect_count, order, n_rec, t, *cfg, ranges, vals, capacity, n_isect,
+                           n_spans, workspace, ws_bytes, as_stream(stream));
 }
 
 int xpr_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
@@ -767,16 +819,57 @@ int xpr_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tile_coun
     int s = validate_camera_config(cam, cfg);
     if (s) return s;
     if ((s = check_n(n))) return s;
-    if (cfg->method == XPR_METHOD_LINPRIM)
-        return fail(XPR_ERR_INVALID, "xpr_bin_rows: LinPrim is binned by xpr_tile_bin_lp");
-    if (!ranges || !n_isect || !n_spans) return fail(XPR_ERR_INVALID, "xpr_bin_rows: NULL ranges, n_isect or n_spans");
-    if (capacity < 0) return fail(XPR_ERR_INVALID, "xpr_bin_rows: negative capacity");
-    if (n > 0 && (!rec || !bbox || !tile_count || !order || !workspace || (capacity > 0 && !vals)))
-        return fail(XPR_ERR_INVALID, "xpr_bin_rows: NULL pointer");
-    if (n > 0 && (!aligned(rec, 16) || !aligned(bbox, 16) || !aligned(workspace, 256)))
-        return fail(XPR_ERR_INVALID, "xpr_bin_rows: rec/bbox must be 16-byte and workspace 256-byte aligned");
-    return launch_bin_rows(rec, bbox, tile_count, isect_count, order, n, *cam, *cfg, ranges, vals, capacity, n_isect,
-                           n_spans, workspace, ws_bytes, as_stream(stream));
+    return bin_rows_call("xpr_bin_rows", rec, bbox, tile_count, isect_count, order, n,
+                         row_items_views(*cam, *cfg, n, 1), cfg, ranges, vals, capacity, n_isect, n_spans, workspace,
+                         ws_bytes, stream);
+}
+
+size_t xpr_bin_rows_views_workspace(int64_t n, int32_t n_views, int64_t n_spans, int64_t n_isect,
+                                    const XprCamera *cam, const XprConfig *cfg) {
+    if (validate_camera_config(cam, cfg) != XPR_OK || n < 0 || n_views < 1 || n_views > kMaxViews ||
+        n * (int64_t)n_views > 0x7fffffffLL || n_spans < 0 || n_isect < 0)
+        return 0;
+    const RowItems t = row_items_views(*cam, *cfg, n, n_views);
+    if (!bin_rows_supported(t)) return 0;
+    return bin_rows_workspace_bytes(n * n_views, n_spans, n_isect, t);
+}
+
+int xpr_bin_rows_views(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                       const int32_t *order, int64_t n, int32_t n_views, const XprCamera *cam, const XprConfig *cfg,
+                       int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans,
+                       void *workspace, size_t ws_bytes, void *stream) {
+    int s = validate_camera_config(cam, cfg);
+    if (s) return s;
+    if ((s = check_views(n_views, n))) return s;
+    return bin_rows_call("xpr_bin_rows_views", rec, bbox, tile_count, isect_count, order, n * n_views,
+                         row_items_views(*cam, *cfg, n, n_views), cfg, ranges, vals, capacity, n_isect, n_spans,
+                         workspace, ws_bytes, stream);
+}
+
+size_t xpr_bin_rows_items_workspace(const XprCamera *cams, const XprItem *items, int32_t n_items,
+                                    const XprConfig *cfg, int64_t n_spans, int64_t n_isect) {
+    ItemTable it;
+    int64_t R = 0;
+    if (!cfg || n_spans < 0 || n_isect < 0 ||
+        make_item_table(cams, items, n_items, *cfg, it, &R, "xpr_bin_rows_items_workspace") != XPR_OK)
+        return 0;
+    const RowItems t = row_items_items(cams, items, n_items, *cfg);
+    if (!bin_rows_supported(t)) return 0;
+    return bin_rows_workspace_bytes(R, n_spans, n_isect, t);
+}
+
+int xpr_bin_rows_items(const float *rec, const int32_t *bbox, const int32_t *tile_count, const int32_t *isect_count,
+                       const int32_t *order, const XprCamera *cams, const XprItem *items, int32_t n_items,
+                       const XprConfig *cfg, int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect,
+                       int64_t *n_spans, void *workspace, size_t ws_bytes, void *stream) {
+    if (!cfg) return fail(XPR_ERR_INVALID, "xpr_bin_rows_items: NULL config");
+    ItemTable it;
+    int64_t R = 0;
+    int s = make_item_table(cams, items, n_items, *cfg, it, &R, "xpr_bin_rows_items");
+    if (s) return s;
+    return bin_rows_call("xpr_bin_rows_items", rec, bbox, tile_count, isect_count, order, R,
+                         row_items_items(cams, items, n_items, *cfg), cfg, ranges, vals, capacity, n_isect, n_spans,
+                         workspace, ws_bytes, stream);
 }
 
 // ---- 3DGUT --------------------------------------------------------------------------------

@@ -1,24 +1,26 @@
 // Rasterizer first half by rows (Sec. 4.2: Replicate, Assign tile ID, Cull, Sort and identify bounds)
-// for one view whose tile grid has at most 128 columns and 128 rows.
+// for one view, for V views of one camera or for K multi-scene items (Sec. 4.3's batches), every
+// tile grid at most 128 columns and 128 rows.
 //
 // The tile cull in row form (cull.cuh) gives, for every primitive and every tile row of its box, one
 // interval [ka, kb] of kept tile columns: a span.  The per-tile lists are built from spans:
 //   1. span slots: each position j of the depth order owns one slot per row of its box (offsets by
 //      a scan of the box heights in depth order); the emit kernel writes each slot as a 4-byte key
 //      (its tile row, or 255 for a row with no kept tile, in bits 0-7; the first kept column in
-//      bits 8-14; the number of kept tiles in bits 15-22) and its primitive as the value;
+//      bits 8-14; the number of kept tiles in bits 15-22; the record's item in bits 23-26) and its
+//      record as the value;
 //   2. one stable radix pass over the span slots by the row bits, moving key and value: spans
-//      grouped by row, each row's spans in depth order (the empty rows last);
+//      grouped by row, each row's spans in slot order (the empty rows last);
 //   3. an exclusive scan of the span lengths in that order gives every span its first pair, and
-//      the expansion writes the pairs of each span contiguously: tile code (tx << 7) | ty and the
-//      primitive, so the pairs are grouped by tile row, in depth order inside every row (every
-//      read of these passes is a coalesced one of the sorted spans);
+//      the expansion writes the pairs of each span contiguously: tile code (k << 14) | (tx << 7) |
+//      ty and the record, so the pairs are grouped by tile row and, inside a row, by item in depth
+//      order (every read of these passes is a coalesced one of the sorted spans);
 //   4. one stable radix pass over the pairs by the code's column bits [7, 14): the pairs end
-//      grouped by (column, row), i.e. by tile, and inside every tile still in depth order, which is
-//      the tile-major depth-sorted list of Sec. 4.2 with one radix pass over the pairs instead of
-//      two (the rows were sorted on the spans, about seven pairs each here).
-// The tile ranges are found in the code order (column-major over a 128-row grid) and permuted to
-// the row-major tile ids the render uses.  The result is identical, list for list, to the depth-
+//      grouped by (column, row, item), so every tile (k, tx, ty) is one contiguous run, inside it
+//      still in depth order: the tile-major depth-sorted list of Sec. 4.2 with one radix pass over
+//      the pairs instead of two (the rows were sorted on the spans, about seven pairs each here).
+// The tile ranges are found per code and permuted to the tile ids the render uses (item k's tile
+// (tx, ty) at tile0[k] + ty Wt[k] + tx).  The result is identical, list for list, to the depth-
 // ordered emission followed by the stable sort of the tile ids.
 #include "cull.cuh"
 
@@ -27,20 +29,38 @@ namespace {
 
 constexpr uint32_t kRowNone = 255;  // key of a span slot whose box row keeps no tile: sorted last
 constexpr int kMaxRowGrid = 128;    // tile columns and rows: 7 bits each in the pair's tile code
+constexpr int kItemShift = 14;      // the item's bits in the tile code
+constexpr int kSpanItemShift = 23;  // and in the span key
 
+// Item of record i (rec0 increasing; at most kMaxItems items).
+__device__ __forceinline__ int item_of_record(const RowItems &t, int64_t i) {
+    int k = 0;
+#pragma unroll 1
+    while (k + 1 < t.count && i >= t.rec0[k + 1]) ++k;
+    return k;
+}
+
+template <bool ITEMS>
 __global__ void box_rows_kernel(const int4 *__restrict__ bbox, const int *__restrict__ tcount, int64_t n, Grid g,
-                                int32_t *__restrict__ rows) {
+                                RowItems t, int32_t *__restrict__ rows) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (ITEMS) {
+        const int k = item_of_record(t, i);
+        g.Wt = t.Wt[k];
+        g.Ht = t.Ht[k];
+    }
     int4 bb;
     rows[i] = box_of(bbox, tcount, (int)i, g, bb) > 0 ? bb.w - bb.y : 0;
 }
 
 // Warp w takes the positions w, w + nw, ... (interleaved over the depth order, as the pair
 // emission does) and flattens their box rows over its lanes; each row's span goes to its slot.
+// With items, each lane's image size and item travel with its rows through the shuffles.
+template <bool ITEMS>
 __global__ void __launch_bounds__(256) span_emit_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
                                                         const int *__restrict__ tcount,
-                                                        const int *__restrict__ order, int64_t n, Grid g,
+                                                        const int *__restrict__ order, int64_t n, Grid g, RowItems t,
                                                         const int32_t *__restrict__ slot0,
                                                         uint32_t *__restrict__ span_key,
                                                         uint32_t *__restrict__ span_prim) {
@@ -49,13 +69,21 @@ __global__ void __launch_bounds__(256) span_emit_kernel(const float *__restrict_
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= nw) return;
     const int64_t j = w + (int64_t)lane * nw;
-    int i = 0, area = 0, base = 0;
+    int i = 0, area = 0, base = 0, k = 0;
     int4 bb = make_int4(0, 0, 0, 0);
     CullData d = {};
+    Grid gl = g;
     if (j < n) {
         i = order[j];
         base = slot0[j];
-        area = box_of(bbox, tcount, i, g, bb);
+        if (ITEMS) {
+            k = item_of_record(t, i);
+            gl.W = t.W[k];
+            gl.H = t.H[k];
+            gl.Wt = t.Wt[k];
+            gl.Ht = t.Ht[k];
+        }
+        area = box_of(bbox, tcount, i, gl, bb);
         if (area > 0) d = load_cull(rec, i);
     }
     const int h = area > 0 ? bb.w - bb.y : 0;
@@ -70,15 +98,24 @@ __global__ void __launch_bounds__(256) span_emit_kernel(const float *__restrict_
         const int ty = __shfl_sync(kFullMask, bb.y, p) + f - excl_p;
         const int x0 = __shfl_sync(kFullMask, bb.x, p), x1 = __shfl_sync(kFullMask, bb.z, p);
         const int base_p = __shfl_sync(kFullMask, base, p), i_p = __shfl_sync(kFullMask, i, p);
+        Grid gp = g;
+        uint32_t item = 0;
+        if (ITEMS) {
+            gp.W = __shfl_sync(kFullMask, gl.W, p);
+            gp.H = __shfl_sync(kFullMask, gl.H, p);
+            item = (uint32_t)__shfl_sync(kFullMask, k, p) << kSpanItemShift;
+        }
         if (f < rows) {
             int ka = 0, kb = -1;
-            const int c = row_span_in_box(e, g, ty, x0, x1, ka, kb);
+            const int c = row_span_in_box(e, gp, ty, x0, x1, ka, kb);
             const int64_t s = (int64_t)base_p + (f - excl_p);
-            span_key[s] = c > 0 ? ((uint32_t)c << 15) | ((uint32_t)ka << 8) | (uint32_t)ty : kRowNone;
+            span_key[s] = c > 0 ? item | ((uint32_t)c << 15) | ((uint32_t)ka << 8) | (uint32_t)ty : kRowNone;
             span_prim[s] = (uint32_t)i_p;
         }
     }
 }
+
+__device__ __forceinline__ int span_len(uint32_t key) { return (int)((key >> 15) & 0xffu); }
 
 // Warp w takes the sorted spans [32 w, 32 w + 32): their pairs are contiguous from the first span's
 // offset, and the warp writes them 32 at a time, lane k writing pair k of the warp's flattened list
@@ -98,9 +135,9 @@ __global__ void __launch_bounds__(256) span_expand_kernel(const uint32_t *__rest
     uint32_t code0 = 0, prim = 0;
     if (q < ns) {
         const uint32_t key = skey[q];
-        len = (int)(key >> 15);
-        if (len > 0) {
-            code0 = (((key >> 8) & 0x7fu) << 7) | (key & 0x7fu);  // first kept column, row
+        len = span_len(key);
+        if (len > 0) {  // item, first kept column, row
+            code0 = ((key >> kSpanItemShift) << kItemShift) | (((key >> 8) & 0x7fu) << 7) | (key & 0x7fu);
             prim = sprim[q];
         }
     }
@@ -132,27 +169,47 @@ __global__ void __launch_bounds__(256) span_expand_kernel(const uint32_t *__rest
 
 __global__ void span_len_kernel(const uint32_t *__restrict__ skey, int64_t ns, int32_t *__restrict__ len) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < ns) len[q] = (int32_t)(skey[q] >> 15);
+    if (q < ns) len[q] = span_len(skey[q]);
 }
 
-// ranges[ty Wt + tx] = the range found for tile code (tx << 7) | ty
-__global__ void permute_ranges_kernel(const int2 *__restrict__ by_code, int Wt, int Ht, int2 *__restrict__ ranges) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= Wt * Ht) return;
-    const int tx = t % Wt, ty = t / Wt;
-    ranges[t] = by_code[(tx << 7) | ty];
+// ranges[tile0[k] + ty Wt[k] + tx] = the range found for tile code (k << 14) | (tx << 7) | ty
+__global__ void permute_ranges_kernel(const int2 *__restrict__ by_code, RowItems t, int64_t n_tiles,
+                                      int2 *__restrict__ ranges) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= n_tiles) return;
+    int k = 0;
+    while (k + 1 < t.count && gt >= t.tile0[k + 1]) ++k;
+    const int local = (int)(gt - t.tile0[k]);
+    const int tx = local % t.Wt[k], ty = local / t.Wt[k];
+    ranges[gt] = by_code[((int64_t)k << kItemShift) | (tx << 7) | ty];
 }
 
 size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
 
+// Tile codes a table can produce: (count - 1) << 14 plus the widest grid's (tx << 7) | ty.
+int64_t n_codes(const RowItems &t) {
+    int wt = 1;
+    for (int k = 0; k < t.count; ++k) wt = t.Wt[k] > wt ? t.Wt[k] : wt;
+    return ((int64_t)(t.count - 1) << kItemShift) + (int64_t)wt * kMaxRowGrid;
+}
+
+int column_bits(const RowItems &t) {
+    int wt = 1, b = 0;
+    for (int k = 0; k < t.count; ++k) wt = t.Wt[k] > wt ? t.Wt[k] : wt;
+    while ((1 << b) < wt) ++b;
+    return b;
+}
+
+// The span lengths overwrite the span keys and the pair offsets the span records once the span
+// sort has moved both (so a span costs 16 bytes of workspace besides the sort's scratch).
 struct RowsLayout {
-    size_t rows, slot0, part_n, isect_out, totals;           // depend on n only
-    size_t key, prim, skey, sprim, len, pair0, part_s;       // on the span slots
-    size_t sort_ws, codes, pvals, by_code;                   // on the pairs
+    size_t rows, slot0, part_n, isect_out, totals;  // depend on the records only
+    size_t key, prim, skey, sprim, part_s;          // on the span slots (key: then len; prim: then pair0)
+    size_t sort_ws, codes, pvals, by_code;          // on the pairs
     size_t total;
 };
 
-RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, int Wt) {
+RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, const RowItems &t) {
     RowsLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -160,65 +217,120 @@ RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, int Wt) {
         o += align_up(bytes);
         return at;
     };
+    const int64_t nc = n_codes(t);
     L.rows = take((size_t)n * 4);
     L.slot0 = take((size_t)(n + 1) * 4);
     L.part_n = take(scan_partials_bytes(n));
     L.isect_out = take((size_t)(n + 1) * 4);
     L.totals = take(4 * sizeof(int64_t));
     L.key = take((size_t)ns * 4);
-    L.prim = take((size_t)ns * 4);
+    L.prim = take((size_t)(ns + 1) * 4);
     L.skey = take((size_t)ns * 4);
     L.sprim = take((size_t)ns * 4);
-    L.len = take((size_t)ns * 4);
-    L.pair0 = take((size_t)(ns + 1) * 4);
     L.part_s = take(scan_partials_bytes(ns));
-    const size_t sws = sort_tiles_workspace_bytes(ns, 256), pws = sort_tiles_workspace_bytes(ni, Wt * kMaxRowGrid);
-    L.sort_ws = take(sws > pws ? sws : pws);  // the span sort, then the pair sort
+    // the span sort, then the pair sort: one pass each (8 row bits, at most 7 column bits)
+    const size_t sws = sort_u32_onepass_workspace_bytes(ns), pws = sort_u32_onepass_workspace_bytes(ni);
+    L.sort_ws = take(sws > pws ? sws : pws);
     L.codes = take((size_t)ni * 4);
     L.pvals = take((size_t)ni * 4);
-    L.by_code = take((size_t)Wt * kMaxRowGrid * 8);
+    L.by_code = take((size_t)nc * 8);
     L.total = o;
     return L;
 }
 
 }  // namespace
 
+RowItems row_items_views(const XprCamera &cam, const XprConfig &cfg, int64_t n, int n_views) {
+    RowItems t;
+    memset(&t, 0, sizeof(t));
+    t.count = n_views;
+    const int Wt = tiles_x(cam, cfg), Ht = tiles_y(cam, cfg);
+    for (int v = 0; v <= n_views; ++v) {
+        t.rec0[v] = (int64_t)v * n;
+        t.tile0[v] = (int64_t)v * Wt * Ht;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        t.W[v] = cam.width;
+        t.H[v] = cam.height;
+        t.Wt[v] = Wt;
+        t.Ht[v] = Ht;
+    }
+    return t;
+}
+
+RowItems row_items_items(const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg) {
+    RowItems t;
+    memset(&t, 0, sizeof(t));
+    t.count = n_items;
+    int64_t tile = 0;
+    for (int k = 0; k < n_items; ++k) {
+        t.rec0[k] = items[k].rec_offset;
+        t.tile0[k] = tile;
+        t.W[k] = cams[k].width;
+        t.H[k] = cams[k].height;
+        t.Wt[k] = tiles_x(cams[k], cfg);
+        t.Ht[k] = tiles_y(cams[k], cfg);
+        tile += (int64_t)t.Wt[k] * t.Ht[k];
+    }
+    t.rec0[n_items] = n_items > 0 ? items[n_items - 1].rec_offset + (items[n_items - 1].n + 31) / 32 * 32 : 0;
+    t.tile0[n_items] = tile;
+    return t;
+}
+
 bool bin_rows_supported(const XprCamera &cam, const XprConfig &cfg) {
     return tiles_x(cam, cfg) <= kMaxRowGrid && tiles_y(cam, cfg) <= kMaxRowGrid;
 }
 
-size_t bin_rows_workspace_bytes(int64_t n, int64_t n_spans, int64_t n_isect, const XprCamera &cam,
-                                const XprConfig &cfg) {
-    return rows_layout(n, n_spans, n_isect, tiles_x(cam, cfg)).total;
+bool bin_rows_supported(const RowItems &t) {
+    if (t.count < 1 || t.count > kMaxItems) return false;
+    for (int k = 0; k < t.count; ++k)
+        if (t.Wt[k] > kMaxRowGrid || t.Ht[k] > kMaxRowGrid) return false;
+    return true;
 }
 
-// order: the depth order of the n records; isect_count (NULL: none): their kept tile counts, whose
-// total is read back with the span count (one synchronisation) so that both capacities are checked
-// before any span is written.  Returns XPR_ERR_CAPACITY (n_isect, n_spans set, nothing written)
-// when vals holds fewer than n_isect pairs or the workspace is below bin_rows_workspace_bytes.
+size_t bin_rows_workspace_bytes(int64_t n_records, int64_t n_spans, int64_t n_isect, const RowItems &t) {
+    return rows_layout(n_records, n_spans, n_isect, t).total;
+}
+
+// order: the depth order of the n records (each item's in its own block); isect_count (NULL: none):
+// their kept tile counts, whose total is read back with the span count (one synchronisation) so
+// that both capacities are checked before any span is written.  Returns XPR_ERR_CAPACITY
+// (n_isect, n_spans set, nothing written) when vals holds fewer than n_isect pairs or the
+// workspace is below bin_rows_workspace_bytes.
 int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *isect_count,
-                    const int32_t *order, int64_t n, const XprCamera &cam, const XprConfig &cfg, int32_t *ranges,
+                    const int32_t *order, int64_t n, const RowItems &t, const XprConfig &cfg, int32_t *ranges,
                     uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *ws, size_t ws_bytes,
                     cudaStream_t st) {
-    const Grid g = make_grid(cam, cfg);
-    const int Wt = g.Wt, Ht = g.Ht, T = Wt * Ht;
-    if (!bin_rows_supported(cam, cfg))
-        return fail(XPR_ERR_INVALID, "xpr_bin_rows: a %d x %d tile grid has more than 128 tile columns or rows", Wt,
-                    Ht);
+    if (!bin_rows_supported(t))
+        return fail(XPR_ERR_INVALID, "xpr_bin_rows: %d items, or a tile grid with more than 128 tile columns or rows",
+                    t.count);
+    Grid g;
+    g.W = t.W[0];
+    g.H = t.H[0];
+    g.tw = cfg.tile_w;
+    g.th = cfg.tile_h;
+    g.Wt = t.Wt[0];
+    g.Ht = t.Ht[0];
+    g.ext = cfg.method == XPR_METHOD_3DGUT ? 1 : 0;
+    const bool items = t.count > 1;
+    const int64_t T = t.tile0[t.count];
     *n_isect = 0;
     *n_spans = 0;
     if (n == 0) {
         if (T > 0) XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)T * 8, st));
         return XPR_OK;
     }
-    const RowsLayout L0 = rows_layout(n, 0, 0, Wt);
+    const RowsLayout L0 = rows_layout(n, 0, 0, t);
     if (ws_bytes < L0.total) return fail(XPR_ERR_INVALID, "xpr_bin_rows: workspace %zu < %zu bytes", ws_bytes, L0.total);
     char *p = reinterpret_cast<char *>(ws);
     int32_t *rows = reinterpret_cast<int32_t *>(p + L0.rows);
     int32_t *slot0 = reinterpret_cast<int32_t *>(p + L0.slot0);
     int64_t *tot = reinterpret_cast<int64_t *>(p + L0.totals);
     const unsigned nb = (unsigned)((n + 255) / 256);
-    box_rows_kernel<<<nb, 256, 0, st>>>(reinterpret_cast<const int4 *>(bbox), tc, n, g, rows);
+    if (items)
+        box_rows_kernel<true><<<nb, 256, 0, st>>>(reinterpret_cast<const int4 *>(bbox), tc, n, g, t, rows);
+    else
+        box_rows_kernel<false><<<nb, 256, 0, st>>>(reinterpret_cast<const int4 *>(bbox), tc, n, g, t, rows);
     XPR_LAUNCH_CHECK("box_rows_kernel");
     int s = launch_exclusive_scan(rows, slot0, n, p + L0.part_n, tot, st, order);
     if (s != XPR_OK) return s;
@@ -231,6 +343,8 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     XPR_CUDA_TRY(cudaMemcpyAsync(h_tot, tot, (isect_count ? 2 : 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     XPR_CUDA_TRY(cudaStreamSynchronize(st));
     const int64_t ns = h_tot[0];
+    *n_spans = ns;
+    if (isect_count) *n_isect = h_tot[1];
     if (ns > 0x7fffffffLL || h_tot[1] > 0x7fffffffLL)
         return fail(XPR_ERR_CAPACITY, "xpr_bin_rows: more than 2^31 - 1 spans or pairs");
     *n_spans = ns;
@@ -238,18 +352,23 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     // is checked here (its regions do not depend on the pair count) and the pair phase after
     int64_t ni = isect_count ? h_tot[1] : 0;
     if (isect_count) *n_isect = ni;
-    const RowsLayout L = rows_layout(n, ns, ni, Wt);
+    const RowsLayout L = rows_layout(n, ns, ni, t);
     if ((isect_count && ni > capacity) || ws_bytes < L.total) return XPR_ERR_CAPACITY;
     uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
     uint32_t *skey = reinterpret_cast<uint32_t *>(p + L.skey), *sprim = reinterpret_cast<uint32_t *>(p + L.sprim);
-    int32_t *len = reinterpret_cast<int32_t *>(p + L.len);
-    int32_t *pair0 = reinterpret_cast<int32_t *>(p + L.pair0);
+    int32_t *len = reinterpret_cast<int32_t *>(key);     // the keys are dead once sorted into skey
+    int32_t *pair0 = reinterpret_cast<int32_t *>(prim);  // and the records once moved into sprim
     const int64_t warps = (n + 31) / 32;
-    span_emit_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, g, slot0, key, prim);
+    const unsigned eg = (unsigned)((warps * 32 + 255) / 256);
+    if (items)
+        span_emit_kernel<true><<<eg, 256, 0, st>>>(rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, g, t,
+                                                   slot0, key, prim);
+    else
+        span_emit_kernel<false><<<eg, 256, 0, st>>>(rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, g, t,
+                                                    slot0, key, prim);
     XPR_LAUNCH_CHECK("span_emit_kernel");
     s = launch_sort_u32_bits(key, prim, ns, 256, 0, 8, skey, sprim, nullptr, p + L.sort_ws,
-                             sort_tiles_workspace_bytes(ns, 256), st);
+                             sort_u32_onepass_workspace_bytes(ns), st);
     if (s != XPR_OK) return s;
     if (ns > 0) {
         span_len_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(skey, ns, len);
@@ -261,9 +380,9 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
         XPR_CUDA_TRY(cudaMemcpyAsync(&ni, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         XPR_CUDA_TRY(cudaStreamSynchronize(st));
         *n_isect = ni;
-        if (ni > capacity || ws_bytes < rows_layout(n, ns, ni, Wt).total) return XPR_ERR_CAPACITY;
+        if (ni > capacity || ws_bytes < rows_layout(n, ns, ni, t).total) return XPR_ERR_CAPACITY;
     }
-    const RowsLayout LP = rows_layout(n, ns, ni, Wt);
+    const RowsLayout LP = rows_layout(n, ns, ni, t);
     uint32_t *codes = reinterpret_cast<uint32_t *>(p + LP.codes), *pvals = reinterpret_cast<uint32_t *>(p + LP.pvals);
     const int64_t swarps = (ns + 31) / 32;
     if (ns > 0) {
@@ -271,16 +390,17 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
                                                                                   pvals);
         XPR_LAUNCH_CHECK("span_expand_kernel");
     }
+    const int64_t nc = n_codes(t);
     int2 *by_code = reinterpret_cast<int2 *>(p + LP.by_code);
-    int colbits = 0;
-    while ((1 << colbits) < Wt) ++colbits;
-    s = launch_sort_u32_bits(codes, pvals, ni, Wt * kMaxRowGrid, 7, 7 + colbits, nullptr, vals,
+    s = launch_sort_u32_bits(codes, pvals, ni, (int32_t)nc, 7, 7 + column_bits(t), nullptr, vals,
                              reinterpret_cast<int32_t *>(by_code), p + LP.sort_ws,
-                             sort_tiles_workspace_bytes(ni, Wt * kMaxRowGrid), st);
+                             sort_u32_onepass_workspace_bytes(ni), st);
     if (s != XPR_OK) return s;
-    permute_ranges_kernel<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(by_code, Wt, Ht,
-                                                                        reinterpret_cast<int2 *>(ranges));
-    XPR_LAUNCH_CHECK("permute_ranges_kernel");
+    if (T > 0) {
+        permute_ranges_kernel<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(by_code, t, T,
+                                                                            reinterpret_cast<int2 *>(ranges));
+        XPR_LAUNCH_CHECK("permute_ranges_kernel");
+    }
     return XPR_OK;
 }
 

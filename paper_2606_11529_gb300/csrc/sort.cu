@@ -660,14 +660,15 @@ int bits_for(int64_t x) {
 
 inline bool is_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// Workspace: the ping-pong copies of keys and values, two (block x digit) matrices (chained:
-// the words of the current and the next pass; reduce-then-scan: the offset matrix and the segment
-// sums) and the digit counts with the block counters (reduce-then-scan: the digit totals).
+// Workspace: the ping-pong copies of keys and values (only for more than one pass: a single pass
+// reads the input and writes the output), two (block x digit) matrices (chained: the words of the
+// current and the next pass; reduce-then-scan: the offset matrix and the segment sums) and the
+// digit counts with the block counters (reduce-then-scan: the digit totals).
 template <typename K>
-size_t workspace_bytes(int64_t n) {
+size_t workspace_bytes(int64_t n, int passes = kMaxPasses) {
     const int64_t nb = max((int64_t)1, (n + kTileR - 1) / kTileR);  // kTileR < kTile: the larger count
-    return align256((size_t)n * sizeof(K)) + align256((size_t)n * 4) + 2 * align256((size_t)nb * kRadix * 4) +
-           align256((size_t)kMaxPasses * (kRadix + 1) * 4);
+    const size_t alt = passes > 1 ? align256((size_t)n * sizeof(K)) + align256((size_t)n * 4) : 0;
+    return alt + 2 * align256((size_t)nb * kRadix * 4) + align256((size_t)kMaxPasses * (kRadix + 1) * 4);
 }
 
 template <typename K, int NB>
@@ -707,17 +708,20 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
     if (ranges) XPR_CUDA_TRY(cudaMemsetAsync(ranges, 0, (size_t)n_tiles * 2 * sizeof(int32_t), st));
     if (n == 0) return XPR_OK;
     if (n > 0x7fffffffLL) return fail(XPR_ERR_INVALID, "sort: more than 2^31 - 1 keys");
-    if (ws_bytes < workspace_bytes<K>(n))
-        return fail(XPR_ERR_INVALID, "sort: workspace %zu bytes < required %zu", ws_bytes, workspace_bytes<K>(n));
+    const int passes = begin_bit < end_bit ? (end_bit - begin_bit + 7) / 8 : 0;
+    if (passes > kMaxPasses) return fail(XPR_ERR_INVALID, "sort: %d passes > %d", passes, kMaxPasses);
+    if (ws_bytes < workspace_bytes<K>(n, passes))
+        return fail(XPR_ERR_INVALID, "sort: workspace %zu bytes < required %zu", ws_bytes,
+                    workspace_bytes<K>(n, passes));
     const bool chained = n <= kChainedMaxKeys;
     const int tile_keys = chained ? kTile : kTileR;
     const int64_t nb = (n + tile_keys - 1) / tile_keys;
     const int64_t nseg = (nb + kSegRows - 1) / kSegRows;
     char *p = reinterpret_cast<char *>(ws);
-    K *alt_k = reinterpret_cast<K *>(p);
-    p += align256((size_t)n * sizeof(K));
+    K *alt_k = reinterpret_cast<K *>(p);  // the ping-pong copies: used (and present) for 2+ passes only
+    if (passes > 1) p += align256((size_t)n * sizeof(K));
     uint32_t *alt_v = reinterpret_cast<uint32_t *>(p);
-    p += align256((size_t)n * 4);
+    if (passes > 1) p += align256((size_t)n * 4);
     uint32_t *mat[2];
     mat[0] = reinterpret_cast<uint32_t *>(p);
     p += align256((size_t)nb * kRadix * 4);
@@ -726,8 +730,6 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
     uint32_t *ghist = reinterpret_cast<uint32_t *>(p);  // kMaxPasses x kRadix counts, then kMaxPasses counters
     uint32_t *ctr = ghist + kMaxPasses * kRadix;
 
-    const int passes = begin_bit < end_bit ? (end_bit - begin_bit + 7) / 8 : 0;
-    if (passes > kMaxPasses) return fail(XPR_ERR_INVALID, "sort: %d passes > %d", passes, kMaxPasses);
     int2 *rg = reinterpret_cast<int2 *>(ranges);
     if (passes == 0) {
         if (keys_out)
@@ -870,6 +872,8 @@ size_t sort_tiles_workspace_bytes(int64_t n, int32_t n_tiles) {
     (void)n_tiles;
     return workspace_bytes<uint32_t>(n);
 }
+
+size_t sort_u32_onepass_workspace_bytes(int64_t n) { return workspace_bytes<uint32_t>(n, 1); }
 
 int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
                 uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {

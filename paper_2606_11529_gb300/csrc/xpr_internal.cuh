@@ -120,14 +120,24 @@ int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, c
 int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,
                     const XprCamera &cam, const XprConfig &cfg, const int32_t *offsets, uint64_t *keys,
                     uint32_t *tiles, uint32_t *vals, cudaStream_t st, int64_t per_view = 0);
-// binning and tile sort by rows (binrows.cu): one view, at most 128 tile columns and rows
+// binning and tile sort by rows (binrows.cu) of one view, of V views of one camera, or of K
+// multi-scene items, each grid at most 128 tile columns and rows.  Item k holds the records
+// [rec0[k], rec0[k + 1]) and is binned on a W[k] x H[k] image whose tiles are numbered from tile0[k].
+struct RowItems {
+    int count;
+    int64_t rec0[kMaxItems + 1];
+    int64_t tile0[kMaxItems + 1];
+    int W[kMaxItems], H[kMaxItems], Wt[kMaxItems], Ht[kMaxItems];
+};
+RowItems row_items_views(const XprCamera &cam, const XprConfig &cfg, int64_t n, int n_views);
+RowItems row_items_items(const XprCamera *cams, const XprItem *items, int n_items, const XprConfig &cfg);
 bool bin_rows_supported(const XprCamera &cam, const XprConfig &cfg);
-size_t bin_rows_workspace_bytes(int64_t n, int64_t n_spans, int64_t n_isect, const XprCamera &cam,
-                                const XprConfig &cfg);
+bool bin_rows_supported(const RowItems &t);
+size_t bin_rows_workspace_bytes(int64_t n_records, int64_t n_spans, int64_t n_isect, const RowItems &t);
 int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *isect_count,
-                    const int32_t *order, int64_t n, const XprCamera &cam, const XprConfig &cfg, int32_t *ranges,
-                    uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *ws, size_t ws_bytes,
-                    cudaStream_t st);
+                    const int32_t *order, int64_t n_records, const RowItems &t, const XprConfig &cfg,
+                    int32_t *ranges, uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *ws,
+                    size_t ws_bytes, cudaStream_t st);
 size_t depth_order_workspace_bytes(int64_t n);
 int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *order, void *ws, size_t ws_bytes,
                        cudaStream_t st, int64_t per_view = 0, int n_views = 1);
@@ -201,6 +211,8 @@ int launch_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t
                       cudaStream_t st);
 // stable sort of 4-byte keys by bits [begin_bit, end_bit) (workspace: sort_tiles_workspace_bytes(n, .));
 // ranges (NULL: none) are those of the whole key values, 0 .. n_tiles - 1
+// scratch of launch_sort_u32_bits for at most 8 key bits (one pass: no ping-pong copies)
+size_t sort_u32_onepass_workspace_bytes(int64_t n);
 int launch_sort_u32_bits(const uint32_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
                          int end_bit, uint32_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws,
                          size_t ws_bytes, cudaStream_t st);

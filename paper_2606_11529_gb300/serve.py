@@ -34,6 +34,7 @@ device dependence, so its behaviour is testable without a GPU.
 from __future__ import annotations
 
 import collections
+import ctypes
 import dataclasses
 import math
 import time
@@ -199,20 +200,17 @@ def latency_stats(reqs: list[Request], warmup: int = 0) -> dict:
 # ------------------------------------------------------------------------------------------ device side
 
 def footprint_bytes_items(n_prims: int, width: int, height: int, n_isect: int, cfg) -> int:
-    """Device working memory of one request rendered as an item of a multi-scene batch: records,
-    boxes, counts and depth order of its padded record block, the depth-order scratch, the fused
-    bin + sort's count matrix and scans, the pair buffer at the capacity asked for, the tile ranges
-    and work list, and the image planes."""
+    """Device working memory of one request rendered as an item of a multi-scene batch: the
+    workspace `xpr_forward_items` asks for one item of this size at a capacity of ``n_isect`` pairs
+    (records, boxes, counts, depth order and its scratch, the binning's scratch, the sorted pairs,
+    the tile ranges and work list), plus the image planes, t_final and n_contrib."""
     from . import binding as B
+    from . import scenes as S
     L = B.load()
-    R = (n_prims + 31) // 32 * 32
-    tw, th = int(cfg.tile_w), int(cfg.tile_h)
-    nt = ((width + tw - 1) // tw) * ((height + th - 1) // th)
-    cap = int(n_isect * 1.25) + 1024
-    chunks = max(1, (n_prims + 4095) // 4096)
-    binsort = chunks * nt * 4 + (chunks // 32 + 1) * nt * 4 + (nt + 1) * 4 + 4096
-    return int(R * (12 * 4 + 16 + 4 + 4) + int(L.xpr_depth_order_workspace(R)) + binsort + cap * 4 +
-               int(L.xpr_tile_worklist_workspace(nt)) + nt * 12 + width * height * (3 * 4 + 4 + 4))
+    layout = B.ItemLayout([0], [int(n_prims)], [S.pinhole(int(width), int(height), float(width))], cfg)
+    g = B.make_config(cfg)
+    ws = int(L.xpr_forward_items_workspace(layout.carr, layout.arr, 1, ctypes.byref(g), int(n_isect)))
+    return ws + int(width) * int(height) * (3 * 4 + 4 + 4)
 
 
 def footprint_bytes(n_prims: int, width: int, height: int, n_isect: int, cfg, n_views: int = 1) -> int:

@@ -3,14 +3,19 @@ record indices equals the oracle's exact-FP32 binning followed by the oracle's
 sort by (tile, depth, index), and equals the key path (xpr_tile_bin +
 xpr_sort_tiles) on the GPU's own records, for 3DGS and 3DGUT, ragged grids, 8x8
 tiles, the headline workload, with and without the kept counts, and across the
-capacity and workspace protocol.  (Its tiles' segments lie in column-major tile
-order, the key path's in row-major order; the ranges locate them.)"""
+capacity and workspace protocol.  The batch forms (xpr_bin_rows_views over the
+views of one camera, xpr_bin_rows_items over multi-scene items, and the one-call
+xpr_forward_items that bins by rows) give every view's and item's lists of the
+key path and of the fused counting sort.  (Their tiles' segments lie in
+column-major tile order, the key path's in row-major order; the ranges locate
+them.)"""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+from paper_2606_11529_gb300 import batched as BT
 from paper_2606_11529_gb300 import binding as B
 from paper_2606_11529_gb300 import render as R
 from paper_2606_11529_gb300 import scenes
@@ -132,3 +137,84 @@ def test_bin_rows_rejects_wide_grids_and_takes_empty_input():
     cam = scenes.pinhole(100, 60, 100.0)
     rg, v, I, S, _ = B.xpr_bin_rows(buf.view(torch.float32), buf, buf, buf, 0, cam, cfg)
     assert (I, S) == (0, 0) and v.numel() == 0 and torch.all(rg == 0)
+
+
+@pytest.mark.parametrize("method,tile", [(0, 16), (0, 8), (1, 16)])
+def test_bin_rows_views_equal_key_path(method, tile):
+    sc = scenes.uniform_scene(30_000, seed=11, sh_degree=1)
+    sc.scale[::89] *= 8.0
+    cams = scenes.multiview_cameras(5, 330, 200, 330.0, seed=1)  # ragged: 21 x 13 tiles of 16
+    cfg = scenes.RenderConfig(tile_w=tile, tile_h=tile, sh_degree=1, method=method)
+    P = R.scene_to_device(sc)
+    a = BT.forward_views(*P, cams, cfg)             # by rows
+    b = BT.forward_views(*P, cams, cfg, rows=False)  # tile ids, then the tile sort
+    assert a.n_isect == b.n_isect > 100_000
+    assert_same_tile_lists(a.vals_sorted, a.ranges, b.vals_sorted, b.ranges)
+    assert torch.equal(a.image, b.image) and torch.equal(a.n_contrib, b.n_contrib)
+
+
+def test_bin_rows_views_capacity_protocol():
+    sc = scenes.uniform_scene(20_000, seed=12)
+    cams = scenes.multiview_cameras(3, 300, 200, 300.0, seed=2)
+    cfg = scenes.RenderConfig()
+    P = R.scene_to_device(sc)
+    ref = BT.forward_views(*P, cams, cfg, rows=False)
+    n, V = sc.n, len(cams)
+    rec, bbox, tc, cnt = B.xpr_project_views(*P, cams, B.make_config(cfg), with_isect_count=True)
+    order = B.xpr_depth_order_views(rec, tc, n, V)
+    # started with room for 16 pairs and no workspace: grown from the reported counts
+    rg, v, I, S, ws = B.xpr_bin_rows_views(rec, bbox, tc, order, n, V, cams[0], B.make_config(cfg), capacity=16)
+    assert I == ref.n_isect and S > 0 and ws.numel() >= B.bin_rows_views_workspace_bytes(n, V, S, I, cams[0], cfg)
+    assert_same_tile_lists(v, rg, ref.vals_sorted, ref.ranges)
+    rg2, v2, I2, S2, _ = B.xpr_bin_rows_views(rec, bbox, tc, order, n, V, cams[0], B.make_config(cfg),
+                                              isect_count=cnt, capacity=16)
+    assert (I2, S2) == (I, S) and torch.equal(rg2, rg) and torch.equal(v2, v)
+
+
+def _items(tile=16):
+    scs = [scenes.clustered_scene(n, seed=s, n_centers=20, width=W, height=H, focal=float(W), sh_degree=1)
+           for s, (n, W, H) in enumerate([(9003, 320, 180), (40_000, 256, 256), (1201, 200, 150)])]
+    cams = [scenes.pinhole(320, 180, 320.0, scenes.yaw_view(2.0, (0.01, 0.0, 0.02))),
+            scenes.pinhole(256, 256, 256.0),
+            scenes.pinhole(200, 150, 200.0),
+            scenes.pinhole(250, 170, 256.0, scenes.yaw_view(-4.0, (0.0, 0.02, 0.0))),
+            scenes.pinhole(64, 48, 64.0)]
+    cfg = scenes.RenderConfig(tile_w=tile, tile_h=tile, sh_degree=1)
+    ss = BT.SceneSet([R.scene_to_device(s) for s in scs])
+    return ss, ss.layout([0, 1, 2, 1, 0], cams, cfg), cfg
+
+
+@pytest.mark.parametrize("tile", [16, 8])
+def test_bin_rows_items_equal_the_fused_sort_and_the_one_call_forward(tile):
+    ss, layout, cfg = _items(tile)
+    a = BT.forward_items(*ss.params, layout, cfg)             # by rows
+    b = BT.forward_items(*ss.params, layout, cfg, rows=False)  # the fused counting sort
+    assert a.n_isect == b.n_isect > 50_000
+    assert_same_tile_lists(a.vals_sorted, a.ranges, b.vals_sorted, b.ranges)
+    assert torch.equal(a.image, b.image) and torch.equal(a.n_contrib, b.n_contrib)
+    image, tfin, ncon, I, _ = B.xpr_forward_items(*ss.params, layout, B.make_config(cfg), capacity=a.n_isect)
+    assert I == a.n_isect
+    assert torch.equal(image, a.image) and torch.equal(tfin, a.t_final) and torch.equal(ncon, a.n_contrib)
+
+
+def test_forward_items_bins_tall_boxes_by_the_key_path_when_the_spans_outgrow_their_room():
+    # needles one tile wide and many rows tall: about one pair per span, so at a capacity of exactly
+    # the pair count the cap / 2 + R span slots the one-call forward reserves are too few for the
+    # rows binning, and it bins by tile ids and the tile sort instead (the same lists and image)
+    sc = scenes.uniform_scene(3000, seed=13, sh_degree=0)
+    sc.scale[:, 0] = 0.002
+    sc.scale[:, 1] = 0.4
+    sc.scale[:, 2] = 0.002
+    sc.quat[:] = np.array([1.0, 0.0, 0.0, 0.0], np.float32)
+    cam = scenes.pinhole(480, 480, 480.0)
+    cfg = scenes.RenderConfig(sh_degree=0)
+    ss = BT.SceneSet([R.scene_to_device(sc)])
+    layout = ss.layout([0], [cam], cfg)
+    ref = BT.forward_items(*ss.params, layout, cfg, rows=False)
+    rec, bbox, tc = B.xpr_project_items(*ss.params, layout, B.make_config(cfg))
+    order = B.xpr_depth_order_items(rec, tc, layout)
+    _, _, I, S, _ = B.xpr_bin_rows_items(rec, bbox, tc, order, layout, B.make_config(cfg))
+    assert I == ref.n_isect and S > I // 2 + layout.R  # the fallback's condition holds
+    image, tfin, ncon, I2, _ = B.xpr_forward_items(*ss.params, layout, B.make_config(cfg), capacity=I)
+    assert I2 == I
+    assert torch.equal(image, ref.image) and torch.equal(ncon, ref.n_contrib)
