@@ -6,6 +6,7 @@
 // from the count pass here) are prefix-summed into offsets, then the emit pass writes every kept
 // pair at its offset: culled pairs are never written, so the sort moves only survivors.
 #include "cull.cuh"
+#include "scan.cuh"
 
 namespace xpr {
 namespace {
@@ -195,102 +196,21 @@ __global__ void depth_key_items_kernel(const float *__restrict__ rec, const int 
     vals[i] = (uint32_t)i;
 }
 
-// ---- device-wide exclusive scan (three phases: block reduce, scan of block sums, block scan) ----
-// Item j is in[gather[j]] when gather is non-NULL, else in[j].
-constexpr int kScanThreads = 512;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
-__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *smem_warp, int64_t *total) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int64_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) smem_warp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-        int64_t w = lane < nw ? smem_warp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < nw) smem_warp[lane] = w;
-    }
-    __syncthreads();
-    int64_t prefix = wid > 0 ? smem_warp[wid - 1] : 0;
-    *total = smem_warp[(blockDim.x >> 5) - 1];
-    __syncthreads();
-    return prefix + x - v;
-}
-
-__device__ __forceinline__ int32_t scan_item(const int32_t *in, const int32_t *gather, int64_t j) {
-    return in[gather ? (int64_t)gather[j] : j];
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t *__restrict__ in,
-                                                                   const int32_t *__restrict__ gather, int64_t n,
-                                                                   int64_t *__restrict__ partials) {
-    __shared__ int64_t sw[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int64_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        int64_t j = base + (int64_t)k * kScanThreads + threadIdx.x;
-        if (j < n) s += scan_item(in, gather, j);
-    }
-    int64_t tot;
-    block_exclusive_scan(s, sw, &tot);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_partials_kernel(int64_t *__restrict__ partials, int64_t nb,
-                                                                     int64_t *__restrict__ total_out) {
-    __shared__ int64_t sw[32];
-    int64_t carry = 0;
-    for (int64_t base = 0; base < nb; base += kScanThreads) {
-        int64_t j = base + threadIdx.x;
-        int64_t v = j < nb ? partials[j] : 0;
-        int64_t tot;
-        int64_t ex = block_exclusive_scan(v, sw, &tot);
-        if (j < nb) partials[j] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) *total_out = carry;
-}
-
-// Items are read in a blocked layout (thread t owns kScanItems consecutive items) so the
-// in-place case (in == out, no gather) is safe: every item is read before it is written, by its owner.
-__global__ void __launch_bounds__(kScanThreads) scan_downsweep_kernel(const int32_t *in, const int32_t *gather,
-                                                                      int32_t *out, int64_t n,
-                                                                      const int64_t *__restrict__ partials,
-                                                                      const int64_t *__restrict__ total) {
-    __shared__ int64_t sw[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    int32_t v[kScanItems];
-    int64_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        int64_t j = base + k;
-        v[k] = j < n ? scan_item(in, gather, j) : 0;
-        s += v[k];
-    }
-    int64_t tot;
-    int64_t ex = block_exclusive_scan(s, sw, &tot) + partials[blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        int64_t j = base + k;
-        if (j < n) out[j] = (int32_t)ex;
-        ex += v[k];
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (int32_t)*total;
-}
+// ---- device-wide exclusive scan (scan.cuh) ----
+// Items of the offsets scans: in[j], or in[gather[j]] gathered through the emission order.
+struct ScanArray {
+    const int32_t *in;
+    __device__ __forceinline__ int32_t operator()(int64_t j) const { return in[j]; }
+};
+struct ScanGather {
+    const int32_t *in;
+    const int32_t *gather;
+    __device__ __forceinline__ int32_t operator()(int64_t j) const { return in[gather[j]]; }
+};
 
 }  // namespace
+
+constexpr int kScanTile = scan_detail::kTile;
 
 int64_t *scan_total_ptr(void *partials, int64_t n) {
     return reinterpret_cast<int64_t *>(partials) + (n + kScanTile - 1) / kScanTile + 1;
@@ -304,21 +224,8 @@ size_t scan_partials_bytes(int64_t n) {
 // partials layout: [nb] block sums, then the total (device int64) if total_out is NULL.
 int launch_exclusive_scan(const int32_t *in, int32_t *out, int64_t n, void *partials, int64_t *total_out,
                           cudaStream_t st, const int32_t *gather) {
-    int64_t nb = (n + kScanTile - 1) / kScanTile;
-    int64_t *part = reinterpret_cast<int64_t *>(partials);
-    int64_t *tot = total_out ? total_out : scan_total_ptr(partials, n);
-    if (n == 0) {
-        XPR_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int32_t), st));
-        XPR_CUDA_TRY(cudaMemsetAsync(tot, 0, sizeof(int64_t), st));
-        return XPR_OK;
-    }
-    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, n, part);
-    XPR_LAUNCH_CHECK("scan_reduce_kernel");
-    scan_partials_kernel<<<1, kScanThreads, 0, st>>>(part, nb, tot);
-    XPR_LAUNCH_CHECK("scan_partials_kernel");
-    scan_downsweep_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, gather, out, n, part, tot);
-    XPR_LAUNCH_CHECK("scan_downsweep_kernel");
-    return XPR_OK;
+    if (gather) return launch_scan(ScanGather{in, gather}, out, n, partials, total_out, st);
+    return launch_scan(ScanArray{in}, out, n, partials, total_out, st);
 }
 
 int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *order, int64_t n,

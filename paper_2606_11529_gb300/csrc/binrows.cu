@@ -23,6 +23,7 @@
 // (tx, ty) at tile0[k] + ty Wt[k] + tx).  The result is identical, list for list, to the depth-
 // ordered emission followed by the stable sort of the tile ids.
 #include "cull.cuh"
+#include "scan.cuh"
 
 namespace xpr {
 namespace {
@@ -40,19 +41,31 @@ __device__ __forceinline__ int item_of_record(const RowItems &t, int64_t i) {
     return k;
 }
 
+// Scan items: the box height (tile rows) of the record at depth position j, on its item's grid.
 template <bool ITEMS>
-__global__ void box_rows_kernel(const int4 *__restrict__ bbox, const int *__restrict__ tcount, int64_t n, Grid g,
-                                RowItems t, int32_t *__restrict__ rows) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (ITEMS) {
-        const int k = item_of_record(t, i);
-        g.Wt = t.Wt[k];
-        g.Ht = t.Ht[k];
+struct BoxRowsItem {
+    const int4 *bbox;
+    const int *tcount;
+    const int *order;
+    Grid g;
+    RowItems t;
+    __device__ __forceinline__ int32_t operator()(int64_t j) const {
+        const int i = order[j];
+        Grid gl = g;
+        if (ITEMS) {
+            const int k = item_of_record(t, i);
+            gl.Wt = t.Wt[k];
+            gl.Ht = t.Ht[k];
+        }
+        int4 bb;
+        return box_of(bbox, tcount, i, gl, bb) > 0 ? bb.w - bb.y : 0;
     }
-    int4 bb;
-    rows[i] = box_of(bbox, tcount, (int)i, g, bb) > 0 ? bb.w - bb.y : 0;
-}
+};
+
+struct CountItem {  // the kept tile counts, summed for the pair total
+    const int32_t *in;
+    __device__ __forceinline__ int32_t operator()(int64_t j) const { return in[j]; }
+};
 
 // Warp w takes the positions w, w + nw, ... (interleaved over the depth order, as the pair
 // emission does) and flattens their box rows over its lanes; each row's span goes to its slot.
@@ -167,10 +180,10 @@ __global__ void __launch_bounds__(256) span_expand_kernel(const uint32_t *__rest
     }
 }
 
-__global__ void span_len_kernel(const uint32_t *__restrict__ skey, int64_t ns, int32_t *__restrict__ len) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < ns) len[q] = span_len(skey[q]);
-}
+struct SpanLenItem {  // scan items: the pairs of sorted span q
+    const uint32_t *skey;
+    __device__ __forceinline__ int32_t operator()(int64_t q) const { return span_len(skey[q]); }
+};
 
 // ranges[tile0[k] + ty Wt[k] + tx] = the range found for tile code (k << 14) | (tx << 7) | ty
 __global__ void permute_ranges_kernel(const int2 *__restrict__ by_code, RowItems t, int64_t n_tiles,
@@ -200,12 +213,12 @@ int column_bits(const RowItems &t) {
     return b;
 }
 
-// The span lengths overwrite the span keys and the pair offsets the span records once the span
-// sort has moved both (so a span costs 16 bytes of workspace besides the sort's scratch).
+// The pair offsets overwrite the span records once the span sort has moved them (so a span costs
+// 16 bytes of workspace besides the sort's scratch).
 struct RowsLayout {
-    size_t rows, slot0, part_n, isect_out, totals;  // depend on the records only
-    size_t key, prim, skey, sprim, part_s;          // on the span slots (key: then len; prim: then pair0)
-    size_t sort_ws, codes, pvals, by_code;          // on the pairs
+    size_t slot0, part_n, totals;          // depend on the records only
+    size_t key, prim, skey, sprim, part_s;  // on the span slots (prim: then pair0)
+    size_t sort_ws, codes, pvals, by_code;  // on the pairs
     size_t total;
 };
 
@@ -218,10 +231,8 @@ RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, const RowItems &t) {
         return at;
     };
     const int64_t nc = n_codes(t);
-    L.rows = take((size_t)n * 4);
     L.slot0 = take((size_t)(n + 1) * 4);
     L.part_n = take(scan_partials_bytes(n));
-    L.isect_out = take((size_t)(n + 1) * 4);
     L.totals = take(4 * sizeof(int64_t));
     L.key = take((size_t)ns * 4);
     L.prim = take((size_t)(ns + 1) * 4);
@@ -323,20 +334,16 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     const RowsLayout L0 = rows_layout(n, 0, 0, t);
     if (ws_bytes < L0.total) return fail(XPR_ERR_INVALID, "xpr_bin_rows: workspace %zu < %zu bytes", ws_bytes, L0.total);
     char *p = reinterpret_cast<char *>(ws);
-    int32_t *rows = reinterpret_cast<int32_t *>(p + L0.rows);
     int32_t *slot0 = reinterpret_cast<int32_t *>(p + L0.slot0);
     int64_t *tot = reinterpret_cast<int64_t *>(p + L0.totals);
-    const unsigned nb = (unsigned)((n + 255) / 256);
-    if (items)
-        box_rows_kernel<true><<<nb, 256, 0, st>>>(reinterpret_cast<const int4 *>(bbox), tc, n, g, t, rows);
-    else
-        box_rows_kernel<false><<<nb, 256, 0, st>>>(reinterpret_cast<const int4 *>(bbox), tc, n, g, t, rows);
-    XPR_LAUNCH_CHECK("box_rows_kernel");
-    int s = launch_exclusive_scan(rows, slot0, n, p + L0.part_n, tot, st, order);
+    // span slot offsets: the scan of the box heights in depth order (the heights computed in the
+    // scan's own reads); the pair total: the sum of the kept counts
+    const int4 *bb4 = reinterpret_cast<const int4 *>(bbox);
+    int s = items ? launch_scan(BoxRowsItem<true>{bb4, tc, order, g, t}, slot0, n, p + L0.part_n, tot, st)
+                  : launch_scan(BoxRowsItem<false>{bb4, tc, order, g, t}, slot0, n, p + L0.part_n, tot, st);
     if (s != XPR_OK) return s;
     if (isect_count) {
-        s = launch_exclusive_scan(isect_count, reinterpret_cast<int32_t *>(p + L0.isect_out), n, p + L0.part_n,
-                                  tot + 1, st);
+        s = launch_scan(CountItem{isect_count}, nullptr, n, p + L0.part_n, tot + 1, st);
         if (s != XPR_OK) return s;
     }
     int64_t h_tot[2] = {0, -1};
@@ -356,8 +363,7 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     if ((isect_count && ni > capacity) || ws_bytes < L.total) return XPR_ERR_CAPACITY;
     uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
     uint32_t *skey = reinterpret_cast<uint32_t *>(p + L.skey), *sprim = reinterpret_cast<uint32_t *>(p + L.sprim);
-    int32_t *len = reinterpret_cast<int32_t *>(key);     // the keys are dead once sorted into skey
-    int32_t *pair0 = reinterpret_cast<int32_t *>(prim);  // and the records once moved into sprim
+    int32_t *pair0 = reinterpret_cast<int32_t *>(prim);  // the records are dead once moved into sprim
     const int64_t warps = (n + 31) / 32;
     const unsigned eg = (unsigned)((warps * 32 + 255) / 256);
     if (items)
@@ -370,11 +376,7 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     s = launch_sort_u32_bits(key, prim, ns, 256, 0, 8, skey, sprim, nullptr, p + L.sort_ws,
                              sort_u32_onepass_workspace_bytes(ns), st);
     if (s != XPR_OK) return s;
-    if (ns > 0) {
-        span_len_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(skey, ns, len);
-        XPR_LAUNCH_CHECK("span_len_kernel");
-    }
-    s = launch_exclusive_scan(len, pair0, ns, p + L.part_s, tot + 2, st);
+    s = launch_scan(SpanLenItem{skey}, pair0, ns, p + L.part_s, tot + 2, st);
     if (s != XPR_OK) return s;
     if (!isect_count) {
         XPR_CUDA_TRY(cudaMemcpyAsync(&ni, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
