@@ -82,12 +82,14 @@ def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | 
     fused = fused and not rows and B.binsort_ok(cam0, cfg, V)
     ut = _is_ut(cfg)
     sd = None
+    # the key path needs the kept-tile counts; the rows binning finds the pair total in its span scan
+    want_cnt = not fused and not rows
     if ut:
         rec, sd, bbox, tc, cnt = B.xpr_project_ut_views(mu, scale, quat, opacity, sh, cams, ccfg, stream=stream,
-                                                        with_isect_count=not fused)
+                                                        with_isect_count=want_cnt)
     else:
         rec, bbox, tc, cnt = B.xpr_project_views(mu, scale, quat, opacity, sh, cams, ccfg, stream=stream,
-                                                 with_isect_count=not fused)
+                                                 with_isect_count=want_cnt)
     order = B.xpr_depth_order_views(rec, tc, n, V, workspace=ws.scratch("depth", L.xpr_depth_order_workspace(n * V),
                                                                          dev), stream=stream)
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)

@@ -697,16 +697,19 @@ int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprIte
     int64_t total = 0;
     bool binned = false;
     if (R > 0) {
-        // projection with the exact kept-tile counts, depth order per item
-        if ((s = launch_project_items(*prims, cams, items, n_items, *cfg, rec, bbox, tc, st, isect))) return s;
+        // projection (with the exact kept-tile counts for the key path; the rows binning finds the
+        // pair total in its span scan), depth order per item
+        if ((s = launch_project_items(*prims, cams, items, n_items, *cfg, rec, bbox, tc, st,
+                                      by_rows ? nullptr : isect)))
+            return s;
         if ((s = launch_depth_order_items(rec, tc, items, n_items, order, w + L.depth,
                                           depth_order_workspace_bytes(R), st)))
             return s;
     }
     if (R > 0 && by_rows) {
-        // binning and tile sort by rows (one synchronisation: the span and pair totals)
+        // binning and tile sort by rows (synchronises for the span total, then for the pair total)
         int64_t spans = 0;
-        s = launch_bin_rows(rec, bbox, tc, isect, order, R, rt, *cfg, ranges, vals, capacity, &total, &spans, bin,
+        s = launch_bin_rows(rec, bbox, tc, nullptr, order, R, rt, *cfg, ranges, vals, capacity, &total, &spans, bin,
                             L.bin_bytes, st);
         *n_isect = total;
         if (s == XPR_OK) binned = true;
@@ -714,7 +717,10 @@ int xpr_forward_items(const XprPrims *prims, const XprCamera *cams, const XprIte
         else if (total > capacity)
             return fail(XPR_ERR_CAPACITY, "xpr_forward_items: %lld intersections > capacity %lld", (long long)total,
                         (long long)capacity);
-        // else the spans outgrew their room: the key path below gives the same lists
+        // else the spans outgrew their room: the key path below gives the same lists, from the
+        // kept-tile counts (the projection again, now with them: the same records)
+        else if ((s = launch_project_items(*prims, cams, items, n_items, *cfg, rec, bbox, tc, st, isect)))
+            return s;
     }
     if (!binned) {
         int32_t *offsets = reinterpret_cast<int32_t *>(bin + L.k_offsets);

@@ -30,13 +30,18 @@ class Workspace:
     xpr_tile_bin) and the transient scratch of xpr_tile_bin / xpr_sort.  Per-frame outputs are
     fresh tensors from PyTorch's caching allocator, so a Frame stays valid after later calls."""
 
-    def __init__(self, fused: bool = False, rows: bool = True):
+    def __init__(self, fused: bool = False, rows: bool = True, rows_counts: bool = False):
         self.last_isect = 0
         self.last_spans = 0
         self.bufs = {}
         self.fused = fused  # xpr_bin_sorted (True) or xpr_tile_bin + xpr_sort_tiles (False)
         # with fused False: xpr_bin_rows where the grid allows it (True), else the key path
         self.rows = rows
+        # binning by rows: the projection also counts each primitive's kept tiles (True: the pair
+        # total is read back with the span total), or the pair total comes from the span scan (False,
+        # the default: the count costs the projection 35 us on the 1M / 1080p headline, the second
+        # read-back the binning 7 us)
+        self.rows_counts = rows_counts
         self.sh_events = None  # set by a caller whose SH copy is still in flight (consumed by one forward)
         # set by a caller whose inputs are still in pinned host memory: (host (mu, scale, quat,
         # opacity, sh), copy stream); the forward brings them over itself (consumed by one forward)
@@ -96,8 +101,9 @@ _NO_TIMERS = _NoTimers()
 class Frame:
     """Everything the forward produces (kept for the backward and for tests).  On the key path the
     pairs are emitted in depth order, so `tiles` (u32 tile ids, int32 storage) sorted stably by
-    tile give the (tile, depth) order of Sec. 4.2; the fused path produces `vals_sorted` and
-    `ranges` directly and leaves isect_count, offsets, tiles, vals and tiles_sorted as None."""
+    tile give the (tile, depth) order of Sec. 4.2; the fused path and the binning by rows produce
+    `vals_sorted` and `ranges` directly and leave offsets, tiles, vals and tiles_sorted as None (and
+    isect_count, unless the workspace asks the rows path for the kept counts)."""
     rec: torch.Tensor
     bbox: torch.Tensor
     tile_count: torch.Tensor
@@ -153,6 +159,7 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     ut, lp = is_ut(cfg), is_lp(cfg)
     fused = fused and not lp  # LinPrim is binned by xpr_tile_bin_lp
     rows = not fused and not keep_sorted_tiles and getattr(ws, "rows", True) and B.bin_rows_ok(cam, cfg)
+    want_cnt = not fused and (not rows or getattr(ws, "rows_counts", True))
     sd = None
     deferred = sh_events is not None and not (ut or lp)
     from_host = host_inputs is not None and not (ut or lp)
@@ -165,19 +172,19 @@ def forward_frame(mu, scale, quat, opacity, sh, cam, cfg, ws: Workspace | None =
     tm.start("project", stream)
     if ut:
         rec, sd, bbox, tc, cnt = B.xpr_project_ut(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream,
-                                                  with_isect_count=not fused)
+                                                  with_isect_count=want_cnt)
     elif lp:
         rec, sd, bbox, tc, cnt = B.xpr_project_lp(mu, scale, quat, opacity, sh, ccam, ccfg, stream=stream)
     elif from_host:
         hs, cs = host_inputs
         out = B.xpr_project_host(hs[:4], (mu, scale, quat, opacity, None), ccam, ccfg, stream=stream,
-                                 with_isect_count=not fused)
+                                 with_isect_count=want_cnt)
         rec, bbox, tc = out[:3]
         cnt = out[3] if len(out) > 3 else None
         sh_events = _copy_on(cs, (sh,), hs[4:], stream)  # after the projection: the host link is free
     else:
         out = B.xpr_project(mu, scale, quat, opacity, None if deferred else sh, ccam, ccfg, stream=stream,
-                            with_isect_count=not fused)
+                            with_isect_count=want_cnt)
         rec, bbox, tc = out[:3]
         cnt = out[3] if len(out) > 3 else None
     tm.stop("project", stream)

@@ -222,7 +222,7 @@ def test_projection_from_pinned_host_equals_resident():
     cam = scenes.pinhole(320, 180, 320.0, scenes.yaw_view(3.0, (0.02, 0.0, 0.05)))
     cfg = scenes.RenderConfig(sh_degree=3, bg=(0.2, 0.1, 0.0))
     P = [t.requires_grad_(True) for t in R.scene_to_device(sc)]
-    ref = R.forward_frame(*[p.detach() for p in P], cam, cfg)
+    ref = R.forward_frame(*[p.detach() for p in P], cam, cfg, R.Workspace(rows_counts=True))
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in sc.arrays()]
     up = R.Uploader()
     dst = [torch.zeros_like(p.detach()) for p in P]
@@ -232,7 +232,7 @@ def test_projection_from_pinned_host_equals_resident():
     for d, h in zip(dst[:4], host[:4]):
         assert torch.equal(d.cpu(), h)
     dst = [torch.zeros_like(p.detach()) for p in P]
-    fr = R.forward_frame(*dst, cam, cfg, host_inputs=(host, up.stream))
+    fr = R.forward_frame(*dst, cam, cfg, R.Workspace(rows_counts=True), host_inputs=(host, up.stream))
     for name in ("rec", "bbox", "tile_count", "isect_count", "vals_sorted", "ranges", "image", "t_final", "n_contrib"):
         assert torch.equal(getattr(ref, name), getattr(fr, name)), name
     w = torch.from_numpy(np.random.default_rng(5).normal(size=tuple(ref.image.shape)).astype(np.float32)).cuda()
