@@ -14,8 +14,10 @@
  *   - All array pointers are DEVICE pointers (CUDA global memory) unless the
  *     comment says "host".  The caller allocates and owns every buffer; the
  *     library never allocates device memory and keeps no state between calls
- *     except a per-host-thread last-error string and a process-wide counter
- *     of launched kernels.
+ *     except a per-host-thread last-error string, a process-wide counter of
+ *     launched kernels and, per host thread and device, a 64-byte page-locked
+ *     host buffer with two events for the counts the binning by rows reads
+ *     back.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *     enqueued asynchronously on it; entry points that must return a count to
  *     the host (xpr_tile_bin, xpr_bin_sorted, xpr_bin_rows) synchronise that
@@ -463,8 +465,13 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
  *     xpr_bin_rows_workspace(n, S, I, cam, cfg), the call returns
  *     XPR_ERR_CAPACITY with both counts set and without writing vals or
  *     ranges; call again with enough of both.
- * The call synchronises the stream once with isect_count (twice without).
- * Grids with more than 128 tile columns or rows are rejected with
+ * The counts are read back at two points (the span total, and the pair
+ * total: with the span total when isect_count is given, else from the
+ * emission).  When the workspace holds room for `capacity` pairs and some
+ * span slots, the host waits for each count through an event while the
+ * kernels that do not need it are already queued (the emission is bounded by
+ * that room); otherwise it synchronises the stream before the work that
+ * needs the count.  Grids with more than 128 tile columns or rows are rejected with
  * XPR_ERR_INVALID (use xpr_tile_bin + xpr_sort_tiles for them).
  * workspace (device, 256-byte aligned, caller-owned):
  * xpr_bin_rows_workspace(n, S, I, cam, cfg) bytes (0 for invalid arguments);

@@ -68,63 +68,81 @@ struct CountItem {  // the kept tile counts, summed for the pair total
 };
 
 // Warp w takes the positions w, w + nw, ... (interleaved over the depth order, as the pair
-// emission does) and flattens their box rows over its lanes; each row's span goes to its slot.
-// With items, each lane's image size and item travel with its rows through the shuffles.
+// emission does) and flattens their box rows over its lanes; each row's span goes to its slot
+// (slots at or beyond ns_cap are not written: the launch may precede the check of the slot total
+// against the workspace).  With items, each lane's image size and item travel with its rows
+// through the shuffles.  pair_total (may be NULL): receives the sum of the kept counts.
 template <bool ITEMS>
 __global__ void __launch_bounds__(256) span_emit_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
                                                         const int *__restrict__ tcount,
                                                         const int *__restrict__ order, int64_t n, Grid g, RowItems t,
-                                                        const int32_t *__restrict__ slot0,
+                                                        const int32_t *__restrict__ slot0, int64_t ns_cap,
                                                         uint32_t *__restrict__ span_key,
-                                                        uint32_t *__restrict__ span_prim) {
+                                                        uint32_t *__restrict__ span_prim,
+                                                        unsigned long long *__restrict__ pair_total) {
+    __shared__ unsigned long long s_pairs;
+    if (threadIdx.x == 0) s_pairs = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nw = (n + 31) / 32;
     const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= nw) return;
-    const int64_t j = w + (int64_t)lane * nw;
-    int i = 0, area = 0, base = 0, k = 0;
-    int4 bb = make_int4(0, 0, 0, 0);
-    CullData d = {};
-    Grid gl = g;
-    if (j < n) {
-        i = order[j];
-        base = slot0[j];
-        if (ITEMS) {
-            k = item_of_record(t, i);
-            gl.W = t.W[k];
-            gl.H = t.H[k];
-            gl.Wt = t.Wt[k];
-            gl.Ht = t.Ht[k];
+    int kept = 0;
+    if (w < nw) {
+        const int64_t j = w + (int64_t)lane * nw;
+        int i = 0, area = 0, base = 0, k = 0;
+        int4 bb = make_int4(0, 0, 0, 0);
+        CullData d = {};
+        Grid gl = g;
+        if (j < n) {
+            i = order[j];
+            base = slot0[j];
+            if (ITEMS) {
+                k = item_of_record(t, i);
+                gl.W = t.W[k];
+                gl.H = t.H[k];
+                gl.Wt = t.Wt[k];
+                gl.Ht = t.Ht[k];
+            }
+            area = box_of(bbox, tcount, i, gl, bb);
+            if (area > 0) d = load_cull(rec, i);
         }
-        area = box_of(bbox, tcount, i, gl, bb);
-        if (area > 0) d = load_cull(rec, i);
+        const int h = area > 0 ? bb.w - bb.y : 0;
+        const int incl = warp_incl_scan(h);
+        const int rows = __shfl_sync(kFullMask, incl, 31);
+        const int excl = incl - h;
+        for (int f0 = 0; f0 < rows; f0 += 32) {
+            const int f = f0 + lane;
+            const int p = lane_of(incl, f);
+            const CullData e = shfl_cull(d, p);
+            const int excl_p = __shfl_sync(kFullMask, excl, p);
+            const int ty = __shfl_sync(kFullMask, bb.y, p) + f - excl_p;
+            const int x0 = __shfl_sync(kFullMask, bb.x, p), x1 = __shfl_sync(kFullMask, bb.z, p);
+            const int base_p = __shfl_sync(kFullMask, base, p), i_p = __shfl_sync(kFullMask, i, p);
+            Grid gp = g;
+            uint32_t item = 0;
+            if (ITEMS) {
+                gp.W = __shfl_sync(kFullMask, gl.W, p);
+                gp.H = __shfl_sync(kFullMask, gl.H, p);
+                item = (uint32_t)__shfl_sync(kFullMask, k, p) << kSpanItemShift;
+            }
+            if (f < rows) {
+                int ka = 0, kb = -1;
+                const int c = row_span_in_box(e, gp, ty, x0, x1, ka, kb);
+                const int64_t s = (int64_t)base_p + (f - excl_p);
+                if (s < ns_cap) {
+                    span_key[s] = c > 0 ? item | ((uint32_t)c << 15) | ((uint32_t)ka << 8) | (uint32_t)ty : kRowNone;
+                    span_prim[s] = (uint32_t)i_p;
+                }
+                kept += c;
+            }
+        }
     }
-    const int h = area > 0 ? bb.w - bb.y : 0;
-    const int incl = warp_incl_scan(h);
-    const int rows = __shfl_sync(kFullMask, incl, 31);
-    const int excl = incl - h;
-    for (int f0 = 0; f0 < rows; f0 += 32) {
-        const int f = f0 + lane;
-        const int p = lane_of(incl, f);
-        const CullData e = shfl_cull(d, p);
-        const int excl_p = __shfl_sync(kFullMask, excl, p);
-        const int ty = __shfl_sync(kFullMask, bb.y, p) + f - excl_p;
-        const int x0 = __shfl_sync(kFullMask, bb.x, p), x1 = __shfl_sync(kFullMask, bb.z, p);
-        const int base_p = __shfl_sync(kFullMask, base, p), i_p = __shfl_sync(kFullMask, i, p);
-        Grid gp = g;
-        uint32_t item = 0;
-        if (ITEMS) {
-            gp.W = __shfl_sync(kFullMask, gl.W, p);
-            gp.H = __shfl_sync(kFullMask, gl.H, p);
-            item = (uint32_t)__shfl_sync(kFullMask, k, p) << kSpanItemShift;
-        }
-        if (f < rows) {
-            int ka = 0, kb = -1;
-            const int c = row_span_in_box(e, gp, ty, x0, x1, ka, kb);
-            const int64_t s = (int64_t)base_p + (f - excl_p);
-            span_key[s] = c > 0 ? item | ((uint32_t)c << 15) | ((uint32_t)ka << 8) | (uint32_t)ty : kRowNone;
-            span_prim[s] = (uint32_t)i_p;
-        }
+    if (pair_total) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(kFullMask, kept, o);
+        if (lane == 0 && kept) atomicAdd(&s_pairs, (unsigned long long)kept);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_pairs) atomicAdd(pair_total, s_pairs);
     }
 }
 
@@ -303,11 +321,64 @@ size_t bin_rows_workspace_bytes(int64_t n_records, int64_t n_spans, int64_t n_is
     return rows_layout(n_records, n_spans, n_isect, t).total;
 }
 
+namespace {
+
+// The largest span-slot room the workspace holds beside room for `capacity` pairs (-1: none).
+int64_t span_room(int64_t n, int64_t capacity, const RowItems &t, size_t ws_bytes) {
+    if (rows_layout(n, 0, capacity, t).total > ws_bytes) return -1;
+    int64_t lo = 0, hi = 0x7fffffffLL;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (rows_layout(n, mid, capacity, t).total <= ws_bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per host thread and device: a page-locked buffer for the counts the binning reads back and two
+// events that mark when each count has landed, so the host waits on a count while the kernels
+// that do not need it are already queued behind it.  NULL when they cannot be created.
+struct Readback {
+    int64_t *host = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+Readback *readback_slots() {
+    constexpr int kDevices = 64;
+    thread_local Readback r[kDevices];
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    Readback &s = r[dev];
+    if (!s.host) {
+        void *h = nullptr;
+        if (cudaHostAlloc(&h, 64, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (auto &e : s.ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;  // the buffer stays for the next attempt
+            }
+        s.host = reinterpret_cast<int64_t *>(h);
+    }
+    return &s;
+}
+
+}  // namespace
+
 // order: the depth order of the n records (each item's in its own block); isect_count (NULL: none):
-// their kept tile counts, whose total is read back with the span count (one synchronisation) so
-// that both capacities are checked before any span is written.  Returns XPR_ERR_CAPACITY
-// (n_isect, n_spans set, nothing written) when vals holds fewer than n_isect pairs or the
-// workspace is below bin_rows_workspace_bytes.
+// their kept tile counts.  The span total (and, with isect_count, the pair total) is read back
+// after the scan of the box heights, the pair total otherwise from the emission.  When the
+// workspace has room for `capacity` pairs and some span slots, the emission is queued before the
+// host reads the span total (its writes bounded by that room) and the span sort before it reads
+// the pair total, so the device does not idle while the host waits; otherwise each count is read
+// with the stream synchronised before the work that needs it.  Returns XPR_ERR_CAPACITY (n_isect
+// and n_spans set as far as known, vals and ranges unwritten) when vals holds fewer than n_isect
+// pairs or the workspace is below bin_rows_workspace_bytes.
 int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, const int32_t *isect_count,
                     const int32_t *order, int64_t n, const RowItems &t, const XprConfig &cfg, int32_t *ranges,
                     uint32_t *vals, int64_t capacity, int64_t *n_isect, int64_t *n_spans, void *ws, size_t ws_bytes,
@@ -335,56 +406,89 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     if (ws_bytes < L0.total) return fail(XPR_ERR_INVALID, "xpr_bin_rows: workspace %zu < %zu bytes", ws_bytes, L0.total);
     char *p = reinterpret_cast<char *>(ws);
     int32_t *slot0 = reinterpret_cast<int32_t *>(p + L0.slot0);
-    int64_t *tot = reinterpret_cast<int64_t *>(p + L0.totals);
-    // span slot offsets: the scan of the box heights in depth order (the heights computed in the
-    // scan's own reads); the pair total: the sum of the kept counts
+    int64_t *tot = reinterpret_cast<int64_t *>(p + L0.totals);  // span total, kept total, pair total, emitted pairs
     const int4 *bb4 = reinterpret_cast<const int4 *>(bbox);
+    const int64_t ns_cap = span_room(n, capacity, t, ws_bytes);
+    Readback *rb = ns_cap >= 0 ? readback_slots() : nullptr;
+    // span slot offsets: the scan of the box heights in depth order (the heights computed in the
+    // scan's own reads); with the kept counts, the pair total is their sum
     int s = items ? launch_scan(BoxRowsItem<true>{bb4, tc, order, g, t}, slot0, n, p + L0.part_n, tot, st)
                   : launch_scan(BoxRowsItem<false>{bb4, tc, order, g, t}, slot0, n, p + L0.part_n, tot, st);
     if (s != XPR_OK) return s;
     if (isect_count) {
         s = launch_scan(CountItem{isect_count}, nullptr, n, p + L0.part_n, tot + 1, st);
         if (s != XPR_OK) return s;
+    } else if (rb) {
+        XPR_CUDA_TRY(cudaMemsetAsync(tot + 3, 0, sizeof(int64_t), st));
     }
-    int64_t h_tot[2] = {0, -1};
-    XPR_CUDA_TRY(cudaMemcpyAsync(h_tot, tot, (isect_count ? 2 : 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    XPR_CUDA_TRY(cudaStreamSynchronize(st));
-    const int64_t ns = h_tot[0];
+    auto emit = [&](const RowsLayout &L, int64_t room, unsigned long long *pairs) -> int {
+        uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
+        const unsigned eg = (unsigned)(((n + 31) / 32 * 32 + 255) / 256);
+        if (items)
+            span_emit_kernel<true><<<eg, 256, 0, st>>>(rec, bb4, tc, order, n, g, t, slot0, room, key, prim, pairs);
+        else
+            span_emit_kernel<false><<<eg, 256, 0, st>>>(rec, bb4, tc, order, n, g, t, slot0, room, key, prim, pairs);
+        XPR_LAUNCH_CHECK("span_emit_kernel");
+        return XPR_OK;
+    };
+    int64_t ns = 0, ni = 0;
+    RowsLayout L;
+    bool early = rb != nullptr;
+    if (early) {
+        L = rows_layout(n, ns_cap, capacity, t);
+        XPR_CUDA_TRY(cudaMemcpyAsync(rb->host, tot, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        XPR_CUDA_TRY(cudaEventRecord(rb->ev[0], st));
+        if ((s = emit(L, ns_cap, isect_count ? nullptr : reinterpret_cast<unsigned long long *>(tot + 3)))) return s;
+        if (!isect_count) {
+            XPR_CUDA_TRY(cudaMemcpyAsync(rb->host + 2, tot + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            XPR_CUDA_TRY(cudaEventRecord(rb->ev[1], st));
+        }
+        XPR_CUDA_TRY(cudaEventSynchronize(rb->ev[0]));
+        ns = rb->host[0];
+        ni = isect_count ? rb->host[1] : 0;
+    } else {
+        int64_t h_tot[2] = {0, 0};
+        XPR_CUDA_TRY(cudaMemcpyAsync(h_tot, tot, (isect_count ? 2 : 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        XPR_CUDA_TRY(cudaStreamSynchronize(st));
+        ns = h_tot[0];
+        ni = isect_count ? h_tot[1] : 0;
+    }
     *n_spans = ns;
-    if (isect_count) *n_isect = h_tot[1];
-    if (ns > 0x7fffffffLL || h_tot[1] > 0x7fffffffLL)
-        return fail(XPR_ERR_CAPACITY, "xpr_bin_rows: more than 2^31 - 1 spans or pairs");
-    *n_spans = ns;
-    // without the kept counts the pair total is known only once the spans exist: the span phase
-    // is checked here (its regions do not depend on the pair count) and the pair phase after
-    int64_t ni = isect_count ? h_tot[1] : 0;
     if (isect_count) *n_isect = ni;
-    const RowsLayout L = rows_layout(n, ns, ni, t);
-    if ((isect_count && ni > capacity) || ws_bytes < L.total) return XPR_ERR_CAPACITY;
+    if (ns > 0x7fffffffLL || ni > 0x7fffffffLL)
+        return fail(XPR_ERR_CAPACITY, "xpr_bin_rows: more than 2^31 - 1 spans or pairs");
+    // the spans outgrew the room (or the pairs the capacity): on as if nothing had been queued
+    // early (the emission again, into the regions this count fixes), so that the counts reported
+    // are those of the synchronised protocol
+    if (early && (ns > ns_cap || (isect_count && ni > capacity))) early = false;
+    if (!early) {
+        // without the kept counts the pair total is known only once the spans exist: the span
+        // phase is checked here (its regions do not depend on the pair count) and the pair phase after
+        L = rows_layout(n, ns, ni, t);
+        if ((isect_count && ni > capacity) || ws_bytes < L.total) return XPR_ERR_CAPACITY;
+        if ((s = emit(L, ns, nullptr))) return s;
+    }
     uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
     uint32_t *skey = reinterpret_cast<uint32_t *>(p + L.skey), *sprim = reinterpret_cast<uint32_t *>(p + L.sprim);
     int32_t *pair0 = reinterpret_cast<int32_t *>(prim);  // the records are dead once moved into sprim
-    const int64_t warps = (n + 31) / 32;
-    const unsigned eg = (unsigned)((warps * 32 + 255) / 256);
-    if (items)
-        span_emit_kernel<true><<<eg, 256, 0, st>>>(rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, g, t,
-                                                   slot0, key, prim);
-    else
-        span_emit_kernel<false><<<eg, 256, 0, st>>>(rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, g, t,
-                                                    slot0, key, prim);
-    XPR_LAUNCH_CHECK("span_emit_kernel");
     s = launch_sort_u32_bits(key, prim, ns, 256, 0, 8, skey, sprim, nullptr, p + L.sort_ws,
                              sort_u32_onepass_workspace_bytes(ns), st);
     if (s != XPR_OK) return s;
     s = launch_scan(SpanLenItem{skey}, pair0, ns, p + L.part_s, tot + 2, st);
     if (s != XPR_OK) return s;
     if (!isect_count) {
-        XPR_CUDA_TRY(cudaMemcpyAsync(&ni, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        XPR_CUDA_TRY(cudaStreamSynchronize(st));
+        if (early) {
+            XPR_CUDA_TRY(cudaEventSynchronize(rb->ev[1]));
+            ni = rb->host[2];
+        } else {
+            XPR_CUDA_TRY(cudaMemcpyAsync(&ni, tot + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            XPR_CUDA_TRY(cudaStreamSynchronize(st));
+        }
         *n_isect = ni;
-        if (ni > capacity || ws_bytes < rows_layout(n, ns, ni, t).total) return XPR_ERR_CAPACITY;
+        if (ni > 0x7fffffffLL) return fail(XPR_ERR_CAPACITY, "xpr_bin_rows: more than 2^31 - 1 pairs");
+        if (ni > capacity || (!early && ws_bytes < rows_layout(n, ns, ni, t).total)) return XPR_ERR_CAPACITY;
     }
-    const RowsLayout LP = rows_layout(n, ns, ni, t);
+    const RowsLayout LP = early ? L : rows_layout(n, ns, ni, t);
     uint32_t *codes = reinterpret_cast<uint32_t *>(p + LP.codes), *pvals = reinterpret_cast<uint32_t *>(p + LP.pvals);
     const int64_t swarps = (ns + 31) / 32;
     if (ns > 0) {

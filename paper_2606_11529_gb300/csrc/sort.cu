@@ -26,7 +26,10 @@ namespace xpr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;               // keys per thread of the chained-scan kernels
+#ifndef XPR_CHAINED_ITEMS
+#define XPR_CHAINED_ITEMS 16
+#endif
+constexpr int kItems = XPR_CHAINED_ITEMS;  // keys per thread of the chained-scan kernels
 constexpr int kWarps = kThreads / 32;
 constexpr int kWarpKeys = 32 * kItems;    // 512
 constexpr int kTile = kThreads * kItems;  // 4096
@@ -666,7 +669,8 @@ inline bool is_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p)
 // digit counts with the block counters (reduce-then-scan: the digit totals).
 template <typename K>
 size_t workspace_bytes(int64_t n, int passes = kMaxPasses) {
-    const int64_t nb = max((int64_t)1, (n + kTileR - 1) / kTileR);  // kTileR < kTile: the larger count
+    const int64_t tk = kTileR < kTile ? kTileR : kTile;  // the smaller tile: the larger block count
+    const int64_t nb = max((int64_t)1, (n + tk - 1) / tk);
     const size_t alt = passes > 1 ? align256((size_t)n * sizeof(K)) + align256((size_t)n * 4) : 0;
     return alt + 2 * align256((size_t)nb * kRadix * 4) + align256((size_t)kMaxPasses * (kRadix + 1) * 4);
 }
