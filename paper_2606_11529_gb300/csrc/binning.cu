@@ -179,6 +179,15 @@ __global__ void depth_key_kernel(const float *__restrict__ rec, const int *__res
     vals[i] = (uint32_t)i;
 }
 
+// One view: the 32-bit key alone (half the key traffic of the sort's passes).
+__global__ void depth_key32_kernel(const float *__restrict__ rec, const int *__restrict__ tcount, int64_t n,
+                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = tcount[i] > 0 ? __float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]) : 0xffffffffu;
+    vals[i] = (uint32_t)i;
+}
+
 // Multi-scene items: the item of record i (its block [rec0[k], rec0[k + 1])) goes in bits 32..
 struct KeyItems {
     int count;
@@ -299,6 +308,13 @@ int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *
     uint64_t *keys = reinterpret_cast<uint64_t *>(p);
     uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
     void *sort_ws = p + 2 * a + b + 256;
+    if (n_views == 1) {  // the u64 key buffer holds the u32 keys; the u64 sort's scratch the u32 sort's
+        uint32_t *k32 = reinterpret_cast<uint32_t *>(keys);
+        depth_key32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, tc, n, k32, vals);
+        XPR_LAUNCH_CHECK("depth_key32_kernel");
+        return launch_sort_u32_bits(k32, vals, n, 1, 0, 32, nullptr, reinterpret_cast<uint32_t *>(order), nullptr,
+                                    sort_ws, sort_workspace_bytes(n, n_views), st);
+    }
     depth_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, tc, n, per_view, keys, vals);
     XPR_LAUNCH_CHECK("depth_key_kernel");
     // the sort's "tile" is the view: keys (view << 32 | depth bits) sort over 32 + ceil(log2 views) bits;
