@@ -50,6 +50,7 @@ def _is_ut(cfg) -> bool:
 class ViewsWorkspace:
     def __init__(self):
         self.last_isect = 0
+        self.last_spans = 0
         self.bufs = {}
         # consecutive view chunks a batch of these views is split into (grown when one batch would
         # hold more than 2^31 - 1 pairs, the limit of the 32-bit pair index)
@@ -96,9 +97,14 @@ def forward_views(mu, scale, quat, opacity, sh, cams, cfg, ws: ViewsWorkspace | 
     Wt, Ht = B.tiles_of(cam0, cfg)
     nt = V * Wt * Ht
     if rows:
-        ranges, vs, I, _, ws.bufs["rows"] = B.xpr_bin_rows_views(rec, bbox, tc, order, n, V, cam0, ccfg,
+        # room for the pairs asked for and a quarter more span slots than last time, so that the
+        # binning queues its work ahead of the counts it reads back
+        need = B.bin_rows_views_workspace_bytes(n, V, int(ws.last_spans * 1.25) + 1024, cap, cam0, ccfg)
+        ranges, vs, I, S, ws.bufs["rows"] = B.xpr_bin_rows_views(rec, bbox, tc, order, n, V, cam0, ccfg,
                                                                  isect_count=cnt, capacity=cap,
-                                                                 workspace=ws.bufs.get("rows"), stream=stream)
+                                                                 workspace=ws.scratch("rows", need, dev),
+                                                                 stream=stream)
+        ws.last_spans = S
     elif fused:
         ranges, vs, I = B.xpr_bin_sorted(rec, bbox, tc, order, n, cam0, ccfg, n_views=V, capacity=cap,
                                          workspace=ws.scratch("binsort", B.bin_sorted_workspace_bytes(
@@ -298,8 +304,11 @@ def forward_items(mu, scale, quat, opacity, sh, layout, cfg, ws: ViewsWorkspace 
         layout.R), dev), stream=stream)
     cap = max(int(ws.last_isect * 1.25) + 1024, 1024)
     if rows and B.bin_rows_items_ok(layout, cfg):
-        ranges, vs, I, _, ws.bufs["rows"] = B.xpr_bin_rows_items(rec, bbox, tc, order, layout, ccfg, capacity=cap,
-                                                                 workspace=ws.bufs.get("rows"), stream=stream)
+        need = B.bin_rows_items_workspace_bytes(layout, int(ws.last_spans * 1.25) + 1024, cap, ccfg)
+        ranges, vs, I, S, ws.bufs["rows"] = B.xpr_bin_rows_items(rec, bbox, tc, order, layout, ccfg, capacity=cap,
+                                                                 workspace=ws.scratch("rows", need, dev),
+                                                                 stream=stream)
+        ws.last_spans = S
     else:
         ranges, vs, I = B.xpr_bin_sorted_items(rec, bbox, tc, order, layout, ccfg, capacity=cap,
                                                workspace=ws.scratch("binsort", B.bin_sorted_items_workspace_bytes(

@@ -612,7 +612,9 @@ def _bin_rows_retry(name, call, need, n_tiles, dev, cap, workspace):
         if s == XPR_ERR_CAPACITY and got_i.value <= 0x7FFFFFFF and got_s.value <= 0x7FFFFFFF:
             if got_i.value > vals.numel():
                 vals = torch.empty(got_i.value, dtype=torch.int32, device=dev)
-            n1 = need(got_s.value, got_i.value)
+            # room for a quarter more span slots beside the pairs: the calls that follow (the next
+            # frame) then find it and queue their work ahead of the counts they read back
+            n1 = need(int(got_s.value * 1.25) + 1024, max(got_i.value, vals.numel()))
             if workspace.numel() < n1:
                 workspace = torch.empty(n1, dtype=torch.uint8, device=dev)
             continue
