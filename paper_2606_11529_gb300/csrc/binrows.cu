@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) span_emit_kernel(const float *__restrict_
                                                         uint32_t *__restrict__ span_key,
                                                         uint32_t *__restrict__ span_prim,
                                                         unsigned long long *__restrict__ pair_total) {
+    grid_dep_wait();
     __shared__ unsigned long long s_pairs;
     if (threadIdx.x == 0) s_pairs = 0;
     __syncthreads();
@@ -155,6 +156,7 @@ __global__ void __launch_bounds__(256) span_expand_kernel(const uint32_t *__rest
                                                           const uint32_t *__restrict__ sprim, int64_t ns,
                                                           const int32_t *__restrict__ pair0, int64_t capacity,
                                                           uint32_t *__restrict__ codes, uint32_t *__restrict__ vals) {
+    grid_dep_wait();
     __shared__ uint2 s_sp[8][32];  // per warp: the non-empty spans' (first code, primitive)
     __shared__ int s_x[8][32];     // and the index of their first pair in the warp's list
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -206,6 +208,7 @@ struct SpanLenItem {  // scan items: the pairs of sorted span q
 // ranges[tile0[k] + ty Wt[k] + tx] = the range found for tile code (k << 14) | (tx << 7) | ty
 __global__ void permute_ranges_kernel(const int2 *__restrict__ by_code, RowItems t, int64_t n_tiles,
                                       int2 *__restrict__ ranges) {
+    grid_dep_wait();
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gt >= n_tiles) return;
     int k = 0;
@@ -424,10 +427,9 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     auto emit = [&](const RowsLayout &L, int64_t room, unsigned long long *pairs) -> int {
         uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
         const unsigned eg = (unsigned)(((n + 31) / 32 * 32 + 255) / 256);
-        if (items)
-            span_emit_kernel<true><<<eg, 256, 0, st>>>(rec, bb4, tc, order, n, g, t, slot0, room, key, prim, pairs);
-        else
-            span_emit_kernel<false><<<eg, 256, 0, st>>>(rec, bb4, tc, order, n, g, t, slot0, room, key, prim, pairs);
+        XPR_CUDA_TRY(launch_dependent(items ? span_emit_kernel<true> : span_emit_kernel<false>, dim3(eg), dim3(256),
+                                      0, st, rec, bb4, tc, order, n, g, t, (const int32_t *)slot0, room, key, prim,
+                                      pairs));
         XPR_LAUNCH_CHECK("span_emit_kernel");
         return XPR_OK;
     };
@@ -492,8 +494,9 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     uint32_t *codes = reinterpret_cast<uint32_t *>(p + LP.codes), *pvals = reinterpret_cast<uint32_t *>(p + LP.pvals);
     const int64_t swarps = (ns + 31) / 32;
     if (ns > 0) {
-        span_expand_kernel<<<(unsigned)((swarps * 32 + 255) / 256), 256, 0, st>>>(skey, sprim, ns, pair0, ni, codes,
-                                                                                  pvals);
+        XPR_CUDA_TRY(launch_dependent(span_expand_kernel, dim3((unsigned)((swarps * 32 + 255) / 256)), dim3(256), 0,
+                                      st, (const uint32_t *)skey, (const uint32_t *)sprim, ns,
+                                      (const int32_t *)pair0, ni, codes, pvals));
         XPR_LAUNCH_CHECK("span_expand_kernel");
     }
     const int64_t nc = n_codes(t);
@@ -503,8 +506,8 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
                              sort_u32_onepass_workspace_bytes(ni), st);
     if (s != XPR_OK) return s;
     if (T > 0) {
-        permute_ranges_kernel<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(by_code, t, T,
-                                                                            reinterpret_cast<int2 *>(ranges));
+        XPR_CUDA_TRY(launch_dependent(permute_ranges_kernel, dim3((unsigned)((T + 255) / 256)), dim3(256), 0, st,
+                                      (const int2 *)by_code, t, T, reinterpret_cast<int2 *>(ranges)));
         XPR_LAUNCH_CHECK("permute_ranges_kernel");
     }
     return XPR_OK;

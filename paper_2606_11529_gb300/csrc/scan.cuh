@@ -54,6 +54,7 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *smem
 
 template <class F>
 __global__ void __launch_bounds__(kThreads) reduce_kernel(F f, int64_t n, int64_t *__restrict__ partials) {
+    grid_dep_wait();
     __shared__ int64_t sw[32];
     const int64_t base = (int64_t)blockIdx.x * kTile;
     int64_t s = 0;
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(F f, int64_t n, int64_
 
 __global__ void __launch_bounds__(kThreads) partials_kernel(int64_t *__restrict__ partials, int64_t nb,
                                                             int64_t *__restrict__ total_out) {
+    grid_dep_wait();
     __shared__ int64_t sw[32];
     int64_t carry = 0;
     for (int64_t base = 0; base < nb; base += kThreads) {
@@ -86,6 +88,7 @@ template <class F>
 __global__ void __launch_bounds__(kThreads) downsweep_kernel(F f, int32_t *out, int64_t n,
                                                              const int64_t *__restrict__ partials,
                                                              const int64_t *__restrict__ total) {
+    grid_dep_wait();
     __shared__ int32_t s_v[kPad];
     __shared__ int64_t sw[32];
     const int64_t base = (int64_t)blockIdx.x * kTile;
@@ -137,12 +140,13 @@ int launch_scan(F f, int32_t *out, int64_t n, void *partials, int64_t *total_out
         XPR_CUDA_TRY(cudaMemsetAsync(tot, 0, sizeof(int64_t), st));
         return XPR_OK;
     }
-    reduce_kernel<F><<<(unsigned)nb, kThreads, 0, st>>>(f, n, part);
+    XPR_CUDA_TRY(launch_dependent(reduce_kernel<F>, dim3((unsigned)nb), dim3(kThreads), 0, st, f, n, part));
     XPR_LAUNCH_CHECK("scan reduce_kernel");
-    partials_kernel<<<1, kThreads, 0, st>>>(part, nb, tot);
+    XPR_CUDA_TRY(launch_dependent(partials_kernel, dim3(1), dim3(kThreads), 0, st, part, nb, tot));
     XPR_LAUNCH_CHECK("scan partials_kernel");
     if (out) {
-        downsweep_kernel<F><<<(unsigned)nb, kThreads, 0, st>>>(f, out, n, part, tot);
+        XPR_CUDA_TRY(launch_dependent(downsweep_kernel<F>, dim3((unsigned)nb), dim3(kThreads), 0, st, f, out, n,
+                                      (const int64_t *)part, (const int64_t *)tot));
         XPR_LAUNCH_CHECK("scan downsweep_kernel");
     }
     return XPR_OK;

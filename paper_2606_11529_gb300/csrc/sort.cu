@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(kThreads) sort_hist_kernel(const K *__restrict
 template <typename K>
 __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const K *__restrict__ kin, int64_t n, int shift,
                                                               uint32_t mask, int32_t *__restrict__ hist, bool vec) {
+    grid_dep_wait();
     __shared__ int s[kWarps][kRadix];
     for (int d = threadIdx.x; d < kWarps * kRadix; d += kThreads) (&s[0][0])[d] = 0;
     __syncthreads();
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const K *__restric
 // Column scan of the (block x digit) matrix, step 1: part[g][d] = sum of rows [32 g, 32 g + 32).
 __global__ void __launch_bounds__(kRadix) colsum_kernel(const int32_t *__restrict__ hist, int64_t nb,
                                                         int32_t *__restrict__ part) {
+    grid_dep_wait();
     const int64_t g = blockIdx.x;
     const int64_t r0 = g * kSegRows, r1 = min(r0 + kSegRows, nb);
     const int32_t *h = hist + r0 * kRadix + threadIdx.x;
@@ -244,6 +246,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *s_warp, int *total) {
 // the digit's total.
 __global__ void __launch_bounds__(1024) segscan_kernel(int32_t *__restrict__ part, int64_t nseg,
                                                        int32_t *__restrict__ dtot) {
+    grid_dep_wait();
     __shared__ int s_warp[32];
     const int d = blockIdx.x;
     int carry = 0;
@@ -262,6 +265,7 @@ __global__ void __launch_bounds__(1024) segscan_kernel(int32_t *__restrict__ par
 __global__ void __launch_bounds__(kRadix) colapply_kernel(int32_t *__restrict__ hist, int64_t nb,
                                                           const int32_t *__restrict__ part,
                                                           const int32_t *__restrict__ dtot) {
+    grid_dep_wait();
     __shared__ int s_warp[32];
     const int64_t g = blockIdx.x;
     const int d = threadIdx.x;
@@ -500,6 +504,7 @@ __global__ void __launch_bounds__(kThreads, 4) radix_scatter_kernel(const K *__r
                                                                  int64_t n, int shift, uint32_t mask,
                                                                  const int32_t *__restrict__ offs,
                                                                  int2 *__restrict__ ranges, uint32_t n_tiles) {
+    grid_dep_wait();
     extern __shared__ __align__(16) unsigned char smem[];
     K *s_key = reinterpret_cast<K *>(smem);
     uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + (size_t)kTileR * sizeof(K));
@@ -609,11 +614,13 @@ __global__ void __launch_bounds__(kThreads, 4) radix_scatter_kernel(const K *__r
 }
 
 __global__ void init_ranges_kernel(int2 *__restrict__ ranges, int n_tiles) {
+    grid_dep_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n_tiles) ranges[t] = make_int2(0x7fffffff, 0);
 }
 
 __global__ void fix_empty_ranges_kernel(int2 *__restrict__ ranges, int n_tiles) {
+    grid_dep_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n_tiles && ranges[t].x == 0x7fffffff) ranges[t] = make_int2(0, 0);
 }
@@ -749,7 +756,7 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
     }
     const unsigned tgrid = (unsigned)((n_tiles + 255) / 256);
     if (rg) {
-        init_ranges_kernel<<<tgrid, 256, 0, st>>>(rg, n_tiles);
+        XPR_CUDA_TRY(launch_dependent(init_ranges_kernel, dim3(tgrid), dim3(256), 0, st, rg, (int)n_tiles));
         XPR_LAUNCH_CHECK("init_ranges_kernel");
     }
     if (chained) {
@@ -786,19 +793,22 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
             int32_t *part = reinterpret_cast<int32_t *>(mat[1]);
             int32_t *dtot = reinterpret_cast<int32_t *>(ghist);
             const uint32_t mask = (1u << nbits) - 1u;
-            radix_hist_kernel<K><<<(unsigned)nb, kThreads, 0, st>>>(src_k, n, shift, mask, hist,
-                                                                    is_aligned16(src_k));
+            XPR_CUDA_TRY(launch_dependent(radix_hist_kernel<K>, dim3((unsigned)nb), dim3(kThreads), 0, st, src_k, n,
+                                          shift, mask, hist, is_aligned16(src_k)));
             XPR_LAUNCH_CHECK("radix_hist_kernel");
-            colsum_kernel<<<(unsigned)nseg, kRadix, 0, st>>>(hist, nb, part);
+            XPR_CUDA_TRY(launch_dependent(colsum_kernel, dim3((unsigned)nseg), dim3(kRadix), 0, st,
+                                          (const int32_t *)hist, nb, part));
             XPR_LAUNCH_CHECK("colsum_kernel");
-            segscan_kernel<<<kRadix, 1024, 0, st>>>(part, nseg, dtot);
+            XPR_CUDA_TRY(launch_dependent(segscan_kernel, dim3(kRadix), dim3(1024), 0, st, part, nseg, dtot));
             XPR_LAUNCH_CHECK("segscan_kernel");
-            colapply_kernel<<<(unsigned)nseg, kRadix, 0, st>>>(hist, nb, part, dtot);
+            XPR_CUDA_TRY(launch_dependent(colapply_kernel, dim3((unsigned)nseg), dim3(kRadix), 0, st, hist, nb,
+                                          (const int32_t *)part, (const int32_t *)dtot));
             XPR_LAUNCH_CHECK("colapply_kernel");
             XPR_CUDA_TRY(cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)scatter_smem<K>()));
-            radix_scatter_kernel<K><<<(unsigned)nb, kThreads, scatter_smem<K>(), st>>>(
-                src_k, src_v, dst_k, dst_v, n, shift, mask, hist, last ? rg : nullptr, (uint32_t)n_tiles);
+            XPR_CUDA_TRY(launch_dependent(radix_scatter_kernel<K>, dim3((unsigned)nb), dim3(kThreads), scatter_smem<K>(), st,
+                                          src_k, src_v, dst_k, dst_v, n, shift, mask, (const int32_t *)hist,
+                                          last ? rg : (int2 *)nullptr, (uint32_t)n_tiles));
             XPR_LAUNCH_CHECK("radix_scatter_kernel");
             s = XPR_OK;
         }
@@ -807,7 +817,7 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
         src_v = dst_v;
     }
     if (rg) {
-        fix_empty_ranges_kernel<<<tgrid, 256, 0, st>>>(rg, n_tiles);
+        XPR_CUDA_TRY(launch_dependent(fix_empty_ranges_kernel, dim3(tgrid), dim3(256), 0, st, rg, (int)n_tiles));
         XPR_LAUNCH_CHECK("fix_empty_ranges_kernel");
     }
     return XPR_OK;

@@ -28,6 +28,30 @@ int check_launch(const char *what);
 
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Programmatic dependent launch: a kernel launched with launch_dependent may be set up on the
+// device while the kernel before it in the stream is still finishing, and waits in grid_dep_wait()
+// (its first statement, before any read of what earlier work wrote) until that kernel has
+// completed and its writes are visible.  Kernels that call grid_dep_wait() may also be launched
+// the ordinary way, where the wait returns at once.
+#ifdef __CUDACC__
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+template <typename... Params, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    Args... args) {
+    cudaLaunchConfig_t c = {};
+    c.gridDim = grid;
+    c.blockDim = block;
+    c.dynamicSmemBytes = smem;
+    c.stream = st;
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a[0].val.programmaticStreamSerializationAllowed = 1;
+    c.attrs = a;
+    c.numAttrs = 1;
+    return cudaLaunchKernelEx(&c, kernel, static_cast<Params>(args)...);
+}
+
 __host__ __device__ inline int tiles_x(const XprCamera &c, const XprConfig &g) {
     return (c.width + g.tile_w - 1) / g.tile_w;
 }
