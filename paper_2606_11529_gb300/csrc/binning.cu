@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
 // Multi-view: the view of record i (i div per_view) goes in bits 32.. so views stay in order.
 __global__ void depth_key_kernel(const float *__restrict__ rec, const int *__restrict__ tcount, int64_t n,
                                  int64_t per_view, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    grid_dep_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint64_t view = per_view ? (uint64_t)(i / per_view) : 0ull;
@@ -182,6 +183,7 @@ __global__ void depth_key_kernel(const float *__restrict__ rec, const int *__res
 // One view: the 32-bit key alone (half the key traffic of the sort's passes).
 __global__ void depth_key32_kernel(const float *__restrict__ rec, const int *__restrict__ tcount, int64_t n,
                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    grid_dep_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     keys[i] = tcount[i] > 0 ? __float_as_uint(rec[(size_t)i * XPR_REC_FLOATS + 9]) : 0xffffffffu;
@@ -196,6 +198,7 @@ struct KeyItems {
 
 __global__ void depth_key_items_kernel(const float *__restrict__ rec, const int *__restrict__ tcount, KeyItems ki,
                                        uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    grid_dep_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ki.rec0[ki.count]) return;
     int k = 0;
@@ -310,12 +313,14 @@ int launch_depth_order(const float *rec, const int32_t *tc, int64_t n, int32_t *
     void *sort_ws = p + 2 * a + b + 256;
     if (n_views == 1) {  // the u64 key buffer holds the u32 keys; the u64 sort's scratch the u32 sort's
         uint32_t *k32 = reinterpret_cast<uint32_t *>(keys);
-        depth_key32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, tc, n, k32, vals);
+        XPR_CUDA_TRY(launch_dependent(depth_key32_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, rec, tc,
+                                      n, k32, vals));
         XPR_LAUNCH_CHECK("depth_key32_kernel");
         return launch_sort_u32_bits(k32, vals, n, 1, 0, 32, nullptr, reinterpret_cast<uint32_t *>(order), nullptr,
                                     sort_ws, sort_workspace_bytes(n, n_views), st);
     }
-    depth_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(rec, tc, n, per_view, keys, vals);
+    XPR_CUDA_TRY(launch_dependent(depth_key_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, rec, tc, n,
+                                  per_view, keys, vals));
     XPR_LAUNCH_CHECK("depth_key_kernel");
     // the sort's "tile" is the view: keys (view << 32 | depth bits) sort over 32 + ceil(log2 views) bits;
     // only the order is wanted (no sorted keys, which lets the sort use `keys` as scratch, and no
@@ -341,7 +346,8 @@ int launch_depth_order_items(const float *rec, const int32_t *tc, const XprItem 
     uint64_t *keys = reinterpret_cast<uint64_t *>(p);
     uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
     void *sort_ws = p + 2 * a + b + 256;
-    depth_key_items_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(rec, tc, ki, keys, vals);
+    XPR_CUDA_TRY(launch_dependent(depth_key_items_kernel, dim3((unsigned)((R + 255) / 256)), dim3(256), 0, st, rec,
+                                  tc, ki, keys, vals));
     XPR_LAUNCH_CHECK("depth_key_items_kernel");
     return launch_sort(keys, vals, R, n_items, 0, nullptr, reinterpret_cast<uint32_t *>(order), nullptr, sort_ws,
                        sort_workspace_bytes(R, n_items), st);

@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kProjWarps * 32) project_fwd_kernel(
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
     float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount, int *__restrict__ isect_count,
     XprPrimsGrad copy) {
+    grid_dep_wait();
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_fwd[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -367,6 +368,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 5) project_bwd_kernel(
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
     const float *__restrict__ d_rec, float *__restrict__ gmu, float *__restrict__ gscale, float *__restrict__ gquat,
     float *__restrict__ gopac, float *__restrict__ gsh) {
+    grid_dep_wait();
     constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_bwd[];
@@ -594,15 +596,16 @@ int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
     if (p.sh) {
-        XPR_DEG_DISPATCH(DEG, project_fwd_kernel<DEG, true><<<blocks, tpb,
-                                                               (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float),
-                                                               st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs,
-                                                                     cfg, rec, reinterpret_cast<int4 *>(bbox), tc,
-                                                                     isect_count, cp));
+        XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(
+                                  project_fwd_kernel<DEG, true>, dim3(blocks), dim3(tpb),
+                                  (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st, p.mu, p.scale, p.quat,
+                                  p.opacity, p.sh, n, cs, cfg, rec, reinterpret_cast<int4 *>(bbox), tc, isect_count,
+                                  cp)));
     } else {
-        XPR_DEG_DISPATCH(DEG, project_fwd_kernel<DEG, false><<<blocks, tpb, 0, st>>>(
-                                  p.mu, p.scale, p.quat, p.opacity, nullptr, n, cs, cfg, rec,
-                                  reinterpret_cast<int4 *>(bbox), tc, isect_count, cp));
+        XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(
+                                  project_fwd_kernel<DEG, false>, dim3(blocks), dim3(tpb), 0, st, p.mu, p.scale,
+                                  p.quat, p.opacity, (const float *)nullptr, n, cs, cfg, rec,
+                                  reinterpret_cast<int4 *>(bbox), tc, isect_count, cp)));
     }
     XPR_LAUNCH_CHECK("project_fwd_kernel");
     return XPR_OK;
@@ -634,8 +637,9 @@ int launch_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *cams
         attr = cudaFuncSetAttribute(project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         // one view: one row buffer per warp (half the limit)
         if (attr == cudaSuccess)
-            project_bwd_kernel<DEG><<<blocks, tpb, n_views == 1 ? smem / 2 : smem, st>>>(
-                p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, d_rec, g.mu, g.scale, g.quat, g.opacity, g.sh);
+            attr = launch_dependent(project_bwd_kernel<DEG>, dim3(blocks), dim3(tpb), n_views == 1 ? smem / 2 : smem,
+                                    st, p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, d_rec, g.mu, g.scale,
+                                    g.quat, g.opacity, g.sh);
     });
     XPR_CUDA_TRY(attr);
     XPR_LAUNCH_CHECK("project_bwd_kernel");

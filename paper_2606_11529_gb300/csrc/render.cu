@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(TW *TH / fwd_px<TW, TH>()) render_fwd_kernel(c
                                                                   float *__restrict__ image,
                                                                   float *__restrict__ tfin, int *__restrict__ ncon,
                                                                   Work w) {
+    grid_dep_wait();
     __shared__ float4 s_g[kMaxBatch];  // mx, my, A, B
     __shared__ float4 s_c[kMaxBatch];  // C, o, r, g
     __shared__ float s_b[kMaxBatch];   // b
@@ -423,6 +424,7 @@ __global__ void __launch_bounds__(TW *TH / bwd_px<TW, TH>()) render_bwd_kernel(c
                                                                   const int *__restrict__ ncon,
                                                                   const float *__restrict__ dimg,
                                                                   float *__restrict__ d_rec, Work w) {
+    grid_dep_wait();
     __shared__ float4 s_g[kBwdBatch];
     __shared__ float4 s_c[kBwdBatch];
     __shared__ float s_b[kBwdBatch];
@@ -497,7 +499,8 @@ int launch_render_fwd_views(const float *rec, int64_t n, const uint32_t *vals, c
     XPR_TILE_DISPATCH(TW, TH, {
         const int threads = TW * TH / fwd_px<TW, TH>();
         const int grid = worklist ? persistent_grid(render_fwd_kernel<TW, TH>, threads, items) : items;
-        render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, image, t_final, n_contrib, w);
+        XPR_CUDA_TRY(launch_dependent(render_fwd_kernel<TW, TH>, dim3(grid), dim3(threads), 0, st, rec, vals, rg, k,
+                                      image, t_final, n_contrib, w));
     });
     XPR_LAUNCH_CHECK("render_fwd_kernel");
     return XPR_OK;
@@ -518,7 +521,8 @@ int launch_render_bwd_views(const float *rec, const uint32_t *vals, const int32_
     XPR_TILE_DISPATCH(TW, TH, {
         const int threads = TW * TH / bwd_px<TW, TH>();
         const int grid = worklist ? persistent_grid(render_bwd_kernel<TW, TH>, threads, items) : items;
-        render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, t_final, n_contrib, d_image, d_rec, w);
+        XPR_CUDA_TRY(launch_dependent(render_bwd_kernel<TW, TH>, dim3(grid), dim3(threads), 0, st, rec, vals, rg, k,
+                                      t_final, n_contrib, d_image, d_rec, w));
     });
     XPR_LAUNCH_CHECK("render_bwd_kernel");
     return XPR_OK;
@@ -543,7 +547,8 @@ int launch_render_fwd_items(const float *rec, int64_t n_rec, const uint32_t *val
     XPR_TILE_DISPATCH(TW, TH, {
         const int threads = TW * TH / fwd_px<TW, TH>();
         const int grid = worklist ? persistent_grid(render_fwd_kernel<TW, TH>, threads, (int)items) : (int)items;
-        render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, image, t_final, n_contrib, w);
+        XPR_CUDA_TRY(launch_dependent(render_fwd_kernel<TW, TH>, dim3(grid), dim3(threads), 0, st, rec, vals, rg, k,
+                                      image, t_final, n_contrib, w));
     });
     XPR_LAUNCH_CHECK("render_fwd_kernel");
     return XPR_OK;
@@ -569,7 +574,8 @@ int launch_render_bwd_items(const float *rec, int64_t n_rec, const uint32_t *val
     XPR_TILE_DISPATCH(TW, TH, {
         const int threads = TW * TH / bwd_px<TW, TH>();
         const int grid = worklist ? persistent_grid(render_bwd_kernel<TW, TH>, threads, (int)items) : (int)items;
-        render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(rec, vals, rg, k, t_final, n_contrib, d_image, d_rec, w);
+        XPR_CUDA_TRY(launch_dependent(render_bwd_kernel<TW, TH>, dim3(grid), dim3(threads), 0, st, rec, vals, rg, k,
+                                      t_final, n_contrib, d_image, d_rec, w));
     });
     XPR_LAUNCH_CHECK("render_bwd_kernel");
     return XPR_OK;

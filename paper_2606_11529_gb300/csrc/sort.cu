@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kThreads) sort_hist_kernel(const K *__restrict
                                                              int end_bit, int passes, uint32_t *__restrict__ ghist,
                                                              uint4 *__restrict__ status0, int64_t status_vecs,
                                                              bool vec) {
+    grid_dep_wait();
     __shared__ uint32_t s[kMaxPasses][kRadix];
     for (int d = threadIdx.x; d < kMaxPasses * kRadix; d += kThreads) (&s[0][0])[d] = 0;
     const int64_t gt = (int64_t)blockIdx.x * kThreads + threadIdx.x, gs = (int64_t)gridDim.x * kThreads;
@@ -374,6 +375,7 @@ __global__ void __launch_bounds__(kThreads)
                            uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ ghist,
                            uint32_t *status, uint32_t *__restrict__ status_next, uint32_t *ctr,
                            int2 *__restrict__ ranges, uint32_t n_tiles) {
+    grid_dep_wait();
     constexpr uint32_t kMask = (1u << NB) - 1u;
     extern __shared__ __align__(16) unsigned char smem[];
     K *s_key = reinterpret_cast<K *>(smem);
@@ -690,8 +692,9 @@ int launch_chained(int64_t nb, cudaStream_t st, const K *kin, const uint32_t *vi
     // (one value per instantiation, so concurrent callers all set the same limit)
     XPR_CUDA_TRY(cudaFuncSetAttribute(chained_scatter_kernel<K, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)chained_smem<K>()));
-    chained_scatter_kernel<K, NB><<<(unsigned)nb, kThreads, chained_smem<K>(), st>>>(
-        kin, vin, kout, vout, n, shift, ghist, status, status_next, ctr, ranges, n_tiles);
+    XPR_CUDA_TRY(launch_dependent(chained_scatter_kernel<K, NB>, dim3((unsigned)nb), dim3(kThreads), chained_smem<K>(),
+                                  st, kin, vin, kout, vout, n, shift, ghist, status, status_next, ctr, ranges,
+                                  n_tiles));
     XPR_LAUNCH_CHECK("chained_scatter_kernel");
     return XPR_OK;
 }
@@ -765,9 +768,9 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
         XPR_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         XPR_CUDA_TRY(cudaMemsetAsync(ghist, 0, (size_t)kMaxPasses * (kRadix + 1) * 4, st));
         const unsigned hgrid = (unsigned)min(nb, (int64_t)8 * max(sms, 1));
-        sort_hist_kernel<K><<<hgrid, kThreads, 0, st>>>(keys_in, n, begin_bit, end_bit, passes, ghist,
-                                                        reinterpret_cast<uint4 *>(mat[0]), nb * kRadix / 4,
-                                                        is_aligned16(keys_in));
+        XPR_CUDA_TRY(launch_dependent(sort_hist_kernel<K>, dim3(hgrid), dim3(kThreads), 0, st, keys_in, n, begin_bit,
+                                      end_bit, passes, ghist, reinterpret_cast<uint4 *>(mat[0]), nb * kRadix / 4,
+                                      is_aligned16(keys_in)));
         XPR_LAUNCH_CHECK("sort_hist_kernel");
     }
     const K *src_k = keys_in;
