@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float *__restrict_
                                                         const int *__restrict__ tcount,
                                                         const int *__restrict__ order, int64_t n, Grid g,
                                                         int32_t *__restrict__ counts) {
+    grid_dep_wait();
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int i = 0, area = 0;
     int4 bb = make_int4(0, 0, 0, 0);
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(256) bin_emit_kernel(const float *__restrict__
                                                        const int32_t *__restrict__ offsets,
                                                        uint64_t *__restrict__ keys, uint32_t *__restrict__ tiles,
                                                        uint32_t *__restrict__ vals) {
+    grid_dep_wait();
     __shared__ int4 s_rows[8][32];  // per warp: the compacted rows of the current step
     __shared__ uint32_t s_dbs[8][32];
     const int lane = threadIdx.x & 31;
@@ -244,8 +246,8 @@ int launch_bin_count(const float *rec, const int32_t *bbox, const int32_t *tc, c
                      const XprCamera &cam, const XprConfig &cfg, int32_t *counts, cudaStream_t st) {
     if (n == 0) return XPR_OK;
     const int tpb = 256;
-    bin_count_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg), counts);
+    XPR_CUDA_TRY(launch_dependent(bin_count_kernel, dim3((unsigned)((n + tpb - 1) / tpb)), dim3(tpb), 0, st, rec,
+                                  reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg), counts));
     XPR_LAUNCH_CHECK("bin_count_kernel");
     return XPR_OK;
 }
@@ -258,9 +260,9 @@ int launch_bin_emit(const float *rec, const int32_t *bbox, const int32_t *tc, co
     const int64_t warps = (n + 31) / 32;
     BinItems bi;
     memset(&bi, 0, sizeof(bi));
-    bin_emit_kernel<false><<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg), per_view,
-        tiles_x(cam, cfg) * tiles_y(cam, cfg), bi, offsets, keys, tiles, vals);
+    XPR_CUDA_TRY(launch_dependent(bin_emit_kernel<false>, dim3((unsigned)((warps * 32 + tpb - 1) / tpb)), dim3(tpb), 0,
+                                  st, rec, reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg),
+                                  per_view, tiles_x(cam, cfg) * tiles_y(cam, cfg), bi, offsets, keys, tiles, vals));
     XPR_LAUNCH_CHECK("bin_emit_kernel");
     return XPR_OK;
 }
@@ -287,9 +289,9 @@ int launch_bin_emit_items(const float *rec, const int32_t *bbox, const int32_t *
     if (R == 0) return XPR_OK;
     const int tpb = 256;
     const int64_t warps = (R + 31) / 32;
-    bin_emit_kernel<true><<<(unsigned)((warps * 32 + tpb - 1) / tpb), tpb, 0, st>>>(
-        rec, reinterpret_cast<const int4 *>(bbox), tc, order, R, make_grid(cams[0], cfg), 0, 0, bi, offsets, nullptr,
-        tiles, vals);
+    XPR_CUDA_TRY(launch_dependent(bin_emit_kernel<true>, dim3((unsigned)((warps * 32 + tpb - 1) / tpb)), dim3(tpb), 0,
+                                  st, rec, reinterpret_cast<const int4 *>(bbox), tc, order, R, make_grid(cams[0], cfg),
+                                  0, 0, bi, offsets, nullptr, tiles, vals));
     XPR_LAUNCH_CHECK("bin_emit_kernel<items>");
     return XPR_OK;
 }
@@ -346,8 +348,8 @@ int launch_depth_order_items(const float *rec, const int32_t *tc, const XprItem 
     uint64_t *keys = reinterpret_cast<uint64_t *>(p);
     uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
     void *sort_ws = p + 2 * a + b + 256;
-    XPR_CUDA_TRY(launch_dependent(depth_key_items_kernel, dim3((unsigned)((R + 255) / 256)), dim3(256), 0, st, rec,
-                                  tc, ki, keys, vals));
+    XPR_CUDA_TRY(launch_dependent(depth_key_items_kernel, dim3((unsigned)((R + 255) / 256)), dim3(256), 0, st, rec, tc,
+                                  ki, keys, vals));
     XPR_LAUNCH_CHECK("depth_key_items_kernel");
     return launch_sort(keys, vals, R, n_items, 0, nullptr, reinterpret_cast<uint32_t *>(order), nullptr, sort_ws,
                        sort_workspace_bytes(R, n_items), st);

@@ -427,9 +427,8 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     auto emit = [&](const RowsLayout &L, int64_t room, unsigned long long *pairs) -> int {
         uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
         const unsigned eg = (unsigned)(((n + 31) / 32 * 32 + 255) / 256);
-        XPR_CUDA_TRY(launch_dependent(items ? span_emit_kernel<true> : span_emit_kernel<false>, dim3(eg), dim3(256),
-                                      0, st, rec, bb4, tc, order, n, g, t, (const int32_t *)slot0, room, key, prim,
-                                      pairs));
+        XPR_CUDA_TRY(launch_dependent(items ? span_emit_kernel<true> : span_emit_kernel<false>, dim3(eg), dim3(256), 0,
+                                      st, rec, bb4, tc, order, n, g, t, (const int32_t *)slot0, room, key, prim, pairs));
         XPR_LAUNCH_CHECK("span_emit_kernel");
         return XPR_OK;
     };
@@ -494,9 +493,9 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     uint32_t *codes = reinterpret_cast<uint32_t *>(p + LP.codes), *pvals = reinterpret_cast<uint32_t *>(p + LP.pvals);
     const int64_t swarps = (ns + 31) / 32;
     if (ns > 0) {
-        XPR_CUDA_TRY(launch_dependent(span_expand_kernel, dim3((unsigned)((swarps * 32 + 255) / 256)), dim3(256), 0,
-                                      st, (const uint32_t *)skey, (const uint32_t *)sprim, ns,
-                                      (const int32_t *)pair0, ni, codes, pvals));
+        XPR_CUDA_TRY(launch_dependent(span_expand_kernel, dim3((unsigned)((swarps * 32 + 255) / 256)), dim3(256), 0, st,
+                                      (const uint32_t *)skey, (const uint32_t *)sprim, ns, (const int32_t *)pair0, ni,
+                                      codes, pvals));
         XPR_LAUNCH_CHECK("span_expand_kernel");
     }
     const int64_t nc = n_codes(t);

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(TW *TH / feat_px<TW, TH, NF>()) render_feat_fw
     const float *__restrict__ rec, const float *__restrict__ feat, const uint32_t *__restrict__ vals,
     const int2 *__restrict__ ranges, FeatConsts k, float *__restrict__ image, float *__restrict__ features,
     float *__restrict__ tfin, int *__restrict__ ncon) {
+    grid_dep_wait();
     constexpr int PX = feat_px<TW, TH, NF>();
     constexpr int NT = TW * TH / PX, RS = TH / PX;
     static_assert(NT % 32 == 0, "a tile's block must be whole warps");
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(TW *TH / feat_px<TW, TH, NF>()) render_feat_bw
     const int2 *__restrict__ ranges, FeatConsts k, const float *__restrict__ tfin, const int *__restrict__ ncon,
     const float *__restrict__ dimg, const float *__restrict__ dfeat_img, float *__restrict__ d_rec,
     float *__restrict__ d_feat) {
+    grid_dep_wait();
     constexpr int PX = feat_px<TW, TH, NF>();
     constexpr int NT = TW * TH / PX, NW = NT / 32, RS = TH / PX;
     constexpr int NV = 9 + NF;
@@ -385,8 +387,9 @@ int launch_render_feat_fwd(const float *rec, int64_t n, const float *feat, int n
     const int2 *rg = reinterpret_cast<const int2 *>(ranges);
     const int nf = nfeat + (depth ? 1 : 0);
     XPR_FEAT_TILE_DISPATCH(TW, TH, XPR_FEAT_NF_DISPATCH(NF, nf, {
-        render_feat_fwd_kernel<TW, TH, NF><<<k.T, TW * TH / feat_px<TW, TH, NF>(), 0, st>>>(
-            rec, feat, vals, rg, k, image, features, t_final, n_contrib);
+        XPR_CUDA_TRY(launch_dependent(render_feat_fwd_kernel<TW, TH, NF>, dim3(k.T),
+                                      dim3(TW * TH / feat_px<TW, TH, NF>()), 0, st, rec, feat, vals, rg, k, image,
+                                      features, t_final, n_contrib));
     }));
     XPR_LAUNCH_CHECK("render_feat_fwd_kernel");
     return XPR_OK;
@@ -403,8 +406,9 @@ int launch_render_feat_bwd(const float *rec, int64_t n, const float *feat, int n
     const int2 *rg = reinterpret_cast<const int2 *>(ranges);
     const int nf = nfeat + (depth ? 1 : 0);
     XPR_FEAT_TILE_DISPATCH(TW, TH, XPR_FEAT_NF_DISPATCH(NF, nf, {
-        render_feat_bwd_kernel<TW, TH, NF><<<k.T, TW * TH / feat_px<TW, TH, NF>(), 0, st>>>(
-            rec, feat, vals, rg, k, t_final, n_contrib, d_image, d_features, d_rec, d_feat);
+        XPR_CUDA_TRY(launch_dependent(render_feat_bwd_kernel<TW, TH, NF>, dim3(k.T),
+                                      dim3(TW * TH / feat_px<TW, TH, NF>()), 0, st, rec, feat, vals, rg, k, t_final,
+                                      n_contrib, d_image, d_features, d_rec, d_feat));
     }));
     XPR_LAUNCH_CHECK("render_feat_bwd_kernel");
     return XPR_OK;

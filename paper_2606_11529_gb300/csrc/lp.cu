@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(kProjWarps * 32) lp_project_fwd_kernel(
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
     float *__restrict__ rec, float *__restrict__ sd, int4 *__restrict__ bbox, int *__restrict__ tcount,
     int *__restrict__ isect_count) {
+    grid_dep_wait();
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_lpf[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(256) lp_bin_kernel(const float *__restrict__ r
                                                      int32_t *__restrict__ counts, const int32_t *__restrict__ offsets,
                                                      uint64_t *__restrict__ keys, uint32_t *__restrict__ tiles,
                                                      uint32_t *__restrict__ vals, int64_t per_view) {
+    grid_dep_wait();
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -505,6 +507,7 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH / lp_px<TW, TH>()) lp_render_fwd_kernel(
     const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, LpConsts k,
     float *__restrict__ image, float *__restrict__ tfin, int *__restrict__ ncon, LpWork w) {
+    grid_dep_wait();
     __shared__ float4 s_u0[kLpBatch], s_u1[kLpBatch], s_u2[kLpBatch], s_u3[kLpBatch], s_u4[kLpBatch];
     const LpStage S = {s_u0, s_u1, s_u2, s_u3, s_u4, nullptr};
     if (w.list == nullptr) {
@@ -701,6 +704,7 @@ __global__ void __launch_bounds__(TW *TH / lp_px<TW, TH>()) lp_render_bwd_kernel
     const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, LpConsts k,
     const float *__restrict__ tfin, const int *__restrict__ ncon, const float *__restrict__ dimg,
     float *__restrict__ d_sd, LpWork w) {
+    grid_dep_wait();
     constexpr int NW = TW * TH / lp_px<TW, TH>() / 32;
     __shared__ float4 s_u0[kLpBwdBatch], s_u1[kLpBwdBatch], s_u2[kLpBwdBatch], s_u3[kLpBwdBatch],
         s_u4[kLpBwdBatch];
@@ -807,6 +811,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 3) lp_project_bwd_kernel(
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
     const float *__restrict__ d_sd, float *__restrict__ gmu, float *__restrict__ gscale,
     float *__restrict__ gquat, float *__restrict__ gopac, float *__restrict__ gsh) {
+    grid_dep_wait();
     constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_lpb[];
@@ -897,10 +902,10 @@ int launch_lp_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *c
     const int tpb = kProjWarps * 32;
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
-    XPR_DEG_DISPATCH(DEG, lp_project_fwd_kernel<DEG><<<blocks, tpb,
-                                                        (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
-                              p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, rec, sd,
-                              reinterpret_cast<int4 *>(bbox), tc, isect_count));
+    XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(lp_project_fwd_kernel<DEG>, dim3(blocks), dim3(tpb),
+                                                        (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st,
+                                                        p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, rec, sd,
+                                                        reinterpret_cast<int4 *>(bbox), tc, isect_count)));
     XPR_LAUNCH_CHECK("lp_project_fwd_kernel");
     return XPR_OK;
 }
@@ -918,8 +923,9 @@ int launch_lp_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *c
         attr = cudaFuncSetAttribute(lp_project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
         if (attr == cudaSuccess)
-            lp_project_bwd_kernel<DEG><<<blocks, tpb, smem, st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg,
-                                                                  d_sd, g.mu, g.scale, g.quat, g.opacity, g.sh);
+            XPR_CUDA_TRY(launch_dependent(lp_project_bwd_kernel<DEG>, dim3(blocks), dim3(tpb), smem, st, p.mu, p.scale,
+                                          p.quat, p.opacity, p.sh, n, cs, cfg, d_sd, g.mu, g.scale, g.quat, g.opacity,
+                                          g.sh));
     });
     XPR_CUDA_TRY(attr);
     XPR_LAUNCH_CHECK("lp_project_bwd_kernel");
@@ -930,9 +936,9 @@ int launch_lp_bin_count(const float *sd, const int32_t *bbox, const int32_t *tc,
                         const XprCamera &cam, const XprConfig &cfg, int32_t *counts, cudaStream_t st) {
     if (n == 0) return XPR_OK;
     const unsigned warps = (unsigned)((n + 31) / 32);
-    lp_bin_kernel<false><<<(warps + 7) / 8, 256, 0, st>>>(nullptr, sd, reinterpret_cast<const int4 *>(bbox), tc, order,
-                                                           n, make_grid(cam, cfg), counts, nullptr, nullptr, nullptr,
-                                                           nullptr, 0);
+    XPR_CUDA_TRY(launch_dependent(lp_bin_kernel<false>, dim3((warps + 7) / 8), dim3(256), 0, st, nullptr, sd,
+                                  reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg), counts,
+                                  nullptr, nullptr, nullptr, nullptr, 0));
     XPR_LAUNCH_CHECK("lp_bin_kernel<count>");
     return XPR_OK;
 }
@@ -943,9 +949,9 @@ int launch_lp_bin_emit(const float *rec, const float *sd, const int32_t *bbox, c
                        int64_t per_view) {
     if (n == 0) return XPR_OK;
     const unsigned warps = (unsigned)((n + 31) / 32);
-    lp_bin_kernel<true><<<(warps + 7) / 8, 256, 0, st>>>(rec, sd, reinterpret_cast<const int4 *>(bbox), tc, order, n,
-                                                          make_grid(cam, cfg), nullptr, offsets, keys, tiles, vals,
-                                                          per_view);
+    XPR_CUDA_TRY(launch_dependent(lp_bin_kernel<true>, dim3((warps + 7) / 8), dim3(256), 0, st, rec, sd,
+                                  reinterpret_cast<const int4 *>(bbox), tc, order, n, make_grid(cam, cfg), nullptr,
+                                  offsets, keys, tiles, vals, per_view));
     XPR_LAUNCH_CHECK("lp_bin_kernel<emit>");
     return XPR_OK;
 }
@@ -962,7 +968,8 @@ int launch_lp_render_fwd(const float *sd, int64_t n, const uint32_t *vals, const
     XPR_LP_TILE_DISPATCH(TW, TH, {
         const int threads = TW * TH / lp_px<TW, TH>();
         const int grid = worklist ? lp_persistent_grid(lp_render_fwd_kernel<TW, TH>, threads, items) : items;
-        lp_render_fwd_kernel<TW, TH><<<grid, threads, 0, st>>>(sd, vals, rg, k, image, t_final, n_contrib, w);
+        XPR_CUDA_TRY(launch_dependent(lp_render_fwd_kernel<TW, TH>, dim3(grid), dim3(threads), 0, st, sd, vals, rg, k,
+                                      image, t_final, n_contrib, w));
     });
     XPR_LAUNCH_CHECK("lp_render_fwd_kernel");
     return XPR_OK;
@@ -982,8 +989,8 @@ int launch_lp_render_bwd(const float *sd, int64_t n, const uint32_t *vals, const
     XPR_LP_TILE_DISPATCH(TW, TH, {
         const int threads = TW * TH / lp_px<TW, TH>();
         const int grid = worklist ? lp_persistent_grid(lp_render_bwd_kernel<TW, TH>, threads, items) : items;
-        lp_render_bwd_kernel<TW, TH><<<grid, threads, 0, st>>>(sd, vals, rg, k, t_final, n_contrib, d_image, d_sd,
-                                                                 w);
+        XPR_CUDA_TRY(launch_dependent(lp_render_bwd_kernel<TW, TH>, dim3(grid), dim3(threads), 0, st, sd, vals, rg, k,
+                                      t_final, n_contrib, d_image, d_sd, w));
     });
     XPR_LAUNCH_CHECK("lp_render_bwd_kernel");
     return XPR_OK;

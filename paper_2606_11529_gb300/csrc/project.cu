@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kProjWarps * 32) project_color_kernel(const fl
                                                                         const float *__restrict__ sh, int64_t n,
                                                                         CamSet cs, XprConfig cfg,
                                                                         float *__restrict__ rec) {
+    grid_dep_wait();
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_col[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -445,6 +446,7 @@ __global__ void __launch_bounds__(kProjWarps * 32) project_items_kernel(
     const float *__restrict__ mu, const float *__restrict__ scale, const float *__restrict__ quat,
     const float *__restrict__ opac, const float *__restrict__ sh, ItemSet is, XprConfig cfg,
     float *__restrict__ rec, int4 *__restrict__ bbox, int *__restrict__ tcount, int *__restrict__ isect_count) {
+    grid_dep_wait();
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_fwd[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -483,6 +485,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) project_bwd_items_kernel(
     const float *__restrict__ opac, const float *__restrict__ sh, ItemSet is, XprConfig cfg,
     const float *__restrict__ d_rec, float *__restrict__ gmu, float *__restrict__ gscale, float *__restrict__ gquat,
     float *__restrict__ gopac, float *__restrict__ gsh) {
+    grid_dep_wait();
     constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_bwd[];
@@ -551,10 +554,10 @@ int launch_project_items(const XprPrims &p, const XprCamera *cams, const XprItem
     if (R == 0) return XPR_OK;
     const int tpb = kProjWarps * 32;
     const unsigned blocks = (unsigned)((R + tpb - 1) / tpb);
-    XPR_DEG_DISPATCH(DEG, project_items_kernel<DEG><<<blocks, tpb,
-                                                       (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
-                              p.mu, p.scale, p.quat, p.opacity, p.sh, is, cfg, rec, reinterpret_cast<int4 *>(bbox),
-                              tc, isect_count));
+    XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(project_items_kernel<DEG>, dim3(blocks), dim3(tpb),
+                                                        (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st,
+                                                        p.mu, p.scale, p.quat, p.opacity, p.sh, is, cfg, rec,
+                                                        reinterpret_cast<int4 *>(bbox), tc, isect_count)));
     XPR_LAUNCH_CHECK("project_items_kernel");
     return XPR_OK;
 }
@@ -579,8 +582,9 @@ int launch_project_bwd_items(const XprPrims &p, int64_t n_prims, const XprCamera
         attr = cudaFuncSetAttribute(project_bwd_items_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
         if (attr == cudaSuccess)
-            project_bwd_items_kernel<DEG><<<blocks, tpb, smem, st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, is, cfg,
-                                                                     d_rec, g.mu, g.scale, g.quat, g.opacity, g.sh);
+            XPR_CUDA_TRY(launch_dependent(project_bwd_items_kernel<DEG>, dim3(blocks), dim3(tpb), smem, st, p.mu,
+                                          p.scale, p.quat, p.opacity, p.sh, is, cfg, d_rec, g.mu, g.scale, g.quat,
+                                          g.opacity, g.sh));
     });
     XPR_CUDA_TRY(attr);
     XPR_LAUNCH_CHECK("project_bwd_items_kernel");
@@ -596,16 +600,15 @@ int launch_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *cams
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
     if (p.sh) {
-        XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(
-                                  project_fwd_kernel<DEG, true>, dim3(blocks), dim3(tpb),
-                                  (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st, p.mu, p.scale, p.quat,
-                                  p.opacity, p.sh, n, cs, cfg, rec, reinterpret_cast<int4 *>(bbox), tc, isect_count,
-                                  cp)));
+        XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(project_fwd_kernel<DEG, true>, dim3(blocks), dim3(tpb),
+                                                            (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st,
+                                                            p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, rec,
+                                                            reinterpret_cast<int4 *>(bbox), tc, isect_count, cp)));
     } else {
-        XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(
-                                  project_fwd_kernel<DEG, false>, dim3(blocks), dim3(tpb), 0, st, p.mu, p.scale,
-                                  p.quat, p.opacity, (const float *)nullptr, n, cs, cfg, rec,
-                                  reinterpret_cast<int4 *>(bbox), tc, isect_count, cp)));
+        XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(project_fwd_kernel<DEG, false>, dim3(blocks), dim3(tpb), 0,
+                                                            st, p.mu, p.scale, p.quat, p.opacity,
+                                                            (const float *)nullptr, n, cs, cfg, rec,
+                                                            reinterpret_cast<int4 *>(bbox), tc, isect_count, cp)));
     }
     XPR_LAUNCH_CHECK("project_fwd_kernel");
     return XPR_OK;
@@ -617,9 +620,9 @@ int launch_project_color_views(const float *mu, const float *sh, int64_t n, cons
     const int tpb = kProjWarps * 32;
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
-    XPR_DEG_DISPATCH(DEG, project_color_kernel<DEG><<<blocks, tpb,
-                                                       (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
-                              mu, sh, n, cs, cfg, rec));
+    XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(project_color_kernel<DEG>, dim3(blocks), dim3(tpb),
+                                                        (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st, mu,
+                                                        sh, n, cs, cfg, rec)));
     XPR_LAUNCH_CHECK("project_color_kernel");
     return XPR_OK;
 }

@@ -693,8 +693,7 @@ int launch_chained(int64_t nb, cudaStream_t st, const K *kin, const uint32_t *vi
     XPR_CUDA_TRY(cudaFuncSetAttribute(chained_scatter_kernel<K, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)chained_smem<K>()));
     XPR_CUDA_TRY(launch_dependent(chained_scatter_kernel<K, NB>, dim3((unsigned)nb), dim3(kThreads), chained_smem<K>(),
-                                  st, kin, vin, kout, vout, n, shift, ghist, status, status_next, ctr, ranges,
-                                  n_tiles));
+                                  st, kin, vin, kout, vout, n, shift, ghist, status, status_next, ctr, ranges, n_tiles));
     XPR_LAUNCH_CHECK("chained_scatter_kernel");
     return XPR_OK;
 }
@@ -809,9 +808,9 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
             XPR_LAUNCH_CHECK("colapply_kernel");
             XPR_CUDA_TRY(cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)scatter_smem<K>()));
-            XPR_CUDA_TRY(launch_dependent(radix_scatter_kernel<K>, dim3((unsigned)nb), dim3(kThreads), scatter_smem<K>(), st,
-                                          src_k, src_v, dst_k, dst_v, n, shift, mask, (const int32_t *)hist,
-                                          last ? rg : (int2 *)nullptr, (uint32_t)n_tiles));
+            XPR_CUDA_TRY(launch_dependent(radix_scatter_kernel<K>, dim3((unsigned)nb), dim3(kThreads),
+                                          scatter_smem<K>(), st, src_k, src_v, dst_k, dst_v, n, shift, mask,
+                                          (const int32_t *)hist, last ? rg : (int2 *)nullptr, (uint32_t)n_tiles));
             XPR_LAUNCH_CHECK("radix_scatter_kernel");
             s = XPR_OK;
         }
@@ -829,6 +828,7 @@ int radix_sort(const K *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_t
 // key = UINT32_MAX - list length: ascending keys = descending lengths (ties keep tile order)
 __global__ void worklist_keys_kernel(const int2 *__restrict__ ranges, int n_tiles, uint32_t *__restrict__ keys,
                                      uint32_t *__restrict__ vals) {
+    grid_dep_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
     const int2 r = ranges[t];
@@ -873,8 +873,8 @@ int launch_tile_worklist(const int32_t *ranges, int32_t n_tiles, int32_t *workli
     uint32_t *keys_sorted = reinterpret_cast<uint32_t *>(p + a);
     uint32_t *vals = reinterpret_cast<uint32_t *>(p + 2 * a);
     int32_t *dummy_ranges = reinterpret_cast<int32_t *>(p + 3 * a);
-    worklist_keys_kernel<<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(reinterpret_cast<const int2 *>(ranges),
-                                                                            n_tiles, keys, vals);
+    XPR_CUDA_TRY(launch_dependent(worklist_keys_kernel, dim3((unsigned)((n_tiles + 255) / 256)), dim3(256), 0, st,
+                                  reinterpret_cast<const int2 *>(ranges), n_tiles, keys, vals));
     XPR_LAUNCH_CHECK("worklist_keys_kernel");
     return radix_sort<uint32_t>(keys, vals, n_tiles, 1, 0, 32, keys_sorted, reinterpret_cast<uint32_t *>(worklist),
                                 dummy_ranges, p + 3 * a + 256, workspace_bytes<uint32_t>(n_tiles), st);

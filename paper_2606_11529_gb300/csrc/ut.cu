@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(kProjWarps * 32) ut_project_fwd_kernel(
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
     float *__restrict__ rec, float *__restrict__ sd, int4 *__restrict__ bbox, int *__restrict__ tcount,
     int *__restrict__ isect_count) {
+    grid_dep_wait();
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_utf[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -419,6 +420,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 4) ut_project_bwd_kernel(
     const float *__restrict__ opac, const float *__restrict__ sh, int64_t n, CamSet cs, XprConfig cfg,
     const float *__restrict__ d_sd, float *__restrict__ gmu, float *__restrict__ gscale,
     float *__restrict__ gquat, float *__restrict__ gopac, float *__restrict__ gsh) {
+    grid_dep_wait();
     constexpr int KC = (DEG + 1) * (DEG + 1) * 3;
     constexpr int LD = sh_ld<DEG>();
     extern __shared__ float s_utb[];
@@ -655,6 +657,7 @@ template <int TW, int TH, bool FISH>
 __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_fwd_kernel(
     const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, UtConsts k,
     float *__restrict__ image, float *__restrict__ tfin, int *__restrict__ ncon, UtWork w) {
+    grid_dep_wait();
     __shared__ float4 s_u0[kUtBatch], s_u1[kUtBatch], s_u2[kUtBatch], s_u3[kUtBatch];
     const UtStage S = {s_u0, s_u1, s_u2, s_u3, nullptr};
     if (w.list == nullptr) {
@@ -855,6 +858,7 @@ __global__ void __launch_bounds__(TW *TH / ut_px<TW, TH>()) ut_render_bwd_kernel
     const float *__restrict__ sd, const uint32_t *__restrict__ vals, const int2 *__restrict__ ranges, UtConsts k,
     const float *__restrict__ tfin, const int *__restrict__ ncon, const float *__restrict__ dimg,
     float *__restrict__ d_sd, UtWork w) {
+    grid_dep_wait();
     constexpr int NW = TW * TH / ut_px<TW, TH>() / 32;
     __shared__ float4 s_u0[kUtBwdBatch], s_u1[kUtBwdBatch], s_u2[kUtBwdBatch], s_u3[kUtBwdBatch];
     __shared__ uint32_t s_id[kUtBwdBatch];
@@ -915,10 +919,10 @@ int launch_ut_project_fwd_views(const XprPrims &p, int64_t n, const XprCamera *c
     const int tpb = kProjWarps * 32;
     const unsigned blocks = (unsigned)((n + tpb - 1) / tpb);
     const CamSet cs = make_camset(cams, n_views);
-    XPR_DEG_DISPATCH(DEG, ut_project_fwd_kernel<DEG><<<blocks, tpb,
-                                                        (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st>>>(
-                              p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, rec, sd,
-                              reinterpret_cast<int4 *>(bbox), tc, isect_count));
+    XPR_DEG_DISPATCH(DEG, XPR_CUDA_TRY(launch_dependent(ut_project_fwd_kernel<DEG>, dim3(blocks), dim3(tpb),
+                                                        (size_t)kProjWarps * 32 * sh_ld<DEG>() * sizeof(float), st,
+                                                        p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg, rec, sd,
+                                                        reinterpret_cast<int4 *>(bbox), tc, isect_count)));
     XPR_LAUNCH_CHECK("ut_project_fwd_kernel");
     return XPR_OK;
 }
@@ -936,8 +940,9 @@ int launch_ut_project_bwd_views(const XprPrims &p, int64_t n, const XprCamera *c
         attr = cudaFuncSetAttribute(ut_project_bwd_kernel<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
         if (attr == cudaSuccess)
-            ut_project_bwd_kernel<DEG><<<blocks, tpb, smem, st>>>(p.mu, p.scale, p.quat, p.opacity, p.sh, n, cs, cfg,
-                                                                  d_sd, g.mu, g.scale, g.quat, g.opacity, g.sh);
+            XPR_CUDA_TRY(launch_dependent(ut_project_bwd_kernel<DEG>, dim3(blocks), dim3(tpb), smem, st, p.mu, p.scale,
+                                          p.quat, p.opacity, p.sh, n, cs, cfg, d_sd, g.mu, g.scale, g.quat, g.opacity,
+                                          g.sh));
     });
     XPR_CUDA_TRY(attr);
     XPR_LAUNCH_CHECK("ut_project_bwd_kernel");
@@ -970,14 +975,15 @@ int launch_ut_render_fwd(const float *sd, int64_t n, const uint32_t *vals, const
         XPR_UT_TILE_DISPATCH(TW, TH, {
             const int threads = TW * TH / ut_px<TW, TH>();
             const int grid = worklist ? ut_persistent_grid(ut_render_fwd_kernel<TW, TH, true>, threads, items) : items;
-            ut_render_fwd_kernel<TW, TH, true><<<grid, threads, 0, st>>>(sd, vals, rg, k, image, t_final, n_contrib, w);
+            XPR_CUDA_TRY(launch_dependent(ut_render_fwd_kernel<TW, TH, true>, dim3(grid), dim3(threads), 0, st, sd,
+                                          vals, rg, k, image, t_final, n_contrib, w));
         });
     } else {
         XPR_UT_TILE_DISPATCH(TW, TH, {
             const int threads = TW * TH / ut_px<TW, TH>();
             const int grid = worklist ? ut_persistent_grid(ut_render_fwd_kernel<TW, TH, false>, threads, items) : items;
-            ut_render_fwd_kernel<TW, TH, false><<<grid, threads, 0, st>>>(sd, vals, rg, k, image, t_final, n_contrib,
-                                                                          w);
+            XPR_CUDA_TRY(launch_dependent(ut_render_fwd_kernel<TW, TH, false>, dim3(grid), dim3(threads), 0, st, sd,
+                                          vals, rg, k, image, t_final, n_contrib, w));
         });
     }
     XPR_LAUNCH_CHECK("ut_render_fwd_kernel");
@@ -999,15 +1005,15 @@ int launch_ut_render_bwd(const float *sd, int64_t n, const uint32_t *vals, const
         XPR_UT_TILE_DISPATCH(TW, TH, {
             const int threads = TW * TH / ut_px<TW, TH>();
             const int grid = worklist ? ut_persistent_grid(ut_render_bwd_kernel<TW, TH, true>, threads, items) : items;
-            ut_render_bwd_kernel<TW, TH, true><<<grid, threads, 0, st>>>(sd, vals, rg, k, t_final, n_contrib, d_image,
-                                                                         d_sd, w);
+            XPR_CUDA_TRY(launch_dependent(ut_render_bwd_kernel<TW, TH, true>, dim3(grid), dim3(threads), 0, st, sd,
+                                          vals, rg, k, t_final, n_contrib, d_image, d_sd, w));
         });
     } else {
         XPR_UT_TILE_DISPATCH(TW, TH, {
             const int threads = TW * TH / ut_px<TW, TH>();
             const int grid = worklist ? ut_persistent_grid(ut_render_bwd_kernel<TW, TH, false>, threads, items) : items;
-            ut_render_bwd_kernel<TW, TH, false><<<grid, threads, 0, st>>>(sd, vals, rg, k, t_final, n_contrib, d_image,
-                                                                          d_sd, w);
+            XPR_CUDA_TRY(launch_dependent(ut_render_bwd_kernel<TW, TH, false>, dim3(grid), dim3(threads), 0, st, sd,
+                                          vals, rg, k, t_final, n_contrib, d_image, d_sd, w));
         });
     }
     XPR_LAUNCH_CHECK("ut_render_bwd_kernel");
