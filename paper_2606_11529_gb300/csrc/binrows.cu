@@ -152,10 +152,11 @@ __device__ __forceinline__ int span_len(uint32_t key) { return (int)((key >> 15)
 // Warp w takes the sorted spans [32 w, 32 w + 32): their pairs are contiguous from the first span's
 // offset, and the warp writes them 32 at a time, lane k writing pair k of the warp's flattened list
 // (its span found from the ends of the non-empty spans, which are distinct).
+template <typename CT>  // the tile code's type: 16 bits when every code fits, else 32
 __global__ void __launch_bounds__(256) span_expand_kernel(const uint32_t *__restrict__ skey,
                                                           const uint32_t *__restrict__ sprim, int64_t ns,
                                                           const int32_t *__restrict__ pair0, int64_t capacity,
-                                                          uint32_t *__restrict__ codes, uint32_t *__restrict__ vals) {
+                                                          CT *__restrict__ codes, uint32_t *__restrict__ vals) {
     grid_dep_wait();
     __shared__ uint2 s_sp[8][32];  // per warp: the non-empty spans' (first code, primitive)
     __shared__ int s_x[8][32];     // and the index of their first pair in the warp's list
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(256) span_expand_kernel(const uint32_t *__rest
             const uint2 r = s_sp[wl][sp];
             const int64_t pos = base + k;
             if (pos < capacity) {
-                codes[pos] = r.x + ((uint32_t)(k - s_x[wl][sp]) << 7);
+                codes[pos] = (CT)(r.x + ((uint32_t)(k - s_x[wl][sp]) << 7));
                 vals[pos] = r.y;
             }
         }
@@ -490,19 +491,32 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
         if (ni > capacity || (!early && ws_bytes < rows_layout(n, ns, ni, t).total)) return XPR_ERR_CAPACITY;
     }
     const RowsLayout LP = early ? L : rows_layout(n, ns, ni, t);
-    uint32_t *codes = reinterpret_cast<uint32_t *>(p + LP.codes), *pvals = reinterpret_cast<uint32_t *>(p + LP.pvals);
+    // tile codes of 16 bits when every code fits (at most four items of 128 x 128 tiles): half the
+    // key bytes the expansion writes and the column pass reads
+    const int64_t nc = n_codes(t);
+    const bool narrow = nc <= 65536;
+    void *codes = p + LP.codes;
+    uint32_t *pvals = reinterpret_cast<uint32_t *>(p + LP.pvals);
     const int64_t swarps = (ns + 31) / 32;
     if (ns > 0) {
-        XPR_CUDA_TRY(launch_dependent(span_expand_kernel, dim3((unsigned)((swarps * 32 + 255) / 256)), dim3(256), 0, st,
-                                      (const uint32_t *)skey, (const uint32_t *)sprim, ns, (const int32_t *)pair0, ni,
-                                      codes, pvals));
+        const dim3 eg((unsigned)((swarps * 32 + 255) / 256));
+        if (narrow)
+            XPR_CUDA_TRY(launch_dependent(span_expand_kernel<uint16_t>, eg, dim3(256), 0, st, (const uint32_t *)skey,
+                                          (const uint32_t *)sprim, ns, (const int32_t *)pair0, ni,
+                                          reinterpret_cast<uint16_t *>(codes), pvals));
+        else
+            XPR_CUDA_TRY(launch_dependent(span_expand_kernel<uint32_t>, eg, dim3(256), 0, st, (const uint32_t *)skey,
+                                          (const uint32_t *)sprim, ns, (const int32_t *)pair0, ni,
+                                          reinterpret_cast<uint32_t *>(codes), pvals));
         XPR_LAUNCH_CHECK("span_expand_kernel");
     }
-    const int64_t nc = n_codes(t);
     int2 *by_code = reinterpret_cast<int2 *>(p + LP.by_code);
-    s = launch_sort_u32_bits(codes, pvals, ni, (int32_t)nc, 7, 7 + column_bits(t), nullptr, vals,
-                             reinterpret_cast<int32_t *>(by_code), p + LP.sort_ws,
-                             sort_u32_onepass_workspace_bytes(ni), st);
+    s = narrow ? launch_sort_u16_bits(reinterpret_cast<const uint16_t *>(codes), pvals, ni, (int32_t)nc, 7,
+                                      7 + column_bits(t), nullptr, vals, reinterpret_cast<int32_t *>(by_code),
+                                      p + LP.sort_ws, sort_u16_onepass_workspace_bytes(ni), st)
+               : launch_sort_u32_bits(reinterpret_cast<const uint32_t *>(codes), pvals, ni, (int32_t)nc, 7,
+                                      7 + column_bits(t), nullptr, vals, reinterpret_cast<int32_t *>(by_code),
+                                      p + LP.sort_ws, sort_u32_onepass_workspace_bytes(ni), st);
     if (s != XPR_OK) return s;
     if (T > 0) {
         XPR_CUDA_TRY(launch_dependent(permute_ranges_kernel, dim3((unsigned)((T + 255) / 256)), dim3(256), 0, st,
