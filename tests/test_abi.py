@@ -87,8 +87,10 @@ def _cam_cfg(**over):
 def test_invalid_arguments_rejected_on_host(lib, over, frag):
     from paper_2606_11529_gb300 import binding
     cam, cfg = _cam_cfg(**over)
-    p = binding.XprPrims(1, 1, 16, 1, 1)  # never dereferenced: validation fails first
-    s = lib.xpr_project(ctypes.byref(p), 1, ctypes.byref(cam), ctypes.byref(cfg), 16, 16, 16, None, None)
+    # NULL device pointers: the camera / config check fails first, and a check reordered after the
+    # NULL-pointer check would still stop on the host
+    p = binding.XprPrims(None, None, None, None, None)
+    s = lib.xpr_project(ctypes.byref(p), 1, ctypes.byref(cam), ctypes.byref(cfg), None, None, None, None, None)
     assert s == binding.XPR_ERR_INVALID
     assert frag in lib.xpr_last_error()
 
