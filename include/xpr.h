@@ -447,9 +447,10 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
  * identify bounds" for one view whose tile grid has at most 128 columns and
  * 128 rows, with one radix pass over the pairs: the row form of the cull gives
  * every primitive one span of kept tile columns per row of its box; the spans
- * (about seven pairs each on the headline workload) are sorted by row in depth
- * order, expanded into pairs grouped by row, and one stable pass over the
- * pairs' column groups them by tile.  Every tile's list is bit-identical to
+ * (about seven pairs each on the headline workload) are written grouped by row
+ * in depth order (their places from a scanned count of box rows per row and
+ * chunk of depth positions), expanded into pairs grouped by row, and one
+ * stable pass over the pairs' column groups them by tile.  Every tile's list is bit-identical to
  * xpr_tile_bin in the same order followed by xpr_sort_tiles: the same kept
  * pairs (same FP32 cull), each tile's list in emission order; the tiles'
  * segments lie in column-major tile order (the ranges locate them).

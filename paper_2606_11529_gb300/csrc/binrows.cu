@@ -4,21 +4,22 @@
 //
 // The tile cull in row form (cull.cuh) gives, for every primitive and every tile row of its box, one
 // interval [ka, kb] of kept tile columns: a span.  The per-tile lists are built from spans:
-//   1. span slots: each position j of the depth order owns one slot per row of its box (offsets by
-//      a scan of the box heights in depth order); the emit kernel writes each slot as a 4-byte key
-//      (its tile row, or 255 for a row with no kept tile, in bits 0-7; the first kept column in
-//      bits 8-14; the number of kept tiles in bits 15-22; the record's item in bits 23-26) and its
-//      record as the value;
-//   2. one stable radix pass over the span slots by the row bits, moving key and value: spans
-//      grouped by row, each row's spans in slot order (the empty rows last);
+//   1. span slots: each position j of the depth order owns one slot per row of its box, the slots
+//      grouped by row and each row's in depth order.  A count kernel tallies the box rows per
+//      (tile row, chunk of 256 depth positions); the exclusive scan of that row-major matrix is
+//      where each chunk's slots of each row start;
+//   2. the emit kernel writes every slot in place as a 4-byte key (its tile row, or 255 for a row
+//      with no kept tile, in bits 0-7; the first kept column in bits 8-14; the number of kept tiles
+//      in bits 15-22; the record's item in bits 23-26) and its record as the value: the spans lie
+//      as a stable sort of the depth-ordered slots by row would leave them, without the sort;
 //   3. an exclusive scan of the span lengths in that order gives every span its first pair, and
 //      the expansion writes the pairs of each span contiguously: tile code (k << 14) | (tx << 7) |
 //      ty and the record, so the pairs are grouped by tile row and, inside a row, by item in depth
-//      order (every read of these passes is a coalesced one of the sorted spans);
+//      order (every read of these passes is a coalesced one of the grouped spans);
 //   4. one stable radix pass over the pairs by the code's column bits [7, 14): the pairs end
 //      grouped by (column, row, item), so every tile (k, tx, ty) is one contiguous run, inside it
 //      still in depth order: the tile-major depth-sorted list of Sec. 4.2 with one radix pass over
-//      the pairs instead of two (the rows were sorted on the spans, about seven pairs each here).
+//      the pairs instead of two (the rows were grouped on the spans, about seven pairs each here).
 // The tile ranges are found per code and permuted to the tile ids the render uses (item k's tile
 // (tx, ty) at tile0[k] + ty Wt[k] + tx).  The result is identical, list for list, to the depth-
 // ordered emission followed by the stable sort of the tile ids.
@@ -41,101 +42,142 @@ __device__ __forceinline__ int item_of_record(const RowItems &t, int64_t i) {
     return k;
 }
 
-// Scan items: the box height (tile rows) of the record at depth position j, on its item's grid.
+constexpr int kChunk = 256;  // depth positions per chunk of the row grouping (one block, 8 warps)
+
+// This lane's record at depth position j (j < n): its item's grid, clamped tile box and box height.
 template <bool ITEMS>
-struct BoxRowsItem {
-    const int4 *bbox;
-    const int *tcount;
-    const int *order;
-    Grid g;
-    RowItems t;
-    __device__ __forceinline__ int32_t operator()(int64_t j) const {
-        const int i = order[j];
-        Grid gl = g;
-        if (ITEMS) {
-            const int k = item_of_record(t, i);
-            gl.Wt = t.Wt[k];
-            gl.Ht = t.Ht[k];
-        }
-        int4 bb;
-        return box_of(bbox, tcount, i, gl, bb) > 0 ? bb.w - bb.y : 0;
+__device__ __forceinline__ int position_box(const int4 *__restrict__ bbox, const int *__restrict__ tcount,
+                                            const int *__restrict__ order, int64_t j, const Grid &g,
+                                            const RowItems &t, int &i, int &k, Grid &gl, int4 &bb) {
+    i = order[j];
+    k = 0;
+    gl = g;
+    if (ITEMS) {
+        k = item_of_record(t, i);
+        gl.W = t.W[k];
+        gl.H = t.H[k];
+        gl.Wt = t.Wt[k];
+        gl.Ht = t.Ht[k];
     }
-};
+    return box_of(bbox, tcount, i, gl, bb) > 0 ? bb.w - bb.y : 0;
+}
+
+// count[r * n_chunks + b] = number of box rows at tile row r among the records at depth positions
+// [256 b, 256 b + 256): with one slot per box row, the exclusive scan of this row-major matrix is
+// where chunk b's slots of row r start when the slots are grouped by row, in depth order.
+template <bool ITEMS>
+__global__ void __launch_bounds__(kChunk) row_count_kernel(const int4 *__restrict__ bbox,
+                                                           const int *__restrict__ tcount,
+                                                           const int *__restrict__ order, int64_t n, Grid g,
+                                                           RowItems t, int64_t n_chunks, int32_t *__restrict__ count) {
+    grid_dep_wait();
+    __shared__ int s_cnt[kMaxRowGrid];
+    for (int r = threadIdx.x; r < kMaxRowGrid; r += kChunk) s_cnt[r] = 0;
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * kChunk + threadIdx.x;
+    if (j < n) {
+        int i, k;
+        Grid gl;
+        int4 bb;
+        const int h = position_box<ITEMS>(bbox, tcount, order, j, g, t, i, k, gl, bb);
+        for (int r = bb.y; r < bb.y + h; ++r) atomicAdd(&s_cnt[r], 1);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < kMaxRowGrid; r += kChunk) count[(int64_t)r * n_chunks + blockIdx.x] = s_cnt[r];
+}
 
 struct CountItem {  // the kept tile counts, summed for the pair total
     const int32_t *in;
     __device__ __forceinline__ int32_t operator()(int64_t j) const { return in[j]; }
 };
 
-// Warp w takes the positions w, w + nw, ... (interleaved over the depth order, as the pair
-// emission does) and flattens their box rows over its lanes; each row's span goes to its slot
-// (slots at or beyond ns_cap are not written: the launch may precede the check of the slot total
-// against the workspace).  With items, each lane's image size and item travel with its rows
+// Block b takes the depth positions [256 b, 256 b + 256), warp w the 32 from 256 b + 32 w, and
+// writes each row's span (the row-form cull of one (primitive, tile row)) straight to its place in
+// the slots grouped by row: the row's start for this chunk (the scanned count matrix), plus the
+// row's slots in the warps before this one, plus those of the lanes before this one in the warp
+// (one ballot per row of the warp's boxes).  So every row's spans lie in depth order, as a stable
+// sort of depth-ordered slots by row would leave them.  The warp flattens its boxes' rows over its
+// lanes; slots at or beyond ns_cap are not written (the launch may precede the check of the slot
+// total against the workspace).  With items, each lane's image size and item travel with its rows
 // through the shuffles.  pair_total (may be NULL): receives the sum of the kept counts.
 template <bool ITEMS>
-__global__ void __launch_bounds__(256) span_emit_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
-                                                        const int *__restrict__ tcount,
-                                                        const int *__restrict__ order, int64_t n, Grid g, RowItems t,
-                                                        const int32_t *__restrict__ slot0, int64_t ns_cap,
-                                                        uint32_t *__restrict__ span_key,
-                                                        uint32_t *__restrict__ span_prim,
-                                                        unsigned long long *__restrict__ pair_total) {
+__global__ void __launch_bounds__(kChunk) span_emit_kernel(const float *__restrict__ rec, const int4 *__restrict__ bbox,
+                                                           const int *__restrict__ tcount,
+                                                           const int *__restrict__ order, int64_t n, Grid g,
+                                                           RowItems t, int64_t n_chunks,
+                                                           const int32_t *__restrict__ row0, int64_t ns_cap,
+                                                           uint32_t *__restrict__ span_key,
+                                                           uint32_t *__restrict__ span_prim,
+                                                           unsigned long long *__restrict__ pair_total) {
     grid_dep_wait();
     __shared__ unsigned long long s_pairs;
+    __shared__ int s_base[kChunk / 32][kMaxRowGrid];       // per warp and row: slots before this warp's
+    __shared__ unsigned s_mask[kChunk / 32][kMaxRowGrid];  // per warp and row: the lanes covering it
+    __shared__ int s_row0[kMaxRowGrid];                    // this chunk's start of each row
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_pairs = 0;
+    for (int r = threadIdx.x; r < kMaxRowGrid; r += kChunk) s_row0[r] = row0[(int64_t)r * n_chunks + blockIdx.x];
+    for (int x = threadIdx.x; x < (kChunk / 32) * kMaxRowGrid; x += kChunk) (&s_base[0][0])[x] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (n + 31) / 32;
-    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int kept = 0;
-    if (w < nw) {
-        const int64_t j = w + (int64_t)lane * nw;
-        int i = 0, area = 0, base = 0, k = 0;
-        int4 bb = make_int4(0, 0, 0, 0);
-        CullData d = {};
-        Grid gl = g;
-        if (j < n) {
-            i = order[j];
-            base = slot0[j];
-            if (ITEMS) {
-                k = item_of_record(t, i);
-                gl.W = t.W[k];
-                gl.H = t.H[k];
-                gl.Wt = t.Wt[k];
-                gl.Ht = t.Ht[k];
-            }
-            area = box_of(bbox, tcount, i, gl, bb);
-            if (area > 0) d = load_cull(rec, i);
+    const int64_t j = (int64_t)blockIdx.x * kChunk + threadIdx.x;
+    int i = 0, h = 0, k = 0;
+    int4 bb = make_int4(0, 0, 0, 0);
+    Grid gl = g;
+    CullData d = {};
+    if (j < n) {
+        h = position_box<ITEMS>(bbox, tcount, order, j, g, t, i, k, gl, bb);
+        if (h > 0) d = load_cull(rec, i);
+    }
+    // the warp's rows [rlo, rhi): each row's lanes (ballot) and their number
+    const int rlo = __reduce_min_sync(kFullMask, h > 0 ? bb.y : kMaxRowGrid);
+    const int rhi = __reduce_max_sync(kFullMask, h > 0 ? bb.y + h : 0);
+    for (int r = rlo; r < rhi; ++r) {
+        const unsigned m = __ballot_sync(kFullMask, h > 0 && bb.y <= r && r < bb.y + h);
+        if (lane == 0) {
+            s_mask[wl][r] = m;
+            s_base[wl][r] = __popc(m);
         }
-        const int h = area > 0 ? bb.w - bb.y : 0;
-        const int incl = warp_incl_scan(h);
-        const int rows = __shfl_sync(kFullMask, incl, 31);
-        const int excl = incl - h;
-        for (int f0 = 0; f0 < rows; f0 += 32) {
-            const int f = f0 + lane;
-            const int p = lane_of(incl, f);
-            const CullData e = shfl_cull(d, p);
-            const int excl_p = __shfl_sync(kFullMask, excl, p);
-            const int ty = __shfl_sync(kFullMask, bb.y, p) + f - excl_p;
-            const int x0 = __shfl_sync(kFullMask, bb.x, p), x1 = __shfl_sync(kFullMask, bb.z, p);
-            const int base_p = __shfl_sync(kFullMask, base, p), i_p = __shfl_sync(kFullMask, i, p);
-            Grid gp = g;
-            uint32_t item = 0;
-            if (ITEMS) {
-                gp.W = __shfl_sync(kFullMask, gl.W, p);
-                gp.H = __shfl_sync(kFullMask, gl.H, p);
-                item = (uint32_t)__shfl_sync(kFullMask, k, p) << kSpanItemShift;
+    }
+    __syncthreads();
+    // per row: the counts of the warps before each warp (exclusive prefix over the 8 warps)
+    for (int r = threadIdx.x; r < kMaxRowGrid; r += kChunk) {
+        int acc = 0;
+#pragma unroll
+        for (int w = 0; w < kChunk / 32; ++w) {
+            const int c = s_base[w][r];
+            s_base[w][r] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    const int incl = warp_incl_scan(h);
+    const int rows = __shfl_sync(kFullMask, incl, 31);
+    const int excl = incl - h;
+    int kept = 0;
+    for (int f0 = 0; f0 < rows; f0 += 32) {
+        const int f = f0 + lane;
+        const int p = lane_of(incl, f);
+        const CullData e = shfl_cull(d, p);
+        const int excl_p = __shfl_sync(kFullMask, excl, p);
+        const int ty = __shfl_sync(kFullMask, bb.y, p) + f - excl_p;
+        const int x0 = __shfl_sync(kFullMask, bb.x, p), x1 = __shfl_sync(kFullMask, bb.z, p);
+        const int i_p = __shfl_sync(kFullMask, i, p);
+        Grid gp = g;
+        uint32_t item = 0;
+        if (ITEMS) {
+            gp.W = __shfl_sync(kFullMask, gl.W, p);
+            gp.H = __shfl_sync(kFullMask, gl.H, p);
+            item = (uint32_t)__shfl_sync(kFullMask, k, p) << kSpanItemShift;
+        }
+        if (f < rows) {
+            int ka = 0, kb = -1;
+            const int c = row_span_in_box(e, gp, ty, x0, x1, ka, kb);
+            const int64_t s = (int64_t)s_row0[ty] + s_base[wl][ty] + __popc(s_mask[wl][ty] & ((1u << p) - 1u));
+            if (s < ns_cap) {
+                span_key[s] = c > 0 ? item | ((uint32_t)c << 15) | ((uint32_t)ka << 8) | (uint32_t)ty : kRowNone;
+                span_prim[s] = (uint32_t)i_p;
             }
-            if (f < rows) {
-                int ka = 0, kb = -1;
-                const int c = row_span_in_box(e, gp, ty, x0, x1, ka, kb);
-                const int64_t s = (int64_t)base_p + (f - excl_p);
-                if (s < ns_cap) {
-                    span_key[s] = c > 0 ? item | ((uint32_t)c << 15) | ((uint32_t)ka << 8) | (uint32_t)ty : kRowNone;
-                    span_prim[s] = (uint32_t)i_p;
-                }
-                kept += c;
-            }
+            kept += c;
         }
     }
     if (pair_total) {
@@ -235,14 +277,17 @@ int column_bits(const RowItems &t) {
     return b;
 }
 
-// The pair offsets overwrite the span records once the span sort has moved them (so a span costs
-// 16 bytes of workspace besides the sort's scratch).
+// The row-count matrix (128 rows x chunks of 256 positions) and its scan depend on the records only;
+// a span slot costs 12 bytes (key, record, pair offset), a pair 8 (tile code, record) besides the
+// column pass's scratch.
 struct RowsLayout {
-    size_t slot0, part_n, totals;          // depend on the records only
-    size_t key, prim, skey, sprim, part_s;  // on the span slots (prim: then pair0)
+    size_t count, row0, part_n, totals;     // depend on the records only
+    size_t skey, sprim, pair0, part_s;      // on the span slots
     size_t sort_ws, codes, pvals, by_code;  // on the pairs
     size_t total;
 };
+
+int64_t row_count_entries(int64_t n) { return (int64_t)kMaxRowGrid * ((n + kChunk - 1) / kChunk); }
 
 RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, const RowItems &t) {
     RowsLayout L;
@@ -252,18 +297,16 @@ RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, const RowItems &t) {
         o += align_up(bytes);
         return at;
     };
-    const int64_t nc = n_codes(t);
-    L.slot0 = take((size_t)(n + 1) * 4);
-    L.part_n = take(scan_partials_bytes(n));
+    const int64_t nc = n_codes(t), m = row_count_entries(n);
+    L.count = take((size_t)m * 4);
+    L.row0 = take((size_t)(m + 1) * 4);
+    L.part_n = take(scan_partials_bytes(m > n ? m : n));  // the row-count scan, then the kept-count sum
     L.totals = take(4 * sizeof(int64_t));
-    L.key = take((size_t)ns * 4);
-    L.prim = take((size_t)(ns + 1) * 4);
     L.skey = take((size_t)ns * 4);
     L.sprim = take((size_t)ns * 4);
+    L.pair0 = take((size_t)(ns + 1) * 4);
     L.part_s = take(scan_partials_bytes(ns));
-    // the span sort, then the pair sort: one pass each (8 row bits, at most 7 column bits)
-    const size_t sws = sort_u32_onepass_workspace_bytes(ns), pws = sort_u32_onepass_workspace_bytes(ni);
-    L.sort_ws = take(sws > pws ? sws : pws);
+    L.sort_ws = take(sort_u32_onepass_workspace_bytes(ni));  // the column pass (16- or 32-bit codes)
     L.codes = take((size_t)ni * 4);
     L.pvals = take((size_t)ni * 4);
     L.by_code = take((size_t)nc * 8);
@@ -376,10 +419,10 @@ Readback *readback_slots() {
 
 // order: the depth order of the n records (each item's in its own block); isect_count (NULL: none):
 // their kept tile counts.  The span total (and, with isect_count, the pair total) is read back
-// after the scan of the box heights, the pair total otherwise from the emission.  When the
+// after the scan of the row-count matrix, the pair total otherwise from the emission.  When the
 // workspace has room for `capacity` pairs and some span slots, the emission is queued before the
-// host reads the span total (its writes bounded by that room) and the span sort before it reads
-// the pair total, so the device does not idle while the host waits; otherwise each count is read
+// host reads the span total (its writes bounded by that room) and the span-length scan before it
+// reads the pair total, so the device does not idle while the host waits; otherwise each count is read
 // with the stream synchronised before the work that needs it.  Returns XPR_ERR_CAPACITY (n_isect
 // and n_spans set as far as known, vals and ranges unwritten) when vals holds fewer than n_isect
 // pairs or the workspace is below bin_rows_workspace_bytes.
@@ -409,15 +452,20 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     const RowsLayout L0 = rows_layout(n, 0, 0, t);
     if (ws_bytes < L0.total) return fail(XPR_ERR_INVALID, "xpr_bin_rows: workspace %zu < %zu bytes", ws_bytes, L0.total);
     char *p = reinterpret_cast<char *>(ws);
-    int32_t *slot0 = reinterpret_cast<int32_t *>(p + L0.slot0);
+    int32_t *count = reinterpret_cast<int32_t *>(p + L0.count);
+    int32_t *row0 = reinterpret_cast<int32_t *>(p + L0.row0);
     int64_t *tot = reinterpret_cast<int64_t *>(p + L0.totals);  // span total, kept total, pair total, emitted pairs
     const int4 *bb4 = reinterpret_cast<const int4 *>(bbox);
     const int64_t ns_cap = span_room(n, capacity, t, ws_bytes);
     Readback *rb = ns_cap >= 0 ? readback_slots() : nullptr;
-    // span slot offsets: the scan of the box heights in depth order (the heights computed in the
-    // scan's own reads); with the kept counts, the pair total is their sum
-    int s = items ? launch_scan(BoxRowsItem<true>{bb4, tc, order, g, t}, slot0, n, p + L0.part_n, tot, st)
-                  : launch_scan(BoxRowsItem<false>{bb4, tc, order, g, t}, slot0, n, p + L0.part_n, tot, st);
+    // the slots grouped by row: the box rows counted per (row, chunk of 256 depth positions), the
+    // row-major matrix scanned into each chunk's start in each row (its total: the slot count);
+    // with the kept counts, the pair total is their sum
+    const int64_t n_chunks = (n + kChunk - 1) / kChunk;
+    XPR_CUDA_TRY(launch_dependent(items ? row_count_kernel<true> : row_count_kernel<false>, dim3((unsigned)n_chunks),
+                                  dim3(kChunk), 0, st, bb4, tc, order, n, g, t, n_chunks, count));
+    XPR_LAUNCH_CHECK("row_count_kernel");
+    int s = launch_scan(CountItem{count}, row0, row_count_entries(n), p + L0.part_n, tot, st);
     if (s != XPR_OK) return s;
     if (isect_count) {
         s = launch_scan(CountItem{isect_count}, nullptr, n, p + L0.part_n, tot + 1, st);
@@ -426,10 +474,10 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
         XPR_CUDA_TRY(cudaMemsetAsync(tot + 3, 0, sizeof(int64_t), st));
     }
     auto emit = [&](const RowsLayout &L, int64_t room, unsigned long long *pairs) -> int {
-        uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
-        const unsigned eg = (unsigned)(((n + 31) / 32 * 32 + 255) / 256);
-        XPR_CUDA_TRY(launch_dependent(items ? span_emit_kernel<true> : span_emit_kernel<false>, dim3(eg), dim3(256), 0,
-                                      st, rec, bb4, tc, order, n, g, t, (const int32_t *)slot0, room, key, prim, pairs));
+        uint32_t *skey = reinterpret_cast<uint32_t *>(p + L.skey), *sprim = reinterpret_cast<uint32_t *>(p + L.sprim);
+        XPR_CUDA_TRY(launch_dependent(items ? span_emit_kernel<true> : span_emit_kernel<false>,
+                                      dim3((unsigned)n_chunks), dim3(kChunk), 0, st, rec, bb4, tc, order, n, g, t,
+                                      n_chunks, (const int32_t *)row0, room, skey, sprim, pairs));
         XPR_LAUNCH_CHECK("span_emit_kernel");
         return XPR_OK;
     };
@@ -470,12 +518,8 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
         if ((isect_count && ni > capacity) || ws_bytes < L.total) return XPR_ERR_CAPACITY;
         if ((s = emit(L, ns, nullptr))) return s;
     }
-    uint32_t *key = reinterpret_cast<uint32_t *>(p + L.key), *prim = reinterpret_cast<uint32_t *>(p + L.prim);
     uint32_t *skey = reinterpret_cast<uint32_t *>(p + L.skey), *sprim = reinterpret_cast<uint32_t *>(p + L.sprim);
-    int32_t *pair0 = reinterpret_cast<int32_t *>(prim);  // the records are dead once moved into sprim
-    s = launch_sort_u32_bits(key, prim, ns, 256, 0, 8, skey, sprim, nullptr, p + L.sort_ws,
-                             sort_u32_onepass_workspace_bytes(ns), st);
-    if (s != XPR_OK) return s;
+    int32_t *pair0 = reinterpret_cast<int32_t *>(p + L.pair0);
     s = launch_scan(SpanLenItem{skey}, pair0, ns, p + L.part_s, tot + 2, st);
     if (s != XPR_OK) return s;
     if (!isect_count) {
