@@ -191,55 +191,193 @@ __global__ void __launch_bounds__(kChunk) span_emit_kernel(const float *__restri
 
 __device__ __forceinline__ int span_len(uint32_t key) { return (int)((key >> 15) & 0xffu); }
 
-// Warp w takes the sorted spans [32 w, 32 w + 32): their pairs are contiguous from the first span's
-// offset, and the warp writes them 32 at a time, lane k writing pair k of the warp's flattened list
-// (its span found from the ends of the non-empty spans, which are distinct).
-template <typename CT>  // the tile code's type: 16 bits when every code fits, else 32
-__global__ void __launch_bounds__(256) span_expand_kernel(const uint32_t *__restrict__ skey,
-                                                          const uint32_t *__restrict__ sprim, int64_t ns,
-                                                          const int32_t *__restrict__ pair0, int64_t capacity,
-                                                          CT *__restrict__ codes, uint32_t *__restrict__ vals) {
+constexpr int kColPairs = 4096;                     // pairs per block of the column scatter
+constexpr int kColStage = kColPairs + kMaxRowGrid;  // a block's pairs (its last span may run past the window)
+constexpr int kColWarps = 8;
+
+// Block b of the column scatter takes the spans whose first pair lies in [b P, b P + P), P = 4096:
+// first[b] = the first span at or past b P (every span holds at most 128 < P pairs, so one window
+// boundary at most falls inside a span's pairs), first[nb] = ns.  pair0[ns + 1]: the spans' first pairs.
+__global__ void col_first_kernel(const int32_t *__restrict__ pair0, int64_t ns, int64_t nb,
+                                 int32_t *__restrict__ first) {
     grid_dep_wait();
-    __shared__ uint2 s_sp[8][32];  // per warp: the non-empty spans' (first code, primitive)
-    __shared__ int s_x[8][32];     // and the index of their first pair in the warp's list
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > ns) return;
+    if (q == 0) {
+        first[0] = 0;
+        first[nb] = (int32_t)ns;
+        return;
+    }
+    const int64_t a = pair0[q - 1], z = pair0[q];
+    const int64_t b = z / kColPairs;
+    if (b < nb && b * kColPairs > a) first[b] = (int32_t)q;
+}
+
+// Column coverage of the spans [q0, q1) into d[0..128] as a difference array (+1 at the first kept
+// column, -1 one past the last): its prefix over the columns is the number of pairs per column.
+__device__ __forceinline__ void add_span_columns(const uint32_t *__restrict__ skey, int64_t q0, int64_t q1, int step,
+                                                 int lane0, int *d) {
+    for (int64_t q = q0 + lane0; q < q1; q += step) {
+        const uint32_t key = skey[q];
+        const int c = span_len(key);
+        if (c > 0) {
+            const int ka = (int)((key >> 8) & 0x7fu);
+            atomicAdd(&d[ka], 1);
+            atomicAdd(&d[ka + c], -1);
+        }
+    }
+}
+
+// In place: the inclusive prefix of d[0..127] over the columns, by one warp (4 columns a lane).
+__device__ __forceinline__ void warp_column_prefix(int *d) {
+    const int lane = threadIdx.x & 31;
+    int v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = d[4 * lane + j] + (j > 0 ? v[j - 1] : 0);
+    const int ex = warp_incl_scan(v[3]) - v[3];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[4 * lane + j] = ex + v[j];
+    __syncwarp();
+}
+
+// hist[tx * nb + b] = the pairs of column tx among block b's spans (tx < ncol).
+__global__ void __launch_bounds__(256) col_hist_kernel(const uint32_t *__restrict__ skey,
+                                                       const int32_t *__restrict__ first, int64_t nb, int ncol,
+                                                       int32_t *__restrict__ hist) {
+    grid_dep_wait();
+    __shared__ int d[kMaxRowGrid + 1];
+    for (int x = threadIdx.x; x <= kMaxRowGrid; x += blockDim.x) d[x] = 0;
+    __syncthreads();
+    add_span_columns(skey, first[blockIdx.x], first[blockIdx.x + 1], blockDim.x, threadIdx.x, d);
+    __syncthreads();
+    if (threadIdx.x < 32) warp_column_prefix(d);
+    __syncthreads();
+    for (int tx = threadIdx.x; tx < ncol; tx += blockDim.x) hist[(int64_t)tx * nb + blockIdx.x] = d[tx];
+}
+
+// The stable pass by column over the row-grouped spans, without expanding them first: block b
+// places the pairs of its spans (the window of col_first_kernel) at off[tx * nb + b] (the scanned
+// column-major histogram) plus their rank among the block's pairs of column tx.  The 8 warps take
+// contiguous runs of the block's spans; a warp's counts per column (difference arrays) give every
+// warp its start in each column; inside a warp, 32 spans at a time, the lanes flatten the spans'
+// pairs, first marking each covered column with the span's bit, then ranking each pair by the
+// bits of the earlier spans on its column.  The pairs are staged in shared memory in output order
+// and written out coalesced, with the tile code's range bounds where the code changes (by_code:
+// x the least position, y the complement of the greatest end, both as unsigned minima over
+// 0xffffffff-filled entries).
+__global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__restrict__ skey,
+                                                          const uint32_t *__restrict__ sprim,
+                                                          const int32_t *__restrict__ first, int64_t nb, int ncol,
+                                                          const int32_t *__restrict__ off,
+                                                          uint32_t *__restrict__ vals, uint2 *__restrict__ by_code) {
+    grid_dep_wait();
+    __shared__ uint32_t s_val[kColStage];
+    __shared__ uint32_t s_code[kColStage];
+    __shared__ int s_base[kColWarps][kMaxRowGrid + 1];  // per warp and column: counts, then its next place
+    __shared__ unsigned s_mask[kColWarps][kMaxRowGrid];  // per warp and column: the spans covering it
+    __shared__ uint2 s_sp[kColWarps][32];                 // per warp: the non-empty spans' (first code, record)
+    __shared__ int s_x[kColWarps][32];                    // and their first pair in the warp's flattened list
+    __shared__ int s_gofs[kMaxRowGrid];                   // per column: output position minus staged position
+    __shared__ int s_wsum[4];
+    __shared__ int s_total;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t q0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wl) * 32;
-    if (q0 >= ns) return;
-    const int64_t q = q0 + lane;
-    int len = 0;
-    uint32_t code0 = 0, prim = 0;
-    if (q < ns) {
-        const uint32_t key = skey[q];
-        len = span_len(key);
-        if (len > 0) {  // item, first kept column, row
-            code0 = ((key >> kSpanItemShift) << kItemShift) | (((key >> 8) & 0x7fu) << 7) | (key & 0x7fu);
-            prim = sprim[q];
-        }
-    }
-    const int64_t base = pair0[q0];
-    const int incl = warp_incl_scan(len);
-    const int total = __shfl_sync(kFullMask, incl, 31);
-    const unsigned nonempty = __ballot_sync(kFullMask, len > 0);
-    if (len > 0) {
-        const int slot = __popc(nonempty & lt_mask);
-        s_sp[wl][slot] = make_uint2(code0, prim);
-        s_x[wl][slot] = incl - len;
-    }
+    for (int x = threadIdx.x; x < kColWarps * (kMaxRowGrid + 1); x += blockDim.x) (&s_base[0][0])[x] = 0;
+    const int64_t q0 = first[blockIdx.x], q1 = first[blockIdx.x + 1];
+    const int64_t per_warp = ((q1 - q0 + kColWarps - 1) / kColWarps + 31) / 32 * 32;
+    const int64_t wq0 = min(q1, q0 + wl * per_warp), wq1 = min(q1, wq0 + per_warp);
+    __syncthreads();
+    add_span_columns(skey, wq0, wq1, 32, lane, s_base[wl]);
     __syncwarp();
-    for (int k0 = 0; k0 < total; k0 += 32) {
-        const int k = k0 + lane;
-        const int e = incl - k0;
-        const unsigned ends = __reduce_or_sync(kFullMask, (len > 0 && e > 0 && e <= 32) ? 1u << (e - 1) : 0u);
-        const int sp = __popc(__ballot_sync(kFullMask, len > 0 && e <= 0)) + __popc(ends & lt_mask);
-        if (k < total) {
-            const uint2 r = s_sp[wl][sp];
-            const int64_t pos = base + k;
-            if (pos < capacity) {
-                codes[pos] = (CT)(r.x + ((uint32_t)(k - s_x[wl][sp]) << 7));
-                vals[pos] = r.y;
+    warp_column_prefix(s_base[wl]);
+    __syncthreads();
+    // per column: the warps' exclusive prefix, then the columns' starts in the staged order
+    int ctot = 0;
+    if (threadIdx.x < kMaxRowGrid) {
+        const int tx = threadIdx.x;
+#pragma unroll
+        for (int w = 0; w < kColWarps; ++w) {
+            const int c = s_base[w][tx];
+            s_base[w][tx] = ctot;
+            ctot += c;
+        }
+        const int incl = warp_incl_scan(ctot);
+        if (lane == 31) s_wsum[wl] = incl;
+        s_gofs[tx] = incl - ctot;  // exclusive within the warp for now
+    }
+    __syncthreads();
+    if (threadIdx.x < kMaxRowGrid) {
+        const int tx = threadIdx.x;
+        int pre = 0;
+        for (int w = 0; w < wl; ++w) pre += s_wsum[w];
+        const int start = pre + s_gofs[tx];
+#pragma unroll
+        for (int w = 0; w < kColWarps; ++w) s_base[w][tx] += start;
+        s_gofs[tx] = tx < ncol ? off[(int64_t)tx * nb + blockIdx.x] - start : 0;
+        if (tx == kMaxRowGrid - 1) s_total = start + ctot;
+    }
+    __syncthreads();
+    for (int64_t r0 = wq0; r0 < wq1; r0 += 32) {
+        const int64_t q = r0 + lane;
+        int len = 0;
+        uint32_t code0 = 0, prim = 0;
+        if (q < wq1) {
+            const uint32_t key = skey[q];
+            len = span_len(key);
+            if (len > 0) {  // item, first kept column, row
+                code0 = ((key >> kSpanItemShift) << kItemShift) | (((key >> 8) & 0x7fu) << 7) | (key & 0x7fu);
+                prim = sprim[q];
             }
         }
+        const int incl = warp_incl_scan(len);
+        const int total = __shfl_sync(kFullMask, incl, 31);
+        const unsigned nonempty = __ballot_sync(kFullMask, len > 0);
+        if (len > 0) {
+            const int slot = __popc(nonempty & lt_mask);
+            s_sp[wl][slot] = make_uint2(code0, prim);
+            s_x[wl][slot] = incl - len;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s_mask[wl][lane + 32 * j] = 0u;
+        __syncwarp();
+        // pass 1 marks the columns, pass 2 ranks the pairs: pair k of the warp's flattened list
+        // belongs to the non-empty span sp (found from the ends of the spans, which are distinct)
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int k0 = 0; k0 < total; k0 += 32) {
+                const int k = k0 + lane;
+                const int e = incl - k0;
+                const unsigned ends = __reduce_or_sync(kFullMask, (len > 0 && e > 0 && e <= 32) ? 1u << (e - 1) : 0u);
+                const int sp = __popc(__ballot_sync(kFullMask, len > 0 && e <= 0)) + __popc(ends & lt_mask);
+                if (k < total) {
+                    const uint2 r = s_sp[wl][sp];
+                    const uint32_t dx = (uint32_t)(k - s_x[wl][sp]);
+                    const uint32_t code = r.x + (dx << 7);
+                    const int tx = (int)((code >> 7) & 0x7fu);
+                    if (pass == 0) {
+                        atomicOr(&s_mask[wl][tx], 1u << sp);
+                    } else {
+                        const int li = s_base[wl][tx] + __popc(s_mask[wl][tx] & ((1u << sp) - 1u));
+                        s_val[li] = r.y;
+                        s_code[li] = code;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s_base[wl][lane + 32 * j] += __popc(s_mask[wl][lane + 32 * j]);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int T = s_total;
+    for (int li = threadIdx.x; li < T; li += blockDim.x) {
+        const uint32_t code = s_code[li];
+        const uint32_t g = (uint32_t)(s_gofs[(code >> 7) & 0x7fu] + li);
+        vals[g] = s_val[li];
+        if (li == 0 || s_code[li - 1] != code) atomicMin(&by_code[code].x, g);
+        if (li == T - 1 || s_code[li + 1] != code) atomicMin(&by_code[code].y, ~(g + 1u));
     }
 }
 
@@ -249,7 +387,8 @@ struct SpanLenItem {  // scan items: the pairs of sorted span q
 };
 
 // ranges[tile0[k] + ty Wt[k] + tx] = the range found for tile code (k << 14) | (tx << 7) | ty
-__global__ void permute_ranges_kernel(const int2 *__restrict__ by_code, RowItems t, int64_t n_tiles,
+// (by_code as the column scatter leaves it: [x, ~y), x = 0xffffffff for a code with no pair)
+__global__ void permute_ranges_kernel(const uint2 *__restrict__ by_code, RowItems t, int64_t n_tiles,
                                       int2 *__restrict__ ranges) {
     grid_dep_wait();
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -258,7 +397,8 @@ __global__ void permute_ranges_kernel(const int2 *__restrict__ by_code, RowItems
     while (k + 1 < t.count && gt >= t.tile0[k + 1]) ++k;
     const int local = (int)(gt - t.tile0[k]);
     const int tx = local % t.Wt[k], ty = local / t.Wt[k];
-    ranges[gt] = by_code[((int64_t)k << kItemShift) | (tx << 7) | ty];
+    const uint2 r = by_code[((int64_t)k << kItemShift) | (tx << 7) | ty];
+    ranges[gt] = r.x == 0xffffffffu ? make_int2(0, 0) : make_int2((int)r.x, (int)~r.y);
 }
 
 size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
@@ -270,20 +410,23 @@ int64_t n_codes(const RowItems &t) {
     return ((int64_t)(t.count - 1) << kItemShift) + (int64_t)wt * kMaxRowGrid;
 }
 
-int column_bits(const RowItems &t) {
-    int wt = 1, b = 0;
+// The widest grid's tile columns: the columns of the column scatter's histogram.
+int n_columns(const RowItems &t) {
+    int wt = 1;
     for (int k = 0; k < t.count; ++k) wt = t.Wt[k] > wt ? t.Wt[k] : wt;
-    while ((1 << b) < wt) ++b;
-    return b;
+    return wt;
 }
 
+int64_t col_blocks(int64_t ni) { return (ni + kColPairs - 1) / kColPairs; }
+
 // The row-count matrix (128 rows x chunks of 256 positions) and its scan depend on the records only;
-// a span slot costs 12 bytes (key, record, pair offset), a pair 8 (tile code, record) besides the
-// column pass's scratch.
+// a span slot costs 12 bytes (key, record, pair offset); the pairs need the column histogram (one
+// count per column and window of 4096 pairs) and its scan.
 struct RowsLayout {
-    size_t count, row0, part_n, totals;     // depend on the records only
-    size_t skey, sprim, pair0, part_s;      // on the span slots
-    size_t sort_ws, codes, pvals, by_code;  // on the pairs
+    size_t count, row0, part_n, totals;   // depend on the records only
+    size_t skey, sprim, pair0, part_s;    // on the span slots
+    size_t first, hist, off, part_h;      // on the pairs
+    size_t by_code;
     size_t total;
 };
 
@@ -306,9 +449,11 @@ RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, const RowItems &t) {
     L.sprim = take((size_t)ns * 4);
     L.pair0 = take((size_t)(ns + 1) * 4);
     L.part_s = take(scan_partials_bytes(ns));
-    L.sort_ws = take(sort_u32_onepass_workspace_bytes(ni));  // the column pass (16- or 32-bit codes)
-    L.codes = take((size_t)ni * 4);
-    L.pvals = take((size_t)ni * 4);
+    const int64_t nb = col_blocks(ni), mh = nb * n_columns(t);
+    L.first = take((size_t)(nb + 1) * 4);
+    L.hist = take((size_t)mh * 4);
+    L.off = take((size_t)(mh + 1) * 4);
+    L.part_h = take(scan_partials_bytes(mh));
     L.by_code = take((size_t)nc * 8);
     L.total = o;
     return L;
@@ -535,36 +680,31 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
         if (ni > capacity || (!early && ws_bytes < rows_layout(n, ns, ni, t).total)) return XPR_ERR_CAPACITY;
     }
     const RowsLayout LP = early ? L : rows_layout(n, ns, ni, t);
-    // tile codes of 16 bits when every code fits (at most four items of 128 x 128 tiles): half the
-    // key bytes the expansion writes and the column pass reads
-    const int64_t nc = n_codes(t);
-    const bool narrow = nc <= 65536;
-    void *codes = p + LP.codes;
-    uint32_t *pvals = reinterpret_cast<uint32_t *>(p + LP.pvals);
-    const int64_t swarps = (ns + 31) / 32;
-    if (ns > 0) {
-        const dim3 eg((unsigned)((swarps * 32 + 255) / 256));
-        if (narrow)
-            XPR_CUDA_TRY(launch_dependent(span_expand_kernel<uint16_t>, eg, dim3(256), 0, st, (const uint32_t *)skey,
-                                          (const uint32_t *)sprim, ns, (const int32_t *)pair0, ni,
-                                          reinterpret_cast<uint16_t *>(codes), pvals));
-        else
-            XPR_CUDA_TRY(launch_dependent(span_expand_kernel<uint32_t>, eg, dim3(256), 0, st, (const uint32_t *)skey,
-                                          (const uint32_t *)sprim, ns, (const int32_t *)pair0, ni,
-                                          reinterpret_cast<uint32_t *>(codes), pvals));
-        XPR_LAUNCH_CHECK("span_expand_kernel");
+    // the pass by column straight from the spans: windows of 4096 pairs, their column histogram
+    // scanned column-major, each window's pairs placed by column and rank
+    uint2 *by_code = reinterpret_cast<uint2 *>(p + LP.by_code);
+    XPR_CUDA_TRY(cudaMemsetAsync(by_code, 0xff, (size_t)n_codes(t) * 8, st));
+    if (ni > 0) {
+        const int64_t nb = col_blocks(ni);
+        const int ncol = n_columns(t);
+        int32_t *first = reinterpret_cast<int32_t *>(p + LP.first);
+        int32_t *hist = reinterpret_cast<int32_t *>(p + LP.hist), *off = reinterpret_cast<int32_t *>(p + LP.off);
+        XPR_CUDA_TRY(launch_dependent(col_first_kernel, dim3((unsigned)((ns + 1 + 255) / 256)), dim3(256), 0, st,
+                                      (const int32_t *)pair0, ns, nb, first));
+        XPR_LAUNCH_CHECK("col_first_kernel");
+        XPR_CUDA_TRY(launch_dependent(col_hist_kernel, dim3((unsigned)nb), dim3(256), 0, st, (const uint32_t *)skey,
+                                      (const int32_t *)first, nb, ncol, hist));
+        XPR_LAUNCH_CHECK("col_hist_kernel");
+        s = launch_scan(CountItem{hist}, off, nb * ncol, p + LP.part_h, nullptr, st);
+        if (s != XPR_OK) return s;
+        XPR_CUDA_TRY(launch_dependent(col_scatter_kernel, dim3((unsigned)nb), dim3(256), 0, st, (const uint32_t *)skey,
+                                      (const uint32_t *)sprim, (const int32_t *)first, nb, ncol, (const int32_t *)off,
+                                      vals, by_code));
+        XPR_LAUNCH_CHECK("col_scatter_kernel");
     }
-    int2 *by_code = reinterpret_cast<int2 *>(p + LP.by_code);
-    s = narrow ? launch_sort_u16_bits(reinterpret_cast<const uint16_t *>(codes), pvals, ni, (int32_t)nc, 7,
-                                      7 + column_bits(t), nullptr, vals, reinterpret_cast<int32_t *>(by_code),
-                                      p + LP.sort_ws, sort_u16_onepass_workspace_bytes(ni), st)
-               : launch_sort_u32_bits(reinterpret_cast<const uint32_t *>(codes), pvals, ni, (int32_t)nc, 7,
-                                      7 + column_bits(t), nullptr, vals, reinterpret_cast<int32_t *>(by_code),
-                                      p + LP.sort_ws, sort_u32_onepass_workspace_bytes(ni), st);
-    if (s != XPR_OK) return s;
     if (T > 0) {
         XPR_CUDA_TRY(launch_dependent(permute_ranges_kernel, dim3((unsigned)((T + 255) / 256)), dim3(256), 0, st,
-                                      (const int2 *)by_code, t, T, reinterpret_cast<int2 *>(ranges)));
+                                      (const uint2 *)by_code, t, T, reinterpret_cast<int2 *>(ranges)));
         XPR_LAUNCH_CHECK("permute_ranges_kernel");
     }
     return XPR_OK;
