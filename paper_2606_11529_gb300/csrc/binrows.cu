@@ -191,11 +191,11 @@ __global__ void __launch_bounds__(kChunk) span_emit_kernel(const float *__restri
 
 __device__ __forceinline__ int span_len(uint32_t key) { return (int)((key >> 15) & 0xffu); }
 
-constexpr int kColPairs = 4096;                     // pairs per block of the column scatter
-constexpr int kColStage = kColPairs + kMaxRowGrid;  // a block's pairs (its last span may run past the window)
+constexpr int kColPairs = 3968;                     // pairs per window of the column scatter
+constexpr int kColStage = kColPairs + kMaxRowGrid;  // a window's pairs (its last span may run past it): 4096
 constexpr int kColWarps = 8;
 
-// Block b of the column scatter takes the spans whose first pair lies in [b P, b P + P), P = 4096:
+// Block b of the column scatter takes the spans whose first pair lies in [b P, b P + P), P = 3968:
 // first[b] = the first span at or past b P (every span holds at most 128 < P pairs, so one window
 // boundary at most falls inside a span's pairs), first[nb] = ns.  pair0[ns + 1]: the spans' first pairs.
 __global__ void col_first_kernel(const int32_t *__restrict__ pair0, int64_t ns, int64_t nb,
@@ -260,29 +260,28 @@ __global__ void __launch_bounds__(256) col_hist_kernel(const uint32_t *__restric
 // places the pairs of its spans (the window of col_first_kernel) at off[tx * nb + b] (the scanned
 // column-major histogram) plus their rank among the block's pairs of column tx.  The 8 warps take
 // contiguous runs of the block's spans; a warp's counts per column (difference arrays) give every
-// warp its start in each column; inside a warp, 32 spans at a time, the lanes flatten the spans'
-// pairs, first marking each covered column with the span's bit, then ranking each pair by the
-// bits of the earlier spans on its column.  The pairs are staged in shared memory in output order
-// and written out coalesced, with the tile code's range bounds where the code changes (by_code:
-// x the least position, y the complement of the greatest end, both as unsigned minima over
-// 0xffffffff-filled entries).
+// warp its start in each column.  A warp then takes its spans 32 at a time: each span's lane bit is
+// XORed in at its first kept column and out one past its last, so the prefix XOR over the columns
+// is, per column, the mask of the spans covering it; each lane walks an equal share of the 32 spans'
+// pairs in order and ranks pair (span s, column tx) by the covering spans before s.  The pairs are
+// staged in shared memory in output order (tile code and record in one word) and written out
+// coalesced, with the tile code's range bounds where the code changes (by_code: x the least
+// position, y the complement of the greatest end, both as unsigned minima over 0xffffffff-filled
+// entries).
 __global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__restrict__ skey,
                                                           const uint32_t *__restrict__ sprim,
                                                           const int32_t *__restrict__ first, int64_t nb, int ncol,
                                                           const int32_t *__restrict__ off,
                                                           uint32_t *__restrict__ vals, uint2 *__restrict__ by_code) {
     grid_dep_wait();
-    __shared__ uint32_t s_val[kColStage];
-    __shared__ uint32_t s_code[kColStage];
-    __shared__ int s_base[kColWarps][kMaxRowGrid + 1];  // per warp and column: counts, then its next place
-    __shared__ unsigned s_mask[kColWarps][kMaxRowGrid];  // per warp and column: the spans covering it
-    __shared__ uint2 s_sp[kColWarps][32];                 // per warp: the non-empty spans' (first code, record)
-    __shared__ int s_x[kColWarps][32];                    // and their first pair in the warp's flattened list
-    __shared__ int s_gofs[kMaxRowGrid];                   // per column: output position minus staged position
+    __shared__ uint2 s_pc[kColStage];                    // staged pairs: (tile code, record)
+    __shared__ int s_base[kColWarps][kMaxRowGrid + 1];  // per warp and column: counts; then the XOR differences
+    __shared__ uint2 s_mb[kColWarps][kMaxRowGrid];      // per warp and column: (covering spans, next place)
+    __shared__ uint2 s_sp[kColWarps][32];               // per warp: the 32 spans' (first code | length << 24, record)
+    __shared__ int s_gofs[kMaxRowGrid];                 // per column: output position minus staged position
     __shared__ int s_wsum[4];
     __shared__ int s_total;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
     for (int x = threadIdx.x; x < kColWarps * (kMaxRowGrid + 1); x += blockDim.x) (&s_base[0][0])[x] = 0;
     const int64_t q0 = first[blockIdx.x], q1 = first[blockIdx.x + 1];
     const int64_t per_warp = ((q1 - q0 + kColWarps - 1) / kColWarps + 31) / 32 * 32;
@@ -318,66 +317,82 @@ __global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__rest
         if (tx == kMaxRowGrid - 1) s_total = start + ctot;
     }
     __syncthreads();
+    // this lane's columns 4 lane .. 4 lane + 3: the warp's next staged place in each
+    int next[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) next[j] = s_base[wl][4 * lane + j];
+    int *dif = s_base[wl];
     for (int64_t r0 = wq0; r0 < wq1; r0 += 32) {
         const int64_t q = r0 + lane;
-        int len = 0;
+        int len = 0, ka = 0;
         uint32_t code0 = 0, prim = 0;
         if (q < wq1) {
             const uint32_t key = skey[q];
             len = span_len(key);
             if (len > 0) {  // item, first kept column, row
-                code0 = ((key >> kSpanItemShift) << kItemShift) | (((key >> 8) & 0x7fu) << 7) | (key & 0x7fu);
+                ka = (int)((key >> 8) & 0x7fu);
+                code0 = ((key >> kSpanItemShift) << kItemShift) | ((uint32_t)ka << 7) | (key & 0x7fu);
                 prim = sprim[q];
             }
         }
         const int incl = warp_incl_scan(len);
         const int total = __shfl_sync(kFullMask, incl, 31);
-        const unsigned nonempty = __ballot_sync(kFullMask, len > 0);
+        __syncwarp();  // the previous round's readers are done with dif, s_mb and s_sp
+        s_sp[wl][lane] = make_uint2(code0 | ((uint32_t)len << 24), prim);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dif[lane + 32 * j] = 0;
+        if (lane == 0) dif[kMaxRowGrid] = 0;
+        __syncwarp();
         if (len > 0) {
-            const int slot = __popc(nonempty & lt_mask);
-            s_sp[wl][slot] = make_uint2(code0, prim);
-            s_x[wl][slot] = incl - len;
+            atomicXor(&dif[ka], 1 << lane);
+            atomicXor(&dif[ka + len], 1 << lane);
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) s_mask[wl][lane + 32 * j] = 0u;
         __syncwarp();
-        // pass 1 marks the columns, pass 2 ranks the pairs: pair k of the warp's flattened list
-        // belongs to the non-empty span sp (found from the ends of the spans, which are distinct)
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int k0 = 0; k0 < total; k0 += 32) {
-                const int k = k0 + lane;
-                const int e = incl - k0;
-                const unsigned ends = __reduce_or_sync(kFullMask, (len > 0 && e > 0 && e <= 32) ? 1u << (e - 1) : 0u);
-                const int sp = __popc(__ballot_sync(kFullMask, len > 0 && e <= 0)) + __popc(ends & lt_mask);
-                if (k < total) {
-                    const uint2 r = s_sp[wl][sp];
-                    const uint32_t dx = (uint32_t)(k - s_x[wl][sp]);
-                    const uint32_t code = r.x + (dx << 7);
-                    const int tx = (int)((code >> 7) & 0x7fu);
-                    if (pass == 0) {
-                        atomicOr(&s_mask[wl][tx], 1u << sp);
-                    } else {
-                        const int li = s_base[wl][tx] + __popc(s_mask[wl][tx] & ((1u << sp) - 1u));
-                        s_val[li] = r.y;
-                        s_code[li] = code;
-                    }
+        unsigned m[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m[j] = (unsigned)dif[4 * lane + j] ^ (j > 0 ? m[j - 1] : 0u);
+        unsigned x = m[3];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFullMask, x, o);
+            if (lane >= o) x ^= y;
+        }
+        x ^= m[3];  // the columns before this lane's
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            m[j] ^= x;
+            s_mb[wl][4 * lane + j] = make_uint2(m[j], (unsigned)next[j]);
+            next[j] += __popc(m[j]);
+        }
+        // this lane's share of the pairs: [k, kend) of the 32 spans' flattened list
+        int k = (total * lane) >> 5;
+        const int kend = (total * (lane + 1)) >> 5;
+        int sp = lane_of(incl, k);
+        int d = k - (__shfl_sync(kFullMask, incl, sp) - __shfl_sync(kFullMask, len, sp));
+        __syncwarp();
+        if (k < kend) {
+            uint2 e = s_sp[wl][sp];
+            int len_sp = (int)(e.x >> 24);
+            for (; k < kend; ++k, ++d) {
+                while (d == len_sp) {  // on to the next non-empty span
+                    e = s_sp[wl][++sp];
+                    len_sp = (int)(e.x >> 24);
+                    d = 0;
                 }
+                const uint32_t code = (e.x & 0xffffffu) + ((uint32_t)d << 7);
+                const uint2 mb = s_mb[wl][(code >> 7) & 0x7fu];
+                s_pc[mb.y + __popc(mb.x & ((1u << sp) - 1u))] = make_uint2(code, e.y);
             }
-            __syncwarp();
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) s_base[wl][lane + 32 * j] += __popc(s_mask[wl][lane + 32 * j]);
-        __syncwarp();
     }
     __syncthreads();
     const int T = s_total;
     for (int li = threadIdx.x; li < T; li += blockDim.x) {
-        const uint32_t code = s_code[li];
-        const uint32_t g = (uint32_t)(s_gofs[(code >> 7) & 0x7fu] + li);
-        vals[g] = s_val[li];
-        if (li == 0 || s_code[li - 1] != code) atomicMin(&by_code[code].x, g);
-        if (li == T - 1 || s_code[li + 1] != code) atomicMin(&by_code[code].y, ~(g + 1u));
+        const uint2 e = s_pc[li];
+        const uint32_t g = (uint32_t)(s_gofs[(e.x >> 7) & 0x7fu] + li);
+        vals[g] = e.y;
+        if (li == 0 || s_pc[li - 1].x != e.x) atomicMin(&by_code[e.x].x, g);
+        if (li == T - 1 || s_pc[li + 1].x != e.x) atomicMin(&by_code[e.x].y, ~(g + 1u));
     }
 }
 
@@ -421,7 +436,7 @@ int64_t col_blocks(int64_t ni) { return (ni + kColPairs - 1) / kColPairs; }
 
 // The row-count matrix (128 rows x chunks of 256 positions) and its scan depend on the records only;
 // a span slot costs 12 bytes (key, record, pair offset); the pairs need the column histogram (one
-// count per column and window of 4096 pairs) and its scan.
+// count per column and window of 3968 pairs) and its scan.
 struct RowsLayout {
     size_t count, row0, part_n, totals;   // depend on the records only
     size_t skey, sprim, pair0, part_s;    // on the span slots
@@ -680,7 +695,7 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
         if (ni > capacity || (!early && ws_bytes < rows_layout(n, ns, ni, t).total)) return XPR_ERR_CAPACITY;
     }
     const RowsLayout LP = early ? L : rows_layout(n, ns, ni, t);
-    // the pass by column straight from the spans: windows of 4096 pairs, their column histogram
+    // the pass by column straight from the spans: windows of 3968 pairs, their column histogram
     // scanned column-major, each window's pairs placed by column and rank
     uint2 *by_code = reinterpret_cast<uint2 *>(p + LP.by_code);
     XPR_CUDA_TRY(cudaMemsetAsync(by_code, 0xff, (size_t)n_codes(t) * 8, st));
