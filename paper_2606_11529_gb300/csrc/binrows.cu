@@ -95,8 +95,8 @@ struct CountItem {  // the kept tile counts, summed for the pair total
 // writes each row's span (the row-form cull of one (primitive, tile row)) straight to its place in
 // the slots grouped by row: the row's start for this chunk (the scanned count matrix), plus the
 // row's slots in the warps before this one, plus those of the lanes before this one in the warp
-// (one ballot per row of the warp's boxes).  So every row's spans lie in depth order, as a stable
-// sort of depth-ordered slots by row would leave them.  The warp flattens its boxes' rows over its
+// (the lane masks per row from XOR differences over the rows).  So every row's spans lie in depth
+// order, as a stable sort of depth-ordered slots by row would leave them.  The warp flattens its boxes' rows over its
 // lanes; slots at or beyond ns_cap are not written (the launch may precede the check of the slot
 // total against the workspace).  With items, each lane's image size and item travel with its rows
 // through the shuffles.  pair_total (may be NULL): receives the sum of the kept counts.
@@ -112,13 +112,16 @@ __global__ void __launch_bounds__(kChunk) span_emit_kernel(const float *__restri
     grid_dep_wait();
     __shared__ unsigned long long s_pairs;
     __shared__ int s_base[kChunk / 32][kMaxRowGrid];       // per warp and row: slots before this warp's
-    __shared__ unsigned s_mask[kChunk / 32][kMaxRowGrid];  // per warp and row: the lanes covering it
-    __shared__ int s_row0[kMaxRowGrid];                    // this chunk's start of each row
+    __shared__ unsigned s_mask[kChunk / 32][kMaxRowGrid + 1];  // per warp and row: the lanes covering it
+    __shared__ int s_row0[kMaxRowGrid];                        // this chunk's start of each row
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_pairs = 0;
     for (int r = threadIdx.x; r < kMaxRowGrid; r += kChunk) s_row0[r] = row0[(int64_t)r * n_chunks + blockIdx.x];
-    for (int x = threadIdx.x; x < (kChunk / 32) * kMaxRowGrid; x += kChunk) (&s_base[0][0])[x] = 0;
-    __syncthreads();
+    unsigned *dif = s_mask[wl];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dif[lane + 32 * j] = 0u;
+    if (lane == 0) dif[kMaxRowGrid] = 0u;
+    __syncwarp();
     const int64_t j = (int64_t)blockIdx.x * kChunk + threadIdx.x;
     int i = 0, h = 0, k = 0;
     int4 bb = make_int4(0, 0, 0, 0);
@@ -128,14 +131,29 @@ __global__ void __launch_bounds__(kChunk) span_emit_kernel(const float *__restri
         h = position_box<ITEMS>(bbox, tcount, order, j, g, t, i, k, gl, bb);
         if (h > 0) d = load_cull(rec, i);
     }
-    // the warp's rows [rlo, rhi): each row's lanes (ballot) and their number
-    const int rlo = __reduce_min_sync(kFullMask, h > 0 ? bb.y : kMaxRowGrid);
-    const int rhi = __reduce_max_sync(kFullMask, h > 0 ? bb.y + h : 0);
-    for (int r = rlo; r < rhi; ++r) {
-        const unsigned m = __ballot_sync(kFullMask, h > 0 && bb.y <= r && r < bb.y + h);
-        if (lane == 0) {
-            s_mask[wl][r] = m;
-            s_base[wl][r] = __popc(m);
+    // each row's covering lanes: every box's lane bit XORed in at its first row and out one past its
+    // last, then the prefix XOR over the rows (4 rows a lane); their number
+    if (h > 0) {
+        atomicXor(&dif[bb.y], 1u << lane);
+        atomicXor(&dif[bb.y + h], 1u << lane);
+    }
+    __syncwarp();
+    {
+        unsigned m[4];
+#pragma unroll
+        for (int jr = 0; jr < 4; ++jr) m[jr] = dif[4 * lane + jr] ^ (jr > 0 ? m[jr - 1] : 0u);
+        unsigned x = m[3];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFullMask, x, o);
+            if (lane >= o) x ^= y;
+        }
+        x ^= m[3];
+        __syncwarp();
+#pragma unroll
+        for (int jr = 0; jr < 4; ++jr) {
+            dif[4 * lane + jr] = m[jr] ^ x;
+            s_base[wl][4 * lane + jr] = __popc(m[jr] ^ x);
         }
     }
     __syncthreads();
@@ -195,22 +213,27 @@ constexpr int kColPairs = 3968;                     // pairs per window of the c
 constexpr int kColStage = kColPairs + kMaxRowGrid;  // a window's pairs (its last span may run past it): 4096
 constexpr int kColWarps = 8;
 
-// Block b of the column scatter takes the spans whose first pair lies in [b P, b P + P), P = 3968:
-// first[b] = the first span at or past b P (every span holds at most 128 < P pairs, so one window
-// boundary at most falls inside a span's pairs), first[nb] = ns.  pair0[ns + 1]: the spans' first pairs.
-__global__ void col_first_kernel(const int32_t *__restrict__ pair0, int64_t ns, int64_t nb,
+constexpr int kColSub = kColPairs / kColWarps;      // pairs per warp's share of a window: 496
+
+// Window b of the column scatter holds the spans whose first pair lies in [b P, b P + P), P = 3968,
+// and its warp w those whose first pair lies in sub-window u = 8 b + w, [u Q, u Q + Q), Q = 496:
+// first[u] = the first span at or past u Q (every span holds at most 128 < Q pairs, so at most one
+// sub-window boundary falls inside a span's pairs, right after its first); the sub-windows past
+// the last pair start at ns, as does first[8 nb].  pair0[ns + 1]: the spans' first pairs.
+__global__ void col_first_kernel(const int32_t *__restrict__ pair0, int64_t ns, int64_t nsub,
                                  int32_t *__restrict__ first) {
     grid_dep_wait();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q > ns) return;
     if (q == 0) {
         first[0] = 0;
-        first[nb] = (int32_t)ns;
+        for (int64_t u = (int64_t)pair0[ns] / kColSub + 1; u < nsub; ++u) first[u] = (int32_t)ns;
+        first[nsub] = (int32_t)ns;
         return;
     }
     const int64_t a = pair0[q - 1], z = pair0[q];
-    const int64_t b = z / kColPairs;
-    if (b < nb && b * kColPairs > a) first[b] = (int32_t)q;
+    const int64_t u = z / kColSub;
+    if (u < nsub && u * kColSub > a) first[u] = (int32_t)q;
 }
 
 // Column coverage of the spans [q0, q1) into d[0..128] as a difference array (+1 at the first kept
@@ -249,7 +272,8 @@ __global__ void __launch_bounds__(256) col_hist_kernel(const uint32_t *__restric
     __shared__ int d[kMaxRowGrid + 1];
     for (int x = threadIdx.x; x <= kMaxRowGrid; x += blockDim.x) d[x] = 0;
     __syncthreads();
-    add_span_columns(skey, first[blockIdx.x], first[blockIdx.x + 1], blockDim.x, threadIdx.x, d);
+    add_span_columns(skey, first[blockIdx.x * kColWarps], first[(blockIdx.x + 1) * kColWarps], blockDim.x,
+                     threadIdx.x, d);
     __syncthreads();
     if (threadIdx.x < 32) warp_column_prefix(d);
     __syncthreads();
@@ -258,9 +282,9 @@ __global__ void __launch_bounds__(256) col_hist_kernel(const uint32_t *__restric
 
 // The stable pass by column over the row-grouped spans, without expanding them first: block b
 // places the pairs of its spans (the window of col_first_kernel) at off[tx * nb + b] (the scanned
-// column-major histogram) plus their rank among the block's pairs of column tx.  The 8 warps take
-// contiguous runs of the block's spans; a warp's counts per column (difference arrays) give every
-// warp its start in each column.  A warp then takes its spans 32 at a time: each span's lane bit is
+// column-major histogram) plus their rank among the block's pairs of column tx.  Warp w takes the
+// spans of sub-window 8 b + w (about 496 pairs each); a warp's counts per column (difference
+// arrays) give every warp its start in each column.  A warp then takes its spans 32 at a time: each span's lane bit is
 // XORed in at its first kept column and out one past its last, so the prefix XOR over the columns
 // is, per column, the mask of the spans covering it; each lane walks an equal share of the 32 spans'
 // pairs in order and ranks pair (span s, column tx) by the covering spans before s.  The pairs are
@@ -274,7 +298,7 @@ __global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__rest
                                                           const int32_t *__restrict__ off,
                                                           uint32_t *__restrict__ vals, uint2 *__restrict__ by_code) {
     grid_dep_wait();
-    __shared__ uint2 s_pc[kColStage];                    // staged pairs: (tile code, record)
+    __shared__ __align__(16) uint2 s_pc[kColStage];      // staged pairs: (tile code, record)
     __shared__ int s_base[kColWarps][kMaxRowGrid + 1];  // per warp and column: counts; then the XOR differences
     __shared__ uint2 s_mb[kColWarps][kMaxRowGrid];      // per warp and column: (covering spans, next place)
     __shared__ uint2 s_sp[kColWarps][32];               // per warp: the 32 spans' (first code | length << 24, record)
@@ -283,9 +307,7 @@ __global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__rest
     __shared__ int s_total;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     for (int x = threadIdx.x; x < kColWarps * (kMaxRowGrid + 1); x += blockDim.x) (&s_base[0][0])[x] = 0;
-    const int64_t q0 = first[blockIdx.x], q1 = first[blockIdx.x + 1];
-    const int64_t per_warp = ((q1 - q0 + kColWarps - 1) / kColWarps + 31) / 32 * 32;
-    const int64_t wq0 = min(q1, q0 + wl * per_warp), wq1 = min(q1, wq0 + per_warp);
+    const int64_t wq0 = first[blockIdx.x * kColWarps + wl], wq1 = first[blockIdx.x * kColWarps + wl + 1];
     __syncthreads();
     add_span_columns(skey, wq0, wq1, 32, lane, s_base[wl]);
     __syncwarp();
@@ -386,13 +408,25 @@ __global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__rest
         }
     }
     __syncthreads();
+    // two staged pairs a thread: (code, record) of pairs li and li + 1 in one 16-byte read
     const int T = s_total;
-    for (int li = threadIdx.x; li < T; li += blockDim.x) {
-        const uint2 e = s_pc[li];
-        const uint32_t g = (uint32_t)(s_gofs[(e.x >> 7) & 0x7fu] + li);
-        vals[g] = e.y;
-        if (li == 0 || s_pc[li - 1].x != e.x) atomicMin(&by_code[e.x].x, g);
-        if (li == T - 1 || s_pc[li + 1].x != e.x) atomicMin(&by_code[e.x].y, ~(g + 1u));
+    const uint4 *s_pc2 = reinterpret_cast<const uint4 *>(s_pc);
+    for (int li = 2 * threadIdx.x; li < T; li += 2 * blockDim.x) {
+        const uint4 e = s_pc2[li >> 1];
+        const uint32_t g0 = (uint32_t)(s_gofs[(e.x >> 7) & 0x7fu] + li);
+        vals[g0] = e.y;
+        if (li == 0 || s_pc[li - 1].x != e.x) atomicMin(&by_code[e.x].x, g0);
+        if (li + 1 < T) {
+            const uint32_t g1 = (uint32_t)(s_gofs[(e.z >> 7) & 0x7fu] + li + 1);
+            vals[g1] = e.w;
+            if (e.z != e.x) {
+                atomicMin(&by_code[e.x].y, ~(g0 + 1u));
+                atomicMin(&by_code[e.z].x, g1);
+            }
+            if (li + 2 == T || s_pc[li + 2].x != e.z) atomicMin(&by_code[e.z].y, ~(g1 + 1u));
+        } else {
+            atomicMin(&by_code[e.x].y, ~(g0 + 1u));
+        }
     }
 }
 
@@ -465,7 +499,7 @@ RowsLayout rows_layout(int64_t n, int64_t ns, int64_t ni, const RowItems &t) {
     L.pair0 = take((size_t)(ns + 1) * 4);
     L.part_s = take(scan_partials_bytes(ns));
     const int64_t nb = col_blocks(ni), mh = nb * n_columns(t);
-    L.first = take((size_t)(nb + 1) * 4);
+    L.first = take((size_t)(nb * kColWarps + 1) * 4);
     L.hist = take((size_t)mh * 4);
     L.off = take((size_t)(mh + 1) * 4);
     L.part_h = take(scan_partials_bytes(mh));
@@ -705,7 +739,7 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
         int32_t *first = reinterpret_cast<int32_t *>(p + LP.first);
         int32_t *hist = reinterpret_cast<int32_t *>(p + LP.hist), *off = reinterpret_cast<int32_t *>(p + LP.off);
         XPR_CUDA_TRY(launch_dependent(col_first_kernel, dim3((unsigned)((ns + 1 + 255) / 256)), dim3(256), 0, st,
-                                      (const int32_t *)pair0, ns, nb, first));
+                                      (const int32_t *)pair0, ns, nb * kColWarps, first));
         XPR_LAUNCH_CHECK("col_first_kernel");
         XPR_CUDA_TRY(launch_dependent(col_hist_kernel, dim3((unsigned)nb), dim3(256), 0, st, (const uint32_t *)skey,
                                       (const int32_t *)first, nb, ncol, hist));
