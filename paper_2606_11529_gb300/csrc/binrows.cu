@@ -408,14 +408,22 @@ __global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__rest
         }
     }
     __syncthreads();
-    // two staged pairs a thread: (code, record) of pairs li and li + 1 in one 16-byte read
+    // two staged pairs a thread: (code, record) of pairs li and li + 1 in one 16-byte read, the
+    // neighbouring codes from the adjacent lanes
     const int T = s_total;
     const uint4 *s_pc2 = reinterpret_cast<const uint4 *>(s_pc);
-    for (int li = 2 * threadIdx.x; li < T; li += 2 * blockDim.x) {
-        const uint4 e = s_pc2[li >> 1];
+    for (int base = 0; base < T; base += 2 * blockDim.x) {
+        const int li = base + 2 * threadIdx.x;
+        const uint4 e = li < T ? s_pc2[li >> 1] : make_uint4(0u, 0u, 0u, 0u);
+        uint32_t prev = __shfl_up_sync(kFullMask, e.z, 1);
+        uint32_t next = __shfl_down_sync(kFullMask, e.x, 1);
+        if (li >= T) continue;
+        if (lane == 0) prev = li > 0 ? s_pc[li - 1].x : ~e.x;
+        if (li + 2 >= T) next = ~e.z;
+        else if (lane == 31) next = s_pc[li + 2].x;
         const uint32_t g0 = (uint32_t)(s_gofs[(e.x >> 7) & 0x7fu] + li);
         vals[g0] = e.y;
-        if (li == 0 || s_pc[li - 1].x != e.x) atomicMin(&by_code[e.x].x, g0);
+        if (prev != e.x) atomicMin(&by_code[e.x].x, g0);
         if (li + 1 < T) {
             const uint32_t g1 = (uint32_t)(s_gofs[(e.z >> 7) & 0x7fu] + li + 1);
             vals[g1] = e.w;
@@ -423,7 +431,7 @@ __global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__rest
                 atomicMin(&by_code[e.x].y, ~(g0 + 1u));
                 atomicMin(&by_code[e.z].x, g1);
             }
-            if (li + 2 == T || s_pc[li + 2].x != e.z) atomicMin(&by_code[e.z].y, ~(g1 + 1u));
+            if (next != e.z) atomicMin(&by_code[e.z].y, ~(g1 + 1u));
         } else {
             atomicMin(&by_code[e.x].y, ~(g0 + 1u));
         }

@@ -83,25 +83,14 @@ template <>
 __device__ __forceinline__ uint32_t tile_of<uint32_t>(uint32_t key) {
     return key;
 }
-template <>
-__device__ __forceinline__ uint32_t tile_of<uint16_t>(uint16_t key) {
-    return key;
-}
 
-// Loads keys [i, i + 4) (16-byte aligned) of a u16, u32 or u64 array.
+// Loads keys [i, i + 4) (16-byte aligned) of a u32 or u64 array.
 __device__ __forceinline__ void load4(const uint32_t *p, int64_t i, uint32_t (&k)[4]) {
     const uint4 v = *reinterpret_cast<const uint4 *>(p + i);
     k[0] = v.x;
     k[1] = v.y;
     k[2] = v.z;
     k[3] = v.w;
-}
-__device__ __forceinline__ void load4(const uint16_t *p, int64_t i, uint16_t (&k)[4]) {
-    const uint2 v = *reinterpret_cast<const uint2 *>(p + i);
-    k[0] = (uint16_t)(v.x & 0xffffu);
-    k[1] = (uint16_t)(v.x >> 16);
-    k[2] = (uint16_t)(v.y & 0xffffu);
-    k[3] = (uint16_t)(v.y >> 16);
 }
 __device__ __forceinline__ void load4(const uint64_t *p, int64_t i, uint64_t (&k)[4]) {
     const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(p + i);
@@ -901,9 +890,6 @@ size_t sort_tiles_workspace_bytes(int64_t n, int32_t n_tiles) {
     return workspace_bytes<uint32_t>(n);
 }
 
-size_t sort_u32_onepass_workspace_bytes(int64_t n) { return workspace_bytes<uint32_t>(n, 1); }
-size_t sort_u16_onepass_workspace_bytes(int64_t n) { return workspace_bytes<uint16_t>(n, 1); }
-
 int launch_sort(const uint64_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
                 uint64_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int end_bit = 32 + bits_for((int64_t)n_tiles - 1);
@@ -922,13 +908,6 @@ int launch_sort_u32_bits(const uint32_t *keys_in, const uint32_t *vals_in, int64
                          int end_bit, uint32_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws,
                          size_t ws_bytes, cudaStream_t st) {
     return radix_sort<uint32_t>(keys_in, vals_in, n, n_tiles, begin_bit, end_bit, keys_out, vals_out, ranges, ws,
-                                ws_bytes, st);
-}
-
-int launch_sort_u16_bits(const uint16_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
-                         int end_bit, uint16_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws,
-                         size_t ws_bytes, cudaStream_t st) {
-    return radix_sort<uint16_t>(keys_in, vals_in, n, n_tiles, begin_bit, end_bit, keys_out, vals_out, ranges, ws,
                                 ws_bytes, st);
 }
 

@@ -235,15 +235,8 @@ int launch_sort_tiles(const uint32_t *tiles_in, const uint32_t *vals_in, int64_t
                       cudaStream_t st);
 // stable sort of 4-byte keys by bits [begin_bit, end_bit) (workspace: sort_tiles_workspace_bytes(n, .));
 // ranges (NULL: none) are those of the whole key values, 0 .. n_tiles - 1
-// scratch of launch_sort_u32_bits for at most 8 key bits (one pass: no ping-pong copies)
-size_t sort_u32_onepass_workspace_bytes(int64_t n);
 int launch_sort_u32_bits(const uint32_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
                          int end_bit, uint32_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws,
-                         size_t ws_bytes, cudaStream_t st);
-// the same for 16-bit keys (tile codes below 2^16)
-size_t sort_u16_onepass_workspace_bytes(int64_t n);
-int launch_sort_u16_bits(const uint16_t *keys_in, const uint32_t *vals_in, int64_t n, int32_t n_tiles, int begin_bit,
-                         int end_bit, uint16_t *keys_out, uint32_t *vals_out, int32_t *ranges, void *ws,
                          size_t ws_bytes, cudaStream_t st);
 
 int launch_render_fwd(const float *rec, int64_t n, const uint32_t *vals, const int32_t *ranges,
