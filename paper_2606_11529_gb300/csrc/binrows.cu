@@ -217,24 +217,24 @@ constexpr int kColSub = kColPairs / kColWarps;      // pairs per warp's share of
 
 // Window b of the column scatter holds the spans whose first pair lies in [b P, b P + P), P = 3968,
 // and its warp w those whose first pair lies in sub-window u = 8 b + w, [u Q, u Q + Q), Q = 496:
-// first[u] = the first span at or past u Q (every span holds at most 128 < Q pairs, so at most one
-// sub-window boundary falls inside a span's pairs, right after its first); the sub-windows past
-// the last pair start at ns, as does first[8 nb].  pair0[ns + 1]: the spans' first pairs.
-__global__ void col_first_kernel(const int32_t *__restrict__ pair0, int64_t ns, int64_t nsub,
-                                 int32_t *__restrict__ first) {
-    grid_dep_wait();
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q > ns) return;
-    if (q == 0) {
-        first[0] = 0;
-        for (int64_t u = (int64_t)pair0[ns] / kColSub + 1; u < nsub; ++u) first[u] = (int32_t)ns;
-        first[nsub] = (int32_t)ns;
-        return;
+// first[u] = the first span at or past u Q, first[8 nb] = ns.  The scan of the span lengths fills
+// it as its epilogue: span j (first pair ex, v pairs) starts sub-window u = (ex + v) / Q at j + 1
+// when u Q lies in (ex, ex + v] (every span holds at most 128 < Q pairs, so at most one such u); the
+// sub-windows past the last pair start at ns.  Entries at or past cap are not written (the scan may
+// run before the pair total is checked against the workspace).
+struct ColFirstPost {
+    int32_t *first;
+    int64_t cap;
+    __device__ __forceinline__ void operator()(int64_t j, int64_t ex, int32_t v) const {
+        const int64_t u = (ex + v) / kColSub;
+        if (u * kColSub > ex && u < cap) first[u] = (int32_t)(j + 1);
     }
-    const int64_t a = pair0[q - 1], z = pair0[q];
-    const int64_t u = z / kColSub;
-    if (u < nsub && u * kColSub > a) first[u] = (int32_t)q;
-}
+    __device__ __forceinline__ void finish(int64_t ns, int64_t ni) const {
+        const int64_t nsub = (ni + kColPairs - 1) / kColPairs * kColWarps;
+        if (cap > 0) first[0] = 0;
+        for (int64_t u = ni / kColSub + 1; u <= nsub && u < cap; ++u) first[u] = (int32_t)ns;
+    }
+};
 
 // Column coverage of the spans [q0, q1) into d[0..128] as a difference array (+1 at the first kept
 // column, -1 one past the last): its prefix over the columns is the number of pairs per column.
@@ -264,20 +264,23 @@ __device__ __forceinline__ void warp_column_prefix(int *d) {
     __syncwarp();
 }
 
-// hist[tx * nb + b] = the pairs of column tx among block b's spans (tx < ncol).
+// hist[tx * nb + b] = the pairs of column tx among window b's spans (tx < ncol), one warp a window.
 __global__ void __launch_bounds__(256) col_hist_kernel(const uint32_t *__restrict__ skey,
                                                        const int32_t *__restrict__ first, int64_t nb, int ncol,
                                                        int32_t *__restrict__ hist) {
     grid_dep_wait();
-    __shared__ int d[kMaxRowGrid + 1];
-    for (int x = threadIdx.x; x <= kMaxRowGrid; x += blockDim.x) d[x] = 0;
-    __syncthreads();
-    add_span_columns(skey, first[blockIdx.x * kColWarps], first[(blockIdx.x + 1) * kColWarps], blockDim.x,
-                     threadIdx.x, d);
-    __syncthreads();
-    if (threadIdx.x < 32) warp_column_prefix(d);
-    __syncthreads();
-    for (int tx = threadIdx.x; tx < ncol; tx += blockDim.x) hist[(int64_t)tx * nb + blockIdx.x] = d[tx];
+    __shared__ int d[kColWarps][kMaxRowGrid + 1];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * kColWarps + wl;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[wl][lane + 32 * j] = 0;
+    if (lane == 0) d[wl][kMaxRowGrid] = 0;
+    __syncwarp();
+    if (b < nb) add_span_columns(skey, first[b * kColWarps], first[(b + 1) * kColWarps], 32, lane, d[wl]);
+    __syncwarp();
+    warp_column_prefix(d[wl]);
+    if (b < nb)
+        for (int tx = lane; tx < ncol; tx += 32) hist[(int64_t)tx * nb + b] = d[wl][tx];
 }
 
 // The stable pass by column over the row-grouped spans, without expanding them first: block b
@@ -722,7 +725,13 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     }
     uint32_t *skey = reinterpret_cast<uint32_t *>(p + L.skey), *sprim = reinterpret_cast<uint32_t *>(p + L.sprim);
     int32_t *pair0 = reinterpret_cast<int32_t *>(p + L.pair0);
-    s = launch_scan(SpanLenItem{skey}, pair0, ns, p + L.part_s, tot + 2, st);
+    // the first pair of every span; the spans starting each sub-window of the column scatter (its
+    // room: the region sized for the pairs when their count is known here, else what the workspace
+    // leaves after its start)
+    const int64_t first_cap = early || isect_count ? (int64_t)((L.hist - L.first) / 4)
+                                                   : (int64_t)((ws_bytes - L.first) / 4);
+    s = launch_scan(SpanLenItem{skey}, pair0, ns, p + L.part_s, tot + 2, st,
+                    ColFirstPost{reinterpret_cast<int32_t *>(p + L.first), first_cap});
     if (s != XPR_OK) return s;
     if (!isect_count) {
         if (early) {
@@ -744,18 +753,15 @@ int launch_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tc, co
     if (ni > 0) {
         const int64_t nb = col_blocks(ni);
         const int ncol = n_columns(t);
-        int32_t *first = reinterpret_cast<int32_t *>(p + LP.first);
+        const int32_t *first = reinterpret_cast<const int32_t *>(p + LP.first);
         int32_t *hist = reinterpret_cast<int32_t *>(p + LP.hist), *off = reinterpret_cast<int32_t *>(p + LP.off);
-        XPR_CUDA_TRY(launch_dependent(col_first_kernel, dim3((unsigned)((ns + 1 + 255) / 256)), dim3(256), 0, st,
-                                      (const int32_t *)pair0, ns, nb * kColWarps, first));
-        XPR_LAUNCH_CHECK("col_first_kernel");
-        XPR_CUDA_TRY(launch_dependent(col_hist_kernel, dim3((unsigned)nb), dim3(256), 0, st, (const uint32_t *)skey,
-                                      (const int32_t *)first, nb, ncol, hist));
+        XPR_CUDA_TRY(launch_dependent(col_hist_kernel, dim3((unsigned)((nb + kColWarps - 1) / kColWarps)),
+                                      dim3(256), 0, st, (const uint32_t *)skey, first, nb, ncol, hist));
         XPR_LAUNCH_CHECK("col_hist_kernel");
         s = launch_scan(CountItem{hist}, off, nb * ncol, p + LP.part_h, nullptr, st);
         if (s != XPR_OK) return s;
         XPR_CUDA_TRY(launch_dependent(col_scatter_kernel, dim3((unsigned)nb), dim3(256), 0, st, (const uint32_t *)skey,
-                                      (const uint32_t *)sprim, (const int32_t *)first, nb, ncol, (const int32_t *)off,
+                                      (const uint32_t *)sprim, first, nb, ncol, (const int32_t *)off,
                                       vals, by_code));
         XPR_LAUNCH_CHECK("col_scatter_kernel");
     }

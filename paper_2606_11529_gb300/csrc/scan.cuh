@@ -6,8 +6,9 @@
 //      consecutive items there (blocked order), the block adds its partial, and the exclusive
 //      prefixes go back out striped: every global read and write is coalesced.
 // The items come from a functor f(j) (an array, a gathered array, or a quantity computed from the
-// binning's records), so a transform that feeds a scan costs no pass of its own.  With out NULL
-// only the total is produced (steps 1 and 2).  In-place use (out aliasing the functor's input,
+// binning's records), so a transform that feeds a scan costs no pass of its own, and an epilogue
+// functor may consume each prefix in the downsweep.  With out NULL only the total is produced
+// (steps 1 and 2).  In-place use (out aliasing the functor's input,
 // position j read only for item j) is safe: a block reads its whole tile before it writes.
 #pragma once
 
@@ -84,10 +85,10 @@ __global__ void __launch_bounds__(kThreads) partials_kernel(int64_t *__restrict_
     if (threadIdx.x == 0) *total_out = carry;
 }
 
-template <class F>
+template <class F, class Post>
 __global__ void __launch_bounds__(kThreads) downsweep_kernel(F f, int32_t *out, int64_t n,
                                                              const int64_t *__restrict__ partials,
-                                                             const int64_t *__restrict__ total) {
+                                                             const int64_t *__restrict__ total, Post post) {
     grid_dep_wait();
     __shared__ int32_t s_v[kPad];
     __shared__ int64_t sw[32];
@@ -112,6 +113,8 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(F f, int32_t *out, 
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         s_v[padded(t * kItems + k)] = (int32_t)ex;
+        const int64_t j = base + t * kItems + k;
+        if (j < n) post(j, ex, v[k]);
         ex += v[k];
     }
     __syncthreads();
@@ -121,16 +124,27 @@ __global__ void __launch_bounds__(kThreads) downsweep_kernel(F f, int32_t *out, 
         const int64_t j = base + i;
         if (j < n) out[j] = s_v[padded(i)];
     }
-    if (blockIdx.x == 0 && t == 0) out[n] = (int32_t)*total;
+    if (blockIdx.x == 0 && t == 0) {
+        out[n] = (int32_t)*total;
+        post.finish(n, *total);
+    }
 }
 
 }  // namespace scan_detail
 
+// No epilogue: the default of launch_scan's post.
+struct ScanNoPost {
+    __device__ __forceinline__ void operator()(int64_t, int64_t, int32_t) const {}
+    __device__ __forceinline__ void finish(int64_t, int64_t) const {}
+};
+
 // out[j] = sum_{k<j} f(k), out[n] = total (out NULL: the total only); the total (int64) goes to
 // total_out, or to scan_total_ptr(partials, n) when total_out is NULL.  partials: at least
-// scan_partials_bytes(n) bytes.
-template <class F>
-int launch_scan(F f, int32_t *out, int64_t n, void *partials, int64_t *total_out, cudaStream_t st) {
+// scan_partials_bytes(n) bytes.  post (with out only): post(j, out[j], f(j)) runs for every item
+// once its prefix is known, and post.finish(n, total) once, in the same kernel (for n > 0).
+template <class F, class Post = ScanNoPost>
+int launch_scan(F f, int32_t *out, int64_t n, void *partials, int64_t *total_out, cudaStream_t st,
+                Post post = Post()) {
     using namespace scan_detail;
     const int64_t nb = (n + kTile - 1) / kTile;
     int64_t *part = reinterpret_cast<int64_t *>(partials);
@@ -145,8 +159,8 @@ int launch_scan(F f, int32_t *out, int64_t n, void *partials, int64_t *total_out
     XPR_CUDA_TRY(launch_dependent(partials_kernel, dim3(1), dim3(kThreads), 0, st, part, nb, tot));
     XPR_LAUNCH_CHECK("scan partials_kernel");
     if (out) {
-        XPR_CUDA_TRY(launch_dependent(downsweep_kernel<F>, dim3((unsigned)nb), dim3(kThreads), 0, st, f, out, n,
-                                      (const int64_t *)part, (const int64_t *)tot));
+        XPR_CUDA_TRY(launch_dependent(downsweep_kernel<F, Post>, dim3((unsigned)nb), dim3(kThreads), 0, st, f, out,
+                                      n, (const int64_t *)part, (const int64_t *)tot, post));
         XPR_LAUNCH_CHECK("scan downsweep_kernel");
     }
     return XPR_OK;
