@@ -226,8 +226,9 @@ struct ColFirstPost {
     int32_t *first;
     int64_t cap;
     __device__ __forceinline__ void operator()(int64_t j, int64_t ex, int32_t v) const {
-        const int64_t u = (ex + v) / kColSub;
-        if (u * kColSub > ex && u < cap) first[u] = (int32_t)(j + 1);
+        // 32-bit arithmetic: the pair offsets stay below 2^31 (checked before the pairs are placed)
+        const uint32_t e = (uint32_t)ex, u = (e + (uint32_t)v) / (uint32_t)kColSub;
+        if (u * (uint32_t)kColSub > e && (int64_t)u < cap) first[u] = (int32_t)(j + 1);
     }
     __device__ __forceinline__ void finish(int64_t ns, int64_t ni) const {
         const int64_t nsub = (ni + kColPairs - 1) / kColPairs * kColWarps;
