@@ -445,12 +445,14 @@ int xpr_bin_sorted(const float *rec, const int32_t *bbox, const int32_t *tile_co
 /* ---- Bin + sort by tile rows ------------------------------------------------
  * xpr_bin_rows: Sec. 4.2's replicate / assign tile id / cull and "sort and
  * identify bounds" for one view whose tile grid has at most 128 columns and
- * 128 rows, with one radix pass over the pairs: the row form of the cull gives
+ * 128 rows, with no radix pass over the pairs: the row form of the cull gives
  * every primitive one span of kept tile columns per row of its box; the spans
  * (about seven pairs each on the headline workload) are written grouped by row
  * in depth order (their places from a scanned count of box rows per row and
- * chunk of depth positions), expanded into pairs grouped by row, and one
- * stable pass over the pairs' column groups them by tile.  Every tile's list is bit-identical to
+ * chunk of depth positions), and a stable pass by tile column places every
+ * span's pairs straight into the tile-major lists (a column histogram per
+ * window of 3968 pairs, its scan, ranks from the spans covering each column).
+ * Every tile's list is bit-identical to
  * xpr_tile_bin in the same order followed by xpr_sort_tiles: the same kept
  * pairs (same FP32 cull), each tile's list in emission order; the tiles'
  * segments lie in column-major tile order (the ranges locate them).
@@ -488,7 +490,7 @@ int xpr_bin_rows(const float *rec, const int32_t *bbox, const int32_t *tile_coun
  * multi-view and multi-scene forms, Sec. 4.3), every grid at most 128 x 128
  * tiles: each view's or item's lists are bit-identical to xpr_tile_bin_views
  * (or the items' emission) followed by xpr_sort_tiles over all S tiles.  The
- * spans carry their item, the pass over the pairs groups them by (column, row,
+ * spans carry their item, the pass by column groups the pairs by (column, row,
  * item), and the tiles' segments lie in that order (the ranges locate them).
  *   _views: V = n_views (1..16) views of n primitives, records view-major
  *     (rec[V*n,12] ... from xpr_project_views, isect_count[V*n] or NULL,

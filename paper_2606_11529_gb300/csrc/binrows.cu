@@ -12,17 +12,20 @@
 //      with no kept tile, in bits 0-7; the first kept column in bits 8-14; the number of kept tiles
 //      in bits 15-22; the record's item in bits 23-26) and its record as the value: the spans lie
 //      as a stable sort of the depth-ordered slots by row would leave them, without the sort;
-//   3. an exclusive scan of the span lengths in that order gives every span its first pair, and
-//      the expansion writes the pairs of each span contiguously: tile code (k << 14) | (tx << 7) |
-//      ty and the record, so the pairs are grouped by tile row and, inside a row, by item in depth
-//      order (every read of these passes is a coalesced one of the grouped spans);
-//   4. one stable radix pass over the pairs by the code's column bits [7, 14): the pairs end
-//      grouped by (column, row, item), so every tile (k, tx, ty) is one contiguous run, inside it
-//      still in depth order: the tile-major depth-sorted list of Sec. 4.2 with one radix pass over
-//      the pairs instead of two (the rows were grouped on the spans, about seven pairs each here).
-// The tile ranges are found per code and permuted to the tile ids the render uses (item k's tile
-// (tx, ty) at tile0[k] + ty Wt[k] + tx).  The result is identical, list for list, to the depth-
-// ordered emission followed by the stable sort of the tile ids.
+//   3. an exclusive scan of the span lengths in that order gives every span its first pair: the
+//      pairs, were they written out, would be grouped by tile row and, inside a row, by item in
+//      depth order (tile code (k << 14) | (tx << 7) | ty); the scan's epilogue marks the first
+//      span of every 496-pair sub-window;
+//   4. the stable pass by tile column runs on the spans, without expanding them: per window of
+//      3968 pairs a histogram of the pairs per column (difference arrays over the spans' column
+//      intervals), its column-major scan, and a scatter that ranks each pair among the window's
+//      pairs of its column (masks of the spans covering each column, from XOR differences) and
+//      writes the records grouped by (column, row, item): every tile (k, tx, ty) one contiguous
+//      run, inside it still in depth order, the tile-major depth-sorted list of Sec. 4.2 with no
+//      radix pass over the pairs (about seven pairs a span here).
+// The tile ranges are found per code where the staged codes change and permuted to the tile ids
+// the render uses (item k's tile (tx, ty) at tile0[k] + ty Wt[k] + tx).  The result is identical,
+// list for list, to the depth-ordered emission followed by the stable sort of the tile ids.
 #include "cull.cuh"
 #include "scan.cuh"
 
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(256) col_scatter_kernel(const uint32_t *__rest
     }
 }
 
-struct SpanLenItem {  // scan items: the pairs of sorted span q
+struct SpanLenItem {  // scan items: the pairs of row-grouped span q
     const uint32_t *skey;
     __device__ __forceinline__ int32_t operator()(int64_t q) const { return span_len(skey[q]); }
 };
